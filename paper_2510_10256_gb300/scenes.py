@@ -1,0 +1,436 @@
+"""Seeded synthetic scenes shaped like the paper's yarn and cloth workloads.
+
+This module only *places* geometry: polylines, triangle grids, disks and random
+displacements.  It holds none of the contact method's arithmetic (no distances,
+no filter, no barrier), so both the CPU oracle and the CUDA path can take their
+inputs from here without sharing any of the method.
+
+Units are millimetres.  Positions are SoA float64 arrays of shape (3, n).
+
+Workload shapes (paper Table 1 cloth, Table 2 yarn):
+  * woven_patch   -- 8 warp + 8 weft open polylines, over/under weave (yarn, Table 2
+                     thickness range 0.18-0.5 mm; here r = 0.1, thickness 2r).
+  * pleated_sheet -- 256x256 regular triangle grid folded into tight pleats
+                     (cloth, Table 1 sizes 10k-100k triangles).
+  * graded_disk   -- graded Delaunay disk, 0.1 mm edges at the centre, 4 mm at the
+                     rim, twisted about a diameter (cloth, the graded drape of Sec. 4).
+  * rod_batch     -- 64 weave/knit rod scenes of log-uniform size.
+  * tiny scenes   -- small random meshes for property tests.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+BASE_SEED = 20251010
+
+
+@dataclass
+class Scene:
+    kind: str                      # "rod" or "shell"
+    rest: np.ndarray               # (3, n) float64 reference (undeformed) positions
+    x: np.ndarray                  # (3, n) float64 current positions
+    p: np.ndarray                  # (3, n) float64 search direction for the CCD bound
+    thickness: float               # xi: thickness offset (rods: 2r)
+    dhat: float                    # barrier width; activation a = thickness + dhat
+    rod_ptr: np.ndarray | None = None   # int32 (n_rods+1,) for rods
+    tris: np.ndarray | None = None      # int32 (3, T) for shells
+    kappa: float = 1.0
+    name: str = ""
+    seed: int = 0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.rest.shape[1])
+
+    @property
+    def activation(self) -> float:
+        return self.thickness + self.dhat
+
+
+def _soa(a: np.ndarray) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(3, -1))
+
+
+# ---------------------------------------------------------------------------
+# Rods
+# ---------------------------------------------------------------------------
+
+def woven_patch(seed: int = BASE_SEED + 1, n_warp: int = 8, n_weft: int = 8,
+                nseg: int = 256, seg: float = 0.05, r: float = 0.1,
+                spacing: float = 0.5, jitter_frac: float = 0.01,
+                dhat: float = 0.01, sigma: float = 0.02) -> Scene:
+    """Plain-weave patch of open polylines.
+
+    Warp yarn j runs along x at y = spacing*j with height r*cos(pi*x/spacing + pi*j);
+    weft yarn i runs along y at x = spacing*i with height -r*cos(pi*y/spacing + pi*i).
+    At every crossing the two centrelines are exactly 2r apart before jitter.
+    Every coordinate gets seeded uniform jitter of +-jitter_frac*r.  The jittered
+    polylines are both the reference and the current configuration.
+    """
+    rng = np.random.default_rng(seed)
+    length = nseg * seg
+    centre = 0.5 * spacing * (max(n_warp, n_weft) - 1)
+    s0 = centre - 0.5 * length
+    # snap the start to the segment lattice so that vertices land on the crossings
+    # (the spacing is a whole number of segments)
+    s0 = seg * round(s0 / seg)
+    k = np.arange(nseg + 1, dtype=np.float64)
+    coords = []
+    for j in range(n_warp):
+        xs = s0 + seg * k
+        ys = np.full_like(xs, spacing * j)
+        zs = r * np.cos(np.pi * xs / spacing + np.pi * j)
+        coords.append(np.stack([xs, ys, zs]))
+    for i in range(n_weft):
+        ys = s0 + seg * k
+        xs = np.full_like(ys, spacing * i)
+        zs = -r * np.cos(np.pi * ys / spacing + np.pi * i)
+        coords.append(np.stack([xs, ys, zs]))
+    pos = np.concatenate(coords, axis=1)
+    pos = pos + rng.uniform(-jitter_frac * r, jitter_frac * r, size=pos.shape)
+    n_rods = n_warp + n_weft
+    rod_ptr = (np.arange(n_rods + 1) * (nseg + 1)).astype(np.int32)
+    p = rng.normal(0.0, sigma, size=pos.shape)
+    pos = _soa(pos)
+    return Scene("rod", pos.copy(), pos.copy(), _soa(p), 2.0 * r, dhat, rod_ptr=rod_ptr,
+                 name="woven_patch", seed=seed,
+                 meta=dict(n_warp=n_warp, n_weft=n_weft, nseg=nseg, seg=seg, r=r,
+                           spacing=spacing, sigma=sigma))
+
+
+def _helix_row(x0: float, y0: float, n_vert: int, seg: float, radius: float,
+               pitch: float) -> np.ndarray:
+    """Helix along +x: (x0 + pitch*t/2pi, y0 + R cos t, R sin t), sampled at equal
+    parameter steps chosen so that the chord is close to `seg`."""
+    per_turn_len = math.hypot(2 * math.pi * radius, pitch)
+    dt = 2 * math.pi * seg / per_turn_len
+    t = dt * np.arange(n_vert)
+    return np.stack([x0 + pitch * t / (2 * math.pi),
+                     y0 + radius * np.cos(t), radius * np.sin(t)])
+
+
+def _min_helix_gap(radius: float, pitch: float, dy: float) -> float:
+    """Closest approach of two parallel helices, the second shifted by dy across
+    and half a pitch along the axis."""
+    t = np.linspace(0.0, 2 * math.pi, 721)
+    s = np.linspace(-2 * math.pi, 4 * math.pi, 2161)
+    a = np.stack([pitch * t / (2 * math.pi), radius * np.cos(t), radius * np.sin(t)])
+    b = np.stack([0.5 * pitch + pitch * s / (2 * math.pi),
+                  dy + radius * np.cos(s), radius * np.sin(s)])
+    d2 = ((a[:, :, None] - b[:, None, :]) ** 2).sum(0)
+    return float(np.sqrt(d2.min()))
+
+
+def knit_rows(seed: int, n_target: int, r: float, seg: float, dhat: float,
+              sigma: float) -> Scene:
+    """Interlocking-loop knit: rows of helices (radius 2r, pitch 4r) along x, each
+    row half a pitch ahead of the previous one, rows spaced so that neighbouring
+    loops pass at a seeded gap in [0.97, 1.03] x thickness."""
+    rng = np.random.default_rng(seed)
+    radius, pitch, thick = 2.0 * r, 4.0 * r, 2.0 * r
+    target = thick * rng.uniform(0.97, 1.03)
+    lo, hi = 0.0, 4.0 * radius + thick
+    for _ in range(50):
+        mid = 0.5 * (lo + hi)
+        if _min_helix_gap(radius, pitch, mid) < target:
+            lo = mid
+        else:
+            hi = mid
+    dy = hi
+    n_rows = max(2, int(round(math.sqrt(n_target / 60.0))))
+    per_row = max(8, n_target // n_rows)
+    rows = []
+    for k in range(n_rows):
+        rows.append(_helix_row(0.5 * pitch * (k % 2), dy * k, per_row, seg, radius, pitch))
+    pos = np.concatenate(rows, axis=1)
+    rod_ptr = (np.arange(n_rows + 1) * per_row).astype(np.int32)
+    p = rng.normal(0.0, sigma, size=pos.shape)
+    pos = _soa(pos)
+    return Scene("rod", pos.copy(), pos.copy(), _soa(p), thick, dhat, rod_ptr=rod_ptr,
+                 name="knit_rows", seed=seed,
+                 meta=dict(r=r, seg=seg, rows=n_rows, per_row=per_row, dy=dy))
+
+
+def weave_sized(seed: int, n_target: int, r: float, seg: float, dhat: float,
+                sigma: float) -> Scene:
+    """Plain weave with about n_target vertices: square patch, yarn spacing 5r."""
+    spacing = 5.0 * r
+    n_y = max(2, int(round(math.sqrt(n_target * seg / (2 * spacing)))))
+    nseg = max(8, int(round(n_target / (2 * n_y))) - 1)
+    # keep crossings on vertices: spacing must be a multiple of seg
+    seg = spacing / max(1, round(spacing / seg))
+    sc = woven_patch(seed=seed, n_warp=n_y, n_weft=n_y, nseg=nseg, seg=seg, r=r,
+                     spacing=spacing, dhat=dhat, sigma=sigma)
+    sc.name = "weave_sized"
+    return sc
+
+
+def rod_batch(seed: int = BASE_SEED + 4, n_scenes: int = 64, n_lo: float = 1e3,
+              n_hi: float = 6.4e4) -> list[Scene]:
+    """Batch of rod scenes: sizes log-uniform in [n_lo, n_hi] vertices, yarn radius
+    U[0.05, 0.3], segment U[0.2r, 1.0r], dhat = 0.1r; even index weave, odd knit."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_scenes):
+        n_t = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        r = float(rng.uniform(0.05, 0.3))
+        seg = float(rng.uniform(0.2 * r, 1.0 * r))
+        if i % 2 == 0:
+            sc = weave_sized(seed + 1000 + i, n_t, r, seg, 0.1 * r, sigma=0.2 * r)
+        else:
+            sc = knit_rows(seed + 1000 + i, n_t, r, seg, 0.1 * r, sigma=0.2 * r)
+        out.append(sc)
+    return out
+
+
+def straight_rod(n_seg: int = 20, seg: float = 0.1, thickness: float = 0.25,
+                 dhat: float = 0.05) -> Scene:
+    """One straight uniform polyline along x (no jitter)."""
+    xs = seg * np.arange(n_seg + 1, dtype=np.float64)
+    pos = np.stack([xs, np.zeros_like(xs), np.zeros_like(xs)])
+    return Scene("rod", pos.copy(), pos.copy(), np.zeros_like(pos), thickness, dhat,
+                 rod_ptr=np.array([0, n_seg + 1], np.int32), name="straight_rod")
+
+
+# ---------------------------------------------------------------------------
+# Shells
+# ---------------------------------------------------------------------------
+
+def grid_mesh(nx: int, ny: int, L: float) -> tuple[np.ndarray, np.ndarray]:
+    """Regular nx x ny vertex grid, centred at the origin, consistent diagonal.
+    Vertex (i, j) has index j*nx + i; each quad is split along (i,j)-(i+1,j+1)."""
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    X = (i.astype(np.float64) - 0.5 * (nx - 1)) * L
+    Y = (j.astype(np.float64) - 0.5 * (ny - 1)) * L
+    pos = np.stack([X.ravel(), Y.ravel(), np.zeros(nx * ny)])
+    qi, qj = np.meshgrid(np.arange(nx - 1), np.arange(ny - 1), indexing="xy")
+    v00 = (qj * nx + qi).ravel()
+    v10 = v00 + 1
+    v01 = v00 + nx
+    v11 = v01 + 1
+    t1 = np.stack([v00, v10, v11])
+    t2 = np.stack([v00, v11, v01])
+    tris = np.empty((3, 2 * v00.size), np.int64)
+    tris[:, 0::2] = t1
+    tris[:, 1::2] = t2
+    return pos, tris.astype(np.int32)
+
+
+def _fold_profile(s_lo: float, s_hi: float, amps, lams, phis, c: float, ds: float):
+    """Planar curve parametrised by arc length whose tangent angle is
+    theta(s) = c * sum_k (2 pi A_k / lam_k) sin(2 pi s / lam_k + phi_k)."""
+    s = np.arange(s_lo, s_hi + ds, ds)
+    th = np.zeros_like(s)
+    for A, lam, ph in zip(amps, lams, phis):
+        th += (2 * math.pi * A / lam) * np.sin(2 * math.pi * s / lam + ph)
+    th *= c
+    cx, cz = np.cos(th), np.sin(th)
+    px = np.concatenate([[0.0], np.cumsum(0.5 * (cx[1:] + cx[:-1]) * ds)])
+    pz = np.concatenate([[0.0], np.cumsum(0.5 * (cz[1:] + cz[:-1]) * ds)])
+    return s, px, pz
+
+
+def _profile_min_gap(s, px, pz, sep: float, step: int) -> float:
+    """Smallest chord between curve samples at least `sep` apart in arc length."""
+    ss, xx, zz = s[::step], px[::step], pz[::step]
+    best = np.inf
+    m = ss.size
+    for a in range(0, m, 512):
+        b = min(m, a + 512)
+        dx = xx[a:b, None] - xx[None, :]
+        dz = zz[a:b, None] - zz[None, :]
+        d = np.hypot(dx, dz)
+        far = np.abs(ss[a:b, None] - ss[None, :]) >= sep
+        if far.any():
+            best = min(best, float(d[far].min()))
+    return best
+
+
+def pleated_sheet(seed: int = BASE_SEED + 2, nx: int = 256, L: float = 0.5,
+                  thickness: float = 1.0, dhat: float = 0.05, sigma: float = 0.1,
+                  gap_lo: float = 0.9, gap_hi: float = 1.0) -> Scene:
+    """Flat nx x nx grid (rest) folded into three superposed sinusoidal pleats.
+
+    The fold keeps arc length along a seeded in-plane direction u (a developable
+    bend): the cross-section is the curve whose tangent angle is a sum of three
+    sines (amplitudes A_k in U[2,5] mm, wavelengths lam_k in U[3,8] mm, seeded
+    phases), extruded along the perpendicular direction.  A single scale c on the
+    angle is chosen by bisection so that the closest approach between curve points
+    at least one activation distance apart in arc length equals a seeded target in
+    [gap_lo, gap_hi] x thickness: folded layers come within thickness, nothing
+    intersects.  (A pure height field could never do this: projection onto the rest
+    plane shortens distances, so 3D distances would never drop below rest ones.)
+    """
+    rng = np.random.default_rng(seed)
+    rest, tris = grid_mesh(nx, nx, L)
+    amps = rng.uniform(2.0, 5.0, 3)
+    lams = rng.uniform(3.0, 8.0, 3)
+    phis = rng.uniform(0.0, 2 * math.pi, 3)
+    ang = rng.uniform(0.0, math.pi)
+    target = thickness * rng.uniform(gap_lo, gap_hi)
+    u = np.array([math.cos(ang), math.sin(ang)])
+    v = np.array([-math.sin(ang), math.cos(ang)])
+    s_v = u[0] * rest[0] + u[1] * rest[1]
+    t_v = v[0] * rest[0] + v[1] * rest[1]
+    s_lo, s_hi = float(s_v.min()) - 1.0, float(s_v.max()) + 1.0
+    act = thickness + dhat
+    ds = 0.01
+    step = 10
+
+    def gap(c):
+        s, px, pz = _fold_profile(s_lo, s_hi, amps, lams, phis, c, ds)
+        return _profile_min_gap(s, px, pz, act, step)
+
+    lo, hi = 0.0, 1.0
+    if gap(hi) >= target:
+        c = hi
+    else:
+        for _ in range(40):
+            mid = 0.5 * (lo + hi)
+            if gap(mid) > target:
+                lo = mid
+            else:
+                hi = mid
+        c = lo
+    s, px, pz = _fold_profile(s_lo, s_hi, amps, lams, phis, c, ds)
+    fx = np.interp(s_v, s, px)
+    fz = np.interp(s_v, s, pz)
+    fx -= 0.5 * (fx.max() + fx.min())
+    x = np.stack([fx * u[0] + t_v * v[0], fx * u[1] + t_v * v[1], fz])
+    p = rng.normal(0.0, sigma, size=x.shape)
+    return Scene("shell", _soa(rest), _soa(x), _soa(p), thickness, dhat, tris=tris,
+                 name="pleated_sheet", seed=seed,
+                 meta=dict(nx=nx, L=L, amps=amps.tolist(), lams=lams.tolist(),
+                           phis=phis.tolist(), angle=ang, scale=c, target_gap=target,
+                           min_gap=gap(c), sigma=sigma))
+
+
+def graded_points(R: float, L0: float, L1: float, rng: np.random.Generator,
+                  jitter: float = 0.15) -> np.ndarray:
+    """Graded point set on a disk of radius R: rings whose spacing and in-ring
+    spacing follow L(rho) = L0 + (L1 - L0) rho / R, with seeded jitter of
+    `jitter` x L in radius and angle (a cheap stand-in for graded Poisson-disk
+    sampling with the same local spacing)."""
+    pts = [np.zeros((2, 1))]
+    rho = 0.0
+    while True:
+        Lr = L0 + (L1 - L0) * rho / R
+        rho = rho + 0.8660254037844386 * Lr
+        if rho > R:
+            break
+        Lr = L0 + (L1 - L0) * rho / R
+        m = max(6, int(round(2 * math.pi * rho / Lr)))
+        th = 2 * math.pi * (np.arange(m) + rng.uniform(0, 1)) / m
+        rr = np.full(m, rho)
+        if rho < R - 0.5 * Lr:
+            rr = rr + rng.uniform(-jitter, jitter, m) * Lr
+            th = th + rng.uniform(-jitter, jitter, m) * Lr / rho
+        pts.append(np.stack([rr * np.cos(th), rr * np.sin(th)]))
+    return np.concatenate(pts, axis=1)
+
+
+def graded_disk(seed: int = BASE_SEED + 3, target_tris: int = 200_000, L0: float = 0.1,
+                L1: float = 4.0, thickness: float = 1.0, dhat: float = 0.05,
+                sigma: float = 0.1, turns: float = 1.0) -> Scene:
+    """Graded Delaunay disk (edge length L0 at the centre, L1 at the rim) twisted
+    by turns*360 degrees about the in-plane x axis, angle growing linearly along x."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(seed)
+    # points ~ 1.294 R^2 for L0=0.1, L1=4 ; triangles ~ 2x points
+    coef = 2.0 * 1.294 * (0.1 / L0) ** 0.0
+    R = math.sqrt(target_tris / coef)
+    pts = graded_points(R, L0, L1, rng)
+    tri = Delaunay(pts.T)
+    tris = np.ascontiguousarray(tri.simplices.T.astype(np.int32))
+    # orient counter-clockwise in the rest plane
+    a, b, c = pts[:, tris[0]], pts[:, tris[1]], pts[:, tris[2]]
+    cr = (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0])
+    flip = cr < 0
+    tris[1, flip], tris[2, flip] = tris[2, flip].copy(), tris[1, flip].copy()
+    rest = np.stack([pts[0], pts[1], np.zeros(pts.shape[1])])
+    xmin, xmax = rest[0].min(), rest[0].max()
+    th = 2 * math.pi * turns * (rest[0] - xmin) / (xmax - xmin)
+    x = np.stack([rest[0], rest[1] * np.cos(th), rest[1] * np.sin(th)])
+    p = rng.normal(0.0, sigma, size=x.shape)
+    return Scene("shell", _soa(rest), _soa(x), _soa(p), thickness, dhat, tris=tris,
+                 name="graded_disk", seed=seed,
+                 meta=dict(R=R, L0=L0, L1=L1, turns=turns, sigma=sigma,
+                           n_tris=int(tris.shape[1])))
+
+
+def flat_grid(nx: int = 8, L: float = 0.5, thickness: float = 1.0,
+              dhat: float = 0.05) -> Scene:
+    """Flat regular grid at rest (current = rest)."""
+    rest, tris = grid_mesh(nx, nx, L)
+    return Scene("shell", _soa(rest), _soa(rest.copy()), np.zeros_like(rest), thickness,
+                 dhat, tris=tris, name="flat_grid")
+
+
+def tiny_shell(seed: int, nx: int = 5, L: float = 0.3, thickness: float = 0.4,
+               dhat: float = 0.1, noise: float = 0.08, layers: int = 2,
+               sigma: float = 0.1) -> Scene:
+    """Small stacked grids (separate components) with seeded noise: a property-test
+    scene where cross-layer pairs, stencil neighbours and near-threshold pairs
+    all occur."""
+    rng = np.random.default_rng(seed)
+    rs, ts, off = [], [], 0
+    for k in range(layers):
+        r, t = grid_mesh(nx, nx, L)
+        r = r.copy()
+        r[2] += k * (thickness + 0.5 * dhat)
+        r[0] += rng.uniform(-L, L)
+        rs.append(r)
+        ts.append(t + off)
+        off += r.shape[1]
+    rest = np.concatenate(rs, axis=1)
+    tris = np.concatenate(ts, axis=1).astype(np.int32)
+    x = rest + rng.uniform(-noise, noise, size=rest.shape)
+    x[2] += rng.uniform(-0.5 * noise, 0.5 * noise, size=x.shape[1])
+    p = rng.normal(0.0, sigma, size=x.shape)
+    return Scene("shell", _soa(rest), _soa(x), _soa(p), thickness, dhat, tris=tris,
+                 name="tiny_shell", seed=seed)
+
+
+def tiny_rods(seed: int, n_rods: int = 3, nseg: int = 12, seg: float = 0.1,
+              thickness: float = 0.2, dhat: float = 0.05, sigma: float = 0.05) -> Scene:
+    """A few short wiggly polylines laid across each other."""
+    rng = np.random.default_rng(seed)
+    polys = []
+    for r in range(n_rods):
+        ang = rng.uniform(0, math.pi)
+        d = np.array([math.cos(ang), math.sin(ang), 0.0])
+        start = rng.uniform(-0.3, 0.3, 3) - 0.5 * nseg * seg * d
+        start[2] = (r - 0.5 * (n_rods - 1)) * (thickness + 0.3 * dhat)
+        steps = np.cumsum(np.vstack([np.zeros(3)] + [seg * d + rng.uniform(-0.3, 0.3, 3) * seg
+                                                     for _ in range(nseg)]), axis=0)
+        polys.append((start + steps).T)
+    pos = np.concatenate(polys, axis=1)
+    rod_ptr = (np.arange(n_rods + 1) * (nseg + 1)).astype(np.int32)
+    p = rng.normal(0.0, sigma, size=pos.shape)
+    pos = _soa(pos)
+    return Scene("rod", pos.copy(), pos.copy(), _soa(p), thickness, dhat, rod_ptr=rod_ptr,
+                 name="tiny_rods", seed=seed)
+
+
+# ---------------------------------------------------------------------------
+# Named configurations
+# ---------------------------------------------------------------------------
+
+def config(cid: int, reduced: bool = False) -> Scene | list[Scene]:
+    """The five workloads; `reduced` gives a small case with the same recipe."""
+    if cid == 1:
+        if reduced:
+            return woven_patch(n_warp=3, n_weft=3, nseg=64)
+        return woven_patch()
+    if cid == 2:
+        return pleated_sheet(nx=48 if reduced else 256)
+    if cid == 3:
+        return graded_disk(target_tris=6000 if reduced else 200_000,
+                           L0=0.1 if not reduced else 0.5)
+    if cid == 4:
+        return rod_batch(n_scenes=4 if reduced else 64, n_hi=4e3 if reduced else 6.4e4)
+    raise ValueError(cid)
