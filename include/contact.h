@@ -1,0 +1,190 @@
+/*
+ * contact.h -- C ABI of the GB300 barrier-filtered contact library.
+ *
+ * One contact pass of a projected-Newton iteration for thickened rods (yarn
+ * polylines) and shells (triangle meshes) under the IPC log barrier with
+ * thickness offsets, filtered against contact locking as in
+ * "Unlocking Thickness Modeling for Codimensional Contact Simulation":
+ *
+ *   contact_build   (a) broad phase at the full, unmodified activation  Sec. 3.3
+ *   contact_filter  (b) filtered / unfiltered class of every candidate  Sec. 3.2, Eq. 1/4
+ *   barrier_eval    (c) exact point-triangle / edge-edge distances,
+ *                   (d) barrier energy, gradient and PSD-projected 12x12
+ *                       Hessians assembled into a global gradient and a
+ *                       3x3-block BSR matrix                             Eq. 2-4
+ *   ccd_step        (e) conservative additive-CCD step bound with per-class
+ *                       offsets                                          Sec. 3.3
+ *
+ * Conventions
+ *   Units: millimetres.  Positions are FP64 structure-of-arrays [3][n]: all x,
+ *   then all y, then all z.  Every pass buffer lives on the GPU of the scene.
+ *   stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Calls are asynchronous on the stream unless marked "sync"; they may block
+ *   briefly to read counts the next kernel launch needs.  A scene is not
+ *   thread-safe: one caller, one stream at a time.
+ *   Errors: argument / allocation / CUDA errors return immediately.  Device-side
+ *   conditions (capacity overflow, CCD iteration limit, penetration) are
+ *   recorded in the scene's status word and returned by cb_sync_status().
+ *
+ * Pair keys (uint64): bits 63..62 type, 61..31 index i, 30..0 index j.
+ *   type 0 rod edge-edge     i < j edge ids
+ *   type 1 shell point-tri   i = vertex id, j = triangle id
+ *   type 2 shell edge-edge   i < j edge ids
+ * Edge ids: rods -- edges (v, v+1) of each polyline in order; shells -- the
+ * unique (min, max) vertex pairs of the triangles in lexicographic order.
+ * Pair lists are returned sorted by key.
+ */
+#ifndef CONTACT_H
+#define CONTACT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CB_OK = 0,
+  CB_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, bad mode) */
+  CB_ERR_OOM = 2,          /* device allocation failed */
+  CB_ERR_CAPACITY = 3,     /* a fixed-capacity buffer overflowed; results incomplete */
+  CB_ERR_PENETRATION = 4,  /* a pair is at or inside its barrier offset: energy = +inf */
+  CB_ERR_DEGENERATE = 5,   /* zero reference distance between stencil primitives */
+  CB_ERR_ITER_LIMIT = 6,   /* additive CCD hit its iteration cap: alpha is the last safe t */
+  CB_ERR_CUDA = 7          /* CUDA runtime error */
+} cb_status;
+
+#define CB_ROD 0
+#define CB_SHELL 1
+
+/* mode flags */
+#define CB_FILTER_DOUBLE 0          /* Eq. 4: filtered pairs use (offset 0, width dbar_min) */
+#define CB_FILTER_SINGLE 1          /* Eq. 1: single-phase barrier, no offset */
+#define CB_FILTER_OFF 2             /* control: no filtering (plain thickness barrier) */
+#define CB_FILTER_MASK 3
+#define CB_THICK_PAPER_LITERAL 4    /* activation a = thickness, offset = thickness - dhat */
+#define CB_NO_CORE_TEMP 8           /* disable the temporary zero offset of Sec. 3.4 */
+
+/* pair lists for cb_get_pairs */
+#define CB_PAIRS_CANDIDATE 0        /* C: broad-phase candidates */
+#define CB_PAIRS_FILTERED 1         /* candidates of class F */
+#define CB_PAIRS_CORE 2             /* candidates of class C (within the offset) */
+#define CB_PAIRS_ACTIVE 3           /* pairs with a non-zero barrier */
+#define CB_PAIRS_CCD 4              /* CCD candidates (swept boxes) */
+#define CB_PAIRS_REST_FILTERED 5    /* shells: every filtered stencil pair of the rest mesh */
+
+typedef struct cb_scene cb_scene;
+
+/* Scene description.  All pointers are HOST memory, read only during
+ * cb_scene_create (the library copies what it needs). */
+typedef struct {
+  int32_t kind;               /* CB_ROD or CB_SHELL */
+  int32_t n_verts;            /* n >= 1 */
+  const double* rest_xyz;     /* [3][n] reference (undeformed) positions */
+  int32_t n_rods;             /* rods: number of open polylines */
+  const int32_t* rod_ptr;     /* rods: [n_rods+1], polyline r = vertices [rod_ptr[r], rod_ptr[r+1]) */
+  int32_t n_tris;             /* shells: T */
+  const int32_t* tris;        /* shells: [3][T] vertex ids */
+  double thickness;           /* offset xi (eta in the paper); rods: 2 x radius */
+  double dhat;                /* barrier width; full activation a = thickness + dhat */
+  double kappa;               /* barrier stiffness (energy scale); 1 if <= 0 */
+  int32_t mode;               /* CB_FILTER_* | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP */
+} cb_scene_desc;
+
+typedef struct {
+  int64_t n_candidates;       /* |C| */
+  int64_t n_filtered;         /* candidates of class F */
+  int64_t n_core;             /* candidates of class C */
+  int64_t n_active;
+  int64_t n_ccd;              /* |C_ccd| */
+  int64_t nnzb;               /* BSR blocks */
+  int64_t n_rest_filtered;    /* shells: filtered stencil pairs of the rest mesh */
+  double dbar_min;            /* min reference distance over locking stencils (+inf if none) */
+  double offset, dhat, activation;   /* effective xi, dhat, a after the mode mapping */
+  int32_t status_bits;        /* device status word: 1 capacity, 2 penetration, 4 iteration limit */
+  int32_t ccd_max_iters;
+  int64_t device_bytes;       /* device memory held by the scene */
+} cb_stats;
+
+/* Create a scene: uploads topology and rest positions, derives edges and
+ * components, and precomputes the filter tables of Sec. 3.2 on the GPU
+ * (rods: arc-length windows; shells: every stencil pair of the rest mesh
+ * closer than the activation) and dbar_min.  sync.
+ * Errors: CB_ERR_ARG (bad sizes / indices), CB_ERR_DEGENERATE (zero
+ * reference distance), CB_ERR_OOM, CB_ERR_CUDA.  *out is set only on CB_OK. */
+cb_status cb_scene_create(const cb_scene_desc* desc, void* stream, cb_scene** out);
+
+/* Release every device buffer of the scene.  sync on the scene's last stream. */
+cb_status cb_scene_destroy(cb_scene* scene);
+
+/* (a) Broad phase, Sec. 3.3: every non-incident primitive pair (shells:
+ * point-triangle and edge-edge; rods: edge-edge) whose FP64 bounding boxes of
+ * x, each inflated by a/2, overlap (closed intervals).  Runs an FP32 spatial
+ * hash with outward-rounded boxes (a provable superset) and decides ambiguous
+ * pairs in FP64.  x_dev: DEVICE [3][n] FP64, read during the call's kernels.
+ * Result (scene-owned, sorted by key) is the input of the next three calls. */
+cb_status contact_build(cb_scene* scene, const double* x_dev, void* stream);
+
+/* (b) Barrier filter, Sec. 3.2 / Eq. 1, 4: class F for a candidate whose
+ * primitives belong to one component and whose reference distance is below
+ * the activation, U otherwise.  Uses the tables built at create. */
+cb_status contact_filter(cb_scene* scene, void* stream);
+
+/* (c)+(d) Distances, barrier, derivatives and assembly, Eq. 2-4.
+ * Per candidate: exact FP64 distance d; class C (temporary zero offset,
+ * Sec. 3.4) for an unfiltered pair with d <= offset; pair parameters
+ * U (xi, dhat), F (0, dbar_min), C (0, a) (single mode: U (0, a)); active iff
+ * y = d - xi_p < dhat_p.  For active pairs: b(y, dhat_p), its gradient and
+ * the PSD projection of kappa (b'' grad d grad d^T + b' hess d).
+ * energy_dev: DEVICE 1 double (overwritten).  grad_dev: DEVICE [3][n]
+ * (overwritten).  Either may be NULL.  The BSR matrix (full symmetric, sorted
+ * columns, 3x3 row-major blocks) is scene-owned: cb_get_bsr / cb_bsr_device.
+ * A pair at or inside its offset sets CB_ERR_PENETRATION and energy = +inf. */
+cb_status barrier_eval(cb_scene* scene, const double* x_dev, double* energy_dev, double* grad_dev,
+                       void* stream);
+
+/* (e) CCD step bound, Sec. 3.3: candidates are pairs whose swept boxes (x and
+ * x + p) inflated by offset/2 overlap; each is bounded by additive CCD
+ * (s = 0.1, inner factor 0.9) against its class offset (U: offset; F, C: 0).
+ * alpha_dev: DEVICE 1 double = min(1, min_p t_p) (overwritten).
+ * p_dev: DEVICE [3][n] search direction. */
+cb_status ccd_step(cb_scene* scene, const double* x_dev, const double* p_dev, double* alpha_dev,
+                   void* stream);
+
+/* sync getters.  Each copies to HOST buffers of capacity `cap` elements and
+ * writes the full count to *count (CB_ERR_CAPACITY if cap is too small). */
+cb_status cb_get_pairs(cb_scene* scene, int32_t which, uint64_t* keys, int64_t cap, int64_t* count);
+/* active pairs in key order: key, distance, class (0 U, 1 F, 2 C), distance type */
+cb_status cb_get_active(cb_scene* scene, uint64_t* keys, double* d, uint8_t* klass, int8_t* dtype,
+                        int64_t cap, int64_t* count);
+/* per CCD candidate (key order): time of impact bound t_p and class */
+cb_status cb_get_ccd(cb_scene* scene, uint64_t* keys, double* t, uint8_t* klass, int64_t cap,
+                     int64_t* count);
+/* BSR: row_ptr [n+1], col [nnzb], val [nnzb][9] */
+cb_status cb_get_bsr(cb_scene* scene, int32_t* row_ptr, int32_t* col, double* val, int64_t cap,
+                     int64_t* nnzb);
+/* device pointers of the scene-owned BSR (valid until the next barrier_eval) */
+cb_status cb_bsr_device(cb_scene* scene, const int32_t** row_ptr, const int32_t** col,
+                        const double** val, int64_t* nnzb);
+cb_status cb_get_stats(cb_scene* scene, cb_stats* stats);
+/* sync: first device-side condition since the last call (then cleared) */
+cb_status cb_sync_status(cb_scene* scene);
+
+/* Per-stage device times in milliseconds of the last calls (CUDA events):
+ * [0] contact_build, [1] contact_filter, [2] barrier_eval, [3] ccd_step,
+ * [4] barrier_eval Hessian kernel alone.  sync. */
+cb_status cb_get_stage_ms(cb_scene* scene, float* ms5);
+/* enable (1) / disable (0) the stage events; default off */
+cb_status cb_set_timing(cb_scene* scene, int32_t on);
+
+const char* cb_status_str(cb_status s);
+/* process-wide number of CUDA kernels the library has launched so far */
+int64_t cb_kernel_launches(void);
+/* library version string */
+const char* cb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -288,11 +288,11 @@ class PassResult:
     energy: float
     pair_energy: np.ndarray  # per active pair
     grad: np.ndarray         # (3, n)
-    grad_abs: np.ndarray     # (3, n) sum of |contributions|
+    grad_abs: np.ndarray     # (3, n) tolerance scale: sum of |contributions| (floored per pair)
     bsr_row_ptr: np.ndarray
     bsr_col: np.ndarray
     bsr_val: np.ndarray      # (nnzb, 3, 3)
-    bsr_abs: np.ndarray      # (nnzb, 3, 3)
+    bsr_abs: np.ndarray      # (nnzb, 3, 3) tolerance scale, as grad_abs
     penetration: bool
     ccd_keys: np.ndarray | None = None
     ccd_klass: np.ndarray | None = None
@@ -374,17 +374,22 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     grad_abs = np.zeros((3, n))
     gi = (np.arange(3)[None, None, :] * n + st[:, :, None]).reshape(-1)
     np.add.at(grad.reshape(-1), gi, g.reshape(-1))
-    np.add.at(grad_abs.reshape(-1), gi, np.abs(g).reshape(-1))
+    # tolerance scale: |contribution|, floored at 1e-4 of the pair's largest
+    # entry (rounding of a pair's derivatives is relative to its norm)
+    gfloor = 1e-4 * np.abs(g).max(axis=1, keepdims=True) if na else np.zeros((0, 1))
+    np.add.at(grad_abs.reshape(-1), gi, np.maximum(np.abs(g), gfloor).reshape(-1))
     rows = np.repeat(st, 4, axis=1).reshape(-1)                  # r of (i, j)
     cols = np.tile(st, (1, 4)).reshape(-1)                       # c of (i, j)
     blk = H.reshape(na, 4, 3, 4, 3).transpose(0, 1, 3, 2, 4).reshape(-1, 3, 3)
+    hfloor = 1e-4 * np.abs(H).max(axis=1) if na else np.zeros(0)
+    blk_scale = np.maximum(np.abs(blk), np.repeat(hfloor, 16)[:, None, None])
     bkey = rows * n + cols
     ukeys, inv = np.unique(bkey, return_inverse=True)
     nnzb = ukeys.size
     val = np.zeros((nnzb, 3, 3))
     vab = np.zeros((nnzb, 3, 3))
     np.add.at(val, inv, blk)
-    np.add.at(vab, inv, np.abs(blk))
+    np.add.at(vab, inv, blk_scale)
     brow = (ukeys // n).astype(np.int64)
     bcol = (ukeys % n).astype(np.int32)
     row_ptr = np.zeros(n + 1, np.int64)

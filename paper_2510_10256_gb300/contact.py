@@ -1,0 +1,261 @@
+"""Thin ctypes binding of libcontact.so (include/contact.h).
+
+Argument marshalling only: every stage of the pass runs in the library's CUDA
+kernels.  Device buffers are torch CUDA tensors (FP64, SoA [3][n]); streams are
+torch streams.  There is no CPU fallback: if the library cannot be loaded the
+import of the pass functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcontact.so")
+_lib = None
+
+CB_OK, CB_ERR_ARG, CB_ERR_OOM, CB_ERR_CAPACITY, CB_ERR_PENETRATION, CB_ERR_DEGENERATE, \
+    CB_ERR_ITER_LIMIT, CB_ERR_CUDA = range(8)
+CB_ROD, CB_SHELL = 0, 1
+CB_FILTER_DOUBLE, CB_FILTER_SINGLE, CB_FILTER_OFF = 0, 1, 2
+CB_THICK_PAPER_LITERAL = 4
+CB_NO_CORE_TEMP = 8
+PAIRS = {"candidate": 0, "filtered": 1, "core": 2, "active": 3, "ccd": 4, "rest_filtered": 5}
+MODES = {"double": CB_FILTER_DOUBLE, "single": CB_FILTER_SINGLE, "off": CB_FILTER_OFF}
+
+# names declared in include/contact.h (the tests check the library exports each)
+ABI_FUNCTIONS = ["cb_scene_create", "cb_scene_destroy", "contact_build", "contact_filter", "barrier_eval",
+                 "ccd_step", "cb_get_pairs", "cb_get_active", "cb_get_ccd", "cb_get_bsr", "cb_bsr_device",
+                 "cb_get_stats", "cb_sync_status", "cb_get_stage_ms", "cb_set_timing", "cb_status_str",
+                 "cb_version", "cb_kernel_launches"]
+
+
+class ContactError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_str(status)} ({status})")
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_verts", C.c_int32), ("rest_xyz", C.c_void_p),
+                ("n_rods", C.c_int32), ("rod_ptr", C.c_void_p), ("n_tris", C.c_int32),
+                ("tris", C.c_void_p), ("thickness", C.c_double), ("dhat", C.c_double),
+                ("kappa", C.c_double), ("mode", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_candidates", C.c_int64), ("n_filtered", C.c_int64), ("n_core", C.c_int64),
+                ("n_active", C.c_int64), ("n_ccd", C.c_int64), ("nnzb", C.c_int64),
+                ("n_rest_filtered", C.c_int64), ("dbar_min", C.c_double), ("offset", C.c_double),
+                ("dhat", C.c_double), ("activation", C.c_double), ("status_bits", C.c_int32),
+                ("ccd_max_iters", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+def build(force: bool = False) -> str:
+    from . import build as _b
+    return _b.build(force=force)
+
+
+def lib():
+    """Load libcontact.so (raises OSError if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"contact library not built: {LIB_PATH} (run paper_2510_10256_gb300.build)")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        for name in ABI_FUNCTIONS:
+            getattr(L, name).restype = i32
+        L.cb_status_str.restype = C.c_char_p
+        L.cb_status_str.argtypes = [i32]
+        L.cb_version.restype = C.c_char_p
+        L.cb_kernel_launches.restype = i64
+        L.cb_kernel_launches.argtypes = []
+        L.cb_scene_create.argtypes = [C.POINTER(SceneDesc), vp, C.POINTER(vp)]
+        L.cb_scene_destroy.argtypes = [vp]
+        L.contact_build.argtypes = [vp, vp, vp]
+        L.contact_filter.argtypes = [vp, vp]
+        L.barrier_eval.argtypes = [vp, vp, vp, vp, vp]
+        L.ccd_step.argtypes = [vp, vp, vp, vp, vp]
+        L.cb_get_pairs.argtypes = [vp, i32, vp, i64, C.POINTER(i64)]
+        L.cb_get_active.argtypes = [vp, vp, vp, vp, vp, i64, C.POINTER(i64)]
+        L.cb_get_ccd.argtypes = [vp, vp, vp, vp, i64, C.POINTER(i64)]
+        L.cb_get_bsr.argtypes = [vp, vp, vp, vp, i64, C.POINTER(i64)]
+        L.cb_bsr_device.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
+        L.cb_get_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.cb_sync_status.argtypes = [vp]
+        L.cb_get_stage_ms.argtypes = [vp, C.POINTER(C.c_float)]
+        L.cb_set_timing.argtypes = [vp, i32]
+        _lib = L
+    return _lib
+
+
+def kernel_launches() -> int:
+    return int(lib().cb_kernel_launches())
+
+
+def status_str(s: int) -> str:
+    try:
+        return lib().cb_status_str(int(s)).decode()
+    except OSError:
+        return f"status {s}"
+
+
+def _check(status: int, where: str):
+    if status != CB_OK:
+        raise ContactError(status, where)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _dev_ptr(t, n: int | None = None, shape3: bool = True):
+    import torch
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA float64 tensor")
+    if shape3 and n is not None and t.numel() != 3 * n:
+        raise ValueError(f"expected 3*n = {3 * n} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+class ContactScene:
+    """A scene of the contact library: topology, rest mesh, filter tables and
+    the pass buffers, resident on the current CUDA device."""
+
+    def __init__(self, kind: str, rest, thickness: float, dhat: float, rod_ptr=None, tris=None,
+                 kappa: float = 1.0, mode: str = "double", paper_literal: bool = False,
+                 core_temp: bool = True, stream=None):
+        L = lib()
+        rest = np.ascontiguousarray(np.asarray(rest, np.float64).reshape(3, -1))
+        self.n = rest.shape[1]
+        self._keep = [rest]
+        d = SceneDesc()
+        d.kind = CB_ROD if kind == "rod" else CB_SHELL
+        d.n_verts = self.n
+        d.rest_xyz = rest.ctypes.data
+        if kind == "rod":
+            rp = np.ascontiguousarray(np.asarray(rod_ptr, np.int32))
+            self._keep.append(rp)
+            d.n_rods = rp.size - 1
+            d.rod_ptr = rp.ctypes.data
+        else:
+            tr = np.ascontiguousarray(np.asarray(tris, np.int32).reshape(3, -1))
+            self._keep.append(tr)
+            d.n_tris = tr.shape[1]
+            d.tris = tr.ctypes.data
+        d.thickness = float(thickness)
+        d.dhat = float(dhat)
+        d.kappa = float(kappa)
+        d.mode = MODES[mode] | (CB_THICK_PAPER_LITERAL if paper_literal else 0) | \
+            (0 if core_temp else CB_NO_CORE_TEMP)
+        h = C.c_void_p()
+        _check(L.cb_scene_create(C.byref(d), _stream_ptr(stream), C.byref(h)), "cb_scene_create")
+        self.h = h
+        self.kind = kind
+
+    @classmethod
+    def from_scene(cls, sc, mode: str = "double", **kw) -> "ContactScene":
+        return cls(sc.kind, sc.rest, sc.thickness, sc.dhat, rod_ptr=sc.rod_ptr, tris=sc.tris,
+                   kappa=sc.kappa, mode=mode, **kw)
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().cb_scene_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------- pass calls
+    def contact_build(self, x, stream=None):
+        _check(lib().contact_build(self.h, _dev_ptr(x, self.n), _stream_ptr(stream)), "contact_build")
+
+    def contact_filter(self, stream=None):
+        _check(lib().contact_filter(self.h, _stream_ptr(stream)), "contact_filter")
+
+    def barrier_eval(self, x, energy=None, grad=None, stream=None):
+        _check(lib().barrier_eval(self.h, _dev_ptr(x, self.n), _dev_ptr(energy, None, False),
+                                  _dev_ptr(grad, self.n), _stream_ptr(stream)), "barrier_eval")
+
+    def ccd_step(self, x, p, alpha=None, stream=None):
+        _check(lib().ccd_step(self.h, _dev_ptr(x, self.n), _dev_ptr(p, self.n),
+                              _dev_ptr(alpha, None, False), _stream_ptr(stream)), "ccd_step")
+
+    def run_pass(self, x, p, energy, grad, alpha, stream=None):
+        """Stages a-e in order on one stream."""
+        self.contact_build(x, stream)
+        self.contact_filter(stream)
+        self.barrier_eval(x, energy, grad, stream)
+        self.ccd_step(x, p, alpha, stream)
+
+    # -------------------------------------------------------------- getters
+    def pairs(self, which: str = "candidate") -> np.ndarray:
+        cnt = C.c_int64()
+        lib().cb_get_pairs(self.h, PAIRS[which], None, 0, C.byref(cnt))
+        out = np.zeros(cnt.value, np.uint64)
+        _check(lib().cb_get_pairs(self.h, PAIRS[which], out.ctypes.data if out.size else None, out.size,
+                                  C.byref(cnt)), "cb_get_pairs")
+        return out
+
+    def active(self) -> dict:
+        cnt = C.c_int64()
+        lib().cb_get_active(self.h, None, None, None, None, 0, C.byref(cnt))
+        m = cnt.value
+        k = np.zeros(m, np.uint64)
+        d = np.zeros(m)
+        c = np.zeros(m, np.uint8)
+        t = np.zeros(m, np.int8)
+        if m:
+            _check(lib().cb_get_active(self.h, k.ctypes.data, d.ctypes.data, c.ctypes.data, t.ctypes.data, m,
+                                       C.byref(cnt)), "cb_get_active")
+        return dict(keys=k, d=d, klass=c, dtype=t)
+
+    def ccd(self) -> dict:
+        cnt = C.c_int64()
+        lib().cb_get_ccd(self.h, None, None, None, 0, C.byref(cnt))
+        m = cnt.value
+        k = np.zeros(m, np.uint64)
+        t = np.zeros(m)
+        c = np.zeros(m, np.uint8)
+        if m:
+            _check(lib().cb_get_ccd(self.h, k.ctypes.data, t.ctypes.data, c.ctypes.data, m, C.byref(cnt)),
+                   "cb_get_ccd")
+        return dict(keys=k, t=t, klass=c)
+
+    def bsr(self):
+        cnt = C.c_int64()
+        lib().cb_get_bsr(self.h, None, None, None, 0, C.byref(cnt))
+        m = cnt.value
+        rp = np.zeros(self.n + 1, np.int32)
+        col = np.zeros(m, np.int32)
+        val = np.zeros((m, 3, 3))
+        _check(lib().cb_get_bsr(self.h, rp.ctypes.data, col.ctypes.data if m else None,
+                                val.ctypes.data if m else None, m, C.byref(cnt)), "cb_get_bsr")
+        return rp, col, val
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().cb_get_stats(self.h, C.byref(s)), "cb_get_stats")
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def sync_status(self) -> int:
+        return int(lib().cb_sync_status(self.h))
+
+    def set_timing(self, on: bool = True):
+        _check(lib().cb_set_timing(self.h, int(on)), "cb_set_timing")
+
+    def stage_ms(self) -> list[float]:
+        ms = (C.c_float * 5)()
+        _check(lib().cb_get_stage_ms(self.h, ms), "cb_get_stage_ms")
+        return [float(v) for v in ms]

@@ -1,0 +1,451 @@
+// api.cu -- C ABI of the contact library: scene lifetime, the four pass calls,
+// getters.  Host code only orchestrates; every stage runs in the kernels of
+// broad.cu, narrow.cu and ccd.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "scene.cuh"
+
+#include <atomic>
+static std::atomic<long long> g_launches{0};
+long long cb_launch_counter_add() { return g_launches.fetch_add(1, std::memory_order_relaxed) + 1; }
+
+cb_status buf_ensure(DevBuf& b, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return CB_OK;
+  if (b.p) cudaFreeAsync(b.p, st);
+  b.p = nullptr;
+  b.bytes = 0;
+  size_t want = bytes + bytes / 4 + 256;
+  if (cudaMallocAsync(&b.p, want, st) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return CB_ERR_OOM;
+  }
+  b.bytes = want;
+  return CB_OK;
+}
+
+void buf_free(DevBuf& b, cudaStream_t st) {
+  if (b.p) cudaFreeAsync(b.p, st);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+cb_status read_scalars(cb_scene* s, int first, int count, uint64_t* out, cudaStream_t st) {
+  CB_CUDA(cudaMemcpyAsync(s->h_pinned, scalars(s) + first, sizeof(uint64_t) * count, cudaMemcpyDeviceToHost, st));
+  CB_CUDA(cudaStreamSynchronize(st));
+  memcpy(out, s->h_pinned, sizeof(uint64_t) * count);
+  return CB_OK;
+}
+
+static int bits_needed(int64_t max_value) {
+  int b = 1;
+  while ((1ll << b) <= max_value) ++b;
+  return b;
+}
+
+template <typename T>
+static cb_status upload(DevBuf& b, const T* h, size_t count, cudaStream_t st) {
+  CB_TRY(buf_ensure(b, sizeof(T) * std::max<size_t>(count, 1), st));
+  if (count) CB_CUDA(cudaMemcpyAsync(b.p, h, sizeof(T) * count, cudaMemcpyHostToDevice, st));
+  return CB_OK;
+}
+
+static void scene_release(cb_scene* s) {
+  cudaStream_t st = s->last_stream;
+  DevBuf* bufs[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->frest,
+                    &s->frest_dbar, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
+                    &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col, &s->bsr_val,
+                    &s->row_cnt, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->scan_tmp, &s->hist, &s->dev_scalars};
+  for (DevBuf* b : bufs) buf_free(*b, st);
+  for (BroadWork* w : {&s->bw, &s->bwc}) {
+    DevBuf* wb[] = {&w->box32,   &w->box64,  &w->bounds,   &w->cell_cnt, &w->cell_off, &w->ekey[0], &w->ekey[1],
+                    &w->eval[0], &w->eval[1], &w->run_flag, &w->run_id,   &w->run_start, &w->pair_cnt,
+                    &w->pair_off, &w->ckey[0], &w->ckey[1],  &w->scan_tmp, &w->hist};
+    for (DevBuf* b : wb) buf_free(*b, st);
+  }
+  cudaStreamSynchronize(st);
+  if (s->h_pinned) cudaFreeHost(s->h_pinned);
+  for (auto& e : s->ev)
+    if (e) cudaEventDestroy(e);
+  delete s;
+}
+
+template <typename T>
+static cb_status dl(std::vector<T>& h, const DevBuf& b, int64_t count, cudaStream_t st) {
+  h.resize((size_t)count);
+  if (count) CB_CUDA(cudaMemcpyAsync(h.data(), b.p, sizeof(T) * (size_t)count, cudaMemcpyDeviceToHost, st));
+  return CB_OK;
+}
+
+extern "C" {
+
+int64_t cb_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+const char* cb_version(void) { return "gb300-contact 0.1 (sm_103a)"; }
+
+const char* cb_status_str(cb_status st) {
+  switch (st) {
+    case CB_OK: return "ok";
+    case CB_ERR_ARG: return "invalid argument";
+    case CB_ERR_OOM: return "device allocation failed";
+    case CB_ERR_CAPACITY: return "buffer capacity exceeded";
+    case CB_ERR_PENETRATION: return "pair at or inside its barrier offset";
+    case CB_ERR_DEGENERATE: return "zero reference distance between stencil primitives";
+    case CB_ERR_ITER_LIMIT: return "additive CCD iteration limit reached";
+    case CB_ERR_CUDA: return "CUDA runtime error";
+  }
+  return "unknown status";
+}
+
+cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) {
+  if (!d || !out || !d->rest_xyz || d->n_verts < 1) return CB_ERR_ARG;
+  if (d->kind != CB_ROD && d->kind != CB_SHELL) return CB_ERR_ARG;
+  if (!(d->dhat > 0.0) || !(d->thickness >= 0.0) || !std::isfinite(d->thickness) || !std::isfinite(d->dhat))
+    return CB_ERR_ARG;
+  const int fm = d->mode & CB_FILTER_MASK;
+  if (fm == 3 || (d->mode & ~(CB_FILTER_MASK | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP))) return CB_ERR_ARG;
+  const int n = d->n_verts;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int32_t> e0, e1, comp(n);
+  std::vector<int32_t> tris;
+  int T = 0;
+  if (d->kind == CB_ROD) {
+    if (d->n_rods < 1 || !d->rod_ptr) return CB_ERR_ARG;
+    for (int r = 0; r < d->n_rods; ++r)
+      if (d->rod_ptr[r] < 0 || d->rod_ptr[r + 1] < d->rod_ptr[r] || d->rod_ptr[r + 1] > n) return CB_ERR_ARG;
+    for (int v = 0; v < n; ++v) comp[v] = -1 - v;
+    for (int r = 0; r < d->n_rods; ++r) {
+      for (int v = d->rod_ptr[r]; v < d->rod_ptr[r + 1]; ++v) comp[v] = r;
+      for (int v = d->rod_ptr[r]; v + 1 < d->rod_ptr[r + 1]; ++v) {
+        e0.push_back(v);
+        e1.push_back(v + 1);
+      }
+    }
+  } else {
+    T = d->n_tris;
+    if (T < 0 || (T > 0 && !d->tris)) return CB_ERR_ARG;
+    tris.assign(d->tris, d->tris + 3 * (size_t)T);
+    std::vector<uint64_t> ek;
+    ek.reserve(3 * (size_t)T);
+    for (int t = 0; t < T; ++t) {
+      int a = tris[t], b = tris[T + t], c = tris[2 * T + t];
+      if (a < 0 || b < 0 || c < 0 || a >= n || b >= n || c >= n || a == b || b == c || a == c) return CB_ERR_ARG;
+      int vv[3] = {a, b, c};
+      for (int k = 0; k < 3; ++k) {
+        int p = vv[k], q = vv[(k + 1) % 3];
+        ek.push_back((uint64_t)std::min(p, q) * (uint64_t)n + (uint64_t)std::max(p, q));
+      }
+    }
+    std::sort(ek.begin(), ek.end());
+    ek.erase(std::unique(ek.begin(), ek.end()), ek.end());
+    for (uint64_t k : ek) {
+      e0.push_back((int32_t)(k / n));
+      e1.push_back((int32_t)(k % n));
+    }
+    std::vector<int32_t> parent(n);
+    std::iota(parent.begin(), parent.end(), 0);
+    auto find = [&](int i) {
+      while (parent[i] != i) {
+        parent[i] = parent[parent[i]];
+        i = parent[i];
+      }
+      return i;
+    };
+    for (size_t k = 0; k < e0.size(); ++k) {
+      int ra = find(e0[k]), rb = find(e1[k]);
+      if (ra != rb) parent[std::max(ra, rb)] = std::min(ra, rb);
+    }
+    for (int v = 0; v < n; ++v) comp[v] = find(v);
+  }
+  const int E = (int)e0.size();
+  cb_scene* s = new cb_scene();
+  s->kind = d->kind;
+  s->n = n;
+  s->E = E;
+  s->T = T;
+  s->n_rods = d->kind == CB_ROD ? d->n_rods : 0;
+  s->n_prims = d->kind == CB_ROD ? E : n + T + E;
+  if (d->kind == CB_ROD) {
+    s->bits_i = s->bits_j = bits_needed(std::max(E - 1, 1));
+  } else {
+    s->bits_i = bits_needed(std::max(std::max(n, E) - 1, 1));
+    s->bits_j = bits_needed(std::max(std::max(T, E) - 1, 1));
+  }
+  if (s->bits_i > 31 || s->bits_j > 31) {
+    delete s;
+    return CB_ERR_ARG;
+  }
+  s->filter = fm;
+  s->core_temp = (d->mode & CB_NO_CORE_TEMP) ? 0 : 1;
+  if (d->mode & CB_THICK_PAPER_LITERAL) {
+    s->a = d->thickness;
+    s->xi = d->thickness - d->dhat;
+    if (s->xi < 0.0) {
+      delete s;
+      return CB_ERR_ARG;
+    }
+  } else {
+    s->xi = d->thickness;
+    s->a = d->thickness + d->dhat;
+  }
+  s->dhat = d->dhat;
+  s->kappa = d->kappa > 0.0 ? d->kappa : 1.0;
+  s->cell_hint = 1.0f;
+  s->last_stream = st;
+  cudaGetDevice(&s->device);
+  cb_status rc = CB_OK;
+  auto fail = [&](cb_status e) {
+    scene_release(s);
+    return e;
+  };
+  if (cudaMallocHost((void**)&s->h_pinned, 64 * sizeof(uint64_t)) != cudaSuccess) return fail(CB_ERR_OOM);
+  if ((rc = buf_ensure(s->dev_scalars, SC_N * sizeof(uint64_t), st)) != CB_OK) return fail(rc);
+  if (cudaMemsetAsync(s->dev_scalars.p, 0, SC_N * sizeof(uint64_t), st) != cudaSuccess) return fail(CB_ERR_CUDA);
+  if ((rc = upload(s->ev0, e0.data(), e0.size(), st)) != CB_OK) return fail(rc);
+  if ((rc = upload(s->ev1, e1.data(), e1.size(), st)) != CB_OK) return fail(rc);
+  if ((rc = upload(s->tv, tris.data(), tris.size(), st)) != CB_OK) return fail(rc);
+  if ((rc = upload(s->comp, comp.data(), comp.size(), st)) != CB_OK) return fail(rc);
+  if ((rc = upload(s->rest, d->rest_xyz, 3 * (size_t)n, st)) != CB_OK) return fail(rc);
+  if (d->kind == CB_ROD && (rc = upload(s->rod_ptr, d->rod_ptr, (size_t)d->n_rods + 1, st)) != CB_OK) return fail(rc);
+  if (d->kind == CB_ROD && (rc = buf_ensure(s->frest, 16, st)) != CB_OK) return fail(rc);
+  if (d->kind == CB_SHELL && (rc = buf_ensure(s->win, 16, st)) != CB_OK) return fail(rc);
+  for (auto& e : s->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(CB_ERR_CUDA);
+  if ((rc = filter_precompute(s, st)) != CB_OK) return fail(rc);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CB_ERR_CUDA);
+  *out = s;
+  return CB_OK;
+}
+
+cb_status cb_scene_destroy(cb_scene* s) {
+  if (!s) return CB_ERR_ARG;
+  scene_release(s);
+  return CB_OK;
+}
+
+static void stage_begin(cb_scene* s, int k, cudaStream_t st) {
+  if (s->timing) cudaEventRecord(s->ev[2 * k], st);
+}
+static void stage_end(cb_scene* s, int k, cudaStream_t st) {
+  if (s->timing) cudaEventRecord(s->ev[2 * k + 1], st);
+}
+
+cb_status contact_build(cb_scene* s, const double* x, void* stream) {
+  if (!s || !x) return CB_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  s->last_stream = st;
+  stage_begin(s, 0, st);
+  cb_status r = broad_phase(s, s->bw, x, nullptr, 0.5 * s->a, s->cand, &s->n_cand, st);
+  stage_end(s, 0, st);
+  s->n_active = 0;
+  return r;
+}
+
+cb_status contact_filter(cb_scene* s, void* stream) {
+  if (!s) return CB_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  s->last_stream = st;
+  stage_begin(s, 1, st);
+  cb_status r = filter_apply(s, st);
+  stage_end(s, 1, st);
+  return r;
+}
+
+cb_status barrier_eval(cb_scene* s, const double* x, double* energy, double* grad, void* stream) {
+  if (!s || !x) return CB_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  s->last_stream = st;
+  stage_begin(s, 2, st);
+  cb_status r = barrier_run(s, x, energy, grad, st);
+  stage_end(s, 2, st);
+  return r;
+}
+
+cb_status ccd_step(cb_scene* s, const double* x, const double* p, double* alpha, void* stream) {
+  if (!s || !x || !p) return CB_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  s->last_stream = st;
+  stage_begin(s, 3, st);
+  cb_status r = ccd_run(s, x, p, alpha, st);
+  stage_end(s, 3, st);
+  return r;
+}
+
+cb_status cb_set_timing(cb_scene* s, int32_t on) {
+  if (!s) return CB_ERR_ARG;
+  s->timing = on != 0;
+  return CB_OK;
+}
+
+cb_status cb_get_stage_ms(cb_scene* s, float* ms) {
+  if (!s || !ms) return CB_ERR_ARG;
+  CB_CUDA(cudaStreamSynchronize(s->last_stream));
+  for (int k = 0; k < 4; ++k) {
+    ms[k] = 0.f;
+    if (s->timing) cudaEventElapsedTime(&ms[k], s->ev[2 * k], s->ev[2 * k + 1]);
+  }
+  ms[4] = 0.f;
+  if (s->timing && s->n_active > 0) cudaEventElapsedTime(&ms[4], s->ev[10], s->ev[11]);
+  cudaGetLastError();
+  return CB_OK;
+}
+
+cb_status cb_get_pairs(cb_scene* s, int32_t which, uint64_t* keys, int64_t cap, int64_t* count) {
+  if (!s || !count) return CB_ERR_ARG;
+  cudaStream_t st = s->last_stream;
+  std::vector<uint64_t> k;
+  std::vector<uint8_t> c;
+  std::vector<uint32_t> ai;
+  std::vector<uint64_t> res;
+  switch (which) {
+    case CB_PAIRS_CANDIDATE: CB_TRY(dl(res, s->cand, s->n_cand, st)); break;
+    case CB_PAIRS_FILTERED:
+      CB_TRY(dl(k, s->cand, s->n_cand, st));
+      CB_TRY(dl(c, s->klass, s->n_cand, st));
+      CB_CUDA(cudaStreamSynchronize(st));
+      for (size_t i = 0; i < k.size(); ++i)
+        if (c[i] == 1) res.push_back(k[i]);
+      break;
+    case CB_PAIRS_CORE:
+      CB_TRY(dl(k, s->cand, s->n_cand, st));
+      CB_TRY(dl(c, s->ccls, s->n_cand, st));
+      CB_CUDA(cudaStreamSynchronize(st));
+      for (size_t i = 0; i < k.size(); ++i)
+        if (c[i] == 2) res.push_back(k[i]);
+      break;
+    case CB_PAIRS_ACTIVE:
+      CB_TRY(dl(k, s->cand, s->n_cand, st));
+      CB_TRY(dl(ai, s->aidx, s->n_active, st));
+      CB_CUDA(cudaStreamSynchronize(st));
+      for (uint32_t a : ai) res.push_back(k[a]);
+      break;
+    case CB_PAIRS_CCD: CB_TRY(dl(res, s->ccd_keys, s->n_ccd, st)); break;
+    case CB_PAIRS_REST_FILTERED:
+      if (s->kind == CB_SHELL) CB_TRY(dl(res, s->frest, s->n_frest, st));
+      break;
+    default: return CB_ERR_ARG;
+  }
+  CB_CUDA(cudaStreamSynchronize(st));
+  *count = (int64_t)res.size();
+  if ((int64_t)res.size() > cap) return CB_ERR_CAPACITY;
+  if (keys && !res.empty()) memcpy(keys, res.data(), res.size() * sizeof(uint64_t));
+  return CB_OK;
+}
+
+cb_status cb_get_active(cb_scene* s, uint64_t* keys, double* dd, uint8_t* klass, int8_t* dtype, int64_t cap,
+                        int64_t* count) {
+  if (!s || !count) return CB_ERR_ARG;
+  cudaStream_t st = s->last_stream;
+  *count = s->n_active;
+  if (s->n_active > cap) return CB_ERR_CAPACITY;
+  std::vector<uint64_t> k;
+  std::vector<uint32_t> ai;
+  std::vector<double> d;
+  std::vector<uint8_t> c;
+  std::vector<int8_t> t;
+  CB_TRY(dl(k, s->cand, s->n_cand, st));
+  CB_TRY(dl(ai, s->aidx, s->n_active, st));
+  CB_TRY(dl(d, s->cd, s->n_cand, st));
+  CB_TRY(dl(c, s->ccls, s->n_cand, st));
+  CB_TRY(dl(t, s->ctype, s->n_cand, st));
+  CB_CUDA(cudaStreamSynchronize(st));
+  for (size_t q = 0; q < ai.size(); ++q) {
+    if (keys) keys[q] = k[ai[q]];
+    if (dd) dd[q] = d[ai[q]];
+    if (klass) klass[q] = c[ai[q]];
+    if (dtype) dtype[q] = t[ai[q]];
+  }
+  return CB_OK;
+}
+
+cb_status cb_get_ccd(cb_scene* s, uint64_t* keys, double* t, uint8_t* klass, int64_t cap, int64_t* count) {
+  if (!s || !count) return CB_ERR_ARG;
+  cudaStream_t st = s->last_stream;
+  *count = s->n_ccd;
+  if (s->n_ccd > cap) return CB_ERR_CAPACITY;
+  if (s->n_ccd) {
+    if (keys) CB_CUDA(cudaMemcpyAsync(keys, s->ccd_keys.p, 8 * (size_t)s->n_ccd, cudaMemcpyDeviceToHost, st));
+    if (t) CB_CUDA(cudaMemcpyAsync(t, s->ccd_t.p, 8 * (size_t)s->n_ccd, cudaMemcpyDeviceToHost, st));
+    if (klass) CB_CUDA(cudaMemcpyAsync(klass, s->ccd_cls.p, (size_t)s->n_ccd, cudaMemcpyDeviceToHost, st));
+  }
+  CB_CUDA(cudaStreamSynchronize(st));
+  return CB_OK;
+}
+
+cb_status cb_get_bsr(cb_scene* s, int32_t* row_ptr, int32_t* col, double* val, int64_t cap, int64_t* nnzb) {
+  if (!s || !nnzb) return CB_ERR_ARG;
+  cudaStream_t st = s->last_stream;
+  *nnzb = s->nnzb;
+  if (s->nnzb > cap) return CB_ERR_CAPACITY;
+  if (row_ptr) CB_CUDA(cudaMemcpyAsync(row_ptr, s->bsr_row.p, 4 * ((size_t)s->n + 1), cudaMemcpyDeviceToHost, st));
+  if (s->nnzb) {
+    if (col) CB_CUDA(cudaMemcpyAsync(col, s->bsr_col.p, 4 * (size_t)s->nnzb, cudaMemcpyDeviceToHost, st));
+    if (val) CB_CUDA(cudaMemcpyAsync(val, s->bsr_val.p, 72 * (size_t)s->nnzb, cudaMemcpyDeviceToHost, st));
+  }
+  CB_CUDA(cudaStreamSynchronize(st));
+  return CB_OK;
+}
+
+cb_status cb_bsr_device(cb_scene* s, const int32_t** row_ptr, const int32_t** col, const double** val,
+                        int64_t* nnzb) {
+  if (!s) return CB_ERR_ARG;
+  if (row_ptr) *row_ptr = (const int32_t*)s->bsr_row.p;
+  if (col) *col = (const int32_t*)s->bsr_col.p;
+  if (val) *val = (const double*)s->bsr_val.p;
+  if (nnzb) *nnzb = s->nnzb;
+  return CB_OK;
+}
+
+cb_status cb_get_stats(cb_scene* s, cb_stats* o) {
+  if (!s || !o) return CB_ERR_ARG;
+  uint64_t h[SC_N];
+  CB_TRY(read_scalars(s, 0, SC_N, h, s->last_stream));
+  memset(o, 0, sizeof(*o));
+  o->n_candidates = s->n_cand;
+  o->n_filtered = (int64_t)h[SC_NFILT];
+  o->n_core = (int64_t)h[SC_NCORE];
+  o->n_active = s->n_active;
+  o->n_ccd = s->n_ccd;
+  o->nnzb = s->nnzb;
+  o->n_rest_filtered = s->n_frest;
+  o->dbar_min = s->dbar_min;
+  o->offset = s->xi;
+  o->dhat = s->dhat;
+  o->activation = s->a;
+  o->status_bits = (int32_t)h[SC_STATUS];
+  o->ccd_max_iters = (int32_t)h[SC_ITERS];
+  size_t bytes = 0;
+  const DevBuf* all[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->frest,
+                         &s->frest_dbar, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls,
+                         &s->aidx, &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col,
+                         &s->bsr_val, &s->row_cnt, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->scan_tmp, &s->hist};
+  for (const DevBuf* b : all) bytes += b->bytes;
+  for (const BroadWork* w : {&s->bw, &s->bwc}) {
+    const DevBuf* wb[] = {&w->box32,    &w->box64,    &w->bounds,    &w->cell_cnt, &w->cell_off, &w->ekey[0],
+                          &w->ekey[1],  &w->eval[0],  &w->eval[1],   &w->run_flag, &w->run_id,   &w->run_start,
+                          &w->pair_cnt, &w->pair_off, &w->ckey[0],   &w->ckey[1],  &w->scan_tmp, &w->hist};
+    for (const DevBuf* b : wb) bytes += b->bytes;
+  }
+  o->device_bytes = (int64_t)bytes;
+  return CB_OK;
+}
+
+cb_status cb_sync_status(cb_scene* s) {
+  if (!s) return CB_ERR_ARG;
+  uint64_t h;
+  CB_TRY(read_scalars(s, SC_STATUS, 1, &h, s->last_stream));
+  uint64_t zero = 0;
+  CB_CUDA(cudaMemcpyAsync(scalars(s) + SC_STATUS, &zero, 8, cudaMemcpyHostToDevice, s->last_stream));
+  CB_CUDA(cudaStreamSynchronize(s->last_stream));
+  if (h & CB_DEV_CAPACITY) return CB_ERR_CAPACITY;
+  if (h & CB_DEV_PENETRATION) return CB_ERR_PENETRATION;
+  if (h & CB_DEV_ITER_LIMIT) return CB_ERR_ITER_LIMIT;
+  return CB_OK;
+}
+
+}  // extern "C"

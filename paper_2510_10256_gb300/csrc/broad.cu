@@ -1,0 +1,466 @@
+// broad.cu -- stage (a): spatial-hash broad phase at the full activation (Sec. 3.3).
+//
+// Canonical result: every non-incident primitive pair whose FP64 boxes, each
+// inflated by h, overlap on all three axes (closed intervals).  The hash works
+// on FP32 boxes rounded outward from the FP64 ones (lo rounded down, hi up), so
+// FP32 overlap is implied by FP64 overlap: the FP32 candidate stream is a
+// superset.  A pair is then accepted outright when the FP32 test still passes
+// after moving every FP32 bound one ulp inward (the FP64 bound lies within that
+// ulp), rejected when the plain FP32 test fails, and decided on the stored FP64
+// boxes otherwise.
+//
+// Steps: boxes + scene bounds -> cell size -> (cell, primitive) entries for
+// every cell a box covers -> stable radix sort by Morton cell key -> runs of
+// equal cells -> per entry, test the later entries of its run (point vs
+// triangle, edge vs later edge); a pair is reported only in the cell holding
+// the low corner of the two boxes' intersection (its "home" cell) -> compact
+// keys -> radix sort -> canonical keys.
+#include <algorithm>
+#include <cmath>
+
+#include "prims.cuh"
+#include "scene.cuh"
+
+namespace {
+
+struct Topo {
+  int kind, n, T, E;
+  const int32_t* __restrict__ ev0;
+  const int32_t* __restrict__ ev1;
+  const int32_t* __restrict__ tv;
+};
+
+struct Grid {
+  float ox, oy, oz, inv;
+  int dx, dy, dz;
+};
+
+__device__ __forceinline__ int prim_verts(const Topo& t, int q, int v[3]) {
+  if (t.kind == CB_ROD) {
+    v[0] = t.ev0[q];
+    v[1] = t.ev1[q];
+    v[2] = -1;
+    return 2;
+  }
+  if (q < t.n) {
+    v[0] = q;
+    v[1] = v[2] = -1;
+    return 1;
+  }
+  q -= t.n;
+  if (q < t.T) {
+    v[0] = t.tv[q];
+    v[1] = t.tv[t.T + q];
+    v[2] = t.tv[2 * t.T + q];
+    return 3;
+  }
+  q -= t.T;
+  v[0] = t.ev0[q];
+  v[1] = t.ev1[q];
+  v[2] = -1;
+  return 2;
+}
+
+__device__ __forceinline__ uint32_t f2o(float f) {
+  uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__host__ __device__ __forceinline__ float o2f(uint32_t o) {
+  uint32_t b = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float f;
+  memcpy(&f, &b, 4);
+  return f;
+#endif
+}
+
+__global__ void k_bounds_init(uint32_t* b) {
+  if (threadIdx.x < 3) b[threadIdx.x] = 0xffffffffu;
+  else if (threadIdx.x < 6) b[threadIdx.x] = 0u;
+  else if (threadIdx.x < 8) ((unsigned long long*)b)[3] = 0ull;  // extent sum (bits of double) at b[6..7]
+}
+
+__global__ void k_boxes(Topo t, int np, const double* __restrict__ x, const double* __restrict__ p, double h,
+                        float4* __restrict__ box32, double* __restrict__ box64, uint32_t* bounds) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  float lo32[3] = {INFINITY, INFINITY, INFINITY}, hi32[3] = {-INFINITY, -INFINITY, -INFINITY};
+  float ext = 0.f;
+  if (q < np) {
+    int v[3];
+    const int nv = prim_verts(t, q, v);
+    double lo[3], hi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double mn = INFINITY, mx = -INFINITY;
+      for (int a = 0; a < nv; ++a) {
+        double c = x[(size_t)k * t.n + v[a]];
+        mn = fmin(mn, c);
+        mx = fmax(mx, c);
+        if (p) {
+          double c2 = xadd(c, p[(size_t)k * t.n + v[a]]);
+          mn = fmin(mn, c2);
+          mx = fmax(mx, c2);
+        }
+      }
+      lo[k] = xsub(mn, h);
+      hi[k] = xadd(mx, h);
+      lo32[k] = __double2float_rd(lo[k]);
+      hi32[k] = __double2float_ru(hi[k]);
+      box64[(size_t)q * 6 + k] = lo[k];
+      box64[(size_t)q * 6 + 3 + k] = hi[k];
+      ext = fmaxf(ext, hi32[k] - lo32[k]);
+    }
+    box32[2 * (size_t)q] = make_float4(lo32[0], lo32[1], lo32[2], 0.f);
+    box32[2 * (size_t)q + 1] = make_float4(hi32[0], hi32[1], hi32[2], 0.f);
+  }
+  // block reduction of bounds and extent sum
+  __shared__ float s_lo[3][CB_THREADS / 32], s_hi[3][CB_THREADS / 32];
+  __shared__ double s_ext[CB_THREADS / 32];
+  double e = ext;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lo32[k] = fminf(lo32[k], __shfl_xor_sync(0xffffffffu, lo32[k], o));
+      hi32[k] = fmaxf(hi32[k], __shfl_xor_sync(0xffffffffu, hi32[k], o));
+    }
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    for (int k = 0; k < 3; ++k) {
+      s_lo[k][w] = lo32[k];
+      s_hi[k][w] = hi32[k];
+    }
+    s_ext[w] = e;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float l[3] = {INFINITY, INFINITY, INFINITY}, hh[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double es = 0;
+    for (int q2 = 0; q2 < CB_THREADS / 32; ++q2) {
+      for (int k = 0; k < 3; ++k) {
+        l[k] = fminf(l[k], s_lo[k][q2]);
+        hh[k] = fmaxf(hh[k], s_hi[k][q2]);
+      }
+      es += s_ext[q2];
+    }
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(&bounds[k], f2o(l[k]));
+      atomicMax(&bounds[3 + k], f2o(hh[k]));
+    }
+    atomicAdd((double*)(bounds + 6), es);
+  }
+}
+
+__device__ __forceinline__ int cell_of(float v, float o, float inv, int dim) {
+  float tt = __fmul_rn(__fsub_rn(v, o), inv);
+  int c = (int)floorf(tt);
+  return min(max(c, 0), dim - 1);
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+__device__ __forceinline__ uint32_t morton(int x, int y, int z) {
+  return spread10((uint32_t)x) | (spread10((uint32_t)y) << 1) | (spread10((uint32_t)z) << 2);
+}
+
+__global__ void k_cell_count(int np, const float4* __restrict__ box32, Grid g, uint32_t* __restrict__ cnt) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= np) return;
+  float4 lo = box32[2 * (size_t)q], hi = box32[2 * (size_t)q + 1];
+  int nx = cell_of(hi.x, g.ox, g.inv, g.dx) - cell_of(lo.x, g.ox, g.inv, g.dx) + 1;
+  int ny = cell_of(hi.y, g.oy, g.inv, g.dy) - cell_of(lo.y, g.oy, g.inv, g.dy) + 1;
+  int nz = cell_of(hi.z, g.oz, g.inv, g.dz) - cell_of(lo.z, g.oz, g.inv, g.dz) + 1;
+  cnt[q] = (uint32_t)(nx * ny * nz);
+}
+
+__global__ void k_cell_fill(int np, const float4* __restrict__ box32, Grid g, const uint32_t* __restrict__ off,
+                            uint32_t* __restrict__ ekey, uint32_t* __restrict__ eval) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= np) return;
+  float4 lo = box32[2 * (size_t)q], hi = box32[2 * (size_t)q + 1];
+  int x0 = cell_of(lo.x, g.ox, g.inv, g.dx), x1 = cell_of(hi.x, g.ox, g.inv, g.dx);
+  int y0 = cell_of(lo.y, g.oy, g.inv, g.dy), y1 = cell_of(hi.y, g.oy, g.inv, g.dy);
+  int z0 = cell_of(lo.z, g.oz, g.inv, g.dz), z1 = cell_of(hi.z, g.oz, g.inv, g.dz);
+  uint32_t w = off[q];
+  for (int z = z0; z <= z1; ++z)
+    for (int y = y0; y <= y1; ++y)
+      for (int xx = x0; xx <= x1; ++xx) {
+        ekey[w] = morton(xx, y, z);
+        eval[w] = (uint32_t)q;
+        ++w;
+      }
+}
+
+__global__ void k_run_flag(int64_t ne, const uint32_t* __restrict__ key, uint32_t* __restrict__ flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1u : 0u;
+}
+
+// run_id[i] = index of the run holding entry i; run_start[r] = first entry of run r
+__global__ void k_run_start(int64_t ne, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ excl,
+                            uint32_t* __restrict__ run_id, uint32_t* __restrict__ run_start) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  uint32_t f = flag[i], e = excl[i];
+  run_id[i] = e + f - 1u;
+  if (f) run_start[e] = (uint32_t)i;
+  if (i == ne - 1) run_start[e + f] = (uint32_t)ne;
+}
+
+__device__ __forceinline__ float nextup(float v) { return nextafterf(v, INFINITY); }
+__device__ __forceinline__ float nextdn(float v) { return nextafterf(v, -INFINITY); }
+
+// first index in [lo, hi) with eval >= bound (entries of a run are sorted by primitive)
+__device__ __forceinline__ int lower_bound_u32(const uint32_t* __restrict__ a, int lo, int hi, uint32_t bound) {
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < bound) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+struct PairArgs {
+  Topo t;
+  int64_t ne;
+  const uint32_t* __restrict__ ekey;
+  const uint32_t* __restrict__ eval;
+  const uint32_t* __restrict__ run_id;
+  const uint32_t* __restrict__ run_start;
+  const float4* __restrict__ box32;
+  const double* __restrict__ box64;
+  Grid g;
+  int bi, bj;
+};
+
+// count pass (FILL = false): cnt[i] = number of pairs entry i reports;
+// fill pass (FILL = true): writes them at off[i] (cnt read back as the bound)
+template <bool FILL>
+__global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __restrict__ cnt,
+                                                      const uint32_t* __restrict__ off, uint64_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.ne) return;
+  const Topo& t = A.t;
+  const uint32_t P = A.eval[i];
+  const uint32_t kc = A.ekey[i];
+  const uint32_t r = A.run_id[i];
+  const int s = (int)A.run_start[r], e = (int)A.run_start[r + 1];
+  int j0, j1;
+  uint32_t type;
+  uint32_t ibase = 0, jbase = 0;
+  if (t.kind == CB_ROD) {
+    j0 = (int)i + 1;
+    j1 = e;
+    type = CB_KEY_ROD_EE;
+  } else if (P < (uint32_t)t.n) {
+    j0 = lower_bound_u32(A.eval, s, e, (uint32_t)t.n);
+    j1 = lower_bound_u32(A.eval, j0, e, (uint32_t)(t.n + t.T));
+    type = CB_KEY_PT;
+    jbase = (uint32_t)t.n;
+  } else if (P < (uint32_t)(t.n + t.T)) {
+    if (!FILL) cnt[i] = 0;
+    return;
+  } else {
+    j0 = (int)i + 1;
+    j1 = e;
+    type = CB_KEY_EE;
+    ibase = jbase = (uint32_t)(t.n + t.T);
+  }
+  const float4 plo = A.box32[2 * (size_t)P], phi = A.box32[2 * (size_t)P + 1];
+  int pv[3];
+  prim_verts(t, (int)P, pv);
+  const uint64_t tbits = (uint64_t)type << (A.bi + A.bj);
+  const uint64_t ipart = (uint64_t)(P - ibase) << A.bj;
+  uint32_t count = 0;
+  uint64_t w = FILL ? off[i] : 0;
+  // the fill pass re-makes the count pass's decisions; never write past them
+  const uint64_t w_end = FILL ? w + cnt[i] : 0;
+  for (int j = j0; j < j1; ++j) {
+    const uint32_t Q = A.eval[j];
+    const float4 qlo = A.box32[2 * (size_t)Q], qhi = A.box32[2 * (size_t)Q + 1];
+    if (!(plo.x <= qhi.x && qlo.x <= phi.x && plo.y <= qhi.y && qlo.y <= phi.y && plo.z <= qhi.z &&
+          qlo.z <= phi.z))
+      continue;
+    // home cell: low corner of the intersection
+    const uint32_t hc = morton(cell_of(fmaxf(plo.x, qlo.x), A.g.ox, A.g.inv, A.g.dx),
+                               cell_of(fmaxf(plo.y, qlo.y), A.g.oy, A.g.inv, A.g.dy),
+                               cell_of(fmaxf(plo.z, qlo.z), A.g.oz, A.g.inv, A.g.dz));
+    if (hc != kc) continue;
+    int qv[3];
+    prim_verts(t, (int)Q, qv);
+    bool inc = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) inc |= (pv[a] >= 0 && pv[a] == qv[b]);
+    if (inc) continue;
+    const bool sure = nextup(plo.x) <= nextdn(qhi.x) && nextup(qlo.x) <= nextdn(phi.x) &&
+                      nextup(plo.y) <= nextdn(qhi.y) && nextup(qlo.y) <= nextdn(phi.y) &&
+                      nextup(plo.z) <= nextdn(qhi.z) && nextup(qlo.z) <= nextdn(phi.z);
+    if (!sure) {
+      const double* b1 = A.box64 + (size_t)P * 6;
+      const double* b2 = A.box64 + (size_t)Q * 6;
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) ok = ok && (b1[k] <= b2[3 + k]) && (b2[k] <= b1[3 + k]);
+      if (!ok) continue;
+    }
+    if (FILL) {
+      if (w < w_end) out[w++] = tbits | ipart | (uint64_t)(Q - jbase);
+    } else {
+      ++count;
+    }
+  }
+  if (!FILL) cnt[i] = count;
+}
+
+__global__ void k_expand(int64_t nc, const uint64_t* __restrict__ ck, int bi, int bj, uint64_t* __restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nc) return;
+  uint64_t c = ck[q];
+  uint32_t type = (uint32_t)(c >> (bi + bj));
+  uint32_t i = (uint32_t)((c >> bj) & ((1ull << bi) - 1ull));
+  uint32_t j = (uint32_t)(c & ((1ull << bj) - 1ull));
+  out[q] = cb_key(type, i, j);
+}
+
+}  // namespace
+
+cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* p, double h, DevBuf& out,
+                      int64_t* n_out, cudaStream_t st) {
+  const int np = s->n_prims;
+  if (np == 0) {
+    *n_out = 0;
+    return CB_OK;
+  }
+  Topo t{s->kind, s->n, s->T, s->E, bp<int32_t>(s->ev0), bp<int32_t>(s->ev1), bp<int32_t>(s->tv)};
+  CB_TRY(buf_ensure(w.box32, sizeof(float4) * 2 * (size_t)np, st));
+  CB_TRY(buf_ensure(w.box64, sizeof(double) * 6 * (size_t)np, st));
+  CB_TRY(buf_ensure(w.bounds, 64, st));
+  uint32_t* bounds = bp<uint32_t>(w.bounds);
+  k_bounds_init<<<1, 32, 0, cb_count(st)>>>(bounds);
+  k_boxes<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(t, np, x, p, h, bp<float4>(w.box32), bp<double>(w.box64), bounds);
+  CB_CUDA(cudaGetLastError());
+  uint32_t hb[8];
+  CB_CUDA(cudaMemcpyAsync(hb, bounds, 32, cudaMemcpyDeviceToHost, st));
+  CB_CUDA(cudaStreamSynchronize(st));
+  float lo[3], hi[3];
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = o2f(hb[k]);
+    hi[k] = o2f(hb[3 + k]);
+  }
+  double ext_sum;
+  memcpy(&ext_sum, hb + 6, 8);
+  // cell size: mean primitive box extent (scaled by the tuned factor), rounded to
+  // a 1/4-octave grid so that tiny summation-order differences never change it
+  double c = s->cell_hint > 0 ? (double)s->cell_hint * (ext_sum / std::max(1, np)) : ext_sum / std::max(1, np);
+  if (!(c > 0)) c = 1.0;
+  double lg = std::floor(std::log2(c) * 4.0) / 4.0;
+  c = std::exp2(lg);
+  for (int k = 0; k < 3; ++k) {
+    double span = (double)hi[k] - (double)lo[k];
+    if (span / c > 1000.0) c = span / 1000.0;
+  }
+  Grid g;
+  g.inv = (float)(1.0 / c);
+  g.ox = lo[0];
+  g.oy = lo[1];
+  g.oz = lo[2];
+  int* dims[3] = {&g.dx, &g.dy, &g.dz};
+  for (int k = 0; k < 3; ++k) {
+    double span = (double)hi[k] - (double)lo[k];
+    int d = (int)std::floor(span * (double)g.inv) + 2;
+    *dims[k] = std::min(std::max(d, 1), 1024);
+  }
+  w.cell = (float)c;
+
+  CB_TRY(buf_ensure(w.cell_cnt, sizeof(uint32_t) * (size_t)np + 16, st));
+  CB_TRY(buf_ensure(w.cell_off, sizeof(uint32_t) * ((size_t)np + 1), st));
+  CB_TRY(buf_ensure(w.scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(np + 1) + 8), st));
+  k_cell_count<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(np, bp<float4>(w.box32), g, bp<uint32_t>(w.cell_cnt));
+  uint32_t* tot_dev = (uint32_t*)(scalars(s) + SC_COUNT0);
+  cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.cell_cnt), bp<uint32_t>(w.cell_off), np,
+                                          bp<uint32_t>(w.scan_tmp), tot_dev, st);
+  CB_CUDA(cudaGetLastError());
+  uint32_t ne32;
+  CB_CUDA(cudaMemcpyAsync(&ne32, tot_dev, 4, cudaMemcpyDeviceToHost, st));
+  CB_CUDA(cudaStreamSynchronize(st));
+  const int64_t ne = ne32;
+  if (ne == 0) {
+    *n_out = 0;
+    return CB_OK;
+  }
+  for (int b = 0; b < 2; ++b) {
+    CB_TRY(buf_ensure(w.ekey[b], sizeof(uint32_t) * (size_t)ne, st));
+    CB_TRY(buf_ensure(w.eval[b], sizeof(uint32_t) * (size_t)ne, st));
+  }
+  k_cell_fill<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(np, bp<float4>(w.box32), g, bp<uint32_t>(w.cell_off),
+                                                   bp<uint32_t>(w.ekey[0]), bp<uint32_t>(w.eval[0]));
+  CB_TRY(buf_ensure(w.hist, sizeof(uint32_t) * (size_t)cbp::radix_hist_elems(ne), st));
+  CB_TRY(buf_ensure(w.scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(cbp::radix_hist_elems(ne)) +
+                                                             cbp::scan_tmp_elems(ne + 1) + 8),
+                    st));
+  int r = cbp::radix_sort<uint32_t, uint32_t, true>(bp<uint32_t>(w.ekey[0]), bp<uint32_t>(w.eval[0]),
+                                                    bp<uint32_t>(w.ekey[1]), bp<uint32_t>(w.eval[1]), ne, 0, 30,
+                                                    bp<uint32_t>(w.hist), bp<uint32_t>(w.scan_tmp), st);
+  const uint32_t* ekey = bp<uint32_t>(w.ekey[r]);
+  const uint32_t* eval = bp<uint32_t>(w.eval[r]);
+  CB_TRY(buf_ensure(w.run_flag, sizeof(uint32_t) * (size_t)ne, st));
+  CB_TRY(buf_ensure(w.run_id, sizeof(uint32_t) * (size_t)ne, st));
+  CB_TRY(buf_ensure(w.run_start, sizeof(uint32_t) * ((size_t)ne + 2), st));
+  CB_TRY(buf_ensure(w.pair_cnt, sizeof(uint32_t) * (size_t)ne, st));
+  CB_TRY(buf_ensure(w.pair_off, sizeof(uint32_t) * ((size_t)ne + 1), st));
+  k_run_flag<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, ekey, bp<uint32_t>(w.run_flag));
+  // exclusive scan of the flags into pair_off (used as scratch here)
+  cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.run_flag), bp<uint32_t>(w.pair_off), ne,
+                                          bp<uint32_t>(w.scan_tmp), (uint32_t*)nullptr, st);
+  k_run_start<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, bp<uint32_t>(w.run_flag), bp<uint32_t>(w.pair_off),
+                                                   bp<uint32_t>(w.run_id), bp<uint32_t>(w.run_start));
+  PairArgs A;
+  A.t = t;
+  A.ne = ne;
+  A.ekey = ekey;
+  A.eval = eval;
+  A.run_id = bp<uint32_t>(w.run_id);
+  A.run_start = bp<uint32_t>(w.run_start);
+  A.box32 = bp<float4>(w.box32);
+  A.box64 = bp<double>(w.box64);
+  A.g = g;
+  A.bi = s->bits_i;
+  A.bj = s->bits_j;
+  k_pairs<false><<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint32_t>(w.pair_cnt), nullptr, nullptr);
+  cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off), ne,
+                                          bp<uint32_t>(w.scan_tmp), tot_dev, st);
+  CB_CUDA(cudaGetLastError());
+  uint32_t nc32;
+  CB_CUDA(cudaMemcpyAsync(&nc32, tot_dev, 4, cudaMemcpyDeviceToHost, st));
+  CB_CUDA(cudaStreamSynchronize(st));
+  const int64_t nc = nc32;
+  *n_out = nc;
+  if (nc == 0) return CB_OK;
+  for (int b = 0; b < 2; ++b) CB_TRY(buf_ensure(w.ckey[b], sizeof(uint64_t) * (size_t)nc, st));
+  k_pairs<true><<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off),
+                                                                bp<uint64_t>(w.ckey[0]));
+  const int cbits = s->bits_i + s->bits_j + (s->kind == CB_SHELL ? 2 : 0);
+  CB_TRY(buf_ensure(w.hist, sizeof(uint32_t) * (size_t)cbp::radix_hist_elems(nc), st));
+  CB_TRY(buf_ensure(w.scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(cbp::radix_hist_elems(nc)) + 8),
+                    st));
+  int r2 = cbp::radix_sort<uint64_t, uint32_t, false>(bp<uint64_t>(w.ckey[0]), nullptr, bp<uint64_t>(w.ckey[1]),
+                                                      nullptr, nc, 0, cbits, bp<uint32_t>(w.hist),
+                                                      bp<uint32_t>(w.scan_tmp), st);
+  CB_TRY(buf_ensure(out, sizeof(uint64_t) * (size_t)nc, st));
+  k_expand<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(nc, bp<uint64_t>(w.ckey[r2]), s->bits_i, s->bits_j, bp<uint64_t>(out));
+  CB_CUDA(cudaGetLastError());
+  return CB_OK;
+}

@@ -1,0 +1,819 @@
+// narrow.cu -- stages (b), (c), (d): barrier filter, distances, barrier energy,
+// gradient and PSD-projected Hessian, assembly into a global gradient and BSR.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "geometry.cuh"
+#include "prims.cuh"
+#include "scene.cuh"
+
+namespace {
+
+struct Stencil {
+  int v[4];
+  bool ee;
+};
+
+__device__ __forceinline__ Stencil stencil_of(uint64_t key, const int32_t* __restrict__ ev0,
+                                              const int32_t* __restrict__ ev1, const int32_t* __restrict__ tv,
+                                              int T) {
+  Stencil s;
+  const uint32_t ty = cb_key_type(key), i = cb_key_i(key), j = cb_key_j(key);
+  if (ty == CB_KEY_PT) {
+    s.v[0] = (int)i;
+    s.v[1] = tv[j];
+    s.v[2] = tv[T + j];
+    s.v[3] = tv[2 * T + j];
+    s.ee = false;
+  } else {
+    s.v[0] = ev0[i];
+    s.v[1] = ev1[i];
+    s.v[2] = ev0[j];
+    s.v[3] = ev1[j];
+    s.ee = true;
+  }
+  return s;
+}
+
+__device__ __forceinline__ d3 load3(const double* __restrict__ x, int n, int v) {
+  return mk3(x[v], x[(size_t)n + v], x[2 * (size_t)n + v]);
+}
+
+// ------------------------------------------------------------------ (b) ----
+
+// rods: arc length S at every vertex, summed sequentially along each polyline
+__global__ void k_arclength(int n_rods, const int32_t* __restrict__ rod_ptr, const double* __restrict__ rest, int n,
+                            double* __restrict__ S) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rods) return;
+  const int s = rod_ptr[r], e = rod_ptr[r + 1];
+  if (e <= s) return;
+  S[s] = 0.0;
+  for (int v = s + 1; v < e; ++v) {
+    double dx = xsub(rest[v], rest[v - 1]);
+    double dy = xsub(rest[(size_t)n + v], rest[(size_t)n + v - 1]);
+    double dz = xsub(rest[2 * (size_t)n + v], rest[2 * (size_t)n + v - 1]);
+    S[v] = xadd(S[v - 1], __dsqrt_rn(xadd(xadd(xmul(dx, dx), xmul(dy, dy)), xmul(dz, dz))));
+  }
+}
+
+// rods: for edge k the last edge l of the same polyline with S[l0] - S[k1] < a
+// (the reference arc-length gap between the edges); the gap grows with l.
+__global__ void k_rod_window(int E, const int32_t* __restrict__ ev0, const int32_t* __restrict__ ev1,
+                             const int32_t* __restrict__ comp, const double* __restrict__ S, double a,
+                             int32_t* __restrict__ win, unsigned long long* __restrict__ dmin_bits,
+                             unsigned long long* __restrict__ nfilt) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= E) return;
+  const int k1 = ev1[k];
+  int last = k + 1;
+  double mn = INFINITY;
+  unsigned long long cnt = 0;
+  for (int l = k + 1; l < E; ++l) {
+    const int l0 = ev0[l];
+    if (comp[l0] != comp[k1]) break;
+    if (l0 <= k1) continue;
+    const double dbar = xsub(S[l0], S[k1]);
+    if (!(dbar < a)) break;
+    last = l;
+    mn = fmin(mn, dbar);
+    ++cnt;
+  }
+  win[k] = last;
+  if (cnt) {
+    atomicMin(dmin_bits, (unsigned long long)__double_as_longlong(mn));
+    atomicAdd(nfilt, cnt);
+  }
+}
+
+// shells: rest candidates of one component whose rest distance is below a
+__global__ void k_rest_filter(int64_t nc, const uint64_t* __restrict__ keys, const int32_t* __restrict__ ev0,
+                              const int32_t* __restrict__ ev1, const int32_t* __restrict__ tv, int T,
+                              const int32_t* __restrict__ comp, const double* __restrict__ rest, int n, double a,
+                              uint32_t* __restrict__ flag, double* __restrict__ dbar,
+                              unsigned long long* __restrict__ dmin_bits) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  Stencil s = stencil_of(keys[c], ev0, ev1, tv, T);
+  uint32_t f = 0;
+  double d = 0.0;
+  if (comp[s.v[0]] == comp[s.v[2]]) {
+    cbg::stencil_distance(s.ee, load3(rest, n, s.v[0]), load3(rest, n, s.v[1]), load3(rest, n, s.v[2]),
+                          load3(rest, n, s.v[3]), d);
+    if (d < a) {
+      f = 1;
+      atomicMin(dmin_bits, (unsigned long long)__double_as_longlong(d));
+    }
+  }
+  flag[c] = f;
+  dbar[c] = d;
+}
+
+__global__ void k_filter_rod(int64_t nc, const uint64_t* __restrict__ cand, const int32_t* __restrict__ ev0,
+                             const int32_t* __restrict__ comp, const int32_t* __restrict__ win, int off,
+                             uint8_t* __restrict__ klass, unsigned long long* __restrict__ nfilt) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t f = 0;
+  if (c < nc) {
+    const uint64_t key = cand[c];
+    const int k = (int)cb_key_i(key), l = (int)cb_key_j(key);
+    f = (!off && comp[ev0[k]] == comp[ev0[l]] && l <= win[k]) ? 1u : 0u;
+    klass[c] = (uint8_t)f;
+  }
+  uint32_t b = __ballot_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(nfilt, (unsigned long long)__popc(b));
+}
+
+__global__ void k_filter_shell(int64_t nc, const uint64_t* __restrict__ cand, const uint64_t* __restrict__ frest,
+                               int64_t nf, int off, uint8_t* __restrict__ klass,
+                               unsigned long long* __restrict__ nfilt) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t f = 0;
+  if (c < nc) {
+    const uint64_t key = cand[c];
+    if (!off && nf > 0) {
+      int64_t lo = 0, hi = nf;
+      while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (frest[mid] < key) lo = mid + 1;
+        else hi = mid;
+      }
+      f = (lo < nf && frest[lo] == key) ? 1u : 0u;
+    }
+    klass[c] = (uint8_t)f;
+  }
+  uint32_t b = __ballot_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(nfilt, (unsigned long long)__popc(b));
+}
+
+// ------------------------------------------------------------------ (c) ----
+
+struct PassParams {
+  double xi, dhat, a, dbar_min, kappa;
+  int single, core_temp;
+};
+
+// pair parameters: offset xi_p and width dhat_p of a class (0 U, 1 F, 2 C)
+__device__ __forceinline__ void pair_params(const PassParams& P, int k, double& xi_p, double& dh_p) {
+  if (k == 1) {
+    xi_p = 0.0;
+    dh_p = P.dbar_min;
+  } else if (k == 2 || P.single) {
+    xi_p = 0.0;
+    dh_p = P.a;
+  } else {
+    xi_p = P.xi;
+    dh_p = P.dhat;
+  }
+}
+
+__global__ void k_distance(int64_t nc, const uint64_t* __restrict__ cand, const uint8_t* __restrict__ klass_in,
+                           const int32_t* __restrict__ ev0, const int32_t* __restrict__ ev1,
+                           const int32_t* __restrict__ tv, int T, const double* __restrict__ x, int n, PassParams P,
+                           double* __restrict__ dout, int8_t* __restrict__ tout, uint8_t* __restrict__ cls,
+                           uint32_t* __restrict__ flag, unsigned long long* __restrict__ status,
+                           unsigned long long* __restrict__ ncore) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t is_core = 0;
+  if (c < nc) {
+    Stencil s = stencil_of(cand[c], ev0, ev1, tv, T);
+    double d;
+    const int ty = cbg::stencil_distance(s.ee, load3(x, n, s.v[0]), load3(x, n, s.v[1]), load3(x, n, s.v[2]),
+                                         load3(x, n, s.v[3]), d);
+    int k = klass_in[c];
+    if (k == 0 && P.core_temp && !P.single && d <= P.xi) k = 2;
+    double xi_p, dh_p;
+    pair_params(P, k, xi_p, dh_p);
+    const double y = xsub(d, xi_p);
+    const uint32_t act = (y < dh_p) ? 1u : 0u;
+    if (act && y <= 0.0) atomicOr(status, (unsigned long long)CB_DEV_PENETRATION);
+    dout[c] = d;
+    tout[c] = (int8_t)ty;
+    cls[c] = (uint8_t)k;
+    flag[c] = act;
+    is_core = (k == 2);
+  }
+  uint32_t b = __ballot_sync(0xffffffffu, is_core);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(ncore, (unsigned long long)__popc(b));
+}
+
+__global__ void k_active_compact(int64_t nc, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                                 uint32_t* __restrict__ aidx) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc && flag[c]) aidx[pos[c]] = (uint32_t)c;
+}
+
+// ------------------------------------------------------------------ (d) ----
+
+// 16 (row, col) block keys of each active stencil
+__global__ void k_block_keys(int64_t na, const uint32_t* __restrict__ aidx, const uint64_t* __restrict__ cand,
+                             const int32_t* __restrict__ ev0, const int32_t* __restrict__ ev1,
+                             const int32_t* __restrict__ tv, int T, int bits_n, uint64_t* __restrict__ bkey) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= na) return;
+  Stencil s = stencil_of(cand[aidx[a]], ev0, ev1, tv, T);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bkey[16 * a + 4 * i + j] = ((uint64_t)s.v[i] << bits_n) | (uint64_t)s.v[j];
+}
+
+__global__ void k_unique_flag(int64_t m, const uint64_t* __restrict__ k, uint32_t* __restrict__ flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) flag[i] = (i == 0 || k[i] != k[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_unique_write(int64_t m, const uint64_t* __restrict__ k, const uint32_t* __restrict__ flag,
+                               const uint32_t* __restrict__ pos, int bits_n, int32_t* __restrict__ col,
+                               uint32_t* __restrict__ row_cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m || !flag[i]) return;
+  const uint64_t key = k[i];
+  col[pos[i]] = (int32_t)(key & ((1ull << bits_n) - 1ull));
+  atomicAdd(&row_cnt[key >> bits_n], 1u);
+}
+
+// --- analytic derivatives of the squared distance in relative variables ---
+// z_m = sum_i C[m][i] x_i (m < nz) with C rows summing to zero.
+//   PP:    z0 = b - a                       s = |z0|^2
+//   PE:    z0 = w = q - e0, z1 = u = e1-e0  s = |w|^2 - (w.u)^2/|u|^2
+//   plane: z0 = w, z1 = u, z2 = v           s = (w.(u x v))^2 / |u x v|^2
+// (point-triangle face: w = p-t0, u = t1-t0, v = t2-t0; edge-edge interior:
+//  w = b0-a0, u = a1-a0, v = b1-b0.)
+struct TypeInfo {
+  int8_t kind;   // 0 PP, 1 PE, 2 plane
+  int8_t C[3][4];
+};
+
+__constant__ TypeInfo c_pt_types[7] = {
+    {0, {{-1, 1, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}},
+    {0, {{-1, 0, 1, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}},
+    {0, {{-1, 0, 0, 1}, {0, 0, 0, 0}, {0, 0, 0, 0}}},
+    {1, {{1, -1, 0, 0}, {0, -1, 1, 0}, {0, 0, 0, 0}}},
+    {1, {{1, 0, -1, 0}, {0, 0, -1, 1}, {0, 0, 0, 0}}},
+    {1, {{1, 0, 0, -1}, {0, 1, 0, -1}, {0, 0, 0, 0}}},
+    {2, {{1, -1, 0, 0}, {0, -1, 1, 0}, {0, -1, 0, 1}}},
+};
+__constant__ TypeInfo c_ee_types[9] = {
+    {0, {{-1, 0, 1, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}},
+    {0, {{-1, 0, 0, 1}, {0, 0, 0, 0}, {0, 0, 0, 0}}},
+    {0, {{0, -1, 1, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}},
+    {0, {{0, -1, 0, 1}, {0, 0, 0, 0}, {0, 0, 0, 0}}},
+    {1, {{1, 0, -1, 0}, {0, 0, -1, 1}, {0, 0, 0, 0}}},
+    {1, {{0, 1, -1, 0}, {0, 0, -1, 1}, {0, 0, 0, 0}}},
+    {1, {{-1, 0, 1, 0}, {-1, 1, 0, 0}, {0, 0, 0, 0}}},
+    {1, {{-1, 0, 0, 1}, {-1, 1, 0, 0}, {0, 0, 0, 0}}},
+    {2, {{-1, 0, 1, 0}, {-1, 1, 0, 0}, {0, 0, -1, 1}}},
+};
+
+// Orthonormal bases of the complement of rigid translations of the points a
+// stencil type involves: K4[i][a] for 4 points (entries +-1/2), K3 for 3.
+__constant__ double c_K4[4][3] = {{0.5, 0.5, 0.5}, {0.5, -0.5, -0.5}, {-0.5, 0.5, -0.5}, {-0.5, -0.5, 0.5}};
+__constant__ double c_K3[3][2] = {{0.70710678118654752440, 0.40824829046386301637},
+                                  {-0.70710678118654752440, 0.40824829046386301637},
+                                  {0.0, -0.81649658092772603273}};
+
+__device__ __forceinline__ double& zh(double* H, int r, int c) { return H[r * 9 + c]; }
+
+// gradient gs[9] and Hessian Hs[81] (row-major, 3x3 blocks of z) of s
+__device__ void s_derivs(int kind, const d3* z, double* gs, double* Hs) {
+  for (int i = 0; i < 81; ++i) Hs[i] = 0.0;
+  for (int i = 0; i < 9; ++i) gs[i] = 0.0;
+  if (kind == 0) {
+    gs[0] = 2.0 * z[0].x;
+    gs[1] = 2.0 * z[0].y;
+    gs[2] = 2.0 * z[0].z;
+    zh(Hs, 0, 0) = zh(Hs, 1, 1) = zh(Hs, 2, 2) = 2.0;
+    return;
+  }
+  if (kind == 1) {
+    const double w[3] = {z[0].x, z[0].y, z[0].z}, u[3] = {z[1].x, z[1].y, z[1].z};
+    const double al = w[0] * u[0] + w[1] * u[1] + w[2] * u[2];
+    const double be = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double ga = al / be;
+    for (int k = 0; k < 3; ++k) {
+      gs[k] = 2.0 * w[k] - 2.0 * ga * u[k];
+      gs[3 + k] = -2.0 * ga * w[k] + 2.0 * ga * ga * u[k];
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        const double dij = (i == j) ? 1.0 : 0.0;
+        const double ww = 2.0 * dij - 2.0 * u[i] * u[j] / be;
+        const double wu = -2.0 * u[i] * w[j] / be - 2.0 * ga * dij + 4.0 * ga * u[i] * u[j] / be;
+        const double uu = -2.0 * w[i] * w[j] / be + 4.0 * ga * (w[i] * u[j] + u[i] * w[j]) / be +
+                          2.0 * ga * ga * dij - 8.0 * ga * ga * u[i] * u[j] / be;
+        zh(Hs, i, j) = ww;
+        zh(Hs, i, 3 + j) = wu;
+        zh(Hs, 3 + j, i) = wu;
+        zh(Hs, 3 + i, 3 + j) = uu;
+      }
+    return;
+  }
+  // plane: s = g^2 / N, g = w.(u x v), N = |u x v|^2
+  const d3 w = z[0], u = z[1], v = z[2];
+  const double nx = u.y * v.z - u.z * v.y, ny = u.z * v.x - u.x * v.z, nz = u.x * v.y - u.y * v.x;
+  const double g = w.x * nx + w.y * ny + w.z * nz;
+  const double uu = u.x * u.x + u.y * u.y + u.z * u.z;
+  const double vv = v.x * v.x + v.y * v.y + v.z * v.z;
+  const double uv = u.x * v.x + u.y * v.y + u.z * v.z;
+  const double N = nx * nx + ny * ny + nz * nz;
+  // grad g: (n, v x w, w x u)
+  double gg[9] = {nx,
+                  ny,
+                  nz,
+                  v.y * w.z - v.z * w.y,
+                  v.z * w.x - v.x * w.z,
+                  v.x * w.y - v.y * w.x,
+                  w.y * u.z - w.z * u.y,
+                  w.z * u.x - w.x * u.z,
+                  w.x * u.y - w.y * u.x};
+  // grad N: (0, 2 vv u - 2 uv v, 2 uu v - 2 uv u)
+  const double ua[3] = {u.x, u.y, u.z}, va[3] = {v.x, v.y, v.z}, wa[3] = {w.x, w.y, w.z};
+  double gN[9];
+  for (int k = 0; k < 3; ++k) {
+    gN[k] = 0.0;
+    gN[3 + k] = 2.0 * vv * ua[k] - 2.0 * uv * va[k];
+    gN[6 + k] = 2.0 * uu * va[k] - 2.0 * uv * ua[k];
+  }
+  const double iN = 1.0 / N;
+  const double a1 = 2.0 * g * iN, a2 = g * g * iN * iN;
+  for (int k = 0; k < 9; ++k) gs[k] = a1 * gg[k] - a2 * gN[k];
+  // Hessian
+  const double c_gg = 2.0 * iN;              // grad g grad g^T
+  const double c_hg = 2.0 * g * iN;          // hess g
+  const double c_gN = -2.0 * g * iN * iN;    // (grad g grad N^T + grad N grad g^T)
+  const double c_hN = -g * g * iN * iN;      // hess N
+  const double c_NN = 2.0 * g * g * iN * iN * iN;  // grad N grad N^T
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 9; ++c)
+      Hs[r * 9 + c] = c_gg * gg[r] * gg[c] + c_gN * (gg[r] * gN[c] + gN[r] * gg[c]) + c_NN * gN[r] * gN[c];
+  // hess g: blocks (w,u) = -[v]x, (w,v) = [u]x, (u,v) = -[w]x and transposes
+  auto skew_add = [&](int rb, int cb, const double* a, double sc) {
+    // adds sc * [a]x to block (rb, cb) and sc * [a]x^T to block (cb, rb)
+    const double m[3][3] = {{0.0, -a[2], a[1]}, {a[2], 0.0, -a[0]}, {-a[1], a[0], 0.0}};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        Hs[(3 * rb + i) * 9 + 3 * cb + j] += sc * m[i][j];
+        Hs[(3 * cb + j) * 9 + 3 * rb + i] += sc * m[i][j];
+      }
+  };
+  skew_add(0, 1, va, -c_hg);
+  skew_add(0, 2, ua, c_hg);
+  skew_add(1, 2, wa, -c_hg);
+  // hess N: (u,u) 2 vv I - 2 v v^T ; (v,v) 2 uu I - 2 u u^T ; (u,v) 4 u v^T - 2 v u^T - 2 uv I
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double dij = (i == j) ? 1.0 : 0.0;
+      Hs[(3 + i) * 9 + 3 + j] += c_hN * (2.0 * vv * dij - 2.0 * va[i] * va[j]);
+      Hs[(6 + i) * 9 + 6 + j] += c_hN * (2.0 * uu * dij - 2.0 * ua[i] * ua[j]);
+      const double uvb = c_hN * (4.0 * ua[i] * va[j] - 2.0 * va[i] * ua[j] - 2.0 * uv * dij);
+      Hs[(3 + i) * 9 + 6 + j] += uvb;
+      Hs[(6 + j) * 9 + 3 + i] += uvb;
+    }
+}
+
+// cyclic Jacobi on a symmetric n x n A (row-major, n <= 9); V receives the
+// eigenvectors (columns); the eigenvalues are left on the diagonal of A
+__device__ int jacobi_sym(double* A, double* V, const int n) {
+  for (int i = 0; i < n * n; ++i) V[i] = 0.0;
+  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+  int sweep;
+  for (sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, fro = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double a2 = A[i * n + j] * A[i * n + j];
+        fro += a2;
+        if (i != j) off += a2;
+      }
+    if (fro == 0.0 || off <= 1e-30 * fro) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (apq == 0.0) continue;
+        const double tau = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          const double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - s * vkq;
+          V[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  return sweep;
+}
+
+__device__ __forceinline__ int64_t find_block(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                              int r, int c) {
+  int lo = row_ptr[r], hi = row_ptr[r + 1];
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (col[mid] < c) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+struct HessArgs {
+  int64_t na;
+  const uint32_t* __restrict__ aidx;
+  const uint64_t* __restrict__ cand;
+  const double* __restrict__ cd;
+  const int8_t* __restrict__ ctype;
+  const uint8_t* __restrict__ ccls;
+  const int32_t* __restrict__ ev0;
+  const int32_t* __restrict__ ev1;
+  const int32_t* __restrict__ tv;
+  int T;
+  const double* __restrict__ x;
+  int n;
+  PassParams P;
+  const int32_t* __restrict__ row_ptr;
+  const int32_t* __restrict__ col;
+  double* __restrict__ val;
+  double* __restrict__ grad;
+  double* __restrict__ energy;
+  unsigned long long* __restrict__ status;
+};
+
+__global__ void __launch_bounds__(128) k_barrier_hess(HessArgs A) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double e_local = 0.0;
+  if (a < A.na) {
+    const uint32_t c = A.aidx[a];
+    const uint64_t key = A.cand[c];
+    Stencil s = stencil_of(key, A.ev0, A.ev1, A.tv, A.T);
+    const int ty = A.ctype[c];
+    const TypeInfo& TI = s.ee ? c_ee_types[ty] : c_pt_types[ty];
+    const int kind = TI.kind;
+    const int nz = kind + 1;
+    d3 X[4];
+    for (int i = 0; i < 4; ++i) X[i] = load3(A.x, A.n, s.v[i]);
+    d3 P[4];
+    for (int i = 0; i < 4; ++i) P[i] = mk3(X[i].x - X[0].x, X[i].y - X[0].y, X[i].z - X[0].z);
+    d3 z[3];
+    for (int m = 0; m < 3; ++m) {
+      double zx = 0, zy = 0, zz = 0;
+      for (int i = 1; i < 4; ++i) {
+        const double cm = (double)TI.C[m][i];
+        zx += cm * P[i].x;
+        zy += cm * P[i].y;
+        zz += cm * P[i].z;
+      }
+      z[m] = mk3(zx, zy, zz);
+    }
+    const double d = A.cd[c];
+    double xi_p, dh_p;
+    pair_params(A.P, A.ccls[c], xi_p, dh_p);
+    const double y = d - xi_p;
+    double b, b1, b2;
+    {
+      const double r = y - dh_p, l = log(y / dh_p);
+      b = -(r * r) * l;
+      b1 = -2.0 * r * l - (r * r) / y;
+      b2 = -2.0 * l - 4.0 * r / y + (r * r) / (y * y);
+    }
+    const double kap = A.P.kappa;
+    e_local = kap * b;
+    double gs[9], Hs[81];
+    s_derivs(kind, z, gs, Hs);
+    double gd[9];
+    const double i2d = 0.5 / d;
+    for (int k = 0; k < 9; ++k) gd[k] = gs[k] * i2d;
+    // gradient in x: g_x[i] = sum_m C[m][i] kappa b' grad_d[m]
+    double gx[12];
+    for (int i = 0; i < 4; ++i)
+      for (int al = 0; al < 3; ++al) {
+        double v = 0.0;
+        for (int m = 0; m < nz; ++m) v += (double)TI.C[m][i] * gd[3 * m + al];
+        gx[3 * i + al] = kap * b1 * v;
+      }
+    double Hx[144];
+    if (kind == 0) {
+      // point-point: H_z = kappa b'' n n^T + (kappa b'/d)(I - n n^T); clamp each part
+      const double nh[3] = {gd[0], gd[1], gd[2]};
+      const double lam_n = fmax(kap * b2, 0.0), lam_t = fmax(kap * b1 / d, 0.0);
+      double Hz[9];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          Hz[3 * i + j] = lam_n * nh[i] * nh[j] + lam_t * ((i == j ? 1.0 : 0.0) - nh[i] * nh[j]);
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+          const double cc = (double)(TI.C[0][i] * TI.C[0][j]);
+          for (int al = 0; al < 3; ++al)
+            for (int be = 0; be < 3; ++be) Hx[(3 * i + al) * 12 + 3 * j + be] = cc * Hz[3 * al + be];
+        }
+    } else {
+      // points the type involves (columns of C with a nonzero entry)
+      int pts[4], np = 0;
+      for (int i = 0; i < 4; ++i) {
+        bool used = false;
+        for (int m = 0; m < nz; ++m) used |= TI.C[m][i] != 0;
+        if (used) pts[np++] = i;
+      }
+      const int nb = np - 1, D = 3 * nb;
+      // H_z = c1 grad_d grad_d^T + c2 hess_s, then B = M^T H_z M with M = C K
+      const double c1 = kap * (b2 - b1 / d), c2 = kap * b1 * i2d;
+      double Hz[81];
+      for (int r = 0; r < 9; ++r)
+        for (int q = 0; q < 9; ++q) Hz[r * 9 + q] = c1 * gd[r] * gd[q] + c2 * Hs[r * 9 + q];
+      double M[3][3];
+      for (int m = 0; m < 3; ++m)
+        for (int bb = 0; bb < 3; ++bb) {
+          double v = 0.0;
+          if (m < nz && bb < nb)
+            for (int q = 0; q < np; ++q)
+              v += (double)TI.C[m][pts[q]] * (np == 4 ? c_K4[q][bb] : c_K3[q][bb]);
+          M[m][bb] = v;
+        }
+      double B[81];
+      for (int ab = 0; ab < nb; ++ab)
+        for (int bb = 0; bb < nb; ++bb)
+          for (int al = 0; al < 3; ++al)
+            for (int be = 0; be < 3; ++be) {
+              double v = 0.0;
+              for (int m = 0; m < nz; ++m)
+                for (int m2 = 0; m2 < nz; ++m2) v += M[m][ab] * M[m2][bb] * Hz[(3 * m + al) * 9 + 3 * m2 + be];
+              B[(3 * ab + al) * D + 3 * bb + be] = v;
+            }
+      double V[81];
+      jacobi_sym(B, V, D);
+      // W = (K x I) V : 3np x D ; H+ = sum_k max(lambda_k,0) W_k W_k^T on the involved points
+      double W[108];
+      for (int q = 0; q < np; ++q)
+        for (int al = 0; al < 3; ++al)
+          for (int k = 0; k < D; ++k) {
+            double v = 0.0;
+            for (int ab = 0; ab < nb; ++ab) v += (np == 4 ? c_K4[q][ab] : c_K3[q][ab]) * V[(3 * ab + al) * D + k];
+            W[(3 * q + al) * 9 + k] = v;
+          }
+      for (int i = 0; i < 144; ++i) Hx[i] = 0.0;
+      for (int q1 = 0; q1 < np; ++q1)
+        for (int al = 0; al < 3; ++al)
+          for (int q2 = q1; q2 < np; ++q2)
+            for (int be = 0; be < 3; ++be) {
+              const int r = 3 * q1 + al, q = 3 * q2 + be;
+              if (q2 == q1 && be < al) continue;
+              double v = 0.0;
+              for (int k = 0; k < D; ++k) {
+                const double lk = B[k * D + k];
+                if (lk > 0.0) v += lk * W[r * 9 + k] * W[q * 9 + k];
+              }
+              const int gr = 3 * pts[q1] + al, gq = 3 * pts[q2] + be;
+              Hx[gr * 12 + gq] = v;
+              Hx[gq * 12 + gr] = v;
+            }
+    }
+    // scatter
+    if (A.grad)
+      for (int i = 0; i < 4; ++i)
+        for (int al = 0; al < 3; ++al) atomicAdd(&A.grad[(size_t)al * A.n + s.v[i]], gx[3 * i + al]);
+    int used_mask = 0;
+    for (int i = 0; i < 4; ++i)
+      for (int m = 0; m < nz; ++m) used_mask |= (TI.C[m][i] != 0) << i;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        if (!((used_mask >> i) & (used_mask >> j) & 1)) continue;  // structural zero block
+        const int64_t bi = find_block(A.row_ptr, A.col, s.v[i], s.v[j]);
+        if (bi >= A.row_ptr[s.v[i] + 1] || A.col[bi] != s.v[j]) {
+          atomicOr(A.status, (unsigned long long)CB_DEV_CAPACITY);  // pattern miss: never expected
+          continue;
+        }
+        double* dst = A.val + 9 * bi;
+        for (int al = 0; al < 3; ++al)
+          for (int be = 0; be < 3; ++be) atomicAdd(&dst[3 * al + be], Hx[(3 * i + al) * 12 + 3 * j + be]);
+      }
+  }
+  // energy: warp sum then one atomic per warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e_local += __shfl_xor_sync(0xffffffffu, e_local, o);
+  if ((threadIdx.x & 31) == 0 && e_local != 0.0) atomicAdd(A.energy, e_local);
+}
+
+__global__ void k_energy_final(const double* __restrict__ acc, const unsigned long long* __restrict__ status,
+                               double* __restrict__ out) {
+  double e = *acc;
+  if (*status & CB_DEV_PENETRATION) e = __longlong_as_double(0x7ff0000000000000LL);
+  *out = e;
+}
+
+__global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+
+}  // namespace
+
+cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
+  uint64_t* sc = scalars(s);
+  unsigned long long* dmin = (unsigned long long*)(sc + SC_DBAR_MIN_BITS);
+  unsigned long long* nf = (unsigned long long*)(sc + SC_NFILT);
+  k_set_u64<<<1, 1, 0, cb_count(st)>>>(dmin, 0x7ff0000000000000ull);
+  k_set_u64<<<1, 1, 0, cb_count(st)>>>(nf, 0ull);
+  if (s->kind == CB_ROD) {
+    CB_TRY(buf_ensure(s->S, sizeof(double) * (size_t)s->n, st));
+    CB_TRY(buf_ensure(s->win, sizeof(int32_t) * (size_t)std::max(1, s->E), st));
+    k_arclength<<<cb_grid(s->n_rods), CB_THREADS, 0, cb_count(st)>>>(s->n_rods, bp<int32_t>(s->rod_ptr), bp<double>(s->rest),
+                                                           s->n, bp<double>(s->S));
+    if (s->E > 0)
+      k_rod_window<<<cb_grid(s->E), CB_THREADS, 0, cb_count(st)>>>(s->E, bp<int32_t>(s->ev0), bp<int32_t>(s->ev1),
+                                                         bp<int32_t>(s->comp), bp<double>(s->S), s->a,
+                                                         bp<int32_t>(s->win), dmin, nf);
+    CB_CUDA(cudaGetLastError());
+    uint64_t h[2];
+    CB_TRY(read_scalars(s, SC_DBAR_MIN_BITS, 1, &h[0], st));
+    CB_TRY(read_scalars(s, SC_NFILT, 1, &h[1], st));
+    memcpy(&s->dbar_min, &h[0], 8);
+    s->n_frest = (int64_t)h[1];
+  } else {
+    // rest broad phase at the full activation, then rest distances below a
+    int64_t nr = 0;
+    DevBuf rc;
+    CB_TRY(broad_phase(s, s->bw, bp<double>(s->rest), nullptr, 0.5 * s->a, rc, &nr, st));
+    if (nr > 0) {
+      DevBuf flag, pos, dbar;
+      CB_TRY(buf_ensure(flag, sizeof(uint32_t) * (size_t)nr, st));
+      CB_TRY(buf_ensure(pos, sizeof(uint32_t) * ((size_t)nr + 1), st));
+      CB_TRY(buf_ensure(dbar, sizeof(double) * (size_t)nr, st));
+      CB_TRY(buf_ensure(s->scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(nr) + 8), st));
+      k_rest_filter<<<cb_grid(nr), CB_THREADS, 0, cb_count(st)>>>(nr, bp<uint64_t>(rc), bp<int32_t>(s->ev0),
+                                                        bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T,
+                                                        bp<int32_t>(s->comp), bp<double>(s->rest), s->n, s->a,
+                                                        bp<uint32_t>(flag), bp<double>(dbar), dmin);
+      uint32_t* tot = (uint32_t*)(sc + SC_COUNT1);
+      cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(flag), bp<uint32_t>(pos), nr, bp<uint32_t>(s->scan_tmp),
+                                              tot, st);
+      uint64_t h[2];
+      CB_CUDA(cudaGetLastError());
+      CB_TRY(read_scalars(s, SC_COUNT1, 1, &h[0], st));
+      const int64_t nf_ = (int64_t)(uint32_t)h[0];
+      CB_TRY(buf_ensure(s->frest, sizeof(uint64_t) * (size_t)std::max<int64_t>(1, nf_), st));
+      CB_TRY(buf_ensure(s->frest_dbar, sizeof(double) * (size_t)std::max<int64_t>(1, nf_), st));
+      cbp::k_compact<uint64_t, uint32_t><<<cb_grid(nr), CB_THREADS, 0, cb_count(st)>>>(bp<uint64_t>(rc), bp<uint32_t>(flag),
+                                                                         bp<uint32_t>(pos), nr, bp<uint64_t>(s->frest));
+      cbp::k_compact<double, uint32_t><<<cb_grid(nr), CB_THREADS, 0, cb_count(st)>>>(bp<double>(dbar), bp<uint32_t>(flag),
+                                                                       bp<uint32_t>(pos), nr,
+                                                                       bp<double>(s->frest_dbar));
+      CB_CUDA(cudaGetLastError());
+      CB_TRY(read_scalars(s, SC_DBAR_MIN_BITS, 1, &h[1], st));
+      memcpy(&s->dbar_min, &h[1], 8);
+      s->n_frest = nf_;
+      buf_free(flag, st);
+      buf_free(pos, st);
+      buf_free(dbar, st);
+    } else {
+      s->dbar_min = INFINITY;
+      s->n_frest = 0;
+    }
+    buf_free(rc, st);
+  }
+  if (s->n_frest > 0 && !(s->dbar_min > 0.0)) return CB_ERR_DEGENERATE;
+  return CB_OK;
+}
+
+cb_status filter_apply(cb_scene* s, cudaStream_t st) {
+  const int64_t nc = s->n_cand;
+  CB_TRY(buf_ensure(s->klass, (size_t)std::max<int64_t>(1, nc), st));
+  unsigned long long* nf = (unsigned long long*)(scalars(s) + SC_NFILT);
+  k_set_u64<<<1, 1, 0, cb_count(st)>>>(nf, 0ull);
+  if (nc == 0) return CB_OK;
+  const int off = (s->filter == CB_FILTER_OFF) ? 1 : 0;
+  if (s->kind == CB_ROD)
+    k_filter_rod<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(nc, bp<uint64_t>(s->cand), bp<int32_t>(s->ev0),
+                                                     bp<int32_t>(s->comp), bp<int32_t>(s->win), off,
+                                                     bp<uint8_t>(s->klass), nf);
+  else
+    k_filter_shell<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(nc, bp<uint64_t>(s->cand), bp<uint64_t>(s->frest), s->n_frest,
+                                                       off, bp<uint8_t>(s->klass), nf);
+  CB_CUDA(cudaGetLastError());
+  return CB_OK;
+}
+
+static int bits_for(int64_t v) {
+  int b = 1;
+  while ((1ll << b) <= v) ++b;
+  return b;
+}
+
+static PassParams pass_params(const cb_scene* s) {
+  PassParams P;
+  P.xi = s->xi;
+  P.dhat = s->dhat;
+  P.a = s->a;
+  P.dbar_min = std::isfinite(s->dbar_min) ? s->dbar_min : 0.0;
+  P.kappa = s->kappa;
+  P.single = (s->filter == CB_FILTER_SINGLE);
+  P.core_temp = s->core_temp;
+  return P;
+}
+
+cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad, cudaStream_t st) {
+  const int64_t nc = s->n_cand;
+  uint64_t* sc = scalars(s);
+  unsigned long long* status = (unsigned long long*)(sc + SC_STATUS);
+  unsigned long long* ncore = (unsigned long long*)(sc + SC_NCORE);
+  double* eacc = (double*)(sc + SC_ENERGY);
+  k_set_u64<<<1, 1, 0, cb_count(st)>>>(ncore, 0ull);
+  k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)eacc, 0ull);
+  if (grad) CB_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * 3 * (size_t)s->n, st));
+  s->n_active = 0;
+  s->nnzb = 0;
+  CB_TRY(buf_ensure(s->bsr_row, sizeof(int32_t) * ((size_t)s->n + 1), st));
+  CB_CUDA(cudaMemsetAsync(s->bsr_row.p, 0, sizeof(int32_t) * ((size_t)s->n + 1), st));
+  const PassParams P = pass_params(s);
+  if (nc > 0) {
+    CB_TRY(buf_ensure(s->cd, sizeof(double) * (size_t)nc, st));
+    CB_TRY(buf_ensure(s->ctype, (size_t)nc, st));
+    CB_TRY(buf_ensure(s->ccls, (size_t)nc, st));
+    CB_TRY(buf_ensure(s->cflag, sizeof(uint32_t) * (size_t)nc, st));
+    CB_TRY(buf_ensure(s->cpos, sizeof(uint32_t) * ((size_t)nc + 1), st));
+    CB_TRY(buf_ensure(s->scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(nc) + 8), st));
+    k_distance<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(nc, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass),
+                                                   bp<int32_t>(s->ev0), bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T,
+                                                   x, s->n, P, bp<double>(s->cd), bp<int8_t>(s->ctype),
+                                                   bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), status, ncore);
+    uint32_t* tot = (uint32_t*)(sc + SC_COUNT1);
+    cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(s->cflag), bp<uint32_t>(s->cpos), nc,
+                                            bp<uint32_t>(s->scan_tmp), tot, st);
+    CB_CUDA(cudaGetLastError());
+    uint64_t h;
+    CB_TRY(read_scalars(s, SC_COUNT1, 1, &h, st));
+    s->n_active = (int64_t)(uint32_t)h;
+  }
+  const int64_t na = s->n_active;
+  if (na > 0) {
+    CB_TRY(buf_ensure(s->aidx, sizeof(uint32_t) * (size_t)na, st));
+    k_active_compact<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(nc, bp<uint32_t>(s->cflag), bp<uint32_t>(s->cpos),
+                                                         bp<uint32_t>(s->aidx));
+    // BSR pattern: sorted unique (row, col) of the 16 blocks of every active stencil
+    const int64_t m = 16 * na;
+    const int bn = bits_for(s->n);
+    for (int b = 0; b < 2; ++b) CB_TRY(buf_ensure(s->bkey[b], sizeof(uint64_t) * (size_t)m, st));
+    CB_TRY(buf_ensure(s->bflag, sizeof(uint32_t) * (size_t)m, st));
+    CB_TRY(buf_ensure(s->bpos, sizeof(uint32_t) * ((size_t)m + 1), st));
+    CB_TRY(buf_ensure(s->hist, sizeof(uint32_t) * (size_t)cbp::radix_hist_elems(m), st));
+    CB_TRY(buf_ensure(s->scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(cbp::radix_hist_elems(m)) +
+                                                                cbp::scan_tmp_elems(m) + 8),
+                      st));
+    k_block_keys<<<cb_grid(na), CB_THREADS, 0, cb_count(st)>>>(na, bp<uint32_t>(s->aidx), bp<uint64_t>(s->cand),
+                                                     bp<int32_t>(s->ev0), bp<int32_t>(s->ev1), bp<int32_t>(s->tv),
+                                                     s->T, bn, bp<uint64_t>(s->bkey[0]));
+    int r = cbp::radix_sort<uint64_t, uint32_t, false>(bp<uint64_t>(s->bkey[0]), nullptr, bp<uint64_t>(s->bkey[1]),
+                                                       nullptr, m, 0, 2 * bn, bp<uint32_t>(s->hist),
+                                                       bp<uint32_t>(s->scan_tmp), st);
+    const uint64_t* bk = bp<uint64_t>(s->bkey[r]);
+    k_unique_flag<<<cb_grid(m), CB_THREADS, 0, cb_count(st)>>>(m, bk, bp<uint32_t>(s->bflag));
+    uint32_t* tot = (uint32_t*)(sc + SC_COUNT1);
+    cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(s->bflag), bp<uint32_t>(s->bpos), m,
+                                            bp<uint32_t>(s->scan_tmp), tot, st);
+    CB_CUDA(cudaGetLastError());
+    uint64_t h;
+    CB_TRY(read_scalars(s, SC_COUNT1, 1, &h, st));
+    s->nnzb = (int64_t)(uint32_t)h;
+    CB_TRY(buf_ensure(s->bsr_col, sizeof(int32_t) * (size_t)s->nnzb, st));
+    CB_TRY(buf_ensure(s->bsr_val, sizeof(double) * 9 * (size_t)s->nnzb, st));
+    CB_TRY(buf_ensure(s->row_cnt, sizeof(uint32_t) * ((size_t)s->n + 1), st));
+    CB_CUDA(cudaMemsetAsync(s->row_cnt.p, 0, sizeof(uint32_t) * ((size_t)s->n + 1), st));
+    CB_CUDA(cudaMemsetAsync(s->bsr_val.p, 0, sizeof(double) * 9 * (size_t)s->nnzb, st));
+    k_unique_write<<<cb_grid(m), CB_THREADS, 0, cb_count(st)>>>(m, bk, bp<uint32_t>(s->bflag), bp<uint32_t>(s->bpos), bn,
+                                                      bp<int32_t>(s->bsr_col), bp<uint32_t>(s->row_cnt));
+    cbp::exclusive_scan<uint32_t, int32_t>(bp<uint32_t>(s->row_cnt), bp<int32_t>(s->bsr_row), (int64_t)s->n + 1,
+                                           (int32_t*)bp<uint32_t>(s->scan_tmp), (int32_t*)nullptr, st);
+    HessArgs A;
+    A.na = na;
+    A.aidx = bp<uint32_t>(s->aidx);
+    A.cand = bp<uint64_t>(s->cand);
+    A.cd = bp<double>(s->cd);
+    A.ctype = bp<int8_t>(s->ctype);
+    A.ccls = bp<uint8_t>(s->ccls);
+    A.ev0 = bp<int32_t>(s->ev0);
+    A.ev1 = bp<int32_t>(s->ev1);
+    A.tv = bp<int32_t>(s->tv);
+    A.T = s->T;
+    A.x = x;
+    A.n = s->n;
+    A.P = P;
+    A.row_ptr = bp<int32_t>(s->bsr_row);
+    A.col = bp<int32_t>(s->bsr_col);
+    A.val = bp<double>(s->bsr_val);
+    A.grad = grad;
+    A.energy = eacc;
+    A.status = status;
+    if (s->timing) cudaEventRecord(s->ev[10], st);
+    k_barrier_hess<<<cb_grid(na, 128), 128, 0, cb_count(st)>>>(A);
+    if (s->timing) cudaEventRecord(s->ev[11], st);
+    CB_CUDA(cudaGetLastError());
+  }
+  if (energy) k_energy_final<<<1, 1, 0, cb_count(st)>>>(eacc, status, energy);
+  CB_CUDA(cudaGetLastError());
+  return CB_OK;
+}

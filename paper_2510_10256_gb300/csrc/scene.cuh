@@ -1,0 +1,136 @@
+// scene.cuh -- internal scene object and the launchers each stage file provides.
+#pragma once
+#include <vector>
+
+#include "common.cuh"
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// A growable device buffer: keeps its allocation, grows by 25 % headroom.
+cb_status buf_ensure(DevBuf& b, size_t bytes, cudaStream_t st);
+void buf_free(DevBuf& b, cudaStream_t st);
+template <typename T>
+static inline T* bp(const DevBuf& b) {
+  return (T*)b.p;
+}
+
+// Workspace of one broad phase (static or swept) -- reused between calls.
+struct BroadWork {
+  DevBuf box32;       // float4 lo, float4 hi per primitive
+  DevBuf box64;       // double lo[3], hi[3] per primitive
+  DevBuf bounds;      // 8 x uint32 (ordered-float min/max)
+  DevBuf cell_cnt;    // uint32 per primitive
+  DevBuf cell_off;    // uint32 per primitive (+1)
+  DevBuf ekey[2];     // uint32 cell key per entry (ping-pong)
+  DevBuf eval[2];     // uint32 primitive per entry
+  DevBuf run_flag;    // uint32 per entry
+  DevBuf run_id;      // uint32 per entry
+  DevBuf run_start;   // uint32 per run (+1)
+  DevBuf pair_cnt;    // uint32 per entry
+  DevBuf pair_off;    // uint32 per entry (+1)
+  DevBuf ckey[2];     // uint64 compact candidate keys (ping-pong)
+  DevBuf scan_tmp;
+  DevBuf hist;
+  float cell = 0.f;   // cell size used last
+};
+
+struct cb_scene {
+  int kind = 0;
+  int n = 0, E = 0, T = 0, n_rods = 0;
+  int n_prims = 0;     // broad-phase primitives
+  int bits_i = 0, bits_j = 0;
+  double xi = 0, dhat = 0, a = 0, kappa = 1;
+  int filter = CB_FILTER_DOUBLE;
+  int core_temp = 1;
+  double dbar_min = 0;  // +inf when nothing is filtered
+  float cell_hint = 0.f;
+  cudaStream_t last_stream = nullptr;
+  int device = 0;
+
+  // topology on device
+  DevBuf ev0, ev1;      // int32 [E]
+  DevBuf tv;            // int32 [3][T]
+  DevBuf comp;          // int32 [n]
+  DevBuf rest;          // double [3][n]
+  DevBuf rod_ptr;       // int32 [n_rods+1] (rods)
+  // filter tables
+  DevBuf S;             // double [n] rods: arc length
+  DevBuf win;           // int32 [E] rods: last filtered partner edge
+  DevBuf frest;         // uint64 shells: sorted rest-filtered keys
+  DevBuf frest_dbar;    // double
+  int64_t n_frest = 0;
+
+  // pass state
+  BroadWork bw;         // static broad phase
+  BroadWork bwc;        // swept broad phase (CCD)
+  DevBuf cand;          // uint64 [nc] sorted candidate keys
+  int64_t n_cand = 0;
+  DevBuf klass;         // uint8 [nc]
+  DevBuf cd;            // double [nc] distance
+  DevBuf cflag;         // uint32 [nc] active flag
+  DevBuf cpos;          // uint32 [nc+1] scan of flags
+  DevBuf ctype;         // int8 [nc]
+  DevBuf ccls;          // uint8 [nc] final class (with C)
+  int64_t n_active = 0;
+  DevBuf aidx;          // uint32 [na] candidate index of each active pair
+  DevBuf bkey[2];       // uint64 [16 na]
+  DevBuf bflag, bpos;   // uint32
+  DevBuf bsr_row;       // int32 [n+1]
+  DevBuf bsr_col;       // int32 [nnzb]
+  DevBuf bsr_val;       // double [nnzb][9]
+  DevBuf row_cnt;       // uint32 [n+1]
+  int64_t nnzb = 0;
+  DevBuf ccd_keys;      // uint64 [nccd]
+  DevBuf ccd_t;         // double [nccd]
+  DevBuf ccd_cls;       // uint8 [nccd]
+  int64_t n_ccd = 0;
+  DevBuf scan_tmp;
+  DevBuf hist;
+  DevBuf dev_scalars;   // misc device scalars (counters, energy, alpha bits, status)
+
+  uint64_t* h_pinned = nullptr;  // pinned host scratch
+  int32_t status_host = 0;
+
+  bool timing = false;
+  cudaEvent_t ev[12] = {};
+  float stage_ms[5] = {0, 0, 0, 0, 0};
+  int64_t counts_filtered = 0, counts_core = 0;
+  int ccd_max_iters = 0;
+};
+
+// device scalar slots (uint64 each) inside dev_scalars
+enum {
+  SC_COUNT0 = 0,
+  SC_COUNT1 = 1,
+  SC_STATUS = 2,
+  SC_ENERGY = 3,
+  SC_ALPHA_BITS = 4,
+  SC_DBAR_MIN_BITS = 5,
+  SC_ITERS = 6,
+  SC_NFILT = 7,
+  SC_NCORE = 8,
+  SC_N = 16
+};
+
+static inline uint64_t* scalars(cb_scene* s) { return (uint64_t*)s->dev_scalars.p; }
+
+// read n uint64 device scalars into host (sync on stream)
+cb_status read_scalars(cb_scene* s, int first, int count, uint64_t* out, cudaStream_t st);
+
+// broad.cu
+// Candidate pairs of x (p == nullptr) or of the sweep x -> x + p; boxes are
+// inflated by h.  Writes sorted canonical keys into *out (grown as needed) and
+// their count into *n_out.
+cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* p, double h, DevBuf& out,
+                      int64_t* n_out, cudaStream_t st);
+
+// narrow.cu
+cb_status filter_precompute(cb_scene* s, cudaStream_t st);
+cb_status filter_apply(cb_scene* s, cudaStream_t st);
+cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad, cudaStream_t st);
+
+// ccd.cu
+cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, cudaStream_t st);

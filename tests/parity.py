@@ -1,0 +1,109 @@
+"""GPU-vs-oracle comparison used by the -m gpu tests and by smoke().
+
+Acceptance (per pass):
+  * candidate set C, filtered set F, class-C set, CCD candidate set, BSR
+    pattern: bit-exact sorted keys;
+  * active set: bit-exact except pairs whose oracle distance lies within
+    1e-12 (relative) of their activation threshold, where the barrier and its
+    derivatives vanish;
+  * distances of active pairs: 1e-12 relative;
+  * energy: 1e-9 relative;
+  * gradient and BSR entries: |gpu - oracle| <= 1e-9 * sum |contributions|
+    (+ 1e-30 absolute), allowing for summation order;
+  * alpha: alpha_gpu <= alpha_oracle and alpha_oracle - alpha_gpu <= 1e-9.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+
+
+def run_gpu(sc, mode="double", core_temp=True, x=None, p=None, paper_literal=False):
+    import torch
+    from paper_2510_10256_gb300.contact import ContactScene
+    dev = torch.device("cuda:0")
+    cs = ContactScene.from_scene(sc, mode=mode, core_temp=core_temp, paper_literal=paper_literal)
+    xx = torch.from_numpy(np.ascontiguousarray(sc.x if x is None else x)).to(dev)
+    pp = torch.from_numpy(np.ascontiguousarray(sc.p if p is None else p)).to(dev)
+    energy = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad = torch.zeros(3, sc.n, dtype=torch.float64, device=dev)
+    alpha = torch.zeros(1, dtype=torch.float64, device=dev)
+    cs.run_pass(xx, pp, energy, grad, alpha)
+    torch.cuda.synchronize()
+    out = dict(C=cs.pairs("candidate"), F=cs.pairs("filtered"), CC=cs.pairs("core"),
+               A=cs.active(), ccd=cs.ccd(), bsr=cs.bsr(), energy=float(energy.item()),
+               grad=grad.cpu().numpy(), alpha=float(alpha.item()), stats=cs.stats(),
+               status=cs.sync_status(), frest=cs.pairs("rest_filtered"))
+    cs.close()
+    return out
+
+
+def threshold_band(sc, orc: O.PassResult, mode="double"):
+    """Candidates whose distance is within 1e-12 of an activity or class
+    threshold (their activity / class may legitimately differ by rounding)."""
+    xi, a = sc.thickness, sc.activation
+    d = orc.d
+    thr = []
+    if mode != "single":
+        thr.append(np.full_like(d, xi))
+    thr.append(np.where(orc.klass == O.KLASS_F, orc.dbar_min, np.where(
+        (orc.klass == O.KLASS_C) | (mode == "single"), a, xi + sc.dhat)))
+    band = np.zeros(d.size, bool)
+    for t in thr:
+        band |= np.abs(d - t) <= 1e-12 * np.maximum(1.0, np.abs(t))
+    return band
+
+
+def compare(sc, g: dict, orc: O.PassResult, mode="double", check_ccd=True) -> dict:
+    """Raise AssertionError on any violation; return a summary."""
+    rep = {}
+    assert np.array_equal(g["C"], orc.C), f"candidate sets differ: {g['C'].size} vs {orc.C.size}"
+    rep["C"] = int(orc.C.size)
+    assert np.array_equal(g["F"], orc.keys_of(O.KLASS_F)), "filtered sets differ"
+    rep["F"] = int(g["F"].size)
+    if sc.kind == "shell":
+        assert np.array_equal(g["frest"], orc.F_rest), "rest-filtered sets differ"
+    dm_g, dm_o = g["stats"]["dbar_min"], orc.dbar_min
+    assert (np.isinf(dm_g) and np.isinf(dm_o)) or abs(dm_g - dm_o) <= 1e-12 * abs(dm_o), (dm_g, dm_o)
+    band = threshold_band(sc, orc, mode)
+    band_keys = set(orc.C[band].tolist())
+    cc_o = set(orc.keys_of(O.KLASS_C).tolist())
+    cc_g = set(g["CC"].tolist())
+    assert (cc_o ^ cc_g) <= band_keys, "class-C sets differ outside the threshold band"
+    rep["core"] = len(cc_g)
+    act_o = set(orc.active_keys.tolist())
+    act_g = set(g["A"]["keys"].tolist())
+    assert (act_o ^ act_g) <= band_keys, f"active sets differ: {len(act_o ^ act_g)} outside band"
+    assert np.all(np.diff(g["A"]["keys"].astype(np.uint64).view(np.int64)) > 0) or g["A"]["keys"].size < 2
+    rep["active"] = len(act_g)
+    # distances of active pairs
+    idx_o = np.searchsorted(orc.C, g["A"]["keys"])
+    d_o = orc.d[idx_o]
+    rel = np.abs(g["A"]["d"] - d_o) / np.maximum(d_o, 1e-300)
+    assert rel.size == 0 or rel.max() <= 1e-12, f"distance rel err {rel.max()}"
+    rep["d_relerr"] = float(rel.max()) if rel.size else 0.0
+    assert np.array_equal(g["A"]["dtype"], orc.dtype[idx_o]) or (act_o ^ act_g), "distance types differ"
+    # energy / gradient / BSR
+    if np.isfinite(orc.energy):
+        assert abs(g["energy"] - orc.energy) <= 1e-9 * max(abs(orc.energy), 1e-300), (g["energy"], orc.energy)
+        gerr = np.abs(g["grad"] - orc.grad)
+        assert np.all(gerr <= 1e-9 * orc.grad_abs + 1e-30), f"gradient err {float((gerr / (orc.grad_abs + 1e-300)).max())}"
+        rep["grad_relerr"] = float((gerr / (orc.grad_abs + 1e-300)).max()) if gerr.size else 0.0
+        rp, col, val = g["bsr"]
+        if not (act_o ^ act_g):
+            assert np.array_equal(rp, orc.bsr_row_ptr) and np.array_equal(col, orc.bsr_col), "BSR pattern differs"
+            verr = np.abs(val - orc.bsr_val)
+            assert np.all(verr <= 1e-9 * orc.bsr_abs + 1e-30), \
+                f"BSR value err {float((verr / (orc.bsr_abs + 1e-300)).max())}"
+            rep["bsr_relerr"] = float((verr / (orc.bsr_abs + 1e-300)).max()) if verr.size else 0.0
+        rep["nnzb"] = int(col.size)
+    else:
+        assert not np.isfinite(g["energy"])
+    if check_ccd:
+        assert np.array_equal(g["ccd"]["keys"], orc.ccd_keys), "CCD candidate sets differ"
+        rep["ccd"] = int(orc.ccd_keys.size)
+        assert g["alpha"] <= orc.alpha and orc.alpha - g["alpha"] <= 1e-9, (g["alpha"], orc.alpha)
+        rep["alpha"] = g["alpha"]
+        rep["alpha_oracle"] = orc.alpha
+    return rep

@@ -1,0 +1,35 @@
+"""The C-ABI library builds for sm_103a and exports every entry point that
+include/contact.h declares (no GPU needed: symbols only, no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2510_10256_gb300 import contact as CT
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "contact.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:cb_status|const char\*|int64_t)\s+(\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_names_match_binding():
+    assert _declared() == sorted(CT.ABI_FUNCTIONS)
+
+
+def test_library_exports_every_declared_symbol():
+    CT.build()
+    lib = ctypes.CDLL(CT.LIB_PATH)
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_library_pure_calls_without_gpu():
+    CT.build()
+    assert CT.lib().cb_version().decode().startswith("gb300-contact")
+    assert CT.status_str(CT.CB_ERR_PENETRATION).startswith("pair")
+    assert CT.lib().cb_scene_destroy(None) == CT.CB_ERR_ARG

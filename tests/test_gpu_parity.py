@@ -1,0 +1,101 @@
+"""GPU (through the C ABI) vs the FP64 oracle, element by element."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_10256_gb300 import scenes as S
+from tests.parity import compare, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_10256_gb300 import contact
+    contact.build()
+    contact.lib()
+
+
+def _pair(sc, mode="double", **kw):
+    g = run_gpu(sc, mode=mode, **kw)
+    o = O.contact_pass(sc, mode=mode, core_temp=kw.get("core_temp", True))
+    return compare(sc, g, o, mode=mode), g, o
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tiny_shells(seed):
+    rep, _, _ = _pair(S.tiny_shell(seed))
+    assert rep["active"] > 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tiny_rods(seed):
+    rep, _, _ = _pair(S.tiny_rods(seed))
+    assert rep["C"] > 0
+
+
+@pytest.mark.parametrize("mode", ["double", "single", "off"])
+def test_modes_shell(mode):
+    _pair(S.tiny_shell(3, nx=6), mode=mode)
+
+
+@pytest.mark.parametrize("mode", ["double", "single", "off"])
+def test_modes_rod(mode):
+    _pair(S.woven_patch(n_warp=2, n_weft=2, nseg=48), mode=mode)
+
+
+def test_no_core_temp_reports_penetration():
+    sc = S.woven_patch(n_warp=2, n_weft=2, nseg=48)
+    g = run_gpu(sc, core_temp=False)
+    assert g["status"] == 4 and not np.isfinite(g["energy"])
+
+
+def test_woven_patch_full():
+    """The 16-yarn woven patch (4,112 vertices) in full."""
+    rep, g, o = _pair(S.woven_patch())
+    assert rep["core"] > 0 and rep["F"] > 0
+
+
+def test_pleated_sheet_reduced():
+    """48 x 48 pleated sheet: several hash tiles, all three classes active."""
+    rep, g, o = _pair(S.pleated_sheet(nx=48))
+    assert rep["F"] > 0 and rep["active"] > 1000
+
+
+def test_graded_disk_reduced():
+    _pair(S.graded_disk(target_tris=6000, L0=0.5))
+
+
+def test_flat_rest_no_rest_forces():
+    sc = S.flat_grid(nx=20)
+    g = run_gpu(sc)
+    assert g["energy"] == 0.0 and g["A"]["keys"].size == 0
+    g2 = run_gpu(sc, mode="off")
+    assert g2["energy"] > 0.0
+
+
+def test_empty_and_degenerate_inputs():
+    import torch
+    from paper_2510_10256_gb300.contact import ContactScene, ContactError
+    # single triangle: no non-incident pairs at all
+    sc = S.Scene("shell", np.array([[0, 1, 0], [0, 0, 1], [0, 0, 0.]]), np.array([[0, 1, 0], [0, 0, 1], [0, 0, 0.]]),
+                 np.zeros((3, 3)), 0.1, 0.01, tris=np.array([[0], [1], [2]], np.int32))
+    g = run_gpu(sc)
+    assert g["C"].size == 0 and g["energy"] == 0.0 and g["alpha"] == 1.0
+    # far-apart rods: nothing within reach
+    sc = S.tiny_rods(1)
+    sc.x = sc.x.copy()
+    sc.x[2, : sc.rod_ptr[1]] += 100.0
+    g = run_gpu(sc)
+    o = O.contact_pass(sc)
+    compare(sc, g, o)
+    # coincident rest vertices of a stencil -> degenerate
+    rest = np.array([[0, 1, 1, 2.0], [0, 0, 0, 0.0], [0, 0, 0, 0.0]])
+    with pytest.raises(ContactError):
+        ContactScene("rod", rest, 0.5, 0.1, rod_ptr=np.array([0, 4], np.int32))
+    # bad topology
+    with pytest.raises(ContactError):
+        ContactScene("shell", np.zeros((3, 3)), 0.1, 0.01, tris=np.array([[0], [1], [5]], np.int32))
