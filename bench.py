@@ -154,6 +154,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="pleated", choices=["pleated", "woven", "graded"])
+    ap.add_argument("--nx", type=int, default=0, help="pleated grid size (default: the full 256)")
     ap.add_argument("--cpu-nx", type=int, default=128, help="grid size of the oracle baseline sample")
     ap.add_argument("--ref-nx", type=int, default=96, help="grid size of a reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -181,7 +182,7 @@ def main():
         dist.barrier()
     from paper_2510_10256_gb300 import contact as CT
 
-    sc, desc = _workload(args.workload)
+    sc, desc = _workload(args.workload, reduced_nx=args.nx or None)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     cs = CT.ContactScene.from_scene(sc)
@@ -265,8 +266,14 @@ def main():
     hess_ms = statistics.mean(s[4] for s in stage)
     na = st["n_active"]
     achieved = FLOPS_PER_ACTIVE * na / (hess_ms / 1000.0) / 1e12 if hess_ms > 0 else 0.0
+    try:
+        fp64_meas = CT.measure_fma_tflops(True)
+        fp32_meas = CT.measure_fma_tflops(False, iters=65536)
+    except Exception:
+        fp64_meas = fp32_meas = None
     roofline = {"bound": "alu", "kernel": "k_barrier_hess (FP64 stage d)", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_fp64_fma_measured": fp64_meas, "peak_fp32_fma_measured": fp32_meas,
                 "traffic": None, "flops_per_active_pair": FLOPS_PER_ACTIVE, "active_pairs": na,
                 "kernel_ms": hess_ms, "peak_source": "derived: 152 SM x 2070 MHz x 4 FP64 flop/clk/SM"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

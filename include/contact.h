@@ -158,7 +158,10 @@ cb_status cb_get_pairs(cb_scene* scene, int32_t which, uint64_t* keys, int64_t c
 /* active pairs in key order: key, distance, class (0 U, 1 F, 2 C), distance type */
 cb_status cb_get_active(cb_scene* scene, uint64_t* keys, double* d, uint8_t* klass, int8_t* dtype,
                         int64_t cap, int64_t* count);
-/* per CCD candidate (key order): time of impact bound t_p and class */
+/* per CCD candidate (key order): t_p and class.  The step bound needs only
+ * the minimum, so pairs that provably cannot attain it are not iterated: for
+ * them t holds a lower bound of t_p (their first additive-CCD step).  Bit 0x80
+ * of the class byte marks an exact t_p; the low bits are 0 U, 1 F, 2 C. */
 cb_status cb_get_ccd(cb_scene* scene, uint64_t* keys, double* t, uint8_t* klass, int64_t cap,
                      int64_t* count);
 /* BSR: row_ptr [n+1], col [nnzb], val [nnzb][9] */
@@ -181,6 +184,11 @@ cb_status cb_set_timing(cb_scene* scene, int32_t on);
 const char* cb_status_str(cb_status s);
 /* process-wide number of CUDA kernels the library has launched so far */
 int64_t cb_kernel_launches(void);
+/* Diagnostic (no counterpart in the paper): measured fused-multiply-add
+ * throughput of the current GPU in TFLOP/s (2 flops per FMA), fp64 = 1 for
+ * double, 0 for float; `blocks` blocks of 256 threads, `iters` x 8 FMA each.
+ * Used as the roofline denominator of the FP64-bound kernels.  sync. */
+cb_status cb_measure_fma_tflops(int32_t fp64, int32_t blocks, int32_t iters, double* tflops);
 /* library version string */
 const char* cb_version(void);
 

@@ -29,7 +29,7 @@ MODES = {"double": CB_FILTER_DOUBLE, "single": CB_FILTER_SINGLE, "off": CB_FILTE
 ABI_FUNCTIONS = ["cb_scene_create", "cb_scene_destroy", "contact_build", "contact_filter", "barrier_eval",
                  "ccd_step", "cb_get_pairs", "cb_get_active", "cb_get_ccd", "cb_get_bsr", "cb_bsr_device",
                  "cb_get_stats", "cb_sync_status", "cb_get_stage_ms", "cb_set_timing", "cb_status_str",
-                 "cb_version", "cb_kernel_launches"]
+                 "cb_version", "cb_kernel_launches", "cb_measure_fma_tflops"]
 
 
 class ContactError(RuntimeError):
@@ -73,6 +73,7 @@ def lib():
         L.cb_version.restype = C.c_char_p
         L.cb_kernel_launches.restype = i64
         L.cb_kernel_launches.argtypes = []
+        L.cb_measure_fma_tflops.argtypes = [i32, i32, i32, C.POINTER(C.c_double)]
         L.cb_scene_create.argtypes = [C.POINTER(SceneDesc), vp, C.POINTER(vp)]
         L.cb_scene_destroy.argtypes = [vp]
         L.contact_build.argtypes = [vp, vp, vp]
@@ -94,6 +95,13 @@ def lib():
 
 def kernel_launches() -> int:
     return int(lib().cb_kernel_launches())
+
+
+def measure_fma_tflops(fp64: bool = True, blocks: int = 152 * 8, iters: int = 4096) -> float:
+    """Measured FMA throughput of the current GPU (TFLOP/s)."""
+    t = C.c_double()
+    _check(lib().cb_measure_fma_tflops(int(fp64), blocks, iters, C.byref(t)), "cb_measure_fma_tflops")
+    return t.value
 
 
 def status_str(s: int) -> str:

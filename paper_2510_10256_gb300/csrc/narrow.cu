@@ -373,46 +373,98 @@ __device__ void s_derivs(int kind, const d3* z, double* gs, double* Hs) {
     }
 }
 
-// cyclic Jacobi on a symmetric n x n A (row-major, n <= 9); V receives the
-// eigenvectors (columns); the eigenvalues are left on the diagonal of A
-__device__ int jacobi_sym(double* A, double* V, const int n) {
-  for (int i = 0; i < n * n; ++i) V[i] = 0.0;
-  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+// Cyclic Jacobi rotations on a symmetric n x n A (row-major, n <= 9),
+// accumulated into V (V <- V J); runs until the off-diagonal Frobenius norm
+// is at most sqrt(tol2) of the full norm, or max_sweeps.  The eigenvalues are
+// left on the diagonal of A.
+template <typename R>
+__device__ int jacobi_sweeps(R* A, R* V, const int n, const R tol2, const int max_sweeps) {
   int sweep;
-  for (sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0, fro = 0.0;
+  for (sweep = 0; sweep < max_sweeps; ++sweep) {
+    R off = 0, fro = 0;
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) {
-        const double a2 = A[i * n + j] * A[i * n + j];
+        const R a2 = A[i * n + j] * A[i * n + j];
         fro += a2;
         if (i != j) off += a2;
       }
-    if (fro == 0.0 || off <= 1e-30 * fro) break;
+    if (fro == R(0) || off <= tol2 * fro) break;
     for (int p = 0; p < n - 1; ++p)
       for (int q = p + 1; q < n; ++q) {
-        const double apq = A[p * n + q];
-        if (apq == 0.0) continue;
-        const double tau = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        const R apq = A[p * n + q];
+        if (apq == R(0)) continue;
+        const R tau = (A[q * n + q] - A[p * n + p]) / (R(2) * apq);
+        const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
+        const R c = R(1) / sqrt(R(1) + t * t), s = t * c;
         for (int k = 0; k < n; ++k) {
-          const double akp = A[k * n + p], akq = A[k * n + q];
+          const R akp = A[k * n + p], akq = A[k * n + q];
           A[k * n + p] = c * akp - s * akq;
           A[k * n + q] = s * akp + c * akq;
         }
         for (int k = 0; k < n; ++k) {
-          const double apk = A[p * n + k], aqk = A[q * n + k];
+          const R apk = A[p * n + k], aqk = A[q * n + k];
           A[p * n + k] = c * apk - s * aqk;
           A[q * n + k] = s * apk + c * aqk;
         }
         for (int k = 0; k < n; ++k) {
-          const double vkp = V[k * n + p], vkq = V[k * n + q];
+          const R vkp = V[k * n + p], vkq = V[k * n + q];
           V[k * n + p] = c * vkp - s * vkq;
           V[k * n + q] = s * vkp + c * vkq;
         }
       }
   }
   return sweep;
+}
+
+// Symmetric eigendecomposition for the PSD projection, FP32 first: Jacobi in
+// FP32 (the cheap pipe) finds the eigenvectors to ~1e-7; they are
+// re-orthonormalised in FP64 (modified Gram-Schmidt), the matrix is rotated
+// into that basis in FP64 (A = V^T B V), and FP64 Jacobi sweeps finish it to an
+// off-diagonal norm of 1e-14 ||A||.  Projection onto the PSD cone is
+// non-expansive in the Frobenius norm, so the projected matrix is then exact to
+// 1e-14 of ||B||.  On return the eigenvalues are on the diagonal of B and the
+// eigenvectors are the columns of V.
+__device__ void eig_mixed(double* B, double* V, const int n) {
+  double mx = 0.0;
+  for (int i = 0; i < n * n; ++i) mx = fmax(mx, fabs(B[i]));
+  for (int i = 0; i < n * n; ++i) V[i] = 0.0;
+  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+  if (mx == 0.0) return;
+  float A32[81], V32[81];
+  const double inv = 1.0 / mx;
+  for (int i = 0; i < n * n; ++i) {
+    A32[i] = (float)(B[i] * inv);
+    V32[i] = 0.f;
+  }
+  for (int i = 0; i < n; ++i) V32[i * n + i] = 1.f;
+  jacobi_sweeps<float>(A32, V32, n, 1e-12f, 12);
+  for (int k = 0; k < n; ++k) {
+    for (int i = 0; i < n; ++i) V[i * n + k] = (double)V32[i * n + k];
+    for (int j = 0; j < k; ++j) {
+      double dp = 0.0;
+      for (int i = 0; i < n; ++i) dp += V[i * n + j] * V[i * n + k];
+      for (int i = 0; i < n; ++i) V[i * n + k] -= dp * V[i * n + j];
+    }
+    double nn = 0.0;
+    for (int i = 0; i < n; ++i) nn += V[i * n + k] * V[i * n + k];
+    nn = 1.0 / sqrt(nn);
+    for (int i = 0; i < n; ++i) V[i * n + k] *= nn;
+  }
+  double T[81];
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      double v = 0.0;
+      for (int j = 0; j < n; ++j) v += B[i * n + j] * V[j * n + k];
+      T[i * n + k] = v;
+    }
+  for (int k = 0; k < n; ++k)
+    for (int l = k; l < n; ++l) {
+      double v = 0.0;
+      for (int i = 0; i < n; ++i) v += V[i * n + k] * T[i * n + l];
+      B[k * n + l] = v;
+      B[l * n + k] = v;
+    }
+  jacobi_sweeps<double>(B, V, n, 1e-28, 12);
 }
 
 __device__ __forceinline__ int64_t find_block(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -446,11 +498,42 @@ struct HessArgs {
   double* __restrict__ grad;
   double* __restrict__ energy;
   unsigned long long* __restrict__ status;
+  // reduced matrices handed to the projection kernels: B packed upper
+  // triangle, element-major ([e * cap + slot]); slot -> active pair index
+  double* __restrict__ B9;
+  double* __restrict__ B6;
+  uint32_t* __restrict__ slot9;
+  uint32_t* __restrict__ slot6;
+  unsigned int* __restrict__ n9;
+  unsigned int* __restrict__ n6;
+  int64_t cap;
 };
 
-__global__ void __launch_bounds__(128) k_barrier_hess(HessArgs A) {
+__device__ __forceinline__ int tri_idx(int i, int j, int D) {  // packed upper triangle, i <= j
+  return i * D - (i * (i - 1)) / 2 + (j - i);
+}
+
+__device__ __forceinline__ void add_block(const HessArgs& A, int r, int c, const double* blk, bool transpose) {
+  const int64_t bi = find_block(A.row_ptr, A.col, r, c);
+  if (bi >= A.row_ptr[r + 1] || A.col[bi] != c) {
+    atomicOr(A.status, (unsigned long long)CB_DEV_CAPACITY);  // pattern miss: never expected
+    return;
+  }
+  double* dst = A.val + 9 * bi;
+  for (int al = 0; al < 3; ++al)
+    for (int be = 0; be < 3; ++be) atomicAdd(&dst[3 * al + be], transpose ? blk[3 * be + al] : blk[3 * al + be]);
+}
+
+// Stage (d), part 1, one thread per active pair: barrier value and
+// derivatives, energy, gradient scatter, and the Hessian in the orthonormal
+// translation-free basis of the points the distance type involves,
+// B = (M x I)^T H_z (M x I) with M = C K.  Point-point stencils are projected
+// in closed form here; the others are queued for the projection kernels.
+__global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double e_local = 0.0;
+  int want = 0;  // 9 or 6: reduced dimension of the queued matrix
+  double Bp[45];
   if (a < A.na) {
     const uint32_t c = A.aidx[a];
     const uint64_t key = A.cand[c];
@@ -492,15 +575,17 @@ __global__ void __launch_bounds__(128) k_barrier_hess(HessArgs A) {
     double gd[9];
     const double i2d = 0.5 / d;
     for (int k = 0; k < 9; ++k) gd[k] = gs[k] * i2d;
-    // gradient in x: g_x[i] = sum_m C[m][i] kappa b' grad_d[m]
-    double gx[12];
-    for (int i = 0; i < 4; ++i)
-      for (int al = 0; al < 3; ++al) {
-        double v = 0.0;
-        for (int m = 0; m < nz; ++m) v += (double)TI.C[m][i] * gd[3 * m + al];
-        gx[3 * i + al] = kap * b1 * v;
+    if (A.grad)
+      for (int i = 0; i < 4; ++i) {
+        bool used = false;
+        for (int m = 0; m < nz; ++m) used |= TI.C[m][i] != 0;
+        if (!used) continue;
+        for (int al = 0; al < 3; ++al) {
+          double v = 0.0;
+          for (int m = 0; m < nz; ++m) v += (double)TI.C[m][i] * gd[3 * m + al];
+          atomicAdd(&A.grad[(size_t)al * A.n + s.v[i]], kap * b1 * v);
+        }
       }
-    double Hx[144];
     if (kind == 0) {
       // point-point: H_z = kappa b'' n n^T + (kappa b'/d)(I - n n^T); clamp each part
       const double nh[3] = {gd[0], gd[1], gd[2]};
@@ -511,12 +596,13 @@ __global__ void __launch_bounds__(128) k_barrier_hess(HessArgs A) {
           Hz[3 * i + j] = lam_n * nh[i] * nh[j] + lam_t * ((i == j ? 1.0 : 0.0) - nh[i] * nh[j]);
       for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j) {
-          const double cc = (double)(TI.C[0][i] * TI.C[0][j]);
-          for (int al = 0; al < 3; ++al)
-            for (int be = 0; be < 3; ++be) Hx[(3 * i + al) * 12 + 3 * j + be] = cc * Hz[3 * al + be];
+          const int cc = TI.C[0][i] * TI.C[0][j];
+          if (cc == 0) continue;
+          double blk[9];
+          for (int q = 0; q < 9; ++q) blk[q] = (double)cc * Hz[q];
+          add_block(A, s.v[i], s.v[j], blk, false);
         }
     } else {
-      // points the type involves (columns of C with a nonzero entry)
       int pts[4], np = 0;
       for (int i = 0; i < 4; ++i) {
         bool used = false;
@@ -524,11 +610,10 @@ __global__ void __launch_bounds__(128) k_barrier_hess(HessArgs A) {
         if (used) pts[np++] = i;
       }
       const int nb = np - 1, D = 3 * nb;
-      // H_z = c1 grad_d grad_d^T + c2 hess_s, then B = M^T H_z M with M = C K
       const double c1 = kap * (b2 - b1 / d), c2 = kap * b1 * i2d;
-      double Hz[81];
+      // H_z in place of Hs
       for (int r = 0; r < 9; ++r)
-        for (int q = 0; q < 9; ++q) Hz[r * 9 + q] = c1 * gd[r] * gd[q] + c2 * Hs[r * 9 + q];
+        for (int q = 0; q < 9; ++q) Hs[r * 9 + q] = c1 * gd[r] * gd[q] + c2 * Hs[r * 9 + q];
       double M[3][3];
       for (int m = 0; m < 3; ++m)
         for (int bb = 0; bb < 3; ++bb) {
@@ -538,68 +623,229 @@ __global__ void __launch_bounds__(128) k_barrier_hess(HessArgs A) {
               v += (double)TI.C[m][pts[q]] * (np == 4 ? c_K4[q][bb] : c_K3[q][bb]);
           M[m][bb] = v;
         }
-      double B[81];
-      for (int ab = 0; ab < nb; ++ab)
+      // T = H_z (M x I)  (3nz x D), then B = (M x I)^T T  (packed upper triangle)
+      double Tm[81];
+      for (int r = 0; r < 3 * nz; ++r)
         for (int bb = 0; bb < nb; ++bb)
-          for (int al = 0; al < 3; ++al)
-            for (int be = 0; be < 3; ++be) {
-              double v = 0.0;
-              for (int m = 0; m < nz; ++m)
-                for (int m2 = 0; m2 < nz; ++m2) v += M[m][ab] * M[m2][bb] * Hz[(3 * m + al) * 9 + 3 * m2 + be];
-              B[(3 * ab + al) * D + 3 * bb + be] = v;
-            }
-      double V[81];
-      jacobi_sym(B, V, D);
-      // W = (K x I) V : 3np x D ; H+ = sum_k max(lambda_k,0) W_k W_k^T on the involved points
-      double W[108];
-      for (int q = 0; q < np; ++q)
-        for (int al = 0; al < 3; ++al)
-          for (int k = 0; k < D; ++k) {
+          for (int be = 0; be < 3; ++be) {
             double v = 0.0;
-            for (int ab = 0; ab < nb; ++ab) v += (np == 4 ? c_K4[q][ab] : c_K3[q][ab]) * V[(3 * ab + al) * D + k];
-            W[(3 * q + al) * 9 + k] = v;
+            for (int m2 = 0; m2 < nz; ++m2) v += Hs[r * 9 + 3 * m2 + be] * M[m2][bb];
+            Tm[r * 9 + 3 * bb + be] = v;
           }
-      for (int i = 0; i < 144; ++i) Hx[i] = 0.0;
-      for (int q1 = 0; q1 < np; ++q1)
-        for (int al = 0; al < 3; ++al)
-          for (int q2 = q1; q2 < np; ++q2)
-            for (int be = 0; be < 3; ++be) {
-              const int r = 3 * q1 + al, q = 3 * q2 + be;
-              if (q2 == q1 && be < al) continue;
-              double v = 0.0;
-              for (int k = 0; k < D; ++k) {
-                const double lk = B[k * D + k];
-                if (lk > 0.0) v += lk * W[r * 9 + k] * W[q * 9 + k];
-              }
-              const int gr = 3 * pts[q1] + al, gq = 3 * pts[q2] + be;
-              Hx[gr * 12 + gq] = v;
-              Hx[gq * 12 + gr] = v;
-            }
-    }
-    // scatter
-    if (A.grad)
-      for (int i = 0; i < 4; ++i)
-        for (int al = 0; al < 3; ++al) atomicAdd(&A.grad[(size_t)al * A.n + s.v[i]], gx[3 * i + al]);
-    int used_mask = 0;
-    for (int i = 0; i < 4; ++i)
-      for (int m = 0; m < nz; ++m) used_mask |= (TI.C[m][i] != 0) << i;
-    for (int i = 0; i < 4; ++i)
-      for (int j = 0; j < 4; ++j) {
-        if (!((used_mask >> i) & (used_mask >> j) & 1)) continue;  // structural zero block
-        const int64_t bi = find_block(A.row_ptr, A.col, s.v[i], s.v[j]);
-        if (bi >= A.row_ptr[s.v[i] + 1] || A.col[bi] != s.v[j]) {
-          atomicOr(A.status, (unsigned long long)CB_DEV_CAPACITY);  // pattern miss: never expected
-          continue;
+      for (int ab = 0; ab < nb; ++ab)
+        for (int al = 0; al < 3; ++al) {
+          const int row = 3 * ab + al;
+          for (int cl = row; cl < D; ++cl) {
+            double v = 0.0;
+            for (int m = 0; m < nz; ++m) v += M[m][ab] * Tm[(3 * m + al) * 9 + cl];
+            Bp[tri_idx(row, cl, D)] = v;
+          }
         }
-        double* dst = A.val + 9 * bi;
-        for (int al = 0; al < 3; ++al)
-          for (int be = 0; be < 3; ++be) atomicAdd(&dst[3 * al + be], Hx[(3 * i + al) * 12 + 3 * j + be]);
-      }
+      want = D;
+    }
   }
-  // energy: warp sum then one atomic per warp
+  // queue the reduced matrices (warp-aggregated slot allocation)
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int which = 0; which < 2; ++which) {
+    const int Dw = which == 0 ? 9 : 6;
+    const unsigned m = __ballot_sync(0xffffffffu, want == Dw);
+    if (!m) continue;
+    unsigned base = 0;
+    const int leader = __ffs(m) - 1;
+    if ((int)lane == leader) base = atomicAdd(which == 0 ? A.n9 : A.n6, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (want == Dw) {
+      const unsigned slot = base + __popc(m & lt);
+      double* Bo = which == 0 ? A.B9 : A.B6;
+      const int ne = Dw * (Dw + 1) / 2;
+      for (int e = 0; e < ne; ++e) Bo[(size_t)e * A.cap + slot] = Bp[e];
+      (which == 0 ? A.slot9 : A.slot6)[slot] = (uint32_t)a;
+    }
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) e_local += __shfl_xor_sync(0xffffffffu, e_local, o);
-  if ((threadIdx.x & 31) == 0 && e_local != 0.0) atomicAdd(A.energy, e_local);
+  if (lane == 0 && e_local != 0.0) atomicAdd(A.energy, e_local);
+}
+
+// Cyclic Jacobi with symmetric updates on a packed upper-triangular matrix
+// held in shared memory (element e of this thread at Am[e * S]); rotations are
+// accumulated into V (V[(i * D + k) * S]).  Rotations with |a_pq| below
+// 1e-16 of the norm are skipped; stops when off^2 <= tol2 * ||A||^2.
+template <typename R, int D>
+__device__ __forceinline__ void jacobi_packed(R* Am, R* V, const int S, const R tol2, const int max_sweeps) {
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    R off = 0, fro = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const R d = Am[tri_idx(i, i, D) * S];
+      fro += d * d;
+#pragma unroll
+      for (int j = i + 1; j < D; ++j) {
+        const R v = Am[tri_idx(i, j, D) * S];
+        off += R(2) * v * v;
+      }
+    }
+    fro += off;
+    if (fro == R(0) || off <= tol2 * fro) break;
+    const R skip = R(1e-16) * sqrt(fro);
+    for (int p = 0; p < D - 1; ++p)
+      for (int q = p + 1; q < D; ++q) {
+        const R apq = Am[tri_idx(p, q, D) * S];
+        if (fabs(apq) <= skip) continue;
+        const R app = Am[tri_idx(p, p, D) * S], aqq = Am[tri_idx(q, q, D) * S];
+        const R tau = (aqq - app) / (R(2) * apq);
+        const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
+        const R c = R(1) / sqrt(R(1) + t * t), s = t * c;
+        Am[tri_idx(p, p, D) * S] = app - t * apq;
+        Am[tri_idx(q, q, D) * S] = aqq + t * apq;
+        Am[tri_idx(p, q, D) * S] = R(0);
+        for (int k = 0; k < D; ++k) {
+          if (k == p || k == q) continue;
+          const int ikp = (k < p ? tri_idx(k, p, D) : tri_idx(p, k, D)) * S;
+          const int ikq = (k < q ? tri_idx(k, q, D) : tri_idx(q, k, D)) * S;
+          const R akp = Am[ikp], akq = Am[ikq];
+          Am[ikp] = c * akp - s * akq;
+          Am[ikq] = s * akp + c * akq;
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const R vkp = V[(k * D + p) * S], vkq = V[(k * D + q) * S];
+          V[(k * D + p) * S] = c * vkp - s * vkq;
+          V[(k * D + q) * S] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+template <int D>
+struct ProjSmem {
+  static constexpr int NP = D * (D + 1) / 2;
+  // per thread: B (NP doubles) | V (D*D doubles) | Z: A32 (NP floats) + V32 (D*D floats), later A (NP doubles)
+  static constexpr int Z_BYTES = ((NP + D * D) * 4 > NP * 8) ? (NP + D * D) * 4 : NP * 8;
+  static constexpr int PER_THREAD = NP * 8 + D * D * 8 + ((Z_BYTES + 7) / 8) * 8;
+};
+
+// Stage (d), part 2, one thread per queued pair: PSD projection of the D x D
+// reduced matrix and the BSR scatter.  Every per-pair matrix lives in shared
+// memory laid out element-major ([element][thread]), so a warp touches 32
+// consecutive doubles per access.  The eigen-decomposition is FP32 first
+// (Jacobi on the cheap pipe to ~1e-6), then FP64: modified Gram-Schmidt on the
+// eigenvectors, A = V^T B V, and symmetric Jacobi sweeps to an off-diagonal
+// norm of 1e-14 ||A|| (usually one sweep).  Projection onto the PSD cone is
+// non-expansive in the Frobenius norm, so the projected matrix is exact to
+// 1e-14 of ||B||.  B+ = V max(L, 0) V^T is mapped back to the involved points
+// with K (x) I and scattered.
+template <int D>
+__global__ void __launch_bounds__(128) k_hess_proj(HessArgs A, int64_t m) {
+  constexpr int NP = D * (D + 1) / 2;
+  constexpr int S = 128;
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x;
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + tid;
+  double* Bs = smem + tid;                          // [e * S]
+  double* Vs = smem + NP * S + tid;                 // [e * S]
+  char* zbase = (char*)(smem + (NP + D * D) * S);
+  float* A32 = (float*)zbase + tid;                 // [e * S] floats
+  float* V32 = (float*)zbase + NP * S + tid;        // [e * S] floats
+  double* Ad = (double*)zbase + tid;                // [e * S] doubles (aliases A32/V32 later)
+  if (w >= m) return;
+  const double* Bg = D == 9 ? A.B9 : A.B6;
+  const uint32_t a = (D == 9 ? A.slot9 : A.slot6)[w];
+  double mx = 0.0;
+  for (int e = 0; e < NP; ++e) {
+    const double v = Bg[(size_t)e * A.cap + w];
+    Bs[e * S] = v;
+    mx = fmax(mx, fabs(v));
+  }
+  // eigenvalues -> diagonal of Ad, eigenvectors -> Vs
+  if (mx == 0.0) {
+    for (int e = 0; e < NP; ++e) Ad[e * S] = 0.0;
+    for (int i = 0; i < D; ++i)
+      for (int k = 0; k < D; ++k) Vs[(i * D + k) * S] = (i == k) ? 1.0 : 0.0;
+  } else {
+    const double inv = 1.0 / mx;
+    for (int e = 0; e < NP; ++e) A32[e * S] = (float)(Bs[e * S] * inv);
+    for (int i = 0; i < D; ++i)
+      for (int k = 0; k < D; ++k) V32[(i * D + k) * S] = (i == k) ? 1.f : 0.f;
+    jacobi_packed<float, D>(A32, V32, S, 1e-12f, 12);
+    // FP64 re-orthonormalisation of the FP32 eigenvectors (modified Gram-Schmidt)
+    for (int k = 0; k < D; ++k) {
+      for (int i = 0; i < D; ++i) Vs[(i * D + k) * S] = (double)V32[(i * D + k) * S];
+      for (int j = 0; j < k; ++j) {
+        double dp = 0.0;
+        for (int i = 0; i < D; ++i) dp += Vs[(i * D + j) * S] * Vs[(i * D + k) * S];
+        for (int i = 0; i < D; ++i) Vs[(i * D + k) * S] -= dp * Vs[(i * D + j) * S];
+      }
+      double nn = 0.0;
+      for (int i = 0; i < D; ++i) nn += Vs[(i * D + k) * S] * Vs[(i * D + k) * S];
+      nn = rsqrt(nn);
+      for (int i = 0; i < D; ++i) Vs[(i * D + k) * S] *= nn;
+    }
+    // A = V^T B V, column by column (A32 / V32 are dead)
+    for (int l = 0; l < D; ++l) {
+      double t[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        double v = 0.0;
+        for (int j = 0; j < D; ++j)
+          v += Bs[(i <= j ? tri_idx(i, j, D) : tri_idx(j, i, D)) * S] * Vs[(j * D + l) * S];
+        t[i] = v;
+      }
+      for (int k = 0; k <= l; ++k) {
+        double v = 0.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) v += Vs[(i * D + k) * S] * t[i];
+        Ad[tri_idx(k, l, D) * S] = v;
+      }
+    }
+    jacobi_packed<double, D>(Ad, Vs, S, 1e-28, 12);
+  }
+  // B+ = V max(L,0) V^T (packed, over B which is dead)
+  for (int i = 0; i < D; ++i)
+    for (int j = i; j < D; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < D; ++k) {
+        const double lk = Ad[tri_idx(k, k, D) * S];
+        if (lk > 0.0) v += lk * Vs[(i * D + k) * S] * Vs[(j * D + k) * S];
+      }
+      Bs[tri_idx(i, j, D) * S] = v;
+    }
+  // scatter: block (q1, q2) of the involved points = sum_{ab, bb} K[q1][ab] K[q2][bb] B+[ab, bb]
+  const uint32_t c = A.aidx[a];
+  const Stencil st = stencil_of(A.cand[c], A.ev0, A.ev1, A.tv, A.T);
+  const TypeInfo& TI = st.ee ? c_ee_types[A.ctype[c]] : c_pt_types[A.ctype[c]];
+  const int nz = TI.kind + 1;
+  int pts[4], np = 0;
+  for (int i = 0; i < 4; ++i) {
+    bool used = false;
+    for (int mm = 0; mm < nz; ++mm) used |= TI.C[mm][i] != 0;
+    if (used) pts[np++] = i;
+  }
+  constexpr int NB = D / 3;
+  for (int q1 = 0; q1 < np; ++q1)
+    for (int q2 = q1; q2 < np; ++q2) {
+      double blk[9];
+#pragma unroll
+      for (int al = 0; al < 3; ++al)
+#pragma unroll
+        for (int be = 0; be < 3; ++be) {
+          double v = 0.0;
+#pragma unroll
+          for (int ab = 0; ab < NB; ++ab)
+#pragma unroll
+            for (int bb = 0; bb < NB; ++bb) {
+              const int r = 3 * ab + al, cl = 3 * bb + be;
+              const double kk = (D == 9 ? c_K4[q1][ab] * c_K4[q2][bb] : c_K3[q1][ab] * c_K3[q2][bb]);
+              v += kk * Bs[(r <= cl ? tri_idx(r, cl, D) : tri_idx(cl, r, D)) * S];
+            }
+          blk[3 * al + be] = v;
+        }
+      const int r = st.v[pts[q1]], cc = st.v[pts[q2]];
+      add_block(A, r, cc, blk, false);
+      if (q1 != q2) add_block(A, cc, r, blk, true);
+    }
 }
 
 __global__ void k_energy_final(const double* __restrict__ acc, const unsigned long long* __restrict__ status,
@@ -808,8 +1054,42 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     A.grad = grad;
     A.energy = eacc;
     A.status = status;
+    CB_TRY(buf_ensure(s->hB9, sizeof(double) * 45 * (size_t)na, st));
+    CB_TRY(buf_ensure(s->hB6, sizeof(double) * 21 * (size_t)na, st));
+    CB_TRY(buf_ensure(s->hslot, sizeof(uint32_t) * 2 * (size_t)na, st));
+    A.B9 = bp<double>(s->hB9);
+    A.B6 = bp<double>(s->hB6);
+    A.slot9 = bp<uint32_t>(s->hslot);
+    A.slot6 = bp<uint32_t>(s->hslot) + na;
+    A.n9 = (unsigned int*)(sc + SC_N9);
+    A.n6 = (unsigned int*)(sc + SC_N6);
+    A.cap = na;
+    k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_N9), 0ull);
+    k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_N6), 0ull);
     if (s->timing) cudaEventRecord(s->ev[10], st);
-    k_barrier_hess<<<cb_grid(na, 128), 128, 0, cb_count(st)>>>(A);
+    k_hess_prep<<<cb_grid(na, 128), 128, 0, cb_count(st)>>>(A);
+    CB_CUDA(cudaGetLastError());
+    uint64_t hq[2];
+    CB_TRY(read_scalars(s, SC_N9, 2, hq, st));
+    const int64_t m9 = (int64_t)(uint32_t)hq[0], m6 = (int64_t)(uint32_t)hq[1];
+    if (m9 > 0) {
+      const int smem = ProjSmem<9>::PER_THREAD * 128;
+      static bool attr9 = false;
+      if (!attr9) {
+        CB_CUDA(cudaFuncSetAttribute(k_hess_proj<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr9 = true;
+      }
+      k_hess_proj<9><<<cb_grid(m9, 128), 128, smem, cb_count(st)>>>(A, m9);
+    }
+    if (m6 > 0) {
+      const int smem = ProjSmem<6>::PER_THREAD * 128;
+      static bool attr6 = false;
+      if (!attr6) {
+        CB_CUDA(cudaFuncSetAttribute(k_hess_proj<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr6 = true;
+      }
+      k_hess_proj<6><<<cb_grid(m6, 128), 128, smem, cb_count(st)>>>(A, m6);
+    }
     if (s->timing) cudaEventRecord(s->ev[11], st);
     CB_CUDA(cudaGetLastError());
   }

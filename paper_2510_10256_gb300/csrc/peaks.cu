@@ -1,0 +1,53 @@
+// peaks.cu -- arithmetic-throughput probes used to report the FP64 roofline
+// denominator measured on the running GPU (the driver's peak file carries HBM
+// and bf16 figures only).  Independent dependency chains per thread, enough
+// warps to fill every SM, timed with CUDA events.
+#include "scene.cuh"
+
+namespace {
+
+template <typename R>
+__global__ void k_fma_chain(R* out, int iters, R a, R b) {
+  R x0 = (R)threadIdx.x, x1 = x0 + R(1), x2 = x0 + R(2), x3 = x0 + R(3);
+  R x4 = x0 + R(4), x5 = x0 + R(5), x6 = x0 + R(6), x7 = x0 + R(7);
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b);
+    x1 = fma(x1, a, b);
+    x2 = fma(x2, a, b);
+    x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b);
+    x5 = fma(x5, a, b);
+    x6 = fma(x6, a, b);
+    x7 = fma(x7, a, b);
+  }
+  R s = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+  if (s == R(-12345)) out[0] = s;  // keep the chains alive
+}
+
+template <typename R>
+cb_status run(int blocks, int iters, double* tflops) {
+  R* out = nullptr;
+  CB_CUDA(cudaMalloc(&out, sizeof(R)));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fma_chain<R><<<blocks, 256, 0, cb_count(nullptr)>>>(out, iters, (R)0.999999, (R)1e-7);  // warm-up
+  cudaEventRecord(e0);
+  k_fma_chain<R><<<blocks, 256, 0, cb_count(nullptr)>>>(out, iters, (R)0.999999, (R)1e-7);
+  cudaEventRecord(e1);
+  CB_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  *tflops = 2.0 * 8.0 * (double)iters * 256.0 * (double)blocks / (ms * 1e-3) / 1e12;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  return CB_OK;
+}
+
+}  // namespace
+
+extern "C" cb_status cb_measure_fma_tflops(int32_t fp64, int32_t blocks, int32_t iters, double* tflops) {
+  if (!tflops || blocks < 1 || iters < 1) return CB_ERR_ARG;
+  return fp64 ? run<double>(blocks, iters, tflops) : run<float>(blocks, iters, tflops);
+}

@@ -83,9 +83,13 @@ struct cb_scene {
   DevBuf bsr_val;       // double [nnzb][9]
   DevBuf row_cnt;       // uint32 [n+1]
   int64_t nnzb = 0;
+  DevBuf hB9, hB6;       // queued reduced Hessians (packed, element-major)
+  DevBuf hslot;          // uint32 [2][na] active index of each queued matrix
   DevBuf ccd_keys;      // uint64 [nccd]
   DevBuf ccd_t;         // double [nccd]
-  DevBuf ccd_cls;       // uint8 [nccd]
+  DevBuf ccd_cls;       // uint8 [nccd] class | 0x80 when t is exact
+  DevBuf ccd_lb;        // double [nccd] lower bound of t (2 when resolved)
+  DevBuf ccd_flag, ccd_pos, ccd_list;  // uint32 band selection
   int64_t n_ccd = 0;
   DevBuf scan_tmp;
   DevBuf hist;
@@ -112,6 +116,8 @@ enum {
   SC_ITERS = 6,
   SC_NFILT = 7,
   SC_NCORE = 8,
+  SC_N9 = 9,
+  SC_N6 = 10,
   SC_N = 16
 };
 

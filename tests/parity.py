@@ -104,6 +104,15 @@ def compare(sc, g: dict, orc: O.PassResult, mode="double", check_ccd=True) -> di
         assert np.array_equal(g["ccd"]["keys"], orc.ccd_keys), "CCD candidate sets differ"
         rep["ccd"] = int(orc.ccd_keys.size)
         assert g["alpha"] <= orc.alpha and orc.alpha - g["alpha"] <= 1e-9, (g["alpha"], orc.alpha)
+        kl = g["ccd"]["klass"]
+        assert np.array_equal(kl & 0x7F, orc.ccd_klass), "CCD classes differ"
+        exact = (kl & 0x80) != 0
+        t_g, t_o = g["ccd"]["t"], orc.ccd_t
+        assert np.all(np.abs(t_g[exact] - t_o[exact]) <= 1e-12 * np.maximum(t_o[exact], 1e-300)), \
+            "exact CCD times differ"
+        assert np.all(t_g[~exact] <= t_o[~exact]), "CCD lower bound above the oracle's t"
+        assert np.all(t_g[~exact] >= g["alpha"]), "a pruned pair could lower alpha"
+        rep["ccd_exact"] = int(exact.sum())
         rep["alpha"] = g["alpha"]
         rep["alpha_oracle"] = orc.alpha
     return rep
