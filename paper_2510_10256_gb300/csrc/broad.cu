@@ -362,6 +362,11 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   }
   double ext_sum;
   memcpy(&ext_sum, hb + 6, 8);
+  w.X = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    w.ctr[k] = 0.5 * ((double)lo[k] + (double)hi[k]);
+    w.X = std::max(w.X, 0.5 * ((double)hi[k] - (double)lo[k]) * (1.0 + 1e-6));
+  }
   // cell size: mean primitive box extent (scaled by the tuned factor), rounded to
   // a 1/4-octave grid so that tiny summation-order differences never change it
   double c = s->cell_hint > 0 ? (double)s->cell_hint * (ext_sum / std::max(1, np)) : ext_sum / std::max(1, np);

@@ -17,11 +17,13 @@
 // not move, are resolved exactly here).  Pass 2 runs the full iteration on the
 // unresolved pairs with lb_p in a band (lo, hi]; once the minimum m found so
 // far is <= hi, every pair left has t_p >= lb_p > hi >= m and
-// alpha = min(1, m) exactly; otherwise the next band is evaluated.
+// alpha = min(1, m) exactly; otherwise the band (hi, m] is evaluated, after
+// which the same holds.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 
+#include "bound32.cuh"
 #include "geometry.cuh"
 #include "prims.cuh"
 #include "scene.cuh"
@@ -54,6 +56,10 @@ struct CcdArgs {
   unsigned long long* __restrict__ lb_bits;     // min over lower bounds of unresolved pairs
   unsigned long long* __restrict__ status;
   unsigned long long* __restrict__ max_iters;
+  const float* __restrict__ xf;   // FP32 (x - centre)
+  const float* __restrict__ pf;   // FP32 p
+  float X;                        // max |x - centre|
+  double thrC;                    // U pairs with a distance bound above this are surely not class C
 };
 
 __device__ __forceinline__ d3 ld(const double* __restrict__ a, int n, int v) {
@@ -131,32 +137,144 @@ __device__ __forceinline__ AccdStart accd_start(const CcdArgs& A, int64_t q) {
   return S;
 }
 
-// pass 1: lower bound (or exact value) of every pair's t_p
-__global__ void __launch_bounds__(128) k_ccd_bound(CcdArgs A, double* __restrict__ lb_out) {
+__device__ __forceinline__ cbb::f3 ldf(const float* __restrict__ a, int n, int v) {
+  return cbb::f3{a[v], a[(size_t)n + v], a[2 * (size_t)n + v]};
+}
+
+// Minimum of non-negative doubles over the warp (compared as bit patterns),
+// one atomicMin per warp; 2.0 marks "no value".
+__device__ __forceinline__ void warp_min_atomic(double v, unsigned long long* __restrict__ dst) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, b, o);
+    b = u < b ? u : b;
+  }
+  if ((threadIdx.x & 31) == 0 && b < 0x4000000000000000ull) atomicMin(dst, b);
+}
+
+__device__ __forceinline__ void warp_append(bool flag, uint32_t value, uint32_t* __restrict__ list,
+                                            unsigned int* __restrict__ count) {
+  const unsigned m = __ballot_sync(0xffffffffu, flag);
+  if (!m) return;
+  const unsigned lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if ((int)lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (flag) list[base + __popc(m & ((1u << lane) - 1u))] = value;
+}
+
+// pass 1a: an FP32 lower bound of the distance and an FP32 upper bound of
+// l_p give a lower bound of the first step.  A pair whose class is certain and
+// whose bound exceeds 1 is resolved (t_p = 1); a smaller bound is kept as its
+// lower bound.  Pairs the FP32 bounds cannot settle are queued for pass 1b.
+__global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restrict__ lb_out,
+                                                    uint32_t* __restrict__ list, unsigned int* __restrict__ nlist) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= A.np) return;
-  const AccdStart S = accd_start(A, q);
-  double t;
-  bool exact = true;
-  if (S.lp == 0.0) {
-    t = 1.0;
-  } else if (S.g0 <= 0.0) {
-    t = 0.0;
-    atomicOr(A.status, (unsigned long long)CB_DEV_PENETRATION);
-  } else {
-    const double tl = xdiv(xmul(xsub(1.0, ACCD_S), S.g0), S.lp);
-    if (tl > 1.0) {
-      t = 1.0;  // the first step already passes t_c = 1: no contact within the step
+  bool need = false;
+  double m_exact = 2.0, m_lb = 2.0;  // this lane's contributions to the two minima
+  if (q < A.np) {
+    const uint64_t key = A.keys[q];
+    const uint32_t ty = cb_key_type(key), ki = cb_key_i(key), kj = cb_key_j(key);
+    int v[4];
+    bool ee;
+    if (ty == CB_KEY_PT) {
+      v[0] = (int)ki;
+      v[1] = A.tv[kj];
+      v[2] = A.tv[A.T + kj];
+      v[3] = A.tv[2 * A.T + kj];
+      ee = false;
     } else {
-      t = tl;
-      exact = false;
+      v[0] = A.ev0[ki];
+      v[1] = A.ev1[ki];
+      v[2] = A.ev0[kj];
+      v[3] = A.ev1[kj];
+      ee = true;
+    }
+    bool filt = false;
+    if (!A.filter_off) {
+      if (A.kind == CB_ROD) {
+        filt = A.comp[A.ev0[ki]] == A.comp[A.ev0[kj]] && (int)kj <= A.win[ki];
+      } else if (A.nf > 0) {
+        int64_t lo = 0, hi = A.nf;
+        while (lo < hi) {
+          int64_t mid = (lo + hi) >> 1;
+          if (A.frest[mid] < key) lo = mid + 1;
+          else hi = mid;
+        }
+        filt = lo < A.nf && A.frest[lo] == key;
+      }
+    }
+    need = true;
+    const float lb = cbb::lower_bound(ee, ldf(A.xf, A.n, v[0]), ldf(A.xf, A.n, v[1]), ldf(A.xf, A.n, v[2]),
+                                      ldf(A.xf, A.n, v[3]), A.X);
+    if (filt || (double)lb >= A.thrC) {
+      const int cls = filt ? 1 : 0;
+      const double off = (cls == 0 && !A.single) ? A.xi : 0.0;
+      const cbb::f3 p0 = ldf(A.pf, A.n, v[0]), p1 = ldf(A.pf, A.n, v[1]), p2 = ldf(A.pf, A.n, v[2]),
+                    p3 = ldf(A.pf, A.n, v[3]);
+      const cbb::f3 pm = cbb::fscale3(cbb::fadd3(cbb::fadd3(p0, p1), cbb::fadd3(p2, p3)), 0.25f);
+      const float n0 = sqrtf(cbb::fdot3(cbb::fsub3(p0, pm), cbb::fsub3(p0, pm)));
+      const float n1 = sqrtf(cbb::fdot3(cbb::fsub3(p1, pm), cbb::fsub3(p1, pm)));
+      const float n2 = sqrtf(cbb::fdot3(cbb::fsub3(p2, pm), cbb::fsub3(p2, pm)));
+      const float n3 = sqrtf(cbb::fdot3(cbb::fsub3(p3, pm), cbb::fsub3(p3, pm)));
+      const float lp32 = ee ? fmaxf(n0, n1) + fmaxf(n2, n3) : n0 + fmaxf(fmaxf(n1, n2), n3);
+      const float Pm = fmaxf(fmaxf(cbb::fmaxabs3(p0), cbb::fmaxabs3(p1)), fmaxf(cbb::fmaxabs3(p2), cbb::fmaxabs3(p3)));
+      const float u = 5.9604645e-8f;
+      const double lp_ub = (double)lp32 * (1.0 + 64.0 * u) + 64.0 * u * (double)Pm;
+      const double g_lb = (double)lb - off - 1e-12 * (1.0 + (double)A.X);
+      if (lp32 > 1e-30f && g_lb > 0.0) {
+        const double tl_lb = (1.0 - ACCD_S) * g_lb / lp_ub * (1.0 - 1e-9);
+        const bool exact = tl_lb > 1.0 + 1e-9;
+        const double t = exact ? 1.0 : tl_lb;
+        A.t_out[q] = t;
+        lb_out[q] = exact ? 2.0 : t;
+        A.cls_out[q] = (uint8_t)cls | (exact ? EXACT : 0);
+        if (exact) m_exact = t;
+        else m_lb = t;
+        need = false;
+      }
     }
   }
-  A.t_out[q] = t;
-  lb_out[q] = exact ? 2.0 : t;  // 2: resolved (never selected again)
-  A.cls_out[q] = (uint8_t)S.cls | (exact ? EXACT : 0);
-  if (exact) atomicMin(A.alpha_bits, (unsigned long long)__double_as_longlong(t));
-  else atomicMin(A.lb_bits, (unsigned long long)__double_as_longlong(t));
+  warp_min_atomic(m_exact, A.alpha_bits);
+  warp_min_atomic(m_lb, A.lb_bits);
+  warp_append(need, (uint32_t)q, list, nlist);
+}
+
+// pass 1b: exact FP64 first step of the queued pairs
+__global__ void __launch_bounds__(128) k_ccd_bound(CcdArgs A, double* __restrict__ lb_out,
+                                                   const uint32_t* __restrict__ list,
+                                                   const unsigned int* __restrict__ nlist) {
+  const unsigned m = *nlist;
+  double m_exact = 2.0, m_lb = 2.0;
+  for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < m; w += gridDim.x * blockDim.x) {
+    const int64_t q = list[w];
+    const AccdStart S = accd_start(A, q);
+    double t;
+    bool exact = true;
+    if (S.lp == 0.0) {
+      t = 1.0;
+    } else if (S.g0 <= 0.0) {
+      t = 0.0;
+      atomicOr(A.status, (unsigned long long)CB_DEV_PENETRATION);
+    } else {
+      const double tl = xdiv(xmul(xsub(1.0, ACCD_S), S.g0), S.lp);
+      if (tl > 1.0) {
+        t = 1.0;  // the first step already passes t_c = 1: no contact within the step
+      } else {
+        t = tl;
+        exact = false;
+      }
+    }
+    A.t_out[q] = t;
+    lb_out[q] = exact ? 2.0 : t;  // 2: resolved (never selected again)
+    A.cls_out[q] = (uint8_t)S.cls | (exact ? EXACT : 0);
+    if (exact) m_exact = fmin(m_exact, t);
+    else m_lb = fmin(m_lb, t);
+  }
+  warp_min_atomic(m_exact, A.alpha_bits);
+  warp_min_atomic(m_lb, A.lb_bits);
 }
 
 // select unresolved pairs with lo < lb <= hi
@@ -178,6 +296,14 @@ __global__ void __launch_bounds__(128) k_ccd_exact(CcdArgs A, int64_t m, const u
   if (w >= m) return;
   const int64_t q = list[w];
   AccdStart S = accd_start(A, q);
+  if (S.lp == 0.0 || S.g0 <= 0.0) {  // only reachable through an FP32 bound below 1
+    const double t0 = S.lp == 0.0 ? 1.0 : 0.0;
+    if (S.lp != 0.0) atomicOr(A.status, (unsigned long long)CB_DEV_PENETRATION);
+    A.t_out[q] = t0;
+    A.cls_out[q] = (uint8_t)S.cls | EXACT;
+    atomicMin(A.alpha_bits, (unsigned long long)__double_as_longlong(t0));
+    return;
+  }
   const double g = xmul(ACCD_S, S.g0);
   double t = 0.0, d;
   double tl = xdiv(xmul(xsub(1.0, ACCD_S), S.g0), S.lp);
@@ -256,7 +382,18 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     A.lb_bits = lbm;
     A.status = (unsigned long long*)(sc + SC_STATUS);
     A.max_iters = mi;
-    k_ccd_bound<<<cb_grid(np, 128), 128, 0, cb_count(st)>>>(A, bp<double>(s->ccd_lb));
+    CB_TRY(to_f32(s, x, s->bwc.ctr, s->xf, st));
+    CB_TRY(to_f32(s, p, nullptr, s->pf, st));
+    A.xf = bp<float>(s->xf);
+    A.pf = bp<float>(s->pf);
+    A.X = (float)s->bwc.X;
+    A.thrC = s->xi * (1.0 + 1e-9) + 1e-9;
+    CB_TRY(buf_ensure(s->dlist, sizeof(uint32_t) * (size_t)np, st));
+    unsigned int* nl = (unsigned int*)(sc + SC_NLIST);
+    k_set<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_NLIST), 0ull);
+    k_ccd_screen<<<cb_grid(np, 128), 128, 0, cb_count(st)>>>(A, bp<double>(s->ccd_lb), bp<uint32_t>(s->dlist), nl);
+    k_ccd_bound<<<std::min<int64_t>(cb_grid(np, 128), 152 * 16), 128, 0, cb_count(st)>>>(
+        A, bp<double>(s->ccd_lb), bp<uint32_t>(s->dlist), nl);
     CB_CUDA(cudaGetLastError());
     uint64_t h[2];
     CB_TRY(read_scalars(s, SC_COUNT0, 1, &h[0], st));
@@ -284,10 +421,10 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
       CB_TRY(read_scalars(s, SC_ALPHA_BITS, 1, &h[1], st));
       memcpy(&m, &h[1], 8);
       if (m <= hi || hi >= 1.0) break;  // every pair left has t_p >= lb_p > hi >= m
+      // only pairs with lb_p <= m can still lower the minimum: one more band
+      // (hi, m] makes it exact
       lo = hi;
-      double nh = 4.0 * hi;
-      if (!(nh > hi)) nh = 1.0;  // hi == 0 (underflowed first steps): take the rest at once
-      hi = std::min(1.0, nh);
+      hi = std::min(1.0, m);
     }
   }
   if (alpha) k_alpha_final<<<1, 1, 0, cb_count(st)>>>(ab, alpha);

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "bound32.cuh"
 #include "geometry.cuh"
 #include "prims.cuh"
 #include "scene.cuh"
@@ -94,20 +95,29 @@ __global__ void k_rest_filter(int64_t nc, const uint64_t* __restrict__ keys, con
                               uint32_t* __restrict__ flag, double* __restrict__ dbar,
                               unsigned long long* __restrict__ dmin_bits) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
-  Stencil s = stencil_of(keys[c], ev0, ev1, tv, T);
-  uint32_t f = 0;
-  double d = 0.0;
-  if (comp[s.v[0]] == comp[s.v[2]]) {
-    cbg::stencil_distance(s.ee, load3(rest, n, s.v[0]), load3(rest, n, s.v[1]), load3(rest, n, s.v[2]),
-                          load3(rest, n, s.v[3]), d);
-    if (d < a) {
-      f = 1;
-      atomicMin(dmin_bits, (unsigned long long)__double_as_longlong(d));
+  unsigned long long mb = 0x7ff0000000000000ull;  // +inf: no filtered pair in this lane
+  if (c < nc) {
+    Stencil s = stencil_of(keys[c], ev0, ev1, tv, T);
+    uint32_t f = 0;
+    double d = 0.0;
+    if (comp[s.v[0]] == comp[s.v[2]]) {
+      cbg::stencil_distance(s.ee, load3(rest, n, s.v[0]), load3(rest, n, s.v[1]), load3(rest, n, s.v[2]),
+                            load3(rest, n, s.v[3]), d);
+      if (d < a) {
+        f = 1;
+        mb = (unsigned long long)__double_as_longlong(d);
+      }
     }
+    flag[c] = f;
+    dbar[c] = d;
   }
-  flag[c] = f;
-  dbar[c] = d;
+  // one atomicMin per warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = u < mb ? u : mb;
+  }
+  if ((threadIdx.x & 31) == 0 && mb != 0x7ff0000000000000ull) atomicMin(dmin_bits, mb);
 }
 
 __global__ void k_filter_rod(int64_t nc, const uint64_t* __restrict__ cand, const int32_t* __restrict__ ev0,
@@ -168,34 +178,94 @@ __device__ __forceinline__ void pair_params(const PassParams& P, int k, double& 
   }
 }
 
-__global__ void k_distance(int64_t nc, const uint64_t* __restrict__ cand, const uint8_t* __restrict__ klass_in,
-                           const int32_t* __restrict__ ev0, const int32_t* __restrict__ ev1,
-                           const int32_t* __restrict__ tv, int T, const double* __restrict__ x, int n, PassParams P,
-                           double* __restrict__ dout, int8_t* __restrict__ tout, uint8_t* __restrict__ cls,
-                           uint32_t* __restrict__ flag, unsigned long long* __restrict__ status,
-                           unsigned long long* __restrict__ ncore) {
+// Warp-aggregated append of flagged lanes' values to a list.
+__device__ __forceinline__ void warp_append(bool flag, uint32_t value, uint32_t* __restrict__ list,
+                                            unsigned int* __restrict__ count) {
+  const unsigned m = __ballot_sync(0xffffffffu, flag);
+  if (!m) return;
+  const unsigned lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if ((int)lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (flag) list[base + __popc(m & ((1u << lane) - 1u))] = value;
+}
+
+// Per candidate, phase 1: an FP32 lower bound of the distance.  Candidates it
+// places beyond every threshold of their class (U: a, which is above xi; F:
+// dbar_min) are inactive and not class C.  The rest are queued for the exact
+// FP64 phase, so that no warp pays for FP64 on behalf of a few lanes.
+__global__ void k_distance_screen(int64_t nc, const uint64_t* __restrict__ cand,
+                                  const uint8_t* __restrict__ klass_in, const int32_t* __restrict__ ev0,
+                                  const int32_t* __restrict__ ev1, const int32_t* __restrict__ tv, int T,
+                                  const float* __restrict__ xf, float X, double thrU, double thrF, int n,
+                                  double* __restrict__ dout, int8_t* __restrict__ tout, uint8_t* __restrict__ cls,
+                                  uint32_t* __restrict__ flag, uint32_t* __restrict__ list,
+                                  unsigned int* __restrict__ nlist) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t is_core = 0;
+  bool exact = false;
   if (c < nc) {
     Stencil s = stencil_of(cand[c], ev0, ev1, tv, T);
-    double d;
-    const int ty = cbg::stencil_distance(s.ee, load3(x, n, s.v[0]), load3(x, n, s.v[1]), load3(x, n, s.v[2]),
-                                         load3(x, n, s.v[3]), d);
-    int k = klass_in[c];
-    if (k == 0 && P.core_temp && !P.single && d <= P.xi) k = 2;
-    double xi_p, dh_p;
-    pair_params(P, k, xi_p, dh_p);
-    const double y = xsub(d, xi_p);
-    const uint32_t act = (y < dh_p) ? 1u : 0u;
-    if (act && y <= 0.0) atomicOr(status, (unsigned long long)CB_DEV_PENETRATION);
-    dout[c] = d;
-    tout[c] = (int8_t)ty;
-    cls[c] = (uint8_t)k;
-    flag[c] = act;
-    is_core = (k == 2);
+    const int k = klass_in[c];
+    const float lb = cbb::lower_bound(
+        s.ee, cbb::f3{xf[s.v[0]], xf[(size_t)n + s.v[0]], xf[2 * (size_t)n + s.v[0]]},
+        cbb::f3{xf[s.v[1]], xf[(size_t)n + s.v[1]], xf[2 * (size_t)n + s.v[1]]},
+        cbb::f3{xf[s.v[2]], xf[(size_t)n + s.v[2]], xf[2 * (size_t)n + s.v[2]]},
+        cbb::f3{xf[s.v[3]], xf[(size_t)n + s.v[3]], xf[2 * (size_t)n + s.v[3]]}, X);
+    if ((double)lb >= (k == 1 ? thrF : thrU)) {
+      dout[c] = __longlong_as_double(0x7ff0000000000000LL);
+      tout[c] = -1;
+      cls[c] = (uint8_t)k;
+      flag[c] = 0;
+    } else {
+      exact = true;
+    }
   }
-  uint32_t b = __ballot_sync(0xffffffffu, is_core);
-  if ((threadIdx.x & 31) == 0 && b) atomicAdd(ncore, (unsigned long long)__popc(b));
+  warp_append(exact, (uint32_t)c, list, nlist);
+}
+
+// phase 2: exact FP64 distance, class C and activity of the queued candidates
+__global__ void k_distance_exact(const uint32_t* __restrict__ list, const unsigned int* __restrict__ nlist,
+                                 const uint64_t* __restrict__ cand, const uint8_t* __restrict__ klass_in,
+                                 const int32_t* __restrict__ ev0, const int32_t* __restrict__ ev1,
+                                 const int32_t* __restrict__ tv, int T, const double* __restrict__ x, int n,
+                                 PassParams P, double* __restrict__ dout, int8_t* __restrict__ tout,
+                                 uint8_t* __restrict__ cls, uint32_t* __restrict__ flag,
+                                 unsigned long long* __restrict__ status, unsigned long long* __restrict__ ncore) {
+  const unsigned m = *nlist;
+  for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w - threadIdx.x < m; w += gridDim.x * blockDim.x) {
+    uint32_t is_core = 0;
+    if (w < m) {
+      const uint32_t c = list[w];
+      Stencil s = stencil_of(cand[c], ev0, ev1, tv, T);
+      int k = klass_in[c];
+      double d;
+      const int ty = cbg::stencil_distance(s.ee, load3(x, n, s.v[0]), load3(x, n, s.v[1]), load3(x, n, s.v[2]),
+                                           load3(x, n, s.v[3]), d);
+      if (k == 0 && P.core_temp && !P.single && d <= P.xi) k = 2;
+      double xi_p, dh_p;
+      pair_params(P, k, xi_p, dh_p);
+      const double y = xsub(d, xi_p);
+      const uint32_t act = (y < dh_p) ? 1u : 0u;
+      if (act && y <= 0.0) atomicOr(status, (unsigned long long)CB_DEV_PENETRATION);
+      dout[c] = d;
+      tout[c] = (int8_t)ty;
+      cls[c] = (uint8_t)k;
+      flag[c] = act;
+      is_core = (k == 2);
+    }
+    const uint32_t b = __ballot_sync(0xffffffffu, is_core);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(ncore, (unsigned long long)__popc(b));
+  }
+}
+
+__global__ void k_to_f32(int n, const double* __restrict__ v, double c0, double c1, double c2,
+                         float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * (int64_t)n) return;
+  const int k = (int)(i / n);
+  const double c = k == 0 ? c0 : (k == 1 ? c1 : c2);
+  out[i] = (float)(v[i] - c);
 }
 
 __global__ void k_active_compact(int64_t nc, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
@@ -944,6 +1014,14 @@ cb_status filter_apply(cb_scene* s, cudaStream_t st) {
   return CB_OK;
 }
 
+cb_status to_f32(cb_scene* s, const double* v, const double* c3, DevBuf& out, cudaStream_t st) {
+  CB_TRY(buf_ensure(out, sizeof(float) * 3 * (size_t)s->n, st));
+  k_to_f32<<<cb_grid(3 * (int64_t)s->n), CB_THREADS, 0, cb_count(st)>>>(
+      s->n, v, c3 ? c3[0] : 0.0, c3 ? c3[1] : 0.0, c3 ? c3[2] : 0.0, bp<float>(out));
+  CB_CUDA(cudaGetLastError());
+  return CB_OK;
+}
+
 static int bits_for(int64_t v) {
   int b = 1;
   while ((1ll << b) <= v) ++b;
@@ -983,10 +1061,22 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     CB_TRY(buf_ensure(s->cflag, sizeof(uint32_t) * (size_t)nc, st));
     CB_TRY(buf_ensure(s->cpos, sizeof(uint32_t) * ((size_t)nc + 1), st));
     CB_TRY(buf_ensure(s->scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(nc) + 8), st));
-    k_distance<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(nc, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass),
-                                                   bp<int32_t>(s->ev0), bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T,
-                                                   x, s->n, P, bp<double>(s->cd), bp<int8_t>(s->ctype),
-                                                   bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), status, ncore);
+    CB_TRY(to_f32(s, x, s->bw.ctr, s->xf, st));
+    // thresholds beyond which a pair is surely inactive and not class C (the
+    // 1e-9 margins cover the rounding of the FP64 decision)
+    const double thrU = s->a * (1.0 + 1e-9) + 1e-9;
+    const double thrF = P.dbar_min * (1.0 + 1e-9) + 1e-9;
+    CB_TRY(buf_ensure(s->dlist, sizeof(uint32_t) * (size_t)nc, st));
+    unsigned int* nl = (unsigned int*)(sc + SC_NLIST);
+    k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_NLIST), 0ull);
+    k_distance_screen<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(
+        nc, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass), bp<int32_t>(s->ev0), bp<int32_t>(s->ev1),
+        bp<int32_t>(s->tv), s->T, bp<float>(s->xf), (float)s->bw.X, thrU, thrF, s->n, bp<double>(s->cd),
+        bp<int8_t>(s->ctype), bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), bp<uint32_t>(s->dlist), nl);
+    k_distance_exact<<<std::min<int64_t>(cb_grid(nc), 152 * 16), CB_THREADS, 0, cb_count(st)>>>(
+        bp<uint32_t>(s->dlist), nl, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass), bp<int32_t>(s->ev0),
+        bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T, x, s->n, P, bp<double>(s->cd), bp<int8_t>(s->ctype),
+        bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), status, ncore);
     uint32_t* tot = (uint32_t*)(sc + SC_COUNT1);
     cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(s->cflag), bp<uint32_t>(s->cpos), nc,
                                             bp<uint32_t>(s->scan_tmp), tot, st);

@@ -35,6 +35,8 @@ struct BroadWork {
   DevBuf scan_tmp;
   DevBuf hist;
   float cell = 0.f;   // cell size used last
+  double ctr[3] = {0, 0, 0};  // centre of the last boxes' bounds
+  double X = 0;                // max |coordinate - ctr| over the boxes
 };
 
 struct cb_scene {
@@ -85,6 +87,8 @@ struct cb_scene {
   int64_t nnzb = 0;
   DevBuf hB9, hB6;       // queued reduced Hessians (packed, element-major)
   DevBuf hslot;          // uint32 [2][na] active index of each queued matrix
+  DevBuf xf, pf;         // float [3][n]: centred FP32 copies of x and of p
+  DevBuf dlist;          // uint32: candidates / CCD pairs queued for the FP64 phase
   DevBuf ccd_keys;      // uint64 [nccd]
   DevBuf ccd_t;         // double [nccd]
   DevBuf ccd_cls;       // uint8 [nccd] class | 0x80 when t is exact
@@ -118,6 +122,7 @@ enum {
   SC_NCORE = 8,
   SC_N9 = 9,
   SC_N6 = 10,
+  SC_NLIST = 11,
   SC_N = 16
 };
 
@@ -140,3 +145,6 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
 
 // ccd.cu
 cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, cudaStream_t st);
+
+// narrow.cu: FP32 copy of (v - c) (c may be null: no centring)
+cb_status to_f32(cb_scene* s, const double* v, const double* c3, DevBuf& out, cudaStream_t st);

@@ -99,3 +99,18 @@ def test_empty_and_degenerate_inputs():
     # bad topology
     with pytest.raises(ContactError):
         ContactScene("shell", np.zeros((3, 3)), 0.1, 0.01, tris=np.array([[0], [1], [5]], np.int32))
+
+
+@pytest.mark.parametrize("shift", [(1000.0, -500.0, 300.0), (-3.0e4, 2.0e4, 1.0e4)])
+def test_far_from_origin(shift):
+    """Coordinates far from the origin stress the FP32 screens (their rounding
+    grows with |x|); decisions must still match the FP64 oracle."""
+    sc = S.pleated_sheet(nx=24)
+    off = np.array(shift)[:, None]
+    sc.rest = sc.rest + off
+    sc.x = sc.x + off
+    _pair(sc)
+    sc2 = S.woven_patch(n_warp=2, n_weft=2, nseg=40)
+    sc2.rest = sc2.rest + off
+    sc2.x = sc2.x + off
+    _pair(sc2)
