@@ -80,7 +80,7 @@ def lib():
         L.orc_narrow.argtypes = [C.POINTER(_Topo), vp, C.POINTER(_Params), i64, vp, vp, vp, vp, vp,
                                  vp, C.POINTER(i32)]
         L.orc_barrier_pairs.argtypes = [C.POINTER(_Topo), vp, C.POINTER(_Params), i64, vp, vp, vp,
-                                        vp, vp, vp, vp]
+                                        vp, vp, vp, vp, vp]
         L.orc_ccd_pairs.argtypes = [C.POINTER(_Topo), vp, vp, i64, vp, vp, dbl, dbl, dbl, dbl, i32,
                                     vp, vp, vp]
         L.orc_free.argtypes = [vp]
@@ -362,11 +362,12 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     e = np.zeros(na)
     g = np.zeros((na, 12))
     H = np.zeros((na, 144))
+    hmax = np.zeros(na)
     akl = np.ascontiguousarray(kl[active])
     ad = np.ascontiguousarray(d[active])
     adt = np.ascontiguousarray(dty[active])
     lib().orc_barrier_pairs(C.byref(tc), _ptr(x), C.byref(P), na, _ptr(ak), _ptr(akl), _ptr(ad),
-                            _ptr(adt), _ptr(e), _ptr(g), _ptr(H))
+                            _ptr(adt), _ptr(e), _ptr(g), _ptr(H), _ptr(hmax))
     energy = math.fsum(e.tolist()) if na else 0.0
     n = scene.n
     st = stencils(topo, ak)                                      # (na, 4)
@@ -376,12 +377,23 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     np.add.at(grad.reshape(-1), gi, g.reshape(-1))
     # tolerance scale: |contribution|, floored at 1e-4 of the pair's largest
     # entry (rounding of a pair's derivatives is relative to its norm)
-    gfloor = 1e-4 * np.abs(g).max(axis=1, keepdims=True) if na else np.zeros((0, 1))
+    # conditioning of b', b'' in d near the activation (relative errors grow like
+    # kappa = y / (dhat_p - y)); the floor grows with it
+    ad_xi = np.where(akl == KLASS_U, 0.0 if mode == "single" else xi, 0.0)
+    ad_dh = np.where(akl == KLASS_F, dbar_min if np.isfinite(dbar_min) else 0.0,
+                     np.where((akl == KLASS_C) | (mode == "single"), a, dhat))
+    ay = ad - ad_xi
+    kappa_p = np.maximum(1.0, ay / np.maximum(ad_dh - ay, 1e-300)) if na else np.zeros(0)
+    ffac = np.maximum(1e-4, 1e-7 * kappa_p)
+    gfloor = (ffac * np.abs(g).max(axis=1))[:, None] if na else np.zeros((0, 1))
     np.add.at(grad_abs.reshape(-1), gi, np.maximum(np.abs(g), gfloor).reshape(-1))
     rows = np.repeat(st, 4, axis=1).reshape(-1)                  # r of (i, j)
     cols = np.tile(st, (1, 4)).reshape(-1)                       # c of (i, j)
     blk = H.reshape(na, 4, 3, 4, 3).transpose(0, 1, 3, 2, 4).reshape(-1, 3, 3)
-    hfloor = 1e-4 * np.abs(H).max(axis=1) if na else np.zeros(0)
+    # floor: 1e-4 of the pair's largest Hessian entry BEFORE projection -- the
+    # projection is 1-Lipschitz, so rounding in forming H carries into H+ at
+    # the scale of H, however much of H the projection removes
+    hfloor = ffac * np.maximum(hmax, np.abs(H).max(axis=1)) if na else np.zeros(0)
     blk_scale = np.maximum(np.abs(blk), np.repeat(hfloor, 16)[:, None, None])
     bkey = rows * n + cols
     ukeys, inv = np.unique(bkey, return_inverse=True)

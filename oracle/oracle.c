@@ -661,7 +661,7 @@ int64_t orc_narrow(const orc_topo* tp, const double* x, const orc_params* P, int
  * candidate arrays).  grad: [na][12]; hess: [na][144]. */
 void orc_barrier_pairs(const orc_topo* tp, const double* x, const orc_params* P, int64_t na,
                        const uint64_t* keys, const uint8_t* klass, const double* d,
-                       const int8_t* type, double* energy, double* grad, double* hess) {
+                       const int8_t* type, double* energy, double* grad, double* hess, double* hmax) {
     #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t a = 0; a < na; ++a) {
         int v[4], ee;
@@ -675,6 +675,7 @@ void orc_barrier_pairs(const orc_topo* tp, const double* x, const orc_params* P,
             energy[a] = INFINITY;
             for (int i = 0; i < 12; ++i) grad[12 * a + i] = NAN;
             for (int i = 0; i < 144; ++i) hess[144 * a + i] = NAN;
+            if (hmax) hmax[a] = NAN;
             continue;
         }
         orc_barrier(y, dh_p, &b, &b1, &b2);
@@ -684,6 +685,9 @@ void orc_barrier_pairs(const orc_topo* tp, const double* x, const orc_params* P,
         for (int i = 0; i < 12; ++i)
             for (int j = 0; j < 12; ++j)
                 H[12 * i + j] = P->kappa * (b2 * gd[i] * gd[j] + b1 * Hd[12 * i + j]);
+        double mx = 0.0;
+        for (int i = 0; i < 144; ++i) mx = fmax(mx, fabs(H[i]));
+        if (hmax) hmax[a] = mx;   /* largest entry before projection */
         if (P->project) orc_psd_project(12, H, hess + 144 * a, NULL);
         else memcpy(hess + 144 * a, H, sizeof(H));
     }

@@ -94,8 +94,14 @@ def compare(sc, g: dict, orc: O.PassResult, mode="double", check_ccd=True) -> di
         if not (act_o ^ act_g):
             assert np.array_equal(rp, orc.bsr_row_ptr) and np.array_equal(col, orc.bsr_col), "BSR pattern differs"
             verr = np.abs(val - orc.bsr_val)
-            assert np.all(verr <= 1e-9 * orc.bsr_abs + 1e-30), \
-                f"BSR value err {float((verr / (orc.bsr_abs + 1e-300)).max())}"
+            ratio = verr / (orc.bsr_abs + 1e-300)
+            if not np.all(verr <= 1e-9 * orc.bsr_abs + 1e-30):
+                q = int(np.argmax(ratio.reshape(ratio.shape[0], -1).max(axis=1)))
+                row = int(np.searchsorted(rp, q, side="right") - 1)
+                raise AssertionError(
+                    f"BSR value err {float(ratio.max())} at block {q} (row {row}, col {int(col[q])}): "
+                    f"gpu {val[q].ravel().tolist()} oracle {orc.bsr_val[q].ravel().tolist()} "
+                    f"scale {orc.bsr_abs[q].ravel().tolist()}")
             rep["bsr_relerr"] = float((verr / (orc.bsr_abs + 1e-300)).max()) if verr.size else 0.0
         rep["nnzb"] = int(col.size)
     else:

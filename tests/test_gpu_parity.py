@@ -114,3 +114,20 @@ def test_far_from_origin(shift):
     sc2.rest = sc2.rest + off
     sc2.x = sc2.x + off
     _pair(sc2)
+
+
+@pytest.mark.slow
+def test_pleated_sheet_full_size():
+    """The bench workload itself (256 x 256 grid, 130,050 triangles) against the
+    full brute-force oracle: every candidate, class, active pair, distance,
+    gradient entry, BSR block and the step bound."""
+    rep, g, o = _pair(S.pleated_sheet())
+    assert rep["C"] > 10_000_000 and rep["active"] > 500_000
+
+
+@pytest.mark.slow
+def test_graded_disk_full_size():
+    """Graded twisted disk (~200k triangles, 0.1-4 mm edges) against the full
+    oracle."""
+    rep, g, o = _pair(S.graded_disk())
+    assert rep["F"] > 0
