@@ -137,7 +137,7 @@ cb_status contact_filter(cb_scene* scene, void* stream);
  * U (xi, dhat), F (0, dbar_min), C (0, a) (single mode: U (0, a)); active iff
  * y = d - xi_p < dhat_p.  For active pairs: b(y, dhat_p), its gradient and
  * the PSD projection of kappa (b'' grad d grad d^T + b' hess d).
- * energy_dev: DEVICE 1 double (overwritten).  grad_dev: DEVICE [3][n]
+ * energy_dev: DEVICE 1 double per member (overwritten).  grad_dev: DEVICE [3][n]
  * (overwritten).  Either may be NULL.  The BSR matrix (full symmetric, sorted
  * columns, 3x3 row-major blocks) is scene-owned: cb_get_bsr / cb_bsr_device.
  * A pair at or inside its offset sets CB_ERR_PENETRATION and energy = +inf. */
@@ -147,10 +147,28 @@ cb_status barrier_eval(cb_scene* scene, const double* x_dev, double* energy_dev,
 /* (e) CCD step bound, Sec. 3.3: candidates are pairs whose swept boxes (x and
  * x + p) inflated by offset/2 overlap; each is bounded by additive CCD
  * (s = 0.1, inner factor 0.9) against its class offset (U: offset; F, C: 0).
- * alpha_dev: DEVICE 1 double = min(1, min_p t_p) (overwritten).
+ * alpha_dev: DEVICE 1 double per member = min(1, min_p t_p) (overwritten).
  * p_dev: DEVICE [3][n] search direction. */
 cb_status ccd_step(cb_scene* scene, const double* x_dev, const double* p_dev, double* alpha_dev,
                    void* stream);
+
+/* Batch: several scenes of one kind in one pass (one launch per stage for all
+ * of them).  The batch concatenates the members' vertices, edges and
+ * triangles in member order (offsets: cb_batch_offsets) and keeps each
+ * member's parameters, filter tables, hash grid and results separate; pairs of
+ * different members are never formed.  It copies what it needs at creation:
+ * members may be destroyed afterwards.  Use it with the four pass calls: x, p
+ * and grad are [3][N] over the concatenated vertices (N = total), and
+ * energy_dev / alpha_dev receive one double per member, in member order.
+ * Pair keys and the BSR matrix use the concatenated numbering.  sync.
+ * Errors: CB_ERR_ARG (null members, count < 1, mixed kinds, a member that is
+ * itself a batch, index overflow), CB_ERR_OOM, CB_ERR_CUDA. */
+cb_status cb_batch_create(cb_scene* const* members, int32_t count, void* stream, cb_scene** out);
+/* HOST arrays of count+1 entries: first vertex / edge / triangle of each
+ * member in the batch numbering (a plain scene reports one member). */
+cb_status cb_batch_offsets(cb_scene* scene, int64_t* vert_offsets, int64_t* edge_offsets, int64_t* tri_offsets);
+/* members of a scene (1 for a plain scene) */
+int32_t cb_member_count(cb_scene* scene);
 
 /* sync getters.  Each copies to HOST buffers of capacity `cap` elements and
  * writes the full count to *count (CB_ERR_CAPACITY if cap is too small). */

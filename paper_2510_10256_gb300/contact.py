@@ -29,7 +29,8 @@ MODES = {"double": CB_FILTER_DOUBLE, "single": CB_FILTER_SINGLE, "off": CB_FILTE
 ABI_FUNCTIONS = ["cb_scene_create", "cb_scene_destroy", "contact_build", "contact_filter", "barrier_eval",
                  "ccd_step", "cb_get_pairs", "cb_get_active", "cb_get_ccd", "cb_get_bsr", "cb_bsr_device",
                  "cb_get_stats", "cb_sync_status", "cb_get_stage_ms", "cb_set_timing", "cb_status_str",
-                 "cb_version", "cb_kernel_launches", "cb_measure_fma_tflops"]
+                 "cb_version", "cb_kernel_launches", "cb_measure_fma_tflops", "cb_batch_create",
+                 "cb_batch_offsets", "cb_member_count"]
 
 
 class ContactError(RuntimeError):
@@ -74,6 +75,9 @@ def lib():
         L.cb_kernel_launches.restype = i64
         L.cb_kernel_launches.argtypes = []
         L.cb_measure_fma_tflops.argtypes = [i32, i32, i32, C.POINTER(C.c_double)]
+        L.cb_batch_create.argtypes = [C.POINTER(vp), i32, vp, C.POINTER(vp)]
+        L.cb_batch_offsets.argtypes = [vp, vp, vp, vp]
+        L.cb_member_count.argtypes = [vp]
         L.cb_scene_create.argtypes = [C.POINTER(SceneDesc), vp, C.POINTER(vp)]
         L.cb_scene_destroy.argtypes = [vp]
         L.contact_build.argtypes = [vp, vp, vp]
@@ -168,6 +172,16 @@ class ContactScene:
         _check(L.cb_scene_create(C.byref(d), _stream_ptr(stream), C.byref(h)), "cb_scene_create")
         self.h = h
         self.kind = kind
+        self._load_layout()
+
+    def _load_layout(self):
+        self.count = int(lib().cb_member_count(self.h))
+        vo = np.zeros(self.count + 1, np.int64)
+        eo = np.zeros(self.count + 1, np.int64)
+        to = np.zeros(self.count + 1, np.int64)
+        _check(lib().cb_batch_offsets(self.h, vo.ctypes.data, eo.ctypes.data, to.ctypes.data), "cb_batch_offsets")
+        self.vert_offsets, self.edge_offsets, self.tri_offsets = vo, eo, to
+        self.n = int(vo[-1])
 
     @classmethod
     def from_scene(cls, sc, mode: str = "double", **kw) -> "ContactScene":
@@ -208,6 +222,27 @@ class ContactScene:
         self.ccd_step(x, p, alpha, stream)
 
     # -------------------------------------------------------------- getters
+    def member_of_keys(self, keys: np.ndarray) -> np.ndarray:
+        """member index of each (batch-numbered) pair key"""
+        keys = np.asarray(keys, np.uint64)
+        ty = (keys >> np.uint64(62)).astype(np.int64)
+        i = ((keys >> np.uint64(31)) & np.uint64(0x7FFFFFFF)).astype(np.int64)
+        off = np.where(ty == 1, 0, 1)
+        m_v = np.searchsorted(self.vert_offsets, i, side="right") - 1
+        m_e = np.searchsorted(self.edge_offsets, i, side="right") - 1
+        return np.where(off == 0, m_v, m_e)
+
+    def to_member_keys(self, keys: np.ndarray, m: int) -> np.ndarray:
+        """batch-numbered keys of member m -> the member's own numbering"""
+        keys = np.asarray(keys, np.uint64)
+        ty = keys >> np.uint64(62)
+        i = (keys >> np.uint64(31)) & np.uint64(0x7FFFFFFF)
+        j = keys & np.uint64(0x7FFFFFFF)
+        pt = ty == np.uint64(1)
+        di = np.where(pt, self.vert_offsets[m], self.edge_offsets[m]).astype(np.uint64)
+        dj = np.where(pt, self.tri_offsets[m], self.edge_offsets[m]).astype(np.uint64)
+        return (ty << np.uint64(62)) | ((i - di) << np.uint64(31)) | (j - dj)
+
     def pairs(self, which: str = "candidate") -> np.ndarray:
         cnt = C.c_int64()
         lib().cb_get_pairs(self.h, PAIRS[which], None, 0, C.byref(cnt))
@@ -267,3 +302,19 @@ class ContactScene:
         ms = (C.c_float * 5)()
         _check(lib().cb_get_stage_ms(self.h, ms), "cb_get_stage_ms")
         return [float(v) for v in ms]
+
+
+class ContactBatch(ContactScene):
+    """Several scenes of one kind in one pass (cb_batch_create).  x, p and grad
+    span the concatenated vertices (member order); energy and alpha hold one
+    value per member."""
+
+    def __init__(self, members: list, stream=None):
+        L = lib()
+        arr = (C.c_void_p * len(members))(*[m.h.value for m in members])
+        h = C.c_void_p()
+        _check(L.cb_batch_create(arr, len(members), _stream_ptr(stream), C.byref(h)), "cb_batch_create")
+        self.h = h
+        self.kind = members[0].kind
+        self._keep = []
+        self._load_layout()

@@ -60,20 +60,71 @@ static void scene_release(cb_scene* s) {
   DevBuf* bufs[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->frest,
                     &s->frest_dbar, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
                     &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col, &s->bsr_val,
-                    &s->row_cnt, &s->hB9, &s->hB6, &s->hslot, &s->xf, &s->pf, &s->dlist, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag, &s->ccd_pos, &s->ccd_list, &s->scan_tmp, &s->hist,
+                    &s->row_cnt, &s->hB9, &s->hB6, &s->hslot, &s->xf, &s->pf, &s->dlist, &s->mp, &s->vsc, &s->macc, &s->hstage, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag, &s->ccd_pos, &s->ccd_list, &s->scan_tmp, &s->hist,
                     &s->dev_scalars};
   for (DevBuf* b : bufs) buf_free(*b, st);
   for (BroadWork* w : {&s->bw, &s->bwc}) {
-    DevBuf* wb[] = {&w->box32,   &w->box64,  &w->bounds,   &w->cell_cnt, &w->cell_off, &w->ekey[0], &w->ekey[1],
+    DevBuf* wb[] = {&w->grids, &w->cx, &w->box32,   &w->box64,  &w->bounds,   &w->cell_cnt, &w->cell_off, &w->ekey[0], &w->ekey[1],
                     &w->eval[0], &w->eval[1], &w->run_flag, &w->run_id,   &w->run_start, &w->pair_cnt,
                     &w->pair_off, &w->ckey[0], &w->ckey[1],  &w->scan_tmp, &w->hist};
     for (DevBuf* b : wb) buf_free(*b, st);
   }
   cudaStreamSynchronize(st);
   if (s->h_pinned) cudaFreeHost(s->h_pinned);
+  if (s->hstage_host) cudaFreeHost(s->hstage_host);
   for (auto& e : s->ev)
     if (e) cudaEventDestroy(e);
   delete s;
+}
+
+// --- device helpers for scene / batch set-up -------------------------------
+__global__ void k_offset_copy(int32_t* __restrict__ dst, const int32_t* __restrict__ src, int64_t n, int32_t add) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i] + add;
+}
+__global__ void k_comp_copy(int32_t* __restrict__ dst, const int32_t* __restrict__ src, int64_t n, int32_t add_lbl,
+                            int32_t add_v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i] >= 0 ? src[i] + add_lbl : src[i] - add_v;
+}
+__global__ void k_fill_i32(int32_t* __restrict__ dst, int64_t n, int32_t v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = v;
+}
+// pair keys of a member -> keys of the batch (indices shifted)
+__global__ void k_key_shift(uint64_t* __restrict__ dst, const uint64_t* __restrict__ src, int64_t n, uint32_t add_i,
+                            uint32_t add_j) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const uint64_t k = src[q];
+  dst[q] = cb_key(cb_key_type(k), cb_key_i(k) + add_i, cb_key_j(k) + add_j);
+}
+// number of keys below `bound` in a sorted array (one thread)
+__global__ void k_lower_bound(const uint64_t* __restrict__ a, int64_t n, uint64_t bound, uint64_t* out) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < bound) lo = mid + 1;
+    else hi = mid;
+  }
+  *out = (uint64_t)lo;
+}
+
+static cb_status alloc_members(cb_scene* s, cudaStream_t st) {
+  const int M = s->count;
+  CB_TRY(buf_ensure(s->mp, sizeof(MemberParams) * (size_t)M, st));
+  CB_TRY(buf_ensure(s->macc, sizeof(unsigned long long) * MACC_STRIDE * (size_t)M, st));
+  CB_TRY(buf_ensure(s->hstage, sizeof(double) * (size_t)M + 64, st));
+  CB_CUDA(cudaMemsetAsync(s->macc.p, 0, sizeof(unsigned long long) * MACC_STRIDE * (size_t)M, st));
+  if (cudaMallocHost(&s->hstage_host, 64 * (size_t)M + 256) != cudaSuccess) return CB_ERR_OOM;
+  return CB_OK;
+}
+
+static cb_status upload_members(cb_scene* s, cudaStream_t st) {
+  memcpy(s->hstage_host, s->hmp.data(), sizeof(MemberParams) * s->hmp.size());
+  CB_CUDA(cudaMemcpyAsync(s->mp.p, s->hstage_host, sizeof(MemberParams) * s->hmp.size(), cudaMemcpyHostToDevice, st));
+  CB_CUDA(cudaStreamSynchronize(st));
+  return CB_OK;
 }
 
 template <typename T>
@@ -199,11 +250,20 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
   s->cell_hint = 1.0f;
   s->last_stream = st;
   cudaGetDevice(&s->device);
+  s->count = 1;
+  s->hmp.assign(1, MemberParams{s->xi, s->dhat, s->a, s->kappa, 0.0, fm == CB_FILTER_SINGLE ? 1 : 0, s->core_temp,
+                                fm == CB_FILTER_OFF ? 1 : 0, s->n_prims});
+  s->voff = {0, (int64_t)n};
+  s->eoff = {0, (int64_t)E};
+  s->toff = {0, (int64_t)T};
   cb_status rc = CB_OK;
   auto fail = [&](cb_status e) {
     scene_release(s);
     return e;
   };
+  if ((rc = alloc_members(s, st)) != CB_OK) return fail(rc);
+  if ((rc = buf_ensure(s->vsc, sizeof(int32_t) * (size_t)n, st)) != CB_OK) return fail(rc);
+  if (cudaMemsetAsync(s->vsc.p, 0, sizeof(int32_t) * (size_t)n, st) != cudaSuccess) return fail(CB_ERR_CUDA);
   if (cudaMallocHost((void**)&s->h_pinned, 64 * sizeof(uint64_t)) != cudaSuccess) return fail(CB_ERR_OOM);
   if ((rc = buf_ensure(s->dev_scalars, SC_N * sizeof(uint64_t), st)) != CB_OK) return fail(rc);
   if (cudaMemsetAsync(s->dev_scalars.p, 0, SC_N * sizeof(uint64_t), st) != cudaSuccess) return fail(CB_ERR_CUDA);
@@ -218,10 +278,142 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
   for (auto& e : s->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(CB_ERR_CUDA);
   if ((rc = filter_precompute(s, st)) != CB_OK) return fail(rc);
+  s->hmp[0].dbar_min = std::isfinite(s->dbar_min) ? s->dbar_min : 0.0;
+  if ((rc = upload_members(s, st)) != CB_OK) return fail(rc);
+  if (s->kind == CB_SHELL && s->n_frest > 0) {
+    k_lower_bound<<<1, 1, 0, cb_count(st)>>>(bp<uint64_t>(s->frest), s->n_frest, (uint64_t)CB_KEY_EE << 62,
+                                             scalars(s) + SC_COUNT1);
+    uint64_t h;
+    if ((rc = read_scalars(s, SC_COUNT1, 1, &h, st)) != CB_OK) return fail(rc);
+    s->n_frest_pt = (int64_t)h;
+  }
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CB_ERR_CUDA);
   *out = s;
   return CB_OK;
 }
+
+cb_status cb_batch_create(cb_scene* const* members, int32_t count, void* stream, cb_scene** out) {
+  if (!members || count < 1 || !out) return CB_ERR_ARG;
+  for (int m = 0; m < count; ++m)
+    if (!members[m] || members[m]->count != 1 || members[m]->kind != members[0]->kind) return CB_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cb_scene* b = new cb_scene();
+  b->kind = members[0]->kind;
+  b->count = count;
+  b->last_stream = st;
+  b->cell_hint = members[0]->cell_hint;
+  cudaGetDevice(&b->device);
+  b->voff.assign(count + 1, 0);
+  b->eoff.assign(count + 1, 0);
+  b->toff.assign(count + 1, 0);
+  std::vector<int64_t> roff(count + 1, 0);
+  int64_t nf = 0, nf_pt = 0;
+  for (int m = 0; m < count; ++m) {
+    const cb_scene* s = members[m];
+    b->voff[m + 1] = b->voff[m] + s->n;
+    b->eoff[m + 1] = b->eoff[m] + s->E;
+    b->toff[m + 1] = b->toff[m] + s->T;
+    roff[m + 1] = roff[m] + s->n_rods;
+    b->hmp.push_back(s->hmp[0]);
+    nf += s->n_frest;
+    nf_pt += s->n_frest_pt;
+  }
+  if (b->voff[count] > 0x7fffffff || b->eoff[count] > 0x7fffffff || b->toff[count] > 0x7fffffff) {
+    delete b;
+    return CB_ERR_ARG;
+  }
+  b->n = (int)b->voff[count];
+  b->E = (int)b->eoff[count];
+  b->T = (int)b->toff[count];
+  b->n_rods = (int)roff[count];
+  b->n_prims = b->kind == CB_ROD ? b->E : b->n + b->T + b->E;
+  if (b->kind == CB_ROD) {
+    b->bits_i = b->bits_j = bits_needed(std::max(b->E - 1, 1));
+  } else {
+    b->bits_i = bits_needed(std::max(std::max(b->n, b->E) - 1, 1));
+    b->bits_j = bits_needed(std::max(std::max(b->T, b->E) - 1, 1));
+  }
+  const MemberParams& m0 = b->hmp[0];
+  b->xi = m0.xi;
+  b->dhat = m0.dhat;
+  b->a = m0.a;
+  b->kappa = m0.kappa;
+  b->filter = m0.filter_off ? CB_FILTER_OFF : (m0.single ? CB_FILTER_SINGLE : CB_FILTER_DOUBLE);
+  b->core_temp = m0.core_temp;
+  b->dbar_min = INFINITY;
+  for (int m = 0; m < count; ++m)
+    if (std::isfinite(members[m]->dbar_min)) b->dbar_min = std::min(b->dbar_min, members[m]->dbar_min);
+  cb_status rc = CB_OK;
+  auto fail = [&](cb_status e) {
+    scene_release(b);
+    return e;
+  };
+  if (cudaMallocHost((void**)&b->h_pinned, 64 * sizeof(uint64_t)) != cudaSuccess) return fail(CB_ERR_OOM);
+  if ((rc = buf_ensure(b->dev_scalars, SC_N * sizeof(uint64_t), st)) != CB_OK) return fail(rc);
+  if (cudaMemsetAsync(b->dev_scalars.p, 0, SC_N * sizeof(uint64_t), st) != cudaSuccess) return fail(CB_ERR_CUDA);
+  if ((rc = alloc_members(b, st)) != CB_OK) return fail(rc);
+  if ((rc = buf_ensure(b->ev0, sizeof(int32_t) * (size_t)std::max(1, b->E), st)) != CB_OK) return fail(rc);
+  if ((rc = buf_ensure(b->ev1, sizeof(int32_t) * (size_t)std::max(1, b->E), st)) != CB_OK) return fail(rc);
+  if ((rc = buf_ensure(b->tv, sizeof(int32_t) * 3 * (size_t)std::max(1, b->T), st)) != CB_OK) return fail(rc);
+  if ((rc = buf_ensure(b->comp, sizeof(int32_t) * (size_t)b->n, st)) != CB_OK) return fail(rc);
+  if ((rc = buf_ensure(b->vsc, sizeof(int32_t) * (size_t)b->n, st)) != CB_OK) return fail(rc);
+  if ((rc = buf_ensure(b->win, sizeof(int32_t) * (size_t)std::max(1, b->E), st)) != CB_OK) return fail(rc);
+  if ((rc = buf_ensure(b->frest, sizeof(uint64_t) * (size_t)std::max<int64_t>(1, nf), st)) != CB_OK) return fail(rc);
+  int64_t wpt = 0, wee = nf_pt;
+  for (int m = 0; m < count; ++m) {
+    const cb_scene* s = members[m];
+    const int32_t vo = (int32_t)b->voff[m], eo = (int32_t)b->eoff[m], to = (int32_t)b->toff[m];
+    if (s->E > 0) {
+      k_offset_copy<<<cb_grid(s->E), CB_THREADS, 0, cb_count(st)>>>(bp<int32_t>(b->ev0) + eo, bp<int32_t>(s->ev0),
+                                                                     s->E, vo);
+      k_offset_copy<<<cb_grid(s->E), CB_THREADS, 0, cb_count(st)>>>(bp<int32_t>(b->ev1) + eo, bp<int32_t>(s->ev1),
+                                                                     s->E, vo);
+      if (b->kind == CB_ROD)
+        k_offset_copy<<<cb_grid(s->E), CB_THREADS, 0, cb_count(st)>>>(bp<int32_t>(b->win) + eo,
+                                                                       bp<int32_t>(s->win), s->E, eo);
+    }
+    for (int k = 0; k < 3 && s->T > 0; ++k)
+      k_offset_copy<<<cb_grid(s->T), CB_THREADS, 0, cb_count(st)>>>(
+          bp<int32_t>(b->tv) + (size_t)k * b->T + to, bp<int32_t>(s->tv) + (size_t)k * s->T, s->T, vo);
+    const int32_t lbl = b->kind == CB_ROD ? (int32_t)roff[m] : vo;
+    k_comp_copy<<<cb_grid(s->n), CB_THREADS, 0, cb_count(st)>>>(bp<int32_t>(b->comp) + vo, bp<int32_t>(s->comp),
+                                                                 s->n, lbl, vo);
+    k_fill_i32<<<cb_grid(s->n), CB_THREADS, 0, cb_count(st)>>>(bp<int32_t>(b->vsc) + vo, s->n, m);
+    if (b->kind == CB_SHELL && s->n_frest > 0) {
+      if (s->n_frest_pt > 0)
+        k_key_shift<<<cb_grid(s->n_frest_pt), CB_THREADS, 0, cb_count(st)>>>(
+            bp<uint64_t>(b->frest) + wpt, bp<uint64_t>(s->frest), s->n_frest_pt, (uint32_t)vo, (uint32_t)to);
+      const int64_t nee = s->n_frest - s->n_frest_pt;
+      if (nee > 0)
+        k_key_shift<<<cb_grid(nee), CB_THREADS, 0, cb_count(st)>>>(bp<uint64_t>(b->frest) + wee,
+                                                                    bp<uint64_t>(s->frest) + s->n_frest_pt, nee,
+                                                                    (uint32_t)eo, (uint32_t)eo);
+      wpt += s->n_frest_pt;
+      wee += nee;
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess) return fail(CB_ERR_CUDA);
+  b->n_frest = b->kind == CB_SHELL ? nf : 0;
+  b->n_frest_pt = nf_pt;
+  for (auto& e : b->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(CB_ERR_CUDA);
+  if ((rc = upload_members(b, st)) != CB_OK) return fail(rc);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CB_ERR_CUDA);
+  *out = b;
+  return CB_OK;
+}
+
+cb_status cb_batch_offsets(cb_scene* s, int64_t* vert_offsets, int64_t* edge_offsets, int64_t* tri_offsets) {
+  if (!s) return CB_ERR_ARG;
+  for (int m = 0; m <= s->count; ++m) {
+    if (vert_offsets) vert_offsets[m] = s->voff[m];
+    if (edge_offsets) edge_offsets[m] = s->eoff[m];
+    if (tri_offsets) tri_offsets[m] = s->toff[m];
+  }
+  return CB_OK;
+}
+
+int32_t cb_member_count(cb_scene* s) { return s ? s->count : 0; }
 
 cb_status cb_scene_destroy(cb_scene* s) {
   if (!s) return CB_ERR_ARG;
@@ -241,7 +433,7 @@ cb_status contact_build(cb_scene* s, const double* x, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   s->last_stream = st;
   stage_begin(s, 0, st);
-  cb_status r = broad_phase(s, s->bw, x, nullptr, 0.5 * s->a, s->cand, &s->n_cand, st);
+  cb_status r = broad_phase(s, s->bw, x, nullptr, false, s->cand, &s->n_cand, st);
   stage_end(s, 0, st);
   s->n_active = 0;
   return r;

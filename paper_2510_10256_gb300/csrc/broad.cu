@@ -15,6 +15,10 @@
 // triangle, edge vs later edge); a pair is reported only in the cell holding
 // the low corner of the two boxes' intersection (its "home" cell) -> compact
 // keys -> radix sort -> canonical keys.
+//
+// Several scenes can share one pass (a batch): every member has its own
+// box inflation and grid, and its member index sits above the 30 Morton bits
+// of the cell key, so primitives of different members never meet in a cell.
 #include <algorithm>
 #include <cmath>
 
@@ -28,11 +32,6 @@ struct Topo {
   const int32_t* __restrict__ ev0;
   const int32_t* __restrict__ ev1;
   const int32_t* __restrict__ tv;
-};
-
-struct Grid {
-  float ox, oy, oz, inv;
-  int dx, dy, dz;
 };
 
 __device__ __forceinline__ int prim_verts(const Topo& t, int q, int v[3]) {
@@ -76,20 +75,39 @@ __host__ __device__ __forceinline__ float o2f(uint32_t o) {
 #endif
 }
 
-__global__ void k_bounds_init(uint32_t* b) {
-  if (threadIdx.x < 3) b[threadIdx.x] = 0xffffffffu;
-  else if (threadIdx.x < 6) b[threadIdx.x] = 0u;
-  else if (threadIdx.x < 8) ((unsigned long long*)b)[3] = 0ull;  // extent sum (bits of double) at b[6..7]
+// per member: [0..2] min (ordered), [3..5] max (ordered), [6..7] pad, then a double extent sum
+constexpr int BOUNDS_STRIDE = 10;  // uint32 words per member (40 bytes)
+
+__global__ void k_bounds_init(uint32_t* b, int count) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= count) return;
+  uint32_t* q = b + (size_t)m * BOUNDS_STRIDE;
+  for (int k = 0; k < 3; ++k) {
+    q[k] = 0xffffffffu;
+    q[3 + k] = 0u;
+  }
+  q[6] = q[7] = 0u;
+  *(double*)(q + 8) = 0.0;
 }
 
-__global__ void k_boxes(Topo t, int np, const double* __restrict__ x, const double* __restrict__ p, double h,
+__device__ __forceinline__ int prim_member(const Topo& t, const int32_t* __restrict__ vsc, int q) {
+  int v[3];
+  prim_verts(t, q, v);
+  return vsc[v[0]];
+}
+
+__global__ void k_boxes(Topo t, int np, const double* __restrict__ x, const double* __restrict__ p,
+                        const double* __restrict__ hm, const int32_t* __restrict__ vsc,
                         float4* __restrict__ box32, double* __restrict__ box64, uint32_t* bounds) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   float lo32[3] = {INFINITY, INFINITY, INFINITY}, hi32[3] = {-INFINITY, -INFINITY, -INFINITY};
   float ext = 0.f;
+  int mem = -1;
   if (q < np) {
     int v[3];
     const int nv = prim_verts(t, q, v);
+    mem = vsc[v[0]];
+    const double h = hm[mem];
     double lo[3], hi[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -115,7 +133,32 @@ __global__ void k_boxes(Topo t, int np, const double* __restrict__ x, const doub
     box32[2 * (size_t)q] = make_float4(lo32[0], lo32[1], lo32[2], 0.f);
     box32[2 * (size_t)q + 1] = make_float4(hi32[0], hi32[1], hi32[2], 0.f);
   }
-  // block reduction of bounds and extent sum
+  // per-member bounds and extent sums: a block reduction when the block holds
+  // one member (the usual case: members occupy contiguous primitive ranges),
+  // per-thread atomics at the few blocks that straddle members
+  __shared__ int s_mmin, s_mmax;
+  if (threadIdx.x == 0) {
+    s_mmin = 0x7fffffff;
+    s_mmax = -1;
+  }
+  __syncthreads();
+  if (mem >= 0) {
+    atomicMin(&s_mmin, mem);
+    atomicMax(&s_mmax, mem);
+  }
+  __syncthreads();
+  if (s_mmax < 0) return;
+  if (s_mmin != s_mmax) {
+    if (mem >= 0) {
+      uint32_t* bq = bounds + (size_t)mem * BOUNDS_STRIDE;
+      for (int k = 0; k < 3; ++k) {
+        atomicMin(&bq[k], f2o(lo32[k]));
+        atomicMax(&bq[3 + k], f2o(hi32[k]));
+      }
+      atomicAdd((double*)(bq + 8), (double)ext);
+    }
+    return;
+  }
   __shared__ float s_lo[3][CB_THREADS / 32], s_hi[3][CB_THREADS / 32];
   __shared__ double s_ext[CB_THREADS / 32];
   double e = ext;
@@ -147,11 +190,12 @@ __global__ void k_boxes(Topo t, int np, const double* __restrict__ x, const doub
       }
       es += s_ext[q2];
     }
+    uint32_t* bq = bounds + (size_t)s_mmin * BOUNDS_STRIDE;
     for (int k = 0; k < 3; ++k) {
-      atomicMin(&bounds[k], f2o(l[k]));
-      atomicMax(&bounds[3 + k], f2o(hh[k]));
+      atomicMin(&bq[k], f2o(l[k]));
+      atomicMax(&bq[3 + k], f2o(hh[k]));
     }
-    atomicAdd((double*)(bounds + 6), es);
+    atomicAdd((double*)(bq + 8), es);
   }
 }
 
@@ -173,9 +217,11 @@ __device__ __forceinline__ uint32_t morton(int x, int y, int z) {
   return spread10((uint32_t)x) | (spread10((uint32_t)y) << 1) | (spread10((uint32_t)z) << 2);
 }
 
-__global__ void k_cell_count(int np, const float4* __restrict__ box32, Grid g, uint32_t* __restrict__ cnt) {
+__global__ void k_cell_count(Topo t, int np, const float4* __restrict__ box32, const int32_t* __restrict__ vsc,
+                             const Grid* __restrict__ grids, uint32_t* __restrict__ cnt) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= np) return;
+  const Grid g = grids[prim_member(t, vsc, q)];
   float4 lo = box32[2 * (size_t)q], hi = box32[2 * (size_t)q + 1];
   int nx = cell_of(hi.x, g.ox, g.inv, g.dx) - cell_of(lo.x, g.ox, g.inv, g.dx) + 1;
   int ny = cell_of(hi.y, g.oy, g.inv, g.dy) - cell_of(lo.y, g.oy, g.inv, g.dy) + 1;
@@ -183,25 +229,29 @@ __global__ void k_cell_count(int np, const float4* __restrict__ box32, Grid g, u
   cnt[q] = (uint32_t)(nx * ny * nz);
 }
 
-__global__ void k_cell_fill(int np, const float4* __restrict__ box32, Grid g, const uint32_t* __restrict__ off,
-                            uint32_t* __restrict__ ekey, uint32_t* __restrict__ eval) {
+__global__ void k_cell_fill(Topo t, int np, const float4* __restrict__ box32, const int32_t* __restrict__ vsc,
+                            const Grid* __restrict__ grids, const uint32_t* __restrict__ off,
+                            uint64_t* __restrict__ ekey, uint32_t* __restrict__ eval) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= np) return;
+  const int mem = prim_member(t, vsc, q);
+  const Grid g = grids[mem];
   float4 lo = box32[2 * (size_t)q], hi = box32[2 * (size_t)q + 1];
   int x0 = cell_of(lo.x, g.ox, g.inv, g.dx), x1 = cell_of(hi.x, g.ox, g.inv, g.dx);
   int y0 = cell_of(lo.y, g.oy, g.inv, g.dy), y1 = cell_of(hi.y, g.oy, g.inv, g.dy);
   int z0 = cell_of(lo.z, g.oz, g.inv, g.dz), z1 = cell_of(hi.z, g.oz, g.inv, g.dz);
   uint32_t w = off[q];
+  const uint64_t mbits = (uint64_t)mem << 30;
   for (int z = z0; z <= z1; ++z)
     for (int y = y0; y <= y1; ++y)
       for (int xx = x0; xx <= x1; ++xx) {
-        ekey[w] = morton(xx, y, z);
+        ekey[w] = mbits | morton(xx, y, z);
         eval[w] = (uint32_t)q;
         ++w;
       }
 }
 
-__global__ void k_run_flag(int64_t ne, const uint32_t* __restrict__ key, uint32_t* __restrict__ flag) {
+__global__ void k_run_flag(int64_t ne, const uint64_t* __restrict__ key, uint32_t* __restrict__ flag) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ne) return;
   flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1u : 0u;
@@ -234,13 +284,13 @@ __device__ __forceinline__ int lower_bound_u32(const uint32_t* __restrict__ a, i
 struct PairArgs {
   Topo t;
   int64_t ne;
-  const uint32_t* __restrict__ ekey;
+  const uint64_t* __restrict__ ekey;
   const uint32_t* __restrict__ eval;
   const uint32_t* __restrict__ run_id;
   const uint32_t* __restrict__ run_start;
   const float4* __restrict__ box32;
   const double* __restrict__ box64;
-  Grid g;
+  const Grid* __restrict__ grids;
   int bi, bj;
 };
 
@@ -253,7 +303,8 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __re
   if (i >= A.ne) return;
   const Topo& t = A.t;
   const uint32_t P = A.eval[i];
-  const uint32_t kc = A.ekey[i];
+  const uint64_t kc = A.ekey[i];
+  const Grid G = A.grids[kc >> 30];
   const uint32_t r = A.run_id[i];
   const int s = (int)A.run_start[r], e = (int)A.run_start[r + 1];
   int j0, j1;
@@ -293,10 +344,10 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __re
           qlo.z <= phi.z))
       continue;
     // home cell: low corner of the intersection
-    const uint32_t hc = morton(cell_of(fmaxf(plo.x, qlo.x), A.g.ox, A.g.inv, A.g.dx),
-                               cell_of(fmaxf(plo.y, qlo.y), A.g.oy, A.g.inv, A.g.dy),
-                               cell_of(fmaxf(plo.z, qlo.z), A.g.oz, A.g.inv, A.g.dz));
-    if (hc != kc) continue;
+    const uint32_t hc = morton(cell_of(fmaxf(plo.x, qlo.x), G.ox, G.inv, G.dx),
+                               cell_of(fmaxf(plo.y, qlo.y), G.oy, G.inv, G.dy),
+                               cell_of(fmaxf(plo.z, qlo.z), G.oz, G.inv, G.dz));
+    if (hc != (uint32_t)(kc & 0x3fffffffull)) continue;
     int qv[3];
     prim_verts(t, (int)Q, qv);
     bool inc = false;
@@ -337,9 +388,10 @@ __global__ void k_expand(int64_t nc, const uint64_t* __restrict__ ck, int bi, in
 
 }  // namespace
 
-cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* p, double h, DevBuf& out,
+cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* p, bool swept, DevBuf& out,
                       int64_t* n_out, cudaStream_t st) {
   const int np = s->n_prims;
+  const int M = s->count;
   if (np == 0) {
     *n_out = 0;
     return CB_OK;
@@ -347,79 +399,114 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   Topo t{s->kind, s->n, s->T, s->E, bp<int32_t>(s->ev0), bp<int32_t>(s->ev1), bp<int32_t>(s->tv)};
   CB_TRY(buf_ensure(w.box32, sizeof(float4) * 2 * (size_t)np, st));
   CB_TRY(buf_ensure(w.box64, sizeof(double) * 6 * (size_t)np, st));
-  CB_TRY(buf_ensure(w.bounds, 64, st));
+  CB_TRY(buf_ensure(w.bounds, sizeof(uint32_t) * BOUNDS_STRIDE * (size_t)M, st));
+  CB_TRY(buf_ensure(w.grids, sizeof(Grid) * (size_t)M, st));
+  CB_TRY(buf_ensure(w.cx, sizeof(double) * 4 * (size_t)M, st));
+  // inflation per member: a/2 (static, full activation) or xi/2 (swept, CCD)
+  std::vector<double> hm(M);
+  for (int m = 0; m < M; ++m) hm[m] = swept ? 0.5 * s->hmp[m].xi : 0.5 * s->hmp[m].a;
+  CB_TRY(buf_ensure(s->hstage, sizeof(double) * 8 * (size_t)M + 256, st));
+  double* hstage = (double*)s->hstage_host;
   uint32_t* bounds = bp<uint32_t>(w.bounds);
-  k_bounds_init<<<1, 32, 0, cb_count(st)>>>(bounds);
-  k_boxes<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(t, np, x, p, h, bp<float4>(w.box32), bp<double>(w.box64), bounds);
+  // stage: [0, M) inflation, later grids and centres
+  memcpy(hstage, hm.data(), sizeof(double) * M);
+  CB_CUDA(cudaMemcpyAsync(s->hstage.p, hstage, sizeof(double) * M, cudaMemcpyHostToDevice, st));
+  k_bounds_init<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(bounds, M);
+  k_boxes<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(t, np, x, p, bp<double>(s->hstage), bp<int32_t>(s->vsc),
+                                                       bp<float4>(w.box32), bp<double>(w.box64), bounds);
   CB_CUDA(cudaGetLastError());
-  uint32_t hb[8];
-  CB_CUDA(cudaMemcpyAsync(hb, bounds, 32, cudaMemcpyDeviceToHost, st));
+  std::vector<uint32_t> hb((size_t)M * BOUNDS_STRIDE);
+  CB_CUDA(cudaMemcpyAsync(hstage, bounds, sizeof(uint32_t) * BOUNDS_STRIDE * M, cudaMemcpyDeviceToHost, st));
   CB_CUDA(cudaStreamSynchronize(st));
-  float lo[3], hi[3];
-  for (int k = 0; k < 3; ++k) {
-    lo[k] = o2f(hb[k]);
-    hi[k] = o2f(hb[3 + k]);
+  memcpy(hb.data(), hstage, sizeof(uint32_t) * BOUNDS_STRIDE * M);
+  std::vector<Grid> grids(M);
+  w.hcx.assign(4 * (size_t)M, 0.0);
+  for (int m = 0; m < M; ++m) {
+    const uint32_t* bq = hb.data() + (size_t)m * BOUNDS_STRIDE;
+    float lo[3], hi[3];
+    bool empty = false;
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = o2f(bq[k]);
+      hi[k] = o2f(bq[3 + k]);
+      if (!(hi[k] >= lo[k])) empty = true;
+    }
+    double ext_sum;
+    memcpy(&ext_sum, bq + 8, 8);
+    Grid& g = grids[m];
+    if (empty) {
+      g = Grid{0.f, 0.f, 0.f, 1.f, 1, 1, 1, 0};
+      continue;
+    }
+    double X = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      w.hcx[4 * m + k] = 0.5 * ((double)lo[k] + (double)hi[k]);
+      X = std::max(X, 0.5 * ((double)hi[k] - (double)lo[k]) * (1.0 + 1e-6));
+    }
+    w.hcx[4 * m + 3] = X;
+    // cell size: mean primitive box extent of the member (scaled by the tuned
+    // factor), rounded to a 1/4-octave grid so tiny summation-order
+    // differences never change it
+    const int npm = std::max(1, s->hmp[m].n_prims);
+    double c = (s->cell_hint > 0 ? (double)s->cell_hint : 1.0) * (ext_sum / npm);
+    if (!(c > 0)) c = 1.0;
+    c = std::exp2(std::floor(std::log2(c) * 4.0) / 4.0);
+    for (int k = 0; k < 3; ++k) {
+      double span = (double)hi[k] - (double)lo[k];
+      if (span / c > 1000.0) c = span / 1000.0;
+    }
+    g.inv = (float)(1.0 / c);
+    g.ox = lo[0];
+    g.oy = lo[1];
+    g.oz = lo[2];
+    int* dims[3] = {&g.dx, &g.dy, &g.dz};
+    for (int k = 0; k < 3; ++k) {
+      double span = (double)hi[k] - (double)lo[k];
+      int d = (int)std::floor(span * (double)g.inv) + 2;
+      *dims[k] = std::min(std::max(d, 1), 1024);
+    }
+    g.pad = 0;
+    if (m == 0) w.cell = (float)c;
   }
-  double ext_sum;
-  memcpy(&ext_sum, hb + 6, 8);
-  w.X = 0.0;
-  for (int k = 0; k < 3; ++k) {
-    w.ctr[k] = 0.5 * ((double)lo[k] + (double)hi[k]);
-    w.X = std::max(w.X, 0.5 * ((double)hi[k] - (double)lo[k]) * (1.0 + 1e-6));
-  }
-  // cell size: mean primitive box extent (scaled by the tuned factor), rounded to
-  // a 1/4-octave grid so that tiny summation-order differences never change it
-  double c = s->cell_hint > 0 ? (double)s->cell_hint * (ext_sum / std::max(1, np)) : ext_sum / std::max(1, np);
-  if (!(c > 0)) c = 1.0;
-  double lg = std::floor(std::log2(c) * 4.0) / 4.0;
-  c = std::exp2(lg);
-  for (int k = 0; k < 3; ++k) {
-    double span = (double)hi[k] - (double)lo[k];
-    if (span / c > 1000.0) c = span / 1000.0;
-  }
-  Grid g;
-  g.inv = (float)(1.0 / c);
-  g.ox = lo[0];
-  g.oy = lo[1];
-  g.oz = lo[2];
-  int* dims[3] = {&g.dx, &g.dy, &g.dz};
-  for (int k = 0; k < 3; ++k) {
-    double span = (double)hi[k] - (double)lo[k];
-    int d = (int)std::floor(span * (double)g.inv) + 2;
-    *dims[k] = std::min(std::max(d, 1), 1024);
-  }
-  w.cell = (float)c;
+  memcpy(hstage, grids.data(), sizeof(Grid) * M);
+  CB_CUDA(cudaMemcpyAsync(w.grids.p, hstage, sizeof(Grid) * M, cudaMemcpyHostToDevice, st));
+  CB_CUDA(cudaStreamSynchronize(st));  // the staging buffer is reused below
+  memcpy(hstage, w.hcx.data(), sizeof(double) * 4 * M);
+  CB_CUDA(cudaMemcpyAsync(w.cx.p, hstage, sizeof(double) * 4 * M, cudaMemcpyHostToDevice, st));
+  const Grid* dgrids = bp<Grid>(w.grids);
 
   CB_TRY(buf_ensure(w.cell_cnt, sizeof(uint32_t) * (size_t)np + 16, st));
   CB_TRY(buf_ensure(w.cell_off, sizeof(uint32_t) * ((size_t)np + 1), st));
   CB_TRY(buf_ensure(w.scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(np + 1) + 8), st));
-  k_cell_count<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(np, bp<float4>(w.box32), g, bp<uint32_t>(w.cell_cnt));
+  k_cell_count<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(t, np, bp<float4>(w.box32), bp<int32_t>(s->vsc), dgrids,
+                                                            bp<uint32_t>(w.cell_cnt));
   uint32_t* tot_dev = (uint32_t*)(scalars(s) + SC_COUNT0);
   cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.cell_cnt), bp<uint32_t>(w.cell_off), np,
                                           bp<uint32_t>(w.scan_tmp), tot_dev, st);
   CB_CUDA(cudaGetLastError());
-  uint32_t ne32;
-  CB_CUDA(cudaMemcpyAsync(&ne32, tot_dev, 4, cudaMemcpyDeviceToHost, st));
-  CB_CUDA(cudaStreamSynchronize(st));
-  const int64_t ne = ne32;
+  uint64_t hne;
+  CB_TRY(read_scalars(s, SC_COUNT0, 1, &hne, st));
+  const int64_t ne = (uint32_t)hne;
   if (ne == 0) {
     *n_out = 0;
     return CB_OK;
   }
   for (int b = 0; b < 2; ++b) {
-    CB_TRY(buf_ensure(w.ekey[b], sizeof(uint32_t) * (size_t)ne, st));
+    CB_TRY(buf_ensure(w.ekey[b], sizeof(uint64_t) * (size_t)ne, st));
     CB_TRY(buf_ensure(w.eval[b], sizeof(uint32_t) * (size_t)ne, st));
   }
-  k_cell_fill<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(np, bp<float4>(w.box32), g, bp<uint32_t>(w.cell_off),
-                                                   bp<uint32_t>(w.ekey[0]), bp<uint32_t>(w.eval[0]));
+  k_cell_fill<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(t, np, bp<float4>(w.box32), bp<int32_t>(s->vsc), dgrids,
+                                                           bp<uint32_t>(w.cell_off), bp<uint64_t>(w.ekey[0]),
+                                                           bp<uint32_t>(w.eval[0]));
   CB_TRY(buf_ensure(w.hist, sizeof(uint32_t) * (size_t)cbp::radix_hist_elems(ne), st));
   CB_TRY(buf_ensure(w.scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(cbp::radix_hist_elems(ne)) +
                                                              cbp::scan_tmp_elems(ne + 1) + 8),
                     st));
-  int r = cbp::radix_sort<uint32_t, uint32_t, true>(bp<uint32_t>(w.ekey[0]), bp<uint32_t>(w.eval[0]),
-                                                    bp<uint32_t>(w.ekey[1]), bp<uint32_t>(w.eval[1]), ne, 0, 30,
-                                                    bp<uint32_t>(w.hist), bp<uint32_t>(w.scan_tmp), st);
-  const uint32_t* ekey = bp<uint32_t>(w.ekey[r]);
+  int mbits = 0;
+  while ((1 << mbits) < M) ++mbits;
+  int r = cbp::radix_sort<uint64_t, uint32_t, true>(bp<uint64_t>(w.ekey[0]), bp<uint32_t>(w.eval[0]),
+                                                    bp<uint64_t>(w.ekey[1]), bp<uint32_t>(w.eval[1]), ne, 0,
+                                                    30 + mbits, bp<uint32_t>(w.hist), bp<uint32_t>(w.scan_tmp), st);
+  const uint64_t* ekey = bp<uint64_t>(w.ekey[r]);
   const uint32_t* eval = bp<uint32_t>(w.eval[r]);
   CB_TRY(buf_ensure(w.run_flag, sizeof(uint32_t) * (size_t)ne, st));
   CB_TRY(buf_ensure(w.run_id, sizeof(uint32_t) * (size_t)ne, st));
@@ -431,7 +518,7 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.run_flag), bp<uint32_t>(w.pair_off), ne,
                                           bp<uint32_t>(w.scan_tmp), (uint32_t*)nullptr, st);
   k_run_start<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, bp<uint32_t>(w.run_flag), bp<uint32_t>(w.pair_off),
-                                                   bp<uint32_t>(w.run_id), bp<uint32_t>(w.run_start));
+                                                           bp<uint32_t>(w.run_id), bp<uint32_t>(w.run_start));
   PairArgs A;
   A.t = t;
   A.ne = ne;
@@ -441,17 +528,16 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   A.run_start = bp<uint32_t>(w.run_start);
   A.box32 = bp<float4>(w.box32);
   A.box64 = bp<double>(w.box64);
-  A.g = g;
+  A.grids = dgrids;
   A.bi = s->bits_i;
   A.bj = s->bits_j;
   k_pairs<false><<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint32_t>(w.pair_cnt), nullptr, nullptr);
   cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off), ne,
                                           bp<uint32_t>(w.scan_tmp), tot_dev, st);
   CB_CUDA(cudaGetLastError());
-  uint32_t nc32;
-  CB_CUDA(cudaMemcpyAsync(&nc32, tot_dev, 4, cudaMemcpyDeviceToHost, st));
-  CB_CUDA(cudaStreamSynchronize(st));
-  const int64_t nc = nc32;
+  uint64_t hnc;
+  CB_TRY(read_scalars(s, SC_COUNT0, 1, &hnc, st));
+  const int64_t nc = (uint32_t)hnc;
   *n_out = nc;
   if (nc == 0) return CB_OK;
   for (int b = 0; b < 2; ++b) CB_TRY(buf_ensure(w.ckey[b], sizeof(uint64_t) * (size_t)nc, st));
@@ -465,7 +551,8 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
                                                       nullptr, nc, 0, cbits, bp<uint32_t>(w.hist),
                                                       bp<uint32_t>(w.scan_tmp), st);
   CB_TRY(buf_ensure(out, sizeof(uint64_t) * (size_t)nc, st));
-  k_expand<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(nc, bp<uint64_t>(w.ckey[r2]), s->bits_i, s->bits_j, bp<uint64_t>(out));
+  k_expand<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(nc, bp<uint64_t>(w.ckey[r2]), s->bits_i, s->bits_j,
+                                                        bp<uint64_t>(out));
   CB_CUDA(cudaGetLastError());
   return CB_OK;
 }

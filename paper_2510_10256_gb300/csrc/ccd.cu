@@ -46,21 +46,23 @@ struct CcdArgs {
   const uint64_t* __restrict__ frest;
   int64_t nf;
   int T, n, kind;
-  int filter_off, single, core_temp;
-  double xi;
+  const int32_t* __restrict__ vsc;           // member of each vertex
+  const MemberParams* __restrict__ mp;
+  const double* __restrict__ cx;             // per member: centre[3], X
   const double* __restrict__ x;
   const double* __restrict__ p;
   double* __restrict__ t_out;
   uint8_t* __restrict__ cls_out;
-  unsigned long long* __restrict__ alpha_bits;  // min over exact t_p
-  unsigned long long* __restrict__ lb_bits;     // min over lower bounds of unresolved pairs
+  unsigned long long* __restrict__ macc;     // per member: alpha bits, lb bits, status, band lo/hi
   unsigned long long* __restrict__ status;
   unsigned long long* __restrict__ max_iters;
-  const float* __restrict__ xf;   // FP32 (x - centre)
+  const float* __restrict__ xf;   // FP32 (x - member centre)
   const float* __restrict__ pf;   // FP32 p
-  float X;                        // max |x - centre|
-  double thrC;                    // U pairs with a distance bound above this are surely not class C
 };
+
+__device__ __forceinline__ unsigned long long* macc_of(const CcdArgs& A, int m, int slot) {
+  return &A.macc[(size_t)m * MACC_STRIDE + slot];
+}
 
 __device__ __forceinline__ d3 ld(const double* __restrict__ a, int n, int v) {
   return mk3(a[v], a[(size_t)n + v], a[2 * (size_t)n + v]);
@@ -70,10 +72,25 @@ __device__ __forceinline__ d3 axpy3(d3 x, double t, d3 p) {
   return mk3(xadd(x.x, xmul(t, p.x)), xadd(x.y, xmul(t, p.y)), xadd(x.z, xmul(t, p.z)));
 }
 
+// filtered class of a pair (Sec. 3.2 tables built at scene creation)
+__device__ __forceinline__ bool is_filtered(const CcdArgs& A, const MemberParams& M, uint64_t key, uint32_t ki,
+                                            uint32_t kj) {
+  if (M.filter_off) return false;
+  if (A.kind == CB_ROD) return A.comp[A.ev0[ki]] == A.comp[A.ev0[kj]] && (int)kj <= A.win[ki];
+  if (A.nf <= 0) return false;
+  int64_t lo = 0, hi = A.nf;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (A.frest[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < A.nf && A.frest[lo] == key;
+}
+
 // Everything additive CCD needs before its first step.
 struct AccdStart {
   bool ee;
-  int cls;
+  int cls, mem;
   double off, lp, g0;
   d3 Y0, Y1, Y2, Y3, Q0, Q1, Q2, Q3;
 };
@@ -96,27 +113,16 @@ __device__ __forceinline__ AccdStart accd_start(const CcdArgs& A, int64_t q) {
     v[3] = A.ev1[kj];
     S.ee = true;
   }
-  bool filt = false;
-  if (!A.filter_off) {
-    if (A.kind == CB_ROD) {
-      filt = A.comp[A.ev0[ki]] == A.comp[A.ev0[kj]] && (int)kj <= A.win[ki];
-    } else if (A.nf > 0) {
-      int64_t lo = 0, hi = A.nf;
-      while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (A.frest[mid] < key) lo = mid + 1;
-        else hi = mid;
-      }
-      filt = lo < A.nf && A.frest[lo] == key;
-    }
-  }
+  S.mem = A.vsc[v[0]];
+  const MemberParams& M = A.mp[S.mem];
+  const bool filt = is_filtered(A, M, key, ki, kj);
   const d3 X0 = ld(A.x, A.n, v[0]), X1 = ld(A.x, A.n, v[1]), X2 = ld(A.x, A.n, v[2]), X3 = ld(A.x, A.n, v[3]);
   const d3 P0 = ld(A.p, A.n, v[0]), P1 = ld(A.p, A.n, v[1]), P2 = ld(A.p, A.n, v[2]), P3 = ld(A.p, A.n, v[3]);
   double d;
   cbg::stencil_distance(S.ee, X0, X1, X2, X3, d);
   S.cls = filt ? 1 : 0;
-  if (!filt && A.core_temp && !A.single && d <= A.xi) S.cls = 2;
-  S.off = (S.cls == 0 && !A.single) ? A.xi : 0.0;
+  if (!filt && M.core_temp && !M.single && d <= M.xi) S.cls = 2;
+  S.off = (S.cls == 0 && !M.single) ? M.xi : 0.0;
   const d3 pb = mk3(xmul(xadd(xadd(xadd(P0.x, P1.x), P2.x), P3.x), 0.25),
                     xmul(xadd(xadd(xadd(P0.y, P1.y), P2.y), P3.y), 0.25),
                     xmul(xadd(xadd(xadd(P0.z, P1.z), P2.z), P3.z), 0.25));
@@ -141,16 +147,22 @@ __device__ __forceinline__ cbb::f3 ldf(const float* __restrict__ a, int n, int v
   return cbb::f3{a[v], a[(size_t)n + v], a[2 * (size_t)n + v]};
 }
 
-// Minimum of non-negative doubles over the warp (compared as bit patterns),
-// one atomicMin per warp; 2.0 marks "no value".
-__device__ __forceinline__ void warp_min_atomic(double v, unsigned long long* __restrict__ dst) {
+// Minimum of non-negative doubles per member (compared as bit patterns): one
+// atomicMin per warp when the warp holds one member, per lane otherwise;
+// 2.0 marks "no value".
+__device__ __forceinline__ void member_min_atomic(const CcdArgs& A, double v, int mem, int slot) {
   unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int m0 = __shfl_sync(0xffffffffu, mem, 0);
+  if (__all_sync(0xffffffffu, mem == m0 || mem < 0)) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long u = __shfl_xor_sync(0xffffffffu, b, o);
-    b = u < b ? u : b;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long u = __shfl_xor_sync(0xffffffffu, b, o);
+      b = u < b ? u : b;
+    }
+    if ((threadIdx.x & 31) == 0 && m0 >= 0 && b < 0x4000000000000000ull) atomicMin(macc_of(A, m0, slot), b);
+  } else if (mem >= 0 && b < 0x4000000000000000ull) {
+    atomicMin(macc_of(A, mem, slot), b);
   }
-  if ((threadIdx.x & 31) == 0 && b < 0x4000000000000000ull) atomicMin(dst, b);
 }
 
 __device__ __forceinline__ void warp_append(bool flag, uint32_t value, uint32_t* __restrict__ list,
@@ -174,6 +186,7 @@ __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restric
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool need = false;
   double m_exact = 2.0, m_lb = 2.0;  // this lane's contributions to the two minima
+  int mem = -1;
   if (q < A.np) {
     const uint64_t key = A.keys[q];
     const uint32_t ty = cb_key_type(key), ki = cb_key_i(key), kj = cb_key_j(key);
@@ -192,26 +205,17 @@ __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restric
       v[3] = A.ev1[kj];
       ee = true;
     }
-    bool filt = false;
-    if (!A.filter_off) {
-      if (A.kind == CB_ROD) {
-        filt = A.comp[A.ev0[ki]] == A.comp[A.ev0[kj]] && (int)kj <= A.win[ki];
-      } else if (A.nf > 0) {
-        int64_t lo = 0, hi = A.nf;
-        while (lo < hi) {
-          int64_t mid = (lo + hi) >> 1;
-          if (A.frest[mid] < key) lo = mid + 1;
-          else hi = mid;
-        }
-        filt = lo < A.nf && A.frest[lo] == key;
-      }
-    }
+    mem = A.vsc[v[0]];
+    const MemberParams& M = A.mp[mem];
+    const bool filt = is_filtered(A, M, key, ki, kj);
     need = true;
+    const double Xd = A.cx[4 * mem + 3];
     const float lb = cbb::lower_bound(ee, ldf(A.xf, A.n, v[0]), ldf(A.xf, A.n, v[1]), ldf(A.xf, A.n, v[2]),
-                                      ldf(A.xf, A.n, v[3]), A.X);
-    if (filt || (double)lb >= A.thrC) {
+                                      ldf(A.xf, A.n, v[3]), (float)Xd);
+    const double thrC = M.xi * (1.0 + 1e-9) + 1e-9;   // surely not class C above this
+    if (filt || (double)lb >= thrC) {
       const int cls = filt ? 1 : 0;
-      const double off = (cls == 0 && !A.single) ? A.xi : 0.0;
+      const double off = (cls == 0 && !M.single) ? M.xi : 0.0;
       const cbb::f3 p0 = ldf(A.pf, A.n, v[0]), p1 = ldf(A.pf, A.n, v[1]), p2 = ldf(A.pf, A.n, v[2]),
                     p3 = ldf(A.pf, A.n, v[3]);
       const cbb::f3 pm = cbb::fscale3(cbb::fadd3(cbb::fadd3(p0, p1), cbb::fadd3(p2, p3)), 0.25f);
@@ -223,7 +227,7 @@ __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restric
       const float Pm = fmaxf(fmaxf(cbb::fmaxabs3(p0), cbb::fmaxabs3(p1)), fmaxf(cbb::fmaxabs3(p2), cbb::fmaxabs3(p3)));
       const float u = 5.9604645e-8f;
       const double lp_ub = (double)lp32 * (1.0 + 64.0 * u) + 64.0 * u * (double)Pm;
-      const double g_lb = (double)lb - off - 1e-12 * (1.0 + (double)A.X);
+      const double g_lb = (double)lb - off - 1e-12 * (1.0 + Xd);
       if (lp32 > 1e-30f && g_lb > 0.0) {
         const double tl_lb = (1.0 - ACCD_S) * g_lb / lp_ub * (1.0 - 1e-9);
         const bool exact = tl_lb > 1.0 + 1e-9;
@@ -237,8 +241,8 @@ __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restric
       }
     }
   }
-  warp_min_atomic(m_exact, A.alpha_bits);
-  warp_min_atomic(m_lb, A.lb_bits);
+  member_min_atomic(A, m_exact, mem, MACC_ALPHA);
+  member_min_atomic(A, m_lb, mem, MACC_LB);
   warp_append(need, (uint32_t)q, list, nlist);
 }
 
@@ -247,41 +251,55 @@ __global__ void __launch_bounds__(128) k_ccd_bound(CcdArgs A, double* __restrict
                                                    const uint32_t* __restrict__ list,
                                                    const unsigned int* __restrict__ nlist) {
   const unsigned m = *nlist;
-  double m_exact = 2.0, m_lb = 2.0;
-  for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < m; w += gridDim.x * blockDim.x) {
-    const int64_t q = list[w];
-    const AccdStart S = accd_start(A, q);
-    double t;
-    bool exact = true;
-    if (S.lp == 0.0) {
-      t = 1.0;
-    } else if (S.g0 <= 0.0) {
-      t = 0.0;
-      atomicOr(A.status, (unsigned long long)CB_DEV_PENETRATION);
-    } else {
-      const double tl = xdiv(xmul(xsub(1.0, ACCD_S), S.g0), S.lp);
-      if (tl > 1.0) {
-        t = 1.0;  // the first step already passes t_c = 1: no contact within the step
+  // uniform trip count per block so that every lane reaches the warp minima
+  for (unsigned w0 = blockIdx.x * blockDim.x; w0 < m; w0 += gridDim.x * blockDim.x) {
+    const unsigned w = w0 + threadIdx.x;
+    double m_exact = 2.0, m_lb = 2.0;
+    int mem = -1;
+    if (w < m) {
+      const int64_t q = list[w];
+      const AccdStart S = accd_start(A, q);
+      mem = S.mem;
+      double t;
+      bool exact = true;
+      if (S.lp == 0.0) {
+        t = 1.0;
+      } else if (S.g0 <= 0.0) {
+        t = 0.0;
+        atomicOr(A.status, (unsigned long long)CB_DEV_PENETRATION);
+        atomicOr(macc_of(A, mem, MACC_STATUS), (unsigned long long)CB_DEV_PENETRATION);
       } else {
-        t = tl;
-        exact = false;
+        const double tl = xdiv(xmul(xsub(1.0, ACCD_S), S.g0), S.lp);
+        if (tl > 1.0) {
+          t = 1.0;  // the first step already passes t_c = 1: no contact within the step
+        } else {
+          t = tl;
+          exact = false;
+        }
       }
+      A.t_out[q] = t;
+      lb_out[q] = exact ? 2.0 : t;  // 2: resolved (never selected again)
+      A.cls_out[q] = (uint8_t)S.cls | (exact ? EXACT : 0);
+      if (exact) m_exact = t;
+      else m_lb = t;
     }
-    A.t_out[q] = t;
-    lb_out[q] = exact ? 2.0 : t;  // 2: resolved (never selected again)
-    A.cls_out[q] = (uint8_t)S.cls | (exact ? EXACT : 0);
-    if (exact) m_exact = fmin(m_exact, t);
-    else m_lb = fmin(m_lb, t);
+    member_min_atomic(A, m_exact, mem, MACC_ALPHA);
+    member_min_atomic(A, m_lb, mem, MACC_LB);
   }
-  warp_min_atomic(m_exact, A.alpha_bits);
-  warp_min_atomic(m_lb, A.lb_bits);
 }
 
-// select unresolved pairs with lo < lb <= hi
-__global__ void k_ccd_select(int64_t np, const double* __restrict__ lb, double lo, double hi,
-                             uint32_t* __restrict__ flag) {
+// select unresolved pairs with lo < lb <= hi of their member
+__global__ void k_ccd_select(int64_t np, const uint64_t* __restrict__ keys, const int32_t* __restrict__ ev0,
+                             const int32_t* __restrict__ vsc, const double* __restrict__ lb,
+                             const unsigned long long* __restrict__ macc, uint32_t* __restrict__ flag) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < np) flag[q] = (lb[q] > lo && lb[q] <= hi) ? 1u : 0u;
+  if (q >= np) return;
+  const uint64_t key = keys[q];
+  const int v0 = cb_key_type(key) == CB_KEY_PT ? (int)cb_key_i(key) : ev0[cb_key_i(key)];
+  const int mem = vsc[v0];
+  const double lo = __longlong_as_double(macc[(size_t)mem * MACC_STRIDE + MACC_LO]);
+  const double hi = __longlong_as_double(macc[(size_t)mem * MACC_STRIDE + MACC_HI]);
+  flag[q] = (lb[q] > lo && lb[q] <= hi) ? 1u : 0u;
 }
 
 __global__ void k_list(int64_t np, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
@@ -298,10 +316,13 @@ __global__ void __launch_bounds__(128) k_ccd_exact(CcdArgs A, int64_t m, const u
   AccdStart S = accd_start(A, q);
   if (S.lp == 0.0 || S.g0 <= 0.0) {  // only reachable through an FP32 bound below 1
     const double t0 = S.lp == 0.0 ? 1.0 : 0.0;
-    if (S.lp != 0.0) atomicOr(A.status, (unsigned long long)CB_DEV_PENETRATION);
+    if (S.lp != 0.0) {
+      atomicOr(A.status, (unsigned long long)CB_DEV_PENETRATION);
+      atomicOr(macc_of(A, S.mem, MACC_STATUS), (unsigned long long)CB_DEV_PENETRATION);
+    }
     A.t_out[q] = t0;
     A.cls_out[q] = (uint8_t)S.cls | EXACT;
-    atomicMin(A.alpha_bits, (unsigned long long)__double_as_longlong(t0));
+    atomicMin(macc_of(A, S.mem, MACC_ALPHA), (unsigned long long)__double_as_longlong(t0));
     return;
   }
   const double g = xmul(ACCD_S, S.g0);
@@ -330,23 +351,31 @@ __global__ void __launch_bounds__(128) k_ccd_exact(CcdArgs A, int64_t m, const u
   if (capped) atomicOr(A.status, (unsigned long long)CB_DEV_ITER_LIMIT);
   A.t_out[q] = t;
   A.cls_out[q] = (uint8_t)S.cls | EXACT;
-  atomicMin(A.alpha_bits, (unsigned long long)__double_as_longlong(t));
+  atomicMin(macc_of(A, S.mem, MACC_ALPHA), (unsigned long long)__double_as_longlong(t));
   atomicMax(A.max_iters, (unsigned long long)(it + 1));
 }
 
-__global__ void k_alpha_final(const unsigned long long* bits, double* out) { *out = __longlong_as_double(*bits); }
+__global__ void k_alpha_final(int count, const unsigned long long* __restrict__ macc, double* __restrict__ out) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < count) out[m] = __longlong_as_double(macc[(size_t)m * MACC_STRIDE + MACC_ALPHA]);
+}
 __global__ void k_set(unsigned long long* p, unsigned long long v) { *p = v; }
+__global__ void k_macc_set(int count, unsigned long long* __restrict__ macc, int slot, unsigned long long v) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < count) macc[(size_t)m * MACC_STRIDE + slot] = v;
+}
 
 }  // namespace
 
 cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, cudaStream_t st) {
-  CB_TRY(broad_phase(s, s->bwc, x, p, 0.5 * s->xi, s->ccd_keys, &s->n_ccd, st));
+  CB_TRY(broad_phase(s, s->bwc, x, p, true, s->ccd_keys, &s->n_ccd, st));
   uint64_t* sc = scalars(s);
-  unsigned long long* ab = (unsigned long long*)(sc + SC_ALPHA_BITS);
-  unsigned long long* lbm = (unsigned long long*)(sc + SC_COUNT0);
+  const int M = s->count;
+  unsigned long long* macc = bp<unsigned long long>(s->macc);
   unsigned long long* mi = (unsigned long long*)(sc + SC_ITERS);
-  k_set<<<1, 1, 0, cb_count(st)>>>(ab, 0x3ff0000000000000ull);   // 1.0
-  k_set<<<1, 1, 0, cb_count(st)>>>(lbm, 0x4000000000000000ull);  // 2.0: nothing unresolved
+  k_macc_set<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, MACC_ALPHA, 0x3ff0000000000000ull);  // 1.0
+  k_macc_set<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, MACC_LB, 0x4000000000000000ull);     // 2.0
+  k_macc_set<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, MACC_STATUS, 0ull);
   k_set<<<1, 1, 0, cb_count(st)>>>(mi, 0ull);
   const int64_t np = s->n_ccd;
   if (np > 0) {
@@ -370,24 +399,20 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     A.T = s->T;
     A.n = s->n;
     A.kind = s->kind;
-    A.filter_off = s->filter == CB_FILTER_OFF;
-    A.single = s->filter == CB_FILTER_SINGLE;
-    A.core_temp = s->core_temp;
-    A.xi = s->xi;
+    A.vsc = bp<int32_t>(s->vsc);
+    A.mp = bp<MemberParams>(s->mp);
+    A.cx = bp<double>(s->bwc.cx);
     A.x = x;
     A.p = p;
     A.t_out = bp<double>(s->ccd_t);
     A.cls_out = bp<uint8_t>(s->ccd_cls);
-    A.alpha_bits = ab;
-    A.lb_bits = lbm;
+    A.macc = macc;
     A.status = (unsigned long long*)(sc + SC_STATUS);
     A.max_iters = mi;
-    CB_TRY(to_f32(s, x, s->bwc.ctr, s->xf, st));
+    CB_TRY(to_f32(s, x, bp<double>(s->bwc.cx), s->xf, st));
     CB_TRY(to_f32(s, p, nullptr, s->pf, st));
     A.xf = bp<float>(s->xf);
     A.pf = bp<float>(s->pf);
-    A.X = (float)s->bwc.X;
-    A.thrC = s->xi * (1.0 + 1e-9) + 1e-9;
     CB_TRY(buf_ensure(s->dlist, sizeof(uint32_t) * (size_t)np, st));
     unsigned int* nl = (unsigned int*)(sc + SC_NLIST);
     k_set<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_NLIST), 0ull);
@@ -395,39 +420,80 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     k_ccd_bound<<<std::min<int64_t>(cb_grid(np, 128), 152 * 16), 128, 0, cb_count(st)>>>(
         A, bp<double>(s->ccd_lb), bp<uint32_t>(s->dlist), nl);
     CB_CUDA(cudaGetLastError());
-    uint64_t h[2];
-    CB_TRY(read_scalars(s, SC_COUNT0, 1, &h[0], st));
-    CB_TRY(read_scalars(s, SC_ALPHA_BITS, 1, &h[1], st));
-    double L, m;
-    memcpy(&L, &h[0], 8);
-    memcpy(&m, &h[1], 8);
-    // bands (lo, hi] of lower bounds, grown until the exact minimum found so
-    // far is not above the band's upper end (L > 1: every pair resolved)
-    double lo = -1.0, hi = std::min(1.0, 2.0 * L);
-    while (L <= 1.0 && m > L) {
-      k_ccd_select<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(np, bp<double>(s->ccd_lb), lo, hi,
+    // Per member: bands (lo, hi] of lower bounds.  First (-1, min(1, 2L)], L the
+    // smallest bound; then (hi, m] with m the exact minimum found so far, after
+    // which every pair left has t_p >= lb_p > m.  Members whose minimum is
+    // already below every remaining bound are done.
+    std::vector<unsigned long long> hm((size_t)M * MACC_STRIDE);
+    auto read_macc = [&]() -> cb_status {
+      CB_CUDA(cudaMemcpyAsync(s->hstage_host, macc, sizeof(unsigned long long) * MACC_STRIDE * M,
+                              cudaMemcpyDeviceToHost, st));
+      CB_CUDA(cudaStreamSynchronize(st));
+      memcpy(hm.data(), s->hstage_host, sizeof(unsigned long long) * MACC_STRIDE * M);
+      return CB_OK;
+    };
+    auto dbl = [](unsigned long long b) {
+      double d;
+      memcpy(&d, &b, 8);
+      return d;
+    };
+    CB_TRY(read_macc());
+    std::vector<double> lo(M, -1.0), hi(M, 3.0);
+    std::vector<char> done(M, 0);
+    bool any = false;
+    for (int m = 0; m < M; ++m) {
+      const double L = dbl(hm[(size_t)m * MACC_STRIDE + MACC_LB]);
+      const double mm = dbl(hm[(size_t)m * MACC_STRIDE + MACC_ALPHA]);
+      if (L > 1.0 || mm <= L) {
+        done[m] = 1;
+        lo[m] = 3.0;
+        hi[m] = 3.0;
+      } else {
+        hi[m] = std::min(1.0, 2.0 * L);
+        any = true;
+      }
+    }
+    while (any) {
+      // upload the band limits (hm holds the device values read just before,
+      // and no kernel runs in between)
+      for (int m = 0; m < M; ++m) {
+        memcpy(&hm[(size_t)m * MACC_STRIDE + MACC_LO], &lo[m], 8);
+        memcpy(&hm[(size_t)m * MACC_STRIDE + MACC_HI], &hi[m], 8);
+      }
+      memcpy(s->hstage_host, hm.data(), sizeof(unsigned long long) * MACC_STRIDE * M);
+      CB_CUDA(cudaMemcpyAsync(macc, s->hstage_host, sizeof(unsigned long long) * MACC_STRIDE * M,
+                              cudaMemcpyHostToDevice, st));
+      k_ccd_select<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(np, bp<uint64_t>(s->ccd_keys), bp<int32_t>(s->ev0),
+                                                                  bp<int32_t>(s->vsc), bp<double>(s->ccd_lb), macc,
                                                                   bp<uint32_t>(s->ccd_flag));
       uint32_t* tot = (uint32_t*)(sc + SC_COUNT1);
       cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(s->ccd_flag), bp<uint32_t>(s->ccd_pos), np,
                                               bp<uint32_t>(s->scan_tmp), tot, st);
       k_list<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(np, bp<uint32_t>(s->ccd_flag), bp<uint32_t>(s->ccd_pos),
                                                            bp<uint32_t>(s->ccd_list));
-      uint64_t hm;
-      CB_TRY(read_scalars(s, SC_COUNT1, 1, &hm, st));
-      const int64_t msel = (int64_t)(uint32_t)hm;
+      uint64_t hmsel;
+      CB_TRY(read_scalars(s, SC_COUNT1, 1, &hmsel, st));
+      const int64_t msel = (int64_t)(uint32_t)hmsel;
       if (msel > 0)
         k_ccd_exact<<<cb_grid(msel, 128), 128, 0, cb_count(st)>>>(A, msel, bp<uint32_t>(s->ccd_list));
       CB_CUDA(cudaGetLastError());
-      CB_TRY(read_scalars(s, SC_ALPHA_BITS, 1, &h[1], st));
-      memcpy(&m, &h[1], 8);
-      if (m <= hi || hi >= 1.0) break;  // every pair left has t_p >= lb_p > hi >= m
-      // only pairs with lb_p <= m can still lower the minimum: one more band
-      // (hi, m] makes it exact
-      lo = hi;
-      hi = std::min(1.0, m);
+      CB_TRY(read_macc());
+      any = false;
+      for (int m = 0; m < M; ++m) {
+        if (done[m]) continue;
+        const double mm = dbl(hm[(size_t)m * MACC_STRIDE + MACC_ALPHA]);
+        if (mm <= hi[m] || hi[m] >= 1.0) {
+          done[m] = 1;  // every pair left has t_p >= lb_p > hi >= m
+          lo[m] = hi[m] = 3.0;
+        } else {
+          lo[m] = hi[m];
+          hi[m] = std::min(1.0, mm);
+          any = true;
+        }
+      }
     }
   }
-  if (alpha) k_alpha_final<<<1, 1, 0, cb_count(st)>>>(ab, alpha);
+  if (alpha) k_alpha_final<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, alpha);
   CB_CUDA(cudaGetLastError());
   return CB_OK;
 }

@@ -121,14 +121,16 @@ __global__ void k_rest_filter(int64_t nc, const uint64_t* __restrict__ keys, con
 }
 
 __global__ void k_filter_rod(int64_t nc, const uint64_t* __restrict__ cand, const int32_t* __restrict__ ev0,
-                             const int32_t* __restrict__ comp, const int32_t* __restrict__ win, int off,
+                             const int32_t* __restrict__ comp, const int32_t* __restrict__ win,
+                             const int32_t* __restrict__ vsc, const MemberParams* __restrict__ mp,
                              uint8_t* __restrict__ klass, unsigned long long* __restrict__ nfilt) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t f = 0;
   if (c < nc) {
     const uint64_t key = cand[c];
     const int k = (int)cb_key_i(key), l = (int)cb_key_j(key);
-    f = (!off && comp[ev0[k]] == comp[ev0[l]] && l <= win[k]) ? 1u : 0u;
+    const int v0 = ev0[k];
+    f = (!mp[vsc[v0]].filter_off && comp[v0] == comp[ev0[l]] && l <= win[k]) ? 1u : 0u;
     klass[c] = (uint8_t)f;
   }
   uint32_t b = __ballot_sync(0xffffffffu, f);
@@ -136,13 +138,15 @@ __global__ void k_filter_rod(int64_t nc, const uint64_t* __restrict__ cand, cons
 }
 
 __global__ void k_filter_shell(int64_t nc, const uint64_t* __restrict__ cand, const uint64_t* __restrict__ frest,
-                               int64_t nf, int off, uint8_t* __restrict__ klass,
+                               int64_t nf, const int32_t* __restrict__ ev0, const int32_t* __restrict__ vsc,
+                               const MemberParams* __restrict__ mp, uint8_t* __restrict__ klass,
                                unsigned long long* __restrict__ nfilt) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t f = 0;
   if (c < nc) {
     const uint64_t key = cand[c];
-    if (!off && nf > 0) {
+    const int v0 = cb_key_type(key) == CB_KEY_PT ? (int)cb_key_i(key) : ev0[cb_key_i(key)];
+    if (!mp[vsc[v0]].filter_off && nf > 0) {
       int64_t lo = 0, hi = nf;
       while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
@@ -163,6 +167,18 @@ struct PassParams {
   double xi, dhat, a, dbar_min, kappa;
   int single, core_temp;
 };
+
+__device__ __forceinline__ PassParams member_pass(const MemberParams& m) {
+  PassParams P;
+  P.xi = m.xi;
+  P.dhat = m.dhat;
+  P.a = m.a;
+  P.dbar_min = m.dbar_min;
+  P.kappa = m.kappa;
+  P.single = m.single;
+  P.core_temp = m.core_temp;
+  return P;
+}
 
 // pair parameters: offset xi_p and width dhat_p of a class (0 U, 1 F, 2 C)
 __device__ __forceinline__ void pair_params(const PassParams& P, int k, double& xi_p, double& dh_p) {
@@ -198,7 +214,8 @@ __device__ __forceinline__ void warp_append(bool flag, uint32_t value, uint32_t*
 __global__ void k_distance_screen(int64_t nc, const uint64_t* __restrict__ cand,
                                   const uint8_t* __restrict__ klass_in, const int32_t* __restrict__ ev0,
                                   const int32_t* __restrict__ ev1, const int32_t* __restrict__ tv, int T,
-                                  const float* __restrict__ xf, float X, double thrU, double thrF, int n,
+                                  const float* __restrict__ xf, const double* __restrict__ cx,
+                                  const int32_t* __restrict__ vsc, const MemberParams* __restrict__ mp, int n,
                                   double* __restrict__ dout, int8_t* __restrict__ tout, uint8_t* __restrict__ cls,
                                   uint32_t* __restrict__ flag, uint32_t* __restrict__ list,
                                   unsigned int* __restrict__ nlist) {
@@ -207,6 +224,13 @@ __global__ void k_distance_screen(int64_t nc, const uint64_t* __restrict__ cand,
   if (c < nc) {
     Stencil s = stencil_of(cand[c], ev0, ev1, tv, T);
     const int k = klass_in[c];
+    const int mem = vsc[s.v[0]];
+    const MemberParams& M = mp[mem];
+    // thresholds beyond which a pair is surely inactive and not class C (the
+    // 1e-9 margins cover the rounding of the FP64 decision)
+    const double thrU = M.a * (1.0 + 1e-9) + 1e-9;
+    const double thrF = M.dbar_min * (1.0 + 1e-9) + 1e-9;
+    const float X = (float)cx[4 * mem + 3];
     const float lb = cbb::lower_bound(
         s.ee, cbb::f3{xf[s.v[0]], xf[(size_t)n + s.v[0]], xf[2 * (size_t)n + s.v[0]]},
         cbb::f3{xf[s.v[1]], xf[(size_t)n + s.v[1]], xf[2 * (size_t)n + s.v[1]]},
@@ -229,9 +253,11 @@ __global__ void k_distance_exact(const uint32_t* __restrict__ list, const unsign
                                  const uint64_t* __restrict__ cand, const uint8_t* __restrict__ klass_in,
                                  const int32_t* __restrict__ ev0, const int32_t* __restrict__ ev1,
                                  const int32_t* __restrict__ tv, int T, const double* __restrict__ x, int n,
-                                 PassParams P, double* __restrict__ dout, int8_t* __restrict__ tout,
+                                 const int32_t* __restrict__ vsc, const MemberParams* __restrict__ mp,
+                                 double* __restrict__ dout, int8_t* __restrict__ tout,
                                  uint8_t* __restrict__ cls, uint32_t* __restrict__ flag,
-                                 unsigned long long* __restrict__ status, unsigned long long* __restrict__ ncore) {
+                                 unsigned long long* __restrict__ status, unsigned long long* __restrict__ ncore,
+                                 unsigned long long* __restrict__ macc) {
   const unsigned m = *nlist;
   for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w - threadIdx.x < m; w += gridDim.x * blockDim.x) {
     uint32_t is_core = 0;
@@ -239,6 +265,8 @@ __global__ void k_distance_exact(const uint32_t* __restrict__ list, const unsign
       const uint32_t c = list[w];
       Stencil s = stencil_of(cand[c], ev0, ev1, tv, T);
       int k = klass_in[c];
+      const int mem = vsc[s.v[0]];
+      const PassParams P = member_pass(mp[mem]);
       double d;
       const int ty = cbg::stencil_distance(s.ee, load3(x, n, s.v[0]), load3(x, n, s.v[1]), load3(x, n, s.v[2]),
                                            load3(x, n, s.v[3]), d);
@@ -247,7 +275,10 @@ __global__ void k_distance_exact(const uint32_t* __restrict__ list, const unsign
       pair_params(P, k, xi_p, dh_p);
       const double y = xsub(d, xi_p);
       const uint32_t act = (y < dh_p) ? 1u : 0u;
-      if (act && y <= 0.0) atomicOr(status, (unsigned long long)CB_DEV_PENETRATION);
+      if (act && y <= 0.0) {
+        atomicOr(status, (unsigned long long)CB_DEV_PENETRATION);
+        atomicOr(&macc[(size_t)mem * MACC_STRIDE + MACC_STATUS], (unsigned long long)CB_DEV_PENETRATION);
+      }
       dout[c] = d;
       tout[c] = (int8_t)ty;
       cls[c] = (uint8_t)k;
@@ -259,12 +290,12 @@ __global__ void k_distance_exact(const uint32_t* __restrict__ list, const unsign
   }
 }
 
-__global__ void k_to_f32(int n, const double* __restrict__ v, double c0, double c1, double c2,
-                         float* __restrict__ out) {
+__global__ void k_to_f32(int n, const double* __restrict__ v, const double* __restrict__ cx,
+                         const int32_t* __restrict__ vsc, float* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 3 * (int64_t)n) return;
   const int k = (int)(i / n);
-  const double c = k == 0 ? c0 : (k == 1 ? c1 : c2);
+  const double c = cx ? cx[4 * vsc[i - (int64_t)k * n] + k] : 0.0;
   out[i] = (float)(v[i] - c);
 }
 
@@ -561,12 +592,13 @@ struct HessArgs {
   int T;
   const double* __restrict__ x;
   int n;
-  PassParams P;
+  const int32_t* __restrict__ vsc;
+  const MemberParams* __restrict__ mp;
+  unsigned long long* __restrict__ macc;
   const int32_t* __restrict__ row_ptr;
   const int32_t* __restrict__ col;
   double* __restrict__ val;
   double* __restrict__ grad;
-  double* __restrict__ energy;
   unsigned long long* __restrict__ status;
   // reduced matrices handed to the projection kernels: B packed upper
   // triangle, element-major ([e * cap + slot]); slot -> active pair index
@@ -602,6 +634,7 @@ __device__ __forceinline__ void add_block(const HessArgs& A, int r, int c, const
 __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double e_local = 0.0;
+  int mem = -1;
   int want = 0;  // 9 or 6: reduced dimension of the queued matrix
   double Bp[45];
   if (a < A.na) {
@@ -614,22 +647,24 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
     const int nz = kind + 1;
     d3 X[4];
     for (int i = 0; i < 4; ++i) X[i] = load3(A.x, A.n, s.v[i]);
-    d3 P[4];
-    for (int i = 0; i < 4; ++i) P[i] = mk3(X[i].x - X[0].x, X[i].y - X[0].y, X[i].z - X[0].z);
+    d3 Pl[4];
+    for (int i = 0; i < 4; ++i) Pl[i] = mk3(X[i].x - X[0].x, X[i].y - X[0].y, X[i].z - X[0].z);
     d3 z[3];
     for (int m = 0; m < 3; ++m) {
       double zx = 0, zy = 0, zz = 0;
       for (int i = 1; i < 4; ++i) {
         const double cm = (double)TI.C[m][i];
-        zx += cm * P[i].x;
-        zy += cm * P[i].y;
-        zz += cm * P[i].z;
+        zx += cm * Pl[i].x;
+        zy += cm * Pl[i].y;
+        zz += cm * Pl[i].z;
       }
       z[m] = mk3(zx, zy, zz);
     }
     const double d = A.cd[c];
+    mem = A.vsc[s.v[0]];
+    const PassParams P = member_pass(A.mp[mem]);
     double xi_p, dh_p;
-    pair_params(A.P, A.ccls[c], xi_p, dh_p);
+    pair_params(P, A.ccls[c], xi_p, dh_p);
     const double y = d - xi_p;
     double b, b1, b2;
     {
@@ -638,7 +673,7 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
       b1 = -2.0 * r * l - (r * r) / y;
       b2 = -2.0 * l - 4.0 * r / y + (r * r) / (y * y);
     }
-    const double kap = A.P.kappa;
+    const double kap = P.kappa;
     e_local = kap * b;
     double gs[9], Hs[81];
     s_derivs(kind, z, gs, Hs);
@@ -734,9 +769,16 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
       (which == 0 ? A.slot9 : A.slot6)[slot] = (uint32_t)a;
     }
   }
+  // energy per member: one atomic per warp when the warp holds one member
+  const int m0 = __shfl_sync(0xffffffffu, mem, 0);
+  if (__all_sync(0xffffffffu, mem == m0 || mem < 0)) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) e_local += __shfl_xor_sync(0xffffffffu, e_local, o);
-  if (lane == 0 && e_local != 0.0) atomicAdd(A.energy, e_local);
+    for (int o = 16; o > 0; o >>= 1) e_local += __shfl_xor_sync(0xffffffffu, e_local, o);
+    if (lane == 0 && e_local != 0.0 && m0 >= 0)
+      atomicAdd((double*)&A.macc[(size_t)m0 * MACC_STRIDE + MACC_E], e_local);
+  } else if (mem >= 0 && e_local != 0.0) {
+    atomicAdd((double*)&A.macc[(size_t)mem * MACC_STRIDE + MACC_E], e_local);
+  }
 }
 
 // Cyclic Jacobi with symmetric updates on a packed upper-triangular matrix
@@ -918,11 +960,17 @@ __global__ void __launch_bounds__(128) k_hess_proj(HessArgs A, int64_t m) {
     }
 }
 
-__global__ void k_energy_final(const double* __restrict__ acc, const unsigned long long* __restrict__ status,
-                               double* __restrict__ out) {
-  double e = *acc;
-  if (*status & CB_DEV_PENETRATION) e = __longlong_as_double(0x7ff0000000000000LL);
-  *out = e;
+__global__ void k_energy_final(int count, const unsigned long long* __restrict__ macc, double* __restrict__ out) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= count) return;
+  double e = __longlong_as_double(macc[(size_t)m * MACC_STRIDE + MACC_E]);
+  if (macc[(size_t)m * MACC_STRIDE + MACC_STATUS] & CB_DEV_PENETRATION) e = __longlong_as_double(0x7ff0000000000000LL);
+  out[m] = e;
+}
+
+__global__ void k_macc_reset(int count, unsigned long long* __restrict__ macc, int slot, unsigned long long v) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < count) macc[(size_t)m * MACC_STRIDE + slot] = v;
 }
 
 __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
@@ -954,7 +1002,7 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
     // rest broad phase at the full activation, then rest distances below a
     int64_t nr = 0;
     DevBuf rc;
-    CB_TRY(broad_phase(s, s->bw, bp<double>(s->rest), nullptr, 0.5 * s->a, rc, &nr, st));
+    CB_TRY(broad_phase(s, s->bw, bp<double>(s->rest), nullptr, false, rc, &nr, st));
     if (nr > 0) {
       DevBuf flag, pos, dbar;
       CB_TRY(buf_ensure(flag, sizeof(uint32_t) * (size_t)nr, st));
@@ -1002,22 +1050,22 @@ cb_status filter_apply(cb_scene* s, cudaStream_t st) {
   unsigned long long* nf = (unsigned long long*)(scalars(s) + SC_NFILT);
   k_set_u64<<<1, 1, 0, cb_count(st)>>>(nf, 0ull);
   if (nc == 0) return CB_OK;
-  const int off = (s->filter == CB_FILTER_OFF) ? 1 : 0;
   if (s->kind == CB_ROD)
-    k_filter_rod<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(nc, bp<uint64_t>(s->cand), bp<int32_t>(s->ev0),
-                                                     bp<int32_t>(s->comp), bp<int32_t>(s->win), off,
-                                                     bp<uint8_t>(s->klass), nf);
+    k_filter_rod<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(
+        nc, bp<uint64_t>(s->cand), bp<int32_t>(s->ev0), bp<int32_t>(s->comp), bp<int32_t>(s->win),
+        bp<int32_t>(s->vsc), bp<MemberParams>(s->mp), bp<uint8_t>(s->klass), nf);
   else
-    k_filter_shell<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(nc, bp<uint64_t>(s->cand), bp<uint64_t>(s->frest), s->n_frest,
-                                                       off, bp<uint8_t>(s->klass), nf);
+    k_filter_shell<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(
+        nc, bp<uint64_t>(s->cand), bp<uint64_t>(s->frest), s->n_frest, bp<int32_t>(s->ev0), bp<int32_t>(s->vsc),
+        bp<MemberParams>(s->mp), bp<uint8_t>(s->klass), nf);
   CB_CUDA(cudaGetLastError());
   return CB_OK;
 }
 
-cb_status to_f32(cb_scene* s, const double* v, const double* c3, DevBuf& out, cudaStream_t st) {
+cb_status to_f32(cb_scene* s, const double* v, const double* cx, DevBuf& out, cudaStream_t st) {
   CB_TRY(buf_ensure(out, sizeof(float) * 3 * (size_t)s->n, st));
-  k_to_f32<<<cb_grid(3 * (int64_t)s->n), CB_THREADS, 0, cb_count(st)>>>(
-      s->n, v, c3 ? c3[0] : 0.0, c3 ? c3[1] : 0.0, c3 ? c3[2] : 0.0, bp<float>(out));
+  k_to_f32<<<cb_grid(3 * (int64_t)s->n), CB_THREADS, 0, cb_count(st)>>>(s->n, v, cx, bp<int32_t>(s->vsc),
+                                                                       bp<float>(out));
   CB_CUDA(cudaGetLastError());
   return CB_OK;
 }
@@ -1028,32 +1076,21 @@ static int bits_for(int64_t v) {
   return b;
 }
 
-static PassParams pass_params(const cb_scene* s) {
-  PassParams P;
-  P.xi = s->xi;
-  P.dhat = s->dhat;
-  P.a = s->a;
-  P.dbar_min = std::isfinite(s->dbar_min) ? s->dbar_min : 0.0;
-  P.kappa = s->kappa;
-  P.single = (s->filter == CB_FILTER_SINGLE);
-  P.core_temp = s->core_temp;
-  return P;
-}
-
 cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad, cudaStream_t st) {
   const int64_t nc = s->n_cand;
   uint64_t* sc = scalars(s);
   unsigned long long* status = (unsigned long long*)(sc + SC_STATUS);
   unsigned long long* ncore = (unsigned long long*)(sc + SC_NCORE);
-  double* eacc = (double*)(sc + SC_ENERGY);
+  unsigned long long* macc = bp<unsigned long long>(s->macc);
+  const int M = s->count;
   k_set_u64<<<1, 1, 0, cb_count(st)>>>(ncore, 0ull);
-  k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)eacc, 0ull);
+  k_macc_reset<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, MACC_E, 0ull);
+  k_macc_reset<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, MACC_STATUS, 0ull);
   if (grad) CB_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * 3 * (size_t)s->n, st));
   s->n_active = 0;
   s->nnzb = 0;
   CB_TRY(buf_ensure(s->bsr_row, sizeof(int32_t) * ((size_t)s->n + 1), st));
   CB_CUDA(cudaMemsetAsync(s->bsr_row.p, 0, sizeof(int32_t) * ((size_t)s->n + 1), st));
-  const PassParams P = pass_params(s);
   if (nc > 0) {
     CB_TRY(buf_ensure(s->cd, sizeof(double) * (size_t)nc, st));
     CB_TRY(buf_ensure(s->ctype, (size_t)nc, st));
@@ -1061,22 +1098,20 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     CB_TRY(buf_ensure(s->cflag, sizeof(uint32_t) * (size_t)nc, st));
     CB_TRY(buf_ensure(s->cpos, sizeof(uint32_t) * ((size_t)nc + 1), st));
     CB_TRY(buf_ensure(s->scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(nc) + 8), st));
-    CB_TRY(to_f32(s, x, s->bw.ctr, s->xf, st));
-    // thresholds beyond which a pair is surely inactive and not class C (the
-    // 1e-9 margins cover the rounding of the FP64 decision)
-    const double thrU = s->a * (1.0 + 1e-9) + 1e-9;
-    const double thrF = P.dbar_min * (1.0 + 1e-9) + 1e-9;
+    CB_TRY(to_f32(s, x, bp<double>(s->bw.cx), s->xf, st));
     CB_TRY(buf_ensure(s->dlist, sizeof(uint32_t) * (size_t)nc, st));
     unsigned int* nl = (unsigned int*)(sc + SC_NLIST);
     k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_NLIST), 0ull);
     k_distance_screen<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(
         nc, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass), bp<int32_t>(s->ev0), bp<int32_t>(s->ev1),
-        bp<int32_t>(s->tv), s->T, bp<float>(s->xf), (float)s->bw.X, thrU, thrF, s->n, bp<double>(s->cd),
+        bp<int32_t>(s->tv), s->T, bp<float>(s->xf), bp<double>(s->bw.cx), bp<int32_t>(s->vsc),
+        bp<MemberParams>(s->mp), s->n, bp<double>(s->cd),
         bp<int8_t>(s->ctype), bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), bp<uint32_t>(s->dlist), nl);
     k_distance_exact<<<std::min<int64_t>(cb_grid(nc), 152 * 16), CB_THREADS, 0, cb_count(st)>>>(
         bp<uint32_t>(s->dlist), nl, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass), bp<int32_t>(s->ev0),
-        bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T, x, s->n, P, bp<double>(s->cd), bp<int8_t>(s->ctype),
-        bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), status, ncore);
+        bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T, x, s->n, bp<int32_t>(s->vsc), bp<MemberParams>(s->mp),
+        bp<double>(s->cd), bp<int8_t>(s->ctype), bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), status, ncore,
+        macc);
     uint32_t* tot = (uint32_t*)(sc + SC_COUNT1);
     cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(s->cflag), bp<uint32_t>(s->cpos), nc,
                                             bp<uint32_t>(s->scan_tmp), tot, st);
@@ -1137,12 +1172,13 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     A.T = s->T;
     A.x = x;
     A.n = s->n;
-    A.P = P;
+    A.vsc = bp<int32_t>(s->vsc);
+    A.mp = bp<MemberParams>(s->mp);
+    A.macc = macc;
     A.row_ptr = bp<int32_t>(s->bsr_row);
     A.col = bp<int32_t>(s->bsr_col);
     A.val = bp<double>(s->bsr_val);
     A.grad = grad;
-    A.energy = eacc;
     A.status = status;
     CB_TRY(buf_ensure(s->hB9, sizeof(double) * 45 * (size_t)na, st));
     CB_TRY(buf_ensure(s->hB6, sizeof(double) * 21 * (size_t)na, st));
@@ -1164,26 +1200,18 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     const int64_t m9 = (int64_t)(uint32_t)hq[0], m6 = (int64_t)(uint32_t)hq[1];
     if (m9 > 0) {
       const int smem = ProjSmem<9>::PER_THREAD * 128;
-      static bool attr9 = false;
-      if (!attr9) {
-        CB_CUDA(cudaFuncSetAttribute(k_hess_proj<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr9 = true;
-      }
+      CB_CUDA(cudaFuncSetAttribute(k_hess_proj<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
       k_hess_proj<9><<<cb_grid(m9, 128), 128, smem, cb_count(st)>>>(A, m9);
     }
     if (m6 > 0) {
       const int smem = ProjSmem<6>::PER_THREAD * 128;
-      static bool attr6 = false;
-      if (!attr6) {
-        CB_CUDA(cudaFuncSetAttribute(k_hess_proj<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr6 = true;
-      }
+      CB_CUDA(cudaFuncSetAttribute(k_hess_proj<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
       k_hess_proj<6><<<cb_grid(m6, 128), 128, smem, cb_count(st)>>>(A, m6);
     }
     if (s->timing) cudaEventRecord(s->ev[11], st);
     CB_CUDA(cudaGetLastError());
   }
-  if (energy) k_energy_final<<<1, 1, 0, cb_count(st)>>>(eacc, status, energy);
+  if (energy) k_energy_final<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, energy);
   CB_CUDA(cudaGetLastError());
   return CB_OK;
 }

@@ -17,14 +17,30 @@ static inline T* bp(const DevBuf& b) {
   return (T*)b.p;
 }
 
+// Per-member parameters.  A plain scene has one member; a batch (several
+// scenes merged into one index space, cb_batch_create) has one per scene.
+struct MemberParams {
+  double xi, dhat, a, kappa;
+  double dbar_min;        // 0 when nothing is filtered
+  int32_t single, core_temp, filter_off, n_prims;
+};
+
+// Spatial-hash grid of one member.
+struct Grid {
+  float ox, oy, oz, inv;
+  int dx, dy, dz, pad;
+};
+
 // Workspace of one broad phase (static or swept) -- reused between calls.
 struct BroadWork {
   DevBuf box32;       // float4 lo, float4 hi per primitive
   DevBuf box64;       // double lo[3], hi[3] per primitive
-  DevBuf bounds;      // 8 x uint32 (ordered-float min/max)
+  DevBuf bounds;      // per member: 6 x uint32 ordered-float min/max, 2 pad, double extent sum
+  DevBuf grids;       // Grid per member
+  DevBuf cx;          // per member: double centre[3], X (max |coordinate - centre|)
   DevBuf cell_cnt;    // uint32 per primitive
   DevBuf cell_off;    // uint32 per primitive (+1)
-  DevBuf ekey[2];     // uint32 cell key per entry (ping-pong)
+  DevBuf ekey[2];     // uint64 (member << 30 | Morton cell) per entry (ping-pong)
   DevBuf eval[2];     // uint32 primitive per entry
   DevBuf run_flag;    // uint32 per entry
   DevBuf run_id;      // uint32 per entry
@@ -34,9 +50,8 @@ struct BroadWork {
   DevBuf ckey[2];     // uint64 compact candidate keys (ping-pong)
   DevBuf scan_tmp;
   DevBuf hist;
-  float cell = 0.f;   // cell size used last
-  double ctr[3] = {0, 0, 0};  // centre of the last boxes' bounds
-  double X = 0;                // max |coordinate - ctr| over the boxes
+  float cell = 0.f;   // cell size of member 0 used last
+  std::vector<double> hcx;     // host copy of cx
 };
 
 struct cb_scene {
@@ -44,11 +59,21 @@ struct cb_scene {
   int n = 0, E = 0, T = 0, n_rods = 0;
   int n_prims = 0;     // broad-phase primitives
   int bits_i = 0, bits_j = 0;
-  double xi = 0, dhat = 0, a = 0, kappa = 1;
+  double xi = 0, dhat = 0, a = 0, kappa = 1;   // member 0 (plain scenes: the scene)
   int filter = CB_FILTER_DOUBLE;
   int core_temp = 1;
   double dbar_min = 0;  // +inf when nothing is filtered
   float cell_hint = 0.f;
+  // members (1 for a plain scene)
+  int count = 1;
+  std::vector<MemberParams> hmp;
+  DevBuf mp;            // MemberParams [count]
+  DevBuf vsc;           // int32 [n] member of each vertex
+  std::vector<int64_t> voff, eoff, toff;  // member offsets of vertices, edges, triangles (count+1)
+  int64_t n_frest_pt = 0;                 // shells: point-triangle keys at the head of frest
+  DevBuf macc;          // per member: double energy, u64 alpha bits, u64 lb bits, u64 status, double lo, hi
+  DevBuf hstage;        // device copy of per-member box inflation
+  void* hstage_host = nullptr;  // pinned staging (64 bytes per member + 256)
   cudaStream_t last_stream = nullptr;
   int device = 0;
 
@@ -128,6 +153,9 @@ enum {
 
 static inline uint64_t* scalars(cb_scene* s) { return (uint64_t*)s->dev_scalars.p; }
 
+// per-member accumulator slots (uint64 / double each) inside macc
+enum { MACC_E = 0, MACC_ALPHA = 1, MACC_LB = 2, MACC_STATUS = 3, MACC_LO = 4, MACC_HI = 5, MACC_STRIDE = 6 };
+
 // read n uint64 device scalars into host (sync on stream)
 cb_status read_scalars(cb_scene* s, int first, int count, uint64_t* out, cudaStream_t st);
 
@@ -135,7 +163,8 @@ cb_status read_scalars(cb_scene* s, int first, int count, uint64_t* out, cudaStr
 // Candidate pairs of x (p == nullptr) or of the sweep x -> x + p; boxes are
 // inflated by h.  Writes sorted canonical keys into *out (grown as needed) and
 // their count into *n_out.
-cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* p, double h, DevBuf& out,
+// Boxes are inflated per member by a/2 (static) or xi/2 (swept = true).
+cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* p, bool swept, DevBuf& out,
                       int64_t* n_out, cudaStream_t st);
 
 // narrow.cu
@@ -146,5 +175,5 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
 // ccd.cu
 cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, cudaStream_t st);
 
-// narrow.cu: FP32 copy of (v - c) (c may be null: no centring)
-cb_status to_f32(cb_scene* s, const double* v, const double* c3, DevBuf& out, cudaStream_t st);
+// narrow.cu: FP32 copy of (v - centre of the vertex's member) (cx null: no centring)
+cb_status to_f32(cb_scene* s, const double* v, const double* cx, DevBuf& out, cudaStream_t st);

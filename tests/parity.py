@@ -122,3 +122,51 @@ def compare(sc, g: dict, orc: O.PassResult, mode="double", check_ccd=True) -> di
         rep["alpha"] = g["alpha"]
         rep["alpha_oracle"] = orc.alpha
     return rep
+
+
+def run_gpu_batch(scenes, mode="double", xs=None, ps=None):
+    """One batched pass over several scenes (cb_batch_create); returns one
+    result dict per member in run_gpu's format (member-local numbering)."""
+    import torch
+    from paper_2510_10256_gb300.contact import ContactBatch, ContactScene
+    dev = torch.device("cuda:0")
+    members = [ContactScene.from_scene(sc, mode=mode) for sc in scenes]
+    dbar = [m.stats()["dbar_min"] for m in members]
+    b = ContactBatch(members)
+    for m in members:
+        m.close()
+    xs = xs or [sc.x for sc in scenes]
+    ps = ps or [sc.p for sc in scenes]
+    x = torch.from_numpy(np.ascontiguousarray(np.concatenate(xs, axis=1))).to(dev)
+    p = torch.from_numpy(np.ascontiguousarray(np.concatenate(ps, axis=1))).to(dev)
+    M = len(scenes)
+    energy = torch.zeros(M, dtype=torch.float64, device=dev)
+    grad = torch.zeros(3, b.n, dtype=torch.float64, device=dev)
+    alpha = torch.zeros(M, dtype=torch.float64, device=dev)
+    b.run_pass(x, p, energy, grad, alpha)
+    torch.cuda.synchronize()
+    C, F, CC, fr = b.pairs("candidate"), b.pairs("filtered"), b.pairs("core"), b.pairs("rest_filtered")
+    A, ccd = b.active(), b.ccd()
+    rp, col, val = b.bsr()
+    en, al, gr = energy.cpu().numpy(), alpha.cpu().numpy(), grad.cpu().numpy()
+    status = b.sync_status()
+    out = []
+    for m in range(M):
+        vo, vn = int(b.vert_offsets[m]), int(b.vert_offsets[m + 1])
+
+        def sel(keys):
+            return b.to_member_keys(keys[b.member_of_keys(keys) == m], m) if keys.size else keys
+
+        am = b.member_of_keys(A["keys"]) == m if A["keys"].size else np.zeros(0, bool)
+        cm = b.member_of_keys(ccd["keys"]) == m if ccd["keys"].size else np.zeros(0, bool)
+        lrp = rp[vo:vn + 1] - rp[vo]
+        out.append(dict(
+            C=sel(C), F=sel(F), CC=sel(CC), frest=sel(fr),
+            A=dict(keys=b.to_member_keys(A["keys"][am], m), d=A["d"][am], klass=A["klass"][am],
+                   dtype=A["dtype"][am]),
+            ccd=dict(keys=b.to_member_keys(ccd["keys"][cm], m), t=ccd["t"][cm], klass=ccd["klass"][cm]),
+            bsr=(lrp, col[rp[vo]:rp[vn]] - vo, val[rp[vo]:rp[vn]]),
+            energy=float(en[m]), grad=gr[:, vo:vn], alpha=float(al[m]),
+            stats=dict(dbar_min=dbar[m]), status=status))
+    b.close()
+    return out
