@@ -861,22 +861,21 @@ __global__ void __launch_bounds__(128) k_hess_proj(HessArgs A, int64_t m) {
   char* zbase = (char*)(smem + (NP + D * D) * S);
   float* A32 = (float*)zbase + tid;                 // [e * S] floats
   float* V32 = (float*)zbase + NP * S + tid;        // [e * S] floats
-  double* Ad = (double*)zbase + tid;                // [e * S] doubles (aliases A32/V32 later)
-  if (w >= m) return;
+  // Ad shares its bytes with A32 / V32, and a double element of one thread
+  // covers float words of other threads: Ad is written only after the
+  // barrier below, when every thread of the block is done with A32 / V32.
+  double* Ad = (double*)zbase + tid;                // [e * S] doubles
+  const bool act = w < m;                           // no early exit: all threads reach the barrier
   const double* Bg = D == 9 ? A.B9 : A.B6;
-  const uint32_t a = (D == 9 ? A.slot9 : A.slot6)[w];
+  const uint32_t a = act ? (D == 9 ? A.slot9 : A.slot6)[w] : 0u;
   double mx = 0.0;
-  for (int e = 0; e < NP; ++e) {
-    const double v = Bg[(size_t)e * A.cap + w];
-    Bs[e * S] = v;
-    mx = fmax(mx, fabs(v));
-  }
-  // eigenvalues -> diagonal of Ad, eigenvectors -> Vs
-  if (mx == 0.0) {
-    for (int e = 0; e < NP; ++e) Ad[e * S] = 0.0;
-    for (int i = 0; i < D; ++i)
-      for (int k = 0; k < D; ++k) Vs[(i * D + k) * S] = (i == k) ? 1.0 : 0.0;
-  } else {
+  if (act)
+    for (int e = 0; e < NP; ++e) {
+      const double v = Bg[(size_t)e * A.cap + w];
+      Bs[e * S] = v;
+      mx = fmax(mx, fabs(v));
+    }
+  if (act && mx != 0.0) {
     const double inv = 1.0 / mx;
     for (int e = 0; e < NP; ++e) A32[e * S] = (float)(Bs[e * S] * inv);
     for (int i = 0; i < D; ++i)
@@ -895,7 +894,16 @@ __global__ void __launch_bounds__(128) k_hess_proj(HessArgs A, int64_t m) {
       nn = rsqrt(nn);
       for (int i = 0; i < D; ++i) Vs[(i * D + k) * S] *= nn;
     }
-    // A = V^T B V, column by column (A32 / V32 are dead)
+  }
+  __syncthreads();
+  if (!act) return;
+  // eigenvalues -> diagonal of Ad, eigenvectors -> Vs
+  if (mx == 0.0) {
+    for (int e = 0; e < NP; ++e) Ad[e * S] = 0.0;
+    for (int i = 0; i < D; ++i)
+      for (int k = 0; k < D; ++k) Vs[(i * D + k) * S] = (i == k) ? 1.0 : 0.0;
+  } else {
+    // A = V^T B V, column by column
     for (int l = 0; l < D; ++l) {
       double t[D];
 #pragma unroll

@@ -59,3 +59,15 @@ def test_single_member_batch():
     sc = S.tiny_shell(4)
     (g,) = run_gpu_batch([sc])
     compare(sc, g, O.contact_pass(sc))
+
+
+def test_repeated_batches_match_the_oracle():
+    """Several consecutive batched passes, each against the oracle.  Guards
+    the projection kernel's shared-memory phases: the FP64 matrices share
+    bytes with other threads' FP32 work arrays, so no thread may start its
+    FP64 stage before the whole block has finished the FP32 one."""
+    scenes = [S.tiny_shell(7), S.pleated_sheet(nx=20), S.tiny_shell(8)]
+    orcs = [O.contact_pass(sc) for sc in scenes]
+    for _ in range(4):
+        for sc, g, o in zip(scenes, run_gpu_batch(scenes), orcs):
+            compare(sc, g, o)
