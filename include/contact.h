@@ -52,7 +52,8 @@ typedef enum {
   CB_ERR_PENETRATION = 4,  /* a pair is at or inside its barrier offset: energy = +inf */
   CB_ERR_DEGENERATE = 5,   /* zero reference distance between stencil primitives */
   CB_ERR_ITER_LIMIT = 6,   /* additive CCD hit its iteration cap: alpha is the last safe t */
-  CB_ERR_CUDA = 7          /* CUDA runtime error */
+  CB_ERR_CUDA = 7,         /* CUDA runtime error */
+  CB_ERR_TOO_LARGE = 8     /* input larger than a call's fixed maximum; nothing was run */
 } cb_status;
 
 #define CB_ROD 0
@@ -209,6 +210,39 @@ int64_t cb_kernel_launches(void);
 cb_status cb_measure_fma_tflops(int32_t fp64, int32_t blocks, int32_t iters, double* tflops);
 /* library version string */
 const char* cb_version(void);
+
+/* Step bound of an explicit stencil list that allocates no device memory.
+ * No counterpart in the paper: it is ccd_step's additive CCD (same s, inner
+ * factor, iteration cap and arithmetic) for callers that cannot allocate
+ * device memory while they run it -- a solver that has handed its whole
+ * device budget to its own pool, or a time-critical loop in which an
+ * allocation or a free could stall the device.  The only memory it uses is a
+ * fixed scratch array of the library, 8 MiB + 256 bytes per device, set aside
+ * when the library's code is loaded onto the device.
+ *   x_dev, p_dev  DEVICE [3][n_verts] FP64 positions and search direction.
+ *   stencils_dev  DEVICE [n_stencils][4] int32 vertex ids: point-triangle
+ *                 (p, t0, t1, t2) or edge-edge (a0, a1, b0, b1).
+ *   is_ee_dev     DEVICE [n_stencils] uint8: 1 edge-edge, 0 point-triangle.
+ *   offset_dev    DEVICE [n_stencils] FP64 offset the step keeps (>= 0).
+ *   alpha_dev     DEVICE 1 double: min(1, min_p t_p) (overwritten).
+ *   flags_dev     DEVICE 1 uint32 (overwritten): CB_DEV conditions 2
+ *                 (penetration: a stencil at or inside its offset, t_p = 0),
+ *                 4 (iteration limit) and CB_NOALLOC_BAD_STENCIL (a vertex id
+ *                 outside [0, n_verts) or a bad offset: that stencil skipped).
+ * The caller owns every buffer; the call is asynchronous on `stream`.
+ * n_stencils = 0 gives alpha = 1.  More than CB_NOALLOC_MAX_STENCILS stencils
+ * return CB_ERR_TOO_LARGE before any work; split the list and take the
+ * minimum.  The first call on each device looks up the scratch address and may
+ * make the CUDA runtime load the library's code onto that device: make it
+ * before any stream capture.  All calls on one device share the scratch:
+ * calls that overlap in time on one device (several streams or host threads)
+ * race and give wrong results.  Errors: CB_ERR_ARG, CB_ERR_TOO_LARGE,
+ * CB_ERR_CUDA. */
+#define CB_NOALLOC_MAX_STENCILS (1 << 20)
+#define CB_NOALLOC_BAD_STENCIL 8u
+cb_status ccd_step_noalloc(const double* x_dev, const double* p_dev, int32_t n_verts, const int32_t* stencils_dev,
+                           const uint8_t* is_ee_dev, const double* offset_dev, int64_t n_stencils,
+                           double* alpha_dev, uint32_t* flags_dev, void* stream);
 
 #ifdef __cplusplus
 }

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libcontact.so")
 _lib = None
 
 CB_OK, CB_ERR_ARG, CB_ERR_OOM, CB_ERR_CAPACITY, CB_ERR_PENETRATION, CB_ERR_DEGENERATE, \
-    CB_ERR_ITER_LIMIT, CB_ERR_CUDA = range(8)
+    CB_ERR_ITER_LIMIT, CB_ERR_CUDA, CB_ERR_TOO_LARGE = range(9)
 CB_ROD, CB_SHELL = 0, 1
 CB_FILTER_DOUBLE, CB_FILTER_SINGLE, CB_FILTER_OFF = 0, 1, 2
 CB_THICK_PAPER_LITERAL = 4
@@ -30,7 +30,7 @@ ABI_FUNCTIONS = ["cb_scene_create", "cb_scene_destroy", "contact_build", "contac
                  "ccd_step", "cb_get_pairs", "cb_get_active", "cb_get_ccd", "cb_get_bsr", "cb_bsr_device",
                  "cb_get_stats", "cb_sync_status", "cb_get_stage_ms", "cb_set_timing", "cb_status_str",
                  "cb_version", "cb_kernel_launches", "cb_measure_fma_tflops", "cb_batch_create",
-                 "cb_batch_offsets", "cb_member_count"]
+                 "cb_batch_offsets", "cb_member_count", "ccd_step_noalloc"]
 
 
 class ContactError(RuntimeError):
@@ -93,6 +93,7 @@ def lib():
         L.cb_sync_status.argtypes = [vp]
         L.cb_get_stage_ms.argtypes = [vp, C.POINTER(C.c_float)]
         L.cb_set_timing.argtypes = [vp, i32]
+        L.ccd_step_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, i64, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -106,6 +107,34 @@ def measure_fma_tflops(fp64: bool = True, blocks: int = 152 * 8, iters: int = 40
     t = C.c_double()
     _check(lib().cb_measure_fma_tflops(int(fp64), blocks, iters, C.byref(t)), "cb_measure_fma_tflops")
     return t.value
+
+
+NOALLOC_MAX_STENCILS = 1 << 20
+NOALLOC_BAD_STENCIL = 8
+
+
+def ccd_step_noalloc(x, p, stencils, is_ee, offset, alpha, flags, stream=None):
+    """Step bound of an explicit stencil list without any device allocation
+    (ccd_step_noalloc of the C ABI).  All arguments are CUDA tensors the caller
+    owns: x, p FP64 [3][n]; stencils int32 [m][4]; is_ee uint8 [m]; offset
+    FP64 [m]; alpha FP64 [1] and flags int32 [1] receive the results.  Nothing
+    is copied or converted here, so non-contiguous or mistyped tensors are
+    rejected rather than fixed."""
+    import torch
+
+    def need(t, dtype, numel=None):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+            raise TypeError(f"expected a contiguous CUDA {dtype} tensor")
+        if numel is not None and t.numel() != numel:
+            raise ValueError(f"expected {numel} elements, got {t.numel()}")
+        return t.data_ptr()
+
+    n = x.numel() // 3
+    m = stencils.numel() // 4
+    args = (need(x, torch.float64, 3 * n), need(p, torch.float64, 3 * n), n,
+            need(stencils, torch.int32, 4 * m), need(is_ee, torch.uint8, m), need(offset, torch.float64, m),
+            m, need(alpha, torch.float64, 1), need(flags, torch.int32, 1), _stream_ptr(stream))
+    _check(lib().ccd_step_noalloc(*args), "ccd_step_noalloc")
 
 
 def status_str(s: int) -> str:

@@ -150,6 +150,7 @@ const char* cb_status_str(cb_status st) {
     case CB_ERR_DEGENERATE: return "zero reference distance between stencil primitives";
     case CB_ERR_ITER_LIMIT: return "additive CCD iteration limit reached";
     case CB_ERR_CUDA: return "CUDA runtime error";
+    case CB_ERR_TOO_LARGE: return "input larger than the call's fixed maximum";
   }
   return "unknown status";
 }

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "bound32.cuh"
 #include "geometry.cuh"
@@ -494,6 +495,267 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     }
   }
   if (alpha) k_alpha_final<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, alpha);
+  CB_CUDA(cudaGetLastError());
+  return CB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ccd_step_noalloc: the same additive-CCD step bound over a caller-given list
+// of stencils, with no device allocation at all.
+//
+// Some callers cannot allocate device memory while they run the step bound: a
+// solver that has handed a fixed budget of the device to a memory pool, or a
+// time-critical loop where an allocation or a free could stall the device.
+// For them every buffer this call needs is the one array below, allocated when
+// the library's code is loaded onto a device.  The first call on each device
+// looks up its address (and may make the CUDA runtime load this code onto that
+// device), so it should come before any stream capture.  The array is shared
+// by every call on a device: calls that overlap in time on one device (two
+// streams, two host threads) race and give wrong results.
+//
+// Layout (64-bit words): NA_SLOTS accumulator words (alpha bits, smallest
+// lower bound bits, condition flags), then one lower bound per stencil.
+
+namespace {
+constexpr int NA_SLOTS = 32;  // 256 bytes: keeps the per-stencil part 256-byte aligned
+constexpr int NA_ALPHA = 0, NA_LB = 1, NA_FLAGS = 2;
+constexpr unsigned long long NA_ONE = 0x3ff0000000000000ull;  // 1.0
+constexpr unsigned long long NA_TWO = 0x4000000000000000ull;  // 2.0: "no value"
+}  // namespace
+
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[NA_SLOTS + CB_NOALLOC_MAX_STENCILS];
+
+namespace {
+
+struct NaArgs {
+  int64_t ns;
+  int n;
+  const int32_t* __restrict__ st;   // [ns][4] vertex ids
+  const uint8_t* __restrict__ ee;   // [ns] 1 edge-edge, 0 point-triangle
+  const double* __restrict__ off;   // [ns] offset
+  const double* __restrict__ x;
+  const double* __restrict__ p;
+  unsigned long long* __restrict__ scr;
+};
+
+struct NaStart {
+  bool ee;
+  double off, lp, g0;
+  d3 Y0, Y1, Y2, Y3, Q0, Q1, Q2, Q3;
+};
+
+// first-step data of stencil q (the same arithmetic as accd_start); false for
+// a stencil with a vertex id outside [0, n) or an offset that is negative or
+// not finite
+__device__ __forceinline__ bool na_start(const NaArgs& A, int64_t q, NaStart& S) {
+  int v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = A.st[4 * q + k];
+    if (v[k] < 0 || v[k] >= A.n) return false;
+  }
+  S.ee = A.ee[q] != 0;
+  S.off = A.off[q];
+  if (!(S.off >= 0.0) || !isfinite(S.off)) return false;
+  const d3 X0 = ld(A.x, A.n, v[0]), X1 = ld(A.x, A.n, v[1]), X2 = ld(A.x, A.n, v[2]), X3 = ld(A.x, A.n, v[3]);
+  const d3 P0 = ld(A.p, A.n, v[0]), P1 = ld(A.p, A.n, v[1]), P2 = ld(A.p, A.n, v[2]), P3 = ld(A.p, A.n, v[3]);
+  double d;
+  cbg::stencil_distance(S.ee, X0, X1, X2, X3, d);
+  const d3 pb = mk3(xmul(xadd(xadd(xadd(P0.x, P1.x), P2.x), P3.x), 0.25),
+                    xmul(xadd(xadd(xadd(P0.y, P1.y), P2.y), P3.y), 0.25),
+                    xmul(xadd(xadd(xadd(P0.z, P1.z), P2.z), P3.z), 0.25));
+  S.Y0 = sub3(X0, X0);
+  S.Y1 = sub3(X1, X0);
+  S.Y2 = sub3(X2, X0);
+  S.Y3 = sub3(X3, X0);
+  S.Q0 = sub3(P0, pb);
+  S.Q1 = sub3(P1, pb);
+  S.Q2 = sub3(P2, pb);
+  S.Q3 = sub3(P3, pb);
+  const double n0 = norm3(S.Q0), n1 = norm3(S.Q1), n2 = norm3(S.Q2), n3 = norm3(S.Q3);
+  S.lp = S.ee ? xadd(fmax(n0, n1), fmax(n2, n3)) : xadd(n0, fmax(fmax(n1, n2), n3));
+  S.g0 = (S.lp != 0.0) ? xsub(d, S.off) : 0.0;
+  return true;
+}
+
+// one atomicMin per warp of the lanes' non-negative values (2.0 = none)
+__device__ __forceinline__ void na_warp_min(unsigned long long* slot, double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, b, o);
+    b = u < b ? u : b;
+  }
+  if ((threadIdx.x & 31) == 0 && b < NA_TWO) atomicMin(slot, b);
+}
+
+__global__ void k_na_init(unsigned long long* __restrict__ scr) {
+  if (threadIdx.x == 0) {
+    scr[NA_ALPHA] = NA_ONE;
+    scr[NA_LB] = NA_TWO;
+    scr[NA_FLAGS] = 0ull;
+  }
+}
+
+// first step of every stencil: resolves t_p = 1 (no motion, or the first step
+// already passes 1) and t_p = 0 (at or inside the offset); otherwise stores
+// the lower bound (1-s) g0 / l_p of t_p
+__global__ void __launch_bounds__(128) k_na_first(NaArgs A) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double m_exact = 2.0, m_lb = 2.0;
+  if (q < A.ns) {
+    NaStart S;
+    double lbq = 2.0;
+    if (!na_start(A, q, S)) {
+      atomicOr(&A.scr[NA_FLAGS], (unsigned long long)CB_NOALLOC_BAD_STENCIL);
+    } else if (S.lp == 0.0) {
+      m_exact = 1.0;
+    } else if (S.g0 <= 0.0) {
+      m_exact = 0.0;
+      atomicOr(&A.scr[NA_FLAGS], (unsigned long long)CB_DEV_PENETRATION);
+    } else {
+      const double tl = xdiv(xmul(xsub(1.0, ACCD_S), S.g0), S.lp);
+      if (tl > 1.0) {
+        m_exact = 1.0;
+      } else {
+        lbq = tl;
+        m_lb = tl;
+      }
+    }
+    A.scr[NA_SLOTS + q] = (unsigned long long)__double_as_longlong(lbq);
+  }
+  na_warp_min(&A.scr[NA_ALPHA], m_exact);
+  na_warp_min(&A.scr[NA_LB], m_lb);
+}
+
+// full additive CCD of stencil q (the iteration of k_ccd_exact)
+__device__ double na_iterate(const NaArgs& A, int64_t q) {
+  NaStart S;
+  if (!na_start(A, q, S)) return 2.0;
+  if (S.lp == 0.0) return 1.0;
+  if (S.g0 <= 0.0) return 0.0;
+  const double g = xmul(ACCD_S, S.g0);
+  double t = 0.0, d;
+  double tl = xdiv(xmul(xsub(1.0, ACCD_S), S.g0), S.lp);
+  for (int it = 0; it < ACCD_MAX_ITER; ++it) {
+    S.Y0 = axpy3(S.Y0, tl, S.Q0);
+    S.Y1 = axpy3(S.Y1, tl, S.Q1);
+    S.Y2 = axpy3(S.Y2, tl, S.Q2);
+    S.Y3 = axpy3(S.Y3, tl, S.Q3);
+    cbg::stencil_distance(S.ee, S.Y0, S.Y1, S.Y2, S.Y3, d);
+    if (t > 0.0 && xsub(d, S.off) < g) return t;
+    t = xadd(t, tl);
+    if (t > 1.0) return 1.0;
+    tl = xdiv(xmul(ACCD_C, xsub(d, S.off)), S.lp);
+  }
+  atomicOr(&A.scr[NA_FLAGS], (unsigned long long)CB_DEV_ITER_LIMIT);
+  return t;
+}
+
+// Bands of lower bounds, as in ccd_run but decided on the device: band 0 is
+// (-1, min(1, 2L)] with L the smallest bound; band 1 is (hi0, min(1, m)] with
+// m the minimum after band 0.  Every stencil left after band 1 has
+// t_p >= lb_p > m, so alpha = min(1, m) exactly.  The minimum is read once per
+// block: a smaller value seen later only narrows the band to stencils that
+// still could lower it.
+__global__ void __launch_bounds__(128) k_na_band(NaArgs A, int band) {
+  __shared__ double s_lo, s_hi;
+  if (threadIdx.x == 0) {
+    const double L = __longlong_as_double(A.scr[NA_LB]);
+    const double m = __longlong_as_double(A.scr[NA_ALPHA]);
+    const double h0 = fmin(1.0, 2.0 * L);
+    double lo = 3.0, hi = 3.0;  // empty band
+    if (!(L > 1.0 || m <= L)) {
+      if (band == 0) {
+        lo = -1.0;
+        hi = h0;
+      } else if (!(m <= h0 || h0 >= 1.0)) {
+        lo = h0;
+        hi = fmin(1.0, m);
+      }
+    }
+    s_lo = lo;
+    s_hi = hi;
+  }
+  __syncthreads();
+  const double lo = s_lo, hi = s_hi;
+  if (lo >= 3.0) return;  // uniform over the block
+  for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < A.ns; w0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = w0 + threadIdx.x;
+    double t = 2.0;
+    if (q < A.ns) {
+      const double lbq = __longlong_as_double(A.scr[NA_SLOTS + q]);
+      if (lbq > lo && lbq <= hi) t = na_iterate(A, q);
+    }
+    na_warp_min(&A.scr[NA_ALPHA], t);
+  }
+}
+
+__global__ void k_na_final(const unsigned long long* __restrict__ scr, double* __restrict__ alpha,
+                           uint32_t* __restrict__ flags) {
+  if (threadIdx.x == 0) {
+    *alpha = __longlong_as_double(scr[NA_ALPHA]);
+    *flags = (uint32_t)scr[NA_FLAGS];
+  }
+}
+
+constexpr int NA_MAX_DEVICES = 256;
+std::mutex g_na_mutex;
+unsigned long long* g_na_ptr[NA_MAX_DEVICES];
+
+// address of the scratch array on the current device, looked up once per device
+cb_status na_scratch(unsigned long long** out) {
+  int dev = -1;
+  CB_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NA_MAX_DEVICES) return CB_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_ptr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+      fprintf(stderr, "contact: ccd_step_noalloc: scratch address lookup failed on device %d: %s\n", dev,
+              cudaGetErrorString(e));
+      return CB_ERR_CUDA;
+    }
+    g_na_ptr[dev] = (unsigned long long*)ptr;
+  }
+  *out = g_na_ptr[dev];
+  return CB_OK;
+}
+
+}  // namespace
+
+cb_status ccd_step_noalloc(const double* x_dev, const double* p_dev, int32_t n_verts, const int32_t* stencils_dev,
+                           const uint8_t* is_ee_dev, const double* offset_dev, int64_t n_stencils,
+                           double* alpha_dev, uint32_t* flags_dev, void* stream) {
+  if (!alpha_dev || !flags_dev || n_verts < 0 || n_stencils < 0) return CB_ERR_ARG;
+  if (n_stencils > CB_NOALLOC_MAX_STENCILS) {
+    fprintf(stderr, "contact: ccd_step_noalloc: %lld stencils exceed the fixed maximum of %d per call\n",
+            (long long)n_stencils, (int)CB_NOALLOC_MAX_STENCILS);
+    return CB_ERR_TOO_LARGE;
+  }
+  if (n_stencils > 0 && (n_verts < 1 || !x_dev || !p_dev || !stencils_dev || !is_ee_dev || !offset_dev))
+    return CB_ERR_ARG;
+  unsigned long long* scr = nullptr;
+  CB_TRY(na_scratch(&scr));
+  cudaStream_t st = (cudaStream_t)stream;
+  k_na_init<<<1, 32, 0, cb_count(st)>>>(scr);
+  if (n_stencils > 0) {
+    NaArgs A;
+    A.ns = n_stencils;
+    A.n = n_verts;
+    A.st = stencils_dev;
+    A.ee = is_ee_dev;
+    A.off = offset_dev;
+    A.x = x_dev;
+    A.p = p_dev;
+    A.scr = scr;
+    k_na_first<<<cb_grid(n_stencils, 128), 128, 0, cb_count(st)>>>(A);
+    const int gb = std::min<int64_t>(cb_grid(n_stencils, 128), 152 * 16);
+    k_na_band<<<gb, 128, 0, cb_count(st)>>>(A, 0);
+    k_na_band<<<gb, 128, 0, cb_count(st)>>>(A, 1);
+  }
+  k_na_final<<<1, 32, 0, cb_count(st)>>>(scr, alpha_dev, flags_dev);
   CB_CUDA(cudaGetLastError());
   return CB_OK;
 }
