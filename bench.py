@@ -147,13 +147,134 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def _timed_steps(run, steps, flush, stream):
+    """Device time (ms) of each of `steps` calls of run(), L2 flushed before each."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        run()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def bench_batch(args, rank, world, local, dist):
+    """64 rod scenes (weave / knit, 1k-64k vertices each): the batched pass (one
+    launch per stage for all scenes) against the plain form (one scene per
+    launch sequence, the 64 scenes one after another on the same stream)."""
+    import numpy as np
+    import torch
+    from paper_2510_10256_gb300 import contact as CT
+    from paper_2510_10256_gb300 import scenes as S
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    scenes = S.rod_batch()
+    members = [CT.ContactScene.from_scene(sc) for sc in scenes]
+    batch = CT.ContactBatch(members)
+    M, N = len(scenes), batch.n
+    xs = [torch.from_numpy(sc.x).to(dev) for sc in scenes]
+    ps = [torch.from_numpy(sc.p).to(dev) for sc in scenes]
+    es = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in scenes]
+    gs = [torch.zeros(3, sc.n, dtype=torch.float64, device=dev) for sc in scenes]
+    als = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in scenes]
+    hx_np = np.ascontiguousarray(np.concatenate([sc.x for sc in scenes], axis=1))
+    hp_np = np.ascontiguousarray(np.concatenate([sc.p for sc in scenes], axis=1))
+    x = torch.from_numpy(hx_np).to(dev)
+    p = torch.from_numpy(hp_np).to(dev)
+    energy = torch.zeros(M, dtype=torch.float64, device=dev)
+    grad = torch.zeros(3, N, dtype=torch.float64, device=dev)
+    alpha = torch.zeros(M, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def run_batched():
+        batch.run_pass(x, p, energy, grad, alpha)
+
+    def run_plain():
+        for k, m in enumerate(members):
+            m.run_pass(xs[k], ps[k], es[k], gs[k], als[k])
+
+    batch.set_timing(True)
+    for _ in range(args.warmup):
+        run_batched()
+        run_plain()
+    torch.cuda.synchronize()
+    st = batch.stats()
+    n_cand = int(st["n_candidates"])
+    assert n_cand == sum(int(m.stats()["n_candidates"]) for m in members)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = CT.kernel_launches()
+    stage = []
+
+    def run_b():
+        run_batched()
+        stage.append(batch.stage_ms())
+
+    b_ms = _timed_steps(run_b, args.steps, flush, stream)
+    launches = CT.kernel_launches() - l0
+    p_ms = _timed_steps(run_plain, args.steps, flush, stream)
+    clk = clocks.stop()
+    ms, pms = statistics.mean(b_ms), statistics.mean(p_ms)
+    if dist:
+        t = torch.tensor([ms, pms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, pms = float(t[0]), float(t[1])
+    # end to end: pinned host x, p in; energy, alpha, gradient out
+    hx, hp = torch.from_numpy(hx_np).pin_memory(), torch.from_numpy(hp_np).pin_memory()
+    he = torch.zeros(M, dtype=torch.float64).pin_memory()
+    ha = torch.zeros(M, dtype=torch.float64).pin_memory()
+    hg = torch.zeros(3, N, dtype=torch.float64).pin_memory()
+
+    def run_e2e():
+        x.copy_(hx, non_blocking=True)
+        p.copy_(hp, non_blocking=True)
+        run_batched()
+        he.copy_(energy, non_blocking=True)
+        ha.copy_(alpha, non_blocking=True)
+        hg.copy_(grad, non_blocking=True)
+
+    e2e_ms = statistics.mean(_timed_steps(run_e2e, max(3, args.steps // 2), flush, stream))
+    if rank != 0:
+        return
+    hess_ms = statistics.mean(s[4] for s in stage)
+    med = [statistics.median(s[i] for s in stage) for i in range(5)]
+    na = int(st["n_active"])
+    achieved = FLOPS_PER_ACTIVE * na / (hess_ms / 1000.0) / 1e12 if hess_ms > 0 else 0.0
+    sizes = [sc.n for sc in scenes]
+    line = {"metric": METRIC, "value": world * n_cand / (ms / 1000.0), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{M} rod scenes (even: plain weave, odd: helix-loop knit), "
+                                   f"{min(sizes)}-{max(sizes)} vertices each, {N} in all, batched",
+                       "candidates": n_cand, "active": na, "ccd_pairs": int(st["n_ccd"]), "nnzb": int(st["nnzb"]),
+                       "l2": "flushed (256 MiB write) between steps", "parallelism": f"replicas x{world}"},
+            "plain": {"value": world * n_cand / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
+                      "form": f"{M} single-scene passes in sequence on one stream"},
+            "batched_over_plain": pms / ms,
+            "stage_ms": {"contact_build": med[0], "contact_filter": med[1], "barrier_eval": med[2],
+                         "ccd_step": med[3], "hessian_kernel": med[4]},
+            "roofline": {"bound": "alu", "kernel": "k_hess_prep + k_hess_proj (FP64 stage d)", "achieved": achieved,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": None, "flops_per_active_pair": FLOPS_PER_ACTIVE, "kernel_ms": hess_ms,
+                         "peak_source": "derived: 152 SM x 2070 MHz x 4 FP64 flop/clk/SM"},
+            "e2e": {"value": world * n_cand / (e2e_ms / 1000.0), "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": 2 * 3 * N * 8, "d2h_bytes_per_step": 2 * M * 8 + 3 * N * 8},
+            "clocks": clk, "gpu_launches": int(launches), "status": batch.sync_status()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="pleated", choices=["pleated", "woven", "graded"])
+    ap.add_argument("--workload", default="pleated", choices=["pleated", "woven", "graded", "knit64"])
     ap.add_argument("--nx", type=int, default=0, help="pleated grid size (default: the full 256)")
     ap.add_argument("--cpu-nx", type=int, default=128, help="grid size of the oracle baseline sample")
     ap.add_argument("--ref-nx", type=int, default=96, help="grid size of a reference-arm step")
@@ -182,6 +303,9 @@ def main():
         dist.barrier()
     from paper_2510_10256_gb300 import contact as CT
 
+    if args.workload == "knit64":
+        bench_batch(args, rank, world, local, dist)
+        return
     sc, desc = _workload(args.workload, reduced_nx=args.nx or None)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -271,7 +395,7 @@ def main():
         fp32_meas = CT.measure_fma_tflops(False, iters=65536)
     except Exception:
         fp64_meas = fp32_meas = None
-    roofline = {"bound": "alu", "kernel": "k_barrier_hess (FP64 stage d)", "achieved": achieved,
+    roofline = {"bound": "alu", "kernel": "k_hess_prep + k_hess_proj (FP64 stage d)", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_fp64_fma_measured": fp64_meas, "peak_fp32_fma_measured": fp32_meas,
                 "traffic": None, "flops_per_active_pair": FLOPS_PER_ACTIVE, "active_pairs": na,

@@ -115,14 +115,25 @@ def _helix_row(x0: float, y0: float, n_vert: int, seg: float, radius: float,
 
 def _min_helix_gap(radius: float, pitch: float, dy: float) -> float:
     """Closest approach of two parallel helices, the second shifted by dy across
-    and half a pitch along the axis."""
-    t = np.linspace(0.0, 2 * math.pi, 721)
-    s = np.linspace(-2 * math.pi, 4 * math.pi, 2161)
-    a = np.stack([pitch * t / (2 * math.pi), radius * np.cos(t), radius * np.sin(t)])
-    b = np.stack([0.5 * pitch + pitch * s / (2 * math.pi),
-                  dy + radius * np.cos(s), radius * np.sin(s)])
-    d2 = ((a[:, :, None] - b[:, None, :]) ** 2).sum(0)
-    return float(np.sqrt(d2.min()))
+    and half a pitch along the axis: a coarse parameter grid, then three local
+    zooms around the best cell (each 10x finer)."""
+    def pts(t, shift, y0):
+        return (shift + pitch * t / (2 * math.pi), y0 + radius * np.cos(t), radius * np.sin(t))
+
+    def grid_min(t, s):
+        ax, ay, az = pts(t, 0.0, 0.0)
+        bx, by, bz = pts(s, 0.5 * pitch, dy)
+        d2 = (ax[:, None] - bx[None, :]) ** 2 + (ay[:, None] - by[None, :]) ** 2 + \
+            (az[:, None] - bz[None, :]) ** 2
+        i, j = np.unravel_index(int(np.argmin(d2)), d2.shape)
+        return float(d2[i, j]), float(t[i]), float(s[j])
+
+    ht, hs = 2 * math.pi / 180, 6 * math.pi / 540
+    best, t0, s0 = grid_min(np.linspace(0.0, 2 * math.pi, 181), np.linspace(-2 * math.pi, 4 * math.pi, 541))
+    for _ in range(3):
+        best, t0, s0 = grid_min(np.linspace(t0 - ht, t0 + ht, 21), np.linspace(s0 - hs, s0 + hs, 21))
+        ht, hs = ht / 10, hs / 10
+    return math.sqrt(best)
 
 
 def knit_rows(seed: int, n_target: int, r: float, seg: float, dhat: float,
