@@ -198,11 +198,13 @@ def bench_batch(args, rank, world, local, dist):
     batch.set_timing(True)
     for _ in range(args.warmup):
         run_batched()
-        run_plain()
+        if not args.no_plain:
+            run_plain()
     torch.cuda.synchronize()
     st = batch.stats()
     n_cand = int(st["n_candidates"])
-    assert n_cand == sum(int(m.stats()["n_candidates"]) for m in members)
+    if not args.no_plain:  # the batch forms exactly the members' own pairs
+        assert n_cand == sum(int(m.stats()["n_candidates"]) for m in members)
     clocks = ClockSampler(local)
     clocks.start()
     if dist:
@@ -217,7 +219,7 @@ def bench_batch(args, rank, world, local, dist):
 
     b_ms = _timed_steps(run_b, args.steps, flush, stream)
     launches = CT.kernel_launches() - l0
-    p_ms = _timed_steps(run_plain, args.steps, flush, stream)
+    p_ms = _timed_steps(run_plain, args.steps, flush, stream) if not args.no_plain else [float("nan")]
     clk = clocks.stop()
     ms, pms = statistics.mean(b_ms), statistics.mean(p_ms)
     if dist:
@@ -252,6 +254,7 @@ def bench_batch(args, rank, world, local, dist):
             "config": {"workload": f"{M} rod scenes (even: plain weave, odd: helix-loop knit), "
                                    f"{min(sizes)}-{max(sizes)} vertices each, {N} in all, batched",
                        "candidates": n_cand, "active": na, "ccd_pairs": int(st["n_ccd"]), "nnzb": int(st["nnzb"]),
+                       "ccd_max_iters": int(st["ccd_max_iters"]),
                        "l2": "flushed (256 MiB write) between steps", "parallelism": f"replicas x{world}"},
             "plain": {"value": world * n_cand / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
                       "form": f"{M} single-scene passes in sequence on one stream"},
@@ -279,6 +282,7 @@ def main():
     ap.add_argument("--cpu-nx", type=int, default=128, help="grid size of the oracle baseline sample")
     ap.add_argument("--ref-nx", type=int, default=96, help="grid size of a reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="knit64: skip the one-scene-per-launch arm")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

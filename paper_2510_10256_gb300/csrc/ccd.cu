@@ -11,14 +11,18 @@
 // below s g0.  alpha = min(1, min_p t_p).
 //
 // Only the minimum is needed, so the step bound is computed exactly without
-// iterating every pair: the additive CCD result is never below its first step,
+// iterating every pair to its end: the additive CCD iterate t only grows, and
 // t_p >= min(1, (1-s) g0 / l_p) =: lb_p.  Pass 1 computes lb_p for every pair
 // (one distance each; pairs whose first step already passes t = 1, or that do
-// not move, are resolved exactly here).  Pass 2 runs the full iteration on the
-// unresolved pairs with lb_p in a band (lo, hi]; once the minimum m found so
-// far is <= hi, every pair left has t_p >= lb_p > hi >= m and
-// alpha = min(1, m) exactly; otherwise the band (hi, m] is evaluated, after
-// which the same holds.
+// not move, are resolved exactly here).  Pass 2 works in rounds with a ceiling
+// h per member, starting at 4 L (L the smallest lb_p) and growing 4x: each
+// round iterates the pairs with lb_p <= h, stopping a pair when it finishes
+// (exact t_p) or when its iterate reaches h or the member's current minimum;
+// a stopped pair keeps its iterate as its new lb_p.  After a round every
+// unfinished pair has t_p >= lb_p >= min(h, m) with m the smallest exact t_p
+// found, so once m <= h (or h = 1) alpha = min(1, m) exactly.  A pair's
+// iteration always restarts from t = 0, so an exact t_p is the same number
+// as a single uninterrupted run.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -303,18 +307,41 @@ __global__ void k_ccd_select(int64_t np, const uint64_t* __restrict__ keys, cons
   flag[q] = (lb[q] > lo && lb[q] <= hi) ? 1u : 0u;
 }
 
+// the same over a list of pair indices: flag[w] for pair ulist[w]
+__global__ void k_ccd_select_u(int64_t nu, const uint32_t* __restrict__ ulist, const uint64_t* __restrict__ keys,
+                               const int32_t* __restrict__ ev0, const int32_t* __restrict__ vsc,
+                               const double* __restrict__ lb, const unsigned long long* __restrict__ macc,
+                               uint32_t* __restrict__ flag) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nu) return;
+  const uint32_t q = ulist[w];
+  const uint64_t key = keys[q];
+  const int v0 = cb_key_type(key) == CB_KEY_PT ? (int)cb_key_i(key) : ev0[cb_key_i(key)];
+  const int mem = vsc[v0];
+  const double hi = __longlong_as_double(macc[(size_t)mem * MACC_STRIDE + MACC_HI]);
+  flag[w] = lb[q] <= hi ? 1u : 0u;
+}
+
 __global__ void k_list(int64_t np, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
                        uint32_t* __restrict__ list) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q < np && flag[q]) list[pos[q]] = (uint32_t)q;
 }
 
-// pass 2: full additive CCD of the selected pairs
-__global__ void __launch_bounds__(128) k_ccd_exact(CcdArgs A, int64_t m, const uint32_t* __restrict__ list) {
+__global__ void k_list_u(int64_t nu, const uint32_t* __restrict__ ulist, const uint32_t* __restrict__ flag,
+                         const uint32_t* __restrict__ pos, uint32_t* __restrict__ list) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w < nu && flag[w]) list[pos[w]] = ulist[w];
+}
+
+// pass 2: additive CCD of the selected pairs, each up to its member's ceiling
+__global__ void __launch_bounds__(128) k_ccd_exact(CcdArgs A, int64_t m, const uint32_t* __restrict__ list,
+                                                   double* __restrict__ lb_out) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= m) return;
   const int64_t q = list[w];
   AccdStart S = accd_start(A, q);
+  unsigned long long* amin = macc_of(A, S.mem, MACC_ALPHA);
   if (S.lp == 0.0 || S.g0 <= 0.0) {  // only reachable through an FP32 bound below 1
     const double t0 = S.lp == 0.0 ? 1.0 : 0.0;
     if (S.lp != 0.0) {
@@ -323,14 +350,18 @@ __global__ void __launch_bounds__(128) k_ccd_exact(CcdArgs A, int64_t m, const u
     }
     A.t_out[q] = t0;
     A.cls_out[q] = (uint8_t)S.cls | EXACT;
-    atomicMin(macc_of(A, S.mem, MACC_ALPHA), (unsigned long long)__double_as_longlong(t0));
+    lb_out[q] = 2.0;
+    atomicMin(amin, (unsigned long long)__double_as_longlong(t0));
     return;
   }
+  // ceiling: the band's upper end, lowered to the member's minimum as it falls
+  const double hi = __longlong_as_double(*macc_of(A, S.mem, MACC_HI));
+  double cap = fmin(hi, __longlong_as_double(*(volatile unsigned long long*)amin));
   const double g = xmul(ACCD_S, S.g0);
   double t = 0.0, d;
   double tl = xdiv(xmul(xsub(1.0, ACCD_S), S.g0), S.lp);
   int it;
-  bool capped = true;
+  bool capped = true, stopped = false;
   for (it = 0; it < ACCD_MAX_ITER; ++it) {
     S.Y0 = axpy3(S.Y0, tl, S.Q0);
     S.Y1 = axpy3(S.Y1, tl, S.Q1);
@@ -347,13 +378,25 @@ __global__ void __launch_bounds__(128) k_ccd_exact(CcdArgs A, int64_t m, const u
       capped = false;
       break;
     }
+    if ((it & 7) == 7) cap = fmin(hi, __longlong_as_double(*(volatile unsigned long long*)amin));
+    if (cap < 1.0 && t >= cap) {  // t_p >= t >= cap: this pair cannot lower the minimum now
+      capped = false;
+      stopped = true;
+      break;
+    }
     tl = xdiv(xmul(ACCD_C, xsub(d, S.off)), S.lp);
   }
   if (capped) atomicOr(A.status, (unsigned long long)CB_DEV_ITER_LIMIT);
   A.t_out[q] = t;
-  A.cls_out[q] = (uint8_t)S.cls | EXACT;
-  atomicMin(macc_of(A, S.mem, MACC_ALPHA), (unsigned long long)__double_as_longlong(t));
   atomicMax(A.max_iters, (unsigned long long)(it + 1));
+  if (stopped) {
+    A.cls_out[q] = (uint8_t)S.cls;
+    lb_out[q] = t;
+    return;
+  }
+  A.cls_out[q] = (uint8_t)S.cls | EXACT;
+  lb_out[q] = 2.0;
+  atomicMin(amin, (unsigned long long)__double_as_longlong(t));
 }
 
 __global__ void k_alpha_final(int count, const unsigned long long* __restrict__ macc, double* __restrict__ out) {
@@ -421,10 +464,10 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     k_ccd_bound<<<std::min<int64_t>(cb_grid(np, 128), 152 * 16), 128, 0, cb_count(st)>>>(
         A, bp<double>(s->ccd_lb), bp<uint32_t>(s->dlist), nl);
     CB_CUDA(cudaGetLastError());
-    // Per member: bands (lo, hi] of lower bounds.  First (-1, min(1, 2L)], L the
-    // smallest bound; then (hi, m] with m the exact minimum found so far, after
-    // which every pair left has t_p >= lb_p > m.  Members whose minimum is
-    // already below every remaining bound are done.
+    // Per member: the pairs left unresolved by pass 1 (lb <= 1) are gathered
+    // once; then rounds with ceiling h = 4 L, 16 L, ... (capped at 1) run until
+    // the member's minimum is <= h.  Members whose minimum is already below
+    // every remaining bound are done after pass 1.
     std::vector<unsigned long long> hm((size_t)M * MACC_STRIDE);
     auto read_macc = [&]() -> cb_status {
       CB_CUDA(cudaMemcpyAsync(s->hstage_host, macc, sizeof(unsigned long long) * MACC_STRIDE * M,
@@ -433,30 +476,8 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
       memcpy(hm.data(), s->hstage_host, sizeof(unsigned long long) * MACC_STRIDE * M);
       return CB_OK;
     };
-    auto dbl = [](unsigned long long b) {
-      double d;
-      memcpy(&d, &b, 8);
-      return d;
-    };
-    CB_TRY(read_macc());
-    std::vector<double> lo(M, -1.0), hi(M, 3.0);
-    std::vector<char> done(M, 0);
-    bool any = false;
-    for (int m = 0; m < M; ++m) {
-      const double L = dbl(hm[(size_t)m * MACC_STRIDE + MACC_LB]);
-      const double mm = dbl(hm[(size_t)m * MACC_STRIDE + MACC_ALPHA]);
-      if (L > 1.0 || mm <= L) {
-        done[m] = 1;
-        lo[m] = 3.0;
-        hi[m] = 3.0;
-      } else {
-        hi[m] = std::min(1.0, 2.0 * L);
-        any = true;
-      }
-    }
-    while (any) {
-      // upload the band limits (hm holds the device values read just before,
-      // and no kernel runs in between)
+    auto upload_band = [&](const std::vector<double>& lo, const std::vector<double>& hi) -> cb_status {
+      // hm holds the device values read just before, and no kernel runs in between
       for (int m = 0; m < M; ++m) {
         memcpy(&hm[(size_t)m * MACC_STRIDE + MACC_LO], &lo[m], 8);
         memcpy(&hm[(size_t)m * MACC_STRIDE + MACC_HI], &hi[m], 8);
@@ -464,19 +485,62 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
       memcpy(s->hstage_host, hm.data(), sizeof(unsigned long long) * MACC_STRIDE * M);
       CB_CUDA(cudaMemcpyAsync(macc, s->hstage_host, sizeof(unsigned long long) * MACC_STRIDE * M,
                               cudaMemcpyHostToDevice, st));
+      return CB_OK;
+    };
+    auto dbl = [](unsigned long long b) {
+      double d;
+      memcpy(&d, &b, 8);
+      return d;
+    };
+    CB_TRY(read_macc());
+    std::vector<double> lo(M, 3.0), hi(M, -1.0);
+    std::vector<char> done(M, 1);
+    bool any = false;
+    for (int m = 0; m < M; ++m) {
+      const double L = dbl(hm[(size_t)m * MACC_STRIDE + MACC_LB]);
+      const double mm = dbl(hm[(size_t)m * MACC_STRIDE + MACC_ALPHA]);
+      if (!(L > 1.0 || mm <= L)) {
+        done[m] = 0;
+        lo[m] = -1.0;
+        hi[m] = 1.0;
+        any = true;
+      }
+    }
+    uint32_t* tot = (uint32_t*)(sc + SC_COUNT1);
+    int64_t nu = 0;
+    if (any) {
+      // gather the unresolved pairs (lb <= 1) of the members not yet done
+      CB_TRY(upload_band(lo, hi));
       k_ccd_select<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(np, bp<uint64_t>(s->ccd_keys), bp<int32_t>(s->ev0),
                                                                   bp<int32_t>(s->vsc), bp<double>(s->ccd_lb), macc,
                                                                   bp<uint32_t>(s->ccd_flag));
-      uint32_t* tot = (uint32_t*)(sc + SC_COUNT1);
       cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(s->ccd_flag), bp<uint32_t>(s->ccd_pos), np,
                                               bp<uint32_t>(s->scan_tmp), tot, st);
+      uint64_t hn;
+      CB_TRY(read_scalars(s, SC_COUNT1, 1, &hn, st));
+      nu = (int64_t)(uint32_t)hn;
+      CB_TRY(buf_ensure(s->ccd_ulist, sizeof(uint32_t) * (size_t)std::max<int64_t>(nu, 1), st));
       k_list<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(np, bp<uint32_t>(s->ccd_flag), bp<uint32_t>(s->ccd_pos),
-                                                           bp<uint32_t>(s->ccd_list));
+                                                           bp<uint32_t>(s->ccd_ulist));
+      for (int m = 0; m < M; ++m)
+        if (!done[m]) hi[m] = std::min(1.0, 4.0 * dbl(hm[(size_t)m * MACC_STRIDE + MACC_LB]));
+      any = nu > 0;
+    }
+    while (any) {
+      CB_TRY(upload_band(lo, hi));
+      k_ccd_select_u<<<cb_grid(nu), CB_THREADS, 0, cb_count(st)>>>(
+          nu, bp<uint32_t>(s->ccd_ulist), bp<uint64_t>(s->ccd_keys), bp<int32_t>(s->ev0), bp<int32_t>(s->vsc),
+          bp<double>(s->ccd_lb), macc, bp<uint32_t>(s->ccd_flag));
+      cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(s->ccd_flag), bp<uint32_t>(s->ccd_pos), nu,
+                                              bp<uint32_t>(s->scan_tmp), tot, st);
+      k_list_u<<<cb_grid(nu), CB_THREADS, 0, cb_count(st)>>>(nu, bp<uint32_t>(s->ccd_ulist), bp<uint32_t>(s->ccd_flag),
+                                                             bp<uint32_t>(s->ccd_pos), bp<uint32_t>(s->ccd_list));
       uint64_t hmsel;
       CB_TRY(read_scalars(s, SC_COUNT1, 1, &hmsel, st));
       const int64_t msel = (int64_t)(uint32_t)hmsel;
       if (msel > 0)
-        k_ccd_exact<<<cb_grid(msel, 128), 128, 0, cb_count(st)>>>(A, msel, bp<uint32_t>(s->ccd_list));
+        k_ccd_exact<<<cb_grid(msel, 128), 128, 0, cb_count(st)>>>(A, msel, bp<uint32_t>(s->ccd_list),
+                                                                  bp<double>(s->ccd_lb));
       CB_CUDA(cudaGetLastError());
       CB_TRY(read_macc());
       any = false;
@@ -484,11 +548,10 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
         if (done[m]) continue;
         const double mm = dbl(hm[(size_t)m * MACC_STRIDE + MACC_ALPHA]);
         if (mm <= hi[m] || hi[m] >= 1.0) {
-          done[m] = 1;  // every pair left has t_p >= lb_p > hi >= m
-          lo[m] = hi[m] = 3.0;
+          done[m] = 1;  // every unfinished pair has t_p >= lb_p >= min(h, m)
+          hi[m] = -1.0;
         } else {
-          lo[m] = hi[m];
-          hi[m] = std::min(1.0, mm);
+          hi[m] = std::min(1.0, 4.0 * hi[m]);
           any = true;
         }
       }
