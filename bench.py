@@ -271,13 +271,86 @@ def bench_batch(args, rank, world, local, dist):
     print(json.dumps(line), flush=True)
 
 
+def bench_serve(args, rank, world, local, dist):
+    """Served request stream: Poisson arrivals, each request a sequence of
+    contact steps on its own scene (rods 5k-200k vertices, shells 10k-500k
+    triangles, half and half), admitted under an HBM budget and advanced by
+    continuous batching (paper_2510_10256_gb300.serve)."""
+    import torch
+    from paper_2510_10256_gb300 import contact as CT
+    from paper_2510_10256_gb300 import scenes as S
+    from paper_2510_10256_gb300.serve import DeviceEngine, Server, poisson_requests
+    pool = S.serve_pool()
+    reqs = poisson_requests(pool, args.requests, args.rate, args.req_steps, seed=S.BASE_SEED + 5 + rank)
+    eng = DeviceEngine(torch.device("cuda", local))
+    small = sorted(pool, key=lambda sc: sc.n)
+    sample = [next(sc for sc in small if sc.kind == k) for k in ("rod", "shell")]
+    sample += [next(sc for sc in small if sc.kind == "shell" and sc.name != sample[1].name)]
+    for _ in range(max(1, args.warmup // len(sample))):
+        bpv = eng.calibrate(sample)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    l0 = CT.kernel_launches()
+    rep = Server(eng, hbm_budget=int(args.budget_gb * (1 << 30)), max_slots=args.slots).run(reqs)
+    launches = CT.kernel_launches() - l0
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    wall = rep["wall_s"]
+    if dist:
+        t = torch.tensor([wall], dtype=torch.float64, device=torch.device("cuda", local))
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        wall = float(t.item())
+    eng.close()
+    if rank != 0:
+        return
+    served = [r for r in reqs if r.rid not in set(rep["rejected"])]
+    h2d = sum(8 * r.scene.rest.size + 8 * r.scene.x.size + 4 * (r.scene.tris.size if r.scene.tris is not None else
+                                                                  r.scene.rod_ptr.size) for r in served)
+    steps = max(1, rep["steps"])
+    value = world * rep["pairs"] / wall
+    lat = rep["step_latency_ms"]
+    line = {"metric": "served contact pairs/s (filter+barrier+Hessian+CCD); p50/p99 step latency", "value": value,
+            "unit": UNIT, "n_gpus": world, "steps": rep["steps"], "warmup": max(3, args.warmup),
+            "ms_per_step": lat["mean"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"served stream: {args.requests} Poisson requests at {args.rate:g}/s, "
+                                   f"{args.req_steps} contact steps each, rods {min(s.n for s in pool if s.kind == 'rod')}-"
+                                   f"{max(s.n for s in pool if s.kind == 'rod')} vertices / shells "
+                                   f"{min(s.tris.shape[1] for s in pool if s.kind == 'shell')}-"
+                                   f"{max(s.tris.shape[1] for s in pool if s.kind == 'shell')} triangles (pool of "
+                                   f"{len(pool)} seeded scenes), half and half",
+                       "hbm_budget_gb": args.budget_gb, "slots": args.slots, "bytes_per_vertex_model": bpv,
+                       "l2": "not flushed: every iteration streams pair lists far larger than L2",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"step_p50": lat["p50"], "step_p99": lat["p99"],
+                           "queue_p50": rep["queue_delay_ms"]["p50"], "queue_p99": rep["queue_delay_ms"]["p99"],
+                           "load_p50": rep["load_ms"]["p50"], "load_p99": rep["load_ms"]["p99"]},
+            "served": {"wall_s": wall, "requests": rep["requests"], "rejected": len(rep["rejected"]),
+                       "steps_per_s": rep["steps_per_s"], "iterations": rep["iterations"],
+                       "max_resident": rep["max_resident"], "peak_reserved_gb": rep["peak_reserved_bytes"] / 2 ** 30},
+            "roofline": None,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": 16,
+                    "note": "the served stream is itself end to end: scenes uploaded from host memory at "
+                            "admission, step results read back every step"},
+            "clocks": clk, "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="pleated", choices=["pleated", "woven", "graded", "knit64"])
+    ap.add_argument("--workload", default="pleated", choices=["pleated", "woven", "graded", "knit64", "serve"])
+    ap.add_argument("--requests", type=int, default=1000, help="serve: requests in the stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (requests/s)")
+    ap.add_argument("--req-steps", type=int, default=10, help="serve: contact steps per request")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="serve: HBM admission budget")
+    ap.add_argument("--slots", type=int, default=16, help="serve: most requests resident at once")
     ap.add_argument("--nx", type=int, default=0, help="pleated grid size (default: the full 256)")
     ap.add_argument("--cpu-nx", type=int, default=128, help="grid size of the oracle baseline sample")
     ap.add_argument("--ref-nx", type=int, default=96, help="grid size of a reference-arm step")
@@ -309,6 +382,9 @@ def main():
 
     if args.workload == "knit64":
         bench_batch(args, rank, world, local, dist)
+        return
+    if args.workload == "serve":
+        bench_serve(args, rank, world, local, dist)
         return
     sc, desc = _workload(args.workload, reduced_nx=args.nx or None)
     dev = torch.device("cuda", local)

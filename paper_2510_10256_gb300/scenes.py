@@ -198,6 +198,36 @@ def rod_batch(seed: int = BASE_SEED + 4, n_scenes: int = 64, n_lo: float = 1e3,
     return out
 
 
+def serve_pool(seed: int = BASE_SEED + 5, n_rod: int = 8, n_shell: int = 8, rod_lo: float = 5e3,
+               rod_hi: float = 2e5, tri_lo: float = 1e4, tri_hi: float = 5e5) -> list[Scene]:
+    """Scenes a served request stream draws from: rods with vertex counts and
+    shells with triangle counts log-uniform in the given ranges, seeded.  Rods
+    take the woven-patch parameters (r 0.1, segment 0.05, dhat 0.01, sigma
+    0.02), alternately plain weave and helix-loop knit; shells alternate the
+    pleated sheet (L 0.5, thickness 1, dhat 0.05, sigma 0.1) and the graded
+    twisted disk (0.1-4 mm edges, same thickness and dhat)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_rod):
+        n_t = int(round(math.exp(rng.uniform(math.log(rod_lo), math.log(rod_hi)))))
+        if i % 2 == 0:
+            sc = weave_sized(seed + 100 + i, n_t, 0.1, 0.05, 0.01, 0.02)
+        else:
+            sc = knit_rows(seed + 100 + i, n_t, 0.1, 0.05, 0.01, 0.02)
+        sc.meta = dict(sc.meta or {}, sigma=0.02)
+        out.append(sc)
+    for i in range(n_shell):
+        T = int(round(math.exp(rng.uniform(math.log(tri_lo), math.log(tri_hi)))))
+        if i % 2 == 0:
+            nx = max(8, int(round(1 + math.sqrt(T / 2.0))))
+            sc = pleated_sheet(seed=seed + 200 + i, nx=nx)
+        else:
+            sc = graded_disk(seed=seed + 200 + i, target_tris=T)
+        sc.meta = dict(sc.meta or {}, sigma=0.1)
+        out.append(sc)
+    return out
+
+
 def straight_rod(n_seg: int = 20, seg: float = 0.1, thickness: float = 0.25,
                  dhat: float = 0.05) -> Scene:
     """One straight uniform polyline along x (no jitter)."""
