@@ -37,6 +37,59 @@ FLOPS_PER_ACTIVE = 1.0e4
 L2_FLUSH_BYTES = 256 << 20
 
 
+def _peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _edge_count(scenes) -> int:
+    import numpy as np
+    E = 0
+    for sc in scenes:
+        if sc.kind == "rod":
+            E += sc.n - (len(sc.rod_ptr) - 1)
+        else:
+            t = np.asarray(sc.tris)
+            e = np.concatenate([np.sort(np.stack([t[a], t[b]], 1), 1) for a, b in ((0, 1), (1, 2), (0, 2))])
+            E += np.unique(e, axis=0).shape[0]
+    return E
+
+
+def stage_roofline(st: dict, med: list, scenes) -> dict:
+    """Per stage: algorithmic bytes (what the method must move: inputs read
+    once, outputs written once; no hash, sort or re-gather traffic) over the
+    stage's device time, against the measured HBM copy bandwidth; stage (d)
+    also against the FP64 peak.  Bytes per stage:
+      a  24n + 12T + 8E + 8|C|          (positions, topology, candidate keys)
+      b  16|C| + table                  (keys in, classes out; rods 12E, shells 4|F_rest|)
+      cd 8|C| + 24n + 8|A| + 24n + 76 nnzb + 4(n+1)  (keys+x in; active, gradient, BSR out)
+      e  8|C_ccd| + 48n + 8             (keys, x, p in; alpha out)"""
+    n = sum(sc.n for sc in scenes)
+    T = sum(sc.tris.shape[1] for sc in scenes if sc.kind == "shell")
+    E = _edge_count(scenes)
+    C, A, nnzb, Cc = st["n_candidates"], st["n_active"], st["nnzb"], st["n_ccd"]
+    shell = scenes[0].kind == "shell"
+    table = 4 * st["n_rest_filtered"] if shell else 12 * E
+    by = {"contact_build": 24 * n + 12 * T + 8 * E + 8 * C,
+          "contact_filter": 16 * C + table,
+          "barrier_eval": 8 * C + 24 * n + 8 * A + 24 * n + 76 * nnzb + 4 * (n + 1),
+          "ccd_step": 8 * Cc + 48 * n + 8}
+    hbm = _peaks().get("hbm_gbs")
+    out = {"hbm_peak_gbs": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)" if hbm else None}
+    for i, k in enumerate(("contact_build", "contact_filter", "barrier_eval", "ccd_step")):
+        ms = med[i]
+        gbs = by[k] / (ms / 1000.0) / 1e9 if ms > 0 else None
+        out[k] = {"bytes": int(by[k]), "ms": ms, "gbs": gbs, "hbm_frac": (gbs / hbm) if (gbs and hbm) else None}
+    hess = med[4]
+    out["hessian_kernels"] = {"ms": hess, "fp64_tflops": FLOPS_PER_ACTIVE * A / (hess / 1000.0) / 1e12 if hess > 0
+                              else None}
+    if hess > 0:
+        out["hessian_kernels"]["fp64_frac"] = out["hessian_kernels"]["fp64_tflops"] / FP64_PEAK_TFLOPS
+    return out
+
+
 def _workload(name: str, reduced_nx: int | None = None):
     from paper_2510_10256_gb300 import scenes as S
     if name == "pleated":
@@ -259,6 +312,10 @@ def bench_batch(args, rank, world, local, dist):
             "plain": {"value": world * n_cand / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
                       "form": f"{M} single-scene passes in sequence on one stream"},
             "batched_over_plain": pms / ms,
+            "stage_roofline": stage_roofline(st, med, scenes),
+            "fp32_broad_phase": {"candidates_fp32": st["n_candidates_fp32"], "candidates": n_cand,
+                                 "superset_ratio": st["n_candidates_fp32"] / max(1, n_cand),
+                                 "fp64_decided": st["n_fp64_decided"]},
             "stage_ms": {"contact_build": med[0], "contact_filter": med[1], "barrier_eval": med[2],
                          "ccd_step": med[3], "hessian_kernel": med[4]},
             "roofline": {"bound": "alu", "kernel": "k_hess_prep + k_hess_proj (FP64 stage d)", "achieved": achieved,
@@ -490,6 +547,10 @@ def main():
             "stage_ms": {"contact_build": med[0], "contact_filter": med[1], "barrier_eval": med[2],
                          "ccd_step": med[3], "hessian_kernel": med[4]},
             "roofline": roofline,
+            "stage_roofline": stage_roofline(st, med, [sc]),
+            "fp32_broad_phase": {"candidates_fp32": st["n_candidates_fp32"], "candidates": int(n_cand),
+                                 "superset_ratio": st["n_candidates_fp32"] / max(1, n_cand),
+                                 "fp64_decided": st["n_fp64_decided"]},
             "e2e": {"value": world * n_cand / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "clocks": clk, "gpu_launches": int(launches), "status": status}

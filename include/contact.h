@@ -106,6 +106,9 @@ typedef struct {
   int32_t status_bits;        /* device status word: 1 capacity, 2 penetration, 4 iteration limit */
   int32_t ccd_max_iters;
   int64_t device_bytes;       /* device memory held by the scene */
+  int64_t n_candidates_fp32;  /* last contact_build: non-incident pairs passing the FP32 box test
+                                 (a superset of the candidates; the FP32 effect on |C| is this / n_candidates) */
+  int64_t n_fp64_decided;     /* ... of which the FP32 test was not conclusive and the FP64 boxes decided */
 } cb_stats;
 
 /* Create a scene: uploads topology and rest positions, derives edges and

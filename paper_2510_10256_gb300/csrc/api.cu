@@ -613,6 +613,8 @@ cb_status cb_get_stats(cb_scene* s, cb_stats* o) {
   o->activation = s->a;
   o->status_bits = (int32_t)h[SC_STATUS];
   o->ccd_max_iters = (int32_t)h[SC_ITERS];
+  o->n_candidates_fp32 = (int64_t)h[SC_FP32_PAIRS];
+  o->n_fp64_decided = (int64_t)h[SC_FP64_DECIDED];
   size_t bytes = 0;
   const DevBuf* all[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->frest,
                          &s->frest_dbar, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls,

@@ -292,6 +292,7 @@ struct PairArgs {
   const double* __restrict__ box64;
   const Grid* __restrict__ grids;
   int bi, bj;
+  unsigned long long* fpstat;  // count pass: [0] FP32-accepted pairs, [1] FP64-decided (may be null)
 };
 
 // count pass (FILL = false): cnt[i] = number of pairs entry i reports;
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __re
   prim_verts(t, (int)P, pv);
   const uint64_t tbits = (uint64_t)type << (A.bi + A.bj);
   const uint64_t ipart = (uint64_t)(P - ibase) << A.bj;
-  uint32_t count = 0;
+  uint32_t count = 0, n32 = 0, n64 = 0;
   uint64_t w = FILL ? off[i] : 0;
   // the fill pass re-makes the count pass's decisions; never write past them
   const uint64_t w_end = FILL ? w + cnt[i] : 0;
@@ -359,7 +360,9 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __re
     const bool sure = nextup(plo.x) <= nextdn(qhi.x) && nextup(qlo.x) <= nextdn(phi.x) &&
                       nextup(plo.y) <= nextdn(qhi.y) && nextup(qlo.y) <= nextdn(phi.y) &&
                       nextup(plo.z) <= nextdn(qhi.z) && nextup(qlo.z) <= nextdn(phi.z);
+    ++n32;
     if (!sure) {
+      ++n64;
       const double* b1 = A.box64 + (size_t)P * 6;
       const double* b2 = A.box64 + (size_t)Q * 6;
       bool ok = true;
@@ -373,7 +376,17 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __re
       ++count;
     }
   }
-  if (!FILL) cnt[i] = count;
+  if (!FILL) {
+    cnt[i] = count;
+    if (A.fpstat) {  // one atomic per converged group of lanes
+      const unsigned mask = __activemask();
+      const unsigned a32 = __reduce_add_sync(mask, n32), a64 = __reduce_add_sync(mask, n64);
+      if ((int)(threadIdx.x & 31) == __ffs(mask) - 1) {
+        if (a32) atomicAdd(&A.fpstat[0], (unsigned long long)a32);
+        if (a64) atomicAdd(&A.fpstat[1], (unsigned long long)a64);
+      }
+    }
+  }
 }
 
 __global__ void k_expand(int64_t nc, const uint64_t* __restrict__ ck, int bi, int bj, uint64_t* __restrict__ out) {
@@ -531,6 +544,11 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   A.grids = dgrids;
   A.bi = s->bits_i;
   A.bj = s->bits_j;
+  A.fpstat = nullptr;
+  if (!swept) {
+    A.fpstat = (unsigned long long*)(scalars(s) + SC_FP32_PAIRS);
+    CB_CUDA(cudaMemsetAsync(A.fpstat, 0, 2 * sizeof(unsigned long long), st));
+  }
   k_pairs<false><<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint32_t>(w.pair_cnt), nullptr, nullptr);
   cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off), ne,
                                           bp<uint32_t>(w.scan_tmp), tot_dev, st);

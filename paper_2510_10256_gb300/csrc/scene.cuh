@@ -149,6 +149,8 @@ enum {
   SC_N9 = 9,
   SC_N6 = 10,
   SC_NLIST = 11,
+  SC_FP32_PAIRS = 12,   // broad phase of contact_build: pairs passing the FP32 box test
+  SC_FP64_DECIDED = 13, // ... of which the FP64 boxes decided
   SC_N = 16
 };
 
