@@ -90,6 +90,20 @@ def stage_roofline(st: dict, med: list, scenes) -> dict:
     return out
 
 
+def _autotune(args, runner, scenes, run_pass):
+    """Broad-phase knobs from the autotuner (cached per GPU and scene class)."""
+    if args.no_tune:
+        return {"autotuned": False, "cell_factor": [runner.tuning(0)[0], runner.tuning(1)[0]]}
+    import torch
+    from paper_2510_10256_gb300.tune import Autotuner, scene_key
+    key = scene_key(scenes, torch.cuda.get_device_name())
+    c = Autotuner().tune(runner, key, run_pass)
+    torch.cuda.synchronize()
+    return {"autotuned": True, "cached": c["cached"],
+            "build": {k: c["0"][k] for k in ("cell_factor", "pair_block", "stage_ms", "default_ms")},
+            "ccd": {k: c["1"][k] for k in ("cell_factor", "pair_block", "stage_ms", "default_ms")}}
+
+
 def _workload(name: str, reduced_nx: int | None = None):
     from paper_2510_10256_gb300 import scenes as S
     if name == "pleated":
@@ -248,6 +262,11 @@ def bench_batch(args, rank, world, local, dist):
         for k, m in enumerate(members):
             m.run_pass(xs[k], ps[k], es[k], gs[k], als[k])
 
+    tuning = _autotune(args, batch, scenes, run_batched)
+    if not args.no_plain:  # the plain arm uses the same knobs
+        for m in members:
+            for ph in (0, 1):
+                m.set_tuning(ph, *batch.tuning(ph))
     batch.set_timing(True)
     for _ in range(args.warmup):
         run_batched()
@@ -307,7 +326,7 @@ def bench_batch(args, rank, world, local, dist):
             "config": {"workload": f"{M} rod scenes (even: plain weave, odd: helix-loop knit), "
                                    f"{min(sizes)}-{max(sizes)} vertices each, {N} in all, batched",
                        "candidates": n_cand, "active": na, "ccd_pairs": int(st["n_ccd"]), "nnzb": int(st["nnzb"]),
-                       "ccd_max_iters": int(st["ccd_max_iters"]),
+                       "ccd_max_iters": int(st["ccd_max_iters"]), "tuning": tuning,
                        "l2": "flushed (256 MiB write) between steps", "parallelism": f"replicas x{world}"},
             "plain": {"value": world * n_cand / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
                       "form": f"{M} single-scene passes in sequence on one stream"},
@@ -413,6 +432,7 @@ def main():
     ap.add_argument("--ref-nx", type=int, default=96, help="grid size of a reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="knit64: skip the one-scene-per-launch arm")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default broad-phase knobs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -453,6 +473,7 @@ def main():
     grad = torch.zeros(3, sc.n, dtype=torch.float64, device=dev)
     alpha = torch.zeros(1, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    tuning = _autotune(args, cs, [sc], lambda: cs.run_pass(x, p, energy, grad, alpha))
     cs.set_timing(True)
     for _ in range(args.warmup):
         cs.run_pass(x, p, energy, grad, alpha)
@@ -542,7 +563,8 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "candidates": int(n_cand), "filtered": st["n_filtered"],
                        "core": st["n_core"], "active": int(na), "ccd_pairs": st["n_ccd"], "nnzb": st["nnzb"],
-                       "dbar_min": st["dbar_min"], "seed": sc.seed, "l2": "flushed (256 MiB write) between steps",
+                       "dbar_min": st["dbar_min"], "seed": sc.seed, "tuning": tuning,
+                       "l2": "flushed (256 MiB write) between steps",
                        "parallelism": f"replicas x{world}"},
             "stage_ms": {"contact_build": med[0], "contact_filter": med[1], "barrier_eval": med[2],
                          "ccd_step": med[3], "hessian_kernel": med[4]},

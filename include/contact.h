@@ -200,6 +200,15 @@ cb_status cb_sync_status(cb_scene* scene);
  * [0] contact_build, [1] contact_filter, [2] barrier_eval, [3] ccd_step,
  * [4] barrier_eval Hessian kernel alone.  sync. */
 cb_status cb_get_stage_ms(cb_scene* scene, float* ms5);
+/* Tuning knobs of a broad phase (no counterpart in the paper; no result
+ * depends on them, only speed).  phase 0: contact_build's broad phase, 1:
+ * ccd_step's swept broad phase.  cell_factor in (0, 64]: hash cell edge =
+ * factor x the members' mean primitive box extent (rounded to a quarter
+ * octave; default 1).  pair_block: threads per block of the pair enumeration,
+ * 64, 128 or 256 (default 256).  A batch starts from its first member's
+ * settings.  Errors: CB_ERR_ARG. */
+cb_status cb_set_tuning(cb_scene* scene, int32_t phase, float cell_factor, int32_t pair_block);
+cb_status cb_get_tuning(cb_scene* scene, int32_t phase, float* cell_factor, int32_t* pair_block);
 /* enable (1) / disable (0) the stage events; default off */
 cb_status cb_set_timing(cb_scene* scene, int32_t on);
 

@@ -30,7 +30,8 @@ ABI_FUNCTIONS = ["cb_scene_create", "cb_scene_destroy", "contact_build", "contac
                  "ccd_step", "cb_get_pairs", "cb_get_active", "cb_get_ccd", "cb_get_bsr", "cb_bsr_device",
                  "cb_get_stats", "cb_sync_status", "cb_get_stage_ms", "cb_set_timing", "cb_status_str",
                  "cb_version", "cb_kernel_launches", "cb_measure_fma_tflops", "cb_batch_create",
-                 "cb_batch_offsets", "cb_member_count", "ccd_step_noalloc"]
+                 "cb_batch_offsets", "cb_member_count", "ccd_step_noalloc", "cb_set_tuning",
+                 "cb_get_tuning"]
 
 
 class ContactError(RuntimeError):
@@ -95,6 +96,8 @@ def lib():
         L.cb_get_stage_ms.argtypes = [vp, C.POINTER(C.c_float)]
         L.cb_set_timing.argtypes = [vp, i32]
         L.ccd_step_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, i64, vp, vp, vp]
+        L.cb_set_tuning.argtypes = [vp, i32, C.c_float, i32]
+        L.cb_get_tuning.argtypes = [vp, i32, C.POINTER(C.c_float), C.POINTER(i32)]
         _lib = L
     return _lib
 
@@ -324,6 +327,15 @@ class ContactScene:
 
     def sync_status(self) -> int:
         return int(lib().cb_sync_status(self.h))
+
+    def set_tuning(self, phase: int, cell_factor: float, pair_block: int = 256):
+        """Broad-phase knobs (phase 0: contact_build, 1: ccd_step); speed only."""
+        _check(lib().cb_set_tuning(self.h, int(phase), float(cell_factor), int(pair_block)), "cb_set_tuning")
+
+    def tuning(self, phase: int) -> tuple[float, int]:
+        f, b = C.c_float(), C.c_int32()
+        _check(lib().cb_get_tuning(self.h, int(phase), C.byref(f), C.byref(b)), "cb_get_tuning")
+        return float(f.value), int(b.value)
 
     def set_timing(self, on: bool = True):
         _check(lib().cb_set_timing(self.h, int(on)), "cb_set_timing")

@@ -248,7 +248,6 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
   }
   s->dhat = d->dhat;
   s->kappa = d->kappa > 0.0 ? d->kappa : 1.0;
-  s->cell_hint = 1.0f;
   s->last_stream = st;
   cudaGetDevice(&s->device);
   s->count = 1;
@@ -302,7 +301,12 @@ cb_status cb_batch_create(cb_scene* const* members, int32_t count, void* stream,
   b->kind = members[0]->kind;
   b->count = count;
   b->last_stream = st;
-  b->cell_hint = members[0]->cell_hint;
+  for (int ph = 0; ph < 2; ++ph) {
+    BroadWork& dst = ph ? b->bwc : b->bw;
+    const BroadWork& src = ph ? members[0]->bwc : members[0]->bw;
+    dst.cell_factor = src.cell_factor;
+    dst.pair_block = src.pair_block;
+  }
   cudaGetDevice(&b->device);
   b->voff.assign(count + 1, 0);
   b->eoff.assign(count + 1, 0);
@@ -468,6 +472,23 @@ cb_status ccd_step(cb_scene* s, const double* x, const double* p, double* alpha,
   cb_status r = ccd_run(s, x, p, alpha, st);
   stage_end(s, 3, st);
   return r;
+}
+
+cb_status cb_set_tuning(cb_scene* s, int32_t phase, float cell_factor, int32_t pair_block) {
+  if (!s || (phase != 0 && phase != 1) || !(cell_factor > 0.0f) || !(cell_factor <= 64.0f)) return CB_ERR_ARG;
+  if (pair_block != 64 && pair_block != 128 && pair_block != 256) return CB_ERR_ARG;
+  BroadWork& w = phase ? s->bwc : s->bw;
+  w.cell_factor = cell_factor;
+  w.pair_block = pair_block;
+  return CB_OK;
+}
+
+cb_status cb_get_tuning(cb_scene* s, int32_t phase, float* cell_factor, int32_t* pair_block) {
+  if (!s || (phase != 0 && phase != 1)) return CB_ERR_ARG;
+  const BroadWork& w = phase ? s->bwc : s->bw;
+  if (cell_factor) *cell_factor = w.cell_factor;
+  if (pair_block) *pair_block = w.pair_block;
+  return CB_OK;
 }
 
 cb_status cb_set_timing(cb_scene* s, int32_t on) {

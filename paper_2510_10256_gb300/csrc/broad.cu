@@ -460,7 +460,7 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     // factor), rounded to a 1/4-octave grid so tiny summation-order
     // differences never change it
     const int npm = std::max(1, s->hmp[m].n_prims);
-    double c = (s->cell_hint > 0 ? (double)s->cell_hint : 1.0) * (ext_sum / npm);
+    double c = (w.cell_factor > 0 ? (double)w.cell_factor : 1.0) * (ext_sum / npm);
     if (!(c > 0)) c = 1.0;
     c = std::exp2(std::floor(std::log2(c) * 4.0) / 4.0);
     for (int k = 0; k < 3; ++k) {
@@ -549,7 +549,8 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     A.fpstat = (unsigned long long*)(scalars(s) + SC_FP32_PAIRS);
     CB_CUDA(cudaMemsetAsync(A.fpstat, 0, 2 * sizeof(unsigned long long), st));
   }
-  k_pairs<false><<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint32_t>(w.pair_cnt), nullptr, nullptr);
+  const int pb = w.pair_block;
+  k_pairs<false><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, bp<uint32_t>(w.pair_cnt), nullptr, nullptr);
   cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off), ne,
                                           bp<uint32_t>(w.scan_tmp), tot_dev, st);
   CB_CUDA(cudaGetLastError());
@@ -559,7 +560,7 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   *n_out = nc;
   if (nc == 0) return CB_OK;
   for (int b = 0; b < 2; ++b) CB_TRY(buf_ensure(w.ckey[b], sizeof(uint64_t) * (size_t)nc, st));
-  k_pairs<true><<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off),
+  k_pairs<true><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off),
                                                                 bp<uint64_t>(w.ckey[0]));
   const int cbits = s->bits_i + s->bits_j + (s->kind == CB_SHELL ? 2 : 0);
   CB_TRY(buf_ensure(w.hist, sizeof(uint32_t) * (size_t)cbp::radix_hist_elems(nc), st));

@@ -33,6 +33,8 @@ struct Grid {
 
 // Workspace of one broad phase (static or swept) -- reused between calls.
 struct BroadWork {
+  float cell_factor = 1.0f;  // hash cell edge = factor x mean primitive box extent (tuning knob)
+  int pair_block = CB_THREADS;  // threads per block of the pair enumeration (tuning knob)
   DevBuf box32;       // float4 lo, float4 hi per primitive
   DevBuf box64;       // double lo[3], hi[3] per primitive
   DevBuf bounds;      // per member: 6 x uint32 ordered-float min/max, 2 pad, double extent sum
@@ -63,7 +65,6 @@ struct cb_scene {
   int filter = CB_FILTER_DOUBLE;
   int core_temp = 1;
   double dbar_min = 0;  // +inf when nothing is filtered
-  float cell_hint = 0.f;
   // members (1 for a plain scene)
   int count = 1;
   std::vector<MemberParams> hmp;

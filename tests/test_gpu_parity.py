@@ -131,3 +131,30 @@ def test_graded_disk_full_size():
     oracle."""
     rep, g, o = _pair(S.graded_disk())
     assert rep["F"] > 0
+
+
+@pytest.mark.parametrize("factor,block", [(0.5, 128), (2.0, 64)])
+def test_tuning_knobs_change_nothing(factor, block):
+    """The broad-phase knobs the autotuner sets change speed only: every set
+    and value still matches the oracle."""
+    import torch
+    from paper_2510_10256_gb300.contact import ContactScene
+    sc = S.pleated_sheet(nx=32)
+    o = O.contact_pass(sc)
+    dev = torch.device("cuda:0")
+    cs = ContactScene.from_scene(sc)
+    for ph in (0, 1):
+        cs.set_tuning(ph, factor, block)
+        assert cs.tuning(ph) == (factor, block)
+    x = torch.from_numpy(sc.x).to(dev)
+    p = torch.from_numpy(sc.p).to(dev)
+    energy = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad = torch.zeros(3, sc.n, dtype=torch.float64, device=dev)
+    alpha = torch.zeros(1, dtype=torch.float64, device=dev)
+    cs.run_pass(x, p, energy, grad, alpha)
+    torch.cuda.synchronize()
+    g = dict(C=cs.pairs("candidate"), F=cs.pairs("filtered"), CC=cs.pairs("core"), A=cs.active(), ccd=cs.ccd(),
+             bsr=cs.bsr(), energy=float(energy.item()), grad=grad.cpu().numpy(), alpha=float(alpha.item()),
+             stats=cs.stats(), status=cs.sync_status(), frest=cs.pairs("rest_filtered"))
+    cs.close()
+    compare(sc, g, o)
