@@ -34,6 +34,10 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 # the 12x12 Hessian (~2.5e3) + one symmetric eigendecomposition of the 9x9
 # translation-free block with eigenvectors and the PSD rebuild (~7.5e3)
 FLOPS_PER_ACTIVE = 1.0e4
+# DRAM bytes (read + write) of the stage-(d) kernels per active pair, from one
+# ncu capture of the 128x128 pleated sheet (195,263 active pairs, 379.5 MB);
+# traffic grows in proportion to the active pairs
+HESS_DRAM_BYTES_PER_ACTIVE = 379.5e6 / 195263
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -556,7 +560,9 @@ def main():
     roofline = {"bound": "alu", "kernel": "k_hess_prep + k_hess_proj (FP64 stage d)", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_fp64_fma_measured": fp64_meas, "peak_fp32_fma_measured": fp32_meas,
-                "traffic": None, "flops_per_active_pair": FLOPS_PER_ACTIVE, "active_pairs": na,
+                "traffic": HESS_DRAM_BYTES_PER_ACTIVE * na,
+                "traffic_source": "ncu dram__bytes_read+write of the 128x128 case, scaled by active pairs",
+                "flops_per_active_pair": FLOPS_PER_ACTIVE, "active_pairs": na,
                 "kernel_ms": hess_ms, "peak_source": "derived: 152 SM x 2070 MHz x 4 FP64 flop/clk/SM"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
