@@ -71,3 +71,16 @@ def test_repeated_batches_match_the_oracle():
     for _ in range(4):
         for sc, g, o in zip(scenes, run_gpu_batch(scenes), orcs):
             compare(sc, g, o)
+
+
+@pytest.mark.slow
+def test_rod_batch_64_full_size():
+    """The full 64-scene rod batch (1.09 M vertices) in one batched pass,
+    every member against its own oracle."""
+    scenes = S.rod_batch()
+    res = run_gpu_batch(scenes)
+    total = 0
+    for sc, g in zip(scenes, res):
+        rep = compare(sc, g, O.contact_pass(sc))
+        total += rep["C"]
+    assert total > 5_000_000

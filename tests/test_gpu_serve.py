@@ -39,3 +39,18 @@ def test_served_results_equal_alone():
             assert np.isfinite(a.energy) and np.isfinite(b.energy)
             assert abs(a.energy - b.energy) <= 1e-9 * max(abs(b.energy), 1e-300), (r.rid, k, a.energy, b.energy)
     eng.close()
+
+
+@pytest.mark.slow
+def test_serve_pool_scenes_match_oracle():
+    """The served stream's scenes at full size (every rod, and the shells up
+    to 80k triangles; the two largest shells would take the brute-force
+    oracle minutes each) against the oracle.  Served results equal these
+    single-scene results (test above), so this pins the served stream too."""
+    from tests.parity import compare, run_gpu
+    import oracle as O
+    pool = S.serve_pool()
+    picked = [sc for sc in pool if sc.kind == "rod" or sc.tris.shape[1] <= 80_000]
+    assert sum(sc.kind == "shell" for sc in picked) >= 5
+    for sc in picked:
+        compare(sc, run_gpu(sc), O.contact_pass(sc))
