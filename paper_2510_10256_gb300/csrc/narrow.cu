@@ -392,7 +392,8 @@ __device__ void s_derivs(int kind, const d3* z, double* gs, double* Hs) {
     const double w[3] = {z[0].x, z[0].y, z[0].z}, u[3] = {z[1].x, z[1].y, z[1].z};
     const double al = w[0] * u[0] + w[1] * u[1] + w[2] * u[2];
     const double be = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const double ga = al / be;
+    const double ibe = 1.0 / be;  // one division; the rest multiply
+    const double ga = al * ibe;
     for (int k = 0; k < 3; ++k) {
       gs[k] = 2.0 * w[k] - 2.0 * ga * u[k];
       gs[3 + k] = -2.0 * ga * w[k] + 2.0 * ga * ga * u[k];
@@ -400,10 +401,10 @@ __device__ void s_derivs(int kind, const d3* z, double* gs, double* Hs) {
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) {
         const double dij = (i == j) ? 1.0 : 0.0;
-        const double ww = 2.0 * dij - 2.0 * u[i] * u[j] / be;
-        const double wu = -2.0 * u[i] * w[j] / be - 2.0 * ga * dij + 4.0 * ga * u[i] * u[j] / be;
-        const double uu = -2.0 * w[i] * w[j] / be + 4.0 * ga * (w[i] * u[j] + u[i] * w[j]) / be +
-                          2.0 * ga * ga * dij - 8.0 * ga * ga * u[i] * u[j] / be;
+        const double ww = 2.0 * dij - 2.0 * u[i] * u[j] * ibe;
+        const double wu = -2.0 * u[i] * w[j] * ibe - 2.0 * ga * dij + 4.0 * ga * u[i] * u[j] * ibe;
+        const double uu = -2.0 * w[i] * w[j] * ibe + 4.0 * ga * (w[i] * u[j] + u[i] * w[j]) * ibe +
+                          2.0 * ga * ga * dij - 8.0 * ga * ga * u[i] * u[j] * ibe;
         zh(Hs, i, j) = ww;
         zh(Hs, i, 3 + j) = wu;
         zh(Hs, 3 + j, i) = wu;
@@ -472,100 +473,6 @@ __device__ void s_derivs(int kind, const d3* z, double* gs, double* Hs) {
       Hs[(3 + i) * 9 + 6 + j] += uvb;
       Hs[(6 + j) * 9 + 3 + i] += uvb;
     }
-}
-
-// Cyclic Jacobi rotations on a symmetric n x n A (row-major, n <= 9),
-// accumulated into V (V <- V J); runs until the off-diagonal Frobenius norm
-// is at most sqrt(tol2) of the full norm, or max_sweeps.  The eigenvalues are
-// left on the diagonal of A.
-template <typename R>
-__device__ int jacobi_sweeps(R* A, R* V, const int n, const R tol2, const int max_sweeps) {
-  int sweep;
-  for (sweep = 0; sweep < max_sweeps; ++sweep) {
-    R off = 0, fro = 0;
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        const R a2 = A[i * n + j] * A[i * n + j];
-        fro += a2;
-        if (i != j) off += a2;
-      }
-    if (fro == R(0) || off <= tol2 * fro) break;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        const R apq = A[p * n + q];
-        if (apq == R(0)) continue;
-        const R tau = (A[q * n + q] - A[p * n + p]) / (R(2) * apq);
-        const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
-        const R c = R(1) / sqrt(R(1) + t * t), s = t * c;
-        for (int k = 0; k < n; ++k) {
-          const R akp = A[k * n + p], akq = A[k * n + q];
-          A[k * n + p] = c * akp - s * akq;
-          A[k * n + q] = s * akp + c * akq;
-        }
-        for (int k = 0; k < n; ++k) {
-          const R apk = A[p * n + k], aqk = A[q * n + k];
-          A[p * n + k] = c * apk - s * aqk;
-          A[q * n + k] = s * apk + c * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          const R vkp = V[k * n + p], vkq = V[k * n + q];
-          V[k * n + p] = c * vkp - s * vkq;
-          V[k * n + q] = s * vkp + c * vkq;
-        }
-      }
-  }
-  return sweep;
-}
-
-// Symmetric eigendecomposition for the PSD projection, FP32 first: Jacobi in
-// FP32 (the cheap pipe) finds the eigenvectors to ~1e-7; they are
-// re-orthonormalised in FP64 (modified Gram-Schmidt), the matrix is rotated
-// into that basis in FP64 (A = V^T B V), and FP64 Jacobi sweeps finish it to an
-// off-diagonal norm of 1e-14 ||A||.  Projection onto the PSD cone is
-// non-expansive in the Frobenius norm, so the projected matrix is then exact to
-// 1e-14 of ||B||.  On return the eigenvalues are on the diagonal of B and the
-// eigenvectors are the columns of V.
-__device__ void eig_mixed(double* B, double* V, const int n) {
-  double mx = 0.0;
-  for (int i = 0; i < n * n; ++i) mx = fmax(mx, fabs(B[i]));
-  for (int i = 0; i < n * n; ++i) V[i] = 0.0;
-  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
-  if (mx == 0.0) return;
-  float A32[81], V32[81];
-  const double inv = 1.0 / mx;
-  for (int i = 0; i < n * n; ++i) {
-    A32[i] = (float)(B[i] * inv);
-    V32[i] = 0.f;
-  }
-  for (int i = 0; i < n; ++i) V32[i * n + i] = 1.f;
-  jacobi_sweeps<float>(A32, V32, n, 1e-12f, 12);
-  for (int k = 0; k < n; ++k) {
-    for (int i = 0; i < n; ++i) V[i * n + k] = (double)V32[i * n + k];
-    for (int j = 0; j < k; ++j) {
-      double dp = 0.0;
-      for (int i = 0; i < n; ++i) dp += V[i * n + j] * V[i * n + k];
-      for (int i = 0; i < n; ++i) V[i * n + k] -= dp * V[i * n + j];
-    }
-    double nn = 0.0;
-    for (int i = 0; i < n; ++i) nn += V[i * n + k] * V[i * n + k];
-    nn = 1.0 / sqrt(nn);
-    for (int i = 0; i < n; ++i) V[i * n + k] *= nn;
-  }
-  double T[81];
-  for (int i = 0; i < n; ++i)
-    for (int k = 0; k < n; ++k) {
-      double v = 0.0;
-      for (int j = 0; j < n; ++j) v += B[i * n + j] * V[j * n + k];
-      T[i * n + k] = v;
-    }
-  for (int k = 0; k < n; ++k)
-    for (int l = k; l < n; ++l) {
-      double v = 0.0;
-      for (int i = 0; i < n; ++i) v += V[i * n + k] * T[i * n + l];
-      B[k * n + l] = v;
-      B[l * n + k] = v;
-    }
-  jacobi_sweeps<double>(B, V, n, 1e-28, 12);
 }
 
 __device__ __forceinline__ int64_t find_block(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -668,10 +575,10 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
     const double y = d - xi_p;
     double b, b1, b2;
     {
-      const double r = y - dh_p, l = log(y / dh_p);
+      const double r = y - dh_p, l = log(y / dh_p), iy = 1.0 / y;
       b = -(r * r) * l;
-      b1 = -2.0 * r * l - (r * r) / y;
-      b2 = -2.0 * l - 4.0 * r / y + (r * r) / (y * y);
+      b1 = -2.0 * r * l - (r * r) * iy;
+      b2 = -2.0 * l - 4.0 * r * iy + (r * r) * (iy * iy);
     }
     const double kap = P.kappa;
     e_local = kap * b;
@@ -694,7 +601,7 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
     if (kind == 0) {
       // point-point: H_z = kappa b'' n n^T + (kappa b'/d)(I - n n^T); clamp each part
       const double nh[3] = {gd[0], gd[1], gd[2]};
-      const double lam_n = fmax(kap * b2, 0.0), lam_t = fmax(kap * b1 / d, 0.0);
+      const double lam_n = fmax(kap * b2, 0.0), lam_t = fmax(kap * b1 * (2.0 * i2d), 0.0);
       double Hz[9];
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
@@ -715,7 +622,7 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
         if (used) pts[np++] = i;
       }
       const int nb = np - 1, D = 3 * nb;
-      const double c1 = kap * (b2 - b1 / d), c2 = kap * b1 * i2d;
+      const double c1 = kap * (b2 - b1 * (2.0 * i2d)), c2 = kap * b1 * i2d;
       // H_z in place of Hs
       for (int r = 0; r < 9; ++r)
         for (int q = 0; q < 9; ++q) Hs[r * 9 + q] = c1 * gd[r] * gd[q] + c2 * Hs[r * 9 + q];
@@ -831,6 +738,78 @@ __device__ __forceinline__ void jacobi_packed(R* Am, R* V, const int S, const R 
   }
 }
 
+// 1 / sqrt(u) for u >= 1 in FP64 without the FP64 square root and division:
+// the FP32 estimate (relative error < 1e-7) refined by two Newton steps
+// (error squared each time, so to FP64 rounding).
+__device__ __forceinline__ double rsqrt_refined(double u) {
+  double c = (double)rsqrtf((float)u);
+  c = c * (1.5 - 0.5 * u * c * c);
+  c = c * (1.5 - 0.5 * u * c * c);
+  return c;
+}
+
+// The FP64 sweeps of the projection, after the FP32 eigenvectors: cyclic
+// Jacobi where each rotation's tangent comes from FP32 arithmetic on values
+// scaled by the matrix norm, and the rotation itself is exact: c = 1/sqrt(1+t^2)
+// to FP64 rounding (rsqrt_refined), s = t c, and the 2x2 pivot block is
+// transformed with the full similarity formulas.  A tangent off by a relative
+// 1e-7 leaves a_pq at 1e-7 of its value -- quadratically small after the FP32
+// phase -- for the next sweep, while A stays an exact similarity of the input
+// and V stays orthonormal.  This avoids every FP64 division and square root
+// in the rotations.  Stops when off^2 <= tol2 ||A||^2.
+template <int D>
+__device__ __forceinline__ void jacobi_refine64(double* Am, double* V, const int S, const double tol2,
+                                                const int max_sweeps) {
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0, fro = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const double d = Am[tri_idx(i, i, D) * S];
+      fro += d * d;
+#pragma unroll
+      for (int j = i + 1; j < D; ++j) {
+        const double v = Am[tri_idx(i, j, D) * S];
+        off += 2.0 * v * v;
+      }
+    }
+    fro += off;
+    if (fro == 0.0 || off <= tol2 * fro) break;
+    const double nrm = sqrt(fro);
+    const double skip = 1e-16 * nrm;
+    const double inv = 1.0 / nrm;
+    for (int p = 0; p < D - 1; ++p)
+      for (int q = p + 1; q < D; ++q) {
+        const double apq = Am[tri_idx(p, q, D) * S];
+        if (fabs(apq) <= skip) continue;
+        const double app = Am[tri_idx(p, p, D) * S], aqq = Am[tri_idx(q, q, D) * S];
+        // |apq| > 1e-16 ||A||, so the scaled FP32 values stay normal
+        const float apq32 = (float)(apq * inv), dd32 = (float)((aqq - app) * inv);
+        const float tau = dd32 / (2.f * apq32);
+        const float t32 = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+        const double t = (double)t32;
+        const double c = rsqrt_refined(1.0 + t * t), s = t * c;
+        const double cc = c * c, ss = s * s, cs = c * s;
+        Am[tri_idx(p, p, D) * S] = cc * app - 2.0 * cs * apq + ss * aqq;
+        Am[tri_idx(q, q, D) * S] = ss * app + 2.0 * cs * apq + cc * aqq;
+        Am[tri_idx(p, q, D) * S] = cs * (app - aqq) + (cc - ss) * apq;
+        for (int k = 0; k < D; ++k) {
+          if (k == p || k == q) continue;
+          const int ikp = (k < p ? tri_idx(k, p, D) : tri_idx(p, k, D)) * S;
+          const int ikq = (k < q ? tri_idx(k, q, D) : tri_idx(q, k, D)) * S;
+          const double akp = Am[ikp], akq = Am[ikq];
+          Am[ikp] = c * akp - s * akq;
+          Am[ikq] = s * akp + c * akq;
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const double vkp = V[(k * D + p) * S], vkq = V[(k * D + q) * S];
+          V[(k * D + p) * S] = c * vkp - s * vkq;
+          V[(k * D + q) * S] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+
 template <int D>
 struct ProjSmem {
   static constexpr int NP = D * (D + 1) / 2;
@@ -891,7 +870,7 @@ __global__ void __launch_bounds__(128) k_hess_proj(HessArgs A, int64_t m) {
       }
       double nn = 0.0;
       for (int i = 0; i < D; ++i) nn += Vs[(i * D + k) * S] * Vs[(i * D + k) * S];
-      nn = rsqrt(nn);
+      nn = rsqrt_refined(nn);  // nn is 1 to FP32 accuracy here
       for (int i = 0; i < D; ++i) Vs[(i * D + k) * S] *= nn;
     }
   }
@@ -920,7 +899,7 @@ __global__ void __launch_bounds__(128) k_hess_proj(HessArgs A, int64_t m) {
         Ad[tri_idx(k, l, D) * S] = v;
       }
     }
-    jacobi_packed<double, D>(Ad, Vs, S, 1e-28, 12);
+    jacobi_refine64<D>(Ad, Vs, S, 1e-28, 12);
   }
   // B+ = V max(L,0) V^T (packed, over B which is dead)
   for (int i = 0; i < D; ++i)
