@@ -810,6 +810,15 @@ __device__ __forceinline__ void jacobi_refine64(double* Am, double* V, const int
   }
 }
 
+// Threads (= queued pairs) per block of the projection kernels.  One warp per
+// block: each block's warp moves through the FP32 and FP64 phases on its
+// own, so on every SM some warps keep the scarce FP64 pipe busy while others
+// are in their FP32 phase (with larger blocks the phase barrier would hold all
+// of an SM's warps in step).
+#ifndef PROJ_THREADS
+#define PROJ_THREADS 32
+#endif
+
 template <int D>
 struct ProjSmem {
   static constexpr int NP = D * (D + 1) / 2;
@@ -828,10 +837,9 @@ struct ProjSmem {
 // non-expansive in the Frobenius norm, so the projected matrix is exact to
 // 1e-14 of ||B||.  B+ = V max(L, 0) V^T is mapped back to the involved points
 // with K (x) I and scattered.
-template <int D>
-__global__ void __launch_bounds__(128) k_hess_proj(HessArgs A, int64_t m) {
+template <int D, int S>
+__global__ void __launch_bounds__(S) k_hess_proj(HessArgs A, int64_t m) {
   constexpr int NP = D * (D + 1) / 2;
-  constexpr int S = 128;
   extern __shared__ double smem[];
   const int tid = threadIdx.x;
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + tid;
@@ -1186,14 +1194,14 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     CB_TRY(read_scalars(s, SC_N9, 2, hq, st));
     const int64_t m9 = (int64_t)(uint32_t)hq[0], m6 = (int64_t)(uint32_t)hq[1];
     if (m9 > 0) {
-      const int smem = ProjSmem<9>::PER_THREAD * 128;
-      CB_CUDA(cudaFuncSetAttribute(k_hess_proj<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-      k_hess_proj<9><<<cb_grid(m9, 128), 128, smem, cb_count(st)>>>(A, m9);
+      const int smem = ProjSmem<9>::PER_THREAD * PROJ_THREADS;
+      CB_CUDA(cudaFuncSetAttribute(k_hess_proj<9, PROJ_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      k_hess_proj<9, PROJ_THREADS><<<cb_grid(m9, PROJ_THREADS), PROJ_THREADS, smem, cb_count(st)>>>(A, m9);
     }
     if (m6 > 0) {
-      const int smem = ProjSmem<6>::PER_THREAD * 128;
-      CB_CUDA(cudaFuncSetAttribute(k_hess_proj<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-      k_hess_proj<6><<<cb_grid(m6, 128), 128, smem, cb_count(st)>>>(A, m6);
+      const int smem = ProjSmem<6>::PER_THREAD * PROJ_THREADS;
+      CB_CUDA(cudaFuncSetAttribute(k_hess_proj<6, PROJ_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      k_hess_proj<6, PROJ_THREADS><<<cb_grid(m6, PROJ_THREADS), PROJ_THREADS, smem, cb_count(st)>>>(A, m6);
     }
     if (s->timing) cudaEventRecord(s->ev[11], st);
     CB_CUDA(cudaGetLastError());
