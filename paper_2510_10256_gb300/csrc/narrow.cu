@@ -909,17 +909,49 @@ __global__ void __launch_bounds__(S) k_hess_proj(HessArgs A, int64_t m) {
     }
     jacobi_refine64<D>(Ad, Vs, S, 1e-28, 12);
   }
-  // B+ = V max(L,0) V^T (packed, over B which is dead)
-  for (int i = 0; i < D; ++i)
-    for (int j = i; j < D; ++j) {
-      double v = 0.0;
-      for (int k = 0; k < D; ++k) {
-        const double lk = Ad[tri_idx(k, k, D) * S];
-        if (lk > 0.0) v += lk * Vs[(i * D + k) * S] * Vs[(j * D + k) * S];
+  // B+ from the side with fewer terms: sum over the positive eigenpairs of
+  // lam v v^T, or B minus the sum over the negative ones (B = V A V^T to the
+  // FP64 sweeps' tolerance).  The loop runs as many terms as the warp's
+  // busiest lane needs; each lane adds its own j-th term.
+  double lam[D];
+  int npos = 0, nneg = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    lam[k] = Ad[tri_idx(k, k, D) * S];
+    npos += lam[k] > 0.0;
+    nneg += lam[k] < 0.0;
+  }
+  const bool from_b = nneg < npos;
+  const int nterm = from_b ? nneg : npos;
+  const int wterm = __reduce_max_sync(__activemask(), nterm);
+  if (!from_b)
+    for (int e = 0; e < NP; ++e) Bs[e * S] = 0.0;
+  for (int j = 0; j < wterm; ++j) {
+    int k = -1, cnt = 0;
+    double wk = 0.0;
+#pragma unroll
+    for (int kk = 0; kk < D; ++kk) {
+      const bool sel = from_b ? lam[kk] < 0.0 : lam[kk] > 0.0;
+      if (sel && cnt == j) {
+        k = kk;
+        wk = from_b ? -lam[kk] : lam[kk];
       }
-      Bs[tri_idx(i, j, D) * S] = v;
+      cnt += sel;
     }
-  // scatter: block (q1, q2) of the involved points = sum_{ab, bb} K[q1][ab] K[q2][bb] B+[ab, bb]
+    if (k < 0) continue;
+    double v[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = Vs[(i * D + k) * S];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const double wi = wk * v[i];
+#pragma unroll
+      for (int jj = i; jj < D; ++jj) Bs[tri_idx(i, jj, D) * S] += wi * v[jj];
+    }
+  }
+  // scatter: block (q1, q2) of the involved points
+  //   = sum_ab K[q1][ab] R[q2][ab],  R[q2][ab] = sum_bb K[q2][bb] B+[ab, bb]
+  // (3x3 blocks; R for one q2 at a time)
   const uint32_t c = A.aidx[a];
   const Stencil st = stencil_of(A.cand[c], A.ev0, A.ev1, A.tv, A.T);
   const TypeInfo& TI = st.ee ? c_ee_types[A.ctype[c]] : c_pt_types[A.ctype[c]];
@@ -931,28 +963,37 @@ __global__ void __launch_bounds__(S) k_hess_proj(HessArgs A, int64_t m) {
     if (used) pts[np++] = i;
   }
   constexpr int NB = D / 3;
-  for (int q1 = 0; q1 < np; ++q1)
-    for (int q2 = q1; q2 < np; ++q2) {
-      double blk[9];
+  for (int q2 = 0; q2 < np; ++q2) {
+    double R[NB][9];
+#pragma unroll
+    for (int ab = 0; ab < NB; ++ab)
 #pragma unroll
       for (int al = 0; al < 3; ++al)
 #pragma unroll
         for (int be = 0; be < 3; ++be) {
           double v = 0.0;
 #pragma unroll
-          for (int ab = 0; ab < NB; ++ab)
-#pragma unroll
-            for (int bb = 0; bb < NB; ++bb) {
-              const int r = 3 * ab + al, cl = 3 * bb + be;
-              const double kk = (D == 9 ? c_K4[q1][ab] * c_K4[q2][bb] : c_K3[q1][ab] * c_K3[q2][bb]);
-              v += kk * Bs[(r <= cl ? tri_idx(r, cl, D) : tri_idx(cl, r, D)) * S];
-            }
-          blk[3 * al + be] = v;
+          for (int bb = 0; bb < NB; ++bb) {
+            const int r = 3 * ab + al, cl = 3 * bb + be;
+            const double kq = D == 9 ? c_K4[q2][bb] : c_K3[q2][bb];
+            v += kq * Bs[(r <= cl ? tri_idx(r, cl, D) : tri_idx(cl, r, D)) * S];
+          }
+          R[ab][3 * al + be] = v;
         }
+    for (int q1 = 0; q1 <= q2; ++q1) {
+      double blk[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        double v = 0.0;
+#pragma unroll
+        for (int ab = 0; ab < NB; ++ab) v += (D == 9 ? c_K4[q1][ab] : c_K3[q1][ab]) * R[ab][e];
+        blk[e] = v;
+      }
       const int r = st.v[pts[q1]], cc = st.v[pts[q2]];
       add_block(A, r, cc, blk, false);
       if (q1 != q2) add_block(A, cc, r, blk, true);
     }
+  }
 }
 
 __global__ void k_energy_final(int count, const unsigned long long* __restrict__ macc, double* __restrict__ out) {
