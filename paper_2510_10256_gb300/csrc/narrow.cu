@@ -533,6 +533,44 @@ __device__ __forceinline__ void add_block(const HessArgs& A, int r, int c, const
     for (int be = 0; be < 3; ++be) atomicAdd(&dst[3 * al + be], transpose ? blk[3 * be + al] : blk[3 * al + be]);
 }
 
+// The reduced matrix of one pair, B = c1 gB gB^T + c2 (M x I)^T hess s (M x I)
+// with gB = (M x I)^T grad d, written as a packed upper triangle into the
+// queue (element-major: entry e of slot at e * cap + slot).  D = 9 goes with
+// three z-vectors (plane types), D = 6 with two (point-edge).
+template <int D, int NZ>
+__device__ __forceinline__ void write_reduced(double* __restrict__ Bo, int64_t cap, unsigned slot,
+                                              const double (&M)[3][3], const double* gd, const double* Hs,
+                                              double c1, double c2) {
+  constexpr int NB = D / 3;
+  double gB[D];
+#pragma unroll
+  for (int ab = 0; ab < NB; ++ab)
+#pragma unroll
+    for (int al = 0; al < 3; ++al) {
+      double v = 0.0;
+#pragma unroll
+      for (int m = 0; m < NZ; ++m) v += M[m][ab] * gd[3 * m + al];
+      gB[3 * ab + al] = v;
+    }
+#pragma unroll
+  for (int row = 0; row < D; ++row) {
+    const int ab = row / 3, al = row % 3;
+#pragma unroll
+    for (int col = row; col < D; ++col) {
+      const int bb = col / 3, be = col % 3;
+      double h = 0.0;
+#pragma unroll
+      for (int m = 0; m < NZ; ++m) {
+        double hm = 0.0;
+#pragma unroll
+        for (int m2 = 0; m2 < NZ; ++m2) hm += M[m2][bb] * Hs[(3 * m + al) * 9 + 3 * m2 + be];
+        h += M[m][ab] * hm;
+      }
+      Bo[(size_t)tri_idx(row, col, D) * cap + slot] = c1 * gB[row] * gB[col] + c2 * h;
+    }
+  }
+}
+
 // Stage (d), part 1, one thread per active pair: barrier value and
 // derivatives, energy, gradient scatter, and the Hessian in the orthonormal
 // translation-free basis of the points the distance type involves,
@@ -543,7 +581,10 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
   double e_local = 0.0;
   int mem = -1;
   int want = 0;  // 9 or 6: reduced dimension of the queued matrix
-  double Bp[45];
+  // kept for the reduced matrix, written after the queue slot is known
+  double gd[9], Hs[81], M[3][3];
+  double c1 = 0.0, c2 = 0.0;
+  int nz = 0, nb = 0;
   if (a < A.na) {
     const uint32_t c = A.aidx[a];
     const uint64_t key = A.cand[c];
@@ -551,7 +592,7 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
     const int ty = A.ctype[c];
     const TypeInfo& TI = s.ee ? c_ee_types[ty] : c_pt_types[ty];
     const int kind = TI.kind;
-    const int nz = kind + 1;
+    nz = kind + 1;
     d3 X[4];
     for (int i = 0; i < 4; ++i) X[i] = load3(A.x, A.n, s.v[i]);
     d3 Pl[4];
@@ -582,9 +623,8 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
     }
     const double kap = P.kappa;
     e_local = kap * b;
-    double gs[9], Hs[81];
+    double gs[9];
     s_derivs(kind, z, gs, Hs);
-    double gd[9];
     const double i2d = 0.5 / d;
     for (int k = 0; k < 9; ++k) gd[k] = gs[k] * i2d;
     if (A.grad)
@@ -621,12 +661,9 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
         for (int m = 0; m < nz; ++m) used |= TI.C[m][i] != 0;
         if (used) pts[np++] = i;
       }
-      const int nb = np - 1, D = 3 * nb;
-      const double c1 = kap * (b2 - b1 * (2.0 * i2d)), c2 = kap * b1 * i2d;
-      // H_z in place of Hs
-      for (int r = 0; r < 9; ++r)
-        for (int q = 0; q < 9; ++q) Hs[r * 9 + q] = c1 * gd[r] * gd[q] + c2 * Hs[r * 9 + q];
-      double M[3][3];
+      nb = np - 1;
+      c1 = kap * (b2 - b1 * (2.0 * i2d));
+      c2 = kap * b1 * i2d;
       for (int m = 0; m < 3; ++m)
         for (int bb = 0; bb < 3; ++bb) {
           double v = 0.0;
@@ -635,30 +672,16 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
               v += (double)TI.C[m][pts[q]] * (np == 4 ? c_K4[q][bb] : c_K3[q][bb]);
           M[m][bb] = v;
         }
-      // T = H_z (M x I)  (3nz x D), then B = (M x I)^T T  (packed upper triangle)
-      double Tm[81];
-      for (int r = 0; r < 3 * nz; ++r)
-        for (int bb = 0; bb < nb; ++bb)
-          for (int be = 0; be < 3; ++be) {
-            double v = 0.0;
-            for (int m2 = 0; m2 < nz; ++m2) v += Hs[r * 9 + 3 * m2 + be] * M[m2][bb];
-            Tm[r * 9 + 3 * bb + be] = v;
-          }
-      for (int ab = 0; ab < nb; ++ab)
-        for (int al = 0; al < 3; ++al) {
-          const int row = 3 * ab + al;
-          for (int cl = row; cl < D; ++cl) {
-            double v = 0.0;
-            for (int m = 0; m < nz; ++m) v += M[m][ab] * Tm[(3 * m + al) * 9 + cl];
-            Bp[tri_idx(row, cl, D)] = v;
-          }
-        }
-      want = D;
+      want = 3 * nb;
     }
   }
-  // queue the reduced matrices (warp-aggregated slot allocation)
+  // queue slot (warp-aggregated allocation), then the reduced matrix
+  //   B = (M x I)^T H_z (M x I),  H_z = c1 grad d grad d^T + c2 hess s
+  //     = c1 gB gB^T + c2 (M x I)^T hess s (M x I),  gB = (M x I)^T grad d,
+  // written straight into the queue (packed upper triangle, element-major)
   const unsigned lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
+  unsigned slot = 0;
 #pragma unroll
   for (int which = 0; which < 2; ++which) {
     const int Dw = which == 0 ? 9 : 6;
@@ -668,13 +691,14 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
     const int leader = __ffs(m) - 1;
     if ((int)lane == leader) base = atomicAdd(which == 0 ? A.n9 : A.n6, (unsigned)__popc(m));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (want == Dw) {
-      const unsigned slot = base + __popc(m & lt);
-      double* Bo = which == 0 ? A.B9 : A.B6;
-      const int ne = Dw * (Dw + 1) / 2;
-      for (int e = 0; e < ne; ++e) Bo[(size_t)e * A.cap + slot] = Bp[e];
-      (which == 0 ? A.slot9 : A.slot6)[slot] = (uint32_t)a;
-    }
+    if (want == Dw) slot = base + __popc(m & lt);
+  }
+  if (want == 9) {
+    write_reduced<9, 3>(A.B9, A.cap, slot, M, gd, Hs, c1, c2);
+    A.slot9[slot] = (uint32_t)a;
+  } else if (want == 6) {
+    write_reduced<6, 2>(A.B6, A.cap, slot, M, gd, Hs, c1, c2);
+    A.slot6[slot] = (uint32_t)a;
   }
   // energy per member: one atomic per warp when the warp holds one member
   const int m0 = __shfl_sync(0xffffffffu, mem, 0);
