@@ -127,7 +127,8 @@ cb_status cb_scene_destroy(cb_scene* scene);
  * x, each inflated by a/2, overlap (closed intervals).  Runs an FP32 spatial
  * hash with outward-rounded boxes (a provable superset) and decides ambiguous
  * pairs in FP64.  x_dev: DEVICE [3][n] FP64, read during the call's kernels.
- * Result (scene-owned, sorted by key) is the input of the next three calls. */
+ * Result (scene-owned, kept in hash-cell order; the getters return it sorted
+ * by key) is the input of the next three calls. */
 cb_status contact_build(cb_scene* scene, const double* x_dev, void* stream);
 
 /* (b) Barrier filter, Sec. 3.2 / Eq. 1, 4: class F for a candidate whose

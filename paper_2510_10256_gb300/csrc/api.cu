@@ -438,7 +438,7 @@ cb_status contact_build(cb_scene* s, const double* x, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   s->last_stream = st;
   stage_begin(s, 0, st);
-  cb_status r = broad_phase(s, s->bw, x, nullptr, false, s->cand, &s->n_cand, st);
+  cb_status r = broad_phase(s, s->bw, x, nullptr, false, false, s->cand, &s->n_cand, st);
   stage_end(s, 0, st);
   s->n_active = 0;
   return r;
@@ -510,6 +510,42 @@ cb_status cb_get_stage_ms(cb_scene* s, float* ms) {
   return CB_OK;
 }
 
+// Ascending order of 64-bit keys on the host (the pass keeps its pair lists
+// in hash-cell order; the getters return them sorted): LSD radix sort of
+// (key, original index) with 16-bit digits, skipping digits that are equal
+// in every key.  idx (optional) receives the original positions.
+static void sort_keys(std::vector<uint64_t>& keys, std::vector<uint32_t>* idx) {
+  const size_t n = keys.size();
+  std::vector<uint32_t> ix(n), ix2(idx ? n : 0);
+  for (size_t i = 0; i < n; ++i) ix[i] = (uint32_t)i;
+  if (n < 2) {
+    if (idx) idx->swap(ix);
+    return;
+  }
+  uint64_t all_or = 0, all_and = ~0ull;
+  for (uint64_t k : keys) {
+    all_or |= k;
+    all_and &= k;
+  }
+  const uint64_t varying = all_or & ~all_and;
+  std::vector<uint64_t> k2(n);
+  std::vector<size_t> cnt(65537);
+  for (int sh = 0; sh < 64; sh += 16) {
+    if (((varying >> sh) & 0xffffull) == 0) continue;
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (size_t i = 0; i < n; ++i) ++cnt[((keys[i] >> sh) & 0xffff) + 1];
+    for (size_t d = 1; d < cnt.size(); ++d) cnt[d] += cnt[d - 1];
+    for (size_t i = 0; i < n; ++i) {
+      const size_t o = cnt[(keys[i] >> sh) & 0xffff]++;
+      k2[o] = keys[i];
+      if (idx) ix2[o] = ix[i];
+    }
+    keys.swap(k2);
+    if (idx) ix.swap(ix2);
+  }
+  if (idx) idx->swap(ix);
+}
+
 cb_status cb_get_pairs(cb_scene* s, int32_t which, uint64_t* keys, int64_t cap, int64_t* count) {
   if (!s || !count) return CB_ERR_ARG;
   cudaStream_t st = s->last_stream;
@@ -548,7 +584,10 @@ cb_status cb_get_pairs(cb_scene* s, int32_t which, uint64_t* keys, int64_t cap, 
   CB_CUDA(cudaStreamSynchronize(st));
   *count = (int64_t)res.size();
   if ((int64_t)res.size() > cap) return CB_ERR_CAPACITY;
-  if (keys && !res.empty()) memcpy(keys, res.data(), res.size() * sizeof(uint64_t));
+  if (keys && !res.empty()) {
+    sort_keys(res, nullptr);
+    memcpy(keys, res.data(), res.size() * sizeof(uint64_t));
+  }
   return CB_OK;
 }
 
@@ -569,11 +608,16 @@ cb_status cb_get_active(cb_scene* s, uint64_t* keys, double* dd, uint8_t* klass,
   CB_TRY(dl(c, s->ccls, s->n_cand, st));
   CB_TRY(dl(t, s->ctype, s->n_cand, st));
   CB_CUDA(cudaStreamSynchronize(st));
+  std::vector<uint64_t> ak(ai.size());
+  for (size_t q = 0; q < ai.size(); ++q) ak[q] = k[ai[q]];
+  std::vector<uint32_t> order;
+  sort_keys(ak, &order);
   for (size_t q = 0; q < ai.size(); ++q) {
-    if (keys) keys[q] = k[ai[q]];
-    if (dd) dd[q] = d[ai[q]];
-    if (klass) klass[q] = c[ai[q]];
-    if (dtype) dtype[q] = t[ai[q]];
+    const uint32_t src = ai[order[q]];
+    if (keys) keys[q] = ak[q];
+    if (dd) dd[q] = d[src];
+    if (klass) klass[q] = c[src];
+    if (dtype) dtype[q] = t[src];
   }
   return CB_OK;
 }
@@ -584,11 +628,21 @@ cb_status cb_get_ccd(cb_scene* s, uint64_t* keys, double* t, uint8_t* klass, int
   *count = s->n_ccd;
   if (s->n_ccd > cap) return CB_ERR_CAPACITY;
   if (s->n_ccd) {
-    if (keys) CB_CUDA(cudaMemcpyAsync(keys, s->ccd_keys.p, 8 * (size_t)s->n_ccd, cudaMemcpyDeviceToHost, st));
-    if (t) CB_CUDA(cudaMemcpyAsync(t, s->ccd_t.p, 8 * (size_t)s->n_ccd, cudaMemcpyDeviceToHost, st));
-    if (klass) CB_CUDA(cudaMemcpyAsync(klass, s->ccd_cls.p, (size_t)s->n_ccd, cudaMemcpyDeviceToHost, st));
+    std::vector<uint64_t> k;
+    std::vector<double> tt;
+    std::vector<uint8_t> cc;
+    CB_TRY(dl(k, s->ccd_keys, s->n_ccd, st));
+    if (t) CB_TRY(dl(tt, s->ccd_t, s->n_ccd, st));
+    if (klass) CB_TRY(dl(cc, s->ccd_cls, s->n_ccd, st));
+    CB_CUDA(cudaStreamSynchronize(st));
+    std::vector<uint32_t> order;
+    sort_keys(k, &order);
+    for (size_t q = 0; q < k.size(); ++q) {
+      if (keys) keys[q] = k[q];
+      if (t) t[q] = tt[order[q]];
+      if (klass) klass[q] = cc[order[q]];
+    }
   }
-  CB_CUDA(cudaStreamSynchronize(st));
   return CB_OK;
 }
 

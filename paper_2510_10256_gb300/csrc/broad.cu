@@ -293,6 +293,7 @@ struct PairArgs {
   const Grid* __restrict__ grids;
   int bi, bj;
   unsigned long long* fpstat;  // count pass: [0] FP32-accepted pairs, [1] FP64-decided (may be null)
+  bool canonical;              // fill pass: write canonical keys (else compact ones for the sort)
 };
 
 // count pass (FILL = false): cnt[i] = number of pairs entry i reports;
@@ -371,7 +372,8 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __re
       if (!ok) continue;
     }
     if (FILL) {
-      if (w < w_end) out[w++] = tbits | ipart | (uint64_t)(Q - jbase);
+      if (w < w_end)
+        out[w++] = A.canonical ? cb_key(type, P - ibase, Q - jbase) : (tbits | ipart | (uint64_t)(Q - jbase));
     } else {
       ++count;
     }
@@ -401,8 +403,8 @@ __global__ void k_expand(int64_t nc, const uint64_t* __restrict__ ck, int bi, in
 
 }  // namespace
 
-cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* p, bool swept, DevBuf& out,
-                      int64_t* n_out, cudaStream_t st) {
+cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* p, bool swept, bool sort_out,
+                      DevBuf& out, int64_t* n_out, cudaStream_t st) {
   const int np = s->n_prims;
   const int M = s->count;
   if (np == 0) {
@@ -545,6 +547,7 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   A.bi = s->bits_i;
   A.bj = s->bits_j;
   A.fpstat = nullptr;
+  A.canonical = false;
   if (!swept) {
     A.fpstat = (unsigned long long*)(scalars(s) + SC_FP32_PAIRS);
     CB_CUDA(cudaMemsetAsync(A.fpstat, 0, 2 * sizeof(unsigned long long), st));
@@ -559,9 +562,19 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   const int64_t nc = (uint32_t)hnc;
   *n_out = nc;
   if (nc == 0) return CB_OK;
+  if (!sort_out) {
+    // canonical keys straight from the fill pass, in hash-cell order
+    A.canonical = true;
+    CB_TRY(buf_ensure(out, sizeof(uint64_t) * (size_t)nc, st));
+    k_pairs<true><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off),
+                                                            bp<uint64_t>(out));
+    CB_CUDA(cudaGetLastError());
+    return CB_OK;
+  }
+  A.canonical = false;
   for (int b = 0; b < 2; ++b) CB_TRY(buf_ensure(w.ckey[b], sizeof(uint64_t) * (size_t)nc, st));
   k_pairs<true><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off),
-                                                                bp<uint64_t>(w.ckey[0]));
+                                                          bp<uint64_t>(w.ckey[0]));
   const int cbits = s->bits_i + s->bits_j + (s->kind == CB_SHELL ? 2 : 0);
   CB_TRY(buf_ensure(w.hist, sizeof(uint32_t) * (size_t)cbp::radix_hist_elems(nc), st));
   CB_TRY(buf_ensure(w.scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(cbp::radix_hist_elems(nc)) + 8),

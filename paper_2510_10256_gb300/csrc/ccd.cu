@@ -412,7 +412,7 @@ __global__ void k_macc_set(int count, unsigned long long* __restrict__ macc, int
 }  // namespace
 
 cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, cudaStream_t st) {
-  CB_TRY(broad_phase(s, s->bwc, x, p, true, s->ccd_keys, &s->n_ccd, st));
+  CB_TRY(broad_phase(s, s->bwc, x, p, true, false, s->ccd_keys, &s->n_ccd, st));
   uint64_t* sc = scalars(s);
   const int M = s->count;
   unsigned long long* macc = bp<unsigned long long>(s->macc);

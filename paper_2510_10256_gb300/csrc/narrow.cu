@@ -1062,7 +1062,7 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
     // rest broad phase at the full activation, then rest distances below a
     int64_t nr = 0;
     DevBuf rc;
-    CB_TRY(broad_phase(s, s->bw, bp<double>(s->rest), nullptr, false, rc, &nr, st));
+    CB_TRY(broad_phase(s, s->bw, bp<double>(s->rest), nullptr, false, true, rc, &nr, st));
     if (nr > 0) {
       DevBuf flag, pos, dbar;
       CB_TRY(buf_ensure(flag, sizeof(uint32_t) * (size_t)nr, st));

@@ -164,12 +164,13 @@ enum { MACC_E = 0, MACC_ALPHA = 1, MACC_LB = 2, MACC_STATUS = 3, MACC_LO = 4, MA
 cb_status read_scalars(cb_scene* s, int first, int count, uint64_t* out, cudaStream_t st);
 
 // broad.cu
-// Candidate pairs of x (p == nullptr) or of the sweep x -> x + p; boxes are
-// inflated by h.  Writes sorted canonical keys into *out (grown as needed) and
-// their count into *n_out.
-// Boxes are inflated per member by a/2 (static) or xi/2 (swept = true).
-cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* p, bool swept, DevBuf& out,
-                      int64_t* n_out, cudaStream_t st);
+// Candidate pairs of x (p == nullptr) or of the sweep x -> x + p.  Boxes are
+// inflated per member by a/2 (static) or xi/2 (swept = true).  Writes the
+// canonical keys into *out (grown as needed), in ascending order when
+// sort_out is set and otherwise in hash-cell order, and their count into
+// *n_out.
+cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* p, bool swept, bool sort_out,
+                      DevBuf& out, int64_t* n_out, cudaStream_t st);
 
 // narrow.cu
 cb_status filter_precompute(cb_scene* s, cudaStream_t st);
