@@ -811,6 +811,29 @@ __device__ __forceinline__ void jacobi_refine64(double* Am, double* V, const int
         const float tau = dd32 / (2.f * apq32);
         const float t32 = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
         const double t = (double)t32;
+        if (__all_sync(__activemask(), fabs(t) < 1e-8)) {
+          // small angle in every lane (warp-uniform, so no lane runs both
+          // paths): c = 1/sqrt(1+t^2) rounds to 1 in FP64, s = t; the residual
+          // a_pq (a relative 1e-7 of a_pq, below 1e-15 ||A||) is dropped
+          Am[tri_idx(p, p, D) * S] = app - t * apq;
+          Am[tri_idx(q, q, D) * S] = aqq + t * apq;
+          Am[tri_idx(p, q, D) * S] = 0.0;
+          for (int k = 0; k < D; ++k) {
+            if (k == p || k == q) continue;
+            const int ikp = (k < p ? tri_idx(k, p, D) : tri_idx(p, k, D)) * S;
+            const int ikq = (k < q ? tri_idx(k, q, D) : tri_idx(q, k, D)) * S;
+            const double akp = Am[ikp], akq = Am[ikq];
+            Am[ikp] = akp - t * akq;
+            Am[ikq] = akq + t * akp;
+          }
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const double vkp = V[(k * D + p) * S], vkq = V[(k * D + q) * S];
+            V[(k * D + p) * S] = vkp - t * vkq;
+            V[(k * D + q) * S] = vkq + t * vkp;
+          }
+          continue;
+        }
         const double c = rsqrt_refined(1.0 + t * t), s = t * c;
         const double cc = c * c, ss = s * s, cs = c * s;
         Am[tri_idx(p, p, D) * S] = cc * app - 2.0 * cs * apq + ss * aqq;
@@ -842,6 +865,10 @@ __device__ __forceinline__ void jacobi_refine64(double* Am, double* V, const int
 #ifndef PROJ_THREADS
 #define PROJ_THREADS 32
 #endif
+// squared relative off-diagonal norm at which the FP32 Jacobi phase stops
+#ifndef PROJ_FP32_TOL2
+#define PROJ_FP32_TOL2 1e-12f
+#endif
 
 template <int D>
 struct ProjSmem {
@@ -855,7 +882,7 @@ struct ProjSmem {
 // reduced matrix and the BSR scatter.  Every per-pair matrix lives in shared
 // memory laid out element-major ([element][thread]), so a warp touches 32
 // consecutive doubles per access.  The eigen-decomposition is FP32 first
-// (Jacobi on the cheap pipe to ~1e-6), then FP64: modified Gram-Schmidt on the
+// (Jacobi on the cheap pipe to ~1e-7), then FP64: modified Gram-Schmidt on the
 // eigenvectors, A = V^T B V, and symmetric Jacobi sweeps to an off-diagonal
 // norm of 1e-14 ||A|| (usually one sweep).  Projection onto the PSD cone is
 // non-expansive in the Frobenius norm, so the projected matrix is exact to
@@ -891,7 +918,7 @@ __global__ void __launch_bounds__(S) k_hess_proj(HessArgs A, int64_t m) {
     for (int e = 0; e < NP; ++e) A32[e * S] = (float)(Bs[e * S] * inv);
     for (int i = 0; i < D; ++i)
       for (int k = 0; k < D; ++k) V32[(i * D + k) * S] = (i == k) ? 1.f : 0.f;
-    jacobi_packed<float, D>(A32, V32, S, 1e-12f, 12);
+    jacobi_packed<float, D>(A32, V32, S, PROJ_FP32_TOL2, 12);
     // FP64 re-orthonormalisation of the FP32 eigenvectors (modified Gram-Schmidt)
     for (int k = 0; k < D; ++k) {
       for (int i = 0; i < D; ++i) Vs[(i * D + k) * S] = (double)V32[(i * D + k) * S];
