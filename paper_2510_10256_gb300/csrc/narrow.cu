@@ -714,7 +714,8 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
 
 // Cyclic Jacobi with symmetric updates on a packed upper-triangular matrix
 // held in shared memory (element e of this thread at Am[e * S]); rotations are
-// accumulated into V (V[(i * D + k) * S]).  Rotations with |a_pq| below
+// accumulated into V (column-major: row i of column k at V[(k * D + i) * S]).
+// Rotations with |a_pq| below
 // 1e-16 of the norm are skipped; stops when off^2 <= tol2 * ||A||^2.
 template <typename R, int D>
 __device__ __forceinline__ void jacobi_packed(R* Am, R* V, const int S, const R tol2, const int max_sweeps) {
@@ -754,9 +755,9 @@ __device__ __forceinline__ void jacobi_packed(R* Am, R* V, const int S, const R 
         }
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          const R vkp = V[(k * D + p) * S], vkq = V[(k * D + q) * S];
-          V[(k * D + p) * S] = c * vkp - s * vkq;
-          V[(k * D + q) * S] = s * vkp + c * vkq;
+          const R vkp = V[(p * D + k) * S], vkq = V[(q * D + k) * S];
+          V[(p * D + k) * S] = c * vkp - s * vkq;
+          V[(q * D + k) * S] = s * vkp + c * vkq;
         }
       }
   }
@@ -828,9 +829,9 @@ __device__ __forceinline__ void jacobi_refine64(double* Am, double* V, const int
           }
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            const double vkp = V[(k * D + p) * S], vkq = V[(k * D + q) * S];
-            V[(k * D + p) * S] = vkp - t * vkq;
-            V[(k * D + q) * S] = vkq + t * vkp;
+            const double vkp = V[(p * D + k) * S], vkq = V[(q * D + k) * S];
+            V[(p * D + k) * S] = vkp - t * vkq;
+            V[(q * D + k) * S] = vkq + t * vkp;
           }
           continue;
         }
@@ -849,9 +850,9 @@ __device__ __forceinline__ void jacobi_refine64(double* Am, double* V, const int
         }
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          const double vkp = V[(k * D + p) * S], vkq = V[(k * D + q) * S];
-          V[(k * D + p) * S] = c * vkp - s * vkq;
-          V[(k * D + q) * S] = s * vkp + c * vkq;
+          const double vkp = V[(p * D + k) * S], vkq = V[(q * D + k) * S];
+          V[(p * D + k) * S] = c * vkp - s * vkq;
+          V[(q * D + k) * S] = s * vkp + c * vkq;
         }
       }
   }
@@ -873,97 +874,112 @@ __device__ __forceinline__ void jacobi_refine64(double* Am, double* V, const int
 template <int D>
 struct ProjSmem {
   static constexpr int NP = D * (D + 1) / 2;
-  // per thread: B (NP doubles) | V (D*D doubles) | Z: A32 (NP floats) + V32 (D*D floats), later A (NP doubles)
-  static constexpr int Z_BYTES = ((NP + D * D) * 4 > NP * 8) ? (NP + D * D) * 4 : NP * 8;
-  static constexpr int PER_THREAD = NP * 8 + D * D * 8 + ((Z_BYTES + 7) / 8) * 8;
+  // per thread: V (D*D doubles, column-major; the FP32 eigenvectors occupy its
+  // first D*D floats during the FP32 phase) | A (NP doubles; the FP32 matrix in
+  // its first NP floats during the FP32 phase, then the FP64 matrix, then B+)
+  static constexpr int PER_THREAD = (D * D + NP) * 8;
 };
 
 // Stage (d), part 2, one thread per queued pair: PSD projection of the D x D
-// reduced matrix and the BSR scatter.  Every per-pair matrix lives in shared
-// memory laid out element-major ([element][thread]), so a warp touches 32
-// consecutive doubles per access.  The eigen-decomposition is FP32 first
-// (Jacobi on the cheap pipe to ~1e-7), then FP64: modified Gram-Schmidt on the
-// eigenvectors, A = V^T B V, and symmetric Jacobi sweeps to an off-diagonal
-// norm of 1e-14 ||A|| (usually one sweep).  Projection onto the PSD cone is
-// non-expansive in the Frobenius norm, so the projected matrix is exact to
-// 1e-14 of ||B||.  B+ = V max(L, 0) V^T is mapped back to the involved points
-// with K (x) I and scattered.
+// reduced matrix and the BSR scatter.  The input B stays in registers; the
+// eigenvectors V and the working matrix A live in shared memory laid out
+// element-major ([element][thread]), so a warp touches 32 consecutive words
+// per access, 1008 B per thread for D = 9.  The eigen-decomposition is FP32
+// first (Jacobi on the cheap pipe to ~1e-6), its arrays inside the V and A
+// regions; then FP64: modified Gram-Schmidt on the eigenvectors, A = V^T B V,
+// and symmetric Jacobi sweeps to an off-diagonal norm of 1e-14 ||A||.
+// Projection onto the PSD cone is non-expansive in the Frobenius norm, so the
+// projected matrix is exact to 1e-14 of ||B||.  B+ is mapped back to the
+// involved points with K (x) I and scattered.
 template <int D, int S>
 __global__ void __launch_bounds__(S) k_hess_proj(HessArgs A, int64_t m) {
   constexpr int NP = D * (D + 1) / 2;
   extern __shared__ double smem[];
   const int tid = threadIdx.x;
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + tid;
-  double* Bs = smem + tid;                          // [e * S]
-  double* Vs = smem + NP * S + tid;                 // [e * S]
-  char* zbase = (char*)(smem + (NP + D * D) * S);
-  float* A32 = (float*)zbase + tid;                 // [e * S] floats
-  float* V32 = (float*)zbase + NP * S + tid;        // [e * S] floats
-  // Ad shares its bytes with A32 / V32, and a double element of one thread
-  // covers float words of other threads: Ad is written only after the
-  // barrier below, when every thread of the block is done with A32 / V32.
-  double* Ad = (double*)zbase + tid;                // [e * S] doubles
-  const bool act = w < m;                           // no early exit: all threads reach the barrier
+  double* Vs = smem + tid;                            // V: row i of column k at [(k * D + i) * S]
+  double* Ad = smem + D * D * S + tid;                // A: element e at [e * S]
+  float* V32 = (float*)smem + tid;                    // FP32 V, same indexing, inside the V region
+  float* A32 = (float*)(smem + D * D * S) + tid;      // FP32 A, same indexing, inside the A region
+  const bool act = w < m;                             // no early exit before the last barrier
   const double* Bg = D == 9 ? A.B9 : A.B6;
   const uint32_t a = act ? (D == 9 ? A.slot9 : A.slot6)[w] : 0u;
+  // B stays in registers until B+ is formed
+  double Br[NP];
   double mx = 0.0;
-  if (act)
-    for (int e = 0; e < NP; ++e) {
-      const double v = Bg[(size_t)e * A.cap + w];
-      Bs[e * S] = v;
-      mx = fmax(mx, fabs(v));
-    }
-  if (act && mx != 0.0) {
+#pragma unroll
+  for (int e = 0; e < NP; ++e) {
+    Br[e] = act ? Bg[(size_t)e * A.cap + w] : 0.0;
+    mx = fmax(mx, fabs(Br[e]));
+  }
+  const bool work = act && mx != 0.0;
+  if (work) {
     const double inv = 1.0 / mx;
-    for (int e = 0; e < NP; ++e) A32[e * S] = (float)(Bs[e * S] * inv);
-    for (int i = 0; i < D; ++i)
-      for (int k = 0; k < D; ++k) V32[(i * D + k) * S] = (i == k) ? 1.f : 0.f;
+#pragma unroll
+    for (int e = 0; e < NP; ++e) A32[e * S] = (float)(Br[e] * inv);
+    for (int k = 0; k < D; ++k)
+      for (int i = 0; i < D; ++i) V32[(k * D + i) * S] = (i == k) ? 1.f : 0.f;
     jacobi_packed<float, D>(A32, V32, S, PROJ_FP32_TOL2, 12);
-    // FP64 re-orthonormalisation of the FP32 eigenvectors (modified Gram-Schmidt)
-    for (int k = 0; k < D; ++k) {
-      for (int i = 0; i < D; ++i) Vs[(i * D + k) * S] = (double)V32[(i * D + k) * S];
-      for (int j = 0; j < k; ++j) {
+  }
+  // FP64 re-orthonormalisation of the FP32 eigenvectors (modified Gram-Schmidt),
+  // columns in descending order.  Double column k takes the bytes of float
+  // columns 2k and 2k+1 (column 0: 0 and 1), all read before it is written:
+  // higher columns in earlier steps, column k itself before the barrier.
+  for (int k = D - 1; k >= 0; --k) {
+    double v[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = work ? (double)V32[(k * D + i) * S] : 0.0;
+    __syncthreads();
+    if (work) {
+      for (int j = k + 1; j < D; ++j) {
         double dp = 0.0;
-        for (int i = 0; i < D; ++i) dp += Vs[(i * D + j) * S] * Vs[(i * D + k) * S];
-        for (int i = 0; i < D; ++i) Vs[(i * D + k) * S] -= dp * Vs[(i * D + j) * S];
+#pragma unroll
+        for (int i = 0; i < D; ++i) dp += Vs[(j * D + i) * S] * v[i];
+#pragma unroll
+        for (int i = 0; i < D; ++i) v[i] -= dp * Vs[(j * D + i) * S];
       }
       double nn = 0.0;
-      for (int i = 0; i < D; ++i) nn += Vs[(i * D + k) * S] * Vs[(i * D + k) * S];
+#pragma unroll
+      for (int i = 0; i < D; ++i) nn += v[i] * v[i];
       nn = rsqrt_refined(nn);  // nn is 1 to FP32 accuracy here
-      for (int i = 0; i < D; ++i) Vs[(i * D + k) * S] *= nn;
+#pragma unroll
+      for (int i = 0; i < D; ++i) Vs[(k * D + i) * S] = v[i] * nn;
     }
   }
-  __syncthreads();
+  // from here on every thread touches only its own elements: no more barriers
   if (!act) return;
   // eigenvalues -> diagonal of Ad, eigenvectors -> Vs
-  if (mx == 0.0) {
+  if (!work) {
     for (int e = 0; e < NP; ++e) Ad[e * S] = 0.0;
-    for (int i = 0; i < D; ++i)
-      for (int k = 0; k < D; ++k) Vs[(i * D + k) * S] = (i == k) ? 1.0 : 0.0;
+    for (int k = 0; k < D; ++k)
+      for (int i = 0; i < D; ++i) Vs[(k * D + i) * S] = (i == k) ? 1.0 : 0.0;
   } else {
-    // A = V^T B V, column by column
+    // A = V^T B V, column by column (the FP32 A is dead: every thread passed
+    // the Gram-Schmidt barriers after its FP32 phase)
     for (int l = 0; l < D; ++l) {
-      double t[D];
+      double vl[D], t[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) vl[j] = Vs[(l * D + j) * S];
 #pragma unroll
       for (int i = 0; i < D; ++i) {
         double v = 0.0;
-        for (int j = 0; j < D; ++j)
-          v += Bs[(i <= j ? tri_idx(i, j, D) : tri_idx(j, i, D)) * S] * Vs[(j * D + l) * S];
+#pragma unroll
+        for (int j = 0; j < D; ++j) v += Br[i <= j ? tri_idx(i, j, D) : tri_idx(j, i, D)] * vl[j];
         t[i] = v;
       }
       for (int k = 0; k <= l; ++k) {
         double v = 0.0;
 #pragma unroll
-        for (int i = 0; i < D; ++i) v += Vs[(i * D + k) * S] * t[i];
+        for (int i = 0; i < D; ++i) v += Vs[(k * D + i) * S] * t[i];
         Ad[tri_idx(k, l, D) * S] = v;
       }
     }
     jacobi_refine64<D>(Ad, Vs, S, 1e-28, 12);
   }
-  // B+ from the side with fewer terms: sum over the positive eigenpairs of
-  // lam v v^T, or B minus the sum over the negative ones (B = V A V^T to the
-  // FP64 sweeps' tolerance).  The loop runs as many terms as the warp's
-  // busiest lane needs; each lane adds its own j-th term.
+  // B+ (into the A region) from the side with fewer terms: the sum over the
+  // positive eigenpairs of lam v v^T, or B minus the sum over the negative
+  // ones (B = V A V^T to the FP64 sweeps' tolerance).  The loop runs as many
+  // terms as the warp's busiest lane needs; each lane adds its own j-th term.
   double lam[D];
   int npos = 0, nneg = 0;
 #pragma unroll
@@ -975,8 +991,9 @@ __global__ void __launch_bounds__(S) k_hess_proj(HessArgs A, int64_t m) {
   const bool from_b = nneg < npos;
   const int nterm = from_b ? nneg : npos;
   const int wterm = __reduce_max_sync(__activemask(), nterm);
-  if (!from_b)
-    for (int e = 0; e < NP; ++e) Bs[e * S] = 0.0;
+  double* Bs = Ad;  // B+ replaces A
+#pragma unroll
+  for (int e = 0; e < NP; ++e) Bs[e * S] = from_b ? Br[e] : 0.0;
   for (int j = 0; j < wterm; ++j) {
     int k = -1, cnt = 0;
     double wk = 0.0;
@@ -992,7 +1009,7 @@ __global__ void __launch_bounds__(S) k_hess_proj(HessArgs A, int64_t m) {
     if (k < 0) continue;
     double v[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) v[i] = Vs[(i * D + k) * S];
+    for (int i = 0; i < D; ++i) v[i] = Vs[(k * D + i) * S];
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       const double wi = wk * v[i];
