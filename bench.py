@@ -35,9 +35,9 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 # translation-free block with eigenvectors and the PSD rebuild (~7.5e3)
 FLOPS_PER_ACTIVE = 1.0e4
 # DRAM bytes (read + write) of the stage-(d) kernels per active pair, from one
-# ncu capture of the 128x128 pleated sheet (195,263 active pairs, 379.5 MB);
+# ncu capture of the 128x128 pleated sheet (195,263 active pairs, 139.4 MB);
 # traffic grows in proportion to the active pairs
-HESS_DRAM_BYTES_PER_ACTIVE = 379.5e6 / 195263
+HESS_DRAM_BYTES_PER_ACTIVE = 139.4e6 / 195263
 L2_FLUSH_BYTES = 256 << 20
 
 
