@@ -511,10 +511,13 @@ struct HessArgs {
   // triangle, element-major ([e * cap + slot]); slot -> active pair index
   double* __restrict__ B9;
   double* __restrict__ B6;
+  double* __restrict__ B4;        // point-edge pairs in their own frame: 4x4 (10), 2x2 (3), frame (9)
   uint32_t* __restrict__ slot9;
   uint32_t* __restrict__ slot6;
+  uint32_t* __restrict__ slot4;
   unsigned int* __restrict__ n9;
   unsigned int* __restrict__ n6;
+  unsigned int* __restrict__ n4;
   int64_t cap;
 };
 
@@ -571,6 +574,44 @@ __device__ __forceinline__ void write_reduced(double* __restrict__ Bo, int64_t c
   }
 }
 
+// Point-edge pairs in their own frame: the 6x6 reduced matrix (rows 3 ab + al,
+// al the local axis) has no coupling between the e3 rows (2, 5) and the
+// rest, so only its in-plane 4x4 block (rows 0, 1, 3, 4; 10 packed entries)
+// and out-of-plane 2x2 block (rows 2, 5; 3 entries) are queued, followed by
+// the frame R (row-major, columns e1 e2 e3; 9 entries).
+__device__ __forceinline__ void write_reduced_pe(double* __restrict__ Bo, int64_t cap, unsigned slot,
+                                                 const double (&M)[3][3], const double* gd, const double* Hs,
+                                                 double c1, double c2, const double (&Rf)[9]) {
+  double gB[6];
+#pragma unroll
+  for (int ab = 0; ab < 2; ++ab)
+#pragma unroll
+    for (int al = 0; al < 3; ++al) gB[3 * ab + al] = M[0][ab] * gd[al] + M[1][ab] * gd[3 + al];
+  auto entry = [&](int row, int col) {
+    const int ab = row / 3, al = row % 3, bb = col / 3, be = col % 3;
+    double h = 0.0;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      double hm = 0.0;
+#pragma unroll
+      for (int m2 = 0; m2 < 2; ++m2) hm += M[m2][bb] * Hs[(3 * m + al) * 9 + 3 * m2 + be];
+      h += M[m][ab] * hm;
+    }
+    return c1 * gB[row] * gB[col] + c2 * h;
+  };
+  constexpr int L4[4] = {0, 1, 3, 4};
+  int e = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = i; j < 4; ++j) Bo[(size_t)(e++) * cap + slot] = entry(L4[i], L4[j]);
+  Bo[(size_t)10 * cap + slot] = entry(2, 2);
+  Bo[(size_t)11 * cap + slot] = entry(2, 5);
+  Bo[(size_t)12 * cap + slot] = entry(5, 5);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Bo[(size_t)(13 + k) * cap + slot] = Rf[k];
+}
+
 // Stage (d), part 1, one thread per active pair: barrier value and
 // derivatives, energy, gradient scatter, and the Hessian in the orthonormal
 // translation-free basis of the points the distance type involves,
@@ -582,7 +623,7 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
   int mem = -1;
   int want = 0;  // 9 or 6: reduced dimension of the queued matrix
   // kept for the reduced matrix, written after the queue slot is known
-  double gd[9], Hs[81], M[3][3];
+  double gd[9], Hs[81], M[3][3], Rf[9];
   double c1 = 0.0, c2 = 0.0;
   int nz = 0, nb = 0;
   if (a < A.na) {
@@ -673,6 +714,38 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
           M[m][bb] = v;
         }
       want = 3 * nb;
+      if (kind == 1) {
+        // Point-edge: in the frame e1 along the edge (u), e3 normal to the
+        // plane of the edge and the point (u x w), the configuration is
+        // symmetric under e3 -> -e3, so hess s and grad d have no coupling
+        // between the e3 components and the others: the reduced matrix splits
+        // into an in-plane 4x4 and an out-of-plane 2x2 block.  Evaluated at the
+        // local coordinates w' = (w.e1, w.e2, 0), u' = (|u|, 0, 0) the coupling
+        // entries are exactly zero.  The frame's direction error is about
+        // 1e-16 |w| |u| / |u x w|; beyond a ratio of 64 the pair stays on the
+        // generic 6x6 path.
+        const d3 w = z[0], u = z[1];
+        const d3 n = mk3(u.y * w.z - u.z * w.y, u.z * w.x - u.x * w.z, u.x * w.y - u.y * w.x);
+        const double ln = sqrt(n.x * n.x + n.y * n.y + n.z * n.z);
+        const double lu = sqrt(u.x * u.x + u.y * u.y + u.z * u.z);
+        const double lw = sqrt(w.x * w.x + w.y * w.y + w.z * w.z);
+        if (ln > 0.0 && lw * lu <= 64.0 * ln) {
+          const double iu = 1.0 / lu, inn = 1.0 / ln;
+          const d3 e1 = mk3(u.x * iu, u.y * iu, u.z * iu), e3 = mk3(n.x * inn, n.y * inn, n.z * inn);
+          const d3 e2 = mk3(e3.y * e1.z - e3.z * e1.y, e3.z * e1.x - e3.x * e1.z, e3.x * e1.y - e3.y * e1.x);
+          d3 zl[3];
+          zl[0] = mk3(w.x * e1.x + w.y * e1.y + w.z * e1.z, w.x * e2.x + w.y * e2.y + w.z * e2.z, 0.0);
+          zl[1] = mk3(lu, 0.0, 0.0);
+          zl[2] = mk3(0.0, 0.0, 0.0);
+          double gsl[9];
+          s_derivs(1, zl, gsl, Hs);
+          for (int k = 0; k < 9; ++k) gd[k] = gsl[k] * i2d;
+          Rf[0] = e1.x; Rf[1] = e2.x; Rf[2] = e3.x;
+          Rf[3] = e1.y; Rf[4] = e2.y; Rf[5] = e3.y;
+          Rf[6] = e1.z; Rf[7] = e2.z; Rf[8] = e3.z;
+          want = 4;
+        }
+      }
     }
   }
   // queue slot (warp-aggregated allocation), then the reduced matrix
@@ -683,13 +756,14 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
   const unsigned lt = (1u << lane) - 1u;
   unsigned slot = 0;
 #pragma unroll
-  for (int which = 0; which < 2; ++which) {
-    const int Dw = which == 0 ? 9 : 6;
+  for (int which = 0; which < 3; ++which) {
+    const int Dw = which == 0 ? 9 : (which == 1 ? 6 : 4);
     const unsigned m = __ballot_sync(0xffffffffu, want == Dw);
     if (!m) continue;
     unsigned base = 0;
     const int leader = __ffs(m) - 1;
-    if ((int)lane == leader) base = atomicAdd(which == 0 ? A.n9 : A.n6, (unsigned)__popc(m));
+    if ((int)lane == leader)
+      base = atomicAdd(which == 0 ? A.n9 : (which == 1 ? A.n6 : A.n4), (unsigned)__popc(m));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (want == Dw) slot = base + __popc(m & lt);
   }
@@ -699,6 +773,9 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
   } else if (want == 6) {
     write_reduced<6, 2>(A.B6, A.cap, slot, M, gd, Hs, c1, c2);
     A.slot6[slot] = (uint32_t)a;
+  } else if (want == 4) {
+    write_reduced_pe(A.B4, A.cap, slot, M, gd, Hs, c1, c2, Rf);
+    A.slot4[slot] = (uint32_t)a;
   }
   // energy per member: one atomic per warp when the warp holds one member
   const int m0 = __shfl_sync(0xffffffffu, mem, 0);
@@ -1064,6 +1141,308 @@ __global__ void __launch_bounds__(S) k_hess_proj(HessArgs A, int64_t m) {
   }
 }
 
+// Register-resident versions of the two Jacobi phases for the 4x4 block of
+// the point-edge path: the same arithmetic as jacobi_packed / jacobi_refine64
+// on arrays held in registers (every loop unrolled, every index static).  V
+// is column-major: row i of column k at V[k * D + i].
+template <typename R, int D>
+__device__ __forceinline__ void jacobi_reg(R (&Am)[D * (D + 1) / 2], R (&V)[D * D], const R tol2,
+                                           const int max_sweeps) {
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    R off = 0, fro = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      fro += Am[tri_idx(i, i, D)] * Am[tri_idx(i, i, D)];
+#pragma unroll
+      for (int j = i + 1; j < D; ++j) off += R(2) * Am[tri_idx(i, j, D)] * Am[tri_idx(i, j, D)];
+    }
+    fro += off;
+    if (fro == R(0) || off <= tol2 * fro) break;
+    const R skip = R(1e-16) * sqrt(fro);
+#pragma unroll
+    for (int p = 0; p < D - 1; ++p)
+#pragma unroll
+      for (int q = p + 1; q < D; ++q) {
+        const R apq = Am[tri_idx(p, q, D)];
+        if (fabs(apq) <= skip) continue;
+        const R app = Am[tri_idx(p, p, D)], aqq = Am[tri_idx(q, q, D)];
+        const R tau = (aqq - app) / (R(2) * apq);
+        const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
+        const R c = R(1) / sqrt(R(1) + t * t), s = t * c;
+        Am[tri_idx(p, p, D)] = app - t * apq;
+        Am[tri_idx(q, q, D)] = aqq + t * apq;
+        Am[tri_idx(p, q, D)] = R(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          if (k == p || k == q) continue;
+          const int ikp = k < p ? tri_idx(k, p, D) : tri_idx(p, k, D);
+          const int ikq = k < q ? tri_idx(k, q, D) : tri_idx(q, k, D);
+          const R akp = Am[ikp], akq = Am[ikq];
+          Am[ikp] = c * akp - s * akq;
+          Am[ikq] = s * akp + c * akq;
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const R vkp = V[p * D + k], vkq = V[q * D + k];
+          V[p * D + k] = c * vkp - s * vkq;
+          V[q * D + k] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void jacobi_refine64_reg(double (&Am)[D * (D + 1) / 2], double (&V)[D * D],
+                                                    const double tol2, const int max_sweeps) {
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0, fro = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      fro += Am[tri_idx(i, i, D)] * Am[tri_idx(i, i, D)];
+#pragma unroll
+      for (int j = i + 1; j < D; ++j) off += 2.0 * Am[tri_idx(i, j, D)] * Am[tri_idx(i, j, D)];
+    }
+    fro += off;
+    if (fro == 0.0 || off <= tol2 * fro) break;
+    const double nrm = sqrt(fro);
+    const double skip = 1e-16 * nrm;
+    const double inv = 1.0 / nrm;
+#pragma unroll
+    for (int p = 0; p < D - 1; ++p)
+#pragma unroll
+      for (int q = p + 1; q < D; ++q) {
+        const double apq = Am[tri_idx(p, q, D)];
+        if (fabs(apq) <= skip) continue;
+        const double app = Am[tri_idx(p, p, D)], aqq = Am[tri_idx(q, q, D)];
+        const float apq32 = (float)(apq * inv), dd32 = (float)((aqq - app) * inv);
+        const float tau = dd32 / (2.f * apq32);
+        const float t32 = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+        const double t = (double)t32;
+        const double c = rsqrt_refined(1.0 + t * t), s = t * c;
+        const double cc = c * c, ss = s * s, cs = c * s;
+        Am[tri_idx(p, p, D)] = cc * app - 2.0 * cs * apq + ss * aqq;
+        Am[tri_idx(q, q, D)] = ss * app + 2.0 * cs * apq + cc * aqq;
+        Am[tri_idx(p, q, D)] = cs * (app - aqq) + (cc - ss) * apq;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          if (k == p || k == q) continue;
+          const int ikp = k < p ? tri_idx(k, p, D) : tri_idx(p, k, D);
+          const int ikq = k < q ? tri_idx(k, q, D) : tri_idx(q, k, D);
+          const double akp = Am[ikp], akq = Am[ikq];
+          Am[ikp] = c * akp - s * akq;
+          Am[ikq] = s * akp + c * akq;
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const double vkp = V[p * D + k], vkq = V[q * D + k];
+          V[p * D + k] = c * vkp - s * vkq;
+          V[q * D + k] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+// PSD projection of a symmetric 4x4 (packed upper triangle) in registers:
+// FP32 Jacobi, FP64 Gram-Schmidt, A = V^T B V, FP64 sweeps, then B+ from the
+// side with fewer eigenpairs (as k_hess_proj).
+__device__ __forceinline__ void psd4(const double (&B)[10], double (&P)[10]) {
+  double mx = 0.0;
+#pragma unroll
+  for (int e = 0; e < 10; ++e) mx = fmax(mx, fabs(B[e]));
+  if (mx == 0.0) {
+#pragma unroll
+    for (int e = 0; e < 10; ++e) P[e] = 0.0;
+    return;
+  }
+  double V[16], Am[10];
+  {
+    float A32[10], V32[16];
+    const double inv = 1.0 / mx;
+#pragma unroll
+    for (int e = 0; e < 10; ++e) A32[e] = (float)(B[e] * inv);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) V32[e] = (e % 5 == 0) ? 1.f : 0.f;
+    jacobi_reg<float, 4>(A32, V32, PROJ_FP32_TOL2, 12);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) V[k * 4 + i] = (double)V32[k * 4 + i];
+#pragma unroll
+      for (int j = 0; j < k; ++j) {
+        double dp = 0.0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dp += V[j * 4 + i] * V[k * 4 + i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) V[k * 4 + i] -= dp * V[j * 4 + i];
+      }
+      double nn = 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) nn += V[k * 4 + i] * V[k * 4 + i];
+      nn = rsqrt_refined(nn);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) V[k * 4 + i] *= nn;
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    double t[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      double v = 0.0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v += B[i <= j ? tri_idx(i, j, 4) : tri_idx(j, i, 4)] * V[l * 4 + j];
+      t[i] = v;
+    }
+#pragma unroll
+    for (int k = 0; k <= l; ++k) {
+      double v = 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v += V[k * 4 + i] * t[i];
+      Am[tri_idx(k, l, 4)] = v;
+    }
+  }
+  jacobi_refine64_reg<4>(Am, V, 1e-28, 12);
+  double lam[4];
+  int npos = 0, nneg = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    lam[k] = Am[tri_idx(k, k, 4)];
+    npos += lam[k] > 0.0;
+    nneg += lam[k] < 0.0;
+  }
+  const bool from_b = nneg < npos;
+#pragma unroll
+  for (int e = 0; e < 10; ++e) P[e] = from_b ? B[e] : 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double wk = from_b ? (lam[k] < 0.0 ? -lam[k] : 0.0) : (lam[k] > 0.0 ? lam[k] : 0.0);
+    if (wk == 0.0) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const double wi = wk * V[k * 4 + i];
+#pragma unroll
+      for (int j = i; j < 4; ++j) P[tri_idx(i, j, 4)] += wi * V[k * 4 + j];
+    }
+  }
+}
+
+// PSD projection of a symmetric 2x2 [[a, b], [b, c]] in closed form: with
+// h = (a - c)/2, r = hypot(h, b), m = (a + c)/2 the eigenvalues are m +- r;
+// if one is positive and one negative the result is l+ v v^T with
+// v v^T = [[h + r, b], [b, r - h]] / (2 r), each entry formed without
+// cancellation (h + r = b^2 / (r - h) when h < 0, and the mirror case), and
+// l+ = m + r or det / (m - r) whichever avoids cancellation.
+__device__ __forceinline__ void psd2(double a, double b, double c, double& pa, double& pb, double& pc) {
+  const double h = 0.5 * (a - c), m = 0.5 * (a + c);
+  const double r = hypot(h, b);
+  const double lp = m + r, lm = m - r;
+  if (lm >= 0.0) {
+    pa = a;
+    pb = b;
+    pc = c;
+    return;
+  }
+  if (lp <= 0.0) {
+    pa = pb = pc = 0.0;
+    return;
+  }
+  const double det = fma(a, c, -b * b);
+  const double lpos = m >= 0.0 ? lp : det / lm;
+  const double hp = h >= 0.0 ? h + r : (b * b) / (r - h);
+  const double hm = h >= 0.0 ? (b * b) / (r + h) : r - h;
+  const double sc = lpos / (2.0 * r);
+  pa = sc * hp;
+  pb = sc * b;
+  pc = sc * hm;
+}
+
+// Stage (d), part 2 for point-edge pairs queued in their own frame: the 4x4
+// and 2x2 blocks are projected separately, the 6x6 result is rotated back
+// block by block (B+ = (I x R) B'+ (I x R)^T) and scattered as in
+// k_hess_proj<6>.
+__global__ void __launch_bounds__(128) k_hess_proj_pe(HessArgs A, int64_t m) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= m) return;
+  const uint32_t a = A.slot4[w];
+  double B4[10], R[9];
+#pragma unroll
+  for (int e = 0; e < 10; ++e) B4[e] = A.B4[(size_t)e * A.cap + w];
+  const double a2 = A.B4[(size_t)10 * A.cap + w], b2 = A.B4[(size_t)11 * A.cap + w],
+               c2 = A.B4[(size_t)12 * A.cap + w];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) R[k] = A.B4[(size_t)(13 + k) * A.cap + w];
+  double P4[10], p2[3];
+  psd4(B4, P4);
+  psd2(a2, b2, c2, p2[0], p2[1], p2[2]);
+  // B+ in the K3 basis, world axes: block (ab, bb) = R L(ab, bb) R^T with L
+  // the local 3x3 block (in-plane 2x2 from P4, e3-e3 entry from p2)
+  double Bp[21];
+#pragma unroll
+  for (int ab = 0; ab < 2; ++ab)
+#pragma unroll
+    for (int bb = ab; bb < 2; ++bb) {
+      double L[3][3];
+#pragma unroll
+      for (int al = 0; al < 2; ++al)
+#pragma unroll
+        for (int be = 0; be < 2; ++be) {
+          const int r = 2 * ab + al, cl = 2 * bb + be;
+          L[al][be] = P4[r <= cl ? tri_idx(r, cl, 4) : tri_idx(cl, r, 4)];
+        }
+      L[0][2] = L[1][2] = L[2][0] = L[2][1] = 0.0;
+      L[2][2] = p2[ab == bb ? (ab == 0 ? 0 : 2) : 1];
+      double T[3][3];  // R L
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int be = 0; be < 3; ++be) T[i][be] = R[3 * i] * L[0][be] + R[3 * i + 1] * L[1][be] + R[3 * i + 2] * L[2][be];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const int r = 3 * ab + i, cl = 3 * bb + j;
+          if (r > cl) continue;
+          Bp[tri_idx(r, cl, 6)] = T[i][0] * R[3 * j] + T[i][1] * R[3 * j + 1] + T[i][2] * R[3 * j + 2];
+        }
+    }
+  // scatter, as in k_hess_proj<6>
+  const uint32_t c = A.aidx[a];
+  const Stencil st = stencil_of(A.cand[c], A.ev0, A.ev1, A.tv, A.T);
+  const TypeInfo& TI = st.ee ? c_ee_types[A.ctype[c]] : c_pt_types[A.ctype[c]];
+  const int nz = TI.kind + 1;
+  int pts[4], np = 0;
+  for (int i = 0; i < 4; ++i) {
+    bool used = false;
+    for (int mm = 0; mm < nz; ++mm) used |= TI.C[mm][i] != 0;
+    if (used) pts[np++] = i;
+  }
+  for (int q2 = 0; q2 < np; ++q2) {
+    double Rq[2][9];
+#pragma unroll
+    for (int ab = 0; ab < 2; ++ab)
+#pragma unroll
+      for (int al = 0; al < 3; ++al)
+#pragma unroll
+        for (int be = 0; be < 3; ++be) {
+          double v = 0.0;
+#pragma unroll
+          for (int bb = 0; bb < 2; ++bb) {
+            const int r = 3 * ab + al, cl = 3 * bb + be;
+            v += c_K3[q2][bb] * Bp[r <= cl ? tri_idx(r, cl, 6) : tri_idx(cl, r, 6)];
+          }
+          Rq[ab][3 * al + be] = v;
+        }
+    for (int q1 = 0; q1 <= q2; ++q1) {
+      double blk[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) blk[e] = c_K3[q1][0] * Rq[0][e] + c_K3[q1][1] * Rq[1][e];
+      const int r = st.v[pts[q1]], cc = st.v[pts[q2]];
+      add_block(A, r, cc, blk, false);
+      if (q1 != q2) add_block(A, cc, r, blk, true);
+    }
+  }
+}
+
 __global__ void k_energy_final(int count, const unsigned long long* __restrict__ macc, double* __restrict__ out) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= count) return;
@@ -1286,22 +1665,29 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     A.status = status;
     CB_TRY(buf_ensure(s->hB9, sizeof(double) * 45 * (size_t)na, st));
     CB_TRY(buf_ensure(s->hB6, sizeof(double) * 21 * (size_t)na, st));
-    CB_TRY(buf_ensure(s->hslot, sizeof(uint32_t) * 2 * (size_t)na, st));
+    CB_TRY(buf_ensure(s->hB4, sizeof(double) * 22 * (size_t)na, st));
+    CB_TRY(buf_ensure(s->hslot, sizeof(uint32_t) * 3 * (size_t)na, st));
     A.B9 = bp<double>(s->hB9);
     A.B6 = bp<double>(s->hB6);
+    A.B4 = bp<double>(s->hB4);
     A.slot9 = bp<uint32_t>(s->hslot);
     A.slot6 = bp<uint32_t>(s->hslot) + na;
+    A.slot4 = bp<uint32_t>(s->hslot) + 2 * na;
     A.n9 = (unsigned int*)(sc + SC_N9);
     A.n6 = (unsigned int*)(sc + SC_N6);
+    A.n4 = (unsigned int*)(sc + SC_N4);
     A.cap = na;
     k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_N9), 0ull);
     k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_N6), 0ull);
+    k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_N4), 0ull);
     if (s->timing) cudaEventRecord(s->ev[10], st);
     k_hess_prep<<<cb_grid(na, 128), 128, 0, cb_count(st)>>>(A);
     CB_CUDA(cudaGetLastError());
-    uint64_t hq[2];
-    CB_TRY(read_scalars(s, SC_N9, 2, hq, st));
-    const int64_t m9 = (int64_t)(uint32_t)hq[0], m6 = (int64_t)(uint32_t)hq[1];
+    uint64_t hq[SC_N4 - SC_N9 + 1];
+    CB_TRY(read_scalars(s, SC_N9, SC_N4 - SC_N9 + 1, hq, st));
+    const int64_t m9 = (int64_t)(uint32_t)hq[0], m6 = (int64_t)(uint32_t)hq[SC_N6 - SC_N9],
+                  m4 = (int64_t)(uint32_t)hq[SC_N4 - SC_N9];
+    if (m4 > 0) k_hess_proj_pe<<<cb_grid(m4, 128), 128, 0, cb_count(st)>>>(A, m4);
     if (m9 > 0) {
       const int smem = ProjSmem<9>::PER_THREAD * PROJ_THREADS;
       CB_CUDA(cudaFuncSetAttribute(k_hess_proj<9, PROJ_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

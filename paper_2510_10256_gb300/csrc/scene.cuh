@@ -111,7 +111,7 @@ struct cb_scene {
   DevBuf bsr_val;       // double [nnzb][9]
   DevBuf row_cnt;       // uint32 [n+1]
   int64_t nnzb = 0;
-  DevBuf hB9, hB6;       // queued reduced Hessians (packed, element-major)
+  DevBuf hB9, hB6, hB4;  // queued reduced Hessians (packed, element-major); hB4: point-edge in its own frame
   DevBuf hslot;          // uint32 [2][na] active index of each queued matrix
   DevBuf xf, pf;         // float [3][n]: centred FP32 copies of x and of p
   DevBuf dlist;          // uint32: candidates / CCD pairs queued for the FP64 phase
@@ -150,6 +150,7 @@ enum {
   SC_N9 = 9,
   SC_N6 = 10,
   SC_NLIST = 11,
+  SC_N4 = 14,           // point-edge pairs queued in their own frame
   SC_FP32_PAIRS = 12,   // broad phase of contact_build: pairs passing the FP32 box test
   SC_FP64_DECIDED = 13, // ... of which the FP64 boxes decided
   SC_N = 16
