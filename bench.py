@@ -41,6 +41,17 @@ HESS_DRAM_BYTES_PER_ACTIVE = 139.4e6 / 195263
 L2_FLUSH_BYTES = 256 << 20
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings over all ranks (the slowest
+    replica sets the job's time); identity without a process group."""
+    if not dist:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def _peaks() -> dict:
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -298,10 +309,7 @@ def bench_batch(args, rank, world, local, dist):
     p_ms = _timed_steps(run_plain, args.steps, flush, stream) if not args.no_plain else [float("nan")]
     clk = clocks.stop()
     ms, pms = statistics.mean(b_ms), statistics.mean(p_ms)
-    if dist:
-        t = torch.tensor([ms, pms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, pms = float(t[0]), float(t[1])
+    ms, pms = max_over_ranks([ms, pms], dist, dev)
     # end to end: pinned host x, p in; energy, alpha, gradient out
     hx, hp = torch.from_numpy(hx_np).pin_memory(), torch.from_numpy(hp_np).pin_memory()
     he = torch.zeros(M, dtype=torch.float64).pin_memory()
@@ -379,10 +387,7 @@ def bench_serve(args, rank, world, local, dist):
     torch.cuda.synchronize()
     clk = clocks.stop()
     wall = rep["wall_s"]
-    if dist:
-        t = torch.tensor([wall], dtype=torch.float64, device=torch.device("cuda", local))
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        wall = float(t.item())
+    wall = max_over_ranks([wall], dist, torch.device("cuda", local))[0]
     eng.close()
     if rank != 0:
         return
@@ -507,10 +512,7 @@ def main():
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(step_ms)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks([ms], dist, dev)[0]
     value = world * n_cand / (ms / 1000.0)
     status = cs.sync_status()
 
@@ -535,10 +537,7 @@ def main():
         e_ev[k][1].record(stream)
         stream.synchronize()
     e2e_ms = statistics.mean(a.elapsed_time(b) for a, b in e_ev)
-    if dist:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks([e2e_ms], dist, dev)[0]
     h2d = 2 * 3 * sc.n * 8
     d2h = 8 + 8 + 3 * sc.n * 8
 
