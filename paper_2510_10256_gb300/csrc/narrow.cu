@@ -664,21 +664,57 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
     }
     const double kap = P.kappa;
     e_local = kap * b;
+    // Point-edge: in the frame e1 along the edge (u), e3 normal to the plane
+    // of the edge and the point (u x w), the configuration is symmetric under
+    // e3 -> -e3, so hess s and grad d have no coupling between the e3
+    // components and the others: the reduced matrix splits into an in-plane
+    // 4x4 and an out-of-plane 2x2 block.  Evaluated at the local coordinates
+    // w' = (w.e1, w.e2, 0), u' = (|u|, 0, 0) the coupling entries are exactly
+    // zero.  The frame's direction error is about 1e-16 |w| |u| / |u x w|;
+    // beyond a ratio of 64 the pair stays on the generic 6x6 path.
+    bool pe_local = false;
+    d3 zl[3];
+    if (kind == 1) {
+      const d3 w = z[0], u = z[1];
+      const d3 n = mk3(u.y * w.z - u.z * w.y, u.z * w.x - u.x * w.z, u.x * w.y - u.y * w.x);
+      const double ln = sqrt(n.x * n.x + n.y * n.y + n.z * n.z);
+      const double lu = sqrt(u.x * u.x + u.y * u.y + u.z * u.z);
+      const double lw = sqrt(w.x * w.x + w.y * w.y + w.z * w.z);
+      if (ln > 0.0 && lw * lu <= 64.0 * ln) {
+        const double iu = 1.0 / lu, inn = 1.0 / ln;
+        const d3 e1 = mk3(u.x * iu, u.y * iu, u.z * iu), e3 = mk3(n.x * inn, n.y * inn, n.z * inn);
+        const d3 e2 = mk3(e3.y * e1.z - e3.z * e1.y, e3.z * e1.x - e3.x * e1.z, e3.x * e1.y - e3.y * e1.x);
+        zl[0] = mk3(w.x * e1.x + w.y * e1.y + w.z * e1.z, w.x * e2.x + w.y * e2.y + w.z * e2.z, 0.0);
+        zl[1] = mk3(lu, 0.0, 0.0);
+        zl[2] = mk3(0.0, 0.0, 0.0);
+        Rf[0] = e1.x; Rf[1] = e2.x; Rf[2] = e3.x;
+        Rf[3] = e1.y; Rf[4] = e2.y; Rf[5] = e3.y;
+        Rf[6] = e1.z; Rf[7] = e2.z; Rf[8] = e3.z;
+        pe_local = true;
+      }
+    }
     double gs[9];
-    s_derivs(kind, z, gs, Hs);
+    s_derivs(kind, pe_local ? zl : z, gs, Hs);
     const double i2d = 0.5 / d;
     for (int k = 0; k < 9; ++k) gd[k] = gs[k] * i2d;
-    if (A.grad)
+    if (A.grad) {
+      // grad d in world axes (rotated back from the frame when in it)
+      double gw[9];
+      for (int m = 0; m < 3; ++m)
+        for (int i = 0; i < 3; ++i)
+          gw[3 * m + i] = pe_local ? Rf[3 * i] * gd[3 * m] + Rf[3 * i + 1] * gd[3 * m + 1] + Rf[3 * i + 2] * gd[3 * m + 2]
+                                   : gd[3 * m + i];
       for (int i = 0; i < 4; ++i) {
         bool used = false;
         for (int m = 0; m < nz; ++m) used |= TI.C[m][i] != 0;
         if (!used) continue;
         for (int al = 0; al < 3; ++al) {
           double v = 0.0;
-          for (int m = 0; m < nz; ++m) v += (double)TI.C[m][i] * gd[3 * m + al];
+          for (int m = 0; m < nz; ++m) v += (double)TI.C[m][i] * gw[3 * m + al];
           atomicAdd(&A.grad[(size_t)al * A.n + s.v[i]], kap * b1 * v);
         }
       }
+    }
     if (kind == 0) {
       // point-point: H_z = kappa b'' n n^T + (kappa b'/d)(I - n n^T); clamp each part
       const double nh[3] = {gd[0], gd[1], gd[2]};
@@ -713,39 +749,7 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
               v += (double)TI.C[m][pts[q]] * (np == 4 ? c_K4[q][bb] : c_K3[q][bb]);
           M[m][bb] = v;
         }
-      want = 3 * nb;
-      if (kind == 1) {
-        // Point-edge: in the frame e1 along the edge (u), e3 normal to the
-        // plane of the edge and the point (u x w), the configuration is
-        // symmetric under e3 -> -e3, so hess s and grad d have no coupling
-        // between the e3 components and the others: the reduced matrix splits
-        // into an in-plane 4x4 and an out-of-plane 2x2 block.  Evaluated at the
-        // local coordinates w' = (w.e1, w.e2, 0), u' = (|u|, 0, 0) the coupling
-        // entries are exactly zero.  The frame's direction error is about
-        // 1e-16 |w| |u| / |u x w|; beyond a ratio of 64 the pair stays on the
-        // generic 6x6 path.
-        const d3 w = z[0], u = z[1];
-        const d3 n = mk3(u.y * w.z - u.z * w.y, u.z * w.x - u.x * w.z, u.x * w.y - u.y * w.x);
-        const double ln = sqrt(n.x * n.x + n.y * n.y + n.z * n.z);
-        const double lu = sqrt(u.x * u.x + u.y * u.y + u.z * u.z);
-        const double lw = sqrt(w.x * w.x + w.y * w.y + w.z * w.z);
-        if (ln > 0.0 && lw * lu <= 64.0 * ln) {
-          const double iu = 1.0 / lu, inn = 1.0 / ln;
-          const d3 e1 = mk3(u.x * iu, u.y * iu, u.z * iu), e3 = mk3(n.x * inn, n.y * inn, n.z * inn);
-          const d3 e2 = mk3(e3.y * e1.z - e3.z * e1.y, e3.z * e1.x - e3.x * e1.z, e3.x * e1.y - e3.y * e1.x);
-          d3 zl[3];
-          zl[0] = mk3(w.x * e1.x + w.y * e1.y + w.z * e1.z, w.x * e2.x + w.y * e2.y + w.z * e2.z, 0.0);
-          zl[1] = mk3(lu, 0.0, 0.0);
-          zl[2] = mk3(0.0, 0.0, 0.0);
-          double gsl[9];
-          s_derivs(1, zl, gsl, Hs);
-          for (int k = 0; k < 9; ++k) gd[k] = gsl[k] * i2d;
-          Rf[0] = e1.x; Rf[1] = e2.x; Rf[2] = e3.x;
-          Rf[3] = e1.y; Rf[4] = e2.y; Rf[5] = e3.y;
-          Rf[6] = e1.z; Rf[7] = e2.z; Rf[8] = e3.z;
-          want = 4;
-        }
-      }
+      want = pe_local ? 4 : 3 * nb;
     }
   }
   // queue slot (warp-aggregated allocation), then the reduced matrix
