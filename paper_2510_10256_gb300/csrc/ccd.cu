@@ -63,6 +63,8 @@ struct CcdArgs {
   unsigned long long* __restrict__ max_iters;
   const float* __restrict__ xf;   // FP32 (x - member centre)
   const float* __restrict__ pf;   // FP32 p
+  uint32_t* __restrict__ ulist;   // pairs left unresolved by the first step (lb < 1)
+  unsigned int* __restrict__ nu;
 };
 
 __device__ __forceinline__ unsigned long long* macc_of(const CcdArgs& A, int m, int slot) {
@@ -189,7 +191,7 @@ __device__ __forceinline__ void warp_append(bool flag, uint32_t value, uint32_t*
 __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restrict__ lb_out,
                                                     uint32_t* __restrict__ list, unsigned int* __restrict__ nlist) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool need = false;
+  bool need = false, unres = false;
   double m_exact = 2.0, m_lb = 2.0;  // this lane's contributions to the two minima
   int mem = -1;
   if (q < A.np) {
@@ -238,10 +240,11 @@ __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restric
         const bool exact = tl_lb > 1.0 + 1e-9;
         const double t = exact ? 1.0 : tl_lb;
         A.t_out[q] = t;
-        lb_out[q] = exact ? 2.0 : t;
+        if (!exact) lb_out[q] = t;
         A.cls_out[q] = (uint8_t)cls | (exact ? EXACT : 0);
         if (exact) m_exact = t;
         else m_lb = t;
+        unres = !exact;
         need = false;
       }
     }
@@ -249,6 +252,7 @@ __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restric
   member_min_atomic(A, m_exact, mem, MACC_ALPHA);
   member_min_atomic(A, m_lb, mem, MACC_LB);
   warp_append(need, (uint32_t)q, list, nlist);
+  warp_append(unres, (uint32_t)q, A.ulist, A.nu);
 }
 
 // pass 1b: exact FP64 first step of the queued pairs
@@ -261,6 +265,8 @@ __global__ void __launch_bounds__(128) k_ccd_bound(CcdArgs A, double* __restrict
     const unsigned w = w0 + threadIdx.x;
     double m_exact = 2.0, m_lb = 2.0;
     int mem = -1;
+    bool unres = false;
+    uint32_t qq = 0;
     if (w < m) {
       const int64_t q = list[w];
       const AccdStart S = accd_start(A, q);
@@ -283,31 +289,20 @@ __global__ void __launch_bounds__(128) k_ccd_bound(CcdArgs A, double* __restrict
         }
       }
       A.t_out[q] = t;
-      lb_out[q] = exact ? 2.0 : t;  // 2: resolved (never selected again)
+      if (!exact) lb_out[q] = t;
       A.cls_out[q] = (uint8_t)S.cls | (exact ? EXACT : 0);
       if (exact) m_exact = t;
       else m_lb = t;
+      unres = !exact;
+      qq = (uint32_t)q;
     }
     member_min_atomic(A, m_exact, mem, MACC_ALPHA);
     member_min_atomic(A, m_lb, mem, MACC_LB);
+    warp_append(unres, qq, A.ulist, A.nu);
   }
 }
 
-// select unresolved pairs with lo < lb <= hi of their member
-__global__ void k_ccd_select(int64_t np, const uint64_t* __restrict__ keys, const int32_t* __restrict__ ev0,
-                             const int32_t* __restrict__ vsc, const double* __restrict__ lb,
-                             const unsigned long long* __restrict__ macc, uint32_t* __restrict__ flag) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= np) return;
-  const uint64_t key = keys[q];
-  const int v0 = cb_key_type(key) == CB_KEY_PT ? (int)cb_key_i(key) : ev0[cb_key_i(key)];
-  const int mem = vsc[v0];
-  const double lo = __longlong_as_double(macc[(size_t)mem * MACC_STRIDE + MACC_LO]);
-  const double hi = __longlong_as_double(macc[(size_t)mem * MACC_STRIDE + MACC_HI]);
-  flag[q] = (lb[q] > lo && lb[q] <= hi) ? 1u : 0u;
-}
-
-// the same over a list of pair indices: flag[w] for pair ulist[w]
+// select the listed pairs with lb <= hi of their member: flag[w] for pair ulist[w]
 __global__ void k_ccd_select_u(int64_t nu, const uint32_t* __restrict__ ulist, const uint64_t* __restrict__ keys,
                                const int32_t* __restrict__ ev0, const int32_t* __restrict__ vsc,
                                const double* __restrict__ lb, const unsigned long long* __restrict__ macc,
@@ -320,12 +315,6 @@ __global__ void k_ccd_select_u(int64_t nu, const uint32_t* __restrict__ ulist, c
   const int mem = vsc[v0];
   const double hi = __longlong_as_double(macc[(size_t)mem * MACC_STRIDE + MACC_HI]);
   flag[w] = lb[q] <= hi ? 1u : 0u;
-}
-
-__global__ void k_list(int64_t np, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
-                       uint32_t* __restrict__ list) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < np && flag[q]) list[pos[q]] = (uint32_t)q;
 }
 
 __global__ void k_list_u(int64_t nu, const uint32_t* __restrict__ ulist, const uint32_t* __restrict__ flag,
@@ -458,16 +447,21 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     A.xf = bp<float>(s->xf);
     A.pf = bp<float>(s->pf);
     CB_TRY(buf_ensure(s->dlist, sizeof(uint32_t) * (size_t)np, st));
+    CB_TRY(buf_ensure(s->ccd_ulist, sizeof(uint32_t) * (size_t)np, st));
     unsigned int* nl = (unsigned int*)(sc + SC_NLIST);
     k_set<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_NLIST), 0ull);
+    k_set<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_NU), 0ull);
+    A.ulist = bp<uint32_t>(s->ccd_ulist);
+    A.nu = (unsigned int*)(sc + SC_NU);
     k_ccd_screen<<<cb_grid(np, 128), 128, 0, cb_count(st)>>>(A, bp<double>(s->ccd_lb), bp<uint32_t>(s->dlist), nl);
     k_ccd_bound<<<std::min<int64_t>(cb_grid(np, 128), 152 * 16), 128, 0, cb_count(st)>>>(
         A, bp<double>(s->ccd_lb), bp<uint32_t>(s->dlist), nl);
     CB_CUDA(cudaGetLastError());
-    // Per member: the pairs left unresolved by pass 1 (lb <= 1) are gathered
-    // once; then rounds with ceiling h = 4 L, 16 L, ... (capped at 1) run until
-    // the member's minimum is <= h.  Members whose minimum is already below
-    // every remaining bound are done after pass 1.
+    // Per member: the pairs left unresolved by pass 1 (lb < 1, listed by the
+    // pass-1 kernels themselves) go through rounds with ceiling
+    // h = 4 L, 16 L, ... (capped at 1) until the member's minimum is <= h.
+    // Members whose minimum is already below every remaining bound are done
+    // after pass 1.
     std::vector<unsigned long long> hm((size_t)M * MACC_STRIDE);
     auto read_macc = [&]() -> cb_status {
       CB_CUDA(cudaMemcpyAsync(s->hstage_host, macc, sizeof(unsigned long long) * MACC_STRIDE * M,
@@ -509,19 +503,9 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     uint32_t* tot = (uint32_t*)(sc + SC_COUNT1);
     int64_t nu = 0;
     if (any) {
-      // gather the unresolved pairs (lb <= 1) of the members not yet done
-      CB_TRY(upload_band(lo, hi));
-      k_ccd_select<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(np, bp<uint64_t>(s->ccd_keys), bp<int32_t>(s->ev0),
-                                                                  bp<int32_t>(s->vsc), bp<double>(s->ccd_lb), macc,
-                                                                  bp<uint32_t>(s->ccd_flag));
-      cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(s->ccd_flag), bp<uint32_t>(s->ccd_pos), np,
-                                              bp<uint32_t>(s->scan_tmp), tot, st);
       uint64_t hn;
-      CB_TRY(read_scalars(s, SC_COUNT1, 1, &hn, st));
+      CB_TRY(read_scalars(s, SC_NU, 1, &hn, st));
       nu = (int64_t)(uint32_t)hn;
-      CB_TRY(buf_ensure(s->ccd_ulist, sizeof(uint32_t) * (size_t)std::max<int64_t>(nu, 1), st));
-      k_list<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(np, bp<uint32_t>(s->ccd_flag), bp<uint32_t>(s->ccd_pos),
-                                                           bp<uint32_t>(s->ccd_ulist));
       for (int m = 0; m < M; ++m)
         if (!done[m]) hi[m] = std::min(1.0, 4.0 * dbl(hm[(size_t)m * MACC_STRIDE + MACC_LB]));
       any = nu > 0;

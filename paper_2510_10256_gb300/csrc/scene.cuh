@@ -151,6 +151,7 @@ enum {
   SC_N6 = 10,
   SC_NLIST = 11,
   SC_N4 = 14,           // point-edge pairs queued in their own frame
+  SC_NU = 15,           // CCD pairs left unresolved by the first step
   SC_FP32_PAIRS = 12,   // broad phase of contact_build: pairs passing the FP32 box test
   SC_FP64_DECIDED = 13, // ... of which the FP64 boxes decided
   SC_N = 16
