@@ -35,9 +35,9 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 # translation-free block with eigenvectors and the PSD rebuild (~7.5e3)
 FLOPS_PER_ACTIVE = 1.0e4
 # DRAM bytes (read + write) of the stage-(d) kernels per active pair, from one
-# ncu capture of the 128x128 pleated sheet (195,263 active pairs, 139.4 MB);
+# ncu capture of the 128x128 pleated sheet (195,263 active pairs, 141.2 MB);
 # traffic grows in proportion to the active pairs
-HESS_DRAM_BYTES_PER_ACTIVE = 139.4e6 / 195263
+HESS_DRAM_BYTES_PER_ACTIVE = 141.2e6 / 195263
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -349,7 +349,7 @@ def bench_batch(args, rank, world, local, dist):
                                  "fp64_decided": st["n_fp64_decided"]},
             "stage_ms": {"contact_build": med[0], "contact_filter": med[1], "barrier_eval": med[2],
                          "ccd_step": med[3], "hessian_kernel": med[4]},
-            "roofline": {"bound": "alu", "kernel": "k_hess_prep + k_hess_proj (FP64 stage d)", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": "k_hess_prep + k_hess_proj<9> + k_hess_proj_pe (FP64 stage d)", "achieved": achieved,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                          "traffic": None, "flops_per_active_pair": FLOPS_PER_ACTIVE, "kernel_ms": hess_ms,
                          "peak_source": "derived: 152 SM x 2070 MHz x 4 FP64 flop/clk/SM"},
@@ -556,7 +556,7 @@ def main():
         fp32_meas = CT.measure_fma_tflops(False, iters=65536)
     except Exception:
         fp64_meas = fp32_meas = None
-    roofline = {"bound": "alu", "kernel": "k_hess_prep + k_hess_proj (FP64 stage d)", "achieved": achieved,
+    roofline = {"bound": "alu", "kernel": "k_hess_prep + k_hess_proj<9> + k_hess_proj_pe (FP64 stage d)", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_fp64_fma_measured": fp64_meas, "peak_fp32_fma_measured": fp32_meas,
                 "traffic": HESS_DRAM_BYTES_PER_ACTIVE * na,
