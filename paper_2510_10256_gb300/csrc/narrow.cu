@@ -579,35 +579,41 @@ __device__ __forceinline__ void write_reduced(double* __restrict__ Bo, int64_t c
 // rest, so only its in-plane 4x4 block (rows 0, 1, 3, 4; 10 packed entries)
 // and out-of-plane 2x2 block (rows 2, 5; 3 entries) are queued, followed by
 // the frame R (row-major, columns e1 e2 e3; 9 entries).
-__device__ __forceinline__ void write_reduced_pe(double* __restrict__ Bo, int64_t cap, unsigned slot,
-                                                 const double (&M)[3][3], const double* gd, const double* Hs,
-                                                 double c1, double c2, const double (&Rf)[9]) {
-  double gB[6];
+// At w' = (wx, wy, 0), u' = (lu, 0, 0) the Hessian of s = |w|^2 - (w.u)^2/|u|^2
+// has, per pair of axes, these 2x2 blocks over (w, u) (rows: first axis):
+//   (x, x): 0;  (x, y): [[0, -2 wy/lu], [0, 2 wx wy/lu^2]];  (y, x): its transpose;
+//   (y, y): [[2, -2 wx/lu], [-2 wx/lu, 2 (wx^2 - wy^2)/lu^2]];
+//   (z, z): [[2, -2 wx/lu], [-2 wx/lu, 2 wx^2/lu^2]];  the rest 0,
+// and grad d = (g0, g1) on the y axis only.  With H_z = c1 grad d grad d^T +
+// c2 hess s, block (ab, al; bb, be) of B is (M^T H_z[al, be] M)[ab][bb].
+__device__ __forceinline__ void write_reduced_pe_local(double* __restrict__ Bo, int64_t cap, unsigned slot,
+                                                       const double (&M)[3][3], double g0, double g1, double wx,
+                                                       double wy, double lu, double c1, double c2,
+                                                       const double (&Rf)[9]) {
+  const double il = 1.0 / lu;
+  const double hxy01 = c2 * (-2.0 * wy * il), hxy11 = c2 * (2.0 * wx * wy * il * il);
+  const double hwu = -2.0 * wx * il;
+  const double Hyy[2][2] = {{c1 * g0 * g0 + 2.0 * c2, c1 * g0 * g1 + c2 * hwu},
+                            {c1 * g0 * g1 + c2 * hwu, c1 * g1 * g1 + c2 * 2.0 * (wx * wx - wy * wy) * il * il}};
+  const double Hzz[2][2] = {{2.0 * c2, c2 * hwu}, {c2 * hwu, c2 * 2.0 * wx * wx * il * il}};
+  auto mhm = [&](const double (&H)[2][2], int ab, int bb) {
+    double v = 0.0;
 #pragma unroll
-  for (int ab = 0; ab < 2; ++ab)
+    for (int m = 0; m < 2; ++m)
 #pragma unroll
-    for (int al = 0; al < 3; ++al) gB[3 * ab + al] = M[0][ab] * gd[al] + M[1][ab] * gd[3 + al];
-  auto entry = [&](int row, int col) {
-    const int ab = row / 3, al = row % 3, bb = col / 3, be = col % 3;
-    double h = 0.0;
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      double hm = 0.0;
-#pragma unroll
-      for (int m2 = 0; m2 < 2; ++m2) hm += M[m2][bb] * Hs[(3 * m + al) * 9 + 3 * m2 + be];
-      h += M[m][ab] * hm;
-    }
-    return c1 * gB[row] * gB[col] + c2 * h;
+      for (int m2 = 0; m2 < 2; ++m2) v += M[m][ab] * H[m][m2] * M[m2][bb];
+    return v;
   };
-  constexpr int L4[4] = {0, 1, 3, 4};
-  int e = 0;
+  // (x, y) block: H = [[0, hxy01], [0, hxy11]] -> (M^T H M)[ab][bb]
+  auto mxy = [&](int ab, int bb) { return M[0][ab] * hxy01 * M[1][bb] + M[1][ab] * hxy11 * M[1][bb]; };
+  // 4x4 over (0,x), (0,y), (1,x), (1,y), packed upper triangle
+  const double e4[10] = {0.0,         mxy(0, 0),      0.0,       mxy(0, 1),      mhm(Hyy, 0, 0),
+                         mxy(1, 0),   mhm(Hyy, 0, 1), 0.0,       mxy(1, 1),      mhm(Hyy, 1, 1)};
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = i; j < 4; ++j) Bo[(size_t)(e++) * cap + slot] = entry(L4[i], L4[j]);
-  Bo[(size_t)10 * cap + slot] = entry(2, 2);
-  Bo[(size_t)11 * cap + slot] = entry(2, 5);
-  Bo[(size_t)12 * cap + slot] = entry(5, 5);
+  for (int e = 0; e < 10; ++e) Bo[(size_t)e * cap + slot] = e4[e];
+  Bo[(size_t)10 * cap + slot] = mhm(Hzz, 0, 0);
+  Bo[(size_t)11 * cap + slot] = mhm(Hzz, 0, 1);
+  Bo[(size_t)12 * cap + slot] = mhm(Hzz, 1, 1);
 #pragma unroll
   for (int k = 0; k < 9; ++k) Bo[(size_t)(13 + k) * cap + slot] = Rf[k];
 }
@@ -625,6 +631,7 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
   // kept for the reduced matrix, written after the queue slot is known
   double gd[9], Hs[81], M[3][3], Rf[9];
   double c1 = 0.0, c2 = 0.0;
+  double pwx = 0.0, pwy = 0.0, plu = 1.0;  // point-edge pair in its frame: w', |u|
   int nz = 0, nb = 0;
   if (a < A.na) {
     const uint32_t c = A.aidx[a];
@@ -693,10 +700,22 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
         pe_local = true;
       }
     }
-    double gs[9];
-    s_derivs(kind, pe_local ? zl : z, gs, Hs);
     const double i2d = 0.5 / d;
-    for (int k = 0; k < 9; ++k) gd[k] = gs[k] * i2d;
+    if (pe_local) {
+      // In the frame (w' = (wx, wy, 0), u' = (lu, 0, 0), s = wy^2) grad s has
+      // only the y components 2 wy (w) and -2 wx wy / lu (u); hess s is
+      // formed in write_reduced_pe_local
+      pwx = zl[0].x;
+      pwy = zl[0].y;
+      plu = zl[1].x;
+      for (int k = 0; k < 9; ++k) gd[k] = 0.0;
+      gd[1] = 2.0 * pwy * i2d;
+      gd[4] = -2.0 * pwx * pwy / plu * i2d;
+    } else {
+      double gs[9];
+      s_derivs(kind, z, gs, Hs);
+      for (int k = 0; k < 9; ++k) gd[k] = gs[k] * i2d;
+    }
     if (A.grad) {
       // grad d in world axes (rotated back from the frame when in it)
       double gw[9];
@@ -778,7 +797,7 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
     write_reduced<6, 2>(A.B6, A.cap, slot, M, gd, Hs, c1, c2);
     A.slot6[slot] = (uint32_t)a;
   } else if (want == 4) {
-    write_reduced_pe(A.B4, A.cap, slot, M, gd, Hs, c1, c2, Rf);
+    write_reduced_pe_local(A.B4, A.cap, slot, M, gd[1], gd[4], pwx, pwy, plu, c1, c2, Rf);
     A.slot4[slot] = (uint32_t)a;
   }
   // energy per member: one atomic per warp when the warp holds one member
