@@ -251,6 +251,16 @@ __global__ void k_cell_fill(Topo t, int np, const float4* __restrict__ box32, co
       }
 }
 
+// boxes in entry order, so that the pair loops read their run contiguously
+__global__ void k_gather_boxes(int64_t ne, const uint32_t* __restrict__ eval, const float4* __restrict__ box32,
+                               float4* __restrict__ ebox) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  const uint32_t q = eval[i];
+  ebox[2 * i] = box32[2 * (size_t)q];
+  ebox[2 * i + 1] = box32[2 * (size_t)q + 1];
+}
+
 __global__ void k_run_flag(int64_t ne, const uint64_t* __restrict__ key, uint32_t* __restrict__ flag) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ne) return;
@@ -289,6 +299,7 @@ struct PairArgs {
   const uint32_t* __restrict__ run_id;
   const uint32_t* __restrict__ run_start;
   const float4* __restrict__ box32;
+  const float4* __restrict__ ebox;   // boxes in entry order: entry j at [2 j], [2 j + 1]
   const double* __restrict__ box64;
   const Grid* __restrict__ grids;
   int bi, bj;
@@ -330,7 +341,7 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __re
     type = CB_KEY_EE;
     ibase = jbase = (uint32_t)(t.n + t.T);
   }
-  const float4 plo = A.box32[2 * (size_t)P], phi = A.box32[2 * (size_t)P + 1];
+  const float4 plo = A.ebox[2 * (size_t)i], phi = A.ebox[2 * (size_t)i + 1];
   int pv[3];
   prim_verts(t, (int)P, pv);
   const uint64_t tbits = (uint64_t)type << (A.bi + A.bj);
@@ -341,7 +352,7 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __re
   const uint64_t w_end = FILL ? w + cnt[i] : 0;
   for (int j = j0; j < j1; ++j) {
     const uint32_t Q = A.eval[j];
-    const float4 qlo = A.box32[2 * (size_t)Q], qhi = A.box32[2 * (size_t)Q + 1];
+    const float4 qlo = A.ebox[2 * (size_t)j], qhi = A.ebox[2 * (size_t)j + 1];
     if (!(plo.x <= qhi.x && qlo.x <= phi.x && plo.y <= qhi.y && qlo.y <= phi.y && plo.z <= qhi.z &&
           qlo.z <= phi.z))
       continue;
@@ -542,6 +553,9 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   A.run_id = bp<uint32_t>(w.run_id);
   A.run_start = bp<uint32_t>(w.run_start);
   A.box32 = bp<float4>(w.box32);
+  CB_TRY(buf_ensure(w.ebox, sizeof(float4) * 2 * (size_t)ne, st));
+  k_gather_boxes<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, eval, bp<float4>(w.box32), bp<float4>(w.ebox));
+  A.ebox = bp<float4>(w.ebox);
   A.box64 = bp<double>(w.box64);
   A.grids = dgrids;
   A.bi = s->bits_i;

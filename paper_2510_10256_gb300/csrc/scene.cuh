@@ -49,6 +49,7 @@ struct BroadWork {
   DevBuf run_start;   // uint32 per run (+1)
   DevBuf pair_cnt;    // uint32 per entry
   DevBuf pair_off;    // uint32 per entry (+1)
+  DevBuf ebox;        // float4 lo, float4 hi per entry (boxes gathered into entry order)
   DevBuf ckey[2];     // uint64 compact candidate keys (ping-pong)
   DevBuf scan_tmp;
   DevBuf hist;
