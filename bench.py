@@ -186,18 +186,40 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(nx: int) -> dict:
-    """The oracle as it stands on this host's cores, on a sub-grid of the same
-    pleated-sheet recipe (bounded sample)."""
+def _oracle_sample(scenes, what: str) -> dict:
+    """One full oracle pass (a-e) over each scene, timed on this host's cores."""
     import oracle as O
-    sc, _ = _workload("pleated", reduced_nx=nx)
     O.build()
     t0 = time.perf_counter()
-    r = O.contact_pass(sc)
+    nc = 0
+    for sc in scenes:
+        nc += O.contact_pass(sc).C.size
     dt = time.perf_counter() - t0
-    return {"value": r.C.size / dt, "unit": UNIT, "cores": O.lib().orc_num_threads(), "kind": "oracle",
-            "sample": f"one full oracle pass (a-e) on the pleated-sheet recipe at {nx}x{nx} vertices "
-                      f"(|C| = {r.C.size}, {dt:.1f} s); brute force O(n^2) pair enumeration"}
+    return {"value": nc / dt, "unit": UNIT, "cores": O.lib().orc_num_threads(), "kind": "oracle",
+            "sample": f"{what} (|C| = {nc}, {dt:.1f} s); brute force O(n^2) pair enumeration"}
+
+
+def cpu_baseline(workload: str, nx: int) -> dict:
+    """The oracle as it stands on this host's cores, on a bounded sample of
+    the same workload (seconds of CPU work)."""
+    from paper_2510_10256_gb300 import scenes as S
+    if workload == "pleated":
+        sc, _ = _workload("pleated", reduced_nx=nx)
+        return _oracle_sample([sc], f"one oracle pass on the pleated-sheet recipe at {nx}x{nx} vertices")
+    if workload == "woven":
+        sc, _ = _workload("woven")
+        return _oracle_sample([sc], "one oracle pass on the full woven patch")
+    if workload == "graded":
+        sc = S.graded_disk(target_tris=50_000, L0=0.2)
+        return _oracle_sample([sc], f"one oracle pass on the graded-disk recipe at {sc.tris.shape[1]} triangles")
+    if workload == "knit64":
+        scenes = S.rod_batch()[::4]
+        return _oracle_sample(scenes, f"one oracle pass on every fourth scene of the batch ({len(scenes)} scenes)")
+    if workload == "serve":
+        pool = S.serve_pool()
+        sample = [min((sc for sc in pool if sc.kind == k), key=lambda sc: sc.n) for k in ("rod", "shell")]
+        return _oracle_sample(sample, "one oracle pass on the smallest rod and the smallest shell of the pool")
+    raise ValueError(workload)
 
 
 def run_reference(args, rank: int, world: int):
@@ -356,6 +378,11 @@ def bench_batch(args, rank, world, local, dist):
             "e2e": {"value": world * n_cand / (e2e_ms / 1000.0), "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": 2 * 3 * N * 8, "d2h_bytes_per_step": 2 * M * 8 + 3 * N * 8},
             "clocks": clk, "gpu_launches": int(launches), "status": batch.sync_status()}
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_nx)
+        except Exception as e:  # the baseline is context; never fail the bench on it
+            line["cpu_baseline"] = {"value": None, "error": str(e)}
     print(json.dumps(line), flush=True)
 
 
@@ -421,6 +448,11 @@ def bench_serve(args, rank, world, local, dist):
                     "note": "the served stream is itself end to end: scenes uploaded from host memory at "
                             "admission, step results read back every step"},
             "clocks": clk, "gpu_launches": int(launches)}
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_nx)
+        except Exception as e:  # the baseline is context; never fail the bench on it
+            line["cpu_baseline"] = {"value": None, "error": str(e)}
     print(json.dumps(line), flush=True)
 
 
@@ -583,7 +615,7 @@ def main():
             "clocks": clk, "gpu_launches": int(launches), "status": status}
     if not args.no_cpu_baseline and world == 1:
         try:
-            line["cpu_baseline"] = cpu_baseline(args.cpu_nx)
+            line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_nx)
         except Exception as e:  # the baseline is context; never fail the bench on it
             line["cpu_baseline"] = {"value": None, "error": str(e)}
     print(json.dumps(line), flush=True)
