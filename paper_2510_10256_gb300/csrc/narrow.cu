@@ -375,10 +375,14 @@ __constant__ double c_K3[3][2] = {{0.70710678118654752440, 0.4082482904638630163
                                   {-0.70710678118654752440, 0.40824829046386301637},
                                   {0.0, -0.81649658092772603273}};
 
-__device__ __forceinline__ double& zh(double* H, int r, int c) { return H[r * 9 + c]; }
+__host__ __device__ __forceinline__ int tri_idx(int i, int j, int D) {  // packed upper triangle, i <= j
+  return i * D - (i * (i - 1)) / 2 + (j - i);
+}
+
+__host__ __device__ __forceinline__ double& zh(double* H, int r, int c) { return H[r * 9 + c]; }
 
 // gradient gs[9] and Hessian Hs[81] (row-major, 3x3 blocks of z) of s
-__device__ void s_derivs(int kind, const d3* z, double* gs, double* Hs) {
+__host__ __device__ void s_derivs(int kind, const d3* z, double* gs, double* Hs) {
   for (int i = 0; i < 81; ++i) Hs[i] = 0.0;
   for (int i = 0; i < 9; ++i) gs[i] = 0.0;
   if (kind == 0) {
@@ -475,6 +479,114 @@ __device__ void s_derivs(int kind, const d3* z, double* gs, double* Hs) {
     }
 }
 
+// Reduced barrier Hessian of a plane-type pair (point-triangle face,
+// edge-edge interior) in the translation-free coordinates y of its four
+// points, z = (M x I) y, differentiating the distance itself:
+//   d = |g| / sqrt(N),  g = w.(u x v),  N = |n|^2,  n = u x v,
+//   grad d = sg gam (grad g - h grad N),  gam = 1/sqrt(N), h = g / (2N), sg = sign g,
+//   hess d = sg gam (hess g - h hess N - (grad g grad N^T + grad N grad g^T) / (2N)
+//                    + (3h / (2N)) grad N grad N^T),
+//   B = kappa b'' grad d grad d^T + kappa b' hess d.
+// (Through s = d^2 instead, B = (b'' - b'/d) grad d grad d^T + b'/(2d) hess s
+// adds and then cancels a term of order |grad g|^2 / N, which for
+// near-parallel edges or slender triangles costs about 1/sin of the angle
+// in digits.)  With q_b = M[2][b] u - M[1][b] v (so dn/dy_b = [q_b]x):
+//   grad_y g = (M^T x I) grad_z g,   grad_y N = (M^T x I) grad_z N,
+//   hess_y g, block (a,b) = [r_ab]x,
+//     r_ab = -(M0a M1b - M1a M0b) v + (M0a M2b - M2a M0b) u - (M1a M2b - M2a M1b) w,
+//   hess_y N, block (a,b) = 2 (q_a.q_b) I - 2 q_b q_a^T + 2 (M2a M1b - M1a M2b) [n]x.
+// With e = grad_y g - h grad_y N the rank-one part is
+//   kappa b'' gam^2 e e^T - (s1 / 2N)(e gN^T + gN e^T) + (h s1 / 2N) gN gN^T,
+// s1 = kappa b' sg gam, gN = grad_y N.  Writes grad_z d (gd, 9) and the
+// packed upper triangle of B (Bq, 45); kb1 = kappa b', kb2 = kappa b''.
+__host__ __device__ __forceinline__ void plane_reduced(const double (&z)[3][3], const double (&M)[3][3], double kb1,
+                                                       double kb2, double (&gd)[9], double (&Bq)[45]) {
+  const double* w = z[0];
+  const double* u = z[1];
+  const double* v = z[2];
+  const double n[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+  const double g = w[0] * n[0] + w[1] * n[1] + w[2] * n[2];
+  const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const double vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  const double uv = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+  const double N = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+  const double gam = 1.0 / sqrt(N), iN = gam * gam;
+  const double sg = g >= 0.0 ? 1.0 : -1.0;
+  const double h = 0.5 * g * iN;
+  // z-space gradients of g and N: (n, v x w, w x u) and (0, 2 vv u - 2 uv v, 2 uu v - 2 uv u)
+  const double gg[3][3] = {{n[0], n[1], n[2]},
+                           {v[1] * w[2] - v[2] * w[1], v[2] * w[0] - v[0] * w[2], v[0] * w[1] - v[1] * w[0]},
+                           {w[1] * u[2] - w[2] * u[1], w[2] * u[0] - w[0] * u[2], w[0] * u[1] - w[1] * u[0]}};
+  double gN[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gN[0][k] = 0.0;
+    gN[1][k] = 2.0 * vv * u[k] - 2.0 * uv * v[k];
+    gN[2][k] = 2.0 * uu * v[k] - 2.0 * uv * u[k];
+  }
+  const double sgam = sg * gam;
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gd[3 * m + k] = sgam * (gg[m][k] - h * gN[m][k]);
+  // y-space vectors
+  double e[3][3], gNY[3][3], q[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      gNY[b][k] = M[1][b] * gN[1][k] + M[2][b] * gN[2][k];
+      e[b][k] = M[0][b] * gg[0][k] + M[1][b] * gg[1][k] + M[2][b] * gg[2][k] - h * gNY[b][k];
+      q[b][k] = M[2][b] * u[k] - M[1][b] * v[k];
+    }
+  const double s1 = kb1 * sgam;
+  const double A1 = kb2 * iN, B1 = -0.5 * s1 * iN, C1 = 0.5 * h * s1 * iN;
+  const double kN = -2.0 * s1 * h;  // times hess N / 2
+  const double kg = s1;             // times hess g
+  double U[3][3], W[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      U[b][k] = A1 * e[b][k] + B1 * gNY[b][k];
+      W[b][k] = B1 * e[b][k] + C1 * gNY[b][k];
+    }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a; b < 3; ++b) {
+      const double G = q[a][0] * q[b][0] + q[a][1] * q[b][1] + q[a][2] * q[b][2];
+      double X[3][3];  // [r]x part of the off-diagonal blocks
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) X[i][j] = 0.0;
+      if (a < b) {
+        const double mu = M[2][a] * M[1][b] - M[1][a] * M[2][b];
+        const double m01 = M[0][a] * M[1][b] - M[1][a] * M[0][b];
+        const double m02 = M[0][a] * M[2][b] - M[2][a] * M[0][b];
+        const double m12 = M[1][a] * M[2][b] - M[2][a] * M[1][b];
+        double r[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r[k] = kg * (m02 * u[k] - m01 * v[k] - m12 * w[k]) + kN * mu * n[k];
+        X[0][1] = -r[2];
+        X[0][2] = r[1];
+        X[1][0] = r[2];
+        X[1][2] = -r[0];
+        X[2][0] = -r[1];
+        X[2][1] = r[0];
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = (a == b ? i : 0); j < 3; ++j) {
+          double val = e[a][i] * U[b][j] + gNY[a][i] * W[b][j] - kN * q[b][i] * q[a][j] + X[i][j];
+          if (i == j) val += kN * G;
+          Bq[tri_idx(3 * a + i, 3 * b + j, 9)] = val;
+        }
+    }
+}
+
 __device__ __forceinline__ int64_t find_block(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                               int r, int c) {
   int lo = row_ptr[r], hi = row_ptr[r + 1];
@@ -521,9 +633,6 @@ struct HessArgs {
   int64_t cap;
 };
 
-__device__ __forceinline__ int tri_idx(int i, int j, int D) {  // packed upper triangle, i <= j
-  return i * D - (i * (i - 1)) / 2 + (j - i);
-}
 
 __device__ __forceinline__ void add_block(const HessArgs& A, int r, int c, const double* blk, bool transpose) {
   const int64_t bi = find_block(A.row_ptr, A.col, r, c);
@@ -541,7 +650,7 @@ __device__ __forceinline__ void add_block(const HessArgs& A, int r, int c, const
 // queue (element-major: entry e of slot at e * cap + slot).  D = 9 goes with
 // three z-vectors (plane types), D = 6 with two (point-edge).
 template <int D, int NZ>
-__device__ __forceinline__ void write_reduced(double* __restrict__ Bo, int64_t cap, unsigned slot,
+__host__ __device__ __forceinline__ void write_reduced(double* __restrict__ Bo, int64_t cap, unsigned slot,
                                               const double (&M)[3][3], const double* gd, const double* Hs,
                                               double c1, double c2) {
   constexpr int NB = D / 3;
@@ -628,11 +737,11 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
   double e_local = 0.0;
   int mem = -1;
   int want = 0;  // 9 or 6: reduced dimension of the queued matrix
-  // kept for the reduced matrix, written after the queue slot is known
-  double gd[9], Hs[81], M[3][3], Rf[9];
+  // the reduced matrix (packed upper triangle), written once the queue slot is known
+  double Bq[45];
+  double gd[9], M[3][3], Rf[9];
   double c1 = 0.0, c2 = 0.0;
-  double pwx = 0.0, pwy = 0.0, plu = 1.0;  // point-edge pair in its frame: w', |u|
-  int nz = 0, nb = 0;
+  int nz = 0;
   if (a < A.na) {
     const uint32_t c = A.aidx[a];
     const uint64_t key = A.cand[c];
@@ -701,20 +810,49 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
       }
     }
     const double i2d = 0.5 / d;
+    c1 = kap * (b2 - b1 * (2.0 * i2d));
+    c2 = kap * b1 * i2d;
+    if (kind > 0) {
+      // M = C K: the z-vectors in the orthonormal translation-free basis of
+      // the points the type involves
+      int pts[4], np = 0;
+      for (int i = 0; i < 4; ++i) {
+        bool used = false;
+        for (int m = 0; m < nz; ++m) used |= TI.C[m][i] != 0;
+        if (used) pts[np++] = i;
+      }
+      const int nb = np - 1;
+      for (int m = 0; m < 3; ++m)
+        for (int bb = 0; bb < 3; ++bb) {
+          double v = 0.0;
+          if (m < nz && bb < nb)
+            for (int q = 0; q < np; ++q)
+              v += (double)TI.C[m][pts[q]] * (np == 4 ? c_K4[q][bb] : c_K3[q][bb]);
+          M[m][bb] = v;
+        }
+    }
     if (pe_local) {
       // In the frame (w' = (wx, wy, 0), u' = (lu, 0, 0), s = wy^2) grad s has
       // only the y components 2 wy (w) and -2 wx wy / lu (u); hess s is
       // formed in write_reduced_pe_local
-      pwx = zl[0].x;
-      pwy = zl[0].y;
-      plu = zl[1].x;
+      const double pwx = zl[0].x, pwy = zl[0].y, plu = zl[1].x;
       for (int k = 0; k < 9; ++k) gd[k] = 0.0;
       gd[1] = 2.0 * pwy * i2d;
       gd[4] = -2.0 * pwx * pwy / plu * i2d;
+      write_reduced_pe_local(Bq, 1, 0, M, gd[1], gd[4], pwx, pwy, plu, c1, c2, Rf);
+      want = 4;
+    } else if (kind == 2) {
+      const double zz[3][3] = {{z[0].x, z[0].y, z[0].z}, {z[1].x, z[1].y, z[1].z}, {z[2].x, z[2].y, z[2].z}};
+      plane_reduced(zz, M, kap * b1, kap * b2, gd, Bq);
+      want = 9;
     } else {
-      double gs[9];
+      double gs[9], Hs[81];
       s_derivs(kind, z, gs, Hs);
       for (int k = 0; k < 9; ++k) gd[k] = gs[k] * i2d;
+      if (kind == 1) {
+        write_reduced<6, 2>(Bq, 1, 0, M, gd, Hs, c1, c2);
+        want = 6;
+      }
     }
     if (A.grad) {
       // grad d in world axes (rotated back from the frame when in it)
@@ -750,31 +888,11 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
           for (int q = 0; q < 9; ++q) blk[q] = (double)cc * Hz[q];
           add_block(A, s.v[i], s.v[j], blk, false);
         }
-    } else {
-      int pts[4], np = 0;
-      for (int i = 0; i < 4; ++i) {
-        bool used = false;
-        for (int m = 0; m < nz; ++m) used |= TI.C[m][i] != 0;
-        if (used) pts[np++] = i;
-      }
-      nb = np - 1;
-      c1 = kap * (b2 - b1 * (2.0 * i2d));
-      c2 = kap * b1 * i2d;
-      for (int m = 0; m < 3; ++m)
-        for (int bb = 0; bb < 3; ++bb) {
-          double v = 0.0;
-          if (m < nz && bb < nb)
-            for (int q = 0; q < np; ++q)
-              v += (double)TI.C[m][pts[q]] * (np == 4 ? c_K4[q][bb] : c_K3[q][bb]);
-          M[m][bb] = v;
-        }
-      want = pe_local ? 4 : 3 * nb;
     }
   }
-  // queue slot (warp-aggregated allocation), then the reduced matrix
-  //   B = (M x I)^T H_z (M x I),  H_z = c1 grad d grad d^T + c2 hess s
-  //     = c1 gB gB^T + c2 (M x I)^T hess s (M x I),  gB = (M x I)^T grad d,
-  // written straight into the queue (packed upper triangle, element-major)
+  // queue slot (warp-aggregated allocation), then the reduced matrix, packed
+  // upper triangle, element-major (point-edge pairs in their frame: the
+  // 4x4 and 2x2 blocks and the frame)
   const unsigned lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   unsigned slot = 0;
@@ -790,15 +908,13 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
     base = __shfl_sync(0xffffffffu, base, leader);
     if (want == Dw) slot = base + __popc(m & lt);
   }
-  if (want == 9) {
-    write_reduced<9, 3>(A.B9, A.cap, slot, M, gd, Hs, c1, c2);
-    A.slot9[slot] = (uint32_t)a;
-  } else if (want == 6) {
-    write_reduced<6, 2>(A.B6, A.cap, slot, M, gd, Hs, c1, c2);
-    A.slot6[slot] = (uint32_t)a;
-  } else if (want == 4) {
-    write_reduced_pe_local(A.B4, A.cap, slot, M, gd[1], gd[4], pwx, pwy, plu, c1, c2, Rf);
-    A.slot4[slot] = (uint32_t)a;
+  if (want != 0) {
+    double* Bo = want == 9 ? A.B9 : (want == 6 ? A.B6 : A.B4);
+    const int ne = want == 9 ? 45 : (want == 6 ? 21 : 22);
+#pragma unroll
+    for (int e = 0; e < 45; ++e)
+      if (e < ne) Bo[(size_t)e * A.cap + slot] = Bq[e];
+    (want == 9 ? A.slot9 : (want == 6 ? A.slot6 : A.slot4))[slot] = (uint32_t)a;
   }
   // energy per member: one atomic per warp when the warp holds one member
   const int m0 = __shfl_sync(0xffffffffu, mem, 0);
@@ -971,6 +1087,74 @@ __device__ __forceinline__ void jacobi_refine64(double* Am, double* V, const int
 #define PROJ_FP32_TOL2 1e-12f
 #endif
 
+// The 4-point transform behind K4 = H / 2 (H rows (1,1,1), (1,-1,-1),
+// (-1,1,-1), (-1,-1,1)): h = H p in six additions.
+__host__ __device__ __forceinline__ void had3(double p0, double p1, double p2, double (&h)[4]) {
+  const double t = p1 + p2, d = p1 - p2;
+  h[0] = p0 + t;
+  h[1] = p0 - t;
+  h[2] = d - p0;
+  h[3] = -d - p0;
+}
+
+// Entries (i, j) of all sixteen 3x3 blocks of (K4 x I) B+ (K4 x I)^T: with
+// P[a][b] = B+[3a+i][3b+j] / 4 (Bq holds B+ / 4), X = H P H^T, block
+// (q1, q2) gets X[q1][q2] at (i, j) and, for i != j, X[q2][q1] at (j, i)
+// (B+ is symmetric).  Additions only, instead of the products with K4.
+__host__ __device__ __forceinline__ void hadamard_block_entries(const double* Bq, int S, int i, int j,
+                                                                double (&X)[4][4]) {
+  double Q[3][4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double p[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int r = 3 * a + i, cl = 3 * b + j;
+      p[b] = Bq[(r <= cl ? tri_idx(r, cl, 9) : tri_idx(cl, r, 9)) * S];
+    }
+    had3(p[0], p[1], p[2], Q[a]);
+  }
+#pragma unroll
+  for (int q2 = 0; q2 < 4; ++q2) {
+    double h[4];
+    had3(Q[0][q2], Q[1][q2], Q[2][q2], h);
+#pragma unroll
+    for (int q1 = 0; q1 < 4; ++q1) X[q1][q2] = h[q1];
+  }
+}
+
+__device__ __forceinline__ void hadamard_scatter(const HessArgs& A, const Stencil& st, const double* Bq, int S) {
+  int64_t off[4][4];
+  bool miss = false;
+#pragma unroll
+  for (int q1 = 0; q1 < 4; ++q1)
+#pragma unroll
+    for (int q2 = 0; q2 < 4; ++q2) {
+      const int r = st.v[q1], cc = st.v[q2];
+      const int64_t bi = find_block(A.row_ptr, A.col, r, cc);
+      const bool hit = bi < A.row_ptr[r + 1] && A.col[bi] == cc;
+      miss |= !hit;
+      off[q1][q2] = hit ? 9 * bi : -1;
+    }
+  if (miss) atomicOr(A.status, (unsigned long long)CB_DEV_CAPACITY);  // pattern miss: never expected
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      double X[4][4];
+      hadamard_block_entries(Bq, S, i, j, X);
+#pragma unroll
+      for (int q1 = 0; q1 < 4; ++q1)
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) {
+          if (off[q1][q2] < 0) continue;
+          double* dst = A.val + off[q1][q2];
+          atomicAdd(&dst[3 * i + j], X[q1][q2]);
+          if (i != j) atomicAdd(&dst[3 * j + i], X[q2][q1]);
+        }
+    }
+}
+
 template <int D>
 struct ProjSmem {
   static constexpr int NP = D * (D + 1) / 2;
@@ -1091,9 +1275,10 @@ __global__ void __launch_bounds__(S) k_hess_proj(HessArgs A, int64_t m) {
   const bool from_b = nneg < npos;
   const int nterm = from_b ? nneg : npos;
   const int wterm = __reduce_max_sync(__activemask(), nterm);
-  double* Bs = Ad;  // B+ replaces A
+  double* Bs = Ad;  // B+ replaces A (for D = 9 scaled by 1/4, the square of K4's entries)
+  constexpr double bsc = D == 9 ? 0.25 : 1.0;
 #pragma unroll
-  for (int e = 0; e < NP; ++e) Bs[e * S] = from_b ? Br[e] : 0.0;
+  for (int e = 0; e < NP; ++e) Bs[e * S] = from_b ? Br[e] * bsc : 0.0;
   for (int j = 0; j < wterm; ++j) {
     int k = -1, cnt = 0;
     double wk = 0.0;
@@ -1102,7 +1287,7 @@ __global__ void __launch_bounds__(S) k_hess_proj(HessArgs A, int64_t m) {
       const bool sel = from_b ? lam[kk] < 0.0 : lam[kk] > 0.0;
       if (sel && cnt == j) {
         k = kk;
-        wk = from_b ? -lam[kk] : lam[kk];
+        wk = (from_b ? -lam[kk] : lam[kk]) * bsc;
       }
       cnt += sel;
     }
@@ -1117,49 +1302,53 @@ __global__ void __launch_bounds__(S) k_hess_proj(HessArgs A, int64_t m) {
       for (int jj = i; jj < D; ++jj) Bs[tri_idx(i, jj, D) * S] += wi * v[jj];
     }
   }
-  // scatter: block (q1, q2) of the involved points
-  //   = sum_ab K[q1][ab] R[q2][ab],  R[q2][ab] = sum_bb K[q2][bb] B+[ab, bb]
-  // (3x3 blocks; R for one q2 at a time)
   const uint32_t c = A.aidx[a];
   const Stencil st = stencil_of(A.cand[c], A.ev0, A.ev1, A.tv, A.T);
-  const TypeInfo& TI = st.ee ? c_ee_types[A.ctype[c]] : c_pt_types[A.ctype[c]];
-  const int nz = TI.kind + 1;
-  int pts[4], np = 0;
-  for (int i = 0; i < 4; ++i) {
-    bool used = false;
-    for (int mm = 0; mm < nz; ++mm) used |= TI.C[mm][i] != 0;
-    if (used) pts[np++] = i;
-  }
-  constexpr int NB = D / 3;
-  for (int q2 = 0; q2 < np; ++q2) {
-    double R[NB][9];
+  if constexpr (D == 9) {
+    // the plane types involve all four points, in stencil order
+    hadamard_scatter(A, st, Bs, S);
+  } else {
+    // scatter: block (q1, q2) of the involved points
+    //   = sum_ab K[q1][ab] R[q2][ab],  R[q2][ab] = sum_bb K[q2][bb] B+[ab, bb]
+    // (3x3 blocks; R for one q2 at a time)
+    const TypeInfo& TI = st.ee ? c_ee_types[A.ctype[c]] : c_pt_types[A.ctype[c]];
+    const int nz = TI.kind + 1;
+    int pts[4], np = 0;
+    for (int i = 0; i < 4; ++i) {
+      bool used = false;
+      for (int mm = 0; mm < nz; ++mm) used |= TI.C[mm][i] != 0;
+      if (used) pts[np++] = i;
+    }
+    constexpr int NB = D / 3;
+    for (int q2 = 0; q2 < np; ++q2) {
+      double R[NB][9];
 #pragma unroll
-    for (int ab = 0; ab < NB; ++ab)
+      for (int ab = 0; ab < NB; ++ab)
 #pragma unroll
-      for (int al = 0; al < 3; ++al)
+        for (int al = 0; al < 3; ++al)
 #pragma unroll
-        for (int be = 0; be < 3; ++be) {
+          for (int be = 0; be < 3; ++be) {
+            double v = 0.0;
+#pragma unroll
+            for (int bb = 0; bb < NB; ++bb) {
+              const int r = 3 * ab + al, cl = 3 * bb + be;
+              v += c_K3[q2][bb] * Bs[(r <= cl ? tri_idx(r, cl, D) : tri_idx(cl, r, D)) * S];
+            }
+            R[ab][3 * al + be] = v;
+          }
+      for (int q1 = 0; q1 <= q2; ++q1) {
+        double blk[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
           double v = 0.0;
 #pragma unroll
-          for (int bb = 0; bb < NB; ++bb) {
-            const int r = 3 * ab + al, cl = 3 * bb + be;
-            const double kq = D == 9 ? c_K4[q2][bb] : c_K3[q2][bb];
-            v += kq * Bs[(r <= cl ? tri_idx(r, cl, D) : tri_idx(cl, r, D)) * S];
-          }
-          R[ab][3 * al + be] = v;
+          for (int ab = 0; ab < NB; ++ab) v += c_K3[q1][ab] * R[ab][e];
+          blk[e] = v;
         }
-    for (int q1 = 0; q1 <= q2; ++q1) {
-      double blk[9];
-#pragma unroll
-      for (int e = 0; e < 9; ++e) {
-        double v = 0.0;
-#pragma unroll
-        for (int ab = 0; ab < NB; ++ab) v += (D == 9 ? c_K4[q1][ab] : c_K3[q1][ab]) * R[ab][e];
-        blk[e] = v;
+        const int r = st.v[pts[q1]], cc = st.v[pts[q2]];
+        add_block(A, r, cc, blk, false);
+        if (q1 != q2) add_block(A, cc, r, blk, true);
       }
-      const int r = st.v[pts[q1]], cc = st.v[pts[q2]];
-      add_block(A, r, cc, blk, false);
-      if (q1 != q2) add_block(A, cc, r, blk, true);
     }
   }
 }
