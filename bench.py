@@ -30,14 +30,21 @@ UNIT = "pairs/s"
 # FP64 peak from the part's unit counts and clock: 152 SMs x 2070 MHz x 4 FP64
 # flop/clk/SM (2 DFMA) = 1.26 TFLOP/s, the 1.25 TFLOP/s dense FP64 figure.
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
-# algorithmic FP64 flops of stage (d) per active pair: distance derivatives and
-# the 12x12 Hessian (~2.5e3) + one symmetric eigendecomposition of the 9x9
-# translation-free block with eigenvectors and the PSD rebuild (~7.5e3)
-FLOPS_PER_ACTIVE = 1.0e4
-# DRAM bytes (read + write) of the stage-(d) kernels per active pair, from one
-# ncu capture of the 128x128 pleated sheet (195,263 active pairs, 141.2 MB);
-# traffic grows in proportion to the active pairs
-HESS_DRAM_BYTES_PER_ACTIVE = 141.2e6 / 195263
+# FP64 flop of the stage-(d) kernels per pair each one handles (DADD + DMUL +
+# 2 DFMA executed, from ncu on the 128x128 pleated sheet): k_hess_prep per
+# active pair, k_hess_proj<9> per face / line-line pair, k_hess_proj_pe per
+# point-edge pair in its own frame, k_hess_proj<6> per generic point-edge pair
+HESS_FLOPS = {"prep": 1500.0, "face": 9000.0, "pe_frame": 800.0, "pe": 3000.0}
+# DRAM bytes (read + write) of the stage-(d) kernels per active pair, from the
+# same capture; traffic grows in proportion to the active pairs
+HESS_DRAM_BYTES_PER_ACTIVE = 700.0
+
+
+def hess_flops(st) -> float:
+    """FP64 flop of one pass's stage-(d) kernels: per-kernel counts per pair
+    times the pairs each kernel handled."""
+    return (HESS_FLOPS["prep"] * st["n_active"] + HESS_FLOPS["face"] * st["n_hess_face"]
+            + HESS_FLOPS["pe_frame"] * st["n_hess_pe_frame"] + HESS_FLOPS["pe"] * st["n_hess_pe"])
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -98,7 +105,7 @@ def stage_roofline(st: dict, med: list, scenes) -> dict:
         gbs = by[k] / (ms / 1000.0) / 1e9 if ms > 0 else None
         out[k] = {"bytes": int(by[k]), "ms": ms, "gbs": gbs, "hbm_frac": (gbs / hbm) if (gbs and hbm) else None}
     hess = med[4]
-    out["hessian_kernels"] = {"ms": hess, "fp64_tflops": FLOPS_PER_ACTIVE * A / (hess / 1000.0) / 1e12 if hess > 0
+    out["hessian_kernels"] = {"ms": hess, "fp64_tflops": hess_flops(st) / (hess / 1000.0) / 1e12 if hess > 0
                               else None}
     if hess > 0:
         out["hessian_kernels"]["fp64_frac"] = out["hessian_kernels"]["fp64_tflops"] / FP64_PEAK_TFLOPS
@@ -352,7 +359,7 @@ def bench_batch(args, rank, world, local, dist):
     hess_ms = statistics.mean(s[4] for s in stage)
     med = [statistics.median(s[i] for s in stage) for i in range(5)]
     na = int(st["n_active"])
-    achieved = FLOPS_PER_ACTIVE * na / (hess_ms / 1000.0) / 1e12 if hess_ms > 0 else 0.0
+    achieved = hess_flops(st) / (hess_ms / 1000.0) / 1e12 if hess_ms > 0 else 0.0
     sizes = [sc.n for sc in scenes]
     line = {"metric": METRIC, "value": world * n_cand / (ms / 1000.0), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -373,7 +380,7 @@ def bench_batch(args, rank, world, local, dist):
                          "ccd_step": med[3], "hessian_kernel": med[4]},
             "roofline": {"bound": "alu", "kernel": "k_hess_prep + k_hess_proj<9> + k_hess_proj_pe (FP64 stage d)", "achieved": achieved,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": None, "flops_per_active_pair": FLOPS_PER_ACTIVE, "kernel_ms": hess_ms,
+                         "traffic": None, "flops_per_pass": hess_flops(st), "kernel_ms": hess_ms,
                          "peak_source": "derived: 152 SM x 2070 MHz x 4 FP64 flop/clk/SM"},
             "e2e": {"value": world * n_cand / (e2e_ms / 1000.0), "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": 2 * 3 * N * 8, "d2h_bytes_per_step": 2 * M * 8 + 3 * N * 8},
@@ -582,7 +589,7 @@ def main():
     med = [statistics.median(s[i] for s in stage) for i in range(5)]
     hess_ms = statistics.mean(s[4] for s in stage)
     na = st["n_active"]
-    achieved = FLOPS_PER_ACTIVE * na / (hess_ms / 1000.0) / 1e12 if hess_ms > 0 else 0.0
+    achieved = hess_flops(st) / (hess_ms / 1000.0) / 1e12 if hess_ms > 0 else 0.0
     try:
         fp64_meas = CT.measure_fma_tflops(True)
         fp32_meas = CT.measure_fma_tflops(False, iters=65536)
@@ -593,7 +600,9 @@ def main():
                 "peak_fp64_fma_measured": fp64_meas, "peak_fp32_fma_measured": fp32_meas,
                 "traffic": HESS_DRAM_BYTES_PER_ACTIVE * na,
                 "traffic_source": "ncu dram__bytes_read+write of the 128x128 case, scaled by active pairs",
-                "flops_per_active_pair": FLOPS_PER_ACTIVE, "active_pairs": na,
+                "flops_per_pass": hess_flops(st), "active_pairs": na,
+                "pairs_per_kernel": {"face": st["n_hess_face"], "pe_frame": st["n_hess_pe_frame"],
+                                     "pe": st["n_hess_pe"]},
                 "kernel_ms": hess_ms, "peak_source": "derived: 152 SM x 2070 MHz x 4 FP64 flop/clk/SM"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

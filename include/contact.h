@@ -109,6 +109,9 @@ typedef struct {
   int64_t n_candidates_fp32;  /* last contact_build: non-incident pairs passing the FP32 box test
                                  (a superset of the candidates; the FP32 effect on |C| is this / n_candidates) */
   int64_t n_fp64_decided;     /* ... of which the FP32 test was not conclusive and the FP64 boxes decided */
+  int64_t n_hess_face;        /* last barrier_eval: active face / line-line pairs (9x9 projection) */
+  int64_t n_hess_pe_frame;    /* ... point-edge pairs projected in their own frame (3x3 + 2x2) */
+  int64_t n_hess_pe;          /* ... point-edge pairs on the generic 6x6 projection */
 } cb_stats;
 
 /* Create a scene: uploads topology and rest positions, derives edges and

@@ -60,7 +60,7 @@ static void scene_release(cb_scene* s) {
   DevBuf* bufs[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->frest,
                     &s->frest_dbar, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
                     &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col, &s->bsr_val,
-                    &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->xf, &s->pf, &s->dlist, &s->mp, &s->vsc, &s->macc, &s->hstage, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag, &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist,
+                    &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->mp, &s->vsc, &s->macc, &s->hstage, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag, &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist,
                     &s->dev_scalars};
   for (DevBuf* b : bufs) buf_free(*b, st);
   for (BroadWork* w : {&s->bw, &s->bwc}) {
@@ -690,11 +690,14 @@ cb_status cb_get_stats(cb_scene* s, cb_stats* o) {
   o->ccd_max_iters = (int32_t)h[SC_ITERS];
   o->n_candidates_fp32 = (int64_t)h[SC_FP32_PAIRS];
   o->n_fp64_decided = (int64_t)h[SC_FP64_DECIDED];
+  o->n_hess_face = s->n_hq[0];
+  o->n_hess_pe_frame = s->n_hq[1];
+  o->n_hess_pe = s->n_hq[2];
   size_t bytes = 0;
   const DevBuf* all[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->frest,
                          &s->frest_dbar, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls,
                          &s->aidx, &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col,
-                         &s->bsr_val, &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->xf, &s->pf, &s->dlist, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag,
+                         &s->bsr_val, &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag,
                          &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist};
   for (const DevBuf* b : all) bytes += b->bytes;
   for (const BroadWork* w : {&s->bw, &s->bwc}) {

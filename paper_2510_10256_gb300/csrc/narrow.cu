@@ -600,6 +600,7 @@ __device__ __forceinline__ int64_t find_block(const int32_t* __restrict__ row_pt
 
 struct HessArgs {
   int64_t na;
+  const uint32_t* __restrict__ order;  // prep thread -> active pair index
   const uint32_t* __restrict__ aidx;
   const uint64_t* __restrict__ cand;
   const double* __restrict__ cd;
@@ -623,7 +624,7 @@ struct HessArgs {
   // triangle, element-major ([e * cap + slot]); slot -> active pair index
   double* __restrict__ B9;
   double* __restrict__ B6;
-  double* __restrict__ B4;        // point-edge pairs in their own frame: 4x4 (10), 2x2 (3), frame (9)
+  double* __restrict__ B4;        // point-edge pairs in their own frame: p, r, Y (7), 2x2 (3), frame (9)
   uint32_t* __restrict__ slot9;
   uint32_t* __restrict__ slot6;
   uint32_t* __restrict__ slot4;
@@ -685,16 +686,21 @@ __host__ __device__ __forceinline__ void write_reduced(double* __restrict__ Bo, 
 
 // Point-edge pairs in their own frame: the 6x6 reduced matrix (rows 3 ab + al,
 // al the local axis) has no coupling between the e3 rows (2, 5) and the
-// rest, so only its in-plane 4x4 block (rows 0, 1, 3, 4; 10 packed entries)
-// and out-of-plane 2x2 block (rows 2, 5; 3 entries) are queued, followed by
-// the frame R (row-major, columns e1 e2 e3; 9 entries).
+// rest, so it splits into an in-plane 4x4 block (rows 0, 1, 3, 4) and an
+// out-of-plane 2x2 block (rows 2, 5).
 // At w' = (wx, wy, 0), u' = (lu, 0, 0) the Hessian of s = |w|^2 - (w.u)^2/|u|^2
 // has, per pair of axes, these 2x2 blocks over (w, u) (rows: first axis):
 //   (x, x): 0;  (x, y): [[0, -2 wy/lu], [0, 2 wx wy/lu^2]];  (y, x): its transpose;
 //   (y, y): [[2, -2 wx/lu], [-2 wx/lu, 2 (wx^2 - wy^2)/lu^2]];
 //   (z, z): [[2, -2 wx/lu], [-2 wx/lu, 2 wx^2/lu^2]];  the rest 0,
 // and grad d = (g0, g1) on the y axis only.  With H_z = c1 grad d grad d^T +
-// c2 hess s, block (ab, al; bb, be) of B is (M^T H_z[al, be] M)[ab][bb].
+// c2 hess s, block (ab, al; bb, be) of B is (M^T H_z[al, be] M)[ab][bb].  So
+// the 4x4 block, in the order (x of both reduced points, y of both), is
+//   [[0, p r^T], [r p^T, Y]],  p_ab = M[0][ab] hxy01 + M[1][ab] hxy11,
+//   r_bb = M[1][bb],  Y = (M^T H_z[y, y] M)
+// (the (x, x) block is zero and the (x, y) block has rank one).  Queued:
+// p (2), r (2), Y (3, packed), the 2x2 block (3, packed) and the frame R
+// (row-major, columns e1 e2 e3; 9).
 __device__ __forceinline__ void write_reduced_pe_local(double* __restrict__ Bo, int64_t cap, unsigned slot,
                                                        const double (&M)[3][3], double g0, double g1, double wx,
                                                        double wy, double lu, double c1, double c2,
@@ -713,18 +719,51 @@ __device__ __forceinline__ void write_reduced_pe_local(double* __restrict__ Bo, 
       for (int m2 = 0; m2 < 2; ++m2) v += M[m][ab] * H[m][m2] * M[m2][bb];
     return v;
   };
-  // (x, y) block: H = [[0, hxy01], [0, hxy11]] -> (M^T H M)[ab][bb]
-  auto mxy = [&](int ab, int bb) { return M[0][ab] * hxy01 * M[1][bb] + M[1][ab] * hxy11 * M[1][bb]; };
-  // 4x4 over (0,x), (0,y), (1,x), (1,y), packed upper triangle
-  const double e4[10] = {0.0,         mxy(0, 0),      0.0,       mxy(0, 1),      mhm(Hyy, 0, 0),
-                         mxy(1, 0),   mhm(Hyy, 0, 1), 0.0,       mxy(1, 1),      mhm(Hyy, 1, 1)};
+  const double e[10] = {M[0][0] * hxy01 + M[1][0] * hxy11,
+                        M[0][1] * hxy01 + M[1][1] * hxy11,
+                        M[1][0],
+                        M[1][1],
+                        mhm(Hyy, 0, 0),
+                        mhm(Hyy, 0, 1),
+                        mhm(Hyy, 1, 1),
+                        mhm(Hzz, 0, 0),
+                        mhm(Hzz, 0, 1),
+                        mhm(Hzz, 1, 1)};
 #pragma unroll
-  for (int e = 0; e < 10; ++e) Bo[(size_t)e * cap + slot] = e4[e];
-  Bo[(size_t)10 * cap + slot] = mhm(Hzz, 0, 0);
-  Bo[(size_t)11 * cap + slot] = mhm(Hzz, 0, 1);
-  Bo[(size_t)12 * cap + slot] = mhm(Hzz, 1, 1);
+  for (int k = 0; k < 10; ++k) Bo[(size_t)k * cap + slot] = e[k];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) Bo[(size_t)(13 + k) * cap + slot] = Rf[k];
+  for (int k = 0; k < 9; ++k) Bo[(size_t)(10 + k) * cap + slot] = Rf[k];
+}
+
+// Active pairs in the order k_hess_prep takes them: face / line-line pairs
+// (the branch with the most FP64 work) first, the other pairs from the end
+// backwards, so that a warp of the prep kernel runs one branch rather than
+// both with few lanes each.  Warp-aggregated appends; inside each group the
+// order follows warp arrival.
+__global__ void k_kind_split(int64_t na, const uint32_t* __restrict__ aidx, const uint64_t* __restrict__ cand,
+                             const int8_t* __restrict__ ctype, uint32_t* __restrict__ order,
+                             unsigned* __restrict__ cnt) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool plane = false;
+  if (a < na) {
+    const uint32_t c = aidx[a];
+    const int ty = ctype[c];
+    plane = (cb_key_type(cand[c]) == CB_KEY_PT ? c_pt_types[ty] : c_ee_types[ty]).kind == 2;
+  }
+  const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+  const unsigned mp = __ballot_sync(0xffffffffu, a < na && plane);
+  const unsigned mr = __ballot_sync(0xffffffffu, a < na && !plane);
+  unsigned bp = 0, br = 0;
+  if (lane == 0) {
+    if (mp) bp = atomicAdd(&cnt[0], (unsigned)__popc(mp));
+    if (mr) br = atomicAdd(&cnt[1], (unsigned)__popc(mr));
+  }
+  bp = __shfl_sync(0xffffffffu, bp, 0);
+  br = __shfl_sync(0xffffffffu, br, 0);
+  if (a < na) {
+    if (plane) order[bp + __popc(mp & lt)] = (uint32_t)a;
+    else order[na - 1 - (int64_t)(br + __popc(mr & lt))] = (uint32_t)a;
+  }
 }
 
 // Stage (d), part 1, one thread per active pair: barrier value and
@@ -733,7 +772,8 @@ __device__ __forceinline__ void write_reduced_pe_local(double* __restrict__ Bo, 
 // B = (M x I)^T H_z (M x I) with M = C K.  Point-point stencils are projected
 // in closed form here; the others are queued for the projection kernels.
 __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
-  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t a = t < A.na ? (int64_t)A.order[t] : A.na;
   double e_local = 0.0;
   int mem = -1;
   int want = 0;  // 9 or 6: reduced dimension of the queued matrix
@@ -910,7 +950,7 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
   }
   if (want != 0) {
     double* Bo = want == 9 ? A.B9 : (want == 6 ? A.B6 : A.B4);
-    const int ne = want == 9 ? 45 : (want == 6 ? 21 : 22);
+    const int ne = want == 9 ? 45 : (want == 6 ? 21 : 19);
 #pragma unroll
     for (int e = 0; e < 45; ++e)
       if (e < ne) Bo[(size_t)e * A.cap + slot] = Bq[e];
@@ -1454,86 +1494,88 @@ __device__ __forceinline__ void jacobi_refine64_reg(double (&Am)[D * (D + 1) / 2
   }
 }
 
-// PSD projection of a symmetric 4x4 (packed upper triangle) in registers:
-// FP32 Jacobi, FP64 Gram-Schmidt, A = V^T B V, FP64 sweeps, then B+ from the
-// side with fewer eigenpairs (as k_hess_proj).
-__device__ __forceinline__ void psd4(const double (&B)[10], double (&P)[10]) {
+// PSD projection of a small symmetric D x D (packed upper triangle) in
+// registers: FP32 Jacobi, FP64 Gram-Schmidt, A = V^T B V, FP64 sweeps, then
+// B+ from the side with fewer eigenpairs (as k_hess_proj).
+template <int D>
+__device__ __forceinline__ void psd_small(const double (&B)[D * (D + 1) / 2], double (&P)[D * (D + 1) / 2]) {
+  constexpr int NP = D * (D + 1) / 2;
   double mx = 0.0;
 #pragma unroll
-  for (int e = 0; e < 10; ++e) mx = fmax(mx, fabs(B[e]));
+  for (int e = 0; e < NP; ++e) mx = fmax(mx, fabs(B[e]));
   if (mx == 0.0) {
 #pragma unroll
-    for (int e = 0; e < 10; ++e) P[e] = 0.0;
+    for (int e = 0; e < NP; ++e) P[e] = 0.0;
     return;
   }
-  double V[16], Am[10];
+  double V[D * D], Am[NP];
   {
-    float A32[10], V32[16];
+    float A32[NP], V32[D * D];
     const double inv = 1.0 / mx;
 #pragma unroll
-    for (int e = 0; e < 10; ++e) A32[e] = (float)(B[e] * inv);
+    for (int e = 0; e < NP; ++e) A32[e] = (float)(B[e] * inv);
 #pragma unroll
-    for (int e = 0; e < 16; ++e) V32[e] = (e % 5 == 0) ? 1.f : 0.f;
-    jacobi_reg<float, 4>(A32, V32, PROJ_FP32_TOL2, 12);
+    for (int e = 0; e < D * D; ++e) V32[e] = (e % (D + 1) == 0) ? 1.f : 0.f;
+    jacobi_reg<float, D>(A32, V32, PROJ_FP32_TOL2, 12);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < D; ++k) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) V[k * 4 + i] = (double)V32[k * 4 + i];
+      for (int i = 0; i < D; ++i) V[k * D + i] = (double)V32[k * D + i];
 #pragma unroll
       for (int j = 0; j < k; ++j) {
         double dp = 0.0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) dp += V[j * 4 + i] * V[k * 4 + i];
+        for (int i = 0; i < D; ++i) dp += V[j * D + i] * V[k * D + i];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) V[k * 4 + i] -= dp * V[j * 4 + i];
+        for (int i = 0; i < D; ++i) V[k * D + i] -= dp * V[j * D + i];
       }
       double nn = 0.0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) nn += V[k * 4 + i] * V[k * 4 + i];
+      for (int i = 0; i < D; ++i) nn += V[k * D + i] * V[k * D + i];
       nn = rsqrt_refined(nn);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) V[k * 4 + i] *= nn;
+      for (int i = 0; i < D; ++i) V[k * D + i] *= nn;
     }
   }
 #pragma unroll
-  for (int l = 0; l < 4; ++l) {
-    double t[4];
+  for (int l = 0; l < D; ++l) {
+    double t[D];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < D; ++i) {
       double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) v += B[i <= j ? tri_idx(i, j, 4) : tri_idx(j, i, 4)] * V[l * 4 + j];
+      for (int j = 0; j < D; ++j) v += B[i <= j ? tri_idx(i, j, D) : tri_idx(j, i, D)] * V[l * D + j];
       t[i] = v;
     }
 #pragma unroll
     for (int k = 0; k <= l; ++k) {
       double v = 0.0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) v += V[k * 4 + i] * t[i];
-      Am[tri_idx(k, l, 4)] = v;
+      for (int i = 0; i < D; ++i) v += V[k * D + i] * t[i];
+      Am[tri_idx(k, l, D)] = v;
     }
   }
-  jacobi_refine64_reg<4>(Am, V, 1e-28, 12);
-  double lam[4];
+  jacobi_refine64_reg<D>(Am, V, 1e-28, 12);
+  double lam[D];
   int npos = 0, nneg = 0;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    lam[k] = Am[tri_idx(k, k, 4)];
+  for (int k = 0; k < D; ++k) {
+    lam[k] = Am[tri_idx(k, k, D)];
     npos += lam[k] > 0.0;
     nneg += lam[k] < 0.0;
   }
   const bool from_b = nneg < npos;
 #pragma unroll
-  for (int e = 0; e < 10; ++e) P[e] = from_b ? B[e] : 0.0;
+  for (int e = 0; e < NP; ++e) P[e] = from_b ? B[e] : 0.0;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < D; ++k) {
     const double wk = from_b ? (lam[k] < 0.0 ? -lam[k] : 0.0) : (lam[k] > 0.0 ? lam[k] : 0.0);
     if (wk == 0.0) continue;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const double wi = wk * V[k * 4 + i];
+    for (int i = 0; i < D; ++i) {
+      const double wi = wk * V[k * D + i];
 #pragma unroll
-      for (int j = i; j < 4; ++j) P[tri_idx(i, j, 4)] += wi * V[k * 4 + j];
+      for (int j = i; j < D; ++j) P[tri_idx(i, j, D)] += wi * V[k * D + j];
     }
   }
 }
@@ -1568,24 +1610,37 @@ __device__ __forceinline__ void psd2(double a, double b, double c, double& pa, d
   pc = sc * hm;
 }
 
-// Stage (d), part 2 for point-edge pairs queued in their own frame: the 4x4
-// and 2x2 blocks are projected separately, the 6x6 result is rotated back
-// block by block (B+ = (I x R) B'+ (I x R)^T) and scattered as in
-// k_hess_proj<6>.
+// Stage (d), part 2 for point-edge pairs queued in their own frame.  The
+// in-plane 4x4 block [[0, p r^T], [r p^T, Y]] (x of both reduced points, then
+// y) has the null vector (p_perp, 0) and equals Q T Q^T with
+// Q = [[p/|p|, 0], [0, I]] (orthonormal columns) and the 3x3
+// T = [[0, |p| r^T], [|p| r, Y]], so its projection is Q T+ Q^T: a 3x3
+// eigenproblem instead of a 4x4.  The 2x2 block is projected in closed form,
+// the 6x6 result rotated back block by block (B+ = (I x R) B'+ (I x R)^T) and
+// scattered as in k_hess_proj<6>.
 __global__ void __launch_bounds__(128) k_hess_proj_pe(HessArgs A, int64_t m) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= m) return;
   const uint32_t a = A.slot4[w];
-  double B4[10], R[9];
+  double q[10], R[9];
 #pragma unroll
-  for (int e = 0; e < 10; ++e) B4[e] = A.B4[(size_t)e * A.cap + w];
-  const double a2 = A.B4[(size_t)10 * A.cap + w], b2 = A.B4[(size_t)11 * A.cap + w],
-               c2 = A.B4[(size_t)12 * A.cap + w];
+  for (int e = 0; e < 10; ++e) q[e] = A.B4[(size_t)e * A.cap + w];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) R[k] = A.B4[(size_t)(13 + k) * A.cap + w];
-  double P4[10], p2[3];
-  psd4(B4, P4);
-  psd2(a2, b2, c2, p2[0], p2[1], p2[2]);
+  for (int k = 0; k < 9; ++k) R[k] = A.B4[(size_t)(10 + k) * A.cap + w];
+  const double pn = sqrt(q[0] * q[0] + q[1] * q[1]);
+  double ph0 = 1.0, ph1 = 0.0;
+  if (pn > 0.0) {
+    const double ipn = 1.0 / pn;
+    ph0 = q[0] * ipn;
+    ph1 = q[1] * ipn;
+  }
+  const double T[6] = {0.0, pn * q[2], pn * q[3], q[4], q[5], q[6]};
+  double Tp[6], p2[3];
+  psd_small<3>(T, Tp);
+  psd2(q[7], q[8], q[9], p2[0], p2[1], p2[2]);
+  // Q T+ Q^T in the order (0x, 0y, 1x, 1y), packed
+  const double P4[10] = {ph0 * ph0 * Tp[0], ph0 * Tp[1], ph0 * ph1 * Tp[0], ph0 * Tp[2], Tp[3],
+                         ph1 * Tp[1],       Tp[4],       ph1 * ph1 * Tp[0], ph1 * Tp[2], Tp[5]};
   // B+ in the K3 basis, world axes: block (ab, bb) = R L(ab, bb) R^T with L
   // the local 3x3 block (in-plane 2x2 from P4, e3-e3 entry from p2)
   double Bp[21];
@@ -1783,6 +1838,7 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
   k_macc_reset<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, MACC_STATUS, 0ull);
   if (grad) CB_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * 3 * (size_t)s->n, st));
   s->n_active = 0;
+  s->n_hq[0] = s->n_hq[1] = s->n_hq[2] = 0;
   s->nnzb = 0;
   CB_TRY(buf_ensure(s->bsr_row, sizeof(int32_t) * ((size_t)s->n + 1), st));
   CB_CUDA(cudaMemsetAsync(s->bsr_row.p, 0, sizeof(int32_t) * ((size_t)s->n + 1), st));
@@ -1854,8 +1910,14 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
                                                       bp<int32_t>(s->bsr_col), bp<uint32_t>(s->row_cnt));
     cbp::exclusive_scan<uint32_t, int32_t>(bp<uint32_t>(s->row_cnt), bp<int32_t>(s->bsr_row), (int64_t)s->n + 1,
                                            (int32_t*)bp<uint32_t>(s->scan_tmp), (int32_t*)nullptr, st);
+    CB_TRY(buf_ensure(s->horder, sizeof(uint32_t) * (size_t)na, st));
+    k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_KSPLIT), 0ull);
+    k_kind_split<<<cb_grid(na), CB_THREADS, 0, cb_count(st)>>>(na, bp<uint32_t>(s->aidx), bp<uint64_t>(s->cand),
+                                                             bp<int8_t>(s->ctype), bp<uint32_t>(s->horder),
+                                                             (unsigned*)(sc + SC_KSPLIT));
     HessArgs A;
     A.na = na;
+    A.order = bp<uint32_t>(s->horder);
     A.aidx = bp<uint32_t>(s->aidx);
     A.cand = bp<uint64_t>(s->cand);
     A.cd = bp<double>(s->cd);
@@ -1877,7 +1939,7 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     A.status = status;
     CB_TRY(buf_ensure(s->hB9, sizeof(double) * 45 * (size_t)na, st));
     CB_TRY(buf_ensure(s->hB6, sizeof(double) * 21 * (size_t)na, st));
-    CB_TRY(buf_ensure(s->hB4, sizeof(double) * 22 * (size_t)na, st));
+    CB_TRY(buf_ensure(s->hB4, sizeof(double) * 19 * (size_t)na, st));
     CB_TRY(buf_ensure(s->hslot, sizeof(uint32_t) * 3 * (size_t)na, st));
     A.B9 = bp<double>(s->hB9);
     A.B6 = bp<double>(s->hB6);
@@ -1899,6 +1961,9 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     CB_TRY(read_scalars(s, SC_N9, SC_N4 - SC_N9 + 1, hq, st));
     const int64_t m9 = (int64_t)(uint32_t)hq[0], m6 = (int64_t)(uint32_t)hq[SC_N6 - SC_N9],
                   m4 = (int64_t)(uint32_t)hq[SC_N4 - SC_N9];
+    s->n_hq[0] = m9;
+    s->n_hq[1] = m4;
+    s->n_hq[2] = m6;
     if (m4 > 0) k_hess_proj_pe<<<cb_grid(m4, 128), 128, 0, cb_count(st)>>>(A, m4);
     if (m9 > 0) {
       const int smem = ProjSmem<9>::PER_THREAD * PROJ_THREADS;

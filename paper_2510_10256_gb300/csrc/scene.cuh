@@ -104,6 +104,7 @@ struct cb_scene {
   DevBuf ctype;         // int8 [nc]
   DevBuf ccls;          // uint8 [nc] final class (with C)
   int64_t n_active = 0;
+  int64_t n_hq[3] = {0, 0, 0};  // last pass: face / line-line, point-edge in frame, generic point-edge pairs
   DevBuf aidx;          // uint32 [na] candidate index of each active pair
   DevBuf bkey[2];       // uint64 [16 na]
   DevBuf bflag, bpos;   // uint32
@@ -112,6 +113,7 @@ struct cb_scene {
   DevBuf bsr_val;       // double [nnzb][9]
   DevBuf row_cnt;       // uint32 [n+1]
   int64_t nnzb = 0;
+  DevBuf horder;        // uint32 active pair indices in prep order (face / line-line pairs first)
   DevBuf hB9, hB6, hB4;  // queued reduced Hessians (packed, element-major); hB4: point-edge in its own frame
   DevBuf hslot;          // uint32 [2][na] active index of each queued matrix
   DevBuf xf, pf;         // float [3][n]: centred FP32 copies of x and of p
@@ -155,7 +157,8 @@ enum {
   SC_NU = 15,           // CCD pairs left unresolved by the first step
   SC_FP32_PAIRS = 12,   // broad phase of contact_build: pairs passing the FP32 box test
   SC_FP64_DECIDED = 13, // ... of which the FP64 boxes decided
-  SC_N = 16
+  SC_KSPLIT = 16,       // two uint32 counters: face / line-line pairs, the other active pairs
+  SC_N = 17
 };
 
 static inline uint64_t* scalars(cb_scene* s) { return (uint64_t*)s->dev_scalars.p; }
