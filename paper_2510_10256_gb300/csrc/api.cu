@@ -58,7 +58,7 @@ static cb_status upload(DevBuf& b, const T* h, size_t count, cudaStream_t st) {
 static void scene_release(cb_scene* s) {
   cudaStream_t st = s->last_stream;
   DevBuf* bufs[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->frest,
-                    &s->frest_dbar, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
+                    &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
                     &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col, &s->bsr_val,
                     &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->mp, &s->vsc, &s->macc, &s->hstage, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag, &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist,
                     &s->dev_scalars};
@@ -287,6 +287,7 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
     if ((rc = read_scalars(s, SC_COUNT1, 1, &h, st)) != CB_OK) return fail(rc);
     s->n_frest_pt = (int64_t)h;
   }
+  if ((rc = frest_rows_build(s, st)) != CB_OK) return fail(rc);
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CB_ERR_CUDA);
   *out = s;
   return CB_OK;
@@ -400,6 +401,7 @@ cb_status cb_batch_create(cb_scene* const* members, int32_t count, void* stream,
   if (cudaGetLastError() != cudaSuccess) return fail(CB_ERR_CUDA);
   b->n_frest = b->kind == CB_SHELL ? nf : 0;
   b->n_frest_pt = nf_pt;
+  if ((rc = frest_rows_build(b, st)) != CB_OK) return fail(rc);
   for (auto& e : b->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(CB_ERR_CUDA);
   if ((rc = upload_members(b, st)) != CB_OK) return fail(rc);
@@ -695,7 +697,7 @@ cb_status cb_get_stats(cb_scene* s, cb_stats* o) {
   o->n_hess_pe = s->n_hq[2];
   size_t bytes = 0;
   const DevBuf* all[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->frest,
-                         &s->frest_dbar, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls,
+                         &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls,
                          &s->aidx, &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col,
                          &s->bsr_val, &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag,
                          &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist};

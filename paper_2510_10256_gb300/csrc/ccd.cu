@@ -30,6 +30,7 @@
 
 #include "bound32.cuh"
 #include "geometry.cuh"
+#include "frest.cuh"
 #include "prims.cuh"
 #include "scene.cuh"
 
@@ -48,7 +49,9 @@ struct CcdArgs {
   const int32_t* __restrict__ tv;
   const int32_t* __restrict__ comp;
   const int32_t* __restrict__ win;
-  const uint64_t* __restrict__ frest;
+  const uint64_t* __restrict__ frest;  // sorted rest-filtered keys
+  const uint32_t* __restrict__ frow_pt;  // ... their row offsets by vertex and by edge (frest.cuh)
+  const uint32_t* __restrict__ frow_ee;
   int64_t nf;
   int T, n, kind;
   const int32_t* __restrict__ vsc;           // member of each vertex
@@ -85,13 +88,7 @@ __device__ __forceinline__ bool is_filtered(const CcdArgs& A, const MemberParams
   if (M.filter_off) return false;
   if (A.kind == CB_ROD) return A.comp[A.ev0[ki]] == A.comp[A.ev0[kj]] && (int)kj <= A.win[ki];
   if (A.nf <= 0) return false;
-  int64_t lo = 0, hi = A.nf;
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if (A.frest[mid] < key) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo < A.nf && A.frest[lo] == key;
+  return frest_contains(A.frest, A.frow_pt, A.frow_ee, key);
 }
 
 // Everything additive CCD needs before its first step.
@@ -428,6 +425,8 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     A.comp = bp<int32_t>(s->comp);
     A.win = bp<int32_t>(s->win);
     A.frest = bp<uint64_t>(s->frest);
+    A.frow_pt = bp<uint32_t>(s->frow_pt);
+    A.frow_ee = bp<uint32_t>(s->frow_ee);
     A.nf = s->n_frest;
     A.T = s->T;
     A.n = s->n;

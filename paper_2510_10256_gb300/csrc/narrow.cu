@@ -6,6 +6,7 @@
 
 #include "bound32.cuh"
 #include "geometry.cuh"
+#include "frest.cuh"
 #include "prims.cuh"
 #include "scene.cuh"
 
@@ -138,7 +139,8 @@ __global__ void k_filter_rod(int64_t nc, const uint64_t* __restrict__ cand, cons
 }
 
 __global__ void k_filter_shell(int64_t nc, const uint64_t* __restrict__ cand, const uint64_t* __restrict__ frest,
-                               int64_t nf, const int32_t* __restrict__ ev0, const int32_t* __restrict__ vsc,
+                               const uint32_t* __restrict__ row_pt, const uint32_t* __restrict__ row_ee, int64_t nf,
+                               const int32_t* __restrict__ ev0, const int32_t* __restrict__ vsc,
                                const MemberParams* __restrict__ mp, uint8_t* __restrict__ klass,
                                unsigned long long* __restrict__ nfilt) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -146,15 +148,7 @@ __global__ void k_filter_shell(int64_t nc, const uint64_t* __restrict__ cand, co
   if (c < nc) {
     const uint64_t key = cand[c];
     const int v0 = cb_key_type(key) == CB_KEY_PT ? (int)cb_key_i(key) : ev0[cb_key_i(key)];
-    if (!mp[vsc[v0]].filter_off && nf > 0) {
-      int64_t lo = 0, hi = nf;
-      while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (frest[mid] < key) lo = mid + 1;
-        else hi = mid;
-      }
-      f = (lo < nf && frest[lo] == key) ? 1u : 0u;
-    }
+    if (!mp[vsc[v0]].filter_off && nf > 0) f = frest_contains(frest, row_pt, row_ee, key) ? 1u : 0u;
     klass[c] = (uint8_t)f;
   }
   uint32_t b = __ballot_sync(0xffffffffu, f);
@@ -207,10 +201,26 @@ __device__ __forceinline__ void warp_append(bool flag, uint32_t value, uint32_t*
   if (flag) list[base + __popc(m & ((1u << lane) - 1u))] = value;
 }
 
+// Warp-aggregated append from the end of a list of cap entries backwards.
+__device__ __forceinline__ void warp_append_back(bool flag, uint32_t value, uint32_t* __restrict__ list,
+                                                 int64_t cap, unsigned int* __restrict__ count) {
+  const unsigned m = __ballot_sync(0xffffffffu, flag);
+  if (!m) return;
+  const unsigned lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if ((int)lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (flag) list[cap - 1 - (int64_t)(base + __popc(m & ((1u << lane) - 1u)))] = value;
+}
+
 // Per candidate, phase 1: an FP32 lower bound of the distance.  Candidates it
 // places beyond every threshold of their class (U: a, which is above xi; F:
 // dbar_min) are inactive and not class C.  The rest are queued for the exact
-// FP64 phase, so that no warp pays for FP64 on behalf of a few lanes.
+// FP64 phase, so that no warp pays for FP64 on behalf of a few lanes:
+// point-triangle pairs from the start of the list (count nlist[0]), edge-edge
+// pairs from its end backwards (count nlist[1]), so that the exact kernel's
+// warps run one of the two distance routines.
 __global__ void k_distance_screen(int64_t nc, const uint64_t* __restrict__ cand,
                                   const uint8_t* __restrict__ klass_in, const int32_t* __restrict__ ev0,
                                   const int32_t* __restrict__ ev1, const int32_t* __restrict__ tv, int T,
@@ -220,9 +230,10 @@ __global__ void k_distance_screen(int64_t nc, const uint64_t* __restrict__ cand,
                                   uint32_t* __restrict__ flag, uint32_t* __restrict__ list,
                                   unsigned int* __restrict__ nlist) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool exact = false;
+  bool exact = false, ee = false;
   if (c < nc) {
     Stencil s = stencil_of(cand[c], ev0, ev1, tv, T);
+    ee = s.ee;
     const int k = klass_in[c];
     const int mem = vsc[s.v[0]];
     const MemberParams& M = mp[mem];
@@ -245,11 +256,13 @@ __global__ void k_distance_screen(int64_t nc, const uint64_t* __restrict__ cand,
       exact = true;
     }
   }
-  warp_append(exact, (uint32_t)c, list, nlist);
+  warp_append(exact && !ee, (uint32_t)c, list, &nlist[0]);
+  warp_append_back(exact && ee, (uint32_t)c, list, nc, &nlist[1]);
 }
 
 // phase 2: exact FP64 distance, class C and activity of the queued candidates
-__global__ void k_distance_exact(const uint32_t* __restrict__ list, const unsigned int* __restrict__ nlist,
+// (list entries [0, nlist[0]) and [cap - nlist[1], cap))
+__global__ void k_distance_exact(const uint32_t* __restrict__ list, int64_t cap, const unsigned int* __restrict__ nlist,
                                  const uint64_t* __restrict__ cand, const uint8_t* __restrict__ klass_in,
                                  const int32_t* __restrict__ ev0, const int32_t* __restrict__ ev1,
                                  const int32_t* __restrict__ tv, int T, const double* __restrict__ x, int n,
@@ -258,11 +271,11 @@ __global__ void k_distance_exact(const uint32_t* __restrict__ list, const unsign
                                  uint8_t* __restrict__ cls, uint32_t* __restrict__ flag,
                                  unsigned long long* __restrict__ status, unsigned long long* __restrict__ ncore,
                                  unsigned long long* __restrict__ macc) {
-  const unsigned m = *nlist;
+  const unsigned m0 = nlist[0], m = m0 + nlist[1];
   for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w - threadIdx.x < m; w += gridDim.x * blockDim.x) {
     uint32_t is_core = 0;
     if (w < m) {
-      const uint32_t c = list[w];
+      const uint32_t c = w < m0 ? list[w] : list[cap - 1 - (int64_t)(w - m0)];
       Stencil s = stencil_of(cand[c], ev0, ev1, tv, T);
       int k = klass_in[c];
       const int mem = vsc[s.v[0]];
@@ -1794,6 +1807,34 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
   return CB_OK;
 }
 
+// Row offsets of the sorted rest-filter table: row[r] = first index whose key
+// is at or above (type, r, 0), for r = 0..nrows (row[nrows] ends the type).
+__global__ void k_frest_rows(int64_t nrows, uint32_t type, const uint64_t* __restrict__ frest, int64_t nf,
+                             uint32_t* __restrict__ row) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > nrows) return;
+  const uint64_t bound = ((uint64_t)type << 62) | ((uint64_t)r << 31);
+  int64_t lo = 0, hi = nf;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (frest[mid] < bound) lo = mid + 1;
+    else hi = mid;
+  }
+  row[r] = (uint32_t)lo;
+}
+
+cb_status frest_rows_build(cb_scene* s, cudaStream_t st) {
+  if (s->kind != CB_SHELL || s->n_frest <= 0) return CB_OK;
+  CB_TRY(buf_ensure(s->frow_pt, sizeof(uint32_t) * ((size_t)s->n + 1), st));
+  CB_TRY(buf_ensure(s->frow_ee, sizeof(uint32_t) * ((size_t)s->E + 1), st));
+  k_frest_rows<<<cb_grid((int64_t)s->n + 1), CB_THREADS, 0, cb_count(st)>>>(s->n, CB_KEY_PT, bp<uint64_t>(s->frest),
+                                                                           s->n_frest, bp<uint32_t>(s->frow_pt));
+  k_frest_rows<<<cb_grid((int64_t)s->E + 1), CB_THREADS, 0, cb_count(st)>>>(s->E, CB_KEY_EE, bp<uint64_t>(s->frest),
+                                                                           s->n_frest, bp<uint32_t>(s->frow_ee));
+  CB_CUDA(cudaGetLastError());
+  return CB_OK;
+}
+
 cb_status filter_apply(cb_scene* s, cudaStream_t st) {
   const int64_t nc = s->n_cand;
   CB_TRY(buf_ensure(s->klass, (size_t)std::max<int64_t>(1, nc), st));
@@ -1806,8 +1847,8 @@ cb_status filter_apply(cb_scene* s, cudaStream_t st) {
         bp<int32_t>(s->vsc), bp<MemberParams>(s->mp), bp<uint8_t>(s->klass), nf);
   else
     k_filter_shell<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(
-        nc, bp<uint64_t>(s->cand), bp<uint64_t>(s->frest), s->n_frest, bp<int32_t>(s->ev0), bp<int32_t>(s->vsc),
-        bp<MemberParams>(s->mp), bp<uint8_t>(s->klass), nf);
+        nc, bp<uint64_t>(s->cand), bp<uint64_t>(s->frest), bp<uint32_t>(s->frow_pt), bp<uint32_t>(s->frow_ee),
+        s->n_frest, bp<int32_t>(s->ev0), bp<int32_t>(s->vsc), bp<MemberParams>(s->mp), bp<uint8_t>(s->klass), nf);
   CB_CUDA(cudaGetLastError());
   return CB_OK;
 }
@@ -1859,7 +1900,7 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
         bp<MemberParams>(s->mp), s->n, bp<double>(s->cd),
         bp<int8_t>(s->ctype), bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), bp<uint32_t>(s->dlist), nl);
     k_distance_exact<<<std::min<int64_t>(cb_grid(nc), 152 * 16), CB_THREADS, 0, cb_count(st)>>>(
-        bp<uint32_t>(s->dlist), nl, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass), bp<int32_t>(s->ev0),
+        bp<uint32_t>(s->dlist), nc, nl, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass), bp<int32_t>(s->ev0),
         bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T, x, s->n, bp<int32_t>(s->vsc), bp<MemberParams>(s->mp),
         bp<double>(s->cd), bp<int8_t>(s->ctype), bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), status, ncore,
         macc);

@@ -91,6 +91,8 @@ struct cb_scene {
   DevBuf frest;         // uint64 shells: sorted rest-filtered keys
   DevBuf frest_dbar;    // double
   int64_t n_frest = 0;
+  DevBuf frow_pt;       // uint32 shells: row offsets of frest by vertex (point-triangle keys), n + 1
+  DevBuf frow_ee;       // uint32 shells: row offsets of frest by edge (edge-edge keys), E + 1
 
   // pass state
   BroadWork bw;         // static broad phase
@@ -152,7 +154,7 @@ enum {
   SC_NCORE = 8,
   SC_N9 = 9,
   SC_N6 = 10,
-  SC_NLIST = 11,
+  SC_NLIST = 11,        // two uint32 counters: point-triangle and edge-edge pairs for the exact distance
   SC_N4 = 14,           // point-edge pairs queued in their own frame
   SC_NU = 15,           // CCD pairs left unresolved by the first step
   SC_FP32_PAIRS = 12,   // broad phase of contact_build: pairs passing the FP32 box test
@@ -181,6 +183,7 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
 // narrow.cu
 cb_status filter_precompute(cb_scene* s, cudaStream_t st);
 cb_status filter_apply(cb_scene* s, cudaStream_t st);
+cb_status frest_rows_build(cb_scene* s, cudaStream_t st);
 cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad, cudaStream_t st);
 
 // ccd.cu
