@@ -30,14 +30,17 @@ UNIT = "pairs/s"
 # FP64 peak from the part's unit counts and clock: 152 SMs x 2070 MHz x 4 FP64
 # flop/clk/SM (2 DFMA) = 1.26 TFLOP/s, the 1.25 TFLOP/s dense FP64 figure.
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
-# FP64 flop of the stage-(d) kernels per pair each one handles (DADD + DMUL +
-# 2 DFMA executed, from ncu on the 128x128 pleated sheet): k_hess_prep per
+# FP64 flop of the stage-(d) kernels per pair each one handles: DADD + DMUL +
+# 2 DFMA thread instructions executed, counted by ncu on the 128x128 pleated
+# sheet (195,263 active pairs: 30,807 face / line-line, 151,976 point-edge in
+# their frame) and divided by the pairs of each kernel.  k_hess_prep per
 # active pair, k_hess_proj<9> per face / line-line pair, k_hess_proj_pe per
-# point-edge pair in its own frame, k_hess_proj<6> per generic point-edge pair
-HESS_FLOPS = {"prep": 1500.0, "face": 9000.0, "pe_frame": 800.0, "pe": 3000.0}
+# point-edge pair in its own frame; k_hess_proj<6> (generic point-edge pairs,
+# none in that capture) is scaled from k_hess_proj<9> by (6/9)^3.
+HESS_FLOPS = {"prep": 601.2, "face": 11471.0, "pe_frame": 1269.9, "pe": 11471.0 * (6 / 9) ** 3}
 # DRAM bytes (read + write) of the stage-(d) kernels per active pair, from the
-# same capture; traffic grows in proportion to the active pairs
-HESS_DRAM_BYTES_PER_ACTIVE = 700.0
+# same capture (136.0 MB); traffic grows in proportion to the active pairs
+HESS_DRAM_BYTES_PER_ACTIVE = 136.0e6 / 195263
 
 
 def hess_flops(st) -> float:

@@ -116,11 +116,26 @@ static cb_status alloc_members(cb_scene* s, cudaStream_t st) {
   CB_TRY(buf_ensure(s->macc, sizeof(unsigned long long) * MACC_STRIDE * (size_t)M, st));
   CB_TRY(buf_ensure(s->hstage, sizeof(double) * (size_t)M + 64, st));
   CB_CUDA(cudaMemsetAsync(s->macc.p, 0, sizeof(unsigned long long) * MACC_STRIDE * (size_t)M, st));
-  if (cudaMallocHost(&s->hstage_host, 64 * (size_t)M + 256) != cudaSuccess) return CB_ERR_OOM;
+  // per member: the largest record staged through it (member parameters,
+  // the CCD accumulators, the broad phase's four doubles)
+  const size_t per = std::max({sizeof(MemberParams), sizeof(unsigned long long) * MACC_STRIDE, 4 * sizeof(double)});
+  if (cudaMallocHost(&s->hstage_host, per * (size_t)M + 256) != cudaSuccess) return CB_ERR_OOM;
   return CB_OK;
 }
 
+static float float_up(double v) {
+  float f = (float)v;
+  if ((double)f < v) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
 static cb_status upload_members(cb_scene* s, cudaStream_t st) {
+  for (MemberParams& m : s->hmp) {
+    m.thrU32 = float_up(m.a * (1.0 + 1e-9) + 1e-9);
+    m.thrF32 = float_up(m.dbar_min * (1.0 + 1e-9) + 1e-9);
+    m.thrC32 = float_up(m.xi * (1.0 + 1e-9) + 1e-9);
+    m.xi32 = float_up(m.xi);
+  }
   memcpy(s->hstage_host, s->hmp.data(), sizeof(MemberParams) * s->hmp.size());
   CB_CUDA(cudaMemcpyAsync(s->mp.p, s->hstage_host, sizeof(MemberParams) * s->hmp.size(), cudaMemcpyHostToDevice, st));
   CB_CUDA(cudaStreamSynchronize(st));

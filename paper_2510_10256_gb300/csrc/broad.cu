@@ -308,8 +308,17 @@ struct PairArgs {
 };
 
 // count pass (FILL = false): cnt[i] = number of pairs entry i reports;
-// fill pass (FILL = true): writes them at off[i] (cnt read back as the bound)
-template <bool FILL>
+// fill pass (FILL = true): writes them at off[i] (cnt read back as the bound).
+// A vertex entry of a shell cell tests every triangle entry of the cell (the
+// vertex threads of a cell walk the same triangles in step) and an edge entry
+// every later edge entry.  Rod cells hold many more edges (yarn segments
+// crowd the cells of a knit or weave), so there the m (m - 1) / 2 tests of a
+// cell are shared by its m entries in round-robin order (entry a with
+// a + 1, ..., a + (m - 1) / 2 mod m, and with a + m/2 for a < m/2 when m is
+// even): every thread makes about (m - 1) / 2 tests instead of the first one
+// m - 1 and the last none.  (On shell cells the round robin measured slightly
+// slower.)
+template <bool FILL, bool RR>
 __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __restrict__ cnt,
                                                       const uint32_t* __restrict__ off, uint64_t* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -350,7 +359,20 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __re
   uint64_t w = FILL ? off[i] : 0;
   // the fill pass re-makes the count pass's decisions; never write past them
   const uint64_t w_end = FILL ? w + cnt[i] : 0;
-  for (int j = j0; j < j1; ++j) {
+  // RR (rod scenes): round robin over the cell (entries are sorted by
+  // primitive, so the key takes the lower of the two first); else j in [j0, j1)
+  const int m = e - s, a = (int)(i - s);
+  if (RR) {
+    j0 = 0;
+    j1 = (m % 2 == 0 && a < m / 2) ? m / 2 : (m - 1) / 2;
+  }
+  for (int jj = j0; jj < j1; ++jj) {
+    int j = jj;
+    if (RR) {
+      j = a + 1 + jj;
+      if (j >= m) j -= m;
+      j += s;
+    }
     const uint32_t Q = A.eval[j];
     const float4 qlo = A.ebox[2 * (size_t)j], qhi = A.ebox[2 * (size_t)j + 1];
     if (!(plo.x <= qhi.x && qlo.x <= phi.x && plo.y <= qhi.y && qlo.y <= phi.y && plo.z <= qhi.z &&
@@ -383,8 +405,13 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __re
       if (!ok) continue;
     }
     if (FILL) {
-      if (w < w_end)
-        out[w++] = A.canonical ? cb_key(type, P - ibase, Q - jbase) : (tbits | ipart | (uint64_t)(Q - jbase));
+      if (w < w_end) {
+        if (RR && j < (int)i)  // the partner is the lower primitive
+          out[w++] = A.canonical ? cb_key(type, Q - ibase, P - jbase)
+                                 : (tbits | ((uint64_t)(Q - ibase) << A.bj) | (uint64_t)(P - jbase));
+        else
+          out[w++] = A.canonical ? cb_key(type, P - ibase, Q - jbase) : (tbits | ipart | (uint64_t)(Q - jbase));
+      }
     } else {
       ++count;
     }
@@ -567,7 +594,19 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     CB_CUDA(cudaMemsetAsync(A.fpstat, 0, 2 * sizeof(unsigned long long), st));
   }
   const int pb = w.pair_block;
-  k_pairs<false><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, bp<uint32_t>(w.pair_cnt), nullptr, nullptr);
+  const bool rods = s->kind == CB_ROD;
+  auto pairs = [&](bool fill, uint64_t* o) {
+    uint32_t* c = bp<uint32_t>(w.pair_cnt);
+    const uint32_t* f = fill ? bp<uint32_t>(w.pair_off) : nullptr;
+    if (fill) {
+      if (rods) k_pairs<true, true><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o);
+      else k_pairs<true, false><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o);
+    } else {
+      if (rods) k_pairs<false, true><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o);
+      else k_pairs<false, false><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o);
+    }
+  };
+  pairs(false, nullptr);
   cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off), ne,
                                           bp<uint32_t>(w.scan_tmp), tot_dev, st);
   CB_CUDA(cudaGetLastError());
@@ -580,15 +619,13 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     // canonical keys straight from the fill pass, in hash-cell order
     A.canonical = true;
     CB_TRY(buf_ensure(out, sizeof(uint64_t) * (size_t)nc, st));
-    k_pairs<true><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off),
-                                                            bp<uint64_t>(out));
+    pairs(true, bp<uint64_t>(out));
     CB_CUDA(cudaGetLastError());
     return CB_OK;
   }
   A.canonical = false;
   for (int b = 0; b < 2; ++b) CB_TRY(buf_ensure(w.ckey[b], sizeof(uint64_t) * (size_t)nc, st));
-  k_pairs<true><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off),
-                                                          bp<uint64_t>(w.ckey[0]));
+  pairs(true, bp<uint64_t>(w.ckey[0]));
   const int cbits = s->bits_i + s->bits_j + (s->kind == CB_SHELL ? 2 : 0);
   CB_TRY(buf_ensure(w.hist, sizeof(uint32_t) * (size_t)cbp::radix_hist_elems(nc), st));
   CB_TRY(buf_ensure(w.scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(cbp::radix_hist_elems(nc)) + 8),

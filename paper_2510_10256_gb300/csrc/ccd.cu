@@ -185,6 +185,11 @@ __device__ __forceinline__ void warp_append(bool flag, uint32_t value, uint32_t*
 // l_p give a lower bound of the first step.  A pair whose class is certain and
 // whose bound exceeds 1 is resolved (t_p = 1); a smaller bound is kept as its
 // lower bound.  Pairs the FP32 bounds cannot settle are queued for pass 1b.
+// The bound is formed in FP32 with every operation rounded towards the safe
+// side (__f*_rd for lower bounds, __f*_ru for upper ones) and a final factor
+// 1 - 2^-23, so it stays below the first step as FP64 evaluates it; the
+// thresholds are the members' FP32 copies rounded up.  (FP64 would put ~25
+// operations per candidate on the FP64 pipe, which issues 1/64 as fast.)
 __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restrict__ lb_out,
                                                     uint32_t* __restrict__ list, unsigned int* __restrict__ nlist) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,10 +221,9 @@ __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restric
     const double Xd = A.cx[4 * mem + 3];
     const float lb = cbb::lower_bound(ee, ldf(A.xf, A.n, v[0]), ldf(A.xf, A.n, v[1]), ldf(A.xf, A.n, v[2]),
                                       ldf(A.xf, A.n, v[3]), (float)Xd);
-    const double thrC = M.xi * (1.0 + 1e-9) + 1e-9;   // surely not class C above this
-    if (filt || (double)lb >= thrC) {
+    if (filt || lb >= M.thrC32) {  // surely not class C at or above thrC32
       const int cls = filt ? 1 : 0;
-      const double off = (cls == 0 && !M.single) ? M.xi : 0.0;
+      const float off = (cls == 0 && !M.single) ? M.xi32 : 0.f;
       const cbb::f3 p0 = ldf(A.pf, A.n, v[0]), p1 = ldf(A.pf, A.n, v[1]), p2 = ldf(A.pf, A.n, v[2]),
                     p3 = ldf(A.pf, A.n, v[3]);
       const cbb::f3 pm = cbb::fscale3(cbb::fadd3(cbb::fadd3(p0, p1), cbb::fadd3(p2, p3)), 0.25f);
@@ -229,13 +233,15 @@ __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restric
       const float n3 = sqrtf(cbb::fdot3(cbb::fsub3(p3, pm), cbb::fsub3(p3, pm)));
       const float lp32 = ee ? fmaxf(n0, n1) + fmaxf(n2, n3) : n0 + fmaxf(fmaxf(n1, n2), n3);
       const float Pm = fmaxf(fmaxf(cbb::fmaxabs3(p0), cbb::fmaxabs3(p1)), fmaxf(cbb::fmaxabs3(p2), cbb::fmaxabs3(p3)));
-      const float u = 5.9604645e-8f;
-      const double lp_ub = (double)lp32 * (1.0 + 64.0 * u) + 64.0 * u * (double)Pm;
-      const double g_lb = (double)lb - off - 1e-12 * (1.0 + Xd);
-      if (lp32 > 1e-30f && g_lb > 0.0) {
-        const double tl_lb = (1.0 - ACCD_S) * g_lb / lp_ub * (1.0 - 1e-9);
-        const bool exact = tl_lb > 1.0 + 1e-9;
-        const double t = exact ? 1.0 : tl_lb;
+      const float u64 = 3.8146973e-6f;  // 64 u, u = 2^-24: exact
+      const float lp_ub = __fadd_ru(__fmul_ru(lp32, 1.f + u64), __fmul_ru(u64, Pm));
+      const float slack = __fmul_ru(1e-12f, __fadd_ru(1.f, __double2float_ru(Xd)));
+      const float g_lb = __fsub_rd(__fsub_rd(lb, off), slack);
+      if (lp32 > 1e-30f && g_lb > 0.f) {
+        // (1 - s) g / l_p; 0.9f rounds below 0.9 = 1 - s
+        const float tl_lb = __fmul_rd(__fdiv_rd(__fmul_rd(0.9f, g_lb), lp_ub), 0.99999988f);
+        const bool exact = tl_lb > 1.f;
+        const double t = exact ? 1.0 : (double)tl_lb;
         A.t_out[q] = t;
         if (!exact) lb_out[q] = t;
         A.cls_out[q] = (uint8_t)cls | (exact ? EXACT : 0);

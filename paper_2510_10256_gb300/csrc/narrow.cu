@@ -238,16 +238,16 @@ __global__ void k_distance_screen(int64_t nc, const uint64_t* __restrict__ cand,
     const int mem = vsc[s.v[0]];
     const MemberParams& M = mp[mem];
     // thresholds beyond which a pair is surely inactive and not class C (the
-    // 1e-9 margins cover the rounding of the FP64 decision)
-    const double thrU = M.a * (1.0 + 1e-9) + 1e-9;
-    const double thrF = M.dbar_min * (1.0 + 1e-9) + 1e-9;
+    // 1e-9 margins cover the rounding of the FP64 decision; FP32 copies
+    // rounded up, so the FP32 comparison is as safe)
+    const float thr = k == 1 ? M.thrF32 : M.thrU32;
     const float X = (float)cx[4 * mem + 3];
     const float lb = cbb::lower_bound(
         s.ee, cbb::f3{xf[s.v[0]], xf[(size_t)n + s.v[0]], xf[2 * (size_t)n + s.v[0]]},
         cbb::f3{xf[s.v[1]], xf[(size_t)n + s.v[1]], xf[2 * (size_t)n + s.v[1]]},
         cbb::f3{xf[s.v[2]], xf[(size_t)n + s.v[2]], xf[2 * (size_t)n + s.v[2]]},
         cbb::f3{xf[s.v[3]], xf[(size_t)n + s.v[3]], xf[2 * (size_t)n + s.v[3]]}, X);
-    if ((double)lb >= (k == 1 ? thrF : thrU)) {
+    if (lb >= thr) {
       dout[c] = __longlong_as_double(0x7ff0000000000000LL);
       tout[c] = -1;
       cls[c] = (uint8_t)k;

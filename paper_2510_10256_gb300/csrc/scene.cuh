@@ -23,6 +23,10 @@ struct MemberParams {
   double xi, dhat, a, kappa;
   double dbar_min;        // 0 when nothing is filtered
   int32_t single, core_temp, filter_off, n_prims;
+  // FP32 copies rounded up, for the screens' rigorous FP32 comparisons (set
+  // at upload): a (1 + 1e-9) + 1e-9, dbar_min (1 + 1e-9) + 1e-9,
+  // xi (1 + 1e-9) + 1e-9, xi
+  float thrU32, thrF32, thrC32, xi32;
 };
 
 // Spatial-hash grid of one member.
@@ -75,7 +79,7 @@ struct cb_scene {
   int64_t n_frest_pt = 0;                 // shells: point-triangle keys at the head of frest
   DevBuf macc;          // per member: double energy, u64 alpha bits, u64 lb bits, u64 status, double lo, hi
   DevBuf hstage;        // device copy of per-member box inflation
-  void* hstage_host = nullptr;  // pinned staging (64 bytes per member + 256)
+  void* hstage_host = nullptr;  // pinned staging (the largest per-member record x members + 256)
   cudaStream_t last_stream = nullptr;
   int device = 0;
 
