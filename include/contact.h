@@ -152,6 +152,17 @@ cb_status contact_filter(cb_scene* scene, void* stream);
 cb_status barrier_eval(cb_scene* scene, const double* x_dev, double* energy_dev, double* grad_dev,
                        void* stream);
 
+/* (c)+(d) energy only, for the line search over the step that ccd_step
+ * bounds: E = kappa sum b(y, dhat_p) over the active candidates of the last
+ * contact_build / contact_filter, with the distances, classes and pair
+ * parameters of barrier_eval (Eq. 2-4), and neither gradient nor Hessian.
+ * Call contact_build and contact_filter at the trial positions first.
+ * energy_dev: DEVICE 1 double per member (overwritten; +inf on penetration,
+ * which also sets CB_ERR_PENETRATION in the status word).  Leaves no active
+ * list or BSR matrix (their getters return none until the next barrier_eval).
+ * Errors: CB_ERR_ARG for a NULL scene, x_dev or energy_dev. */
+cb_status barrier_energy(cb_scene* scene, const double* x_dev, double* energy_dev, void* stream);
+
 /* (e) CCD step bound, Sec. 3.3: candidates are pairs whose swept boxes (x and
  * x + p) inflated by offset/2 overlap; each is bounded by additive CCD
  * (s = 0.1, inner factor 0.9) against its class offset (U: offset; F, C: 0).
@@ -196,6 +207,13 @@ cb_status cb_get_bsr(cb_scene* scene, int32_t* row_ptr, int32_t* col, double* va
 /* device pointers of the scene-owned BSR (valid until the next barrier_eval) */
 cb_status cb_bsr_device(cb_scene* scene, const int32_t** row_ptr, const int32_t** col,
                         const double** val, int64_t* nnzb);
+/* y = (H + shift I) v with H the BSR matrix of the last barrier_eval (the
+ * product of a Newton driver's conjugate-gradient solve; App. A).
+ * v_dev, y_dev: DEVICE [3][n] FP64, distinct buffers.  Asynchronous.
+ * After barrier_energy (no BSR) H counts as zero.
+ * Errors: CB_ERR_ARG for a NULL scene / vector, v_dev == y_dev, or a scene
+ * with no barrier_eval / barrier_energy yet. */
+cb_status cb_bsr_spmv(cb_scene* scene, const double* v_dev, double* y_dev, double shift, void* stream);
 cb_status cb_get_stats(cb_scene* scene, cb_stats* stats);
 /* sync: first device-side condition since the last call (then cleared) */
 cb_status cb_sync_status(cb_scene* scene);

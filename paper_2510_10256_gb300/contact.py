@@ -31,7 +31,7 @@ ABI_FUNCTIONS = ["cb_scene_create", "cb_scene_destroy", "contact_build", "contac
                  "cb_get_stats", "cb_sync_status", "cb_get_stage_ms", "cb_set_timing", "cb_status_str",
                  "cb_version", "cb_kernel_launches", "cb_measure_fma_tflops", "cb_batch_create",
                  "cb_batch_offsets", "cb_member_count", "ccd_step_noalloc", "cb_set_tuning",
-                 "cb_get_tuning"]
+                 "cb_get_tuning", "barrier_energy", "cb_bsr_spmv"]
 
 
 class ContactError(RuntimeError):
@@ -86,6 +86,8 @@ def lib():
         L.contact_build.argtypes = [vp, vp, vp]
         L.contact_filter.argtypes = [vp, vp]
         L.barrier_eval.argtypes = [vp, vp, vp, vp, vp]
+        L.barrier_energy.argtypes = [vp, vp, vp, vp]
+        L.cb_bsr_spmv.argtypes = [vp, vp, vp, C.c_double, vp]
         L.ccd_step.argtypes = [vp, vp, vp, vp, vp]
         L.cb_get_pairs.argtypes = [vp, i32, vp, i64, C.POINTER(i64)]
         L.cb_get_active.argtypes = [vp, vp, vp, vp, vp, i64, C.POINTER(i64)]
@@ -243,6 +245,17 @@ class ContactScene:
     def barrier_eval(self, x, energy=None, grad=None, stream=None):
         _check(lib().barrier_eval(self.h, _dev_ptr(x, self.n), _dev_ptr(energy, None, False),
                                   _dev_ptr(grad, self.n), _stream_ptr(stream)), "barrier_eval")
+
+    def barrier_energy(self, x, energy, stream=None):
+        """Energy only (no gradient, Hessian or BSR) at x, over the candidates
+        of the last contact_build / contact_filter: the line-search call."""
+        _check(lib().barrier_energy(self.h, _dev_ptr(x, self.n), _dev_ptr(energy, None, False),
+                                    _stream_ptr(stream)), "barrier_energy")
+
+    def bsr_spmv(self, v, y, shift: float = 0.0, stream=None):
+        """y = (H + shift I) v with the BSR Hessian of the last barrier_eval."""
+        _check(lib().cb_bsr_spmv(self.h, _dev_ptr(v, self.n), _dev_ptr(y, self.n), float(shift),
+                                 _stream_ptr(stream)), "cb_bsr_spmv")
 
     def ccd_step(self, x, p, alpha=None, stream=None):
         _check(lib().ccd_step(self.h, _dev_ptr(x, self.n), _dev_ptr(p, self.n),

@@ -476,7 +476,17 @@ cb_status barrier_eval(cb_scene* s, const double* x, double* energy, double* gra
   cudaStream_t st = (cudaStream_t)stream;
   s->last_stream = st;
   stage_begin(s, 2, st);
-  cb_status r = barrier_run(s, x, energy, grad, st);
+  cb_status r = barrier_run(s, x, energy, grad, false, st);
+  stage_end(s, 2, st);
+  return r;
+}
+
+cb_status barrier_energy(cb_scene* s, const double* x, double* energy, void* stream) {
+  if (!s || !x || !energy) return CB_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  s->last_stream = st;
+  stage_begin(s, 2, st);
+  cb_status r = barrier_run(s, x, energy, nullptr, true, st);
   stage_end(s, 2, st);
   return r;
 }

@@ -188,6 +188,34 @@ __device__ __forceinline__ void pair_params(const PassParams& P, int k, double& 
   }
 }
 
+// The IPC barrier of Eq. 2-4 in y = d - xi_p with width dh:
+//   b = -(y - dh)^2 log(y / dh) for 0 < y < dh, and its first two derivatives.
+__device__ __forceinline__ double barrier_b(double y, double dh) {
+  const double r = y - dh;
+  return -(r * r) * log(y / dh);
+}
+__device__ __forceinline__ void barrier_b012(double y, double dh, double& b, double& b1, double& b2) {
+  const double r = y - dh, l = log(y / dh), iy = 1.0 / y;
+  b = -(r * r) * l;
+  b1 = -2.0 * r * l - (r * r) * iy;
+  b2 = -2.0 * l - 4.0 * r * iy + (r * r) * (iy * iy);
+}
+
+// Per-member sum of lane values: one atomic per warp when the warp holds one
+// member (lanes without a value pass mem < 0), one per lane otherwise.  Every
+// lane of the warp must call it.
+__device__ __forceinline__ void member_energy_add(unsigned long long* __restrict__ macc, int mem, double e) {
+  const int m0 = __shfl_sync(0xffffffffu, mem, 0);
+  if (__all_sync(0xffffffffu, mem == m0 || mem < 0)) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0 && e != 0.0 && m0 >= 0)
+      atomicAdd((double*)&macc[(size_t)m0 * MACC_STRIDE + MACC_E], e);
+  } else if (mem >= 0 && e != 0.0) {
+    atomicAdd((double*)&macc[(size_t)mem * MACC_STRIDE + MACC_E], e);
+  }
+}
+
 // Warp-aggregated append of flagged lanes' values to a list.
 __device__ __forceinline__ void warp_append(bool flag, uint32_t value, uint32_t* __restrict__ list,
                                             unsigned int* __restrict__ count) {
@@ -261,7 +289,9 @@ __global__ void k_distance_screen(int64_t nc, const uint64_t* __restrict__ cand,
 }
 
 // phase 2: exact FP64 distance, class C and activity of the queued candidates
-// (list entries [0, nlist[0]) and [cap - nlist[1], cap))
+// (list entries [0, nlist[0]) and [cap - nlist[1], cap)).  With energy set
+// (the energy-only pass), every active pair also adds kappa b(y) to its
+// member's energy.
 __global__ void k_distance_exact(const uint32_t* __restrict__ list, int64_t cap, const unsigned int* __restrict__ nlist,
                                  const uint64_t* __restrict__ cand, const uint8_t* __restrict__ klass_in,
                                  const int32_t* __restrict__ ev0, const int32_t* __restrict__ ev1,
@@ -270,10 +300,12 @@ __global__ void k_distance_exact(const uint32_t* __restrict__ list, int64_t cap,
                                  double* __restrict__ dout, int8_t* __restrict__ tout,
                                  uint8_t* __restrict__ cls, uint32_t* __restrict__ flag,
                                  unsigned long long* __restrict__ status, unsigned long long* __restrict__ ncore,
-                                 unsigned long long* __restrict__ macc) {
+                                 unsigned long long* __restrict__ macc, bool energy) {
   const unsigned m0 = nlist[0], m = m0 + nlist[1];
   for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w - threadIdx.x < m; w += gridDim.x * blockDim.x) {
     uint32_t is_core = 0;
+    double e_local = 0.0;
+    int e_mem = -1;
     if (w < m) {
       const uint32_t c = w < m0 ? list[w] : list[cap - 1 - (int64_t)(w - m0)];
       Stencil s = stencil_of(cand[c], ev0, ev1, tv, T);
@@ -297,7 +329,12 @@ __global__ void k_distance_exact(const uint32_t* __restrict__ list, int64_t cap,
       cls[c] = (uint8_t)k;
       flag[c] = act;
       is_core = (k == 2);
+      if (energy && act && y > 0.0) {
+        e_local = P.kappa * barrier_b(y, dh_p);
+        e_mem = mem;
+      }
     }
+    if (energy) member_energy_add(macc, e_mem, e_local);
     const uint32_t b = __ballot_sync(0xffffffffu, is_core);
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(ncore, (unsigned long long)__popc(b));
   }
@@ -825,12 +862,7 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
     pair_params(P, A.ccls[c], xi_p, dh_p);
     const double y = d - xi_p;
     double b, b1, b2;
-    {
-      const double r = y - dh_p, l = log(y / dh_p), iy = 1.0 / y;
-      b = -(r * r) * l;
-      b1 = -2.0 * r * l - (r * r) * iy;
-      b2 = -2.0 * l - 4.0 * r * iy + (r * r) * (iy * iy);
-    }
+    barrier_b012(y, dh_p, b, b1, b2);
     const double kap = P.kappa;
     e_local = kap * b;
     // Point-edge: in the frame e1 along the edge (u), e3 normal to the plane
@@ -969,16 +1001,7 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
       if (e < ne) Bo[(size_t)e * A.cap + slot] = Bq[e];
     (want == 9 ? A.slot9 : (want == 6 ? A.slot6 : A.slot4))[slot] = (uint32_t)a;
   }
-  // energy per member: one atomic per warp when the warp holds one member
-  const int m0 = __shfl_sync(0xffffffffu, mem, 0);
-  if (__all_sync(0xffffffffu, mem == m0 || mem < 0)) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e_local += __shfl_xor_sync(0xffffffffu, e_local, o);
-    if (lane == 0 && e_local != 0.0 && m0 >= 0)
-      atomicAdd((double*)&A.macc[(size_t)m0 * MACC_STRIDE + MACC_E], e_local);
-  } else if (mem >= 0 && e_local != 0.0) {
-    atomicAdd((double*)&A.macc[(size_t)mem * MACC_STRIDE + MACC_E], e_local);
-  }
+  member_energy_add(A.macc, mem, e_local);
 }
 
 // Cyclic Jacobi with symmetric updates on a packed upper-triangular matrix
@@ -1867,7 +1890,8 @@ static int bits_for(int64_t v) {
   return b;
 }
 
-cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad, cudaStream_t st) {
+cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad, bool energy_only,
+                      cudaStream_t st) {
   const int64_t nc = s->n_cand;
   uint64_t* sc = scalars(s);
   unsigned long long* status = (unsigned long long*)(sc + SC_STATUS);
@@ -1903,7 +1927,12 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
         bp<uint32_t>(s->dlist), nc, nl, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass), bp<int32_t>(s->ev0),
         bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T, x, s->n, bp<int32_t>(s->vsc), bp<MemberParams>(s->mp),
         bp<double>(s->cd), bp<int8_t>(s->ctype), bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), status, ncore,
-        macc);
+        macc, energy_only);
+    if (energy_only) {
+      if (energy) k_energy_final<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, energy);
+      CB_CUDA(cudaGetLastError());
+      return CB_OK;
+    }
     uint32_t* tot = (uint32_t*)(sc + SC_COUNT1);
     cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(s->cflag), bp<uint32_t>(s->cpos), nc,
                                             bp<uint32_t>(s->scan_tmp), tot, st);

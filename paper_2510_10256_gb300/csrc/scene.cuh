@@ -188,7 +188,9 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
 cb_status filter_precompute(cb_scene* s, cudaStream_t st);
 cb_status filter_apply(cb_scene* s, cudaStream_t st);
 cb_status frest_rows_build(cb_scene* s, cudaStream_t st);
-cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad, cudaStream_t st);
+// energy_only: distances and energy (no active list, gradient, Hessian or BSR)
+cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad, bool energy_only,
+                      cudaStream_t st);
 
 // ccd.cu
 cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, cudaStream_t st);
