@@ -63,6 +63,10 @@ typedef enum {
 #define CB_FILTER_DOUBLE 0          /* Eq. 4: filtered pairs use (offset 0, width dbar_min) */
 #define CB_FILTER_SINGLE 1          /* Eq. 1: single-phase barrier, no offset */
 #define CB_FILTER_OFF 2             /* control: no filtering (plain thickness barrier) */
+#define CB_FILTER_KALDOR 3          /* comparison: no filtering, and rod edge pairs of one polyline at
+                                       most cull_radius edges apart culled (Kaldor et al.'s culling, the
+                                       paper's knot-test comparison): no barrier, no CCD constraint.
+                                       Rods only. */
 #define CB_FILTER_MASK 3
 #define CB_THICK_PAPER_LITERAL 4    /* activation a = thickness, offset = thickness - dhat */
 #define CB_NO_CORE_TEMP 8           /* disable the temporary zero offset of Sec. 3.4 */
@@ -91,6 +95,7 @@ typedef struct {
   double dhat;                /* barrier width; full activation a = thickness + dhat */
   double kappa;               /* barrier stiffness (energy scale); 1 if <= 0 */
   int32_t mode;               /* CB_FILTER_* | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP */
+  int32_t cull_radius;        /* CB_FILTER_KALDOR: culling radius in edges (>= 1); else ignored */
 } cb_scene_desc;
 
 typedef struct {

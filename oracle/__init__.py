@@ -36,7 +36,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 ROD_EE, PT, EE = 0, 1, 2
-KLASS_U, KLASS_F, KLASS_C = 0, 1, 2
+KLASS_U, KLASS_F, KLASS_C, KLASS_X = 0, 1, 2, 3   # X: culled (mode "kaldor")
 
 # additive-CCD constants (C-IPC): minimum-separation fraction s, inner step factor
 ACCD_S = 0.1
@@ -272,7 +272,20 @@ def rest_filter(scene, topo: Topology, a: float) -> tuple[np.ndarray, np.ndarray
     return _take(ok, m, np.uint64), _take(od, m, np.float64)
 
 
-MODES = ("double", "single", "off")
+MODES = ("double", "single", "off", "kaldor")
+
+
+def kaldor_culled(topo: Topology, keys: np.ndarray, radius: int) -> np.ndarray:
+    """Kaldor et al.'s culling, the comparison the paper runs against its
+    filter (the knot test, Fig. 8): rod edge pairs of one polyline at most
+    `radius` edges apart are removed from contact.  Edges are numbered
+    consecutively along each polyline, so the gap is j - i."""
+    keys = np.asarray(keys, np.uint64)
+    i = ((keys >> np.uint64(31)) & np.uint64(0x7FFFFFFF)).astype(np.int64)
+    j = (keys & np.uint64(0x7FFFFFFF)).astype(np.int64)
+    e0 = topo.edges[0].astype(np.int64)
+    same = topo.comp[e0[i]] == topo.comp[e0[j]]
+    return same & (j - i <= radius)
 
 
 @dataclass
@@ -312,8 +325,12 @@ class PassResult:
 
 def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: bool = True,
                  ccd: bool = True, x: np.ndarray | None = None, p: np.ndarray | None = None,
-                 topo: Topology | None = None, filt=None) -> PassResult:
-    """One full pass (stages a-e) at x with CCD direction p."""
+                 topo: Topology | None = None, filt=None, cull_radius: int = 0) -> PassResult:
+    """One full pass (stages a-e) at x with CCD direction p.  Mode "kaldor":
+    no filter, and rod edge pairs of one polyline at most cull_radius edges
+    apart are culled (class X: no barrier, no constraint on the step)."""
+    if mode == "kaldor" and (scene.kind != "rod" or cull_radius < 1):
+        raise ValueError("kaldor mode: rods and cull_radius >= 1")
     import time
     tm = {}
     t0 = time.perf_counter()
@@ -335,8 +352,10 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     tm["broad"] = time.perf_counter() - t1
     # (b) class
     t1 = time.perf_counter()
-    if mode == "off":
+    if mode in ("off", "kaldor"):
         klass_in = np.zeros(Cset.size, np.uint8)
+        if mode == "kaldor":
+            klass_in[kaldor_culled(topo, Cset, cull_radius)] = KLASS_X
     else:
         klass_in = np.isin(Cset, F_rest).astype(np.uint8)
     tm["filter"] = time.perf_counter() - t1
@@ -413,7 +432,7 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     # (e) CCD step bound
     if ccd:
         t1 = time.perf_counter()
-        ck, ckl, tt, it, cs = ccd_bound(scene, topo, x, p, F_rest, mode, core_temp, dbar_min)
+        ck, ckl, tt, it, cs = ccd_bound(scene, topo, x, p, F_rest, mode, core_temp, dbar_min, cull_radius)
         res.ccd_keys, res.ccd_klass, res.ccd_t, res.ccd_iters, res.ccd_status = ck, ckl, tt, it, cs
         res.alpha = float(min(1.0, tt.min())) if tt.size else 1.0
         tm["ccd"] = time.perf_counter() - t1
@@ -421,14 +440,17 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     return res
 
 
-def ccd_bound(scene, topo, x, p, F_rest, mode="double", core_temp=True, dbar_min=0.0):
+def ccd_bound(scene, topo, x, p, F_rest, mode="double", core_temp=True, dbar_min=0.0, cull_radius=0):
     """Swept broad phase with boxes of x and x+p inflated by xi/2, class of each
-    pair at x (offset xi for U, 0 for F and C), additive CCD per pair."""
+    pair at x (offset xi for U, 0 for F and C; culled pairs of mode "kaldor"
+    do not constrain the step), additive CCD per pair."""
     xi, dhat = float(scene.thickness), float(scene.dhat)
     off_u = 0.0 if mode == "single" else xi
     keys = broad_phase(topo, x, 0.5 * xi, p=p)
     m = keys.size
-    klass_in = np.zeros(m, np.uint8) if mode == "off" else np.isin(keys, F_rest).astype(np.uint8)
+    klass_in = np.zeros(m, np.uint8) if mode in ("off", "kaldor") else np.isin(keys, F_rest).astype(np.uint8)
+    if mode == "kaldor":
+        klass_in[kaldor_culled(topo, keys, cull_radius)] = KLASS_X
     P = _Params(xi, dhat, float(scene.kappa), dbar_min if np.isfinite(dbar_min) else 0.0,
                 int(mode == "single"), int(core_temp), 1)
     tc = topo.ctype()

@@ -645,7 +645,9 @@ int64_t orc_narrow(const orc_topo* tp, const double* x, const orc_params* P, int
         double xi_p, dh_p;
         pair_params(P, k, &xi_p, &dh_p);
         double y = d - xi_p;
-        int act = (y < dh_p);
+        /* class 3: culled (Kaldor et al.'s index-radius culling, the paper's
+         * comparison): no barrier */
+        int act = (k != 3) && (y < dh_p);
         if (act && y <= 0.0) pen = 1;
         d_out[c] = d;
         type_out[c] = (int8_t)type;
@@ -753,6 +755,12 @@ void orc_ccd_pairs(const orc_topo* tp, const double* x, const double* p, int64_t
         double x12[12], p12[12];
         gather12(x, tp->n, v, x12);
         gather12(p, tp->n, v, p12);
+        if (klass[q] == 3) {  /* culled: no constraint on the step */
+            t_out[q] = t_c;
+            iters[q] = 0;
+            status[q] = 0;
+            continue;
+        }
         double off = klass[q] == 0 ? xi : 0.0;
         iters[q] = orc_accd(ee, x12, p12, off, s, c_inner, t_c, max_iter, &t_out[q], &st);
         status[q] = st;

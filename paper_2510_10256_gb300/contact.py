@@ -19,11 +19,11 @@ _lib = None
 CB_OK, CB_ERR_ARG, CB_ERR_OOM, CB_ERR_CAPACITY, CB_ERR_PENETRATION, CB_ERR_DEGENERATE, \
     CB_ERR_ITER_LIMIT, CB_ERR_CUDA, CB_ERR_TOO_LARGE = range(9)
 CB_ROD, CB_SHELL = 0, 1
-CB_FILTER_DOUBLE, CB_FILTER_SINGLE, CB_FILTER_OFF = 0, 1, 2
+CB_FILTER_DOUBLE, CB_FILTER_SINGLE, CB_FILTER_OFF, CB_FILTER_KALDOR = 0, 1, 2, 3
 CB_THICK_PAPER_LITERAL = 4
 CB_NO_CORE_TEMP = 8
 PAIRS = {"candidate": 0, "filtered": 1, "core": 2, "active": 3, "ccd": 4, "rest_filtered": 5}
-MODES = {"double": CB_FILTER_DOUBLE, "single": CB_FILTER_SINGLE, "off": CB_FILTER_OFF}
+MODES = {"double": CB_FILTER_DOUBLE, "single": CB_FILTER_SINGLE, "off": CB_FILTER_OFF, "kaldor": CB_FILTER_KALDOR}
 
 # names declared in include/contact.h (the tests check the library exports each)
 ABI_FUNCTIONS = ["cb_scene_create", "cb_scene_destroy", "contact_build", "contact_filter", "barrier_eval",
@@ -44,7 +44,7 @@ class SceneDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_verts", C.c_int32), ("rest_xyz", C.c_void_p),
                 ("n_rods", C.c_int32), ("rod_ptr", C.c_void_p), ("n_tris", C.c_int32),
                 ("tris", C.c_void_p), ("thickness", C.c_double), ("dhat", C.c_double),
-                ("kappa", C.c_double), ("mode", C.c_int32)]
+                ("kappa", C.c_double), ("mode", C.c_int32), ("cull_radius", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -180,7 +180,7 @@ class ContactScene:
 
     def __init__(self, kind: str, rest, thickness: float, dhat: float, rod_ptr=None, tris=None,
                  kappa: float = 1.0, mode: str = "double", paper_literal: bool = False,
-                 core_temp: bool = True, stream=None):
+                 core_temp: bool = True, cull_radius: int = 0, stream=None):
         L = lib()
         rest = np.ascontiguousarray(np.asarray(rest, np.float64).reshape(3, -1))
         self.n = rest.shape[1]
@@ -204,6 +204,7 @@ class ContactScene:
         d.kappa = float(kappa)
         d.mode = MODES[mode] | (CB_THICK_PAPER_LITERAL if paper_literal else 0) | \
             (0 if core_temp else CB_NO_CORE_TEMP)
+        d.cull_radius = int(cull_radius)
         h = C.c_void_p()
         _check(L.cb_scene_create(C.byref(d), _stream_ptr(stream), C.byref(h)), "cb_scene_create")
         self.h = h

@@ -176,7 +176,8 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
   if (!(d->dhat > 0.0) || !(d->thickness >= 0.0) || !std::isfinite(d->thickness) || !std::isfinite(d->dhat))
     return CB_ERR_ARG;
   const int fm = d->mode & CB_FILTER_MASK;
-  if (fm == 3 || (d->mode & ~(CB_FILTER_MASK | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP))) return CB_ERR_ARG;
+  if (d->mode & ~(CB_FILTER_MASK | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP)) return CB_ERR_ARG;
+  if (fm == CB_FILTER_KALDOR && (d->kind != CB_ROD || d->cull_radius < 1)) return CB_ERR_ARG;
   const int n = d->n_verts;
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<int32_t> e0, e1, comp(n);
@@ -267,7 +268,8 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
   cudaGetDevice(&s->device);
   s->count = 1;
   s->hmp.assign(1, MemberParams{s->xi, s->dhat, s->a, s->kappa, 0.0, fm == CB_FILTER_SINGLE ? 1 : 0, s->core_temp,
-                                fm == CB_FILTER_OFF ? 1 : 0, s->n_prims});
+                                (fm == CB_FILTER_OFF || fm == CB_FILTER_KALDOR) ? 1 : 0, s->n_prims});
+  s->hmp[0].cull_radius = fm == CB_FILTER_KALDOR ? d->cull_radius : 0;
   s->voff = {0, (int64_t)n};
   s->eoff = {0, (int64_t)E};
   s->toff = {0, (int64_t)T};
@@ -359,7 +361,8 @@ cb_status cb_batch_create(cb_scene* const* members, int32_t count, void* stream,
   b->dhat = m0.dhat;
   b->a = m0.a;
   b->kappa = m0.kappa;
-  b->filter = m0.filter_off ? CB_FILTER_OFF : (m0.single ? CB_FILTER_SINGLE : CB_FILTER_DOUBLE);
+  b->filter = m0.cull_radius > 0 ? CB_FILTER_KALDOR
+                                 : (m0.filter_off ? CB_FILTER_OFF : (m0.single ? CB_FILTER_SINGLE : CB_FILTER_DOUBLE));
   b->core_temp = m0.core_temp;
   b->dbar_min = INFINITY;
   for (int m = 0; m < count; ++m)

@@ -218,37 +218,48 @@ __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restric
     const MemberParams& M = A.mp[mem];
     const bool filt = is_filtered(A, M, key, ki, kj);
     need = true;
-    const double Xd = A.cx[4 * mem + 3];
-    const float lb = cbb::lower_bound(ee, ldf(A.xf, A.n, v[0]), ldf(A.xf, A.n, v[1]), ldf(A.xf, A.n, v[2]),
-                                      ldf(A.xf, A.n, v[3]), (float)Xd);
-    if (filt || lb >= M.thrC32) {  // surely not class C at or above thrC32
-      const int cls = filt ? 1 : 0;
-      const float off = (cls == 0 && !M.single) ? M.xi32 : 0.f;
-      const cbb::f3 p0 = ldf(A.pf, A.n, v[0]), p1 = ldf(A.pf, A.n, v[1]), p2 = ldf(A.pf, A.n, v[2]),
-                    p3 = ldf(A.pf, A.n, v[3]);
-      const cbb::f3 pm = cbb::fscale3(cbb::fadd3(cbb::fadd3(p0, p1), cbb::fadd3(p2, p3)), 0.25f);
-      const float n0 = sqrtf(cbb::fdot3(cbb::fsub3(p0, pm), cbb::fsub3(p0, pm)));
-      const float n1 = sqrtf(cbb::fdot3(cbb::fsub3(p1, pm), cbb::fsub3(p1, pm)));
-      const float n2 = sqrtf(cbb::fdot3(cbb::fsub3(p2, pm), cbb::fsub3(p2, pm)));
-      const float n3 = sqrtf(cbb::fdot3(cbb::fsub3(p3, pm), cbb::fsub3(p3, pm)));
-      const float lp32 = ee ? fmaxf(n0, n1) + fmaxf(n2, n3) : n0 + fmaxf(fmaxf(n1, n2), n3);
-      const float Pm = fmaxf(fmaxf(cbb::fmaxabs3(p0), cbb::fmaxabs3(p1)), fmaxf(cbb::fmaxabs3(p2), cbb::fmaxabs3(p3)));
-      const float u64 = 3.8146973e-6f;  // 64 u, u = 2^-24: exact
-      const float lp_ub = __fadd_ru(__fmul_ru(lp32, 1.f + u64), __fmul_ru(u64, Pm));
-      const float slack = __fmul_ru(1e-12f, __fadd_ru(1.f, __double2float_ru(Xd)));
-      const float g_lb = __fsub_rd(__fsub_rd(lb, off), slack);
-      if (lp32 > 1e-30f && g_lb > 0.f) {
-        // (1 - s) g / l_p; 0.9f rounds below 0.9 = 1 - s
-        const float tl_lb = __fmul_rd(__fdiv_rd(__fmul_rd(0.9f, g_lb), lp_ub), 0.99999988f);
-        const bool exact = tl_lb > 1.f;
-        const double t = exact ? 1.0 : (double)tl_lb;
-        A.t_out[q] = t;
-        if (!exact) lb_out[q] = t;
-        A.cls_out[q] = (uint8_t)cls | (exact ? EXACT : 0);
-        if (exact) m_exact = t;
-        else m_lb = t;
-        unres = !exact;
-        need = false;
+    // Kaldor culling (rods: edges numbered along each polyline): the pair
+    // does not constrain the step
+    const bool culled = M.cull_radius > 0 && A.comp[A.ev0[ki]] == A.comp[A.ev0[kj]] &&
+                        (int)(kj - ki) <= M.cull_radius;
+    if (culled) {
+      A.t_out[q] = 1.0;
+      A.cls_out[q] = (uint8_t)3 | EXACT;
+      m_exact = 1.0;
+      need = false;
+    } else {
+      const double Xd = A.cx[4 * mem + 3];
+      const float lb = cbb::lower_bound(ee, ldf(A.xf, A.n, v[0]), ldf(A.xf, A.n, v[1]), ldf(A.xf, A.n, v[2]),
+                                        ldf(A.xf, A.n, v[3]), (float)Xd);
+      if (filt || lb >= M.thrC32) {  // surely not class C at or above thrC32
+        const int cls = filt ? 1 : 0;
+        const float off = (cls == 0 && !M.single) ? M.xi32 : 0.f;
+        const cbb::f3 p0 = ldf(A.pf, A.n, v[0]), p1 = ldf(A.pf, A.n, v[1]), p2 = ldf(A.pf, A.n, v[2]),
+                      p3 = ldf(A.pf, A.n, v[3]);
+        const cbb::f3 pm = cbb::fscale3(cbb::fadd3(cbb::fadd3(p0, p1), cbb::fadd3(p2, p3)), 0.25f);
+        const float n0 = sqrtf(cbb::fdot3(cbb::fsub3(p0, pm), cbb::fsub3(p0, pm)));
+        const float n1 = sqrtf(cbb::fdot3(cbb::fsub3(p1, pm), cbb::fsub3(p1, pm)));
+        const float n2 = sqrtf(cbb::fdot3(cbb::fsub3(p2, pm), cbb::fsub3(p2, pm)));
+        const float n3 = sqrtf(cbb::fdot3(cbb::fsub3(p3, pm), cbb::fsub3(p3, pm)));
+        const float lp32 = ee ? fmaxf(n0, n1) + fmaxf(n2, n3) : n0 + fmaxf(fmaxf(n1, n2), n3);
+        const float Pm = fmaxf(fmaxf(cbb::fmaxabs3(p0), cbb::fmaxabs3(p1)), fmaxf(cbb::fmaxabs3(p2), cbb::fmaxabs3(p3)));
+        const float u64 = 3.8146973e-6f;  // 64 u, u = 2^-24: exact
+        const float lp_ub = __fadd_ru(__fmul_ru(lp32, 1.f + u64), __fmul_ru(u64, Pm));
+        const float slack = __fmul_ru(1e-12f, __fadd_ru(1.f, __double2float_ru(Xd)));
+        const float g_lb = __fsub_rd(__fsub_rd(lb, off), slack);
+        if (lp32 > 1e-30f && g_lb > 0.f) {
+          // (1 - s) g / l_p; 0.9f rounds below 0.9 = 1 - s
+          const float tl_lb = __fmul_rd(__fdiv_rd(__fmul_rd(0.9f, g_lb), lp_ub), 0.99999988f);
+          const bool exact = tl_lb > 1.f;
+          const double t = exact ? 1.0 : (double)tl_lb;
+          A.t_out[q] = t;
+          if (!exact) lb_out[q] = t;
+          A.cls_out[q] = (uint8_t)cls | (exact ? EXACT : 0);
+          if (exact) m_exact = t;
+          else m_lb = t;
+          unres = !exact;
+          need = false;
+        }
       }
     }
   }

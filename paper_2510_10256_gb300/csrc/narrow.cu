@@ -131,8 +131,11 @@ __global__ void k_filter_rod(int64_t nc, const uint64_t* __restrict__ cand, cons
     const uint64_t key = cand[c];
     const int k = (int)cb_key_i(key), l = (int)cb_key_j(key);
     const int v0 = ev0[k];
-    f = (!mp[vsc[v0]].filter_off && comp[v0] == comp[ev0[l]] && l <= win[k]) ? 1u : 0u;
-    klass[c] = (uint8_t)f;
+    const MemberParams& M = mp[vsc[v0]];
+    const bool same = comp[v0] == comp[ev0[l]];
+    f = (!M.filter_off && same && l <= win[k]) ? 1u : 0u;
+    // Kaldor culling: edges are numbered along each polyline, so l - k is the gap
+    klass[c] = (M.cull_radius > 0 && same && l - k <= M.cull_radius) ? (uint8_t)3 : (uint8_t)f;
   }
   uint32_t b = __ballot_sync(0xffffffffu, f);
   if ((threadIdx.x & 31) == 0 && b) atomicAdd(nfilt, (unsigned long long)__popc(b));
@@ -265,23 +268,31 @@ __global__ void k_distance_screen(int64_t nc, const uint64_t* __restrict__ cand,
     const int k = klass_in[c];
     const int mem = vsc[s.v[0]];
     const MemberParams& M = mp[mem];
-    // thresholds beyond which a pair is surely inactive and not class C (the
-    // 1e-9 margins cover the rounding of the FP64 decision; FP32 copies
-    // rounded up, so the FP32 comparison is as safe)
-    const float thr = k == 1 ? M.thrF32 : M.thrU32;
-    const float X = (float)cx[4 * mem + 3];
-    const float lb = cbb::lower_bound(
-        s.ee, cbb::f3{xf[s.v[0]], xf[(size_t)n + s.v[0]], xf[2 * (size_t)n + s.v[0]]},
-        cbb::f3{xf[s.v[1]], xf[(size_t)n + s.v[1]], xf[2 * (size_t)n + s.v[1]]},
-        cbb::f3{xf[s.v[2]], xf[(size_t)n + s.v[2]], xf[2 * (size_t)n + s.v[2]]},
-        cbb::f3{xf[s.v[3]], xf[(size_t)n + s.v[3]], xf[2 * (size_t)n + s.v[3]]}, X);
-    if (lb >= thr) {
+    if (k == 3) {  // culled (Kaldor mode): no barrier, no distance needed
       dout[c] = __longlong_as_double(0x7ff0000000000000LL);
       tout[c] = -1;
-      cls[c] = (uint8_t)k;
+      cls[c] = 3;
       flag[c] = 0;
+      ee = false;
     } else {
-      exact = true;
+      // thresholds beyond which a pair is surely inactive and not class C (the
+      // 1e-9 margins cover the rounding of the FP64 decision; FP32 copies
+      // rounded up, so the FP32 comparison is as safe)
+      const float thr = k == 1 ? M.thrF32 : M.thrU32;
+      const float X = (float)cx[4 * mem + 3];
+      const float lb = cbb::lower_bound(
+          s.ee, cbb::f3{xf[s.v[0]], xf[(size_t)n + s.v[0]], xf[2 * (size_t)n + s.v[0]]},
+          cbb::f3{xf[s.v[1]], xf[(size_t)n + s.v[1]], xf[2 * (size_t)n + s.v[1]]},
+          cbb::f3{xf[s.v[2]], xf[(size_t)n + s.v[2]], xf[2 * (size_t)n + s.v[2]]},
+          cbb::f3{xf[s.v[3]], xf[(size_t)n + s.v[3]], xf[2 * (size_t)n + s.v[3]]}, X);
+      if (lb >= thr) {
+        dout[c] = __longlong_as_double(0x7ff0000000000000LL);
+        tout[c] = -1;
+        cls[c] = (uint8_t)k;
+        flag[c] = 0;
+      } else {
+        exact = true;
+      }
     }
   }
   warp_append(exact && !ee, (uint32_t)c, list, &nlist[0]);

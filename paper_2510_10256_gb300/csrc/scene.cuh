@@ -27,6 +27,7 @@ struct MemberParams {
   // at upload): a (1 + 1e-9) + 1e-9, dbar_min (1 + 1e-9) + 1e-9,
   // xi (1 + 1e-9) + 1e-9, xi
   float thrU32, thrF32, thrC32, xi32;
+  int32_t cull_radius;    // CB_FILTER_KALDOR: rod edge pairs of one polyline this close are culled; else 0
 };
 
 // Spatial-hash grid of one member.
