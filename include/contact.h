@@ -70,6 +70,9 @@ typedef enum {
 #define CB_FILTER_MASK 3
 #define CB_THICK_PAPER_LITERAL 4    /* activation a = thickness, offset = thickness - dhat */
 #define CB_NO_CORE_TEMP 8           /* disable the temporary zero offset of Sec. 3.4 */
+#define CB_DBAR_PER_COMPONENT 16    /* a filtered pair's width is the dbar_min of its own component (the
+                                       smallest reference distance of that component's filtered pairs)
+                                       instead of the scene's */
 
 /* pair lists for cb_get_pairs */
 #define CB_PAIRS_CANDIDATE 0        /* C: broad-phase candidates */
@@ -94,7 +97,7 @@ typedef struct {
   double thickness;           /* offset xi (eta in the paper); rods: 2 x radius */
   double dhat;                /* barrier width; full activation a = thickness + dhat */
   double kappa;               /* barrier stiffness (energy scale); 1 if <= 0 */
-  int32_t mode;               /* CB_FILTER_* | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP */
+  int32_t mode;               /* CB_FILTER_* | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP | CB_DBAR_PER_COMPONENT */
   int32_t cull_radius;        /* CB_FILTER_KALDOR: culling radius in edges (>= 1); else ignored */
 } cb_scene_desc;
 

@@ -63,7 +63,7 @@ class _Topo(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("xi", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double),
                 ("dbar_min", C.c_double), ("single", C.c_int), ("core_temp", C.c_int),
-                ("project", C.c_int)]
+                ("project", C.c_int), ("dbar_comp", C.c_void_p)]
 
 
 def lib():
@@ -275,6 +275,16 @@ def rest_filter(scene, topo: Topology, a: float) -> tuple[np.ndarray, np.ndarray
 MODES = ("double", "single", "off", "kaldor")
 
 
+def dbar_min_per_component(topo: Topology, F_rest: np.ndarray, dbar: np.ndarray) -> np.ndarray:
+    """Smallest reference distance of the filtered stencil pairs of each
+    component, indexed by component label (+inf where none is filtered)."""
+    out = np.full(topo.n, np.inf)
+    if F_rest.size:
+        lab = topo.comp[stencils(topo, F_rest)[:, 0]]
+        np.minimum.at(out, lab, dbar)
+    return out
+
+
 def kaldor_culled(topo: Topology, keys: np.ndarray, radius: int) -> np.ndarray:
     """Kaldor et al.'s culling, the comparison the paper runs against its
     filter (the knot test, Fig. 8): rod edge pairs of one polyline at most
@@ -313,6 +323,7 @@ class PassResult:
     ccd_iters: np.ndarray | None = None
     ccd_status: np.ndarray | None = None
     alpha: float | None = None
+    fwidth: np.ndarray | None = None  # per candidate: the class-F width (per_component passes)
     timings: dict = field(default_factory=dict)
 
     @property
@@ -325,10 +336,14 @@ class PassResult:
 
 def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: bool = True,
                  ccd: bool = True, x: np.ndarray | None = None, p: np.ndarray | None = None,
-                 topo: Topology | None = None, filt=None, cull_radius: int = 0) -> PassResult:
+                 topo: Topology | None = None, filt=None, cull_radius: int = 0,
+                 per_component: bool = False) -> PassResult:
     """One full pass (stages a-e) at x with CCD direction p.  Mode "kaldor":
     no filter, and rod edge pairs of one polyline at most cull_radius edges
-    apart are culled (class X: no barrier, no constraint on the step)."""
+    apart are culled (class X: no barrier, no constraint on the step).
+    per_component: a filtered pair's width is the smallest reference distance
+    of the filtered pairs of its own component instead of the scene's
+    (dbar_min per component)."""
     if mode == "kaldor" and (scene.kind != "rod" or cull_radius < 1):
         raise ValueError("kaldor mode: rods and cull_radius >= 1")
     import time
@@ -361,8 +376,11 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     tm["filter"] = time.perf_counter() - t1
     # (c) distances, class C, activity
     t1 = time.perf_counter()
+    # per-component dbar_min by component label (the label of a pair's first vertex)
+    dbar_comp = dbar_min_per_component(topo, F_rest, dbar) if per_component else None
     P = _Params(xi, dhat, float(scene.kappa), dbar_min if np.isfinite(dbar_min) else 0.0,
-                int(mode == "single"), int(core_temp), int(project))
+                int(mode == "single"), int(core_temp), int(project),
+                dbar_comp.ctypes.data if dbar_comp is not None else None)
     tc = topo.ctype()
     m = Cset.size
     d = np.zeros(m)
@@ -399,8 +417,9 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     # conditioning of b', b'' in d near the activation (relative errors grow like
     # kappa = y / (dhat_p - y)); the floor grows with it
     ad_xi = np.where(akl == KLASS_U, 0.0 if mode == "single" else xi, 0.0)
-    ad_dh = np.where(akl == KLASS_F, dbar_min if np.isfinite(dbar_min) else 0.0,
-                     np.where((akl == KLASS_C) | (mode == "single"), a, dhat))
+    fw = (dbar_comp[topo.comp[st[:, 0]]] if dbar_comp is not None
+          else np.full(na, dbar_min if np.isfinite(dbar_min) else 0.0))
+    ad_dh = np.where(akl == KLASS_F, fw, np.where((akl == KLASS_C) | (mode == "single"), a, dhat))
     ay = ad - ad_xi
     kappa_p = np.maximum(1.0, ay / np.maximum(ad_dh - ay, 1e-300)) if na else np.zeros(0)
     ffac = np.maximum(1e-4, 1e-7 * kappa_p)
@@ -429,6 +448,8 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     tm["barrier"] = time.perf_counter() - t1
     res = PassResult(Cset, kl, d, dty, active, F_rest, dbar, dbar_min, energy, e, grad, grad_abs,
                      row_ptr, bcol, val, vab, bool(pen.value))
+    if dbar_comp is not None:
+        res.fwidth = dbar_comp[topo.comp[stencils(topo, Cset)[:, 0]]] if m else np.zeros(0)
     # (e) CCD step bound
     if ccd:
         t1 = time.perf_counter()

@@ -617,11 +617,13 @@ typedef struct {
     int single;      /* 1: Eq. 1 (single-phase) */
     int core_temp;   /* 1: class C on */
     int project;     /* 1: PSD-project the Hessian (0 only for derivative checks) */
+    const double* dbar_comp;  /* per-component dbar_min by component label, or NULL (one scalar) */
 } orc_params;
 
-static void pair_params(const orc_params* P, int klass, double* xi_p, double* dh_p) {
+/* comp: the component label of the pair's first vertex */
+static void pair_params(const orc_params* P, int klass, int comp, double* xi_p, double* dh_p) {
     double a = P->xi + P->dhat;
-    if (klass == 1) { *xi_p = 0.0; *dh_p = P->dbar_min; return; }
+    if (klass == 1) { *xi_p = 0.0; *dh_p = P->dbar_comp ? P->dbar_comp[comp] : P->dbar_min; return; }
     if (klass == 2) { *xi_p = 0.0; *dh_p = a; return; }
     if (P->single) { *xi_p = 0.0; *dh_p = a; return; }
     *xi_p = P->xi; *dh_p = P->dhat;
@@ -643,7 +645,7 @@ int64_t orc_narrow(const orc_topo* tp, const double* x, const orc_params* P, int
         int k = klass_in[c];
         if (k == 0 && P->core_temp && !P->single && d <= P->xi) k = 2;
         double xi_p, dh_p;
-        pair_params(P, k, &xi_p, &dh_p);
+        pair_params(P, k, tp->comp[v[0]], &xi_p, &dh_p);
         double y = d - xi_p;
         /* class 3: culled (Kaldor et al.'s index-radius culling, the paper's
          * comparison): no barrier */
@@ -671,7 +673,7 @@ void orc_barrier_pairs(const orc_topo* tp, const double* x, const orc_params* P,
         double x12[12], gd[12], Hd[144], H[144];
         gather12(x, tp->n, v, x12);
         double xi_p, dh_p, b, b1, b2;
-        pair_params(P, klass[a], &xi_p, &dh_p);
+        pair_params(P, klass[a], tp->comp[v[0]], &xi_p, &dh_p);
         double y = d[a] - xi_p;
         if (y <= 0.0) {
             energy[a] = INFINITY;

@@ -58,7 +58,7 @@ static cb_status upload(DevBuf& b, const T* h, size_t count, cudaStream_t st) {
 static void scene_release(cb_scene* s) {
   cudaStream_t st = s->last_stream;
   DevBuf* bufs[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->frest,
-                    &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
+                    &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
                     &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col, &s->bsr_val,
                     &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->mp, &s->vsc, &s->macc, &s->hstage, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag, &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist,
                     &s->dev_scalars};
@@ -132,7 +132,7 @@ static float float_up(double v) {
 static cb_status upload_members(cb_scene* s, cudaStream_t st) {
   for (MemberParams& m : s->hmp) {
     m.thrU32 = float_up(m.a * (1.0 + 1e-9) + 1e-9);
-    m.thrF32 = float_up(m.dbar_min * (1.0 + 1e-9) + 1e-9);
+    m.thrF32 = float_up(std::max(m.dbar_min, m.dbar_fmax) * (1.0 + 1e-9) + 1e-9);
     m.thrC32 = float_up(m.xi * (1.0 + 1e-9) + 1e-9);
     m.xi32 = float_up(m.xi);
   }
@@ -176,7 +176,8 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
   if (!(d->dhat > 0.0) || !(d->thickness >= 0.0) || !std::isfinite(d->thickness) || !std::isfinite(d->dhat))
     return CB_ERR_ARG;
   const int fm = d->mode & CB_FILTER_MASK;
-  if (d->mode & ~(CB_FILTER_MASK | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP)) return CB_ERR_ARG;
+  if (d->mode & ~(CB_FILTER_MASK | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP | CB_DBAR_PER_COMPONENT))
+    return CB_ERR_ARG;
   if (fm == CB_FILTER_KALDOR && (d->kind != CB_ROD || d->cull_radius < 1)) return CB_ERR_ARG;
   const int n = d->n_verts;
   cudaStream_t st = (cudaStream_t)stream;
@@ -270,6 +271,7 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
   s->hmp.assign(1, MemberParams{s->xi, s->dhat, s->a, s->kappa, 0.0, fm == CB_FILTER_SINGLE ? 1 : 0, s->core_temp,
                                 (fm == CB_FILTER_OFF || fm == CB_FILTER_KALDOR) ? 1 : 0, s->n_prims});
   s->hmp[0].cull_radius = fm == CB_FILTER_KALDOR ? d->cull_radius : 0;
+  s->hmp[0].per_comp = (d->mode & CB_DBAR_PER_COMPONENT) ? 1 : 0;
   s->voff = {0, (int64_t)n};
   s->eoff = {0, (int64_t)E};
   s->toff = {0, (int64_t)T};
@@ -296,6 +298,7 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
     if (cudaEventCreate(&e) != cudaSuccess) return fail(CB_ERR_CUDA);
   if ((rc = filter_precompute(s, st)) != CB_OK) return fail(rc);
   s->hmp[0].dbar_min = std::isfinite(s->dbar_min) ? s->dbar_min : 0.0;
+  s->hmp[0].dbar_fmax = s->hmp[0].per_comp && std::isfinite(s->dbar_fmax) ? s->dbar_fmax : s->hmp[0].dbar_min;
   if ((rc = upload_members(s, st)) != CB_OK) return fail(rc);
   if (s->kind == CB_SHELL && s->n_frest > 0) {
     k_lower_bound<<<1, 1, 0, cb_count(st)>>>(bp<uint64_t>(s->frest), s->n_frest, (uint64_t)CB_KEY_EE << 62,
@@ -419,6 +422,18 @@ cb_status cb_batch_create(cb_scene* const* members, int32_t count, void* stream,
   if (cudaGetLastError() != cudaSuccess) return fail(CB_ERR_CUDA);
   b->n_frest = b->kind == CB_SHELL ? nf : 0;
   b->n_frest_pt = nf_pt;
+  // per-component dbar_min of the members, at the batch's component labels
+  // (rods: polyline index + the member's first polyline; shells: vertex id + vertex offset)
+  if ((rc = buf_ensure(b->dbar_comp, sizeof(unsigned long long) * (size_t)std::max(1, b->n), st)) != CB_OK)
+    return fail(rc);
+  for (int m = 0; m < count; ++m) {
+    const cb_scene* s = members[m];
+    const size_t cnt = b->kind == CB_ROD ? (size_t)s->n_rods : (size_t)s->n;
+    const size_t lbl = b->kind == CB_ROD ? (size_t)roff[m] : (size_t)b->voff[m];
+    if (cnt && cudaMemcpyAsync(bp<unsigned long long>(b->dbar_comp) + lbl, s->dbar_comp.p,
+                               sizeof(unsigned long long) * cnt, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return fail(CB_ERR_CUDA);
+  }
   if ((rc = frest_rows_build(b, st)) != CB_OK) return fail(rc);
   for (auto& e : b->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(CB_ERR_CUDA);
@@ -725,7 +740,7 @@ cb_status cb_get_stats(cb_scene* s, cb_stats* o) {
   o->n_hess_pe = s->n_hq[2];
   size_t bytes = 0;
   const DevBuf* all[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->frest,
-                         &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls,
+                         &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls,
                          &s->aidx, &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col,
                          &s->bsr_val, &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag,
                          &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist};

@@ -65,7 +65,7 @@ __global__ void k_arclength(int n_rods, const int32_t* __restrict__ rod_ptr, con
 __global__ void k_rod_window(int E, const int32_t* __restrict__ ev0, const int32_t* __restrict__ ev1,
                              const int32_t* __restrict__ comp, const double* __restrict__ S, double a,
                              int32_t* __restrict__ win, unsigned long long* __restrict__ dmin_bits,
-                             unsigned long long* __restrict__ nfilt) {
+                             unsigned long long* __restrict__ nfilt, unsigned long long* __restrict__ dmin_comp) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= E) return;
   const int k1 = ev1[k];
@@ -85,6 +85,7 @@ __global__ void k_rod_window(int E, const int32_t* __restrict__ ev0, const int32
   win[k] = last;
   if (cnt) {
     atomicMin(dmin_bits, (unsigned long long)__double_as_longlong(mn));
+    atomicMin(&dmin_comp[comp[k1]], (unsigned long long)__double_as_longlong(mn));
     atomicAdd(nfilt, cnt);
   }
 }
@@ -94,7 +95,8 @@ __global__ void k_rest_filter(int64_t nc, const uint64_t* __restrict__ keys, con
                               const int32_t* __restrict__ ev1, const int32_t* __restrict__ tv, int T,
                               const int32_t* __restrict__ comp, const double* __restrict__ rest, int n, double a,
                               uint32_t* __restrict__ flag, double* __restrict__ dbar,
-                              unsigned long long* __restrict__ dmin_bits) {
+                              unsigned long long* __restrict__ dmin_bits,
+                              unsigned long long* __restrict__ dmin_comp) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long mb = 0x7ff0000000000000ull;  // +inf: no filtered pair in this lane
   if (c < nc) {
@@ -107,6 +109,7 @@ __global__ void k_rest_filter(int64_t nc, const uint64_t* __restrict__ keys, con
       if (d < a) {
         f = 1;
         mb = (unsigned long long)__double_as_longlong(d);
+        atomicMin(&dmin_comp[comp[s.v[0]]], mb);
       }
     }
     flag[c] = f;
@@ -162,7 +165,7 @@ __global__ void k_filter_shell(int64_t nc, const uint64_t* __restrict__ cand, co
 
 struct PassParams {
   double xi, dhat, a, dbar_min, kappa;
-  int single, core_temp;
+  int single, core_temp, per_comp;
 };
 
 __device__ __forceinline__ PassParams member_pass(const MemberParams& m) {
@@ -174,14 +177,23 @@ __device__ __forceinline__ PassParams member_pass(const MemberParams& m) {
   P.kappa = m.kappa;
   P.single = m.single;
   P.core_temp = m.core_temp;
+  P.per_comp = m.per_comp;
   return P;
 }
 
 // pair parameters: offset xi_p and width dhat_p of a class (0 U, 1 F, 2 C)
-__device__ __forceinline__ void pair_params(const PassParams& P, int k, double& xi_p, double& dh_p) {
+// class-F width of a pair whose first vertex is v0: the scene's dbar_min, or
+// its component's (CB_DBAR_PER_COMPONENT)
+__device__ __forceinline__ double f_width(const PassParams& P, const unsigned long long* __restrict__ dbar_comp,
+                                          const int32_t* __restrict__ comp, int v0) {
+  return P.per_comp ? __longlong_as_double((long long)dbar_comp[comp[v0]]) : P.dbar_min;
+}
+
+// offset and width of a pair of class k (U 0, F 1, C 2); fw: its class-F width
+__device__ __forceinline__ void pair_params(const PassParams& P, int k, double fw, double& xi_p, double& dh_p) {
   if (k == 1) {
     xi_p = 0.0;
-    dh_p = P.dbar_min;
+    dh_p = fw;
   } else if (k == 2 || P.single) {
     xi_p = 0.0;
     dh_p = P.a;
@@ -311,7 +323,8 @@ __global__ void k_distance_exact(const uint32_t* __restrict__ list, int64_t cap,
                                  double* __restrict__ dout, int8_t* __restrict__ tout,
                                  uint8_t* __restrict__ cls, uint32_t* __restrict__ flag,
                                  unsigned long long* __restrict__ status, unsigned long long* __restrict__ ncore,
-                                 unsigned long long* __restrict__ macc, bool energy) {
+                                 unsigned long long* __restrict__ macc, const int32_t* __restrict__ comp,
+                                 const unsigned long long* __restrict__ dbar_comp, bool energy) {
   const unsigned m0 = nlist[0], m = m0 + nlist[1];
   for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w - threadIdx.x < m; w += gridDim.x * blockDim.x) {
     uint32_t is_core = 0;
@@ -328,7 +341,7 @@ __global__ void k_distance_exact(const uint32_t* __restrict__ list, int64_t cap,
                                            load3(x, n, s.v[3]), d);
       if (k == 0 && P.core_temp && !P.single && d <= P.xi) k = 2;
       double xi_p, dh_p;
-      pair_params(P, k, xi_p, dh_p);
+      pair_params(P, k, f_width(P, dbar_comp, comp, s.v[0]), xi_p, dh_p);
       const double y = xsub(d, xi_p);
       const uint32_t act = (y < dh_p) ? 1u : 0u;
       if (act && y <= 0.0) {
@@ -676,6 +689,8 @@ struct HessArgs {
   const int32_t* __restrict__ vsc;
   const MemberParams* __restrict__ mp;
   unsigned long long* __restrict__ macc;
+  const int32_t* __restrict__ comp;                 // component label per vertex
+  const unsigned long long* __restrict__ dbar_comp; // per-component dbar_min bits (CB_DBAR_PER_COMPONENT)
   const int32_t* __restrict__ row_ptr;
   const int32_t* __restrict__ col;
   double* __restrict__ val;
@@ -870,7 +885,7 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
     mem = A.vsc[s.v[0]];
     const PassParams P = member_pass(A.mp[mem]);
     double xi_p, dh_p;
-    pair_params(P, A.ccls[c], xi_p, dh_p);
+    pair_params(P, A.ccls[c], f_width(P, A.dbar_comp, A.comp, s.v[0]), xi_p, dh_p);
     const double y = d - xi_p;
     double b, b1, b2;
     barrier_b012(y, dh_p, b, b1, b2);
@@ -1774,12 +1789,22 @@ __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v;
 
 }  // namespace
 
+__global__ void k_fill_u64(int64_t n, unsigned long long* __restrict__ p, unsigned long long v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
 cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
   uint64_t* sc = scalars(s);
   unsigned long long* dmin = (unsigned long long*)(sc + SC_DBAR_MIN_BITS);
   unsigned long long* nf = (unsigned long long*)(sc + SC_NFILT);
   k_set_u64<<<1, 1, 0, cb_count(st)>>>(dmin, 0x7ff0000000000000ull);
   k_set_u64<<<1, 1, 0, cb_count(st)>>>(nf, 0ull);
+  // per-component minima, by component label (rods: polyline index; shells: a vertex id)
+  CB_TRY(buf_ensure(s->dbar_comp, sizeof(unsigned long long) * (size_t)std::max(1, s->n), st));
+  unsigned long long* dcomp = bp<unsigned long long>(s->dbar_comp);
+  k_fill_u64<<<cb_grid(std::max(1, s->n)), CB_THREADS, 0, cb_count(st)>>>(std::max(1, s->n), dcomp,
+                                                                          0x7ff0000000000000ull);
   if (s->kind == CB_ROD) {
     CB_TRY(buf_ensure(s->S, sizeof(double) * (size_t)s->n, st));
     CB_TRY(buf_ensure(s->win, sizeof(int32_t) * (size_t)std::max(1, s->E), st));
@@ -1788,7 +1813,7 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
     if (s->E > 0)
       k_rod_window<<<cb_grid(s->E), CB_THREADS, 0, cb_count(st)>>>(s->E, bp<int32_t>(s->ev0), bp<int32_t>(s->ev1),
                                                          bp<int32_t>(s->comp), bp<double>(s->S), s->a,
-                                                         bp<int32_t>(s->win), dmin, nf);
+                                                         bp<int32_t>(s->win), dmin, nf, dcomp);
     CB_CUDA(cudaGetLastError());
     uint64_t h[2];
     CB_TRY(read_scalars(s, SC_DBAR_MIN_BITS, 1, &h[0], st));
@@ -1809,7 +1834,7 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
       k_rest_filter<<<cb_grid(nr), CB_THREADS, 0, cb_count(st)>>>(nr, bp<uint64_t>(rc), bp<int32_t>(s->ev0),
                                                         bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T,
                                                         bp<int32_t>(s->comp), bp<double>(s->rest), s->n, s->a,
-                                                        bp<uint32_t>(flag), bp<double>(dbar), dmin);
+                                                        bp<uint32_t>(flag), bp<double>(dbar), dmin, dcomp);
       uint32_t* tot = (uint32_t*)(sc + SC_COUNT1);
       cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(flag), bp<uint32_t>(pos), nr, bp<uint32_t>(s->scan_tmp),
                                               tot, st);
@@ -1838,6 +1863,19 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
     buf_free(rc, st);
   }
   if (s->n_frest > 0 && !(s->dbar_min > 0.0)) return CB_ERR_DEGENERATE;
+  s->dbar_fmax = s->dbar_min;
+  if (s->hmp.size() == 1 && s->hmp[0].per_comp) {
+    std::vector<unsigned long long> h((size_t)std::max(1, s->n));
+    CB_CUDA(cudaMemcpyAsync(h.data(), dcomp, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost, st));
+    CB_CUDA(cudaStreamSynchronize(st));
+    double mx = -INFINITY;
+    for (unsigned long long b : h) {
+      double v;
+      memcpy(&v, &b, 8);
+      if (std::isfinite(v)) mx = std::max(mx, v);
+    }
+    if (std::isfinite(mx)) s->dbar_fmax = mx;
+  }
   return CB_OK;
 }
 
@@ -1938,7 +1976,7 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
         bp<uint32_t>(s->dlist), nc, nl, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass), bp<int32_t>(s->ev0),
         bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T, x, s->n, bp<int32_t>(s->vsc), bp<MemberParams>(s->mp),
         bp<double>(s->cd), bp<int8_t>(s->ctype), bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), status, ncore,
-        macc, energy_only);
+        macc, bp<int32_t>(s->comp), bp<unsigned long long>(s->dbar_comp), energy_only);
     if (energy_only) {
       if (energy) k_energy_final<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, energy);
       CB_CUDA(cudaGetLastError());
@@ -2013,6 +2051,8 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     A.vsc = bp<int32_t>(s->vsc);
     A.mp = bp<MemberParams>(s->mp);
     A.macc = macc;
+    A.comp = bp<int32_t>(s->comp);
+    A.dbar_comp = bp<unsigned long long>(s->dbar_comp);
     A.row_ptr = bp<int32_t>(s->bsr_row);
     A.col = bp<int32_t>(s->bsr_col);
     A.val = bp<double>(s->bsr_val);

@@ -28,6 +28,8 @@ struct MemberParams {
   // xi (1 + 1e-9) + 1e-9, xi
   float thrU32, thrF32, thrC32, xi32;
   int32_t cull_radius;    // CB_FILTER_KALDOR: rod edge pairs of one polyline this close are culled; else 0
+  int32_t per_comp;       // CB_DBAR_PER_COMPONENT: class-F width from dbar_comp by component label
+  double dbar_fmax;       // largest class-F width of the member (= dbar_min unless per_comp)
 };
 
 // Spatial-hash grid of one member.
@@ -95,6 +97,8 @@ struct cb_scene {
   DevBuf win;           // int32 [E] rods: last filtered partner edge
   DevBuf frest;         // uint64 shells: sorted rest-filtered keys
   DevBuf frest_dbar;    // double
+  DevBuf dbar_comp;     // uint64 bits of the per-component dbar_min, by component label (n entries)
+  double dbar_fmax = 0.0;  // largest per-component dbar_min (finite), or dbar_min
   int64_t n_frest = 0;
   DevBuf frow_pt;       // uint32 shells: row offsets of frest by vertex (point-triangle keys), n + 1
   DevBuf frow_ee;       // uint32 shells: row offsets of frest by edge (edge-edge keys), E + 1

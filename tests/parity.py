@@ -19,12 +19,13 @@ import numpy as np
 import oracle as O
 
 
-def run_gpu(sc, mode="double", core_temp=True, x=None, p=None, paper_literal=False, cull_radius=0):
+def run_gpu(sc, mode="double", core_temp=True, x=None, p=None, paper_literal=False, cull_radius=0,
+            per_component=False):
     import torch
     from paper_2510_10256_gb300.contact import ContactScene
     dev = torch.device("cuda:0")
     cs = ContactScene.from_scene(sc, mode=mode, core_temp=core_temp, paper_literal=paper_literal,
-                                 cull_radius=cull_radius)
+                                 cull_radius=cull_radius, per_component=per_component)
     xx = torch.from_numpy(np.ascontiguousarray(sc.x if x is None else x)).to(dev)
     pp = torch.from_numpy(np.ascontiguousarray(sc.p if p is None else p)).to(dev)
     energy = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -48,7 +49,8 @@ def threshold_band(sc, orc: O.PassResult, mode="double"):
     thr = []
     if mode != "single":
         thr.append(np.full_like(d, xi))
-    thr.append(np.where(orc.klass == O.KLASS_F, orc.dbar_min, np.where(
+    fw = orc.fwidth if orc.fwidth is not None else orc.dbar_min
+    thr.append(np.where(orc.klass == O.KLASS_F, fw, np.where(
         (orc.klass == O.KLASS_C) | (mode == "single"), a, xi + sc.dhat)))
     band = np.zeros(d.size, bool)
     for t in thr:

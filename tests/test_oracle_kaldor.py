@@ -71,3 +71,45 @@ def test_kaldor_is_the_negative_control_of_invariant_3():
     assert df[O.KLASS_U] > xi and df[O.KLASS_F] > 0 and df[O.KLASS_C] > 0
     # culled model: pairs the filtered model keeps unfiltered end inside the thickness
     assert dk[O.KLASS_U] <= xi or dk[O.KLASS_C] <= xi, dk
+
+
+def two_yarns(L1=0.04, L2=0.1, n1=30, n2=12, thickness=0.25, dhat=0.01):
+    """Two straight yarns 2 mm apart, of segment lengths L1 and L2."""
+    a_pts = np.stack([L1 * np.arange(n1 + 1), np.zeros(n1 + 1), np.zeros(n1 + 1)])
+    b_pts = np.stack([L2 * np.arange(n2 + 1), np.full(n2 + 1, 2.0), np.zeros(n2 + 1)])
+    x = np.concatenate([a_pts, b_pts], axis=1)
+    rp = np.array([0, n1 + 1, n1 + n2 + 2], np.int32)
+    return S.Scene("rod", x.copy(), x.copy(), np.zeros_like(x), thickness, dhat, rod_ptr=rp)
+
+
+def test_per_component_dbar_min():
+    """Two yarns of different segment lengths: with one scene-wide dbar_min
+    the coarse yarn's filtered pairs get the fine yarn's (smaller) width; per
+    component each keeps its own, the smallest reference distance of its own
+    filtered pairs -- the closed form of a straight rod, its segment length."""
+    L1, L2, n1, n2 = 0.04, 0.1, 30, 12
+    sc = two_yarns(L1, L2, n1, n2)
+    x = sc.x
+    glob = O.contact_pass(sc, ccd=False)
+    comp = O.contact_pass(sc, ccd=False, per_component=True)
+    assert np.isclose(glob.dbar_min, L1)
+    topo = O.topology(sc)
+    st = O.stencils(topo, comp.C)
+    Fm = comp.klass == O.KLASS_F
+    lab = topo.comp[st[:, 0]]
+    assert np.allclose(comp.fwidth[Fm & (lab == 0)], L1) and np.allclose(comp.fwidth[Fm & (lab == 1)], L2)
+    # same classes; at rest both models are inactive (every filtered pair sits at
+    # or beyond its own width)
+    assert np.array_equal(glob.klass, comp.klass)
+    assert glob.energy == 0.0 and comp.energy == 0.0
+    # the coarse yarn compressed to 0.85 of its segment length: its filtered
+    # gap-2 pairs (now 0.85 L2 apart) switch on at its own width L2, not at L1
+    xc = x.copy()
+    xc[0, n1 + 1:] = 0.85 * L2 * np.arange(n2 + 1)
+    g2 = O.contact_pass(sc, x=xc, ccd=False)
+    c2 = O.contact_pass(sc, x=xc, ccd=False, per_component=True)
+    act_g, act_c = set(g2.active_keys.tolist()), set(c2.active_keys.tolist())
+    extra = np.array(sorted(act_c - act_g), np.uint64)
+    assert act_g < act_c and extra.size == n2 - 2  # the gap-2 pairs of the n2 edges
+    assert np.all(c2.klass[np.searchsorted(c2.C, extra)] == O.KLASS_F)
+    assert c2.energy > g2.energy
