@@ -1703,72 +1703,74 @@ __global__ void __launch_bounds__(128) k_hess_proj_pe(HessArgs A, int64_t m) {
   // Q T+ Q^T in the order (0x, 0y, 1x, 1y), packed
   const double P4[10] = {ph0 * ph0 * Tp[0], ph0 * Tp[1], ph0 * ph1 * Tp[0], ph0 * Tp[2], Tp[3],
                          ph1 * Tp[1],       Tp[4],       ph1 * ph1 * Tp[0], ph1 * Tp[2], Tp[5]};
-  // B+ in the K3 basis, world axes: block (ab, bb) = R L(ab, bb) R^T with L
-  // the local 3x3 block (in-plane 2x2 from P4, e3-e3 entry from p2)
-  double Bp[21];
+  // Back to the three points and to world axes.  Local block (ab, bb) of the
+  // reduced matrix: L_ab,bb = [[in-plane 2x2 from P4, 0], [0, e3-e3 entry from
+  // p2]]; block (q1, q2) of the points is R L'(q1, q2) R^T with
+  // L'(q1, q2) = sum K3[q1][ab] K3[q2][bb] L_ab,bb.  K3's rows are (c, s),
+  // (-c, s), (0, -2s), c = 1/sqrt2, s = 1/sqrt6, so with X = L00/2,
+  // Y = L11/6, W = L11/3, S = cs (L01 + L10), Dm = cs (L01 - L10),
+  // Z = 2cs L01 (cs = 1/sqrt12):
+  //   L'00 = X + S + Y, L'11 = X - S + Y, L'22 = 2W,
+  //   L'01 = -X + Dm + Y, L'02 = -Z - W, L'12 = Z - W.
+  constexpr double cs = 0.28867513459481288225;  // 1/sqrt(12)
+  const double L00[2][2] = {{P4[0], P4[1]}, {P4[1], P4[4]}}, L01[2][2] = {{P4[2], P4[3]}, {P4[5], P4[6]}},
+               L11[2][2] = {{P4[7], P4[8]}, {P4[8], P4[9]}};
+  double Lq[6][2][2], zq[6];  // 00, 11, 22, 01, 02, 12
 #pragma unroll
-  for (int ab = 0; ab < 2; ++ab)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int bb = ab; bb < 2; ++bb) {
-      double L[3][3];
-#pragma unroll
-      for (int al = 0; al < 2; ++al)
-#pragma unroll
-        for (int be = 0; be < 2; ++be) {
-          const int r = 2 * ab + al, cl = 2 * bb + be;
-          L[al][be] = P4[r <= cl ? tri_idx(r, cl, 4) : tri_idx(cl, r, 4)];
-        }
-      L[0][2] = L[1][2] = L[2][0] = L[2][1] = 0.0;
-      L[2][2] = p2[ab == bb ? (ab == 0 ? 0 : 2) : 1];
-      double T[3][3];  // R L
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int be = 0; be < 3; ++be) T[i][be] = R[3 * i] * L[0][be] + R[3 * i + 1] * L[1][be] + R[3 * i + 2] * L[2][be];
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const int r = 3 * ab + i, cl = 3 * bb + j;
-          if (r > cl) continue;
-          Bp[tri_idx(r, cl, 6)] = T[i][0] * R[3 * j] + T[i][1] * R[3 * j + 1] + T[i][2] * R[3 * j + 2];
-        }
+    for (int j = 0; j < 2; ++j) {
+      const double X = 0.5 * L00[i][j], Y = L11[i][j] * (1.0 / 6.0), W = L11[i][j] * (1.0 / 3.0);
+      const double S = cs * (L01[i][j] + L01[j][i]), Dm = cs * (L01[i][j] - L01[j][i]), Z = 2.0 * cs * L01[i][j];
+      Lq[0][i][j] = X + S + Y;
+      Lq[1][i][j] = X - S + Y;
+      Lq[2][i][j] = 2.0 * W;
+      Lq[3][i][j] = -X + Dm + Y;
+      Lq[4][i][j] = -Z - W;
+      Lq[5][i][j] = Z - W;
     }
-  // scatter, as in k_hess_proj<6>
+  {
+    const double X = 0.5 * p2[0], Y = p2[2] * (1.0 / 6.0), W = p2[2] * (1.0 / 3.0), S = 2.0 * cs * p2[1],
+                 Z = 2.0 * cs * p2[1];
+    zq[0] = X + S + Y;
+    zq[1] = X - S + Y;
+    zq[2] = 2.0 * W;
+    zq[3] = -X + Y;
+    zq[4] = -Z - W;
+    zq[5] = Z - W;
+  }
+  // world block: E2 A2 E2^T + z e3 e3^T, E2 = (e1, e2) = columns 0, 1 of R
+  auto world = [&](const double (&A2)[2][2], double z, double (&w)[9]) {
+    double T[3][2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb) T[i][bb] = R[3 * i] * A2[0][bb] + R[3 * i + 1] * A2[1][bb];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double ze = z * R[3 * i + 2];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) w[3 * i + j] = T[i][0] * R[3 * j] + T[i][1] * R[3 * j + 1] + ze * R[3 * j + 2];
+    }
+  };
+  // scatter: the three points the point-edge type involves, in stencil order
   const uint32_t c = A.aidx[a];
   const Stencil st = stencil_of(A.cand[c], A.ev0, A.ev1, A.tv, A.T);
   const TypeInfo& TI = st.ee ? c_ee_types[A.ctype[c]] : c_pt_types[A.ctype[c]];
-  const int nz = TI.kind + 1;
   int pts[4], np = 0;
   for (int i = 0; i < 4; ++i) {
     bool used = false;
-    for (int mm = 0; mm < nz; ++mm) used |= TI.C[mm][i] != 0;
+    for (int mm = 0; mm < 2; ++mm) used |= TI.C[mm][i] != 0;
     if (used) pts[np++] = i;
   }
-  for (int q2 = 0; q2 < np; ++q2) {
-    double Rq[2][9];
+  const int qa[6] = {0, 1, 2, 0, 0, 1}, qb[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
-    for (int ab = 0; ab < 2; ++ab)
-#pragma unroll
-      for (int al = 0; al < 3; ++al)
-#pragma unroll
-        for (int be = 0; be < 3; ++be) {
-          double v = 0.0;
-#pragma unroll
-          for (int bb = 0; bb < 2; ++bb) {
-            const int r = 3 * ab + al, cl = 3 * bb + be;
-            v += c_K3[q2][bb] * Bp[r <= cl ? tri_idx(r, cl, 6) : tri_idx(cl, r, 6)];
-          }
-          Rq[ab][3 * al + be] = v;
-        }
-    for (int q1 = 0; q1 <= q2; ++q1) {
-      double blk[9];
-#pragma unroll
-      for (int e = 0; e < 9; ++e) blk[e] = c_K3[q1][0] * Rq[0][e] + c_K3[q1][1] * Rq[1][e];
-      const int r = st.v[pts[q1]], cc = st.v[pts[q2]];
-      add_block(A, r, cc, blk, false);
-      if (q1 != q2) add_block(A, cc, r, blk, true);
-    }
+  for (int k = 0; k < 6; ++k) {
+    double blk[9];
+    world(Lq[k], zq[k], blk);
+    const int r = st.v[pts[qa[k]]], cc = st.v[pts[qb[k]]];
+    add_block(A, r, cc, blk, false);
+    if (k >= 3) add_block(A, cc, r, blk, true);
   }
 }
 
