@@ -291,6 +291,10 @@ __device__ __forceinline__ int lower_bound_u32(const uint32_t* __restrict__ a, i
   return lo;
 }
 
+// pairs an entry's thread keeps from the count pass for the fill pass (larger
+// counts are found again by the fill pass's tests)
+constexpr int PAIR_STAGE = 32;
+
 struct PairArgs {
   Topo t;
   int64_t ne;
@@ -307,9 +311,8 @@ struct PairArgs {
   bool canonical;              // fill pass: write canonical keys (else compact ones for the sort)
 };
 
-// count pass (FILL = false): cnt[i] = number of pairs entry i reports;
-// fill pass (FILL = true): writes them at off[i] (cnt read back as the bound).
-// A vertex entry of a shell cell tests every triangle entry of the cell (the
+// The pairs one entry reports, in a fixed order (the count and the fill pass
+// make the same decisions).  A vertex entry of a shell cell tests every triangle entry of the cell (the
 // vertex threads of a cell walk the same triangles in step) and an edge entry
 // every later edge entry.  Rod cells hold many more edges (yarn segments
 // crowd the cells of a knit or weave), so there the m (m - 1) / 2 tests of a
@@ -319,10 +322,10 @@ struct PairArgs {
 // m - 1 and the last none.  (On shell cells the round robin measured slightly
 // slower.)
 template <bool FILL, bool RR>
-__global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __restrict__ cnt,
-                                                      const uint32_t* __restrict__ off, uint64_t* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.ne) return;
+__device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uint32_t* __restrict__ cnt,
+                                               const uint32_t* __restrict__ off, uint64_t* __restrict__ out,
+                                               uint64_t* __restrict__ stage, uint32_t* __restrict__ ovl,
+                                               unsigned int* __restrict__ novl) {
   const Topo& t = A.t;
   const uint32_t P = A.eval[i];
   const uint64_t kc = A.ekey[i];
@@ -354,11 +357,11 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __re
   int pv[3];
   prim_verts(t, (int)P, pv);
   const uint64_t tbits = (uint64_t)type << (A.bi + A.bj);
-  const uint64_t ipart = (uint64_t)(P - ibase) << A.bj;
   uint32_t count = 0, n32 = 0, n64 = 0;
-  uint64_t w = FILL ? off[i] : 0;
   // the fill pass re-makes the count pass's decisions; never write past them
-  const uint64_t w_end = FILL ? w + cnt[i] : 0;
+  const uint32_t c_end = FILL ? cnt[i] : 0;
+  // staged pairs (rod cells; shell cells hold too many pairs per vertex entry)
+  constexpr uint32_t K = RR ? PAIR_STAGE : 0;
   // RR (rod scenes): round robin over the cell (entries are sorted by
   // primitive, so the key takes the lower of the two first); else j in [j0, j1)
   const int m = e - s, a = (int)(i - s);
@@ -404,20 +407,22 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __re
       for (int k = 0; k < 3; ++k) ok = ok && (b1[k] <= b2[3 + k]) && (b2[k] <= b1[3 + k]);
       if (!ok) continue;
     }
+    // the pair's key: RR pairs whose partner is the lower primitive take it first
+    const bool swap = RR && j < (int)i;
+    const uint32_t K1 = swap ? Q : P, K2 = swap ? P : Q;
+    const uint64_t key = A.canonical ? cb_key(type, K1 - ibase, K2 - jbase)
+                                     : (tbits | ((uint64_t)(K1 - ibase) << A.bj) | (uint64_t)(K2 - jbase));
     if (FILL) {
-      if (w < w_end) {
-        if (RR && j < (int)i)  // the partner is the lower primitive
-          out[w++] = A.canonical ? cb_key(type, Q - ibase, P - jbase)
-                                 : (tbits | ((uint64_t)(Q - ibase) << A.bj) | (uint64_t)(P - jbase));
-        else
-          out[w++] = A.canonical ? cb_key(type, P - ibase, Q - jbase) : (tbits | ipart | (uint64_t)(Q - jbase));
-      }
-    } else {
-      ++count;
+      // the pairs past the staged ones, at their place in the entry's range
+      if (count >= K && count < c_end) out[(size_t)off[i] + count] = key;
+    } else if (count < K) {
+      stage[(size_t)count * A.ne + i] = key;
     }
+    ++count;
   }
   if (!FILL) {
     cnt[i] = count;
+    if (K > 0 && count > K) ovl[atomicAdd(novl, 1u)] = (uint32_t)i;
     if (A.fpstat) {  // one atomic per converged group of lanes
       const unsigned mask = __activemask();
       const unsigned a32 = __reduce_add_sync(mask, n32), a64 = __reduce_add_sync(mask, n64);
@@ -427,6 +432,41 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __re
       }
     }
   }
+}
+
+
+// count pass (FILL = false, one thread per entry): cnt[i] = number of pairs
+// entry i reports.  Rod cells (RR): the first PAIR_STAGE of them are staged
+// (element-major, stage[k * ne + i]) and entries with more are listed in
+// ovl; the fill pass (FILL = true) then runs over the listed entries only,
+// writing the pairs past the staged ones at their place, and k_pairs_copy
+// moves the staged keys.  Shell cells: the fill pass runs over every entry
+// (a vertex entry's pairs, one per triangle of its cell, rarely fit a stage;
+// staging them measured no faster).
+template <bool FILL, bool RR>
+__global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __restrict__ cnt,
+                                                      const uint32_t* __restrict__ off, uint64_t* __restrict__ out,
+                                                      uint64_t* __restrict__ stage, uint32_t* __restrict__ ovl,
+                                                      unsigned int* __restrict__ novl) {
+  if (!FILL || !RR) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < A.ne) pairs_of_entry<FILL, RR>(A, i, cnt, off, out, stage, ovl, novl);
+  } else {
+    const unsigned m = *novl;
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x)
+      pairs_of_entry<true, RR>(A, ovl[q], cnt, off, out, stage, ovl, novl);
+  }
+}
+
+// the staged keys of every entry to their place: entry i's first
+// min(cnt[i], PAIR_STAGE) pairs at off[i]
+__global__ void k_pairs_copy(int64_t ne, const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off,
+                             const uint64_t* __restrict__ stage, uint64_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  const uint32_t c = min(cnt[i], (uint32_t)PAIR_STAGE);
+  const size_t o = off[i];
+  for (uint32_t k = 0; k < c; ++k) out[o + k] = stage[(size_t)k * ne + i];
 }
 
 __global__ void k_expand(int64_t nc, const uint64_t* __restrict__ ck, int bi, int bj, uint64_t* __restrict__ out) {
@@ -595,15 +635,30 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   }
   const int pb = w.pair_block;
   const bool rods = s->kind == CB_ROD;
+  // keys are final from the count pass on: canonical straight out, compact for the sort
+  A.canonical = !sort_out;
+  unsigned int* novl = (unsigned int*)(scalars(s) + SC_NOVF);
+  if (rods) {
+    CB_TRY(buf_ensure(w.stage, sizeof(uint64_t) * PAIR_STAGE * (size_t)ne, st));
+    CB_TRY(buf_ensure(w.ovl, sizeof(uint32_t) * (size_t)ne, st));
+    CB_CUDA(cudaMemsetAsync(novl, 0, sizeof(unsigned int), st));
+  }
   auto pairs = [&](bool fill, uint64_t* o) {
     uint32_t* c = bp<uint32_t>(w.pair_cnt);
     const uint32_t* f = fill ? bp<uint32_t>(w.pair_off) : nullptr;
+    uint64_t* sg = bp<uint64_t>(w.stage);
+    uint32_t* ov = bp<uint32_t>(w.ovl);
     if (fill) {
-      if (rods) k_pairs<true, true><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o);
-      else k_pairs<true, false><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o);
+      if (rods) {
+        k_pairs_copy<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, c, f, sg, o);
+        const int g = (int)std::min<int64_t>(cb_grid(ne, pb), 152 * 8);
+        k_pairs<true, true><<<g, pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
+      } else {
+        k_pairs<true, false><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
+      }
     } else {
-      if (rods) k_pairs<false, true><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o);
-      else k_pairs<false, false><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o);
+      if (rods) k_pairs<false, true><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
+      else k_pairs<false, false><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
     }
   };
   pairs(false, nullptr);
@@ -617,13 +672,11 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   if (nc == 0) return CB_OK;
   if (!sort_out) {
     // canonical keys straight from the fill pass, in hash-cell order
-    A.canonical = true;
     CB_TRY(buf_ensure(out, sizeof(uint64_t) * (size_t)nc, st));
     pairs(true, bp<uint64_t>(out));
     CB_CUDA(cudaGetLastError());
     return CB_OK;
   }
-  A.canonical = false;
   for (int b = 0; b < 2; ++b) CB_TRY(buf_ensure(w.ckey[b], sizeof(uint64_t) * (size_t)nc, st));
   pairs(true, bp<uint64_t>(w.ckey[0]));
   const int cbits = s->bits_i + s->bits_j + (s->kind == CB_SHELL ? 2 : 0);

@@ -58,6 +58,8 @@ struct BroadWork {
   DevBuf pair_off;    // uint32 per entry (+1)
   DevBuf ebox;        // float4 lo, float4 hi per entry (boxes gathered into entry order)
   DevBuf ckey[2];     // uint64 compact candidate keys (ping-pong)
+  DevBuf stage;       // uint64 [PAIR_STAGE][entries]: the count pass's first pairs of each entry
+  DevBuf ovl;         // uint32 entries with more pairs than the stage holds
   DevBuf scan_tmp;
   DevBuf hist;
   float cell = 0.f;   // cell size of member 0 used last
@@ -169,7 +171,8 @@ enum {
   SC_FP32_PAIRS = 12,   // broad phase of contact_build: pairs passing the FP32 box test
   SC_FP64_DECIDED = 13, // ... of which the FP64 boxes decided
   SC_KSPLIT = 16,       // two uint32 counters: face / line-line pairs, the other active pairs
-  SC_N = 17
+  SC_NOVF = 17,         // broad phase: entries whose pairs overflow the stage
+  SC_N = 18
 };
 
 static inline uint64_t* scalars(cb_scene* s) { return (uint64_t*)s->dev_scalars.p; }
