@@ -64,8 +64,8 @@ struct CcdArgs {
   unsigned long long* __restrict__ macc;     // per member: alpha bits, lb bits, status, band lo/hi
   unsigned long long* __restrict__ status;
   unsigned long long* __restrict__ max_iters;
-  const float* __restrict__ xf;   // FP32 (x - member centre)
-  const float* __restrict__ pf;   // FP32 p
+  const float4* __restrict__ xf;  // FP32 (x - member centre), one float4 per vertex
+  const float4* __restrict__ pf;  // FP32 p, one float4 per vertex
   uint32_t* __restrict__ ulist;   // pairs left unresolved by the first step (lb < 1)
   unsigned int* __restrict__ nu;
 };
@@ -147,8 +147,9 @@ __device__ __forceinline__ AccdStart accd_start(const CcdArgs& A, int64_t q) {
   return S;
 }
 
-__device__ __forceinline__ cbb::f3 ldf(const float* __restrict__ a, int n, int v) {
-  return cbb::f3{a[v], a[(size_t)n + v], a[2 * (size_t)n + v]};
+__device__ __forceinline__ cbb::f3 ldf(const float4* __restrict__ a, int n, int v) {
+  const float4 q = a[v];
+  return cbb::f3{q.x, q.y, q.z};
 }
 
 // Minimum of non-negative doubles per member (compared as bit patterns): one
@@ -460,8 +461,8 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     A.max_iters = mi;
     CB_TRY(to_f32(s, x, bp<double>(s->bwc.cx), s->xf, st));
     CB_TRY(to_f32(s, p, nullptr, s->pf, st));
-    A.xf = bp<float>(s->xf);
-    A.pf = bp<float>(s->pf);
+    A.xf = bp<float4>(s->xf);
+    A.pf = bp<float4>(s->pf);
     CB_TRY(buf_ensure(s->dlist, sizeof(uint32_t) * (size_t)np, st));
     CB_TRY(buf_ensure(s->ccd_ulist, sizeof(uint32_t) * (size_t)np, st));
     unsigned int* nl = (unsigned int*)(sc + SC_NLIST);

@@ -267,7 +267,7 @@ __device__ __forceinline__ void warp_append_back(bool flag, uint32_t value, uint
 __global__ void k_distance_screen(int64_t nc, const uint64_t* __restrict__ cand,
                                   const uint8_t* __restrict__ klass_in, const int32_t* __restrict__ ev0,
                                   const int32_t* __restrict__ ev1, const int32_t* __restrict__ tv, int T,
-                                  const float* __restrict__ xf, const double* __restrict__ cx,
+                                  const float4* __restrict__ xf, const double* __restrict__ cx,
                                   const int32_t* __restrict__ vsc, const MemberParams* __restrict__ mp, int n,
                                   double* __restrict__ dout, int8_t* __restrict__ tout, uint8_t* __restrict__ cls,
                                   uint32_t* __restrict__ flag, uint32_t* __restrict__ list,
@@ -292,11 +292,9 @@ __global__ void k_distance_screen(int64_t nc, const uint64_t* __restrict__ cand,
       // rounded up, so the FP32 comparison is as safe)
       const float thr = k == 1 ? M.thrF32 : M.thrU32;
       const float X = (float)cx[4 * mem + 3];
-      const float lb = cbb::lower_bound(
-          s.ee, cbb::f3{xf[s.v[0]], xf[(size_t)n + s.v[0]], xf[2 * (size_t)n + s.v[0]]},
-          cbb::f3{xf[s.v[1]], xf[(size_t)n + s.v[1]], xf[2 * (size_t)n + s.v[1]]},
-          cbb::f3{xf[s.v[2]], xf[(size_t)n + s.v[2]], xf[2 * (size_t)n + s.v[2]]},
-          cbb::f3{xf[s.v[3]], xf[(size_t)n + s.v[3]], xf[2 * (size_t)n + s.v[3]]}, X);
+      const float4 q0 = xf[s.v[0]], q1 = xf[s.v[1]], q2 = xf[s.v[2]], q3 = xf[s.v[3]];
+      const float lb = cbb::lower_bound(s.ee, cbb::f3{q0.x, q0.y, q0.z}, cbb::f3{q1.x, q1.y, q1.z},
+                                        cbb::f3{q2.x, q2.y, q2.z}, cbb::f3{q3.x, q3.y, q3.z}, X);
       if (lb >= thr) {
         dout[c] = __longlong_as_double(0x7ff0000000000000LL);
         tout[c] = -1;
@@ -364,13 +362,16 @@ __global__ void k_distance_exact(const uint32_t* __restrict__ list, int64_t cap,
   }
 }
 
+// FP32 copy of a [3][n] FP64 vector, minus the member centre when cx is
+// given, one float4 (x, y, z, 0) per vertex: the screens gather a vertex's
+// three components in one 16-byte load
 __global__ void k_to_f32(int n, const double* __restrict__ v, const double* __restrict__ cx,
-                         const int32_t* __restrict__ vsc, float* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 3 * (int64_t)n) return;
-  const int k = (int)(i / n);
-  const double c = cx ? cx[4 * vsc[i - (int64_t)k * n] + k] : 0.0;
-  out[i] = (float)(v[i] - c);
+                         const int32_t* __restrict__ vsc, float4* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* c = cx ? cx + 4 * vsc[i] : nullptr;
+  out[i] = make_float4((float)(v[i] - (c ? c[0] : 0.0)), (float)(v[(size_t)n + i] - (c ? c[1] : 0.0)),
+                       (float)(v[2 * (size_t)n + i] - (c ? c[2] : 0.0)), 0.f);
 }
 
 __global__ void k_active_compact(int64_t nc, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
@@ -1928,9 +1929,8 @@ cb_status filter_apply(cb_scene* s, cudaStream_t st) {
 }
 
 cb_status to_f32(cb_scene* s, const double* v, const double* cx, DevBuf& out, cudaStream_t st) {
-  CB_TRY(buf_ensure(out, sizeof(float) * 3 * (size_t)s->n, st));
-  k_to_f32<<<cb_grid(3 * (int64_t)s->n), CB_THREADS, 0, cb_count(st)>>>(s->n, v, cx, bp<int32_t>(s->vsc),
-                                                                       bp<float>(out));
+  CB_TRY(buf_ensure(out, sizeof(float4) * (size_t)std::max(1, s->n), st));
+  k_to_f32<<<cb_grid(s->n), CB_THREADS, 0, cb_count(st)>>>(s->n, v, cx, bp<int32_t>(s->vsc), bp<float4>(out));
   CB_CUDA(cudaGetLastError());
   return CB_OK;
 }
@@ -1971,7 +1971,7 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_NLIST), 0ull);
     k_distance_screen<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(
         nc, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass), bp<int32_t>(s->ev0), bp<int32_t>(s->ev1),
-        bp<int32_t>(s->tv), s->T, bp<float>(s->xf), bp<double>(s->bw.cx), bp<int32_t>(s->vsc),
+        bp<int32_t>(s->tv), s->T, bp<float4>(s->xf), bp<double>(s->bw.cx), bp<int32_t>(s->vsc),
         bp<MemberParams>(s->mp), s->n, bp<double>(s->cd),
         bp<int8_t>(s->ctype), bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), bp<uint32_t>(s->dlist), nl);
     k_distance_exact<<<std::min<int64_t>(cb_grid(nc), 152 * 16), CB_THREADS, 0, cb_count(st)>>>(
