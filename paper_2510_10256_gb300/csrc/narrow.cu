@@ -383,16 +383,76 @@ __global__ void k_active_compact(int64_t nc, const uint32_t* __restrict__ flag, 
 // ------------------------------------------------------------------ (d) ----
 
 // 16 (row, col) block keys of each active stencil
-__global__ void k_block_keys(int64_t na, const uint32_t* __restrict__ aidx, const uint64_t* __restrict__ cand,
-                             const int32_t* __restrict__ ev0, const int32_t* __restrict__ ev1,
-                             const int32_t* __restrict__ tv, int T, int bits_n, uint64_t* __restrict__ bkey) {
-  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= na) return;
-  Stencil s = stencil_of(cand[aidx[a]], ev0, ev1, tv, T);
+// BSR pattern keys (row << bits_n | col) of the 16 blocks of every active
+// stencil, made distinct within each run of BK_PAIRS active pairs (in
+// candidate order, i.e. hash-cell order, a run shares most of its vertices:
+// its 16 x 256 keys hold about a fifth as many distinct ones) through an
+// open-addressing set in shared memory (linear probing, at most half full,
+// each probe sequence bounded by the table size).  The distinct keys of each
+// run are appended to bkey in no particular order -- the radix sort and the
+// unique pass that follow make the pattern -- and their count to *m_out.
+constexpr int BK_PAIRS = 256;
+constexpr int BK_SLOTS = 8192;  // 2 x 16 keys x BK_PAIRS
+
+__global__ void __launch_bounds__(BK_PAIRS) k_block_keys(int64_t na, const uint32_t* __restrict__ aidx,
+                                                         const uint64_t* __restrict__ cand,
+                                                         const int32_t* __restrict__ ev0,
+                                                         const int32_t* __restrict__ ev1,
+                                                         const int32_t* __restrict__ tv, int T, int bits_n,
+                                                         uint64_t* __restrict__ bkey, unsigned int* __restrict__ m_out) {
+  extern __shared__ unsigned long long tab[];  // BK_SLOTS
+  __shared__ unsigned int wsum[BK_PAIRS / 32];
+  __shared__ unsigned int base;
+  constexpr unsigned long long EMPTY = ~0ull;  // no key: rows and columns are below 2^31
+  const int tid = threadIdx.x;
+  for (int k = tid; k < BK_SLOTS; k += BK_PAIRS) tab[k] = EMPTY;
+  __syncthreads();
+  const int64_t a = (int64_t)blockIdx.x * BK_PAIRS + tid;
+  if (a < na) {
+    const Stencil s = stencil_of(cand[aidx[a]], ev0, ev1, tv, T);
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) bkey[16 * a + 4 * i + j] = ((uint64_t)s.v[i] << bits_n) | (uint64_t)s.v[j];
+      for (int j = 0; j < 4; ++j) {
+        const unsigned long long key = ((unsigned long long)s.v[i] << bits_n) | (unsigned long long)s.v[j];
+        // Fibonacci hashing (multiplicative, Knuth): the top bits of key x 2^64/phi
+        unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 51);
+        for (int probe = 0; probe < BK_SLOTS; ++probe) {
+          const unsigned long long prev = atomicCAS(&tab[h], EMPTY, key);
+          if (prev == EMPTY || prev == key) break;
+          h = (h + 1) & (BK_SLOTS - 1);
+        }
+      }
+  }
+  __syncthreads();
+  // compaction: thread tid owns slots [tid * 32, tid * 32 + 32)
+  constexpr int PER = BK_SLOTS / BK_PAIRS;
+  unsigned c = 0;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) c += tab[tid * PER + k] != EMPTY;
+  const unsigned lane = tid & 31, wid = tid >> 5;
+  unsigned incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((int)lane >= o) incl += v;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  unsigned woff = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < BK_PAIRS / 32; ++w) {
+    woff += (w < (int)wid) ? wsum[w] : 0u;
+    tot += wsum[w];
+  }
+  if (tid == 0) base = tot ? atomicAdd(m_out, tot) : 0u;
+  __syncthreads();
+  size_t pos = (size_t)base + woff + incl - c;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const unsigned long long key = tab[tid * PER + k];
+    if (key != EMPTY) bkey[pos++] = key;
+  }
 }
 
 __global__ void k_unique_flag(int64_t m, const uint64_t* __restrict__ k, uint32_t* __restrict__ flag) {
@@ -1998,7 +2058,7 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     k_active_compact<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(nc, bp<uint32_t>(s->cflag), bp<uint32_t>(s->cpos),
                                                          bp<uint32_t>(s->aidx));
     // BSR pattern: sorted unique (row, col) of the 16 blocks of every active stencil
-    const int64_t m = 16 * na;
+    int64_t m = 16 * na;  // capacity; the keys actually sorted are counted by k_block_keys
     const int bn = bits_for(s->n);
     for (int b = 0; b < 2; ++b) CB_TRY(buf_ensure(s->bkey[b], sizeof(uint64_t) * (size_t)m, st));
     CB_TRY(buf_ensure(s->bflag, sizeof(uint32_t) * (size_t)m, st));
@@ -2007,9 +2067,19 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     CB_TRY(buf_ensure(s->scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(cbp::radix_hist_elems(m)) +
                                                                 cbp::scan_tmp_elems(m) + 8),
                       st));
-    k_block_keys<<<cb_grid(na), CB_THREADS, 0, cb_count(st)>>>(na, bp<uint32_t>(s->aidx), bp<uint64_t>(s->cand),
-                                                     bp<int32_t>(s->ev0), bp<int32_t>(s->ev1), bp<int32_t>(s->tv),
-                                                     s->T, bn, bp<uint64_t>(s->bkey[0]));
+    unsigned int* nbk = (unsigned int*)(sc + SC_NBK);
+    CB_CUDA(cudaMemsetAsync(nbk, 0, sizeof(unsigned int), st));
+    {
+      const int smem = BK_SLOTS * (int)sizeof(unsigned long long);
+      CB_CUDA(cudaFuncSetAttribute(k_block_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      k_block_keys<<<(int)((na + BK_PAIRS - 1) / BK_PAIRS), BK_PAIRS, smem, cb_count(st)>>>(
+          na, bp<uint32_t>(s->aidx), bp<uint64_t>(s->cand), bp<int32_t>(s->ev0), bp<int32_t>(s->ev1),
+          bp<int32_t>(s->tv), s->T, bn, bp<uint64_t>(s->bkey[0]), nbk);
+      CB_CUDA(cudaGetLastError());
+    }
+    uint64_t hm;
+    CB_TRY(read_scalars(s, SC_NBK, 1, &hm, st));
+    m = (int64_t)(uint32_t)hm;  // keys left after the per-run sets (at most 16 na)
     int r = cbp::radix_sort<uint64_t, uint32_t, false>(bp<uint64_t>(s->bkey[0]), nullptr, bp<uint64_t>(s->bkey[1]),
                                                        nullptr, m, 0, 2 * bn, bp<uint32_t>(s->hist),
                                                        bp<uint32_t>(s->scan_tmp), st);

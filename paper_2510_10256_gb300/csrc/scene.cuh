@@ -172,7 +172,8 @@ enum {
   SC_FP64_DECIDED = 13, // ... of which the FP64 boxes decided
   SC_KSPLIT = 16,       // two uint32 counters: face / line-line pairs, the other active pairs
   SC_NOVF = 17,         // broad phase: entries whose pairs overflow the stage
-  SC_N = 18
+  SC_NBK = 18,          // BSR pattern: keys left after the per-run sets of k_block_keys
+  SC_N = 19
 };
 
 static inline uint64_t* scalars(cb_scene* s) { return (uint64_t*)s->dev_scalars.p; }

@@ -158,3 +158,24 @@ def test_tuning_knobs_change_nothing(factor, block):
              stats=cs.stats(), status=cs.sync_status(), frest=cs.pairs("rest_filtered"))
     cs.close()
     compare(sc, g, o)
+
+
+def test_dense_rod_bundle_overflows_the_pair_stage():
+    """200 short parallel rods 0.005 mm apart (thickness 0.1): every edge has
+    over a hundred candidate partners, so entries find more pairs than the
+    32 the rod broad phase stages and its fill pass re-tests them."""
+    n_rods, nseg, seg = 200, 3, 0.05
+    pts, rp = [], [0]
+    for r in range(n_rods):
+        for k in range(nseg + 1):
+            pts.append((k * seg, 0.005 * r, 0.0))
+        rp.append(len(pts))
+    x = np.array(pts, np.float64).T.copy()
+    rng = np.random.default_rng(5)
+    p = rng.normal(0.0, 0.002, size=x.shape)
+    sc = S.Scene("rod", x.copy(), x.copy(), p, 0.1, 0.01, rod_ptr=np.array(rp, np.int32), name="bundle")
+    g = run_gpu(sc)
+    o = O.contact_pass(sc)
+    rep = compare(sc, g, o)
+    per_edge = 2.0 * rep["C"] / (n_rods * nseg)
+    assert per_edge > 100, per_edge
