@@ -837,12 +837,11 @@ __host__ __device__ __forceinline__ void write_reduced(double* __restrict__ Bo, 
 //   r_bb = M[1][bb],  Y = (M^T H_z[y, y] M)
 // (the (x, x) block is zero and the (x, y) block has rank one).  Queued:
 // p (2), r (2), Y (3, packed), the 2x2 block (3, packed) and the frame R
-// (row-major, columns e1 e2 e3; 9).
+// (row-major, columns e1 e2 e3; 9).  il = 1 / lu.
 __device__ __forceinline__ void write_reduced_pe_local(double* __restrict__ Bo, int64_t cap, unsigned slot,
                                                        const double (&M)[3][3], double g0, double g1, double wx,
-                                                       double wy, double lu, double c1, double c2,
+                                                       double wy, double il, double c1, double c2,
                                                        const double (&Rf)[9]) {
-  const double il = 1.0 / lu;
   const double hxy01 = c2 * (-2.0 * wy * il), hxy11 = c2 * (2.0 * wx * wy * il * il);
   const double hwu = -2.0 * wx * il;
   const double Hyy[2][2] = {{c1 * g0 * g0 + 2.0 * c2, c1 * g0 * g1 + c2 * hwu},
@@ -962,14 +961,17 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
     // beyond a ratio of 64 the pair stays on the generic 6x6 path.
     bool pe_local = false;
     d3 zl[3];
+    double piu = 0.0;  // 1 / |u| of a point-edge pair in its frame
     if (kind == 1) {
       const d3 w = z[0], u = z[1];
       const d3 n = mk3(u.y * w.z - u.z * w.y, u.z * w.x - u.x * w.z, u.x * w.y - u.y * w.x);
-      const double ln = sqrt(n.x * n.x + n.y * n.y + n.z * n.z);
-      const double lu = sqrt(u.x * u.x + u.y * u.y + u.z * u.z);
-      const double lw = sqrt(w.x * w.x + w.y * w.y + w.z * w.z);
-      if (ln > 0.0 && lw * lu <= 64.0 * ln) {
-        const double iu = 1.0 / lu, inn = 1.0 / ln;
+      // squared lengths; the conditioning test |w||u| <= 64 |u x w| squared
+      const double nn2 = n.x * n.x + n.y * n.y + n.z * n.z;
+      const double uu2 = u.x * u.x + u.y * u.y + u.z * u.z;
+      const double ww2 = w.x * w.x + w.y * w.y + w.z * w.z;
+      if (nn2 > 0.0 && ww2 * uu2 <= 4096.0 * nn2) {
+        const double iu = rsqrt(uu2), inn = rsqrt(nn2), lu = uu2 * iu;
+        piu = iu;
         const d3 e1 = mk3(u.x * iu, u.y * iu, u.z * iu), e3 = mk3(n.x * inn, n.y * inn, n.z * inn);
         const d3 e2 = mk3(e3.y * e1.z - e3.z * e1.y, e3.z * e1.x - e3.x * e1.z, e3.x * e1.y - e3.y * e1.x);
         zl[0] = mk3(w.x * e1.x + w.y * e1.y + w.z * e1.z, w.x * e2.x + w.y * e2.y + w.z * e2.z, 0.0);
@@ -1007,11 +1009,11 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
       // In the frame (w' = (wx, wy, 0), u' = (lu, 0, 0), s = wy^2) grad s has
       // only the y components 2 wy (w) and -2 wx wy / lu (u); hess s is
       // formed in write_reduced_pe_local
-      const double pwx = zl[0].x, pwy = zl[0].y, plu = zl[1].x;
+      const double pwx = zl[0].x, pwy = zl[0].y;
       for (int k = 0; k < 9; ++k) gd[k] = 0.0;
       gd[1] = 2.0 * pwy * i2d;
-      gd[4] = -2.0 * pwx * pwy / plu * i2d;
-      write_reduced_pe_local(Bq, 1, 0, M, gd[1], gd[4], pwx, pwy, plu, c1, c2, Rf);
+      gd[4] = -2.0 * pwx * pwy * piu * i2d;
+      write_reduced_pe_local(Bq, 1, 0, M, gd[1], gd[4], pwx, pwy, piu, c1, c2, Rf);
       want = 4;
     } else if (kind == 2) {
       const double zz[3][3] = {{z[0].x, z[0].y, z[0].z}, {z[1].x, z[1].y, z[1].z}, {z[2].x, z[2].y, z[2].z}};
