@@ -37,10 +37,10 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 # active pair, k_hess_proj<9> per face / line-line pair, k_hess_proj_pe per
 # point-edge pair in its own frame; k_hess_proj<6> (generic point-edge pairs,
 # none in that capture) is scaled from k_hess_proj<9> by (6/9)^3.
-HESS_FLOPS = {"prep": 601.2, "face": 11471.0, "pe_frame": 1269.9, "pe": 11471.0 * (6 / 9) ** 3}
+HESS_FLOPS = {"prep": 549.1, "face": 11471.0, "pe_frame": 1091.0, "pe": 11471.0 * (6 / 9) ** 3}
 # DRAM bytes (read + write) of the stage-(d) kernels per active pair, from the
-# same capture (136.0 MB); traffic grows in proportion to the active pairs
-HESS_DRAM_BYTES_PER_ACTIVE = 136.0e6 / 195263
+# same capture (135.3 MB); traffic grows in proportion to the active pairs
+HESS_DRAM_BYTES_PER_ACTIVE = 135.3e6 / 195263
 
 
 def hess_flops(st) -> float:
