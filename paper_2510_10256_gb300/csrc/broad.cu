@@ -294,6 +294,12 @@ __device__ __forceinline__ int lower_bound_u32(const uint32_t* __restrict__ a, i
 // pairs an entry's thread keeps from the count pass for the fill pass (larger
 // counts are found again by the fill pass's tests)
 constexpr int PAIR_STAGE = 32;
+// Shell cells: the count pass keeps the outcome of each entry's first
+// PAIR_MASK_BITS partner positions as bits (bit b = j - j0 of entry i in word
+// mask[(b / 32) * ne + i]), so the keys of those pairs are written from the
+// bits without repeating the tests
+constexpr int PAIR_MASK_WORDS = 16;
+constexpr int PAIR_MASK_BITS = 32 * PAIR_MASK_WORDS;
 
 struct PairArgs {
   Topo t;
@@ -306,10 +312,57 @@ struct PairArgs {
   const float4* __restrict__ ebox;   // boxes in entry order: entry j at [2 j], [2 j + 1]
   const double* __restrict__ box64;
   const Grid* __restrict__ grids;
+  uint32_t* __restrict__ mask;       // shells: [PAIR_MASK_WORDS][entries] partner bits
   int bi, bj;
   unsigned long long* fpstat;  // count pass: [0] FP32-accepted pairs, [1] FP64-decided (may be null)
   bool canonical;              // fill pass: write canonical keys (else compact ones for the sort)
 };
+
+// An entry's partners: entries [j0, j1) of its run s..e (none for a triangle
+// entry of a shell cell), the key type and the id offsets of the two sides.
+struct EntryRange {
+  uint32_t P, type, ibase, jbase;
+  int s, e, j0, j1;
+  bool none;
+};
+
+__device__ __forceinline__ EntryRange entry_range(const PairArgs& A, int64_t i) {
+  const Topo& t = A.t;
+  EntryRange R;
+  R.P = A.eval[i];
+  const uint32_t r = A.run_id[i];
+  R.s = (int)A.run_start[r];
+  R.e = (int)A.run_start[r + 1];
+  R.ibase = R.jbase = 0;
+  R.none = false;
+  if (t.kind == CB_ROD) {
+    R.j0 = (int)i + 1;
+    R.j1 = R.e;
+    R.type = CB_KEY_ROD_EE;
+  } else if (R.P < (uint32_t)t.n) {
+    R.j0 = lower_bound_u32(A.eval, R.s, R.e, (uint32_t)t.n);
+    R.j1 = lower_bound_u32(A.eval, R.j0, R.e, (uint32_t)(t.n + t.T));
+    R.type = CB_KEY_PT;
+    R.jbase = (uint32_t)t.n;
+  } else if (R.P < (uint32_t)(t.n + t.T)) {
+    R.j0 = R.j1 = 0;
+    R.type = 0;
+    R.none = true;
+  } else {
+    R.j0 = (int)i + 1;
+    R.j1 = R.e;
+    R.type = CB_KEY_EE;
+    R.ibase = R.jbase = (uint32_t)(t.n + t.T);
+  }
+  return R;
+}
+
+// key of the pair (k1, k2) (ids already relative to their kind): canonical,
+// or compact (type | k1 | k2 in bi + bj bits) for the sort
+__device__ __forceinline__ uint64_t pair_key(const PairArgs& A, uint32_t type, uint32_t k1, uint32_t k2) {
+  return A.canonical ? cb_key(type, k1, k2)
+                     : (((uint64_t)type << (A.bi + A.bj)) | ((uint64_t)k1 << A.bj) | (uint64_t)k2);
+}
 
 // The pairs one entry reports, in a fixed order (the count and the fill pass
 // make the same decisions).  A vertex entry of a shell cell tests every triangle entry of the cell (the
@@ -327,36 +380,18 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
                                                uint64_t* __restrict__ stage, uint32_t* __restrict__ ovl,
                                                unsigned int* __restrict__ novl) {
   const Topo& t = A.t;
-  const uint32_t P = A.eval[i];
-  const uint64_t kc = A.ekey[i];
-  const Grid G = A.grids[kc >> 30];
-  const uint32_t r = A.run_id[i];
-  const int s = (int)A.run_start[r], e = (int)A.run_start[r + 1];
-  int j0, j1;
-  uint32_t type;
-  uint32_t ibase = 0, jbase = 0;
-  if (t.kind == CB_ROD) {
-    j0 = (int)i + 1;
-    j1 = e;
-    type = CB_KEY_ROD_EE;
-  } else if (P < (uint32_t)t.n) {
-    j0 = lower_bound_u32(A.eval, s, e, (uint32_t)t.n);
-    j1 = lower_bound_u32(A.eval, j0, e, (uint32_t)(t.n + t.T));
-    type = CB_KEY_PT;
-    jbase = (uint32_t)t.n;
-  } else if (P < (uint32_t)(t.n + t.T)) {
+  const EntryRange R = entry_range(A, i);
+  if (R.none) {
     if (!FILL) cnt[i] = 0;
     return;
-  } else {
-    j0 = (int)i + 1;
-    j1 = e;
-    type = CB_KEY_EE;
-    ibase = jbase = (uint32_t)(t.n + t.T);
   }
+  const uint32_t P = R.P;
+  const uint64_t kc = A.ekey[i];
+  const Grid G = A.grids[kc >> 30];
+  int j0 = R.j0, j1 = R.j1;
   const float4 plo = A.ebox[2 * (size_t)i], phi = A.ebox[2 * (size_t)i + 1];
   int pv[3];
   prim_verts(t, (int)P, pv);
-  const uint64_t tbits = (uint64_t)type << (A.bi + A.bj);
   uint32_t count = 0, n32 = 0, n64 = 0;
   // the fill pass re-makes the count pass's decisions; never write past them
   const uint32_t c_end = FILL ? cnt[i] : 0;
@@ -364,65 +399,89 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
   constexpr uint32_t K = RR ? PAIR_STAGE : 0;
   // RR (rod scenes): round robin over the cell (entries are sorted by
   // primitive, so the key takes the lower of the two first); else j in [j0, j1)
-  const int m = e - s, a = (int)(i - s);
+  const int m = R.e - R.s, a = (int)(i - R.s);
   if (RR) {
     j0 = 0;
     j1 = (m % 2 == 0 && a < m / 2) ? m / 2 : (m - 1) / 2;
   }
-  for (int jj = j0; jj < j1; ++jj) {
+  // shells: the fill pass runs only for entries with pairs past the partner
+  // bits (k_pairs_emit writes the pairs of the bits), from there on
+  int jb = j0;
+  if (!RR && FILL) {
+    jb = j0 + PAIR_MASK_BITS;
+#pragma unroll
+    for (int w = 0; w < PAIR_MASK_WORDS; ++w) count += __popc(A.mask[(size_t)w * A.ne + i]);
+  }
+  uint32_t word = 0, beyond = 0;
+  for (int jj = jb; jj < j1; ++jj) {
     int j = jj;
     if (RR) {
       j = a + 1 + jj;
       if (j >= m) j -= m;
-      j += s;
+      j += R.s;
     }
     const uint32_t Q = A.eval[j];
+    bool acc = false;
     const float4 qlo = A.ebox[2 * (size_t)j], qhi = A.ebox[2 * (size_t)j + 1];
-    if (!(plo.x <= qhi.x && qlo.x <= phi.x && plo.y <= qhi.y && qlo.y <= phi.y && plo.z <= qhi.z &&
-          qlo.z <= phi.z))
-      continue;
-    // home cell: low corner of the intersection
-    const uint32_t hc = morton(cell_of(fmaxf(plo.x, qlo.x), G.ox, G.inv, G.dx),
-                               cell_of(fmaxf(plo.y, qlo.y), G.oy, G.inv, G.dy),
-                               cell_of(fmaxf(plo.z, qlo.z), G.oz, G.inv, G.dz));
-    if (hc != (uint32_t)(kc & 0x3fffffffull)) continue;
-    int qv[3];
-    prim_verts(t, (int)Q, qv);
-    bool inc = false;
+    if (plo.x <= qhi.x && qlo.x <= phi.x && plo.y <= qhi.y && qlo.y <= phi.y && plo.z <= qhi.z &&
+        qlo.z <= phi.z) {
+      // home cell: low corner of the intersection
+      const uint32_t hc = morton(cell_of(fmaxf(plo.x, qlo.x), G.ox, G.inv, G.dx),
+                                 cell_of(fmaxf(plo.y, qlo.y), G.oy, G.inv, G.dy),
+                                 cell_of(fmaxf(plo.z, qlo.z), G.oz, G.inv, G.dz));
+      if (hc == (uint32_t)(kc & 0x3fffffffull)) {
+        int qv[3];
+        prim_verts(t, (int)Q, qv);
+        bool inc = false;
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int b = 0; b < 3; ++b) inc |= (pv[a] >= 0 && pv[a] == qv[b]);
-    if (inc) continue;
-    const bool sure = nextup(plo.x) <= nextdn(qhi.x) && nextup(qlo.x) <= nextdn(phi.x) &&
-                      nextup(plo.y) <= nextdn(qhi.y) && nextup(qlo.y) <= nextdn(phi.y) &&
-                      nextup(plo.z) <= nextdn(qhi.z) && nextup(qlo.z) <= nextdn(phi.z);
-    ++n32;
-    if (!sure) {
-      ++n64;
-      const double* b1 = A.box64 + (size_t)P * 6;
-      const double* b2 = A.box64 + (size_t)Q * 6;
-      bool ok = true;
+          for (int b = 0; b < 3; ++b) inc |= (pv[a] >= 0 && pv[a] == qv[b]);
+        if (!inc) {
+          const bool sure = nextup(plo.x) <= nextdn(qhi.x) && nextup(qlo.x) <= nextdn(phi.x) &&
+                            nextup(plo.y) <= nextdn(qhi.y) && nextup(qlo.y) <= nextdn(phi.y) &&
+                            nextup(plo.z) <= nextdn(qhi.z) && nextup(qlo.z) <= nextdn(phi.z);
+          ++n32;
+          acc = true;
+          if (!sure) {
+            ++n64;
+            const double* b1 = A.box64 + (size_t)P * 6;
+            const double* b2 = A.box64 + (size_t)Q * 6;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) ok = ok && (b1[k] <= b2[3 + k]) && (b2[k] <= b1[3 + k]);
-      if (!ok) continue;
+            for (int k = 0; k < 3; ++k) acc = acc && (b1[k] <= b2[3 + k]) && (b2[k] <= b1[3 + k]);
+          }
+        }
+      }
     }
-    // the pair's key: RR pairs whose partner is the lower primitive take it first
-    const bool swap = RR && j < (int)i;
-    const uint32_t K1 = swap ? Q : P, K2 = swap ? P : Q;
-    const uint64_t key = A.canonical ? cb_key(type, K1 - ibase, K2 - jbase)
-                                     : (tbits | ((uint64_t)(K1 - ibase) << A.bj) | (uint64_t)(K2 - jbase));
-    if (FILL) {
-      // the pairs past the staged ones, at their place in the entry's range
-      if (count >= K && count < c_end) out[(size_t)off[i] + count] = key;
-    } else if (count < K) {
-      stage[(size_t)count * A.ne + i] = key;
+    if (acc) {
+      // the pair's key: RR pairs whose partner is the lower primitive take it first
+      const bool swap = RR && j < (int)i;
+      const uint64_t key = pair_key(A, R.type, (swap ? Q : P) - R.ibase, (swap ? P : Q) - R.jbase);
+      if (FILL) {
+        // the pairs past the staged ones, at their place in the entry's range
+        if (count >= K && count < c_end) out[(size_t)off[i] + count] = key;
+      } else if (count < K) {
+        stage[(size_t)count * A.ne + i] = key;
+      }
+      ++count;
     }
-    ++count;
+    if (!RR && !FILL) {
+      // the lanes of a warp are at the same position b: coalesced word stores
+      const int b = jj - j0;
+      if (b < PAIR_MASK_BITS) {
+        word |= (uint32_t)acc << (b & 31);
+        if ((b & 31) == 31 || jj + 1 == j1) {
+          A.mask[(size_t)(b >> 5) * A.ne + i] = word;
+          word = 0;
+        }
+      } else {
+        beyond += acc;
+      }
+    }
   }
   if (!FILL) {
     cnt[i] = count;
-    if (K > 0 && count > K) ovl[atomicAdd(novl, 1u)] = (uint32_t)i;
+    if ((RR && count > K) || (!RR && beyond > 0)) ovl[atomicAdd(novl, 1u)] = (uint32_t)i;
     if (A.fpstat) {  // one atomic per converged group of lanes
       const unsigned mask = __activemask();
       const unsigned a32 = __reduce_add_sync(mask, n32), a64 = __reduce_add_sync(mask, n64);
@@ -438,23 +497,48 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
 // count pass (FILL = false, one thread per entry): cnt[i] = number of pairs
 // entry i reports.  Rod cells (RR): the first PAIR_STAGE of them are staged
 // (element-major, stage[k * ne + i]) and entries with more are listed in
-// ovl; the fill pass (FILL = true) then runs over the listed entries only,
-// writing the pairs past the staged ones at their place, and k_pairs_copy
-// moves the staged keys.  Shell cells: the fill pass runs over every entry
-// (a vertex entry's pairs, one per triangle of its cell, rarely fit a stage;
-// staging them measured no faster).
+// ovl; k_pairs_copy moves the staged keys.  Shell cells: the outcome of the
+// first PAIR_MASK_BITS partner positions is kept as bits, entries with pairs
+// past them are listed in ovl, and k_pairs_emit writes the pairs of the bits.
+// The fill pass (FILL = true) then runs over the listed entries only, writing
+// the remaining pairs at their place.
 template <bool FILL, bool RR>
 __global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __restrict__ cnt,
                                                       const uint32_t* __restrict__ off, uint64_t* __restrict__ out,
                                                       uint64_t* __restrict__ stage, uint32_t* __restrict__ ovl,
                                                       unsigned int* __restrict__ novl) {
-  if (!FILL || !RR) {
+  if (!FILL) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < A.ne) pairs_of_entry<FILL, RR>(A, i, cnt, off, out, stage, ovl, novl);
   } else {
     const unsigned m = *novl;
     for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x)
       pairs_of_entry<true, RR>(A, ovl[q], cnt, off, out, stage, ovl, novl);
+  }
+}
+
+// Shell cells: the pairs of the count pass's partner bits, at the start of
+// each entry's range in partner order (the order the tests found them in)
+__global__ void __launch_bounds__(CB_THREADS) k_pairs_emit(PairArgs A, const uint32_t* __restrict__ cnt,
+                                                           const uint32_t* __restrict__ off,
+                                                           uint64_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.ne) return;
+  const uint32_t c_end = cnt[i];
+  if (c_end == 0) return;
+  const EntryRange R = entry_range(A, i);
+  const int nb = min(R.j1 - R.j0, PAIR_MASK_BITS);
+  const size_t o = off[i];
+  uint32_t count = 0;
+  for (int w = 0; 32 * w < nb; ++w) {
+    uint32_t word = A.mask[(size_t)w * A.ne + i];
+    while (word) {
+      const int b = __ffs(word) - 1;
+      word &= word - 1;
+      const uint32_t Q = A.eval[R.j0 + 32 * w + b];
+      if (count < c_end) out[o + count] = pair_key(A, R.type, R.P - R.ibase, Q - R.jbase);
+      ++count;
+    }
   }
 }
 
@@ -638,11 +722,11 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   // keys are final from the count pass on: canonical straight out, compact for the sort
   A.canonical = !sort_out;
   unsigned int* novl = (unsigned int*)(scalars(s) + SC_NOVF);
-  if (rods) {
-    CB_TRY(buf_ensure(w.stage, sizeof(uint64_t) * PAIR_STAGE * (size_t)ne, st));
-    CB_TRY(buf_ensure(w.ovl, sizeof(uint32_t) * (size_t)ne, st));
-    CB_CUDA(cudaMemsetAsync(novl, 0, sizeof(unsigned int), st));
-  }
+  CB_TRY(buf_ensure(w.stage, rods ? sizeof(uint64_t) * PAIR_STAGE * (size_t)ne
+                                   : sizeof(uint32_t) * PAIR_MASK_WORDS * (size_t)ne, st));
+  CB_TRY(buf_ensure(w.ovl, sizeof(uint32_t) * (size_t)ne, st));
+  CB_CUDA(cudaMemsetAsync(novl, 0, sizeof(unsigned int), st));
+  A.mask = rods ? nullptr : bp<uint32_t>(w.stage);
   auto pairs = [&](bool fill, uint64_t* o) {
     uint32_t* c = bp<uint32_t>(w.pair_cnt);
     const uint32_t* f = fill ? bp<uint32_t>(w.pair_off) : nullptr;
@@ -654,7 +738,9 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
         const int g = (int)std::min<int64_t>(cb_grid(ne, pb), 152 * 8);
         k_pairs<true, true><<<g, pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
       } else {
-        k_pairs<true, false><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
+        k_pairs_emit<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, c, f, o);
+        const int g = (int)std::min<int64_t>(cb_grid(ne, pb), 152 * 8);
+        k_pairs<true, false><<<g, pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
       }
     } else {
       if (rods) k_pairs<false, true><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
