@@ -532,12 +532,24 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs_emit(PairArgs A, const uin
   uint32_t count = 0;
   for (int w = 0; 32 * w < nb; ++w) {
     uint32_t word = A.mask[(size_t)w * A.ne + i];
+    const int jw = R.j0 + 32 * w;
+    // four bits per round, their partner loads issued before any store
     while (word) {
-      const int b = __ffs(word) - 1;
-      word &= word - 1;
-      const uint32_t Q = A.eval[R.j0 + 32 * w + b];
-      if (count < c_end) out[o + count] = pair_key(A, R.type, R.P - R.ibase, Q - R.jbase);
-      ++count;
+      int jb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        jb[u] = word ? jw + __ffs(word) - 1 : -1;
+        word &= word - 1;
+      }
+      uint32_t Q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) Q[u] = jb[u] >= 0 ? A.eval[jb[u]] : 0u;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (jb[u] < 0) break;
+        if (count < c_end) out[o + count] = pair_key(A, R.type, R.P - R.ibase, Q[u] - R.jbase);
+        ++count;
+      }
     }
   }
 }
