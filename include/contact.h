@@ -120,6 +120,9 @@ typedef struct {
   int64_t n_hess_face;        /* last barrier_eval: active face / line-line pairs (9x9 projection) */
   int64_t n_hess_pe_frame;    /* ... point-edge pairs projected in their own frame (3x3 + 2x2) */
   int64_t n_hess_pe;          /* ... point-edge pairs on the generic 6x6 projection */
+  int64_t n_pair_overflow;    /* last broad phase (ccd_step's, once a pass ran it): entries whose pairs
+                                 went past what the count pass keeps (rods: 32 staged keys; shells: the
+                                 partner bits of the first 512 positions), re-tested by the fill pass */
 } cb_stats;
 
 /* Create a scene: uploads topology and rest positions, derives edges and

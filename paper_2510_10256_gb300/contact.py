@@ -55,7 +55,8 @@ class Stats(C.Structure):
                 ("dhat", C.c_double), ("activation", C.c_double), ("status_bits", C.c_int32),
                 ("ccd_max_iters", C.c_int32), ("device_bytes", C.c_int64),
                 ("n_candidates_fp32", C.c_int64), ("n_fp64_decided", C.c_int64),
-                ("n_hess_face", C.c_int64), ("n_hess_pe_frame", C.c_int64), ("n_hess_pe", C.c_int64)]
+                ("n_hess_face", C.c_int64), ("n_hess_pe_frame", C.c_int64), ("n_hess_pe", C.c_int64),
+                ("n_pair_overflow", C.c_int64)]
 
 
 def build(force: bool = False) -> str:

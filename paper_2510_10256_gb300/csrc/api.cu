@@ -738,6 +738,7 @@ cb_status cb_get_stats(cb_scene* s, cb_stats* o) {
   o->n_hess_face = s->n_hq[0];
   o->n_hess_pe_frame = s->n_hq[1];
   o->n_hess_pe = s->n_hq[2];
+  o->n_pair_overflow = (int64_t)(uint32_t)h[SC_NOVF];
   size_t bytes = 0;
   const DevBuf* all[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->frest,
                          &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls,
