@@ -225,6 +225,41 @@ cb_status cb_bsr_device(cb_scene* scene, const int32_t** row_ptr, const int32_t*
  * Errors: CB_ERR_ARG for a NULL scene / vector, v_dev == y_dev, or a scene
  * with no barrier_eval / barrier_energy yet. */
 cb_status cb_bsr_spmv(cb_scene* scene, const double* v_dev, double* y_dev, double shift, void* stream);
+/* Lagged friction on the active pairs (App. A: the paper's solver uses IPC's
+ * contact and friction energies; this is IPC's lagged friction potential on
+ * the pairs the filtered barrier makes active).
+ *
+ * friction_lag: records, for every active pair of the last barrier_eval
+ * (which must have run at x_lag_dev -- barrier_energy keeps no active list),
+ * the normal force lambda = -kappa b'(d - xi_p; dhat_p) >= 0 with the pair's
+ * own offset and width (Eq. 2-4), the closest-point weights beta[4] of its
+ * distance type (w(v) = sum_a beta_a v_a: first primitive's closest point
+ * minus the second's) and the normal n = w(x_lag) / |w(x_lag)|.  mu >= 0 is
+ * the friction coefficient, eps > 0 the sliding displacement (mm) below
+ * which f0 is smoothed.  Single scenes only (CB_ERR_ARG for a batch).
+ *
+ * friction_eval: ADDS D(x) = sum_k mu lambda_k f0(|(I - n n^T) w(x - x_lag)|)
+ * to energy_dev[0] and, when grad_dev is not NULL, its gradient to grad_dev
+ * ([3][n]) and keeps each pair's 3x3 tangent Hessian (PSD by construction,
+ * no projection) for friction_spmv.  f0(y) = -y^3/(3 eps^2) + y^2/eps +
+ * eps/3 for y < eps, y otherwise.  CB_ERR_ARG before friction_lag.
+ *
+ * friction_spmv: y_dev += H_f v_dev (v_dev, y_dev: DEVICE [3][n], distinct),
+ * H_f the friction Hessian of the last friction_eval with a gradient
+ * (CB_ERR_ARG if there was none).
+ *
+ * cb_get_friction (sync): the lagged pairs in the order of the lists above:
+ * keys [nf]; dat [8][nf] = lambda, beta[4], n[3] (element-major); hw [6][nf]
+ * = packed Hessians (xx xy xz yy yz zz) of the last friction_eval with a
+ * gradient.  Any of the three may be NULL; CB_ERR_CAPACITY if cap < nf.
+ * All pointers of the first three calls are DEVICE pointers read or written
+ * by kernels on `stream`. */
+cb_status friction_lag(cb_scene* scene, const double* x_lag_dev, double mu, double eps, void* stream);
+cb_status friction_eval(cb_scene* scene, const double* x_dev, const double* x_lag_dev, double* energy_dev,
+                        double* grad_dev, void* stream);
+cb_status friction_spmv(cb_scene* scene, const double* v_dev, double* y_dev, void* stream);
+cb_status cb_get_friction(cb_scene* scene, uint64_t* keys, double* dat, double* hw, int64_t cap,
+                          int64_t* count);
 cb_status cb_get_stats(cb_scene* scene, cb_stats* stats);
 /* sync: first device-side condition since the last call (then cleared) */
 cb_status cb_sync_status(cb_scene* scene);

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcontact.so")
-SOURCES = ["api.cu", "broad.cu", "narrow.cu", "ccd.cu", "peaks.cu", "spmv.cu"]
+SOURCES = ["api.cu", "broad.cu", "narrow.cu", "ccd.cu", "peaks.cu", "spmv.cu", "friction.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -32,7 +32,8 @@ ABI_FUNCTIONS = ["cb_scene_create", "cb_scene_destroy", "contact_build", "contac
                  "cb_get_stats", "cb_sync_status", "cb_get_stage_ms", "cb_set_timing", "cb_status_str",
                  "cb_version", "cb_kernel_launches", "cb_measure_fma_tflops", "cb_batch_create",
                  "cb_batch_offsets", "cb_member_count", "ccd_step_noalloc", "cb_set_tuning",
-                 "cb_get_tuning", "barrier_energy", "cb_bsr_spmv"]
+                 "cb_get_tuning", "barrier_energy", "cb_bsr_spmv", "friction_lag", "friction_eval",
+                 "friction_spmv", "cb_get_friction"]
 
 
 class ContactError(RuntimeError):
@@ -90,6 +91,10 @@ def lib():
         L.barrier_eval.argtypes = [vp, vp, vp, vp, vp]
         L.barrier_energy.argtypes = [vp, vp, vp, vp]
         L.cb_bsr_spmv.argtypes = [vp, vp, vp, C.c_double, vp]
+        L.friction_lag.argtypes = [vp, vp, C.c_double, C.c_double, vp]
+        L.friction_eval.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.friction_spmv.argtypes = [vp, vp, vp, vp]
+        L.cb_get_friction.argtypes = [vp, vp, vp, vp, i64, C.POINTER(i64)]
         L.ccd_step.argtypes = [vp, vp, vp, vp, vp]
         L.cb_get_pairs.argtypes = [vp, i32, vp, i64, C.POINTER(i64)]
         L.cb_get_active.argtypes = [vp, vp, vp, vp, vp, i64, C.POINTER(i64)]
@@ -259,6 +264,43 @@ class ContactScene:
         """y = (H + shift I) v with the BSR Hessian of the last barrier_eval."""
         _check(lib().cb_bsr_spmv(self.h, _dev_ptr(v, self.n), _dev_ptr(y, self.n), float(shift),
                                  _stream_ptr(stream)), "cb_bsr_spmv")
+
+    def friction_lag(self, x_lag, mu: float, eps: float, stream=None):
+        """Lagged friction data of the active pairs of the last barrier_eval
+        (which must have run at x_lag)."""
+        _check(lib().friction_lag(self.h, _dev_ptr(x_lag, self.n), float(mu), float(eps), _stream_ptr(stream)),
+               "friction_lag")
+
+    def friction_eval(self, x, x_lag, energy, grad=None, stream=None):
+        """Adds the friction energy to energy[0] and, with grad, its gradient
+        to grad (and keeps the pair Hessians for friction_spmv)."""
+        _check(lib().friction_eval(self.h, _dev_ptr(x, self.n), _dev_ptr(x_lag, self.n),
+                                   _dev_ptr(energy, None, False),
+                                   None if grad is None else _dev_ptr(grad, self.n), _stream_ptr(stream)),
+               "friction_eval")
+
+    def friction_spmv(self, v, y, stream=None):
+        """y += H_f v (friction Hessian of the last friction_eval with a gradient)."""
+        _check(lib().friction_spmv(self.h, _dev_ptr(v, self.n), _dev_ptr(y, self.n), _stream_ptr(stream)),
+               "friction_spmv")
+
+    def friction(self, hessian: bool = True) -> dict:
+        """The lagged pairs: keys, lam, beta (nf, 4), nrm (nf, 3) and, if asked,
+        the packed pair Hessians hw (nf, 6)."""
+        cnt = C.c_int64()
+        _check(lib().cb_get_friction(self.h, None, None, None, 0, C.byref(cnt)), "cb_get_friction")
+        nf = cnt.value
+        keys = np.zeros(nf, np.uint64)
+        dat = np.zeros((8, nf))
+        hw = np.zeros((6, nf)) if hessian else None
+        if nf:
+            _check(lib().cb_get_friction(self.h, keys.ctypes.data, dat.ctypes.data,
+                                         hw.ctypes.data if hessian else None, nf, C.byref(cnt)),
+                   "cb_get_friction")
+        out = dict(keys=keys, lam=dat[0].copy(), beta=dat[1:5].T.copy(), nrm=dat[5:8].T.copy())
+        if hessian:
+            out["hw"] = hw.T.copy()
+        return out
 
     def ccd_step(self, x, p, alpha=None, stream=None):
         _check(lib().ccd_step(self.h, _dev_ptr(x, self.n), _dev_ptr(p, self.n),

@@ -61,7 +61,7 @@ static void scene_release(cb_scene* s) {
                     &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
                     &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col, &s->bsr_val,
                     &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->mp, &s->vsc, &s->macc, &s->hstage, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag, &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist,
-                    &s->dev_scalars};
+                    &s->fr_key, &s->fr_st, &s->fr_dat, &s->fr_hw, &s->dev_scalars};
   for (DevBuf* b : bufs) buf_free(*b, st);
   for (BroadWork* w : {&s->bw, &s->bwc}) {
     DevBuf* wb[] = {&w->grids, &w->cx, &w->box32,   &w->box64,  &w->bounds,   &w->cell_cnt, &w->cell_off, &w->ekey[0], &w->ekey[1],
@@ -744,7 +744,8 @@ cb_status cb_get_stats(cb_scene* s, cb_stats* o) {
                          &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls,
                          &s->aidx, &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col,
                          &s->bsr_val, &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag,
-                         &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist};
+                         &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist, &s->fr_key,
+                         &s->fr_st, &s->fr_dat, &s->fr_hw};
   for (const DevBuf* b : all) bytes += b->bytes;
   for (const BroadWork* w : {&s->bw, &s->bwc}) {
     const DevBuf* wb[] = {&w->box32,    &w->box64,    &w->bounds,    &w->cell_cnt, &w->cell_off, &w->ekey[0],

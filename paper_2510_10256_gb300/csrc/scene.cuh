@@ -138,6 +138,14 @@ struct cb_scene {
   DevBuf ccd_flag, ccd_pos, ccd_list;  // uint32 band selection
   DevBuf ccd_ulist;     // uint32 pairs still unresolved after the first-step pass
   int64_t n_ccd = 0;
+  // lagged friction (friction_lag / friction_eval / friction_spmv)
+  DevBuf fr_key;        // uint64 [nf] keys of the lagged pairs
+  DevBuf fr_st;         // int4 [nf] their stencil vertices
+  DevBuf fr_dat;        // double [8][nf]: lambda, beta[4], n[3] (element-major)
+  DevBuf fr_hw;         // double [6][nf]: packed tangent Hessian (xx xy xz yy yz zz) of the last friction_eval
+  int64_t n_fric = 0;
+  double fr_mu = 0.0, fr_eps = 0.0;
+  bool fr_lagged = false, fr_hw_valid = false;
   DevBuf scan_tmp;
   DevBuf hist;
   DevBuf dev_scalars;   // misc device scalars (counters, energy, alpha bits, status)
