@@ -466,13 +466,149 @@ def bench_serve(args, rank, world, local, dist):
     print(json.dumps(line), flush=True)
 
 
+def bench_friction(args, rank, world, local, dist):
+    """Lagged friction on the pleated sheet: one barrier pass at x, friction_lag
+    there (mu 0.4, eps 1e-3 mm), then per step friction_eval (energy, gradient,
+    pair Hessians) at a displaced state and one friction_spmv.  Metric: lagged
+    pairs per second through both calls."""
+    import numpy as np
+    import torch
+    from paper_2510_10256_gb300 import contact as CT
+    sc, desc = _workload("pleated", reduced_nx=args.nx or None)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    cs = CT.ContactScene.from_scene(sc)
+    x = torch.from_numpy(sc.x).to(dev)
+    energy = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad = torch.zeros(3, sc.n, dtype=torch.float64, device=dev)
+    cs.contact_build(x)
+    cs.contact_filter()
+    cs.barrier_eval(x, energy, grad)
+    mu, eps = 0.4, 1e-3
+    cs.friction_lag(x, mu, eps)
+    rng = np.random.default_rng(23)
+    x1 = torch.from_numpy(sc.x + rng.normal(0.0, eps, size=sc.x.shape)).to(dev)
+    v = torch.from_numpy(rng.normal(size=sc.x.shape)).to(dev)
+    y = torch.zeros_like(v)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    fe = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def step():
+        fe.zero_()
+        grad.zero_()
+        y.zero_()
+        cs.friction_eval(x1, x, fe, grad)
+        cs.friction_spmv(v, y)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    nf = int(cs.friction(hessian=False)["keys"].size)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = CT.kernel_launches()
+    for k in range(args.steps):
+        flush.zero_()
+        fe.zero_()
+        grad.zero_()
+        y.zero_()
+        ev[k][0].record(stream)
+        cs.friction_eval(x1, x, fe, grad)
+        ev[k][1].record(stream)
+        cs.friction_spmv(v, y)
+        ev[k][2].record(stream)
+    torch.cuda.synchronize()
+    launches = CT.kernel_launches() - l0
+    clk = clocks.stop()
+    eval_ms = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
+    spmv_ms = statistics.mean(b.elapsed_time(c) for _, b, c in ev)
+    ms = max_over_ranks([eval_ms + spmv_ms], dist, dev)[0]
+    # end to end: displaced state from pinned host memory, energy and gradient back
+    hx = torch.from_numpy(x1.cpu().numpy()).pin_memory()
+    he = torch.zeros(1, dtype=torch.float64).pin_memory()
+    hg = torch.zeros(3, sc.n, dtype=torch.float64).pin_memory()
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(max(3, args.steps // 2))]
+    for a, b in e_ev:
+        flush.zero_()
+        a.record(stream)
+        x1.copy_(hx, non_blocking=True)
+        fe.zero_()
+        grad.zero_()
+        y.zero_()
+        cs.friction_eval(x1, x, fe, grad)
+        cs.friction_spmv(v, y)
+        he.copy_(fe, non_blocking=True)
+        hg.copy_(grad, non_blocking=True)
+        b.record(stream)
+        stream.synchronize()
+    e2e_ms = max_over_ranks([statistics.mean(a.elapsed_time(b) for a, b in e_ev)], dist, dev)[0]
+    status = cs.sync_status()
+    cs.close()
+    if rank != 0:
+        return
+    # friction_eval's algorithmic bytes: per pair the stencil (16 B), lagged
+    # data (64 B) and packed Hessian written (48 B); per vertex x and x_lag
+    # read (48 B) and the gradient read and written (48 B)
+    bytes_eval = nf * (16 + 64 + 48) + sc.n * (48 + 48)
+    hbm = _peaks().get("hbm_gbs") or 6800.0
+    achieved = bytes_eval / (eval_ms / 1000.0) / 1e9
+    line = {"metric": "lagged friction pairs per second (friction_eval + friction_spmv)",
+            "value": world * nf / (ms / 1000.0), "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"lagged friction on the {desc} (mu {mu}, eps {eps} mm, displaced by N(0, eps))",
+                       "friction_pairs": nf, "l2": "flushed (256 MiB write) between steps",
+                       "parallelism": f"replicas x{world}"},
+            "stage_ms": {"friction_eval": eval_ms, "friction_spmv": spmv_ms},
+            "roofline": {"bound": "hbm", "kernel": "k_fric_eval", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "algorithmic_bytes": bytes_eval, "kernel_ms": eval_ms,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)"},
+            "e2e": {"value": world * nf / (e2e_ms / 1000.0), "unit": "pairs/s",
+                    "h2d_bytes_per_step": 3 * sc.n * 8, "d2h_bytes_per_step": 8 + 3 * sc.n * 8,
+                    "ms_per_step": e2e_ms},
+            "clocks": clk, "gpu_launches": int(launches), "status": status}
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            line["cpu_baseline"] = _friction_cpu_baseline(args.cpu_nx)
+        except Exception as e:
+            line["cpu_baseline"] = {"value": None, "error": str(e)}
+    print(json.dumps(line), flush=True)
+
+
+def _friction_cpu_baseline(nx: int) -> dict:
+    """The friction oracle (lag + one evaluation) on a smaller pleated sheet."""
+    import numpy as np
+    import oracle as O
+    import oracle.friction as Fr
+    from paper_2510_10256_gb300 import scenes as S
+    nx = min(nx, 48)
+    sc = S.pleated_sheet(nx=nx)
+    res = O.contact_pass(sc, ccd=False)
+    L = Fr.lag(sc, res, sc.x, 0.4, 1e-3)
+    rng = np.random.default_rng(23)
+    x1 = sc.x + rng.normal(0.0, 1e-3, size=sc.x.shape)
+    t0 = time.perf_counter()
+    ev = Fr.evaluate(L, x1, sc.x)
+    Fr.hessian_matvec(L, ev.Hw, rng.normal(size=sc.x.shape))
+    dt = time.perf_counter() - t0
+    return {"value": L.keys.size / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"friction oracle evaluate + Hessian product on the pleated recipe at {nx}x{nx} "
+                      f"({L.keys.size} lagged pairs, {dt:.2f} s), one Python thread"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="pleated", choices=["pleated", "woven", "graded", "knit64", "serve"])
+    ap.add_argument("--workload", default="pleated",
+                    choices=["pleated", "woven", "graded", "knit64", "serve", "friction"])
     ap.add_argument("--requests", type=int, default=1000, help="serve: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (requests/s)")
     ap.add_argument("--req-steps", type=int, default=10, help="serve: contact steps per request")
@@ -513,6 +649,9 @@ def main():
         return
     if args.workload == "serve":
         bench_serve(args, rank, world, local, dist)
+        return
+    if args.workload == "friction":
+        bench_friction(args, rank, world, local, dist)
         return
     sc, desc = _workload(args.workload, reduced_nx=args.nx or None)
     dev = torch.device("cuda", local)
