@@ -162,6 +162,7 @@ class Topology:
     tris: np.ndarray          # int32 (3, T) (empty for rods)
     comp: np.ndarray          # int32 (n,) component label per vertex
     _keep: list = field(default_factory=list)
+    loop_ne: np.ndarray | None = None   # rods: per edge, the edge count of its closed loop (0: open polyline)
 
     def ctype(self) -> _Topo:
         e = np.ascontiguousarray(self.edges, np.int32)
@@ -178,13 +179,26 @@ def topology(scene) -> Topology:
     n = scene.n
     if scene.kind == "rod":
         rp = np.asarray(scene.rod_ptr, np.int64)
-        e0 = np.concatenate([np.arange(rp[r], rp[r + 1] - 1) for r in range(rp.size - 1)]
-                            + [np.zeros(0, np.int64)])
-        edges = np.stack([e0, e0 + 1]).astype(np.int32)
+        closed = scene.rod_closed if getattr(scene, "rod_closed", None) is not None else np.zeros(rp.size - 1)
+        e0, e1, lne = [], [], []
+        for r in range(rp.size - 1):
+            v = np.arange(rp[r], rp[r + 1] - 1)
+            a, b = [v], [v + 1]
+            ne = v.size
+            if closed[r]:
+                # closed loop: the edge from the last vertex back to the first, after the others
+                a.append(np.array([rp[r + 1] - 1]))
+                b.append(np.array([rp[r]]))
+                ne += 1
+            e0 += a
+            e1 += b
+            lne.append(np.full(ne, ne if closed[r] else 0))
+        cat = lambda xs: np.concatenate(xs + [np.zeros(0, np.int64)])
+        edges = np.stack([cat(e0), cat(e1)]).astype(np.int32)
         comp = np.zeros(n, np.int32)
         for r in range(rp.size - 1):
             comp[rp[r]:rp[r + 1]] = r
-        return Topology(0, n, edges, np.zeros((3, 0), np.int32), comp)
+        return Topology(0, n, edges, np.zeros((3, 0), np.int32), comp, loop_ne=cat(lne).astype(np.int64))
     tris = np.asarray(scene.tris, np.int64)
     a = np.concatenate([tris[0], tris[1], tris[2]])
     b = np.concatenate([tris[1], tris[2], tris[0]])
@@ -264,12 +278,56 @@ def arclength(scene) -> np.ndarray:
 
 def rest_filter(scene, topo: Topology, a: float) -> tuple[np.ndarray, np.ndarray]:
     """Filtered stencil pairs (same component, dbar < a) and their dbar."""
+    if topo.kind == 0 and topo.loop_ne is not None and np.any(topo.loop_ne > 0):
+        return _rod_rest_filter_loops(scene, topo, a)
     tc = topo.ctype()
     rest = np.ascontiguousarray(scene.rest, np.float64)
     S = arclength(scene) if topo.kind == 0 else np.zeros(1)
     ok, od = C.c_void_p(), C.c_void_p()
     m = lib().orc_rest_filter(C.byref(tc), _ptr(rest), float(a), _ptr(S), C.byref(ok), C.byref(od))
     return _take(ok, m, np.uint64), _take(od, m, np.float64)
+
+
+def _rod_rest_filter_loops(scene, topo: Topology, a: float) -> tuple[np.ndarray, np.ndarray]:
+    """Rod rest filter for scenes with closed loops, pair by pair within each
+    polyline.  An edge runs from arc length s0 to s1 along its polyline (S at
+    its vertices; a loop's closing edge ends at the loop length L = S at the
+    last vertex plus the closing edge's length).  The reference distance of
+    two non-incident edges k < l of one polyline is the arc-length gap
+    between them, s0(l) - s1(k); on a closed loop the shorter way round,
+    min(s0(l) - s1(k), (L - s1(l)) + s0(k))."""
+    S = arclength(scene)
+    rest = np.asarray(scene.rest, np.float64)
+    e0, e1 = topo.edges[0].astype(np.int64), topo.edges[1].astype(np.int64)
+    E = e0.size
+    keys, dbs = [], []
+    start = 0
+    while start < E:
+        r = topo.comp[e0[start]]
+        stop = start
+        while stop < E and topo.comp[e0[stop]] == r:
+            stop += 1
+        idx = np.arange(start, stop)
+        s0 = S[e0[idx]]
+        closing = e1[idx] < e0[idx]
+        dv = rest[:, e1[idx]] - rest[:, e0[idx]]
+        ln = np.sqrt((dv[0] * dv[0] + dv[1] * dv[1]) + dv[2] * dv[2])
+        s1 = np.where(closing, s0 + ln, S[np.where(closing, e0[idx], e1[idx])])
+        L = s1[closing][0] if closing.any() else None
+        k, l = np.triu_indices(idx.size, 1)
+        inc = ((e0[idx][k] == e0[idx][l]) | (e0[idx][k] == e1[idx][l]) | (e1[idx][k] == e0[idx][l])
+               | (e1[idx][k] == e1[idx][l]))
+        g = s0[l] - s1[k]
+        if L is not None:
+            g = np.minimum(g, (L - s1[l]) + s0[k])
+        keep = (~inc) & (g < a)
+        keys.append((idx[k][keep].astype(np.uint64) << np.uint64(31)) | idx[l][keep].astype(np.uint64))
+        dbs.append(g[keep])
+        start = stop
+    K = np.concatenate(keys + [np.zeros(0, np.uint64)])
+    D = np.concatenate(dbs + [np.zeros(0)])
+    o = np.argsort(K)
+    return K[o], D[o]
 
 
 MODES = ("double", "single", "off", "kaldor")
@@ -289,13 +347,18 @@ def kaldor_culled(topo: Topology, keys: np.ndarray, radius: int) -> np.ndarray:
     """Kaldor et al.'s culling, the comparison the paper runs against its
     filter (the knot test, Fig. 8): rod edge pairs of one polyline at most
     `radius` edges apart are removed from contact.  Edges are numbered
-    consecutively along each polyline, so the gap is j - i."""
+    consecutively along each polyline, so the gap is j - i (on a closed loop
+    of m edges, min(j - i, m - (j - i)))."""
     keys = np.asarray(keys, np.uint64)
     i = ((keys >> np.uint64(31)) & np.uint64(0x7FFFFFFF)).astype(np.int64)
     j = (keys & np.uint64(0x7FFFFFFF)).astype(np.int64)
     e0 = topo.edges[0].astype(np.int64)
     same = topo.comp[e0[i]] == topo.comp[e0[j]]
-    return same & (j - i <= radius)
+    gap = j - i
+    if topo.loop_ne is not None:
+        ne = topo.loop_ne[i]
+        gap = np.where(ne > 0, np.minimum(gap, ne - gap), gap)   # closed loop: the shorter way round
+    return same & (gap <= radius)
 
 
 @dataclass

@@ -41,6 +41,7 @@ class Scene:
     name: str = ""
     seed: int = 0
     meta: dict = field(default_factory=dict)
+    rod_closed: np.ndarray | None = None  # uint8 (n_rods,) for rods: 1 = closed loop (last vertex joins the first)
 
     @property
     def n(self) -> int:
@@ -455,6 +456,56 @@ def tiny_rods(seed: int, n_rods: int = 3, nseg: int = 12, seg: float = 0.1,
     pos = _soa(pos)
     return Scene("rod", pos.copy(), pos.copy(), _soa(p), thickness, dhat, rod_ptr=rod_ptr,
                  name="tiny_rods", seed=seed)
+
+
+def polygon_loop(m: int, R: float = 1.0, closed: bool = True, thickness: float = 0.3,
+                 dhat: float = 0.05) -> Scene:
+    """One regular m-gon of circumradius R in the xy-plane (a closed yarn
+    loop, or the same vertices as an open polyline)."""
+    th = 2.0 * math.pi * np.arange(m) / m
+    x = np.stack([R * np.cos(th), R * np.sin(th), np.zeros(m)])
+    return Scene("rod", x.copy(), x.copy(), np.zeros_like(x), thickness, dhat,
+                 rod_ptr=np.array([0, m], np.int32), name=f"polygon{m}{'' if closed else '_open'}",
+                 rod_closed=np.array([1 if closed else 0], np.uint8))
+
+
+def ring_chain(seed: int = BASE_SEED + 7, n_rings: int = 3, m: int = 48, R: float = 1.0,
+               thickness: float = 0.3, dhat: float = 0.05, sigma: float = 0.15) -> Scene:
+    """Interlocked closed rings (a chain: ring i in the xy-plane for even i,
+    the xz-plane for odd i, centres along x).  Rest: centres 1.6 R apart.
+    Current positions: the rings pulled apart (each translated along x)
+    until neighbouring rings' vertices come within thickness + 0.6 dhat,
+    plus a little noise; p: Gaussian."""
+    rng = np.random.default_rng(seed)
+
+    def ring(i, spacing):
+        th = 2.0 * math.pi * np.arange(m) / m + 0.37 * i
+        c, s_ = R * np.cos(th), R * np.sin(th)
+        z = np.zeros(m)
+        pts = np.stack([c, s_, z]) if i % 2 == 0 else np.stack([c, z, s_])
+        pts[0] += i * spacing
+        return pts
+
+    def min_gap(spacing):
+        a, b = ring(0, spacing), ring(1, spacing)
+        d = a[:, :, None] - b[:, None, :]
+        return float(np.sqrt((d * d).sum(0)).min())
+
+    target = thickness + 0.6 * dhat
+    lo, hi = 1.6 * R, 2.0 * R   # linked rings: the gap shrinks as they are pulled apart
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if min_gap(mid) > target:
+            lo = mid
+        else:
+            hi = mid
+    rest = np.concatenate([ring(i, 1.6 * R) for i in range(n_rings)], axis=1)
+    x = np.concatenate([ring(i, lo) for i in range(n_rings)], axis=1)
+    x = x + rng.normal(0.0, 0.01 * dhat, size=x.shape)
+    p = rng.normal(0.0, sigma, size=x.shape)
+    rp = np.arange(0, (n_rings + 1) * m, m, dtype=np.int32)
+    return Scene("rod", rest, x, p, thickness, dhat, rod_ptr=rp, name=f"ring_chain{n_rings}x{m}", seed=seed,
+                 rod_closed=np.ones(n_rings, np.uint8))
 
 
 # ---------------------------------------------------------------------------
