@@ -30,7 +30,8 @@
  *   type 0 rod edge-edge     i < j edge ids
  *   type 1 shell point-tri   i = vertex id, j = triangle id
  *   type 2 shell edge-edge   i < j edge ids
- * Edge ids: rods -- edges (v, v+1) of each polyline in order; shells -- the
+ * Edge ids: rods -- edges (v, v+1) of each polyline in order (a closed loop's
+ * closing edge (last, first) after them); shells -- the
  * unique (min, max) vertex pairs of the triangles in lexicographic order.
  * Pair lists are returned sorted by key.
  */
@@ -99,6 +100,10 @@ typedef struct {
   double kappa;               /* barrier stiffness (energy scale); 1 if <= 0 */
   int32_t mode;               /* CB_FILTER_* | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP | CB_DBAR_PER_COMPONENT */
   int32_t cull_radius;        /* CB_FILTER_KALDOR: culling radius in edges (>= 1); else ignored */
+  const uint8_t* rod_closed;  /* rods, HOST [n_rods] or NULL: 1 = closed loop (an edge from the last vertex
+                                 back to the first, numbered after the polyline's others; >= 3 vertices,
+                                 else CB_ERR_ARG).  Its reference distances take the shorter way round the
+                                 loop, Kaldor gaps too.  NULL: every polyline open. */
 } cb_scene_desc;
 
 typedef struct {

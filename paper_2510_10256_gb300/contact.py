@@ -46,7 +46,8 @@ class SceneDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_verts", C.c_int32), ("rest_xyz", C.c_void_p),
                 ("n_rods", C.c_int32), ("rod_ptr", C.c_void_p), ("n_tris", C.c_int32),
                 ("tris", C.c_void_p), ("thickness", C.c_double), ("dhat", C.c_double),
-                ("kappa", C.c_double), ("mode", C.c_int32), ("cull_radius", C.c_int32)]
+                ("kappa", C.c_double), ("mode", C.c_int32), ("cull_radius", C.c_int32),
+                ("rod_closed", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -187,7 +188,8 @@ class ContactScene:
 
     def __init__(self, kind: str, rest, thickness: float, dhat: float, rod_ptr=None, tris=None,
                  kappa: float = 1.0, mode: str = "double", paper_literal: bool = False,
-                 core_temp: bool = True, cull_radius: int = 0, per_component: bool = False, stream=None):
+                 core_temp: bool = True, cull_radius: int = 0, per_component: bool = False, rod_closed=None,
+                 stream=None):
         L = lib()
         rest = np.ascontiguousarray(np.asarray(rest, np.float64).reshape(3, -1))
         self.n = rest.shape[1]
@@ -201,6 +203,12 @@ class ContactScene:
             self._keep.append(rp)
             d.n_rods = rp.size - 1
             d.rod_ptr = rp.ctypes.data
+            if rod_closed is not None:
+                rc = np.ascontiguousarray(np.asarray(rod_closed, np.uint8).reshape(-1))
+                if rc.size != d.n_rods:
+                    raise ValueError("rod_closed: one flag per polyline")
+                self._keep.append(rc)
+                d.rod_closed = rc.ctypes.data
         else:
             tr = np.ascontiguousarray(np.asarray(tris, np.int32).reshape(3, -1))
             self._keep.append(tr)
@@ -230,7 +238,7 @@ class ContactScene:
     @classmethod
     def from_scene(cls, sc, mode: str = "double", **kw) -> "ContactScene":
         return cls(sc.kind, sc.rest, sc.thickness, sc.dhat, rod_ptr=sc.rod_ptr, tris=sc.tris,
-                   kappa=sc.kappa, mode=mode, **kw)
+                   kappa=sc.kappa, mode=mode, rod_closed=getattr(sc, "rod_closed", None), **kw)
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:

@@ -57,7 +57,8 @@ static cb_status upload(DevBuf& b, const T* h, size_t count, cudaStream_t st) {
 
 static void scene_release(cb_scene* s) {
   cudaStream_t st = s->last_stream;
-  DevBuf* bufs[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->frest,
+  DevBuf* bufs[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->wst,
+                    &s->rloop, &s->rlast, &s->frest,
                     &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
                     &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col, &s->bsr_val,
                     &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->mp, &s->vsc, &s->macc, &s->hstage, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag, &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist,
@@ -81,6 +82,12 @@ static void scene_release(cb_scene* s) {
 __global__ void k_offset_copy(int32_t* __restrict__ dst, const int32_t* __restrict__ src, int64_t n, int32_t add) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = src[i] + add;
+}
+// as k_offset_copy, negative entries (markers) copied unchanged
+__global__ void k_offset_copy_nonneg(int32_t* __restrict__ dst, const int32_t* __restrict__ src, int64_t n,
+                                     int32_t add) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i] >= 0 ? src[i] + add : src[i];
 }
 __global__ void k_comp_copy(int32_t* __restrict__ dst, const int32_t* __restrict__ src, int64_t n, int32_t add_lbl,
                             int32_t add_v) {
@@ -181,7 +188,7 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
   if (fm == CB_FILTER_KALDOR && (d->kind != CB_ROD || d->cull_radius < 1)) return CB_ERR_ARG;
   const int n = d->n_verts;
   cudaStream_t st = (cudaStream_t)stream;
-  std::vector<int32_t> e0, e1, comp(n);
+  std::vector<int32_t> e0, e1, comp(n), rloop, rlast;
   std::vector<int32_t> tris;
   int T = 0;
   if (d->kind == CB_ROD) {
@@ -190,10 +197,23 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
       if (d->rod_ptr[r] < 0 || d->rod_ptr[r + 1] < d->rod_ptr[r] || d->rod_ptr[r + 1] > n) return CB_ERR_ARG;
     for (int v = 0; v < n; ++v) comp[v] = -1 - v;
     for (int r = 0; r < d->n_rods; ++r) {
-      for (int v = d->rod_ptr[r]; v < d->rod_ptr[r + 1]; ++v) comp[v] = r;
-      for (int v = d->rod_ptr[r]; v + 1 < d->rod_ptr[r + 1]; ++v) {
+      const int p0 = d->rod_ptr[r], p1 = d->rod_ptr[r + 1];
+      const bool closed = d->rod_closed && d->rod_closed[r];
+      if (closed && p1 - p0 < 3) return CB_ERR_ARG;  // a loop needs three vertices
+      for (int v = p0; v < p1; ++v) comp[v] = r;
+      const int first = (int)e0.size();
+      for (int v = p0; v + 1 < p1; ++v) {
         e0.push_back(v);
         e1.push_back(v + 1);
+      }
+      if (closed) {  // the closing edge, after the polyline's others
+        e0.push_back(p1 - 1);
+        e1.push_back(p0);
+      }
+      const int ne = (int)e0.size() - first;
+      for (int k = 0; k < ne; ++k) {
+        rloop.push_back(closed ? ne : 0);
+        rlast.push_back(closed ? first + ne - 1 : -1);
       }
     }
   } else {
@@ -272,6 +292,8 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
                                 (fm == CB_FILTER_OFF || fm == CB_FILTER_KALDOR) ? 1 : 0, s->n_prims});
   s->hmp[0].cull_radius = fm == CB_FILTER_KALDOR ? d->cull_radius : 0;
   s->hmp[0].per_comp = (d->mode & CB_DBAR_PER_COMPONENT) ? 1 : 0;
+  s->hmp[0].loops = 0;
+  for (int32_t lc : rloop) s->hmp[0].loops |= lc > 0 ? 1 : 0;
   s->voff = {0, (int64_t)n};
   s->eoff = {0, (int64_t)E};
   s->toff = {0, (int64_t)T};
@@ -292,8 +314,12 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
   if ((rc = upload(s->comp, comp.data(), comp.size(), st)) != CB_OK) return fail(rc);
   if ((rc = upload(s->rest, d->rest_xyz, 3 * (size_t)n, st)) != CB_OK) return fail(rc);
   if (d->kind == CB_ROD && (rc = upload(s->rod_ptr, d->rod_ptr, (size_t)d->n_rods + 1, st)) != CB_OK) return fail(rc);
+  if (d->kind == CB_ROD && (rc = upload(s->rloop, rloop.data(), rloop.size(), st)) != CB_OK) return fail(rc);
+  if (d->kind == CB_ROD && (rc = upload(s->rlast, rlast.data(), rlast.size(), st)) != CB_OK) return fail(rc);
   if (d->kind == CB_ROD && (rc = buf_ensure(s->frest, 16, st)) != CB_OK) return fail(rc);
   if (d->kind == CB_SHELL && (rc = buf_ensure(s->win, 16, st)) != CB_OK) return fail(rc);
+  if (d->kind == CB_SHELL && (rc = buf_ensure(s->wst, 16, st)) != CB_OK) return fail(rc);
+  if (d->kind == CB_SHELL && (rc = buf_ensure(s->rloop, 16, st)) != CB_OK) return fail(rc);
   for (auto& e : s->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(CB_ERR_CUDA);
   if ((rc = filter_precompute(s, st)) != CB_OK) return fail(rc);
@@ -385,6 +411,8 @@ cb_status cb_batch_create(cb_scene* const* members, int32_t count, void* stream,
   if ((rc = buf_ensure(b->comp, sizeof(int32_t) * (size_t)b->n, st)) != CB_OK) return fail(rc);
   if ((rc = buf_ensure(b->vsc, sizeof(int32_t) * (size_t)b->n, st)) != CB_OK) return fail(rc);
   if ((rc = buf_ensure(b->win, sizeof(int32_t) * (size_t)std::max(1, b->E), st)) != CB_OK) return fail(rc);
+  if ((rc = buf_ensure(b->wst, sizeof(int32_t) * (size_t)std::max(1, b->E), st)) != CB_OK) return fail(rc);
+  if ((rc = buf_ensure(b->rloop, sizeof(int32_t) * (size_t)std::max(1, b->E), st)) != CB_OK) return fail(rc);
   if ((rc = buf_ensure(b->frest, sizeof(uint64_t) * (size_t)std::max<int64_t>(1, nf), st)) != CB_OK) return fail(rc);
   int64_t wpt = 0, wee = nf_pt;
   for (int m = 0; m < count; ++m) {
@@ -395,9 +423,15 @@ cb_status cb_batch_create(cb_scene* const* members, int32_t count, void* stream,
                                                                      s->E, vo);
       k_offset_copy<<<cb_grid(s->E), CB_THREADS, 0, cb_count(st)>>>(bp<int32_t>(b->ev1) + eo, bp<int32_t>(s->ev1),
                                                                      s->E, vo);
-      if (b->kind == CB_ROD)
+      if (b->kind == CB_ROD) {
         k_offset_copy<<<cb_grid(s->E), CB_THREADS, 0, cb_count(st)>>>(bp<int32_t>(b->win) + eo,
                                                                        bp<int32_t>(s->win), s->E, eo);
+        // wst: -1 (no backward window) stays -1; rloop: counts, no offset
+        k_offset_copy_nonneg<<<cb_grid(s->E), CB_THREADS, 0, cb_count(st)>>>(bp<int32_t>(b->wst) + eo,
+                                                                              bp<int32_t>(s->wst), s->E, eo);
+        k_offset_copy<<<cb_grid(s->E), CB_THREADS, 0, cb_count(st)>>>(bp<int32_t>(b->rloop) + eo,
+                                                                       bp<int32_t>(s->rloop), s->E, 0);
+      }
     }
     for (int k = 0; k < 3 && s->T > 0; ++k)
       k_offset_copy<<<cb_grid(s->T), CB_THREADS, 0, cb_count(st)>>>(
@@ -740,7 +774,8 @@ cb_status cb_get_stats(cb_scene* s, cb_stats* o) {
   o->n_hess_pe = s->n_hq[2];
   o->n_pair_overflow = (int64_t)(uint32_t)h[SC_NOVF];
   size_t bytes = 0;
-  const DevBuf* all[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->frest,
+  const DevBuf* all[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->wst,
+                         &s->rloop, &s->rlast, &s->frest,
                          &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls,
                          &s->aidx, &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col,
                          &s->bsr_val, &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag,

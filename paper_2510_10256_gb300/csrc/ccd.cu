@@ -49,6 +49,8 @@ struct CcdArgs {
   const int32_t* __restrict__ tv;
   const int32_t* __restrict__ comp;
   const int32_t* __restrict__ win;
+  const int32_t* __restrict__ wst;
+  const int32_t* __restrict__ rloop;
   const uint64_t* __restrict__ frest;  // sorted rest-filtered keys
   const uint32_t* __restrict__ frow_pt;  // ... their row offsets by vertex and by edge (frest.cuh)
   const uint32_t* __restrict__ frow_ee;
@@ -86,7 +88,7 @@ __device__ __forceinline__ d3 axpy3(d3 x, double t, d3 p) {
 __device__ __forceinline__ bool is_filtered(const CcdArgs& A, const MemberParams& M, uint64_t key, uint32_t ki,
                                             uint32_t kj) {
   if (M.filter_off) return false;
-  if (A.kind == CB_ROD) return A.comp[A.ev0[ki]] == A.comp[A.ev0[kj]] && (int)kj <= A.win[ki];
+  if (A.kind == CB_ROD) return A.comp[A.ev0[ki]] == A.comp[A.ev0[kj]] && rod_filtered(A.win, A.wst, M.loops != 0, ki, kj);
   if (A.nf <= 0) return false;
   return frest_contains(A.frest, A.frow_pt, A.frow_ee, key);
 }
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restric
     // Kaldor culling (rods: edges numbered along each polyline): the pair
     // does not constrain the step
     const bool culled = M.cull_radius > 0 && A.comp[A.ev0[ki]] == A.comp[A.ev0[kj]] &&
-                        (int)(kj - ki) <= M.cull_radius;
+                        rod_gap(A.rloop, ki, kj) <= M.cull_radius;
     if (culled) {
       A.t_out[q] = 1.0;
       A.cls_out[q] = (uint8_t)3 | EXACT;
@@ -442,6 +444,8 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     A.tv = bp<int32_t>(s->tv);
     A.comp = bp<int32_t>(s->comp);
     A.win = bp<int32_t>(s->win);
+    A.wst = bp<int32_t>(s->wst);
+    A.rloop = bp<int32_t>(s->rloop);
     A.frest = bp<uint64_t>(s->frest);
     A.frow_pt = bp<uint32_t>(s->frow_pt);
     A.frow_ee = bp<uint32_t>(s->frow_ee);

@@ -1,5 +1,6 @@
-// frest.cuh -- membership in the rest-filter table (Sec. 3.2: a candidate is
-// filtered iff its stencil is in the table built at scene creation).  The
+// frest.cuh -- filter membership (Sec. 3.2).  Shells: a candidate is
+// filtered iff its stencil is in the rest-filter table built at scene
+// creation.  Rods: through the per-edge arc-length windows (below).  The shell
 // table is sorted by key (type, i, j), so the keys with one first primitive i
 // form a contiguous row; per-row offsets (by vertex for point-triangle keys,
 // by edge for edge-edge keys) bound the search to that row, a few dozen keys
@@ -22,4 +23,23 @@ __device__ __forceinline__ bool frest_contains(const uint64_t* __restrict__ fres
     else hi = mid;
   }
   return lo < end && frest[lo] == key;
+}
+
+// Rods: edges ki < kj of one polyline are filtered when kj is within the
+// forward window of ki (kj <= win[ki]) or, on a closed loop, within its
+// backward window (kj >= wst[ki] >= 0: the gap the other way round is below
+// the activation).  loops: the member has closed loops (else wst is not read).
+__device__ __forceinline__ bool rod_filtered(const int32_t* __restrict__ win, const int32_t* __restrict__ wst,
+                                             bool loops, uint32_t ki, uint32_t kj) {
+  if ((int)kj <= win[ki]) return true;
+  if (!loops) return false;
+  const int w = wst[ki];
+  return w >= 0 && (int)kj >= w;
+}
+
+// Rods: the index gap of edges ki < kj of one polyline (Kaldor culling);
+// on a closed loop of m edges the shorter way round
+__device__ __forceinline__ int rod_gap(const int32_t* __restrict__ rloop, uint32_t ki, uint32_t kj) {
+  const int g = (int)(kj - ki), m = rloop[ki];
+  return m > 0 ? min(g, m - g) : g;
 }

@@ -32,29 +32,70 @@ __global__ void k_arclength(int n_rods, const int32_t* __restrict__ rod_ptr, con
   }
 }
 
-// rods: for edge k the last edge l of the same polyline with S[l0] - S[k1] < a
-// (the reference arc-length gap between the edges); the gap grows with l.
+// rods: for edge k the last edge l of the same polyline with arc-length gap
+// s0(l) - s1(k) < a (the reference distance between the edges; it grows with
+// l), win[k]; on a closed loop also the first edge l past that window whose
+// gap the other way round, (L - s1(l)) + s0(k), is below a (it shrinks as l
+// grows), wst[k] (-1 if none).  An edge spans arc lengths s0 = S[v0] to s1 =
+// S[v1], the closing edge of a loop from S at the last vertex to the loop
+// length L.  The reference distance of a pair is the smaller gap; incident
+// pairs (a shared vertex) are skipped.
+__device__ __forceinline__ double edge_len(const double* __restrict__ rest, int n, int a, int b) {
+  const double dx = xsub(rest[b], rest[a]);
+  const double dy = xsub(rest[(size_t)n + b], rest[(size_t)n + a]);
+  const double dz = xsub(rest[2 * (size_t)n + b], rest[2 * (size_t)n + a]);
+  return __dsqrt_rn(xadd(xadd(xmul(dx, dx), xmul(dy, dy)), xmul(dz, dz)));
+}
+
 __global__ void k_rod_window(int E, const int32_t* __restrict__ ev0, const int32_t* __restrict__ ev1,
-                             const int32_t* __restrict__ comp, const double* __restrict__ S, double a,
-                             int32_t* __restrict__ win, unsigned long long* __restrict__ dmin_bits,
-                             unsigned long long* __restrict__ nfilt, unsigned long long* __restrict__ dmin_comp) {
+                             const int32_t* __restrict__ comp, const double* __restrict__ S,
+                             const double* __restrict__ rest, int n, const int32_t* __restrict__ rlast, double a,
+                             int32_t* __restrict__ win, int32_t* __restrict__ wst,
+                             unsigned long long* __restrict__ dmin_bits, unsigned long long* __restrict__ nfilt,
+                             unsigned long long* __restrict__ dmin_comp) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= E) return;
-  const int k1 = ev1[k];
+  const int k0 = ev0[k], k1 = ev1[k];
+  const int rl = rlast[k];
+  const double s0k = S[k0];
+  const double s1k = k1 > k0 ? S[k1] : xadd(S[k0], edge_len(rest, n, k0, k1));
+  // closed loop: its length, and the gap the other way round to edge l
+  const bool loop = rl >= 0 && k < rl;
+  const double L = loop ? xadd(S[ev0[rl]], edge_len(rest, n, ev0[rl], ev1[rl])) : 0.0;
+  auto back_gap = [&](int l) {
+    const double s1l = l == rl ? L : S[ev1[l]];
+    return xadd(xsub(L, s1l), s0k);
+  };
+  auto incident = [&](int l) {
+    const int l0 = ev0[l], l1 = ev1[l];
+    return l0 == k0 || l0 == k1 || l1 == k0 || l1 == k1;
+  };
   int last = k + 1;
   double mn = INFINITY;
   unsigned long long cnt = 0;
   for (int l = k + 1; l < E; ++l) {
     const int l0 = ev0[l];
     if (comp[l0] != comp[k1]) break;
-    if (l0 <= k1) continue;
-    const double dbar = xsub(S[l0], S[k1]);
+    if (incident(l)) continue;
+    const double dbar = xsub(S[l0], s1k);
     if (!(dbar < a)) break;
     last = l;
-    mn = fmin(mn, dbar);
+    mn = fmin(mn, loop ? fmin(dbar, back_gap(l)) : dbar);
     ++cnt;
   }
   win[k] = last;
+  int first = -1;
+  if (loop) {
+    for (int l = rl; l > last && l > k; --l) {
+      if (incident(l)) continue;
+      const double g = back_gap(l);
+      if (!(g < a)) break;
+      first = l;
+      mn = fmin(mn, g);
+      ++cnt;
+    }
+  }
+  wst[k] = first;
   if (cnt) {
     atomicMin(dmin_bits, (unsigned long long)__double_as_longlong(mn));
     atomicMin(&dmin_comp[comp[k1]], (unsigned long long)__double_as_longlong(mn));
@@ -98,19 +139,21 @@ __global__ void k_rest_filter(int64_t nc, const uint64_t* __restrict__ keys, con
 
 __global__ void k_filter_rod(int64_t nc, const uint64_t* __restrict__ cand, const int32_t* __restrict__ ev0,
                              const int32_t* __restrict__ comp, const int32_t* __restrict__ win,
+                             const int32_t* __restrict__ wst, const int32_t* __restrict__ rloop,
                              const int32_t* __restrict__ vsc, const MemberParams* __restrict__ mp,
                              uint8_t* __restrict__ klass, unsigned long long* __restrict__ nfilt) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t f = 0;
   if (c < nc) {
     const uint64_t key = cand[c];
-    const int k = (int)cb_key_i(key), l = (int)cb_key_j(key);
+    const uint32_t k = cb_key_i(key), l = cb_key_j(key);
     const int v0 = ev0[k];
     const MemberParams& M = mp[vsc[v0]];
     const bool same = comp[v0] == comp[ev0[l]];
-    f = (!M.filter_off && same && l <= win[k]) ? 1u : 0u;
-    // Kaldor culling: edges are numbered along each polyline, so l - k is the gap
-    klass[c] = (M.cull_radius > 0 && same && l - k <= M.cull_radius) ? (uint8_t)3 : (uint8_t)f;
+    f = (!M.filter_off && same && rod_filtered(win, wst, M.loops != 0, k, l)) ? 1u : 0u;
+    // Kaldor culling: edges are numbered along each polyline, so the gap is
+    // l - k (the shorter way round on a closed loop)
+    klass[c] = (M.cull_radius > 0 && same && rod_gap(rloop, k, l) <= M.cull_radius) ? (uint8_t)3 : (uint8_t)f;
   }
   uint32_t b = __ballot_sync(0xffffffffu, f);
   if ((threadIdx.x & 31) == 0 && b) atomicAdd(nfilt, (unsigned long long)__popc(b));
@@ -1792,12 +1835,14 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
   if (s->kind == CB_ROD) {
     CB_TRY(buf_ensure(s->S, sizeof(double) * (size_t)s->n, st));
     CB_TRY(buf_ensure(s->win, sizeof(int32_t) * (size_t)std::max(1, s->E), st));
+    CB_TRY(buf_ensure(s->wst, sizeof(int32_t) * (size_t)std::max(1, s->E), st));
     k_arclength<<<cb_grid(s->n_rods), CB_THREADS, 0, cb_count(st)>>>(s->n_rods, bp<int32_t>(s->rod_ptr), bp<double>(s->rest),
                                                            s->n, bp<double>(s->S));
     if (s->E > 0)
-      k_rod_window<<<cb_grid(s->E), CB_THREADS, 0, cb_count(st)>>>(s->E, bp<int32_t>(s->ev0), bp<int32_t>(s->ev1),
-                                                         bp<int32_t>(s->comp), bp<double>(s->S), s->a,
-                                                         bp<int32_t>(s->win), dmin, nf, dcomp);
+      k_rod_window<<<cb_grid(s->E), CB_THREADS, 0, cb_count(st)>>>(
+          s->E, bp<int32_t>(s->ev0), bp<int32_t>(s->ev1), bp<int32_t>(s->comp), bp<double>(s->S),
+          bp<double>(s->rest), s->n, bp<int32_t>(s->rlast), s->a, bp<int32_t>(s->win), bp<int32_t>(s->wst), dmin,
+          nf, dcomp);
     CB_CUDA(cudaGetLastError());
     uint64_t h[2];
     CB_TRY(read_scalars(s, SC_DBAR_MIN_BITS, 1, &h[0], st));
@@ -1900,7 +1945,8 @@ cb_status filter_apply(cb_scene* s, cudaStream_t st) {
   if (s->kind == CB_ROD)
     k_filter_rod<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(
         nc, bp<uint64_t>(s->cand), bp<int32_t>(s->ev0), bp<int32_t>(s->comp), bp<int32_t>(s->win),
-        bp<int32_t>(s->vsc), bp<MemberParams>(s->mp), bp<uint8_t>(s->klass), nf);
+        bp<int32_t>(s->wst), bp<int32_t>(s->rloop), bp<int32_t>(s->vsc), bp<MemberParams>(s->mp),
+        bp<uint8_t>(s->klass), nf);
   else
     k_filter_shell<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(
         nc, bp<uint64_t>(s->cand), bp<uint64_t>(s->frest), bp<uint32_t>(s->frow_pt), bp<uint32_t>(s->frow_ee),

@@ -30,6 +30,7 @@ struct MemberParams {
   int32_t cull_radius;    // CB_FILTER_KALDOR: rod edge pairs of one polyline this close are culled; else 0
   int32_t per_comp;       // CB_DBAR_PER_COMPONENT: class-F width from dbar_comp by component label
   double dbar_fmax;       // largest class-F width of the member (= dbar_min unless per_comp)
+  int32_t loops;          // rods: the member has closed loops (backward arc-length windows to test)
 };
 
 // Spatial-hash grid of one member.
@@ -97,6 +98,9 @@ struct cb_scene {
   // filter tables
   DevBuf S;             // double [n] rods: arc length
   DevBuf win;           // int32 [E] rods: last filtered partner edge
+  DevBuf wst;           // int32 [E] rods: first partner edge of the backward window on a closed loop (-1: none)
+  DevBuf rloop;         // int32 [E] rods: edge count of the edge's closed loop (0: open polyline)
+  DevBuf rlast;         // int32 [E] rods: last (closing) edge of the edge's closed loop (-1: open)
   DevBuf frest;         // uint64 shells: sorted rest-filtered keys
   DevBuf frest_dbar;    // double
   DevBuf dbar_comp;     // uint64 bits of the per-component dbar_min, by component label (n entries)
