@@ -141,6 +141,11 @@ def _workload(name: str, reduced_nx: int | None = None):
     elif name == "graded":
         sc = S.graded_disk(target_tris=200_000 if not reduced_nx else 6000, L0=0.1 if not reduced_nx else 0.5)
         desc = f"graded twisted disk ({sc.tris.shape[1]} tris), 0.1-4 mm edges, thickness 1 mm"
+    elif name == "chain":
+        n_rings = reduced_nx or 2000
+        sc = S.ring_chain(n_rings=n_rings, m=96)
+        desc = (f"chain of {n_rings} interlocked closed yarn loops x 96 segments ({sc.n} vertices), "
+                f"R 1 mm, thickness 0.3 mm, dhat 0.05 mm")
     else:
         raise ValueError(name)
     return sc, desc
@@ -222,6 +227,9 @@ def cpu_baseline(workload: str, nx: int) -> dict:
     if workload == "graded":
         sc = S.graded_disk(target_tris=50_000, L0=0.2)
         return _oracle_sample([sc], f"one oracle pass on the graded-disk recipe at {sc.tris.shape[1]} triangles")
+    if workload == "chain":
+        sc = S.ring_chain(n_rings=500, m=96)
+        return _oracle_sample([sc], "one oracle pass on a 500-loop chain of the same recipe")
     if workload == "knit64":
         scenes = S.rod_batch()[::4]
         return _oracle_sample(scenes, f"one oracle pass on every fourth scene of the batch ({len(scenes)} scenes)")
@@ -608,13 +616,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="pleated",
-                    choices=["pleated", "woven", "graded", "knit64", "serve", "friction"])
+                    choices=["pleated", "woven", "graded", "knit64", "serve", "friction", "chain"])
     ap.add_argument("--requests", type=int, default=1000, help="serve: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (requests/s)")
     ap.add_argument("--req-steps", type=int, default=10, help="serve: contact steps per request")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serve: HBM admission budget")
     ap.add_argument("--slots", type=int, default=16, help="serve: most requests resident at once")
-    ap.add_argument("--nx", type=int, default=0, help="pleated grid size (default: the full 256)")
+    ap.add_argument("--nx", type=int, default=0, help="pleated grid size (default: the full 256); chain: loops")
     ap.add_argument("--cpu-nx", type=int, default=128, help="grid size of the oracle baseline sample")
     ap.add_argument("--ref-nx", type=int, default=96, help="grid size of a reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
