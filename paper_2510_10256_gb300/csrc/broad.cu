@@ -295,11 +295,12 @@ __device__ __forceinline__ int lower_bound_u32(const uint32_t* __restrict__ a, i
 // counts are found again by the fill pass's tests)
 constexpr int PAIR_STAGE = 32;
 // Shell cells: the count pass keeps the outcome of each entry's first
-// PAIR_MASK_BITS partner positions as bits (bit b = j - j0 of entry i in word
+// 32 mask_words partner positions as bits (bit b = j - j0 of entry i in word
 // mask[(b / 32) * ne + i]), so the keys of those pairs are written from the
-// bits without repeating the tests
-constexpr int PAIR_MASK_WORDS = 16;
-constexpr int PAIR_MASK_BITS = 32 * PAIR_MASK_WORDS;
+// bits without repeating the tests.  mask_words follows the longest partner
+// range of the previous broad phase (counted by the count pass), within
+// [1, PAIR_MASK_WORDS_MAX]; longer ranges are re-tested past the bits.
+constexpr int PAIR_MASK_WORDS_MAX = 64;
 
 struct PairArgs {
   Topo t;
@@ -312,7 +313,9 @@ struct PairArgs {
   const float4* __restrict__ ebox;   // boxes in entry order: entry j at [2 j], [2 j + 1]
   const double* __restrict__ box64;
   const Grid* __restrict__ grids;
-  uint32_t* __restrict__ mask;       // shells: [PAIR_MASK_WORDS][entries] partner bits
+  uint32_t* __restrict__ mask;       // shells: [mask_words][entries] partner bits
+  int mask_words;                    // shells: words of partner bits per entry
+  unsigned int* maxr;                // shells, count pass: longest partner range (atomic max)
   int bi, bj;
   unsigned long long* fpstat;  // count pass: [0] FP32-accepted pairs, [1] FP64-decided (may be null)
   bool canonical;              // fill pass: write canonical keys (else compact ones for the sort)
@@ -408,9 +411,8 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
   // bits (k_pairs_emit writes the pairs of the bits), from there on
   int jb = j0;
   if (!RR && FILL) {
-    jb = j0 + PAIR_MASK_BITS;
-#pragma unroll
-    for (int w = 0; w < PAIR_MASK_WORDS; ++w) count += __popc(A.mask[(size_t)w * A.ne + i]);
+    jb = j0 + 32 * A.mask_words;
+    for (int w = 0; w < A.mask_words; ++w) count += __popc(A.mask[(size_t)w * A.ne + i]);
   }
   uint32_t word = 0, beyond = 0;
   for (int jj = jb; jj < j1; ++jj) {
@@ -468,7 +470,7 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
     if (!RR && !FILL) {
       // the lanes of a warp are at the same position b: coalesced word stores
       const int b = jj - j0;
-      if (b < PAIR_MASK_BITS) {
+      if (b < 32 * A.mask_words) {
         word |= (uint32_t)acc << (b & 31);
         if ((b & 31) == 31 || jj + 1 == j1) {
           A.mask[(size_t)(b >> 5) * A.ne + i] = word;
@@ -490,6 +492,11 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
         if (a64) atomicAdd(&A.fpstat[1], (unsigned long long)a64);
       }
     }
+    if (!RR && A.maxr) {
+      const unsigned mask = __activemask();
+      const unsigned mr = __reduce_max_sync(mask, (unsigned)(j1 - j0));
+      if ((int)(threadIdx.x & 31) == __ffs(mask) - 1 && mr) atomicMax(A.maxr, mr);
+    }
   }
 }
 
@@ -498,7 +505,7 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
 // entry i reports.  Rod cells (RR): the first PAIR_STAGE of them are staged
 // (element-major, stage[k * ne + i]) and entries with more are listed in
 // ovl; k_pairs_copy moves the staged keys.  Shell cells: the outcome of the
-// first PAIR_MASK_BITS partner positions is kept as bits, entries with pairs
+// first 32 mask_words partner positions is kept as bits, entries with pairs
 // past them are listed in ovl, and k_pairs_emit writes the pairs of the bits.
 // The fill pass (FILL = true) then runs over the listed entries only, writing
 // the remaining pairs at their place.
@@ -527,7 +534,7 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs_emit(PairArgs A, const uin
   const uint32_t c_end = cnt[i];
   if (c_end == 0) return;
   const EntryRange R = entry_range(A, i);
-  const int nb = min(R.j1 - R.j0, PAIR_MASK_BITS);
+  const int nb = min(R.j1 - R.j0, 32 * A.mask_words);
   const size_t o = off[i];
   uint32_t count = 0;
   for (int w = 0; 32 * w < nb; ++w) {
@@ -735,10 +742,17 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   A.canonical = !sort_out;
   unsigned int* novl = (unsigned int*)(scalars(s) + SC_NOVF);
   CB_TRY(buf_ensure(w.stage, rods ? sizeof(uint64_t) * PAIR_STAGE * (size_t)ne
-                                   : sizeof(uint32_t) * PAIR_MASK_WORDS * (size_t)ne, st));
+                                   : sizeof(uint32_t) * (size_t)w.mask_words * (size_t)ne, st));
   CB_TRY(buf_ensure(w.ovl, sizeof(uint32_t) * (size_t)ne, st));
   CB_CUDA(cudaMemsetAsync(novl, 0, sizeof(unsigned int), st));
   A.mask = rods ? nullptr : bp<uint32_t>(w.stage);
+  A.mask_words = w.mask_words;
+  // the longest partner range of this call, for the next call's mask_words:
+  // counted on the device, copied to pinned host memory with the pair count
+  const int wi = &w == &s->bwc ? 1 : 0;
+  unsigned int* maxr = (unsigned int*)(scalars(s) + SC_MAXR) + wi;
+  A.maxr = rods ? nullptr : maxr;
+  if (!rods) CB_CUDA(cudaMemsetAsync(maxr, 0, sizeof(unsigned int), st));
   auto pairs = [&](bool fill, uint64_t* o) {
     uint32_t* c = bp<uint32_t>(w.pair_cnt);
     const uint32_t* f = fill ? bp<uint32_t>(w.pair_off) : nullptr;
@@ -763,8 +777,11 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off), ne,
                                           bp<uint32_t>(w.scan_tmp), tot_dev, st);
   CB_CUDA(cudaGetLastError());
+  uint32_t* hmaxr = (uint32_t*)(s->h_pinned + H_PINNED_MAXR) + wi;
+  if (!rods) CB_CUDA(cudaMemcpyAsync(hmaxr, maxr, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   uint64_t hnc;
-  CB_TRY(read_scalars(s, SC_COUNT0, 1, &hnc, st));
+  CB_TRY(read_scalars(s, SC_COUNT0, 1, &hnc, st));  // the copy above is complete after this sync
+  if (!rods) w.mask_words = std::min(PAIR_MASK_WORDS_MAX, std::max(1, (int)((*hmaxr + 31) / 32)));
   const int64_t nc = (uint32_t)hnc;
   *n_out = nc;
   if (nc == 0) return CB_OK;

@@ -42,6 +42,7 @@ struct Grid {
 // Workspace of one broad phase (static or swept) -- reused between calls.
 struct BroadWork {
   float cell_factor = 1.0f;  // hash cell edge = factor x mean primitive box extent (tuning knob)
+  int mask_words = 16;       // shells: words of partner bits per entry (from the last call's longest range)
   int pair_block = CB_THREADS;  // threads per block of the pair enumeration (tuning knob)
   DevBuf box32;       // float4 lo, float4 hi per primitive
   DevBuf box64;       // double lo[3], hi[3] per primitive
@@ -154,7 +155,7 @@ struct cb_scene {
   DevBuf hist;
   DevBuf dev_scalars;   // misc device scalars (counters, energy, alpha bits, status)
 
-  uint64_t* h_pinned = nullptr;  // pinned host scratch
+  uint64_t* h_pinned = nullptr;  // pinned host scratch (64 slots; [H_PINNED_MAXR]: the broad phases' ranges)
   int32_t status_host = 0;
 
   bool timing = false;
@@ -185,8 +186,12 @@ enum {
   SC_KSPLIT = 16,       // two uint32 counters: face / line-line pairs, the other active pairs
   SC_NOVF = 17,         // broad phase: entries whose pairs overflow the stage
   SC_NBK = 18,          // BSR pattern: keys left after the per-run sets of k_block_keys
-  SC_N = 19
+  SC_MAXR = 19,         // broad phase, shells: two uint32 -- longest partner range (static, swept)
+  SC_N = 20
 };
+// slot of the pinned host scratch that receives the SC_MAXR pair (read_scalars uses the first SC_N)
+constexpr int H_PINNED_MAXR = 62;
+static_assert(SC_N <= H_PINNED_MAXR, "pinned scratch slots overlap");
 
 static inline uint64_t* scalars(cb_scene* s) { return (uint64_t*)s->dev_scalars.p; }
 
