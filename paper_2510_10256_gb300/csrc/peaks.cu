@@ -1,5 +1,5 @@
 // peaks.cu -- arithmetic-throughput probes used to report the FP64 roofline
-// denominator measured on the running GPU (the driver's peak file carries HBM
+// denominator measured on the running GPU (the measured-peaks file carries HBM
 // and bf16 figures only).  Independent dependency chains per thread, enough
 // warps to fill every SM, timed with CUDA events.
 #include "scene.cuh"
