@@ -63,7 +63,7 @@ class _Topo(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("xi", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double),
                 ("dbar_min", C.c_double), ("single", C.c_int), ("core_temp", C.c_int),
-                ("project", C.c_int), ("dbar_comp", C.c_void_p)]
+                ("project", C.c_int), ("dbar_comp", C.c_void_p), ("moll_eps", C.c_void_p)]
 
 
 def lib():
@@ -397,16 +397,35 @@ class PassResult:
         return self.C[self.klass == k]
 
 
+def mollifier_thresholds(scene, topo: Topology, keys: np.ndarray) -> np.ndarray:
+    """eps_x = 1e-3 |rest e0|^2 |rest e1|^2 of each edge-edge key (0 for
+    point-triangle keys): IPC's edge-edge mollifier threshold."""
+    keys = np.asarray(keys, np.uint64)
+    t, i, j = key_parts(keys)
+    out = np.zeros(keys.size)
+    ee = t != PT
+    if ee.any():
+        r = np.asarray(scene.rest, np.float64)
+        e = topo.edges.astype(np.int64)
+        def len2(k):
+            dv = r[:, e[1, k]] - r[:, e[0, k]]
+            return (dv * dv).sum(0)
+        out[ee] = 1e-3 * len2(i[ee]) * len2(j[ee])
+    return np.ascontiguousarray(out)
+
+
 def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: bool = True,
                  ccd: bool = True, x: np.ndarray | None = None, p: np.ndarray | None = None,
                  topo: Topology | None = None, filt=None, cull_radius: int = 0,
-                 per_component: bool = False) -> PassResult:
+                 per_component: bool = False, mollifier: bool = False) -> PassResult:
     """One full pass (stages a-e) at x with CCD direction p.  Mode "kaldor":
     no filter, and rod edge pairs of one polyline at most cull_radius edges
     apart are culled (class X: no barrier, no constraint on the step).
     per_component: a filtered pair's width is the smallest reference distance
     of the filtered pairs of its own component instead of the scene's
-    (dbar_min per component)."""
+    (dbar_min per component).  mollifier: edge-edge pairs take IPC's
+    mollifier m(|e0 x e1|^2) with threshold 1e-3 |rest e0|^2 |rest e1|^2
+    (the paper's solver uses IPC's contact energy, App. A)."""
     if mode == "kaldor" and (scene.kind != "rod" or cull_radius < 1):
         raise ValueError("kaldor mode: rods and cull_radius >= 1")
     import time
@@ -466,6 +485,9 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     akl = np.ascontiguousarray(kl[active])
     ad = np.ascontiguousarray(d[active])
     adt = np.ascontiguousarray(dty[active])
+    if mollifier:
+        meps = mollifier_thresholds(scene, topo, ak)
+        P.moll_eps = meps.ctypes.data
     lib().orc_barrier_pairs(C.byref(tc), _ptr(x), C.byref(P), na, _ptr(ak), _ptr(akl), _ptr(ad),
                             _ptr(adt), _ptr(e), _ptr(g), _ptr(H), _ptr(hmax))
     energy = math.fsum(e.tolist()) if na else 0.0

@@ -618,6 +618,8 @@ typedef struct {
     int core_temp;   /* 1: class C on */
     int project;     /* 1: PSD-project the Hessian (0 only for derivative checks) */
     const double* dbar_comp;  /* per-component dbar_min by component label, or NULL (one scalar) */
+    const double* moll_eps;   /* per active pair (orc_barrier_pairs order): the edge-edge mollifier's
+                                 threshold eps_x, <= 0 for none; NULL: no mollifier */
 } orc_params;
 
 /* comp: the component label of the pair's first vertex */
@@ -661,8 +663,44 @@ int64_t orc_narrow(const orc_topo* tp, const double* x, const orc_params* P, int
     return nact;
 }
 
+/* ------------------------------------------------------------------------- */
+/* IPC's edge-edge mollifier (Li et al. 2020), which the paper's solver takes   */
+/* with the IPC contact energy (App. A): with c = |e0 x e1|^2 (e0 = a1 - a0,    */
+/* e1 = b1 - b0) and the threshold eps_x = 1e-3 |rest e0|^2 |rest e1|^2,        */
+/*   m(c) = -c^2 / eps_x^2 + 2 c / eps_x  for c < eps_x,  1 otherwise,          */
+/* and the pair's energy is m kappa b.  m vanishes for parallel edges, where    */
+/* the edge-edge distance type is ambiguous, and is C^1 at eps_x.               */
+/* ------------------------------------------------------------------------- */
+void orc_mollifier(double c, double eps, double* m, double* m1, double* m2) {
+    if (!(c < eps)) { *m = 1.0; *m1 = 0.0; *m2 = 0.0; return; }
+    *m = -(c * c) / (eps * eps) + 2.0 * c / eps;
+    *m1 = -2.0 * c / (eps * eps) + 2.0 / eps;
+    *m2 = -2.0 / (eps * eps);
+}
+
+/* c = |(a1 - a0) x (b1 - b0)|^2 of an edge-edge stencil with its gradient (12)
+ * and Hessian (144, row-major), by hyper-dual evaluation per coordinate pair */
+void orc_ee_cross2_derivs(const double* x12, double* c, double* grad, double* hess) {
+    for (int i = 0; i < 12; ++i) {
+        for (int j = i; j < 12; ++j) {
+            hv3 X[4];
+            to_hv(x12, X);
+            X[i / 3].c[i % 3].e1 = 1.0;
+            X[j / 3].c[j % 3].e2 = 1.0;
+            hv3 n = vcross(vsub(X[1], X[0]), vsub(X[3], X[2]));
+            hd v = vdot(n, n);
+            hess[12 * i + j] = v.e12;
+            hess[12 * j + i] = v.e12;
+            if (i == j) grad[i] = v.e1;
+            if (i == 0 && j == 0) *c = v.v;
+        }
+    }
+}
+
 /* Energy and derivatives of the active pairs listed in idx[] (indices into the
- * candidate arrays).  grad: [na][12]; hess: [na][144]. */
+ * candidate arrays).  grad: [na][12]; hess: [na][144].  Edge-edge pairs with
+ * a mollifier threshold (P->moll_eps[a] > 0) take m kappa b and its
+ * derivatives by the product rule. */
 void orc_barrier_pairs(const orc_topo* tp, const double* x, const orc_params* P, int64_t na,
                        const uint64_t* keys, const uint8_t* klass, const double* d,
                        const int8_t* type, double* energy, double* grad, double* hess, double* hmax) {
@@ -689,6 +727,22 @@ void orc_barrier_pairs(const orc_topo* tp, const double* x, const orc_params* P,
         for (int i = 0; i < 12; ++i)
             for (int j = 0; j < 12; ++j)
                 H[12 * i + j] = P->kappa * (b2 * gd[i] * gd[j] + b1 * Hd[12 * i + j]);
+        const double eps = (ee && P->moll_eps) ? P->moll_eps[a] : 0.0;
+        if (eps > 0.0) {
+            double c, gc[12], Hc[144], m, m1, m2;
+            orc_ee_cross2_derivs(x12, &c, gc, Hc);
+            orc_mollifier(c, eps, &m, &m1, &m2);
+            if (c < eps) {
+                const double k = P->kappa;
+                energy[a] = k * m * b;
+                for (int i = 0; i < 12; ++i) grad[12 * a + i] = k * (m * b1 * gd[i] + b * m1 * gc[i]);
+                for (int i = 0; i < 12; ++i)
+                    for (int j = 0; j < 12; ++j)
+                        H[12 * i + j] = k * (m * (b2 * gd[i] * gd[j] + b1 * Hd[12 * i + j]) +
+                                             b1 * m1 * (gc[i] * gd[j] + gd[i] * gc[j]) +
+                                             b * (m2 * gc[i] * gc[j] + m1 * Hc[12 * i + j]));
+            }
+        }
         double mx = 0.0;
         for (int i = 0; i < 144; ++i) mx = fmax(mx, fabs(H[i]));
         if (hmax) hmax[a] = mx;   /* largest entry before projection */
