@@ -74,6 +74,11 @@ typedef enum {
 #define CB_DBAR_PER_COMPONENT 16    /* a filtered pair's width is the dbar_min of its own component (the
                                        smallest reference distance of that component's filtered pairs)
                                        instead of the scene's */
+#define CB_EE_MOLLIFIER 32          /* IPC's edge-edge mollifier (App. A: the paper's solver uses IPC's
+                                       contact energy): an edge-edge pair's energy is m(c) kappa b with
+                                       c = |e0 x e1|^2, m = -c^2/eps_x^2 + 2c/eps_x below eps_x =
+                                       1e-3 |rest e0|^2 |rest e1|^2 and 1 above; derivatives by the
+                                       product rule, projected with the pair's 9x9 matrix */
 
 /* pair lists for cb_get_pairs */
 #define CB_PAIRS_CANDIDATE 0        /* C: broad-phase candidates */
@@ -98,7 +103,8 @@ typedef struct {
   double thickness;           /* offset xi (eta in the paper); rods: 2 x radius */
   double dhat;                /* barrier width; full activation a = thickness + dhat */
   double kappa;               /* barrier stiffness (energy scale); 1 if <= 0 */
-  int32_t mode;               /* CB_FILTER_* | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP | CB_DBAR_PER_COMPONENT */
+  int32_t mode;               /* CB_FILTER_* | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP | CB_DBAR_PER_COMPONENT
+                                 | CB_EE_MOLLIFIER */
   int32_t cull_radius;        /* CB_FILTER_KALDOR: culling radius in edges (>= 1); else ignored */
   const uint8_t* rod_closed;  /* rods, HOST [n_rods] or NULL: 1 = closed loop (an edge from the last vertex
                                  back to the first, numbered after the polyline's others; >= 3 vertices,

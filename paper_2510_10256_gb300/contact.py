@@ -23,6 +23,7 @@ CB_FILTER_DOUBLE, CB_FILTER_SINGLE, CB_FILTER_OFF, CB_FILTER_KALDOR = 0, 1, 2, 3
 CB_THICK_PAPER_LITERAL = 4
 CB_NO_CORE_TEMP = 8
 CB_DBAR_PER_COMPONENT = 16
+CB_EE_MOLLIFIER = 32
 PAIRS = {"candidate": 0, "filtered": 1, "core": 2, "active": 3, "ccd": 4, "rest_filtered": 5}
 MODES = {"double": CB_FILTER_DOUBLE, "single": CB_FILTER_SINGLE, "off": CB_FILTER_OFF, "kaldor": CB_FILTER_KALDOR}
 
@@ -189,7 +190,7 @@ class ContactScene:
     def __init__(self, kind: str, rest, thickness: float, dhat: float, rod_ptr=None, tris=None,
                  kappa: float = 1.0, mode: str = "double", paper_literal: bool = False,
                  core_temp: bool = True, cull_radius: int = 0, per_component: bool = False, rod_closed=None,
-                 stream=None):
+                 mollifier: bool = False, stream=None):
         L = lib()
         rest = np.ascontiguousarray(np.asarray(rest, np.float64).reshape(3, -1))
         self.n = rest.shape[1]
@@ -218,7 +219,8 @@ class ContactScene:
         d.dhat = float(dhat)
         d.kappa = float(kappa)
         d.mode = MODES[mode] | (CB_THICK_PAPER_LITERAL if paper_literal else 0) | \
-            (0 if core_temp else CB_NO_CORE_TEMP) | (CB_DBAR_PER_COMPONENT if per_component else 0)
+            (0 if core_temp else CB_NO_CORE_TEMP) | (CB_DBAR_PER_COMPONENT if per_component else 0) | \
+            (CB_EE_MOLLIFIER if mollifier else 0)
         d.cull_radius = int(cull_radius)
         h = C.c_void_p()
         _check(L.cb_scene_create(C.byref(d), _stream_ptr(stream), C.byref(h)), "cb_scene_create")

@@ -58,7 +58,7 @@ static cb_status upload(DevBuf& b, const T* h, size_t count, cudaStream_t st) {
 static void scene_release(cb_scene* s) {
   cudaStream_t st = s->last_stream;
   DevBuf* bufs[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->wst,
-                    &s->rloop, &s->rlast, &s->frest,
+                    &s->rloop, &s->rlast, &s->elen2, &s->hmoll, &s->mlist, &s->frest,
                     &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
                     &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col, &s->bsr_val,
                     &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->mp, &s->vsc, &s->macc, &s->hstage, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag, &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist,
@@ -183,7 +183,8 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
   if (!(d->dhat > 0.0) || !(d->thickness >= 0.0) || !std::isfinite(d->thickness) || !std::isfinite(d->dhat))
     return CB_ERR_ARG;
   const int fm = d->mode & CB_FILTER_MASK;
-  if (d->mode & ~(CB_FILTER_MASK | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP | CB_DBAR_PER_COMPONENT))
+  if (d->mode & ~(CB_FILTER_MASK | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP | CB_DBAR_PER_COMPONENT |
+                  CB_EE_MOLLIFIER))
     return CB_ERR_ARG;
   if (fm == CB_FILTER_KALDOR && (d->kind != CB_ROD || d->cull_radius < 1)) return CB_ERR_ARG;
   const int n = d->n_verts;
@@ -292,6 +293,7 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
                                 (fm == CB_FILTER_OFF || fm == CB_FILTER_KALDOR) ? 1 : 0, s->n_prims});
   s->hmp[0].cull_radius = fm == CB_FILTER_KALDOR ? d->cull_radius : 0;
   s->hmp[0].per_comp = (d->mode & CB_DBAR_PER_COMPONENT) ? 1 : 0;
+  s->hmp[0].mollify = (d->mode & CB_EE_MOLLIFIER) ? 1 : 0;
   s->hmp[0].loops = 0;
   for (int32_t lc : rloop) s->hmp[0].loops |= lc > 0 ? 1 : 0;
   s->voff = {0, (int64_t)n};
@@ -310,6 +312,19 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
   if (cudaMemsetAsync(s->dev_scalars.p, 0, SC_N * sizeof(uint64_t), st) != cudaSuccess) return fail(CB_ERR_CUDA);
   if ((rc = upload(s->ev0, e0.data(), e0.size(), st)) != CB_OK) return fail(rc);
   if ((rc = upload(s->ev1, e1.data(), e1.size(), st)) != CB_OK) return fail(rc);
+  {
+    // squared rest length of every edge (the edge-edge mollifier's threshold)
+    std::vector<double> l2(e0.size());
+    for (size_t k = 0; k < e0.size(); ++k) {
+      double acc = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        const double dv = d->rest_xyz[(size_t)c * n + e1[k]] - d->rest_xyz[(size_t)c * n + e0[k]];
+        acc += dv * dv;
+      }
+      l2[k] = acc;
+    }
+    if ((rc = upload(s->elen2, l2.data(), l2.size(), st)) != CB_OK) return fail(rc);
+  }
   if ((rc = upload(s->tv, tris.data(), tris.size(), st)) != CB_OK) return fail(rc);
   if ((rc = upload(s->comp, comp.data(), comp.size(), st)) != CB_OK) return fail(rc);
   if ((rc = upload(s->rest, d->rest_xyz, 3 * (size_t)n, st)) != CB_OK) return fail(rc);
@@ -412,6 +427,7 @@ cb_status cb_batch_create(cb_scene* const* members, int32_t count, void* stream,
   if ((rc = buf_ensure(b->vsc, sizeof(int32_t) * (size_t)b->n, st)) != CB_OK) return fail(rc);
   if ((rc = buf_ensure(b->win, sizeof(int32_t) * (size_t)std::max(1, b->E), st)) != CB_OK) return fail(rc);
   if ((rc = buf_ensure(b->wst, sizeof(int32_t) * (size_t)std::max(1, b->E), st)) != CB_OK) return fail(rc);
+  if ((rc = buf_ensure(b->elen2, sizeof(double) * (size_t)std::max(1, b->E), st)) != CB_OK) return fail(rc);
   if ((rc = buf_ensure(b->rloop, sizeof(int32_t) * (size_t)std::max(1, b->E), st)) != CB_OK) return fail(rc);
   if ((rc = buf_ensure(b->frest, sizeof(uint64_t) * (size_t)std::max<int64_t>(1, nf), st)) != CB_OK) return fail(rc);
   int64_t wpt = 0, wee = nf_pt;
@@ -423,6 +439,8 @@ cb_status cb_batch_create(cb_scene* const* members, int32_t count, void* stream,
                                                                      s->E, vo);
       k_offset_copy<<<cb_grid(s->E), CB_THREADS, 0, cb_count(st)>>>(bp<int32_t>(b->ev1) + eo, bp<int32_t>(s->ev1),
                                                                      s->E, vo);
+      CB_CUDA(cudaMemcpyAsync(bp<double>(b->elen2) + eo, s->elen2.p, sizeof(double) * (size_t)s->E,
+                              cudaMemcpyDeviceToDevice, st));
       if (b->kind == CB_ROD) {
         k_offset_copy<<<cb_grid(s->E), CB_THREADS, 0, cb_count(st)>>>(bp<int32_t>(b->win) + eo,
                                                                        bp<int32_t>(s->win), s->E, eo);
@@ -775,7 +793,7 @@ cb_status cb_get_stats(cb_scene* s, cb_stats* o) {
   o->n_pair_overflow = (int64_t)(uint32_t)h[SC_NOVF];
   size_t bytes = 0;
   const DevBuf* all[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->wst,
-                         &s->rloop, &s->rlast, &s->frest,
+                         &s->rloop, &s->rlast, &s->elen2, &s->hmoll, &s->mlist, &s->frest,
                          &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls,
                          &s->aidx, &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col,
                          &s->bsr_val, &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag,

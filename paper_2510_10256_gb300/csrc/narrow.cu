@@ -275,6 +275,7 @@ __global__ void k_distance_screen(int64_t nc, const uint64_t* __restrict__ cand,
 // (list entries [0, nlist[0]) and [cap - nlist[1], cap)).  With energy set
 // (the energy-only pass), every active pair also adds kappa b(y) to its
 // member's energy.
+template <bool ENERGY>
 __global__ void k_distance_exact(const uint32_t* __restrict__ list, int64_t cap, const unsigned int* __restrict__ nlist,
                                  const uint64_t* __restrict__ cand, const uint8_t* __restrict__ klass_in,
                                  const int32_t* __restrict__ ev0, const int32_t* __restrict__ ev1,
@@ -284,7 +285,8 @@ __global__ void k_distance_exact(const uint32_t* __restrict__ list, int64_t cap,
                                  uint8_t* __restrict__ cls, uint32_t* __restrict__ flag,
                                  unsigned long long* __restrict__ status, unsigned long long* __restrict__ ncore,
                                  unsigned long long* __restrict__ macc, const int32_t* __restrict__ comp,
-                                 const unsigned long long* __restrict__ dbar_comp, bool energy) {
+                                 const unsigned long long* __restrict__ dbar_comp, const double* __restrict__ elen2) {
+  constexpr bool energy = ENERGY;  // energy only (barrier_energy): add kappa b per active pair
   const unsigned m0 = nlist[0], m = m0 + nlist[1];
   for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w - threadIdx.x < m; w += gridDim.x * blockDim.x) {
     uint32_t is_core = 0;
@@ -314,7 +316,15 @@ __global__ void k_distance_exact(const uint32_t* __restrict__ list, int64_t cap,
       flag[c] = act;
       is_core = (k == 2);
       if (energy && act && y > 0.0) {
-        e_local = P.kappa * barrier_b(y, dh_p);
+        double mf = 1.0;
+        if (P.mollify && s.ee) {  // IPC's edge-edge mollifier
+          const double eps = 1e-3 * elen2[cb_key_i(cand[c])] * elen2[cb_key_j(cand[c])];
+          double m1, m2;
+          ee_mollifier(ee_cross2(load3(x, n, s.v[0]), load3(x, n, s.v[1]), load3(x, n, s.v[2]),
+                                 load3(x, n, s.v[3])),
+                       eps, mf, m1, m2);
+        }
+        e_local = P.kappa * mf * barrier_b(y, dh_p);
         e_mem = mem;
       }
     }
@@ -731,6 +741,11 @@ struct HessArgs {
   unsigned int* __restrict__ n6;
   unsigned int* __restrict__ n4;
   int64_t cap;
+  // CB_EE_MOLLIFIER: pairs handled by k_moll_hess (hmoll null: none)
+  const uint8_t* __restrict__ hmoll;
+  const uint32_t* __restrict__ mlist;
+  const unsigned* __restrict__ nmoll;
+  const double* __restrict__ elen2;
 };
 
 
@@ -838,16 +853,43 @@ __device__ __forceinline__ void write_reduced_pe_local(double* __restrict__ Bo, 
 // backwards, so that a warp of the prep kernel runs one branch rather than
 // both with few lanes each.  Warp-aggregated appends; inside each group the
 // order follows warp arrival.
+struct MollArgs {                   // CB_EE_MOLLIFIER scenes only (mp null: no mollifier)
+  const double* __restrict__ x;
+  int n;
+  const int32_t* __restrict__ ev0;
+  const int32_t* __restrict__ ev1;
+  const int32_t* __restrict__ vsc;
+  const MemberParams* __restrict__ mp;
+  const double* __restrict__ elen2;
+  uint8_t* __restrict__ hmoll;       // [na] 1: mollified edge-edge pair
+  uint32_t* __restrict__ mlist;      // their active indices
+  unsigned* __restrict__ nmoll;
+};
+
 __global__ void k_kind_split(int64_t na, const uint32_t* __restrict__ aidx, const uint64_t* __restrict__ cand,
                              const int8_t* __restrict__ ctype, uint32_t* __restrict__ order,
-                             unsigned* __restrict__ cnt) {
+                             unsigned* __restrict__ cnt, MollArgs MA) {
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool plane = false;
+  bool plane = false, moll = false;
   if (a < na) {
     const uint32_t c = aidx[a];
     const int ty = ctype[c];
-    plane = (cb_key_type(cand[c]) == CB_KEY_PT ? c_pt_types[ty] : c_ee_types[ty]).kind == 2;
+    const uint64_t key = cand[c];
+    plane = (cb_key_type(key) == CB_KEY_PT ? c_pt_types[ty] : c_ee_types[ty]).kind == 2;
+    if (MA.mp && cb_key_type(key) != CB_KEY_PT) {
+      // edge-edge pair below its mollifier threshold: its energy, gradient
+      // and 9x9 matrix come from k_moll_hess instead of k_hess_prep
+      const uint32_t i = cb_key_i(key), j = cb_key_j(key);
+      const int a0 = MA.ev0[i], a1 = MA.ev1[i], b0 = MA.ev0[j], b1 = MA.ev1[j];
+      if (MA.mp[MA.vsc[a0]].mollify) {
+        const double c2 = ee_cross2(load3(MA.x, MA.n, a0), load3(MA.x, MA.n, a1), load3(MA.x, MA.n, b0),
+                                    load3(MA.x, MA.n, b1));
+        moll = c2 < 1e-3 * MA.elen2[i] * MA.elen2[j];
+      }
+    }
+    if (MA.mp) MA.hmoll[a] = moll ? 1 : 0;
   }
+  if (MA.mp) warp_append(moll, (uint32_t)a, MA.mlist, MA.nmoll);
   const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
   const unsigned mp = __ballot_sync(0xffffffffu, a < na && plane);
   const unsigned mr = __ballot_sync(0xffffffffu, a < na && !plane);
@@ -871,7 +913,8 @@ __global__ void k_kind_split(int64_t na, const uint32_t* __restrict__ aidx, cons
 // in closed form here; the others are queued for the projection kernels.
 __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t a = t < A.na ? (int64_t)A.order[t] : A.na;
+  int64_t a = t < A.na ? (int64_t)A.order[t] : A.na;
+  if (A.hmoll && a < A.na && A.hmoll[a]) a = A.na;  // mollified edge-edge pair: k_moll_hess
   double e_local = 0.0;
   int mem = -1;
   int want = 0;  // 9 or 6: reduced dimension of the queued matrix
@@ -1051,6 +1094,146 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
     for (int e = 0; e < 45; ++e)
       if (e < ne) Bo[(size_t)e * A.cap + slot] = Bq[e];
     (want == 9 ? A.slot9 : (want == 6 ? A.slot6 : A.slot4))[slot] = (uint32_t)a;
+  }
+  member_energy_add(A.macc, mem, e_local);
+}
+
+// ---- IPC's edge-edge mollifier (CB_EE_MOLLIFIER) -------------------------
+// A mollified pair's energy m(c) kappa b(d) depends on all four points
+// whatever its distance type, so it leaves the reduced paths of k_hess_prep:
+// here its gradient and Hessian come from hyper-dual evaluation (value + e1
+// + e2 + e1 e2 parts, exact first and second derivatives) of the typed d^2
+// and of c = |e0 x e1|^2 in coordinates relative to the first point, the
+// Hessian by the product rule
+//   H = kappa (m (b'' gd gd^T + b' Hd) + b' m' (gc gd^T + gd gc^T)
+//              + b (m'' gc gc^T + m' Hc)),
+// and the 9x9 matrix of the four-point translation-free basis
+// (B = (K4 x I)^T H (K4 x I)) is queued for k_hess_proj<9>.
+struct hdn {
+  double v, a, b, ab;
+};
+__device__ __forceinline__ hdn operator+(hdn x, hdn y) { return {x.v + y.v, x.a + y.a, x.b + y.b, x.ab + y.ab}; }
+__device__ __forceinline__ hdn operator-(hdn x, hdn y) { return {x.v - y.v, x.a - y.a, x.b - y.b, x.ab - y.ab}; }
+__device__ __forceinline__ hdn operator*(hdn x, hdn y) {
+  return {x.v * y.v, x.a * y.v + x.v * y.a, x.b * y.v + x.v * y.b, x.ab * y.v + x.a * y.b + x.b * y.a + x.v * y.ab};
+}
+__device__ __forceinline__ hdn h_inv(hdn y) {
+  const double i = 1.0 / y.v;
+  return {i, -y.a * i * i, -y.b * i * i, 2.0 * y.a * y.b * i * i * i - y.ab * i * i};
+}
+__device__ __forceinline__ hdn h_sqrt(hdn x) {
+  const double r = sqrt(x.v), i = 0.5 / r;
+  return {r, x.a * i, x.b * i, x.ab * i - x.a * x.b * i / (2.0 * x.v)};
+}
+struct hv {
+  hdn x, y, z;
+};
+__device__ __forceinline__ hv hv_sub(hv p, hv q) { return {p.x - q.x, p.y - q.y, p.z - q.z}; }
+__device__ __forceinline__ hdn hv_dot(hv p, hv q) { return p.x * q.x + p.y * q.y + p.z * q.z; }
+__device__ __forceinline__ hv hv_cross(hv p, hv q) {
+  return {p.y * q.z - p.z * q.y, p.z * q.x - p.x * q.z, p.x * q.y - p.y * q.x};
+}
+// typed squared edge-edge distance (types as in geometry.cuh) of R (a0 a1 b0 b1)
+__device__ hdn ee_d2_typed(int ty, const hv (&R)[4]) {
+  auto pp = [](hv p, hv q) {
+    const hv d = hv_sub(q, p);
+    return hv_dot(d, d);
+  };
+  auto pe = [](hv q, hv e0, hv e1) {
+    const hv u = hv_sub(e1, e0), c = hv_cross(hv_sub(q, e0), u);
+    return hv_dot(c, c) * h_inv(hv_dot(u, u));
+  };
+  switch (ty) {
+    case 0: return pp(R[0], R[2]);
+    case 1: return pp(R[0], R[3]);
+    case 2: return pp(R[1], R[2]);
+    case 3: return pp(R[1], R[3]);
+    case 4: return pe(R[0], R[2], R[3]);
+    case 5: return pe(R[1], R[2], R[3]);
+    case 6: return pe(R[2], R[0], R[1]);
+    case 7: return pe(R[3], R[0], R[1]);
+    default: {
+      const hv n = hv_cross(hv_sub(R[1], R[0]), hv_sub(R[3], R[2]));
+      const hdn g = hv_dot(hv_sub(R[2], R[0]), n);
+      return g * g * h_inv(hv_dot(n, n));
+    }
+  }
+}
+// d and c of the stencil X (4 points, 12 doubles point-major) with the
+// hyper-dual parts seeded on coordinates i (e1) and j (e2)
+__device__ void moll_eval(int ty, const double (&X)[12], int i, int j, hdn& d, hdn& c) {
+  hdn Y[12];
+  for (int k = 0; k < 12; ++k) Y[k] = {X[k], k == i ? 1.0 : 0.0, k == j ? 1.0 : 0.0, 0.0};
+  hv R[4];
+  for (int q = 0; q < 4; ++q)
+    R[q] = {Y[3 * q] - Y[0], Y[3 * q + 1] - Y[1], Y[3 * q + 2] - Y[2]};
+  d = h_sqrt(ee_d2_typed(ty, R));
+  const hv n = hv_cross(hv_sub(R[1], R[0]), hv_sub(R[3], R[2]));
+  c = hv_dot(n, n);
+}
+
+// one thread per mollified pair (listed by k_kind_split)
+__global__ void __launch_bounds__(128) k_moll_hess(HessArgs A) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double e_local = 0.0;
+  int mem = -1;
+  if (t < (int64_t)*A.nmoll) {
+    const uint32_t a = A.mlist[t];
+    const uint32_t c = A.aidx[a];
+    const uint64_t key = A.cand[c];
+    const Stencil s = stencil_of(key, A.ev0, A.ev1, A.tv, A.T);
+    const int ty = A.ctype[c];
+    mem = A.vsc[s.v[0]];
+    const PassParams P = member_pass(A.mp[mem]);
+    double xi_p, dh_p;
+    pair_params(P, A.ccls[c], f_width(P, A.dbar_comp, A.comp, s.v[0]), xi_p, dh_p);
+    double b, b1, b2;
+    barrier_b012(A.cd[c] - xi_p, dh_p, b, b1, b2);
+    double X[12];
+    for (int q = 0; q < 4; ++q) {
+      const d3 p = load3(A.x, A.n, s.v[q]);
+      X[3 * q] = p.x;
+      X[3 * q + 1] = p.y;
+      X[3 * q + 2] = p.z;
+    }
+    double gd[12], gc[12], cval = 0.0;
+    for (int i = 0; i < 12; ++i) {
+      hdn d, cc;
+      moll_eval(ty, X, i, i, d, cc);
+      gd[i] = d.a;
+      gc[i] = cc.a;
+      cval = cc.v;
+    }
+    const double eps = 1e-3 * A.elen2[cb_key_i(key)] * A.elen2[cb_key_j(key)];
+    double m, m1, m2;
+    ee_mollifier(cval, eps, m, m1, m2);
+    const double kap = P.kappa;
+    e_local = kap * m * b;
+    if (A.grad)
+      for (int i = 0; i < 12; ++i) {
+        const double g = kap * (m * b1 * gd[i] + b * m1 * gc[i]);
+        if (g != 0.0) atomicAdd(&A.grad[(size_t)(i % 3) * A.n + s.v[i / 3]], g);
+      }
+    double Bf[81];
+    for (int k = 0; k < 81; ++k) Bf[k] = 0.0;
+    for (int i = 0; i < 12; ++i)
+      for (int j = i; j < 12; ++j) {
+        hdn d, cc;
+        moll_eval(ty, X, i, j, d, cc);
+        const double h = kap * (m * (b2 * gd[i] * gd[j] + b1 * d.ab) + b1 * m1 * (gc[i] * gd[j] + gd[i] * gc[j]) +
+                                b * (m2 * gc[i] * gc[j] + m1 * cc.ab));
+        const int q1 = i / 3, al = i % 3, q2 = j / 3, be = j % 3;
+        for (int p1 = 0; p1 < 3; ++p1)
+          for (int p2 = 0; p2 < 3; ++p2) {
+            const double w = c_K4[q1][p1] * c_K4[q2][p2] * h;
+            Bf[(3 * p1 + al) * 9 + 3 * p2 + be] += w;
+            if (i != j) Bf[(3 * p2 + be) * 9 + 3 * p1 + al] += w;
+          }
+      }
+    const unsigned slot = atomicAdd(A.n9, 1u);
+    for (int i = 0; i < 9; ++i)
+      for (int j = i; j < 9; ++j) A.B9[(size_t)tri_idx(i, j, 9) * A.cap + slot] = Bf[i * 9 + j];
+    A.slot9[slot] = a;
   }
   member_energy_add(A.macc, mem, e_local);
 }
@@ -2001,11 +2184,11 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
         bp<int32_t>(s->tv), s->T, bp<float4>(s->xf), bp<double>(s->bw.cx), bp<int32_t>(s->vsc),
         bp<MemberParams>(s->mp), s->n, bp<double>(s->cd),
         bp<int8_t>(s->ctype), bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), bp<uint32_t>(s->dlist), nl);
-    k_distance_exact<<<std::min<int64_t>(cb_grid(nc), 152 * 16), CB_THREADS, 0, cb_count(st)>>>(
+    (energy_only ? k_distance_exact<true> : k_distance_exact<false>)<<<std::min<int64_t>(cb_grid(nc), 152 * 16), CB_THREADS, 0, cb_count(st)>>>(
         bp<uint32_t>(s->dlist), nc, nl, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass), bp<int32_t>(s->ev0),
         bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T, x, s->n, bp<int32_t>(s->vsc), bp<MemberParams>(s->mp),
         bp<double>(s->cd), bp<int8_t>(s->ctype), bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), status, ncore,
-        macc, bp<int32_t>(s->comp), bp<unsigned long long>(s->dbar_comp), energy_only);
+        macc, bp<int32_t>(s->comp), bp<unsigned long long>(s->dbar_comp), bp<double>(s->elen2));
     if (energy_only) {
       if (energy) k_energy_final<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, energy);
       CB_CUDA(cudaGetLastError());
@@ -2070,9 +2253,20 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
                                            (int32_t*)bp<uint32_t>(s->scan_tmp), (int32_t*)nullptr, st);
     CB_TRY(buf_ensure(s->horder, sizeof(uint32_t) * (size_t)na, st));
     k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_KSPLIT), 0ull);
+    bool mollify = false;
+    for (const MemberParams& mpm : s->hmp) mollify |= mpm.mollify != 0;
+    MollArgs MA{};
+    if (mollify) {
+      CB_TRY(buf_ensure(s->hmoll, (size_t)na, st));
+      CB_TRY(buf_ensure(s->mlist, sizeof(uint32_t) * (size_t)na, st));
+      k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_NMOLL), 0ull);
+      MA = MollArgs{x, s->n, bp<int32_t>(s->ev0), bp<int32_t>(s->ev1), bp<int32_t>(s->vsc),
+                    bp<MemberParams>(s->mp), bp<double>(s->elen2), bp<uint8_t>(s->hmoll),
+                    bp<uint32_t>(s->mlist), (unsigned*)(sc + SC_NMOLL)};
+    }
     k_kind_split<<<cb_grid(na), CB_THREADS, 0, cb_count(st)>>>(na, bp<uint32_t>(s->aidx), bp<uint64_t>(s->cand),
                                                              bp<int8_t>(s->ctype), bp<uint32_t>(s->horder),
-                                                             (unsigned*)(sc + SC_KSPLIT));
+                                                             (unsigned*)(sc + SC_KSPLIT), MA);
     HessArgs A;
     A.na = na;
     A.order = bp<uint32_t>(s->horder);
@@ -2111,11 +2305,16 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     A.n6 = (unsigned int*)(sc + SC_N6);
     A.n4 = (unsigned int*)(sc + SC_N4);
     A.cap = na;
+    A.hmoll = mollify ? bp<uint8_t>(s->hmoll) : nullptr;
+    A.mlist = bp<uint32_t>(s->mlist);
+    A.nmoll = (const unsigned*)(sc + SC_NMOLL);
+    A.elen2 = bp<double>(s->elen2);
     k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_N9), 0ull);
     k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_N6), 0ull);
     k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_N4), 0ull);
     if (s->timing) cudaEventRecord(s->ev[10], st);
     k_hess_prep<<<cb_grid(na, 128), 128, 0, cb_count(st)>>>(A);
+    if (mollify) k_moll_hess<<<cb_grid(na, 128), 128, 0, cb_count(st)>>>(A);
     CB_CUDA(cudaGetLastError());
     uint64_t hq[SC_N4 - SC_N9 + 1];
     CB_TRY(read_scalars(s, SC_N9, SC_N4 - SC_N9 + 1, hq, st));

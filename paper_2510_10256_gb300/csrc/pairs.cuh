@@ -39,7 +39,7 @@ __device__ __forceinline__ d3 load3(const double* __restrict__ x, int n, int v) 
 
 struct PassParams {
   double xi, dhat, a, dbar_min, kappa;
-  int single, core_temp, per_comp;
+  int single, core_temp, per_comp, mollify;
 };
 
 __device__ __forceinline__ PassParams member_pass(const MemberParams& m) {
@@ -52,7 +52,32 @@ __device__ __forceinline__ PassParams member_pass(const MemberParams& m) {
   P.single = m.single;
   P.core_temp = m.core_temp;
   P.per_comp = m.per_comp;
+  P.mollify = m.mollify;
   return P;
+}
+
+// IPC's edge-edge mollifier of c = |e0 x e1|^2 with threshold eps:
+// m = -c^2/eps^2 + 2c/eps below eps, 1 above, and its first two derivatives
+__device__ __forceinline__ void ee_mollifier(double c, double eps, double& m, double& m1, double& m2) {
+  if (!(c < eps)) {
+    m = 1.0;
+    m1 = 0.0;
+    m2 = 0.0;
+    return;
+  }
+  const double ie = 1.0 / eps;
+  m = -(c * c) * (ie * ie) + 2.0 * c * ie;
+  m1 = -2.0 * c * (ie * ie) + 2.0 * ie;
+  m2 = -2.0 * (ie * ie);
+}
+
+// c = |(a1 - a0) x (b1 - b0)|^2 of an edge-edge stencil and the mollifier's
+// threshold 1e-3 |rest e0|^2 |rest e1|^2
+__device__ __forceinline__ double ee_cross2(d3 a0, d3 a1, d3 b0, d3 b1) {
+  const double ux = a1.x - a0.x, uy = a1.y - a0.y, uz = a1.z - a0.z;
+  const double vx = b1.x - b0.x, vy = b1.y - b0.y, vz = b1.z - b0.z;
+  const double nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+  return nx * nx + ny * ny + nz * nz;
 }
 
 // pair parameters: offset xi_p and width dhat_p of a class (0 U, 1 F, 2 C)

@@ -31,6 +31,7 @@ struct MemberParams {
   int32_t per_comp;       // CB_DBAR_PER_COMPONENT: class-F width from dbar_comp by component label
   double dbar_fmax;       // largest class-F width of the member (= dbar_min unless per_comp)
   int32_t loops;          // rods: the member has closed loops (backward arc-length windows to test)
+  int32_t mollify;        // CB_EE_MOLLIFIER: edge-edge pairs take IPC's mollifier
 };
 
 // Spatial-hash grid of one member.
@@ -102,6 +103,7 @@ struct cb_scene {
   DevBuf wst;           // int32 [E] rods: first partner edge of the backward window on a closed loop (-1: none)
   DevBuf rloop;         // int32 [E] rods: edge count of the edge's closed loop (0: open polyline)
   DevBuf rlast;         // int32 [E] rods: last (closing) edge of the edge's closed loop (-1: open)
+  DevBuf elen2;         // double [E] squared rest length of each edge (the mollifier's threshold)
   DevBuf frest;         // uint64 shells: sorted rest-filtered keys
   DevBuf frest_dbar;    // double
   DevBuf dbar_comp;     // uint64 bits of the per-component dbar_min, by component label (n entries)
@@ -132,6 +134,8 @@ struct cb_scene {
   DevBuf row_cnt;       // uint32 [n+1]
   int64_t nnzb = 0;
   DevBuf horder;        // uint32 active pair indices in prep order (face / line-line pairs first)
+  DevBuf hmoll;         // uint8 [na] mollified edge-edge pair (CB_EE_MOLLIFIER), handled by k_moll_hess
+  DevBuf mlist;         // uint32 active indices of the mollified pairs
   DevBuf hB9, hB6, hB4;  // queued reduced Hessians (packed, element-major); hB4: point-edge in its own frame
   DevBuf hslot;          // uint32 [2][na] active index of each queued matrix
   DevBuf xf, pf;         // float [3][n]: centred FP32 copies of x and of p
@@ -187,7 +191,8 @@ enum {
   SC_NOVF = 17,         // broad phase: entries whose pairs overflow the stage
   SC_NBK = 18,          // BSR pattern: keys left after the per-run sets of k_block_keys
   SC_MAXR = 19,         // broad phase, shells: two uint32 -- longest partner range (static, swept)
-  SC_N = 20
+  SC_NMOLL = 20,        // barrier_eval: mollified edge-edge pairs
+  SC_N = 21
 };
 // slot of the pinned host scratch that receives the SC_MAXR pair (read_scalars uses the first SC_N)
 constexpr int H_PINNED_MAXR = 62;

@@ -20,12 +20,12 @@ import oracle as O
 
 
 def run_gpu(sc, mode="double", core_temp=True, x=None, p=None, paper_literal=False, cull_radius=0,
-            per_component=False):
+            per_component=False, mollifier=False):
     import torch
     from paper_2510_10256_gb300.contact import ContactScene
     dev = torch.device("cuda:0")
     cs = ContactScene.from_scene(sc, mode=mode, core_temp=core_temp, paper_literal=paper_literal,
-                                 cull_radius=cull_radius, per_component=per_component)
+                                 cull_radius=cull_radius, per_component=per_component, mollifier=mollifier)
     xx = torch.from_numpy(np.ascontiguousarray(sc.x if x is None else x)).to(dev)
     pp = torch.from_numpy(np.ascontiguousarray(sc.p if p is None else p)).to(dev)
     energy = torch.zeros(1, dtype=torch.float64, device=dev)
