@@ -628,6 +628,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="knit64: skip the one-scene-per-launch arm")
     ap.add_argument("--no-tune", action="store_true", help="keep the default broad-phase knobs")
+    ap.add_argument("--mollifier", action="store_true", help="single-scene workloads: IPC's edge-edge mollifier")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -664,7 +665,7 @@ def main():
     sc, desc = _workload(args.workload, reduced_nx=args.nx or None)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    cs = CT.ContactScene.from_scene(sc)
+    cs = CT.ContactScene.from_scene(sc, mollifier=args.mollifier)
     x = torch.from_numpy(sc.x).to(dev)
     p = torch.from_numpy(sc.p).to(dev)
     energy = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -760,6 +761,7 @@ def main():
             "config": {"workload": desc, "candidates": int(n_cand), "filtered": st["n_filtered"],
                        "core": st["n_core"], "active": int(na), "ccd_pairs": st["n_ccd"], "nnzb": st["nnzb"],
                        "dbar_min": st["dbar_min"], "seed": sc.seed, "tuning": tuning,
+                       "mollifier": bool(args.mollifier), "mollified_pairs": st["n_mollified"],
                        "l2": "flushed (256 MiB write) between steps",
                        "parallelism": f"replicas x{world}"},
             "stage_ms": {"contact_build": med[0], "contact_filter": med[1], "barrier_eval": med[2],

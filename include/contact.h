@@ -133,7 +133,8 @@ typedef struct {
   int64_t n_hess_pe;          /* ... point-edge pairs on the generic 6x6 projection */
   int64_t n_pair_overflow;    /* last broad phase (ccd_step's, once a pass ran it): entries whose pairs
                                  went past what the count pass keeps (rods: 32 staged keys; shells: the
-                                 partner bits of the first 512 positions), re-tested by the fill pass */
+                                 partner bits of the positions the count pass keeps), re-tested by the fill pass */
+  int64_t n_mollified;        /* last barrier_eval with CB_EE_MOLLIFIER: edge-edge pairs below their threshold */
 } cb_stats;
 
 /* Create a scene: uploads topology and rest positions, derives edges and

@@ -59,7 +59,7 @@ class Stats(C.Structure):
                 ("ccd_max_iters", C.c_int32), ("device_bytes", C.c_int64),
                 ("n_candidates_fp32", C.c_int64), ("n_fp64_decided", C.c_int64),
                 ("n_hess_face", C.c_int64), ("n_hess_pe_frame", C.c_int64), ("n_hess_pe", C.c_int64),
-                ("n_pair_overflow", C.c_int64)]
+                ("n_pair_overflow", C.c_int64), ("n_mollified", C.c_int64)]
 
 
 def build(force: bool = False) -> str:

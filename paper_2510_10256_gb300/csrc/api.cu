@@ -791,6 +791,7 @@ cb_status cb_get_stats(cb_scene* s, cb_stats* o) {
   o->n_hess_pe_frame = s->n_hq[1];
   o->n_hess_pe = s->n_hq[2];
   o->n_pair_overflow = (int64_t)(uint32_t)h[SC_NOVF];
+  o->n_mollified = (int64_t)(uint32_t)h[SC_NMOLL];
   size_t bytes = 0;
   const DevBuf* all[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->wst,
                          &s->rloop, &s->rlast, &s->elen2, &s->hmoll, &s->mlist, &s->frest,
