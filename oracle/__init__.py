@@ -414,10 +414,32 @@ def mollifier_thresholds(scene, topo: Topology, keys: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(out)
 
 
+def _within_own_width(topo: Topology, x, keys, klass, dbar_comp, dbar_min: float) -> np.ndarray:
+    """Per candidate: True unless it is filtered and its FP64 boxes, each
+    inflated by half its own width, do not overlap (closed intervals)."""
+    keep = np.ones(keys.size, bool)
+    F = np.flatnonzero(klass == KLASS_F)
+    if F.size == 0:
+        return keep
+    st = stencils(topo, keys[F])
+    t, _, _ = key_parts(keys[F])
+    pt = t == PT
+    fw = dbar_comp[topo.comp[st[:, 0]]] if dbar_comp is not None else np.full(F.size, dbar_min)
+    h = 0.5 * fw
+    # first primitive: the point (PT) or edge (EE); second: the triangle or edge
+    a = np.where(pt[:, None], st[:, [0, 0]], st[:, [0, 1]])
+    b = np.where(pt[:, None], st[:, 1:4], st[:, [2, 3, 3]])
+    lo1, hi1 = x[:, a].min(axis=2), x[:, a].max(axis=2)
+    lo2, hi2 = x[:, b].min(axis=2), x[:, b].max(axis=2)
+    ov = np.all((lo1 - h <= hi2 + h) & (lo2 - h <= hi1 + h), axis=0)
+    keep[F] = ov
+    return keep
+
+
 def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: bool = True,
                  ccd: bool = True, x: np.ndarray | None = None, p: np.ndarray | None = None,
                  topo: Topology | None = None, filt=None, cull_radius: int = 0,
-                 per_component: bool = False, mollifier: bool = False) -> PassResult:
+                 per_component: bool = False, mollifier: bool = False, per_stencil: bool = False) -> PassResult:
     """One full pass (stages a-e) at x with CCD direction p.  Mode "kaldor":
     no filter, and rod edge pairs of one polyline at most cull_radius edges
     apart are culled (class X: no barrier, no constraint on the step).
@@ -425,7 +447,12 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     of the filtered pairs of its own component instead of the scene's
     (dbar_min per component).  mollifier: edge-edge pairs take IPC's
     mollifier m(|e0 x e1|^2) with threshold 1e-3 |rest e0|^2 |rest e1|^2
-    (the paper's solver uses IPC's contact energy, App. A)."""
+    (the paper's solver uses IPC's contact energy, App. A).  per_stencil:
+    each filtered candidate is kept only if its FP64 boxes, inflated by half
+    of its own width (dbar_min, or its component's) instead of a / 2,
+    overlap -- the per-stencil activation the paper leaves for later
+    (Sec. 3.3); a filtered pair outside it is inactive, so only the
+    candidate set changes."""
     if mode == "kaldor" and (scene.kind != "rod" or cull_radius < 1):
         raise ValueError("kaldor mode: rods and cull_radius >= 1")
     import time
@@ -460,6 +487,10 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     t1 = time.perf_counter()
     # per-component dbar_min by component label (the label of a pair's first vertex)
     dbar_comp = dbar_min_per_component(topo, F_rest, dbar) if per_component else None
+    if per_stencil and Cset.size:
+        keep = _within_own_width(topo, x, Cset, klass_in, dbar_comp,
+                                 dbar_min if np.isfinite(dbar_min) else 0.0)
+        Cset, klass_in = np.ascontiguousarray(Cset[keep]), np.ascontiguousarray(klass_in[keep])
     P = _Params(xi, dhat, float(scene.kappa), dbar_min if np.isfinite(dbar_min) else 0.0,
                 int(mode == "single"), int(core_temp), int(project),
                 dbar_comp.ctypes.data if dbar_comp is not None else None)
