@@ -18,6 +18,13 @@ Steps of one pass, in the paper's order:
   6. CCD candidates (swept boxes), additive CCD with per-class offsets,
      step bound alpha = min(1, min_p t_p)                                   Sec. 3.3
 
+Options of contact_pass beside the paper's pass: mode "single" / "off" /
+"kaldor" (Eq. 1, no filter, Kaldor culling), per_component (dbar_min per
+component), mollifier (IPC's edge-edge mollifier), per_stencil (filtered
+candidates kept at their own width); rod scenes may mark closed loops
+(scene.rod_closed: reference distances the shorter way round).  Lagged
+friction on the active pairs: oracle/friction.py.
+
 Pins: tests/test_oracle_*.py.  parity pinned for every function exported here.
 """
 from __future__ import annotations
