@@ -33,3 +33,26 @@ def test_library_pure_calls_without_gpu():
     assert CT.lib().cb_version().decode().startswith("gb300-contact")
     assert CT.status_str(CT.CB_ERR_PENETRATION).startswith("pair")
     assert CT.lib().cb_scene_destroy(None) == CT.CB_ERR_ARG
+
+
+@pytest.mark.parametrize("cname,pytype", [("cb_scene_desc", "SceneDesc"), ("cb_stats", "Stats")])
+def test_struct_layouts_match_the_header(cname, pytype, tmp_path):
+    """The ctypes mirrors of the header's structs: same size, same field
+    offsets (a C probe compiled against include/contact.h prints them)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    st = getattr(CT, pytype)
+    fields = [f for f, _ in st._fields_]
+    src = tmp_path / "probe.c"
+    lines = ["#include <stdio.h>", '#include "contact.h"', "int main(void) {",
+             f'  printf("%zu\\n", sizeof({cname}));']
+    lines += [f'  printf("%zu\\n", offsetof({cname}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(st), (out[0], ctypes.sizeof(st))
+    assert out[1:] == [getattr(st, f).offset for f in fields]
