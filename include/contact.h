@@ -110,6 +110,10 @@ typedef struct {
                                  back to the first, numbered after the polyline's others; >= 3 vertices,
                                  else CB_ERR_ARG).  Its reference distances take the shorter way round the
                                  loop, Kaldor gaps too.  NULL: every polyline open. */
+  const double* rest_uv;      /* shells, HOST [2][n] or NULL: the flat pattern the shell is cut from.
+                                 Reference distances (Sec. 3.2: the 2D rest-domain distance) are taken in
+                                 the pattern -- the geodesic distance of a developable rest shape -- while
+                                 rest_xyz keeps the 3D rest shape.  Non-NULL for rods: CB_ERR_ARG. */
 } cb_scene_desc;
 
 typedef struct {

@@ -22,7 +22,9 @@ Options of contact_pass beside the paper's pass: mode "single" / "off" /
 "kaldor" (Eq. 1, no filter, Kaldor culling), per_component (dbar_min per
 component), mollifier (IPC's edge-edge mollifier), per_stencil (filtered
 candidates kept at their own width); rod scenes may mark closed loops
-(scene.rod_closed: reference distances the shorter way round).  Lagged
+(scene.rod_closed: reference distances the shorter way round); shell
+scenes may carry the flat pattern they are cut from (scene.rest_uv:
+reference distances taken there).  Lagged
 friction on the active pairs: oracle/friction.py.
 
 Pins: tests/test_oracle_*.py.  parity pinned for every function exported here.
@@ -289,6 +291,11 @@ def rest_filter(scene, topo: Topology, a: float) -> tuple[np.ndarray, np.ndarray
         return _rod_rest_filter_loops(scene, topo, a)
     tc = topo.ctype()
     rest = np.ascontiguousarray(scene.rest, np.float64)
+    if topo.kind == 1 and getattr(scene, "rest_uv", None) is not None:
+        # a shell cut from a flat pattern: the reference distance is taken in
+        # the pattern (the geodesic distance of its developable rest shape)
+        uv = np.asarray(scene.rest_uv, np.float64)
+        rest = np.ascontiguousarray(np.vstack([uv, np.zeros((1, uv.shape[1]))]))
     S = arclength(scene) if topo.kind == 0 else np.zeros(1)
     ok, od = C.c_void_p(), C.c_void_p()
     m = lib().orc_rest_filter(C.byref(tc), _ptr(rest), float(a), _ptr(S), C.byref(ok), C.byref(od))

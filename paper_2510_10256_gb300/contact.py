@@ -48,7 +48,7 @@ class SceneDesc(C.Structure):
                 ("n_rods", C.c_int32), ("rod_ptr", C.c_void_p), ("n_tris", C.c_int32),
                 ("tris", C.c_void_p), ("thickness", C.c_double), ("dhat", C.c_double),
                 ("kappa", C.c_double), ("mode", C.c_int32), ("cull_radius", C.c_int32),
-                ("rod_closed", C.c_void_p)]
+                ("rod_closed", C.c_void_p), ("rest_uv", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -190,7 +190,7 @@ class ContactScene:
     def __init__(self, kind: str, rest, thickness: float, dhat: float, rod_ptr=None, tris=None,
                  kappa: float = 1.0, mode: str = "double", paper_literal: bool = False,
                  core_temp: bool = True, cull_radius: int = 0, per_component: bool = False, rod_closed=None,
-                 mollifier: bool = False, stream=None):
+                 mollifier: bool = False, rest_uv=None, stream=None):
         L = lib()
         rest = np.ascontiguousarray(np.asarray(rest, np.float64).reshape(3, -1))
         self.n = rest.shape[1]
@@ -215,6 +215,12 @@ class ContactScene:
             self._keep.append(tr)
             d.n_tris = tr.shape[1]
             d.tris = tr.ctypes.data
+            if rest_uv is not None:
+                uv = np.ascontiguousarray(np.asarray(rest_uv, np.float64).reshape(2, -1))
+                if uv.shape[1] != self.n:
+                    raise ValueError("rest_uv: (2, n)")
+                self._keep.append(uv)
+                d.rest_uv = uv.ctypes.data
         d.thickness = float(thickness)
         d.dhat = float(dhat)
         d.kappa = float(kappa)
@@ -240,7 +246,8 @@ class ContactScene:
     @classmethod
     def from_scene(cls, sc, mode: str = "double", **kw) -> "ContactScene":
         return cls(sc.kind, sc.rest, sc.thickness, sc.dhat, rod_ptr=sc.rod_ptr, tris=sc.tris,
-                   kappa=sc.kappa, mode=mode, rod_closed=getattr(sc, "rod_closed", None), **kw)
+                   kappa=sc.kappa, mode=mode, rod_closed=getattr(sc, "rod_closed", None),
+                   rest_uv=getattr(sc, "rest_uv", None), **kw)
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:

@@ -58,7 +58,7 @@ static cb_status upload(DevBuf& b, const T* h, size_t count, cudaStream_t st) {
 static void scene_release(cb_scene* s) {
   cudaStream_t st = s->last_stream;
   DevBuf* bufs[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->wst,
-                    &s->rloop, &s->rlast, &s->elen2, &s->hmoll, &s->mlist, &s->frest,
+                    &s->rloop, &s->rlast, &s->elen2, &s->hmoll, &s->mlist, &s->ruv, &s->frest,
                     &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
                     &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col, &s->bsr_val,
                     &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->mp, &s->vsc, &s->macc, &s->hstage, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag, &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist,
@@ -187,6 +187,7 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
                   CB_EE_MOLLIFIER))
     return CB_ERR_ARG;
   if (fm == CB_FILTER_KALDOR && (d->kind != CB_ROD || d->cull_radius < 1)) return CB_ERR_ARG;
+  if (d->rest_uv && d->kind != CB_SHELL) return CB_ERR_ARG;
   const int n = d->n_verts;
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<int32_t> e0, e1, comp(n), rloop, rlast;
@@ -328,6 +329,11 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
   if ((rc = upload(s->tv, tris.data(), tris.size(), st)) != CB_OK) return fail(rc);
   if ((rc = upload(s->comp, comp.data(), comp.size(), st)) != CB_OK) return fail(rc);
   if ((rc = upload(s->rest, d->rest_xyz, 3 * (size_t)n, st)) != CB_OK) return fail(rc);
+  if (d->rest_uv) {  // the pattern as (u, v, 0): the rest-filter precompute runs on it
+    std::vector<double> uv3(3 * (size_t)n, 0.0);
+    std::memcpy(uv3.data(), d->rest_uv, sizeof(double) * 2 * (size_t)n);
+    if ((rc = upload(s->ruv, uv3.data(), uv3.size(), st)) != CB_OK) return fail(rc);
+  }
   if (d->kind == CB_ROD && (rc = upload(s->rod_ptr, d->rod_ptr, (size_t)d->n_rods + 1, st)) != CB_OK) return fail(rc);
   if (d->kind == CB_ROD && (rc = upload(s->rloop, rloop.data(), rloop.size(), st)) != CB_OK) return fail(rc);
   if (d->kind == CB_ROD && (rc = upload(s->rlast, rlast.data(), rlast.size(), st)) != CB_OK) return fail(rc);
@@ -794,7 +800,7 @@ cb_status cb_get_stats(cb_scene* s, cb_stats* o) {
   o->n_mollified = (int64_t)(uint32_t)h[SC_NMOLL];
   size_t bytes = 0;
   const DevBuf* all[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->wst,
-                         &s->rloop, &s->rlast, &s->elen2, &s->hmoll, &s->mlist, &s->frest,
+                         &s->rloop, &s->rlast, &s->elen2, &s->hmoll, &s->mlist, &s->ruv, &s->frest,
                          &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls,
                          &s->aidx, &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col,
                          &s->bsr_val, &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag,

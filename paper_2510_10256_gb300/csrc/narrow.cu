@@ -2036,7 +2036,9 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
     // rest broad phase at the full activation, then rest distances below a
     int64_t nr = 0;
     DevBuf rc;
-    CB_TRY(broad_phase(s, s->bw, bp<double>(s->rest), nullptr, false, true, rc, &nr, st));
+    // positions of the reference distances: the flat pattern when given, else the rest shape
+    const double* rf = s->ruv.p ? bp<double>(s->ruv) : bp<double>(s->rest);
+    CB_TRY(broad_phase(s, s->bw, rf, nullptr, false, true, rc, &nr, st));
     if (nr > 0) {
       DevBuf flag, pos, dbar;
       CB_TRY(buf_ensure(flag, sizeof(uint32_t) * (size_t)nr, st));
@@ -2045,7 +2047,7 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
       CB_TRY(buf_ensure(s->scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(nr) + 8), st));
       k_rest_filter<<<cb_grid(nr), CB_THREADS, 0, cb_count(st)>>>(nr, bp<uint64_t>(rc), bp<int32_t>(s->ev0),
                                                         bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T,
-                                                        bp<int32_t>(s->comp), bp<double>(s->rest), s->n, s->a,
+                                                        bp<int32_t>(s->comp), rf, s->n, s->a,
                                                         bp<uint32_t>(flag), bp<double>(dbar), dmin, dcomp);
       uint32_t* tot = (uint32_t*)(sc + SC_COUNT1);
       cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(flag), bp<uint32_t>(pos), nr, bp<uint32_t>(s->scan_tmp),

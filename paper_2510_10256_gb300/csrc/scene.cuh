@@ -104,6 +104,7 @@ struct cb_scene {
   DevBuf rloop;         // int32 [E] rods: edge count of the edge's closed loop (0: open polyline)
   DevBuf rlast;         // int32 [E] rods: last (closing) edge of the edge's closed loop (-1: open)
   DevBuf elen2;         // double [E] squared rest length of each edge (the mollifier's threshold)
+  DevBuf ruv;           // double [3][n] shells: the flat pattern (u, v, 0), when given; reference distances there
   DevBuf frest;         // uint64 shells: sorted rest-filtered keys
   DevBuf frest_dbar;    // double
   DevBuf dbar_comp;     // uint64 bits of the per-component dbar_min, by component label (n entries)

@@ -42,6 +42,7 @@ class Scene:
     seed: int = 0
     meta: dict = field(default_factory=dict)
     rod_closed: np.ndarray | None = None  # uint8 (n_rods,) for rods: 1 = closed loop (last vertex joins the first)
+    rest_uv: np.ndarray | None = None     # (2, n) for shells: the flat pattern the rest shape is made from
 
     @property
     def n(self) -> int:
@@ -410,6 +411,30 @@ def flat_grid(nx: int = 8, L: float = 0.5, thickness: float = 1.0,
     rest, tris = grid_mesh(nx, nx, L)
     return Scene("shell", _soa(rest), _soa(rest.copy()), np.zeros_like(rest), thickness,
                  dhat, tris=tris, name="flat_grid")
+
+
+def rolled_sheet(seed: int = BASE_SEED + 8, nx: int = 24, ny: int = 12, L: float = 0.25, radius: float = 1.5,
+                 thickness: float = 0.4, dhat: float = 0.05, sigma: float = 0.05, layers: int = 2) -> Scene:
+    """Sheets cut from a flat nx x ny grid pattern (edge L) and rolled at rest
+    onto coaxial cylinders (the outer one thickness + 0.6 dhat further out),
+    so their rest shape is curved while their pattern is flat: reference
+    distances are taken in the pattern (rest_uv).  Current positions: the
+    rest shape plus a little noise; p: Gaussian."""
+    rng = np.random.default_rng(seed)
+    pat, t = grid_mesh(nx, ny, L)
+    rest_l, tris_l, uv_l = [], [], []
+    for k in range(layers):
+        R = radius + k * (thickness + 0.6 * dhat)
+        ang = pat[0] / radius   # same angles for every layer: the pattern is rolled, not stretched
+        rest_l.append(np.stack([R * np.sin(ang), pat[1], radius - R * np.cos(ang)]))
+        tris_l.append(t + k * pat.shape[1])
+        uv_l.append(pat[:2])
+    rest = np.concatenate(rest_l, axis=1)
+    tris = np.concatenate(tris_l, axis=1).astype(np.int32)
+    x = rest + rng.normal(0.0, 0.01 * dhat, size=rest.shape)
+    p = rng.normal(0.0, sigma, size=rest.shape)
+    return Scene("shell", _soa(rest), _soa(x), _soa(p), thickness, dhat, tris=tris, name="rolled_sheet", seed=seed,
+                 rest_uv=np.ascontiguousarray(np.concatenate(uv_l, axis=1)))
 
 
 def tiny_shell(seed: int, nx: int = 5, L: float = 0.3, thickness: float = 0.4,
