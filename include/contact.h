@@ -324,13 +324,18 @@ const char* cb_version(void);
  *   flags_dev     DEVICE 1 uint32 (overwritten): CB_DEV conditions 2
  *                 (penetration: a stencil at or inside its offset, t_p = 0),
  *                 4 (iteration limit) and CB_NOALLOC_BAD_STENCIL (a vertex id
- *                 outside [0, n_verts) or a bad offset: that stencil skipped).
- * The caller owns every buffer; the call is asynchronous on `stream`.
+ *                 outside [0, n_verts), a negative or non-finite offset, or a
+ *                 non-finite position or displacement: that stencil is
+ *                 skipped and does not bound alpha -- check the flag).
+ * The caller owns every buffer; each must be memory of the current device
+ * (or managed memory), else CB_ERR_ARG before any work.  The call is
+ * asynchronous on `stream`, which must belong to the current device.
  * n_stencils = 0 gives alpha = 1.  More than CB_NOALLOC_MAX_STENCILS stencils
  * return CB_ERR_TOO_LARGE before any work; split the list and take the
  * minimum.  The first call on each device looks up the scratch address and may
  * make the CUDA runtime load the library's code onto that device: make it
- * before any stream capture.  All calls on one device share the scratch:
+ * before any stream capture.  The address is kept for the life of the
+ * process: do not use this call on a device after cudaDeviceReset there.  All calls on one device share the scratch:
  * calls that overlap in time on one device (several streams or host threads)
  * race and give wrong results.  Errors: CB_ERR_ARG, CB_ERR_TOO_LARGE,
  * CB_ERR_CUDA. */

@@ -21,7 +21,8 @@ Steps of one pass, in the paper's order:
 Options of contact_pass beside the paper's pass: mode "single" / "off" /
 "kaldor" (Eq. 1, no filter, Kaldor culling), per_component (dbar_min per
 component), mollifier (IPC's edge-edge mollifier), per_stencil (filtered
-candidates kept at their own width); rod scenes may mark closed loops
+candidates kept at their own width), paper_literal (activation = thickness,
+offset = thickness - dhat); rod scenes may mark closed loops
 (scene.rod_closed: reference distances the shorter way round); shell
 scenes may carry the flat pattern they are cut from (scene.rest_uv:
 reference distances taken there).  Lagged
@@ -453,7 +454,8 @@ def _within_own_width(topo: Topology, x, keys, klass, dbar_comp, dbar_min: float
 def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: bool = True,
                  ccd: bool = True, x: np.ndarray | None = None, p: np.ndarray | None = None,
                  topo: Topology | None = None, filt=None, cull_radius: int = 0,
-                 per_component: bool = False, mollifier: bool = False, per_stencil: bool = False) -> PassResult:
+                 per_component: bool = False, mollifier: bool = False, per_stencil: bool = False,
+                 paper_literal: bool = False) -> PassResult:
     """One full pass (stages a-e) at x with CCD direction p.  Mode "kaldor":
     no filter, and rod edge pairs of one polyline at most cull_radius edges
     apart are culled (class X: no barrier, no constraint on the step).
@@ -466,7 +468,10 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     of its own width (dbar_min, or its component's) instead of a / 2,
     overlap -- the per-stencil activation the paper leaves for later
     (Sec. 3.3); a filtered pair outside it is inactive, so only the
-    candidate set changes."""
+    candidate set changes.  paper_literal: the paper's own reading of the
+    thickness h (Sec. 3.1 puts the activation at h, Sec. 3.3 splits it as
+    eta + dhat): activation a = thickness and offset xi = thickness - dhat,
+    instead of xi = thickness, a = thickness + dhat."""
     if mode == "kaldor" and (scene.kind != "rod" or cull_radius < 1):
         raise ValueError("kaldor mode: rods and cull_radius >= 1")
     import time
@@ -475,7 +480,7 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     topo = topo or topology(scene)
     x = np.ascontiguousarray(scene.x if x is None else x, np.float64)
     p = np.ascontiguousarray(scene.p if p is None else p, np.float64)
-    xi, dhat = float(scene.thickness), float(scene.dhat)
+    xi, dhat = offsets(scene, paper_literal)
     a = xi + dhat
     # (b) precompute: reference distances on the rest mesh
     if filt is None:
@@ -583,7 +588,8 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     # (e) CCD step bound
     if ccd:
         t1 = time.perf_counter()
-        ck, ckl, tt, it, cs = ccd_bound(scene, topo, x, p, F_rest, mode, core_temp, dbar_min, cull_radius)
+        ck, ckl, tt, it, cs = ccd_bound(scene, topo, x, p, F_rest, mode, core_temp, dbar_min, cull_radius,
+                                        paper_literal)
         res.ccd_keys, res.ccd_klass, res.ccd_t, res.ccd_iters, res.ccd_status = ck, ckl, tt, it, cs
         res.alpha = float(min(1.0, tt.min())) if tt.size else 1.0
         tm["ccd"] = time.perf_counter() - t1
@@ -591,11 +597,26 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     return res
 
 
-def ccd_bound(scene, topo, x, p, F_rest, mode="double", core_temp=True, dbar_min=0.0, cull_radius=0):
+def offsets(scene, paper_literal: bool = False) -> tuple[float, float]:
+    """(xi, dhat): the offset and barrier width of a scene.  Default: xi =
+    thickness, so the activation a = xi + dhat lies dhat beyond the
+    thickness.  paper_literal: the activation is the thickness itself (the
+    h of Eq. 1 and Eq. 4) and xi = thickness - dhat (Sec. 3.3: a = eta +
+    dhat); a thickness below dhat is an error."""
+    th, dhat = float(scene.thickness), float(scene.dhat)
+    if not paper_literal:
+        return th, dhat
+    if th - dhat < 0.0:
+        raise ValueError("paper_literal: thickness below dhat")
+    return th - dhat, dhat
+
+
+def ccd_bound(scene, topo, x, p, F_rest, mode="double", core_temp=True, dbar_min=0.0, cull_radius=0,
+              paper_literal=False):
     """Swept broad phase with boxes of x and x+p inflated by xi/2, class of each
     pair at x (offset xi for U, 0 for F and C; culled pairs of mode "kaldor"
     do not constrain the step), additive CCD per pair."""
-    xi, dhat = float(scene.thickness), float(scene.dhat)
+    xi, dhat = offsets(scene, paper_literal)
     off_u = 0.0 if mode == "single" else xi
     keys = broad_phase(topo, x, 0.5 * xi, p=p)
     m = keys.size
@@ -630,6 +651,7 @@ def bsr_dense(res: PassResult, n: int) -> np.ndarray:
     return A
 
 
-def total_energy(scene, x, mode="double", core_temp=True, topo=None, filt=None) -> float:
-    r = contact_pass(scene, mode=mode, core_temp=core_temp, ccd=False, x=x, topo=topo, filt=filt)
+def total_energy(scene, x, mode="double", core_temp=True, topo=None, filt=None, paper_literal=False) -> float:
+    r = contact_pass(scene, mode=mode, core_temp=core_temp, ccd=False, x=x, topo=topo, filt=filt,
+                     paper_literal=paper_literal)
     return r.energy

@@ -135,22 +135,27 @@ def ccd_step_noalloc(x, p, stencils, is_ee, offset, alpha, flags, stream=None):
     owns: x, p FP64 [3][n]; stencils int32 [m][4]; is_ee uint8 [m]; offset
     FP64 [m]; alpha FP64 [1] and flags int32 [1] receive the results.  Nothing
     is copied or converted here, so non-contiguous or mistyped tensors are
-    rejected rather than fixed."""
+    rejected rather than fixed.  Every tensor must live on one GPU; the call
+    runs with that GPU current (and on its current stream unless `stream` is
+    given)."""
     import torch
 
     def need(t, dtype, numel=None):
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
             raise TypeError(f"expected a contiguous CUDA {dtype} tensor")
+        if t.device != x.device:
+            raise ValueError(f"every tensor must be on {x.device}, got one on {t.device}")
         if numel is not None and t.numel() != numel:
             raise ValueError(f"expected {numel} elements, got {t.numel()}")
         return t.data_ptr()
 
     n = x.numel() // 3
     m = stencils.numel() // 4
-    args = (need(x, torch.float64, 3 * n), need(p, torch.float64, 3 * n), n,
-            need(stencils, torch.int32, 4 * m), need(is_ee, torch.uint8, m), need(offset, torch.float64, m),
-            m, need(alpha, torch.float64, 1), need(flags, torch.int32, 1), _stream_ptr(stream))
-    _check(lib().ccd_step_noalloc(*args), "ccd_step_noalloc")
+    with torch.cuda.device(x.device):
+        args = (need(x, torch.float64, 3 * n), need(p, torch.float64, 3 * n), n,
+                need(stencils, torch.int32, 4 * m), need(is_ee, torch.uint8, m), need(offset, torch.float64, m),
+                m, need(alpha, torch.float64, 1), need(flags, torch.int32, 1), _stream_ptr(stream))
+        _check(lib().ccd_step_noalloc(*args), "ccd_step_noalloc")
 
 
 def status_str(s: int) -> str:

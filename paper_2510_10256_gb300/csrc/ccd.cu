@@ -613,8 +613,9 @@ struct NaStart {
 };
 
 // first-step data of stencil q (the same arithmetic as accd_start); false for
-// a stencil with a vertex id outside [0, n) or an offset that is negative or
-// not finite
+// a stencil with a vertex id outside [0, n), an offset that is negative or
+// not finite, or positions / displacements that make its distance or motion
+// bound non-finite (such a stencil is reported, never silently passed)
 __device__ __forceinline__ bool na_start(const NaArgs& A, int64_t q, NaStart& S) {
   int v[4];
 #pragma unroll
@@ -641,9 +642,11 @@ __device__ __forceinline__ bool na_start(const NaArgs& A, int64_t q, NaStart& S)
   S.Q2 = sub3(P2, pb);
   S.Q3 = sub3(P3, pb);
   const double n0 = norm3(S.Q0), n1 = norm3(S.Q1), n2 = norm3(S.Q2), n3 = norm3(S.Q3);
+  // fmax drops a NaN operand, so a non-finite displacement is caught from the norms themselves
+  if (!isfinite(n0) || !isfinite(n1) || !isfinite(n2) || !isfinite(n3) || !isfinite(d)) return false;
   S.lp = S.ee ? xadd(fmax(n0, n1), fmax(n2, n3)) : xadd(n0, fmax(fmax(n1, n2), n3));
   S.g0 = (S.lp != 0.0) ? xsub(d, S.off) : 0.0;
-  return true;
+  return isfinite(S.lp) && isfinite(S.g0);
 }
 
 // one atomicMin per warp of the lanes' non-negative values (2.0 = none)
@@ -770,9 +773,11 @@ __global__ void k_na_final(const unsigned long long* __restrict__ scr, double* _
 constexpr int NA_MAX_DEVICES = 256;
 std::mutex g_na_mutex;
 unsigned long long* g_na_ptr[NA_MAX_DEVICES];
+int g_na_sms[NA_MAX_DEVICES];
 
-// address of the scratch array on the current device, looked up once per device
-cb_status na_scratch(unsigned long long** out) {
+// address of the scratch array on the current device and the device's SM
+// count, looked up once per device (valid until the device is reset)
+cb_status na_scratch(int* dev_out, unsigned long long** out, int* sms) {
   int dev = -1;
   CB_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= NA_MAX_DEVICES) return CB_ERR_ARG;
@@ -785,10 +790,27 @@ cb_status na_scratch(unsigned long long** out) {
               cudaGetErrorString(e));
       return CB_ERR_CUDA;
     }
+    int nsm = 0;
+    CB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    g_na_sms[dev] = nsm > 0 ? nsm : 1;
     g_na_ptr[dev] = (unsigned long long*)ptr;
   }
+  *dev_out = dev;
   *out = g_na_ptr[dev];
+  *sms = g_na_sms[dev];
   return CB_OK;
+}
+
+// true if p is device memory of `dev` or managed memory; a host pointer or
+// memory of another device is rejected before any kernel dereferences it
+bool na_on_device(const void* p, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -805,7 +827,13 @@ cb_status ccd_step_noalloc(const double* x_dev, const double* p_dev, int32_t n_v
   if (n_stencils > 0 && (n_verts < 1 || !x_dev || !p_dev || !stencils_dev || !is_ee_dev || !offset_dev))
     return CB_ERR_ARG;
   unsigned long long* scr = nullptr;
-  CB_TRY(na_scratch(&scr));
+  int dev = -1, nsm = 1;
+  CB_TRY(na_scratch(&dev, &scr, &nsm));
+  if (!na_on_device(alpha_dev, dev) || !na_on_device(flags_dev, dev)) return CB_ERR_ARG;
+  if (n_stencils > 0 && (!na_on_device(x_dev, dev) || !na_on_device(p_dev, dev) ||
+                         !na_on_device(stencils_dev, dev) || !na_on_device(is_ee_dev, dev) ||
+                         !na_on_device(offset_dev, dev)))
+    return CB_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   k_na_init<<<1, 32, 0, cb_count(st)>>>(scr);
   if (n_stencils > 0) {
@@ -819,7 +847,8 @@ cb_status ccd_step_noalloc(const double* x_dev, const double* p_dev, int32_t n_v
     A.p = p_dev;
     A.scr = scr;
     k_na_first<<<cb_grid(n_stencils, 128), 128, 0, cb_count(st)>>>(A);
-    const int gb = std::min<int64_t>(cb_grid(n_stencils, 128), 152 * 16);
+    // the band kernels stride over the list: up to 16 resident blocks of 128 threads per SM
+    const int gb = (int)std::min<int64_t>(cb_grid(n_stencils, 128), (int64_t)nsm * 16);
     k_na_band<<<gb, 128, 0, cb_count(st)>>>(A, 0);
     k_na_band<<<gb, 128, 0, cb_count(st)>>>(A, 1);
   }

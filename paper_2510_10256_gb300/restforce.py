@@ -49,8 +49,9 @@ def shell_at_rest(nx: int, size: float = 4.0, thickness: float = 1.0, dhat: floa
     return S.flat_grid(nx=nx, L=size / (nx - 1), thickness=thickness, dhat=dhat)
 
 
-def rest_force(sc: S.Scene, mode: str) -> dict:
-    """Energy, force norm and active pairs of the contact pass at x = rest."""
+def rest_force(sc: S.Scene, mode: str, keep_grad: bool = False) -> dict:
+    """Energy, force norm and active pairs of the contact pass at x = rest
+    (keep_grad: also the gradient itself, [3][n] on the host)."""
     import torch
     from .contact import ContactScene
     dev = torch.device("cuda:0")
@@ -66,6 +67,8 @@ def rest_force(sc: S.Scene, mode: str) -> dict:
     out = {"energy": float(energy.item()), "force_norm": float(torch.linalg.vector_norm(grad).item()),
            "force_max": float(grad.abs().max().item()), "active": int(st["n_active"]),
            "filtered": int(st["n_filtered"]), "candidates": int(st["n_candidates"])}
+    if keep_grad:
+        out["grad"] = grad.cpu().numpy()
     cs.close()
     return out
 

@@ -79,8 +79,12 @@ def test_rod_batch_64_full_size():
     every member against its own oracle."""
     scenes = S.rod_batch()
     res = run_gpu_batch(scenes)
-    total = 0
+    total = compared = skipped = 0
     for sc, g in zip(scenes, res):
         rep = compare(sc, g, O.contact_pass(sc))
         total += rep["C"]
+        compared += rep["bsr_compared"]
+        skipped += rep["bsr_blocks_skipped"]
+    print("rod batch 64", {"candidates": total, "bsr_compared": compared, "bsr_blocks_skipped": skipped})
     assert total > 5_000_000
+    assert compared > 0 and skipped <= 1e-4 * compared, (compared, skipped)

@@ -21,8 +21,9 @@ def _built():
 
 def _pair(sc, mode="double", **kw):
     g = run_gpu(sc, mode=mode, **kw)
-    o = O.contact_pass(sc, mode=mode, core_temp=kw.get("core_temp", True))
-    return compare(sc, g, o, mode=mode), g, o
+    lit = kw.get("paper_literal", False)
+    o = O.contact_pass(sc, mode=mode, core_temp=kw.get("core_temp", True), paper_literal=lit)
+    return compare(sc, g, o, mode=mode, paper_literal=lit), g, o
 
 
 @pytest.mark.parametrize("seed", range(6))
@@ -45,6 +46,24 @@ def test_modes_shell(mode):
 @pytest.mark.parametrize("mode", ["double", "single", "off"])
 def test_modes_rod(mode):
     _pair(S.woven_patch(n_warp=2, n_weft=2, nseg=48), mode=mode)
+
+
+@pytest.mark.parametrize("make", [lambda: S.woven_patch(n_warp=2, n_weft=2, nseg=48),
+                                  lambda: S.tiny_rods(2), lambda: S.tiny_shell(3, nx=6),
+                                  lambda: S.pleated_sheet(nx=24)])
+@pytest.mark.parametrize("mode", ["double", "single"])
+def test_paper_literal_mapping(make, mode):
+    """CB_THICK_PAPER_LITERAL (activation = thickness, offset = thickness -
+    dhat; Sec. 3.1 / 3.3, Eq. 1 / 4) against the oracle's paper_literal pass:
+    a smaller activation changes the candidate, filtered, class-C and active
+    sets, the offsets of the barrier and of the CCD step."""
+    sc = make()
+    rep, g, o = _pair(sc, mode=mode, paper_literal=True)
+    st = g["stats"]
+    assert st["offset"] == sc.thickness - sc.dhat and st["activation"] == sc.thickness
+    assert rep["C"] > 0 and rep["active"] > 0 and rep["bsr_compared"] > 0
+    # the default mapping really is different on this scene
+    assert not np.array_equal(O.contact_pass(sc, mode=mode, ccd=False).C, o.C)
 
 
 def test_no_core_temp_reports_penetration():
@@ -122,7 +141,10 @@ def test_pleated_sheet_full_size():
     full brute-force oracle: every candidate, class, active pair, distance,
     gradient entry, BSR block and the step bound."""
     rep, g, o = _pair(S.pleated_sheet())
+    print("pleated 256x256", rep)
     assert rep["C"] > 10_000_000 and rep["active"] > 500_000
+    # the BSR was compared, all but the blocks of tie-band pairs
+    assert rep["bsr_compared"] > 1_000_000 and rep["bsr_blocks_skipped"] <= 1e-4 * rep["nnzb"], rep
 
 
 @pytest.mark.slow
@@ -130,7 +152,9 @@ def test_graded_disk_full_size():
     """Graded twisted disk (~200k triangles, 0.1-4 mm edges) against the full
     oracle."""
     rep, g, o = _pair(S.graded_disk())
+    print("graded disk", rep)
     assert rep["F"] > 0
+    assert rep["bsr_compared"] > 0 and rep["bsr_blocks_skipped"] <= 1e-4 * rep["nnzb"], rep
 
 
 @pytest.mark.parametrize("factor,block", [(0.5, 128), (2.0, 64), (32.0, 128)])

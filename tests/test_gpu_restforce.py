@@ -40,8 +40,13 @@ def test_rest_force_sweep():
 def test_rest_force_matches_oracle(kind):
     sc = R.rod_at_rest(40) if kind == "rod" else R.shell_at_rest(17)
     for mode in ("double", "off"):
-        g = R.rest_force(sc, mode)
-        sc_rest = sc
-        o = O.contact_pass(sc_rest, mode=mode, ccd=False)
+        g = R.rest_force(sc, mode, keep_grad=True)
+        o = O.contact_pass(sc, mode=mode, ccd=False)
         assert abs(g["energy"] - o.energy) <= 1e-9 * max(abs(o.energy), 1e-300), (mode, g["energy"], o.energy)
-        assert abs(g["force_norm"] - float(np.linalg.norm(o.grad))) <= 1e-9 * max(float(np.linalg.norm(o.grad)), 1e-300)
+        # the rest force element by element, within the parity tolerance of each entry
+        err = np.abs(g["grad"] - o.grad)
+        assert np.all(err <= 1e-9 * o.grad_abs + 1e-30), (mode, float((err / (o.grad_abs + 1e-300)).max()))
+        if mode == "double":
+            assert np.all(g["grad"] == 0.0) and np.all(o.grad == 0.0)
+        else:
+            assert np.count_nonzero(o.grad) > 0

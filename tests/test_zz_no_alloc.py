@@ -1,16 +1,23 @@
-"""ccd_step_noalloc (fixed device scratch, no allocation) against ccd_step.
+"""ccd_step_noalloc (fixed device scratch, no allocation) against ccd_step
+and the oracle.
 
-The stencil list is the scene's own CCD candidate set, rebuilt on the host
-from the pair keys and the edge numbering the C ABI documents; each stencil
-keeps the offset of its class.  The step bound must agree with ccd_step's
-within the parity tolerance of alpha, on consecutive calls (the scratch is
-reused, so every call must start from cleared accumulators).
+Some callers cannot allocate device memory while they run (a solver that
+hands its whole device budget to its own pool, a loop in which an allocation
+could stall the device); ccd_step_noalloc serves them from one fixed scratch
+array.  The stencil list is the scene's own CCD candidate set, rebuilt on the
+host from the pair keys and the edge numbering the C ABI documents; each
+stencil keeps the offset of its class.  The step bound must agree with
+ccd_step's within the parity tolerance of alpha, and never exceed the
+oracle's (alpha <= alpha_oracle, alpha_oracle - alpha <= 1e-9), on
+consecutive calls (the scratch is reused, so every call must start from
+cleared accumulators).
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2510_10256_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -91,9 +98,10 @@ def test_noalloc_matches_ccd_step_on_consecutive_calls():
     cases = [S.pleated_sheet(nx=24), S.woven_patch(n_warp=2, n_weft=2, nseg=48), S.tiny_shell(3),
              S.tiny_rods(2)]
     refs = [_reference(sc) for sc in cases]
+    orcs = [O.contact_pass(sc).alpha for sc in cases]
     assert len({a for a, _ in refs}) > 1, "cases should have different step bounds"
     assert any(a < 1.0 for a, _ in refs)
-    for alpha_ref, inp in refs:
+    for (alpha_ref, inp), alpha_orc in zip(refs, orcs):
         assert inp["st"].shape[0] > 0
         for _ in range(2):
             n0 = contact.kernel_launches()
@@ -101,6 +109,7 @@ def test_noalloc_matches_ccd_step_on_consecutive_calls():
             assert contact.kernel_launches() - n0 == 5
             assert f == 0
             assert a <= 1.0 and abs(a - alpha_ref) <= 1e-9, (a, alpha_ref)
+            assert a <= alpha_orc and alpha_orc - a <= 1e-9, (a, alpha_orc)
 
 
 def test_noalloc_empty_bad_full_and_oversized_inputs():
@@ -116,6 +125,24 @@ def test_noalloc_empty_bad_full_and_oversized_inputs():
     bad["st"][0, 2] = inp["x"].shape[1]
     a, f = _noalloc(bad)
     assert a == 1.0 and f & contact.NOALLOC_BAD_STENCIL
+    # a non-finite displacement of a stencil vertex: reported, not passed as alpha = 1 silently
+    v = int(inp["st"][0, 1].item())
+    pn = inp["p"].clone()
+    pn[0, v] = float("nan")
+    a, f = _noalloc(dict(inp, p=pn, st=inp["st"][:1], ee=inp["ee"][:1], off=inp["off"][:1]))
+    assert f & contact.NOALLOC_BAD_STENCIL
+    # ... the remaining stencils still bound the step, and the flag says one was skipped
+    a, f = _noalloc(dict(inp, p=pn))
+    assert f & contact.NOALLOC_BAD_STENCIL and a <= 1.0
+    # an output in (device-reachable) pinned host memory is rejected before any launch
+    host_alpha = torch.zeros(1, dtype=torch.float64).pin_memory()
+    host_flags = torch.zeros(1, dtype=torch.int32).pin_memory()
+    n0 = contact.kernel_launches()
+    st = contact.lib().ccd_step_noalloc(inp["x"].data_ptr(), inp["p"].data_ptr(), inp["x"].shape[1],
+                                        inp["st"].data_ptr(), inp["ee"].data_ptr(), inp["off"].data_ptr(),
+                                        m, host_alpha.data_ptr(), host_flags.data_ptr(),
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == contact.CB_ERR_ARG and contact.kernel_launches() == n0
     # exactly the maximum: the candidate list repeated
     M = contact.NOALLOC_MAX_STENCILS
     rep = (M + m - 1) // m
