@@ -549,15 +549,19 @@ def contact_pass(scene, mode: str = "double", core_temp: bool = True, project: b
     np.add.at(grad.reshape(-1), gi, g.reshape(-1))
     # tolerance scale: |contribution|, floored at 1e-4 of the pair's largest
     # entry (rounding of a pair's derivatives is relative to its norm)
-    # conditioning of b', b'' in d near the activation (relative errors grow like
-    # kappa = y / (dhat_p - y)); the floor grows with it
+    # conditioning of b', b'' in the computed distance d near the activation:
+    # Eq. 2 is evaluated at y = d - xi_p, so a relative rounding u of d moves y
+    # by u d, b'' (~ dhat_p - y) relatively by u kappa and b' (~ (dhat_p -
+    # y)^2) by 2 u kappa, kappa = d / (dhat_p - y) (= y / (dhat_p - y) at
+    # offset 0).  The floor covers about one ulp of d on either side times the
+    # gradient's 2 kappa: 1e-9 f_p >= 2 kappa * 2.2e-16
     ad_xi = np.where(akl == KLASS_U, 0.0 if mode == "single" else xi, 0.0)
     fw = (dbar_comp[topo.comp[st[:, 0]]] if dbar_comp is not None
           else np.full(na, dbar_min if np.isfinite(dbar_min) else 0.0))
     ad_dh = np.where(akl == KLASS_F, fw, np.where((akl == KLASS_C) | (mode == "single"), a, dhat))
     ay = ad - ad_xi
-    kappa_p = np.maximum(1.0, ay / np.maximum(ad_dh - ay, 1e-300)) if na else np.zeros(0)
-    ffac = np.maximum(1e-4, 1e-7 * kappa_p)
+    kappa_p = np.maximum(1.0, ad / np.maximum(ad_dh - ay, 1e-300)) if na else np.zeros(0)
+    ffac = np.maximum(1e-4, 5e-7 * kappa_p)
     gfloor = (ffac * np.abs(g).max(axis=1))[:, None] if na else np.zeros((0, 1))
     np.add.at(grad_abs.reshape(-1), gi, np.maximum(np.abs(g), gfloor).reshape(-1))
     rows = np.repeat(st, 4, axis=1).reshape(-1)                  # r of (i, j)
