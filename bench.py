@@ -41,6 +41,7 @@ HESS_FLOPS = {"prep": 549.1, "face": 11471.0, "pe_frame": 1091.0, "pe": 11471.0 
 # DRAM bytes (read + write) of the stage-(d) kernels per active pair, from the
 # same capture (135.3 MB); traffic grows in proportion to the active pairs
 HESS_DRAM_BYTES_PER_ACTIVE = 135.3e6 / 195263
+HESS_TRAFFIC_SOURCE = "ncu dram__bytes_read+write of the 128x128 case, scaled by active pairs"
 
 
 def hess_flops(st) -> float:
@@ -90,6 +91,7 @@ def stage_roofline(st: dict, med: list, scenes) -> dict:
       a  24n + 12T + 8E + 8|C|          (positions, topology, candidate keys)
       b  16|C| + table                  (keys in, classes out; rods 12E, shells 4|F_rest|)
       cd 8|C| + 24n + 8|A| + 24n + 76 nnzb + 4(n+1)  (keys+x in; active, gradient, BSR out)
+         of which c: 8|C| + 24n (keys, x in) and d: 8|A| + 24n + 76 nnzb + 4(n+1)
       e  8|C_ccd| + 48n + 8             (keys, x, p in; alpha out)"""
     n = sum(sc.n for sc in scenes)
     T = sum(sc.tris.shape[1] for sc in scenes if sc.kind == "shell")
@@ -100,11 +102,15 @@ def stage_roofline(st: dict, med: list, scenes) -> dict:
     by = {"contact_build": 24 * n + 12 * T + 8 * E + 8 * C,
           "contact_filter": 16 * C + table,
           "barrier_eval": 8 * C + 24 * n + 8 * A + 24 * n + 76 * nnzb + 4 * (n + 1),
+          "distances_c": 8 * C + 24 * n,
+          "assembly_d": 8 * A + 24 * n + 76 * nnzb + 4 * (n + 1),
           "ccd_step": 8 * Cc + 48 * n + 8}
     hbm = _peaks().get("hbm_gbs")
     out = {"hbm_peak_gbs": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)" if hbm else None}
-    for i, k in enumerate(("contact_build", "contact_filter", "barrier_eval", "ccd_step")):
-        ms = med[i]
+    idx = {"contact_build": 0, "contact_filter": 1, "barrier_eval": 2, "ccd_step": 3, "distances_c": 5,
+           "assembly_d": 6}
+    for k, i in idx.items():
+        ms = med[i] if i < len(med) else 0.0
         gbs = by[k] / (ms / 1000.0) / 1e9 if ms > 0 else None
         out[k] = {"bytes": int(by[k]), "ms": ms, "gbs": gbs, "hbm_frac": (gbs / hbm) if (gbs and hbm) else None}
     hess = med[4]
@@ -256,7 +262,7 @@ def run_reference(args, rank: int, world: int):
         r = O.contact_pass(sc)
         times.append(time.perf_counter() - t0)
         nc = r.C.size
-    ms = 1000.0 * statistics.mean(times)
+    ms = 1000.0 * statistics.median(times)
     val = nc / (ms / 1000.0)
     cores = O.lib().orc_num_threads()
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
@@ -348,7 +354,7 @@ def bench_batch(args, rank, world, local, dist):
     launches = CT.kernel_launches() - l0
     p_ms = _timed_steps(run_plain, args.steps, flush, stream) if not args.no_plain else [float("nan")]
     clk = clocks.stop()
-    ms, pms = statistics.mean(b_ms), statistics.mean(p_ms)
+    ms, pms = statistics.median(b_ms), statistics.median(p_ms)
     ms, pms = max_over_ranks([ms, pms], dist, dev)
     # end to end: pinned host x, p in; energy, alpha, gradient out
     hx, hp = torch.from_numpy(hx_np).pin_memory(), torch.from_numpy(hp_np).pin_memory()
@@ -368,7 +374,7 @@ def bench_batch(args, rank, world, local, dist):
     if rank != 0:
         return
     hess_ms = statistics.mean(s[4] for s in stage)
-    med = [statistics.median(s[i] for s in stage) for i in range(5)]
+    med = [statistics.median(s[i] for s in stage) for i in range(7)]
     na = int(st["n_active"])
     achieved = hess_flops(st) / (hess_ms / 1000.0) / 1e12 if hess_ms > 0 else 0.0
     sizes = [sc.n for sc in scenes]
@@ -387,8 +393,7 @@ def bench_batch(args, rank, world, local, dist):
             "fp32_broad_phase": {"candidates_fp32": st["n_candidates_fp32"], "candidates": n_cand,
                                  "superset_ratio": st["n_candidates_fp32"] / max(1, n_cand),
                                  "fp64_decided": st["n_fp64_decided"]},
-            "stage_ms": {"contact_build": med[0], "contact_filter": med[1], "barrier_eval": med[2],
-                         "ccd_step": med[3], "hessian_kernel": med[4]},
+            "stage_ms": _stage_dict(med),
             "roofline": {"bound": "alu", "kernel": "k_hess_prep + k_hess_proj<9> + k_hess_proj_pe (FP64 stage d)", "achieved": achieved,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                          "traffic": None, "flops_per_pass": hess_flops(st), "kernel_ms": hess_ms,
@@ -404,68 +409,126 @@ def bench_batch(args, rank, world, local, dist):
     print(json.dumps(line), flush=True)
 
 
-def bench_serve(args, rank, world, local, dist):
-    """Served request stream: Poisson arrivals, each request a sequence of
-    contact steps on its own scene (rods 5k-200k vertices, shells 10k-500k
-    triangles, half and half), admitted under an HBM budget and advanced by
-    continuous batching (paper_2510_10256_gb300.serve)."""
-    import torch
+def _serve_config(pool, n, rate, steps, budget_gb, slots) -> dict:
+    rods = [s.n for s in pool if s.kind == "rod"]
+    tris = [s.tris.shape[1] for s in pool if s.kind == "shell"]
+    return {"workload": f"served stream: {n} Poisson requests at {rate:g}/s, {steps} contact steps each, "
+                        f"rods {min(rods)}-{max(rods)} vertices / shells {min(tris)}-{max(tris)} triangles "
+                        f"(pool of {len(pool)} seeded scenes), half and half",
+            "hbm_budget_gb": budget_gb, "slots": slots}
+
+
+def serve_measure(eng, pool, n, rate, steps, budget_gb, slots, seed, plain=False) -> dict:
+    """One served stream (continuous batching, paper_2510_10256_gb300.serve) or
+    its plain form (the same trace FIFO, one single-scene pass per step):
+    throughput and per-step latency, with the kernel launches it made."""
     from paper_2510_10256_gb300 import contact as CT
+    from paper_2510_10256_gb300.serve import Server, poisson_requests, run_plain
+    reqs = poisson_requests(pool, n, rate, steps, seed=seed)
+    l0 = CT.kernel_launches()
+    if plain:
+        rep = run_plain(eng, reqs)
+    else:
+        rep = Server(eng, hbm_budget=int(budget_gb * (1 << 30)), max_slots=slots).run(reqs)
+    launches = CT.kernel_launches() - l0
+    lat = rep["step_latency_ms"]
+    return {"form": "plain: FIFO, one request at a time, each step a single-scene pass" if plain else
+            "served: continuous batching under the HBM budget",
+            "rate_per_s": rate, "requests": rep["requests"], "rejected": len(rep["rejected"]),
+            "steps": rep["steps"], "pairs": rep["pairs"], "wall_s": rep["wall_s"],
+            "pairs_per_s": rep["pairs"] / rep["wall_s"] if rep["wall_s"] > 0 else 0.0,
+            "steps_per_s": rep["steps_per_s"], "iterations": rep["iterations"],
+            "max_resident": rep["max_resident"], "peak_reserved_gb": rep["peak_reserved_bytes"] / 2 ** 30,
+            "latency_ms": {"step_p50": lat["p50"], "step_p99": lat["p99"], "step_mean": lat["mean"],
+                           "queue_p50": rep["queue_delay_ms"]["p50"], "queue_p99": rep["queue_delay_ms"]["p99"],
+                           "load_p50": rep["load_ms"]["p50"], "load_p99": rep["load_ms"]["p99"]},
+            "gpu_launches": int(launches), "_h2d": sum(
+                8 * r.scene.rest.size + 8 * r.scene.x.size + 4 * (r.scene.tris.size if r.scene.tris is not None
+                                                                  else r.scene.rod_ptr.size) for r in reqs)}
+
+
+def _serve_engine(local, warmup):
+    import torch
     from paper_2510_10256_gb300 import scenes as S
-    from paper_2510_10256_gb300.serve import DeviceEngine, Server, poisson_requests
+    from paper_2510_10256_gb300.serve import DeviceEngine
     pool = S.serve_pool()
-    reqs = poisson_requests(pool, args.requests, args.rate, args.req_steps, seed=S.BASE_SEED + 5 + rank)
     eng = DeviceEngine(torch.device("cuda", local))
     small = sorted(pool, key=lambda sc: sc.n)
     sample = [next(sc for sc in small if sc.kind == k) for k in ("rod", "shell")]
     sample += [next(sc for sc in small if sc.kind == "shell" and sc.name != sample[1].name)]
-    for _ in range(max(1, args.warmup // len(sample))):
+    bpv = None
+    for _ in range(max(1, warmup // len(sample))):
         bpv = eng.calibrate(sample)
     torch.cuda.synchronize()
+    return pool, eng, bpv
+
+
+def serve_suite(args, local, seed, n_req, sustain_rate, sustain_n) -> dict:
+    """The served stream at the configured arrival rate, its plain form on the
+    same trace, and the served stream at an arrival rate one GPU sustains."""
+    pool, eng, bpv = _serve_engine(local, args.warmup)
+    try:
+        served = serve_measure(eng, pool, n_req, args.rate, args.req_steps, args.budget_gb, args.slots, seed)
+        plain = serve_measure(eng, pool, n_req, args.rate, args.req_steps, args.budget_gb, args.slots, seed,
+                              plain=True)
+        sustained = serve_measure(eng, pool, sustain_n, sustain_rate, args.req_steps, args.budget_gb, args.slots,
+                                  seed + 1)
+    finally:
+        eng.close()
+    for r in (served, plain, sustained):
+        r.pop("_h2d", None)
+    return {"config": dict(_serve_config(pool, n_req, args.rate, args.req_steps, args.budget_gb, args.slots),
+                           bytes_per_vertex_model=bpv),
+            "served": served, "plain": plain, "served_over_plain": served["pairs_per_s"] / plain["pairs_per_s"]
+            if plain["pairs_per_s"] > 0 else None, "sustained": sustained}
+
+
+def bench_serve(args, rank, world, local, dist):
+    """Served request stream: Poisson arrivals, each request a sequence of
+    contact steps on its own scene (rods 5k-200k vertices, shells 10k-500k
+    triangles, half and half), admitted under an HBM budget and advanced by
+    continuous batching (paper_2510_10256_gb300.serve); beside it the same
+    trace in its plain form (FIFO, one single-scene pass per step)."""
+    import torch
+    from paper_2510_10256_gb300 import scenes as S
+    pool, eng, bpv = _serve_engine(local, args.warmup)
     clocks = ClockSampler(local)
     clocks.start()
     if dist:
         dist.barrier()
-    l0 = CT.kernel_launches()
-    rep = Server(eng, hbm_budget=int(args.budget_gb * (1 << 30)), max_slots=args.slots).run(reqs)
-    launches = CT.kernel_launches() - l0
+    seed = S.BASE_SEED + 5 + rank
+    rep = serve_measure(eng, pool, args.requests, args.rate, args.req_steps, args.budget_gb, args.slots, seed)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    wall = rep["wall_s"]
-    wall = max_over_ranks([wall], dist, torch.device("cuda", local))[0]
+    wall = max_over_ranks([rep["wall_s"]], dist, torch.device("cuda", local))[0]
+    plain = None
+    if not args.no_plain:
+        plain = serve_measure(eng, pool, args.requests, args.rate, args.req_steps, args.budget_gb, args.slots, seed,
+                              plain=True)
+        plain.pop("_h2d", None)
     eng.close()
     if rank != 0:
         return
-    served = [r for r in reqs if r.rid not in set(rep["rejected"])]
-    h2d = sum(8 * r.scene.rest.size + 8 * r.scene.x.size + 4 * (r.scene.tris.size if r.scene.tris is not None else
-                                                                  r.scene.rod_ptr.size) for r in served)
+    h2d = rep.pop("_h2d")
     steps = max(1, rep["steps"])
     value = world * rep["pairs"] / wall
-    lat = rep["step_latency_ms"]
+    lat = rep["latency_ms"]
     line = {"metric": "served contact pairs/s (filter+barrier+Hessian+CCD); p50/p99 step latency", "value": value,
             "unit": UNIT, "n_gpus": world, "steps": rep["steps"], "warmup": max(3, args.warmup),
-            "ms_per_step": lat["mean"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": lat["step_p50"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"served stream: {args.requests} Poisson requests at {args.rate:g}/s, "
-                                   f"{args.req_steps} contact steps each, rods {min(s.n for s in pool if s.kind == 'rod')}-"
-                                   f"{max(s.n for s in pool if s.kind == 'rod')} vertices / shells "
-                                   f"{min(s.tris.shape[1] for s in pool if s.kind == 'shell')}-"
-                                   f"{max(s.tris.shape[1] for s in pool if s.kind == 'shell')} triangles (pool of "
-                                   f"{len(pool)} seeded scenes), half and half",
-                       "hbm_budget_gb": args.budget_gb, "slots": args.slots, "bytes_per_vertex_model": bpv,
-                       "l2": "not flushed: every iteration streams pair lists far larger than L2",
-                       "parallelism": f"replicas x{world}"},
-            "latency_ms": {"step_p50": lat["p50"], "step_p99": lat["p99"],
-                           "queue_p50": rep["queue_delay_ms"]["p50"], "queue_p99": rep["queue_delay_ms"]["p99"],
-                           "load_p50": rep["load_ms"]["p50"], "load_p99": rep["load_ms"]["p99"]},
-            "served": {"wall_s": wall, "requests": rep["requests"], "rejected": len(rep["rejected"]),
-                       "steps_per_s": rep["steps_per_s"], "iterations": rep["iterations"],
-                       "max_resident": rep["max_resident"], "peak_reserved_gb": rep["peak_reserved_bytes"] / 2 ** 30},
+            "config": dict(_serve_config(pool, args.requests, args.rate, args.req_steps, args.budget_gb, args.slots),
+                           bytes_per_vertex_model=bpv,
+                           l2="not flushed: every iteration streams pair lists far larger than L2",
+                           parallelism=f"replicas x{world}"),
+            "latency_ms": lat, "served": rep,
+            "plain": plain, "served_over_plain": (rep["pairs_per_s"] / plain["pairs_per_s"])
+            if plain and plain["pairs_per_s"] > 0 else None,
             "roofline": None,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": 16,
                     "note": "the served stream is itself end to end: scenes uploaded from host memory at "
                             "admission, step results read back every step"},
-            "clocks": clk, "gpu_launches": int(launches)}
+            "clocks": clk, "gpu_launches": rep["gpu_launches"]}
     if not args.no_cpu_baseline and world == 1:
         try:
             line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_nx)
@@ -626,9 +689,16 @@ def main():
     ap.add_argument("--cpu-nx", type=int, default=128, help="grid size of the oracle baseline sample")
     ap.add_argument("--ref-nx", type=int, default=96, help="grid size of a reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-plain", action="store_true", help="knit64: skip the one-scene-per-launch arm")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="knit64 / serve: skip the one-scene-per-launch (plain) arm")
     ap.add_argument("--no-tune", action="store_true", help="keep the default broad-phase knobs")
     ap.add_argument("--mollifier", action="store_true", help="single-scene workloads: IPC's edge-edge mollifier")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="pleated: skip the graded disk and the served stream that the default line carries")
+    ap.add_argument("--extra-requests", type=int, default=100, help="default line: requests of each served stream")
+    ap.add_argument("--sustain-rate", type=float, default=10.0,
+                    help="default line: arrival rate (requests/s) of the sustained served stream")
+    ap.add_argument("--sustain-requests", type=int, default=100)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -662,10 +732,67 @@ def main():
     if args.workload == "friction":
         bench_friction(args, rank, world, local, dist)
         return
-    sc, desc = _workload(args.workload, reduced_nx=args.nx or None)
+    res = measure_single(args, args.workload, args.steps, local, dist, nx=args.nx or None,
+                         mollifier=args.mollifier)
+    extras = (args.workload == "pleated" and not args.nx and not args.no_extras and not args.mollifier)
+    extra = {}
+    if extras:
+        # the larger single scene of the metric's configs, and the served stream
+        g = measure_single(args, "graded", max(5, args.steps // 2), local, dist, clocks=False)
+        extra["graded"] = _single_summary(g, world)
+        from paper_2510_10256_gb300 import scenes as S
+        extra["serve"] = serve_suite(args, local, S.BASE_SEED + 5 + rank, args.extra_requests, args.sustain_rate,
+                                     args.sustain_requests)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = _single_line(args, res, world)
+    if extras:
+        sv = extra["serve"]["served"]
+        line["latency_ms"] = {"step_p50": sv["latency_ms"]["step_p50"], "step_p99": sv["latency_ms"]["step_p99"],
+                              "source": "the served stream in extra.serve.served"}
+        line["extra"] = extra
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_nx)
+            if args.workload == "pleated":
+                line["cpu_baseline"]["one_core"] = one_core_baselines()
+        except Exception as e:  # the baseline is context; never fail the bench on it
+            line["cpu_baseline"] = {"value": None, "error": str(e)}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def one_core_baselines() -> dict:
+    """The oracle on one host core: the full woven rod patch and the pleated
+    recipe at 64 x 64 (brute force, so a full 256 x 256 pass would take
+    minutes)."""
+    import oracle as O
+    from paper_2510_10256_gb300 import scenes as S
+    prev = O.set_num_threads(1)
+    try:
+        out = {}
+        for key, sc, what in (("woven", S.woven_patch(), "one oracle pass on the full woven patch, 1 core"),
+                              ("pleated", S.pleated_sheet(nx=64), "one oracle pass on the pleated recipe at 64x64, 1 core")):
+            out[key] = _oracle_sample([sc], what)
+        return out
+    finally:
+        O.set_num_threads(prev)
+
+
+def measure_single(args, name, steps, local, dist, nx=None, mollifier=False, clocks=True) -> dict:
+    """One scene of the named workload: autotuned broad-phase knobs, W warm-up
+    passes, then `steps` passes timed on the device (L2 flushed before each),
+    the per-stage times of each pass, and an end-to-end leg through the C ABI
+    with host buffers (copies inside the timed region)."""
+    import torch
+    from paper_2510_10256_gb300 import contact as CT
+    sc, desc = _workload(name, reduced_nx=nx)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    cs = CT.ContactScene.from_scene(sc, mollifier=args.mollifier)
+    cs = CT.ContactScene.from_scene(sc, mollifier=mollifier)
     x = torch.from_numpy(sc.x).to(dev)
     p = torch.from_numpy(sc.p).to(dev)
     energy = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -678,18 +805,17 @@ def main():
         cs.run_pass(x, p, energy, grad, alpha)
     torch.cuda.synchronize()
     st = cs.stats()
-    n_cand = st["n_candidates"]
-
     # ---- device-resident timed region
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     stage = []
-    clocks = ClockSampler(local)
-    clocks.start()
+    clk_s = ClockSampler(local) if clocks else None
+    if clk_s:
+        clk_s.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     l0 = CT.kernel_launches()
-    for k in range(args.steps):
+    for k in range(steps):
         flush.zero_()
         ev[k][0].record(stream)
         cs.run_pass(x, p, energy, grad, alpha)
@@ -699,20 +825,17 @@ def main():
     launches = CT.kernel_launches() - l0
     if dist:
         dist.barrier()
-    clk = clocks.stop()
+    clk = clk_s.stop() if clk_s else None
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = statistics.mean(step_ms)
-    ms = max_over_ranks([ms], dist, dev)[0]
-    value = world * n_cand / (ms / 1000.0)
+    ms = max_over_ranks([statistics.median(step_ms)], dist, dev)[0]
     status = cs.sync_status()
-
     # ---- end to end through the C ABI with host buffers (copies timed)
     hx = torch.from_numpy(sc.x).pin_memory()
     hp = torch.from_numpy(sc.p).pin_memory()
     he = torch.zeros(1, dtype=torch.float64).pin_memory()
     ha = torch.zeros(1, dtype=torch.float64).pin_memory()
     hg = torch.zeros(3, sc.n, dtype=torch.float64).pin_memory()
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = max(3, steps // 2)
     torch.cuda.synchronize()
     e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
     for k in range(e2e_steps):
@@ -726,19 +849,39 @@ def main():
         hg.copy_(grad, non_blocking=True)
         e_ev[k][1].record(stream)
         stream.synchronize()
-    e2e_ms = statistics.mean(a.elapsed_time(b) for a, b in e_ev)
-    e2e_ms = max_over_ranks([e2e_ms], dist, dev)[0]
-    h2d = 2 * 3 * sc.n * 8
-    d2h = 8 + 8 + 3 * sc.n * 8
+    e2e_ms = max_over_ranks([statistics.median(a.elapsed_time(b) for a, b in e_ev)], dist, dev)[0]
+    cs.close()
+    return {"sc": sc, "desc": desc, "st": st, "step_ms": step_ms, "ms": ms, "stage": stage, "e2e_ms": e2e_ms,
+            "launches": launches, "tuning": tuning, "clocks": clk, "status": status, "steps": steps,
+            "h2d": 2 * 3 * sc.n * 8, "d2h": 8 + 8 + 3 * sc.n * 8}
 
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        cs.close()
-        return
-    # ---- roofline of the dominant kernel (FP64 barrier/Hessian kernel)
-    med = [statistics.median(s[i] for s in stage) for i in range(5)]
-    hess_ms = statistics.mean(s[4] for s in stage)
+
+def _stage_dict(med) -> dict:
+    return {"contact_build": med[0], "contact_filter": med[1], "barrier_eval": med[2], "ccd_step": med[3],
+            "hessian_kernel": med[4], "distances_c": med[5], "assembly_d": med[6]}
+
+
+def _single_summary(r, world) -> dict:
+    st = r["st"]
+    med = [statistics.median(s[i] for s in r["stage"]) for i in range(7)]
+    return {"workload": r["desc"], "value": world * st["n_candidates"] / (r["ms"] / 1000.0), "unit": UNIT,
+            "ms_per_step": r["ms"], "ms_mean": statistics.mean(r["step_ms"]), "steps": r["steps"],
+            "candidates": int(st["n_candidates"]), "filtered": st["n_filtered"], "active": int(st["n_active"]),
+            "ccd_pairs": st["n_ccd"], "nnzb": st["nnzb"], "stage_ms": _stage_dict(med),
+            "stage_roofline": stage_roofline(st, med, [r["sc"]]),
+            "e2e": {"value": world * st["n_candidates"] / (r["e2e_ms"] / 1000.0), "unit": UNIT,
+                    "ms_per_step": r["e2e_ms"], "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+            "tuning": r["tuning"], "gpu_launches": int(r["launches"]), "status": r["status"]}
+
+
+def _single_line(args, r, world) -> dict:
+    """The JSON line of a single-scene workload, with the roofline of the
+    dominant (FP64 stage-d) kernels."""
+    from paper_2510_10256_gb300 import contact as CT
+    st, sc = r["st"], r["sc"]
+    n_cand = st["n_candidates"]
+    med = [statistics.median(s[i] for s in r["stage"]) for i in range(7)]
+    hess_ms = statistics.mean(s[4] for s in r["stage"])
     na = st["n_active"]
     achieved = hess_flops(st) / (hess_ms / 1000.0) / 1e12 if hess_ms > 0 else 0.0
     try:
@@ -746,43 +889,34 @@ def main():
         fp32_meas = CT.measure_fma_tflops(False, iters=65536)
     except Exception:
         fp64_meas = fp32_meas = None
-    roofline = {"bound": "alu", "kernel": "k_hess_prep + k_hess_proj<9> + k_hess_proj_pe (FP64 stage d)", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+    roofline = {"bound": "alu", "kernel": "k_hess_prep + k_hess_proj<9> + k_hess_proj_pe (FP64 stage d)",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_fp64_fma_measured": fp64_meas, "peak_fp32_fma_measured": fp32_meas,
-                "traffic": HESS_DRAM_BYTES_PER_ACTIVE * na,
-                "traffic_source": "ncu dram__bytes_read+write of the 128x128 case, scaled by active pairs",
+                "traffic": HESS_DRAM_BYTES_PER_ACTIVE * na if HESS_DRAM_BYTES_PER_ACTIVE else None,
+                "traffic_source": HESS_TRAFFIC_SOURCE,
                 "flops_per_pass": hess_flops(st), "active_pairs": na,
                 "pairs_per_kernel": {"face": st["n_hess_face"], "pe_frame": st["n_hess_pe_frame"],
                                      "pe": st["n_hess_pe"]},
                 "kernel_ms": hess_ms, "peak_source": "derived: 152 SM x 2070 MHz x 4 FP64 flop/clk/SM"}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+    return {"metric": METRIC, "value": world * n_cand / (r["ms"] / 1000.0), "unit": UNIT, "n_gpus": world,
+            "steps": r["steps"], "warmup": args.warmup, "ms_per_step": r["ms"],
+            "ms_mean": statistics.mean(r["step_ms"]), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "candidates": int(n_cand), "filtered": st["n_filtered"],
+            "config": {"workload": r["desc"], "candidates": int(n_cand), "filtered": st["n_filtered"],
                        "core": st["n_core"], "active": int(na), "ccd_pairs": st["n_ccd"], "nnzb": st["nnzb"],
-                       "dbar_min": st["dbar_min"], "seed": sc.seed, "tuning": tuning,
+                       "dbar_min": st["dbar_min"], "seed": sc.seed, "tuning": r["tuning"],
                        "mollifier": bool(args.mollifier), "mollified_pairs": st["n_mollified"],
-                       "l2": "flushed (256 MiB write) between steps",
+                       "l2": "flushed (256 MiB write) between steps", "timing": "median of the timed passes",
                        "parallelism": f"replicas x{world}"},
-            "stage_ms": {"contact_build": med[0], "contact_filter": med[1], "barrier_eval": med[2],
-                         "ccd_step": med[3], "hessian_kernel": med[4]},
+            "stage_ms": _stage_dict(med),
             "roofline": roofline,
             "stage_roofline": stage_roofline(st, med, [sc]),
             "fp32_broad_phase": {"candidates_fp32": st["n_candidates_fp32"], "candidates": int(n_cand),
                                  "superset_ratio": st["n_candidates_fp32"] / max(1, n_cand),
                                  "fp64_decided": st["n_fp64_decided"]},
-            "e2e": {"value": world * n_cand / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "clocks": clk, "gpu_launches": int(launches), "status": status}
-    if not args.no_cpu_baseline and world == 1:
-        try:
-            line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_nx)
-        except Exception as e:  # the baseline is context; never fail the bench on it
-            line["cpu_baseline"] = {"value": None, "error": str(e)}
-    print(json.dumps(line), flush=True)
-    cs.close()
-    if dist:
-        dist.destroy_process_group()
+            "e2e": {"value": world * n_cand / (r["e2e_ms"] / 1000.0), "unit": UNIT,
+                    "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"], "ms_per_step": r["e2e_ms"]},
+            "clocks": r["clocks"], "gpu_launches": int(r["launches"]), "status": r["status"]}
 
 
 if __name__ == "__main__":

@@ -90,6 +90,25 @@ typedef enum {
 
 typedef struct cb_scene cb_scene;
 
+/* Device memory of a scene or batch: by default the library allocates from
+ * the CUDA runtime's stream-ordered pool.  A caller that accounts for device
+ * memory itself (a framework with its own caching allocator, a server that
+ * admits work under a memory budget) passes an allocator instead; every
+ * device buffer the scene ever holds then comes from it and goes back to it:
+ *   alloc(bytes, stream, ctx) -> a DEVICE pointer of the scene's GPU, 256-byte
+ *     aligned, or NULL (the call fails with CB_ERR_OOM);
+ *   free(ptr, bytes, stream, ctx) -- called once the work queued on `stream`
+ *     has finished (the library synchronizes the stream first), so the memory
+ *     may be handed out again at once.
+ * `stream` is the cudaStream_t (as void*) of the call that grows or releases
+ * the buffer.  Both are called from the thread that makes the library call.
+ * cb_stats.device_bytes is the total the scene holds at any moment. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+  void* ctx;
+} cb_allocator;
+
 /* Scene description.  All pointers are HOST memory, read only during
  * cb_scene_create (the library copies what it needs). */
 typedef struct {
@@ -144,10 +163,12 @@ typedef struct {
 /* Create a scene: uploads topology and rest positions, derives edges and
  * components, and precomputes the filter tables of Sec. 3.2 on the GPU
  * (rods: arc-length windows; shells: every stencil pair of the rest mesh
- * closer than the activation) and dbar_min.  sync.
- * Errors: CB_ERR_ARG (bad sizes / indices), CB_ERR_DEGENERATE (zero
- * reference distance), CB_ERR_OOM, CB_ERR_CUDA.  *out is set only on CB_OK. */
-cb_status cb_scene_create(const cb_scene_desc* desc, void* stream, cb_scene** out);
+ * closer than the activation) and dbar_min.  allocator: NULL (the library's
+ * pool) or the caller's (copied; its ctx must outlive the scene).  sync.
+ * Errors: CB_ERR_ARG (bad sizes / indices, an allocator without alloc or
+ * free), CB_ERR_DEGENERATE (zero reference distance), CB_ERR_OOM,
+ * CB_ERR_CUDA.  *out is set only on CB_OK. */
+cb_status cb_scene_create(const cb_scene_desc* desc, const cb_allocator* allocator, void* stream, cb_scene** out);
 
 /* Release every device buffer of the scene.  sync on the scene's last stream. */
 cb_status cb_scene_destroy(cb_scene* scene);
@@ -203,13 +224,15 @@ cb_status ccd_step(cb_scene* scene, const double* x_dev, const double* p_dev, do
  * triangles in member order (offsets: cb_batch_offsets) and keeps each
  * member's parameters, filter tables, hash grid and results separate; pairs of
  * different members are never formed.  It copies what it needs at creation:
- * members may be destroyed afterwards.  Use it with the four pass calls: x, p
+ * members may be destroyed afterwards.  allocator: as for cb_scene_create (the
+ * batch's own buffers; the members keep theirs).  Use it with the four pass calls: x, p
  * and grad are [3][N] over the concatenated vertices (N = total), and
  * energy_dev / alpha_dev receive one double per member, in member order.
  * Pair keys and the BSR matrix use the concatenated numbering.  sync.
  * Errors: CB_ERR_ARG (null members, count < 1, mixed kinds, a member that is
  * itself a batch, index overflow), CB_ERR_OOM, CB_ERR_CUDA. */
-cb_status cb_batch_create(cb_scene* const* members, int32_t count, void* stream, cb_scene** out);
+cb_status cb_batch_create(cb_scene* const* members, int32_t count, const cb_allocator* allocator, void* stream,
+                          cb_scene** out);
 /* HOST arrays of count+1 entries: first vertex / edge / triangle of each
  * member in the batch numbering (a plain scene reports one member). */
 cb_status cb_batch_offsets(cb_scene* scene, int64_t* vert_offsets, int64_t* edge_offsets, int64_t* tri_offsets);
@@ -284,6 +307,13 @@ cb_status cb_sync_status(cb_scene* scene);
  * [0] contact_build, [1] contact_filter, [2] barrier_eval, [3] ccd_step,
  * [4] barrier_eval Hessian kernel alone.  sync. */
 cb_status cb_get_stage_ms(cb_scene* scene, float* ms5);
+/* The same times and the two parts of barrier_eval, `count` floats (HOST):
+ * [0..4] as cb_get_stage_ms, [5] stage (c) -- FP32 screen, exact distances,
+ * classes and the active set (Eq. 2-4, Sec. 3.4) -- and [6] stage (d) --
+ * compaction, BSR pattern, barrier derivatives, PSD projection, assembly;
+ * [5] + [6] = [2].  [5] and [6] are 0 after a barrier_energy or a pass with no
+ * candidates; entries past 7 are 0.  sync.  Errors: CB_ERR_ARG. */
+cb_status cb_get_stage_times(cb_scene* scene, float* ms, int32_t count);
 /* Tuning knobs of a broad phase (no counterpart in the paper; no result
  * depends on them, only speed).  phase 0: contact_build's broad phase, 1:
  * ccd_step's swept broad phase.  cell_factor in (0, 64]: hash cell edge =

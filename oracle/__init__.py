@@ -105,8 +105,17 @@ def lib():
         L.orc_stencil.restype = i32
         L.orc_stencil.argtypes = [C.POINTER(_Topo), C.c_uint64, vp]
         L.orc_num_threads.restype = i32
+        L.orc_set_num_threads.argtypes = [i32]
         _lib = L
     return _lib
+
+
+def set_num_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (for timing; results do not
+    depend on it); returns the previous count."""
+    prev = lib().orc_num_threads()
+    lib().orc_set_num_threads(int(n))
+    return prev
 
 
 def _ptr(a: np.ndarray | None):

@@ -41,6 +41,16 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads the oracle's parallel loops use from now on (timing only; the
+ * results do not depend on it: every loop writes per-pair outputs). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 void orc_free(void* p) { free(p); }
 
 /* ------------------------------------------------------------------------- */

@@ -30,11 +30,69 @@ MODES = {"double": CB_FILTER_DOUBLE, "single": CB_FILTER_SINGLE, "off": CB_FILTE
 # names declared in include/contact.h (the tests check the library exports each)
 ABI_FUNCTIONS = ["cb_scene_create", "cb_scene_destroy", "contact_build", "contact_filter", "barrier_eval",
                  "ccd_step", "cb_get_pairs", "cb_get_active", "cb_get_ccd", "cb_get_bsr", "cb_bsr_device",
-                 "cb_get_stats", "cb_sync_status", "cb_get_stage_ms", "cb_set_timing", "cb_status_str",
+                 "cb_get_stats", "cb_sync_status", "cb_get_stage_ms", "cb_get_stage_times", "cb_set_timing", "cb_status_str",
                  "cb_version", "cb_kernel_launches", "cb_measure_fma_tflops", "cb_batch_create",
                  "cb_batch_offsets", "cb_member_count", "ccd_step_noalloc", "cb_set_tuning",
                  "cb_get_tuning", "barrier_energy", "cb_bsr_spmv", "friction_lag", "friction_eval",
                  "friction_spmv", "cb_get_friction"]
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    """cb_allocator of the C ABI."""
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", C.c_void_p)]
+
+
+_TORCH_ALLOCATORS: dict = {}
+
+
+def torch_allocator(device=None) -> Allocator:
+    """PyTorch's CUDA caching allocator as the library's allocator for one
+    device: every device buffer of a scene created with it is a block of
+    torch's pool, so torch.cuda.memory_allocated / memory_reserved account for
+    it and a budget charged from them sees the library's memory.  The
+    callbacks live for the whole process (scenes keep pointers to them)."""
+    import torch
+    if device is None:
+        dev = torch.cuda.current_device()
+    elif isinstance(device, int):
+        dev = device
+    else:
+        dev = torch.device(device).index
+        if dev is None:
+            dev = torch.cuda.current_device()
+    got = _TORCH_ALLOCATORS.get(dev)
+    if got is not None:
+        return got[0]
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+        except Exception:  # out of memory: the library reports CB_ERR_OOM
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    fa, ff = _ALLOC_FN(_alloc), _FREE_FN(_free)
+    a = Allocator(fa, ff, None)
+    _TORCH_ALLOCATORS[dev] = (a, fa, ff)
+    return a
+
+
+def _allocator_arg(allocator):
+    """allocator argument of the create calls: "torch" (default), None (the
+    library's own stream-ordered pool) or an Allocator."""
+    if allocator is None:
+        return None
+    if isinstance(allocator, str):
+        if allocator != "torch":
+            raise ValueError(f"unknown allocator {allocator!r}")
+        return C.byref(torch_allocator())
+    return C.byref(allocator)
 
 
 class ContactError(RuntimeError):
@@ -83,10 +141,10 @@ def lib():
         L.cb_kernel_launches.restype = i64
         L.cb_kernel_launches.argtypes = []
         L.cb_measure_fma_tflops.argtypes = [i32, i32, i32, C.POINTER(C.c_double)]
-        L.cb_batch_create.argtypes = [C.POINTER(vp), i32, vp, C.POINTER(vp)]
+        L.cb_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(Allocator), vp, C.POINTER(vp)]
         L.cb_batch_offsets.argtypes = [vp, vp, vp, vp]
         L.cb_member_count.argtypes = [vp]
-        L.cb_scene_create.argtypes = [C.POINTER(SceneDesc), vp, C.POINTER(vp)]
+        L.cb_scene_create.argtypes = [C.POINTER(SceneDesc), C.POINTER(Allocator), vp, C.POINTER(vp)]
         L.cb_scene_destroy.argtypes = [vp]
         L.contact_build.argtypes = [vp, vp, vp]
         L.contact_filter.argtypes = [vp, vp]
@@ -106,6 +164,7 @@ def lib():
         L.cb_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.cb_sync_status.argtypes = [vp]
         L.cb_get_stage_ms.argtypes = [vp, C.POINTER(C.c_float)]
+        L.cb_get_stage_times.argtypes = [vp, C.POINTER(C.c_float), C.c_int32]
         L.cb_set_timing.argtypes = [vp, i32]
         L.ccd_step_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, i64, vp, vp, vp]
         L.cb_set_tuning.argtypes = [vp, i32, C.c_float, i32]
@@ -195,7 +254,7 @@ class ContactScene:
     def __init__(self, kind: str, rest, thickness: float, dhat: float, rod_ptr=None, tris=None,
                  kappa: float = 1.0, mode: str = "double", paper_literal: bool = False,
                  core_temp: bool = True, cull_radius: int = 0, per_component: bool = False, rod_closed=None,
-                 mollifier: bool = False, rest_uv=None, stream=None):
+                 mollifier: bool = False, rest_uv=None, stream=None, allocator="torch"):
         L = lib()
         rest = np.ascontiguousarray(np.asarray(rest, np.float64).reshape(3, -1))
         self.n = rest.shape[1]
@@ -234,7 +293,8 @@ class ContactScene:
             (CB_EE_MOLLIFIER if mollifier else 0)
         d.cull_radius = int(cull_radius)
         h = C.c_void_p()
-        _check(L.cb_scene_create(C.byref(d), _stream_ptr(stream), C.byref(h)), "cb_scene_create")
+        _check(L.cb_scene_create(C.byref(d), _allocator_arg(allocator), _stream_ptr(stream), C.byref(h)),
+               "cb_scene_create")
         self.h = h
         self.kind = kind
         self._load_layout()
@@ -422,8 +482,10 @@ class ContactScene:
         _check(lib().cb_set_timing(self.h, int(on)), "cb_set_timing")
 
     def stage_ms(self) -> list[float]:
-        ms = (C.c_float * 5)()
-        _check(lib().cb_get_stage_ms(self.h, ms), "cb_get_stage_ms")
+        """Device ms of the last calls: build, filter, barrier_eval, ccd_step,
+        Hessian kernels, and barrier_eval's stage (c) and stage (d) parts."""
+        ms = (C.c_float * 7)()
+        _check(lib().cb_get_stage_times(self.h, ms, 7), "cb_get_stage_times")
         return [float(v) for v in ms]
 
 
@@ -432,11 +494,12 @@ class ContactBatch(ContactScene):
     span the concatenated vertices (member order); energy and alpha hold one
     value per member."""
 
-    def __init__(self, members: list, stream=None):
+    def __init__(self, members: list, stream=None, allocator="torch"):
         L = lib()
         arr = (C.c_void_p * len(members))(*[m.h.value for m in members])
         h = C.c_void_p()
-        _check(L.cb_batch_create(arr, len(members), _stream_ptr(stream), C.byref(h)), "cb_batch_create")
+        _check(L.cb_batch_create(arr, len(members), _allocator_arg(allocator), _stream_ptr(stream), C.byref(h)),
+               "cb_batch_create")
         self.h = h
         self.kind = members[0].kind
         self._keep = []

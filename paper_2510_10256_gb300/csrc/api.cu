@@ -13,26 +13,53 @@
 static std::atomic<long long> g_launches{0};
 long long cb_launch_counter_add() { return g_launches.fetch_add(1, std::memory_order_relaxed) + 1; }
 
+AllocCtx& alloc_ctx() {
+  static thread_local AllocCtx ctx;
+  return ctx;
+}
+
 cb_status buf_ensure(DevBuf& b, size_t bytes, cudaStream_t st) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return CB_OK;
-  if (b.p) cudaFreeAsync(b.p, st);
-  b.p = nullptr;
-  b.bytes = 0;
-  size_t want = bytes + bytes / 4 + 256;
-  if (cudaMallocAsync(&b.p, want, st) != cudaSuccess) {
+  buf_free(b, st);
+  const size_t want = bytes + bytes / 4 + 256;
+  const AllocCtx& c = alloc_ctx();
+  if (c.alloc) {
+    void* p = c.alloc->alloc(want, (void*)st, c.alloc->ctx);
+    if (!p) return CB_ERR_OOM;
+    if ((uintptr_t)p & 255u) {  // every buffer must be 256-byte aligned (vector loads of any width)
+      fprintf(stderr, "contact: the caller's allocator returned a pointer that is not 256-byte aligned\n");
+      c.alloc->free(p, want, (void*)st, c.alloc->ctx);
+      return CB_ERR_OOM;
+    }
+    b.p = p;
+  } else if (cudaMallocAsync(&b.p, want, st) != cudaSuccess) {
     cudaGetLastError();
     b.p = nullptr;
     return CB_ERR_OOM;
   }
   b.bytes = want;
+  b.alloc = c.alloc;
+  b.charged = c.charged;
+  if (b.charged) *b.charged += (int64_t)want;
   return CB_OK;
 }
 
 void buf_free(DevBuf& b, cudaStream_t st) {
-  if (b.p) cudaFreeAsync(b.p, st);
+  if (b.p) {
+    if (b.alloc) {
+      // the caller's allocator may reuse the memory as soon as it has it back
+      cudaStreamSynchronize(st);
+      b.alloc->free(b.p, b.bytes, (void*)st, b.alloc->ctx);
+    } else {
+      cudaFreeAsync(b.p, st);
+    }
+    if (b.charged) *b.charged -= (int64_t)b.bytes;
+  }
   b.p = nullptr;
   b.bytes = 0;
+  b.alloc = nullptr;
+  b.charged = nullptr;
 }
 
 cb_status read_scalars(cb_scene* s, int first, int count, uint64_t* out, cudaStream_t st) {
@@ -177,8 +204,9 @@ const char* cb_status_str(cb_status st) {
   return "unknown status";
 }
 
-cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) {
+cb_status cb_scene_create(const cb_scene_desc* d, const cb_allocator* allocator, void* stream, cb_scene** out) {
   if (!d || !out || !d->rest_xyz || d->n_verts < 1) return CB_ERR_ARG;
+  if (allocator && (!allocator->alloc || !allocator->free)) return CB_ERR_ARG;
   if (d->kind != CB_ROD && d->kind != CB_SHELL) return CB_ERR_ARG;
   if (!(d->dhat > 0.0) || !(d->thickness >= 0.0) || !std::isfinite(d->thickness) || !std::isfinite(d->dhat))
     return CB_ERR_ARG;
@@ -256,6 +284,11 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
   }
   const int E = (int)e0.size();
   cb_scene* s = new cb_scene();
+  if (allocator) {
+    s->allocator = *allocator;
+    s->has_alloc = true;
+  }
+  AllocScope scope(s->alloc_ptr(), &s->live_bytes);
   s->kind = d->kind;
   s->n = n;
   s->E = E;
@@ -360,12 +393,19 @@ cb_status cb_scene_create(const cb_scene_desc* d, void* stream, cb_scene** out) 
   return CB_OK;
 }
 
-cb_status cb_batch_create(cb_scene* const* members, int32_t count, void* stream, cb_scene** out) {
+cb_status cb_batch_create(cb_scene* const* members, int32_t count, const cb_allocator* allocator, void* stream,
+                          cb_scene** out) {
   if (!members || count < 1 || !out) return CB_ERR_ARG;
+  if (allocator && (!allocator->alloc || !allocator->free)) return CB_ERR_ARG;
   for (int m = 0; m < count; ++m)
     if (!members[m] || members[m]->count != 1 || members[m]->kind != members[0]->kind) return CB_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   cb_scene* b = new cb_scene();
+  if (allocator) {
+    b->allocator = *allocator;
+    b->has_alloc = true;
+  }
+  AllocScope scope(b->alloc_ptr(), &b->live_bytes);
   b->kind = members[0]->kind;
   b->count = count;
   b->last_stream = st;
@@ -528,6 +568,7 @@ static void stage_end(cb_scene* s, int k, cudaStream_t st) {
 
 cb_status contact_build(cb_scene* s, const double* x, void* stream) {
   if (!s || !x) return CB_ERR_ARG;
+  AllocScope scope(s->alloc_ptr(), &s->live_bytes);
   cudaStream_t st = (cudaStream_t)stream;
   s->last_stream = st;
   stage_begin(s, 0, st);
@@ -539,6 +580,7 @@ cb_status contact_build(cb_scene* s, const double* x, void* stream) {
 
 cb_status contact_filter(cb_scene* s, void* stream) {
   if (!s) return CB_ERR_ARG;
+  AllocScope scope(s->alloc_ptr(), &s->live_bytes);
   cudaStream_t st = (cudaStream_t)stream;
   s->last_stream = st;
   stage_begin(s, 1, st);
@@ -549,6 +591,7 @@ cb_status contact_filter(cb_scene* s, void* stream) {
 
 cb_status barrier_eval(cb_scene* s, const double* x, double* energy, double* grad, void* stream) {
   if (!s || !x) return CB_ERR_ARG;
+  AllocScope scope(s->alloc_ptr(), &s->live_bytes);
   cudaStream_t st = (cudaStream_t)stream;
   s->last_stream = st;
   stage_begin(s, 2, st);
@@ -559,6 +602,7 @@ cb_status barrier_eval(cb_scene* s, const double* x, double* energy, double* gra
 
 cb_status barrier_energy(cb_scene* s, const double* x, double* energy, void* stream) {
   if (!s || !x || !energy) return CB_ERR_ARG;
+  AllocScope scope(s->alloc_ptr(), &s->live_bytes);
   cudaStream_t st = (cudaStream_t)stream;
   s->last_stream = st;
   stage_begin(s, 2, st);
@@ -569,6 +613,7 @@ cb_status barrier_energy(cb_scene* s, const double* x, double* energy, void* str
 
 cb_status ccd_step(cb_scene* s, const double* x, const double* p, double* alpha, void* stream) {
   if (!s || !x || !p) return CB_ERR_ARG;
+  AllocScope scope(s->alloc_ptr(), &s->live_bytes);
   cudaStream_t st = (cudaStream_t)stream;
   s->last_stream = st;
   stage_begin(s, 3, st);
@@ -610,6 +655,20 @@ cb_status cb_get_stage_ms(cb_scene* s, float* ms) {
   ms[4] = 0.f;
   if (s->timing && s->n_active > 0) cudaEventElapsedTime(&ms[4], s->ev[10], s->ev[11]);
   cudaGetLastError();
+  return CB_OK;
+}
+
+cb_status cb_get_stage_times(cb_scene* s, float* ms, int32_t count) {
+  if (!s || !ms || count < 0) return CB_ERR_ARG;
+  float all[7] = {0, 0, 0, 0, 0, 0, 0};
+  CB_TRY(cb_get_stage_ms(s, all));
+  if (s->timing && s->cd_split) {
+    cudaEventElapsedTime(&all[5], s->ev[4], s->ev[12]);
+    cudaEventElapsedTime(&all[6], s->ev[12], s->ev[5]);
+    cudaGetLastError();
+  }
+  for (int k = 0; k < count && k < 7; ++k) ms[k] = all[k];
+  for (int k = 7; k < count; ++k) ms[k] = 0.f;
   return CB_OK;
 }
 
@@ -798,22 +857,7 @@ cb_status cb_get_stats(cb_scene* s, cb_stats* o) {
   o->n_hess_pe = s->n_hq[2];
   o->n_pair_overflow = (int64_t)(uint32_t)h[SC_NOVF];
   o->n_mollified = (int64_t)(uint32_t)h[SC_NMOLL];
-  size_t bytes = 0;
-  const DevBuf* all[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->wst,
-                         &s->rloop, &s->rlast, &s->elen2, &s->hmoll, &s->mlist, &s->ruv, &s->frest,
-                         &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls,
-                         &s->aidx, &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col,
-                         &s->bsr_val, &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag,
-                         &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist, &s->fr_key,
-                         &s->fr_st, &s->fr_dat, &s->fr_hw};
-  for (const DevBuf* b : all) bytes += b->bytes;
-  for (const BroadWork* w : {&s->bw, &s->bwc}) {
-    const DevBuf* wb[] = {&w->box32,    &w->box64,    &w->bounds,    &w->cell_cnt, &w->cell_off, &w->ekey[0],
-                          &w->ekey[1],  &w->eval[0],  &w->eval[1],   &w->run_flag, &w->run_id,   &w->run_start,
-                          &w->pair_cnt, &w->pair_off, &w->ebox, &w->ckey[0],   &w->ckey[1],  &w->stage, &w->ovl, &w->scan_tmp, &w->hist};
-    for (const DevBuf* b : wb) bytes += b->bytes;
-  }
-  o->device_bytes = (int64_t)bytes;
+  o->device_bytes = s->live_bytes;
   return CB_OK;
 }
 

@@ -236,6 +236,7 @@ __global__ void k_fric_spmv(int64_t nf, int n, const int4* __restrict__ stn, con
 
 extern "C" cb_status friction_lag(cb_scene* s, const double* x_lag, double mu, double eps, void* stream) {
   if (!s || !x_lag || !(mu >= 0.0) || !(eps > 0.0) || s->count != 1) return CB_ERR_ARG;
+  AllocScope scope(s->alloc_ptr(), &s->live_bytes);
   cudaStream_t st = (cudaStream_t)stream;
   s->last_stream = st;
   const int64_t na = s->n_active;

@@ -2161,6 +2161,7 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
   unsigned long long* ncore = (unsigned long long*)(sc + SC_NCORE);
   unsigned long long* macc = bp<unsigned long long>(s->macc);
   const int M = s->count;
+  s->cd_split = false;
   k_set_u64<<<1, 1, 0, cb_count(st)>>>(ncore, 0ull);
   k_macc_reset<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, MACC_E, 0ull);
   k_macc_reset<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, MACC_STATUS, 0ull);
@@ -2203,6 +2204,9 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     uint64_t h;
     CB_TRY(read_scalars(s, SC_COUNT1, 1, &h, st));
     s->n_active = (int64_t)(uint32_t)h;
+    // end of stage (c): distances, classes and the active set
+    if (s->timing) cudaEventRecord(s->ev[12], st);
+    s->cd_split = true;
   }
   const int64_t na = s->n_active;
   if (na > 0) {

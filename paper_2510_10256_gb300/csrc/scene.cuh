@@ -4,12 +4,36 @@
 
 #include "common.cuh"
 
+// A device buffer remembers the allocator that made it (NULL: the library's
+// own stream-ordered pool) and the byte counter of the scene it is charged to.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  const cb_allocator* alloc = nullptr;
+  int64_t* charged = nullptr;
+};
+
+// Where the buffers of the current API call come from: set for the duration
+// of each call that may allocate (AllocScope), read by buf_ensure.
+struct AllocCtx {
+  const cb_allocator* alloc = nullptr;
+  int64_t* charged = nullptr;
+};
+AllocCtx& alloc_ctx();
+struct AllocScope {
+  AllocCtx saved;
+  AllocScope(const cb_allocator* a, int64_t* charged) : saved(alloc_ctx()) {
+    alloc_ctx().alloc = a;
+    alloc_ctx().charged = charged;
+  }
+  ~AllocScope() { alloc_ctx() = saved; }
 };
 
 // A growable device buffer: keeps its allocation, grows by 25 % headroom.
+// Allocates through the current AllocScope's allocator (or the library's
+// pool) and charges the scope's counter; frees through the buffer's own
+// allocator (after the stream's work is done, since a caller's allocator may
+// hand the memory out again at once).
 cb_status buf_ensure(DevBuf& b, size_t bytes, cudaStream_t st);
 void buf_free(DevBuf& b, cudaStream_t st);
 template <typename T>
@@ -70,6 +94,12 @@ struct BroadWork {
 };
 
 struct cb_scene {
+  // the caller's allocator (copied at create; has_alloc false: the library's pool)
+  // and the bytes of device memory the scene holds now
+  cb_allocator allocator{};
+  bool has_alloc = false;
+  int64_t live_bytes = 0;
+  const cb_allocator* alloc_ptr() const { return has_alloc ? &allocator : nullptr; }
   int kind = 0;
   int n = 0, E = 0, T = 0, n_rods = 0;
   int n_prims = 0;     // broad-phase primitives
@@ -164,7 +194,11 @@ struct cb_scene {
   int32_t status_host = 0;
 
   bool timing = false;
-  cudaEvent_t ev[12] = {};
+  // stage events: [2k, 2k+1] around stage k of cb_get_stage_ms, [10, 11] around
+  // the Hessian kernels, [12] the end of stage (c) inside barrier_eval (the
+  // active count known); cd_split: the last barrier_eval recorded [12]
+  cudaEvent_t ev[13] = {};
+  bool cd_split = false;
   float stage_ms[5] = {0, 0, 0, 0, 0};
   int64_t counts_filtered = 0, counts_core = 0;
   int ccd_max_iters = 0;

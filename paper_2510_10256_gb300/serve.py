@@ -120,7 +120,8 @@ class Server:
         loading: dict = {}                      # future -> (request, reserved bytes, admission time)
         resident = {"rod": [], "shell": []}     # kind -> slots
         inflight: dict = {}                     # kind -> (future, slots of the running iteration)
-        used = peak_used = 0
+        used = peak_used = peak_real = 0
+        live_bytes = getattr(eng, "live_bytes", None)
         lat, queue, load = [], [], []
         results = collections.defaultdict(list) if self.keep else None
         rejected = []
@@ -138,16 +139,25 @@ class Server:
                 now = clock() - t0
                 while pending and pending[0].arrival <= now:
                     waiting.append(pending.popleft())
-                # admission: FIFO while a slot is free and the footprint fits the budget
+                # admission: FIFO while a slot is free and the footprint fits the budget.
+                # What is charged is the larger of the footprint estimates of everything
+                # admitted and, where the engine can tell, the device memory it really
+                # holds now (plus the estimates of the scenes still loading).
                 n_res = len(resident["rod"]) + len(resident["shell"])
+                charged = used
+                if live_bytes is not None:
+                    real = int(live_bytes()) + sum(v[1] for v in loading.values())
+                    peak_real = max(peak_real, real)
+                    charged = max(used, real)
                 while waiting and n_res + len(loading) < self.max_slots:
                     req = waiting[0]
                     need = int(eng.footprint(req))
                     if need > self.budget:
                         rejected.append(waiting.popleft().rid)
                         continue
-                    if used + need > self.budget:
+                    if charged + need > self.budget:
                         break
+                    charged += need
                     waiting.popleft()
                     used += need
                     peak_used = max(peak_used, used)
@@ -207,7 +217,8 @@ class Server:
                                    "mean": _ms(statistics.mean(lat)) if lat else None},
                "queue_delay_ms": {"p50": _ms(_pct(queue, 50)), "p99": _ms(_pct(queue, 99))},
                "load_ms": {"p50": _ms(_pct(load, 50)), "p99": _ms(_pct(load, 99))},
-               "peak_reserved_bytes": peak_used, "max_resident": max_resident}
+               "peak_reserved_bytes": peak_used, "peak_live_bytes": peak_real if live_bytes is not None else None,
+               "max_resident": max_resident}
         if self.keep:
             rep["results"] = dict(results)
         return rep
@@ -220,9 +231,13 @@ def _ms(v):
 class DeviceEngine:
     """The GPU engine: scenes of the contact library, one batch per kind.
 
-    Footprint model: device bytes per vertex of each kind, measured by
-    calibrate() on sample scenes (scene + batch copy + pass buffers), times a
-    safety factor."""
+    Every device buffer of its scenes and batches comes from PyTorch's caching
+    allocator, so live_bytes() -- torch's allocated bytes on the device since
+    the engine started -- is what the resident requests really hold; the
+    scheduler charges the budget from it.  Footprint model (the estimate a
+    request is admitted on, before it holds anything): device bytes per
+    vertex of each kind, measured by calibrate() on sample scenes (scene +
+    batch copy + pass buffers), times a safety factor."""
 
     def __init__(self, device=None, mode: str = "double", safety: float = 1.25):
         import torch
@@ -237,6 +252,13 @@ class DeviceEngine:
         self.batches = {}
         self.bytes_per_vertex = {"rod": 4096.0, "shell": 16384.0}
         self.lock = threading.Lock()
+        torch.cuda.synchronize(self.dev)
+        self.base_bytes = torch.cuda.memory_allocated(self.dev)
+
+    def live_bytes(self) -> int:
+        """Device memory allocated since the engine started: the scenes,
+        batches and step tensors of the resident requests."""
+        return max(0, self.torch.cuda.memory_allocated(self.dev) - self.base_bytes)
 
     # -- footprint
     def calibrate(self, scenes: list):
@@ -322,6 +344,44 @@ class _Handle:
     gen: object
     sigma: float
     n: int
+
+
+def run_plain(engine, requests: list[Request], clock=time.perf_counter, sleep=time.sleep) -> dict:
+    """The plain form of a request stream, for comparison with Server: the
+    same requests in arrival order (FIFO), one at a time, each step a plain
+    single-scene pass; nothing overlaps.  Reports like Server.run (step
+    latency from the step becoming runnable to its result, queueing delay
+    from arrival to the start of the request's scene creation)."""
+    lat, queue, load = [], [], []
+    steps_done = pairs = 0
+    t0 = clock()
+    for req in sorted(requests, key=lambda r: (r.arrival, r.rid)):
+        now = clock() - t0
+        if req.arrival > now:
+            sleep(req.arrival - now)
+        adm = clock() - t0
+        queue.append(adm - req.arrival)
+        h = engine.create(req)
+        ready = clock() - t0
+        load.append(ready - adm)
+        runnable = ready
+        for _ in range(req.steps):
+            _, npairs = engine.run_step(req.kind, [h])
+            done = clock() - t0
+            lat.append(done - runnable)
+            runnable = done
+            steps_done += 1
+            pairs += int(npairs)
+        engine.release(h)
+    wall = clock() - t0
+    return {"wall_s": wall, "steps": steps_done, "pairs": pairs, "iterations": steps_done,
+            "pairs_per_s": pairs / wall if wall > 0 else 0.0, "steps_per_s": steps_done / wall if wall > 0 else 0.0,
+            "requests": len(requests), "rejected": [],
+            "step_latency_ms": {"p50": _ms(_pct(lat, 50)), "p99": _ms(_pct(lat, 99)),
+                                "mean": _ms(statistics.mean(lat)) if lat else None},
+            "queue_delay_ms": {"p50": _ms(_pct(queue, 50)), "p99": _ms(_pct(queue, 99))},
+            "load_ms": {"p50": _ms(_pct(load, 50)), "p99": _ms(_pct(load, 99))},
+            "peak_reserved_bytes": 0, "max_resident": 1}
 
 
 def run_alone(engine, req: Request) -> list[StepResult]:

@@ -129,3 +129,63 @@ def test_poisson_stream_is_seeded():
     assert abs(gaps.mean() - 1 / 200.0) < 0.3 / 200.0
     kinds = [r.kind for r in a]
     assert 60 < kinds.count("rod") < 140
+
+
+def test_plain_form_runs_fifo_one_request_at_a_time():
+    """run_plain, the comparison arm of the served stream: the same trace in
+    arrival order, one request and one single-scene step at a time."""
+    from paper_2510_10256_gb300.serve import run_plain
+    reqs = _reqs(12, rate=4000.0, steps=3)
+    eng = FakeEngine(budget=10_000, step_s=0.001)
+    rep = run_plain(eng, reqs)
+    assert rep["steps"] == 12 * 3 and rep["iterations"] == rep["steps"]
+    assert eng.max_live == 1 and eng.max_concurrent == 1 and not eng.live
+    assert eng.created == [r.rid for r in sorted(reqs, key=lambda r: (r.arrival, r.rid))]
+    assert rep["pairs"] == 10 * rep["steps"]
+    lat = rep["step_latency_ms"]
+    assert lat["p99"] >= lat["p50"] > 0
+    # the served form batches the same trace into fewer iterations
+    served = Server(FakeEngine(budget=10_000, step_s=0.001), hbm_budget=10_000, max_slots=16).run(reqs)
+    assert served["steps"] == rep["steps"] and served["iterations"] < rep["iterations"]
+
+
+def test_budget_is_charged_from_the_memory_really_held():
+    """An engine that reports the device memory its resident requests really
+    hold (live_bytes) is charged that, not the smaller footprint estimate:
+    here every scene holds five times its estimate, so while the first
+    request is resident (1000 of an 1100 budget) nothing else is admitted,
+    which the estimates alone (200 each) would allow."""
+    pool = [FakeScene("shell", 200)]
+    # the first request is resident (3 steps of 20 ms) when the others arrive
+    reqs = [Request(i, 0.0 if i == 0 else 0.02, pool[0], 3) for i in range(4)]
+
+    class Heavy(FakeEngine):
+        def __init__(self, *a, **k):
+            super().__init__(*a, **k)
+            self.events = []
+
+        def create(self, req):
+            h = super().create(req)
+            with self.lock:
+                self.events.append(("create", req.rid))
+            return h
+
+        def release(self, h):
+            with self.lock:
+                self.events.append(("release", h["req"].rid))
+            super().release(h)
+
+        def live_bytes(self):
+            with self.lock:
+                return 5 * sum(self.live.values())
+
+    eng = Heavy(budget=10_000, step_s=0.02)
+    rep = Server(eng, hbm_budget=1100, max_slots=4).run(reqs)
+    assert rep["steps"] == 12
+    assert eng.events[:2] == [("create", 0), ("release", 0)], eng.events
+    assert rep["peak_live_bytes"] >= 1000
+    # without the report the estimates alone let the others in beside the first
+    eng2 = Heavy(budget=10_000, step_s=0.02)
+    eng2.live_bytes = None
+    Server(eng2, hbm_budget=1100, max_slots=4).run(reqs)
+    assert eng2.events[1][0] == "create", eng2.events
