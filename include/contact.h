@@ -74,6 +74,13 @@ typedef enum {
 #define CB_DBAR_PER_COMPONENT 16    /* a filtered pair's width is the dbar_min of its own component (the
                                        smallest reference distance of that component's filtered pairs)
                                        instead of the scene's */
+#define CB_PER_STENCIL 64           /* per-stencil activation (Sec. 3.3 leaves it for later; the paper's
+                                       hash uses the full activation): after the filter, a class-F
+                                       candidate stays a candidate only if its two primitives' FP64 boxes,
+                                       each inflated by half the pair's own width (dbar_min, or its
+                                       component's), overlap (closed intervals).  A dropped pair is farther
+                                       apart than its width, so no barrier value changes; the candidate set
+                                       shrinks.  The CCD candidates are unaffected. */
 #define CB_EE_MOLLIFIER 32          /* IPC's edge-edge mollifier (App. A: the paper's solver uses IPC's
                                        contact energy): an edge-edge pair's energy is m(c) kappa b with
                                        c = |e0 x e1|^2, m = -c^2/eps_x^2 + 2c/eps_x below eps_x =
@@ -123,7 +130,7 @@ typedef struct {
   double dhat;                /* barrier width; full activation a = thickness + dhat */
   double kappa;               /* barrier stiffness (energy scale); 1 if <= 0 */
   int32_t mode;               /* CB_FILTER_* | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP | CB_DBAR_PER_COMPONENT
-                                 | CB_EE_MOLLIFIER */
+                                 | CB_EE_MOLLIFIER | CB_PER_STENCIL */
   int32_t cull_radius;        /* CB_FILTER_KALDOR: culling radius in edges (>= 1); else ignored */
   const uint8_t* rod_closed;  /* rods, HOST [n_rods] or NULL: 1 = closed loop (an edge from the last vertex
                                  back to the first, numbered after the polyline's others; >= 3 vertices,
@@ -158,6 +165,8 @@ typedef struct {
                                  went past what the count pass keeps (rods: 32 staged keys; shells: the
                                  partner bits of the positions the count pass keeps), re-tested by the fill pass */
   int64_t n_mollified;        /* last barrier_eval with CB_EE_MOLLIFIER: edge-edge pairs below their threshold */
+  int64_t n_stencil_dropped;  /* last contact_filter with CB_PER_STENCIL: filtered broad-phase pairs outside
+                                 their own width, removed from the candidates */
 } cb_stats;
 
 /* Create a scene: uploads topology and rest positions, derives edges and
@@ -184,7 +193,10 @@ cb_status contact_build(cb_scene* scene, const double* x_dev, void* stream);
 
 /* (b) Barrier filter, Sec. 3.2 / Eq. 1, 4: class F for a candidate whose
  * primitives belong to one component and whose reference distance is below
- * the activation, U otherwise.  Uses the tables built at create. */
+ * the activation, U otherwise.  Uses the tables built at create.  With
+ * CB_PER_STENCIL it then removes the class-F candidates outside their own
+ * width (boxes of the last contact_build's x); this reads a count back
+ * (sync). */
 cb_status contact_filter(cb_scene* scene, void* stream);
 
 /* (c)+(d) Distances, barrier, derivatives and assembly, Eq. 2-4.

@@ -15,7 +15,10 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcontact.so")
 SOURCES = ["api.cu", "broad.cu", "narrow.cu", "ccd.cu", "peaks.cu", "spmv.cu", "friction.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+# a non-void function (or lambda) that can fall off its end is an error, not a
+# warning: in the CUDA front end (diagnostic 940) and in the host compiler
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Werror=return-type",
+         "-Xcudafe", "--diag_error=940", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
 
 

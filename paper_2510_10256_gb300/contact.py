@@ -24,6 +24,7 @@ CB_THICK_PAPER_LITERAL = 4
 CB_NO_CORE_TEMP = 8
 CB_DBAR_PER_COMPONENT = 16
 CB_EE_MOLLIFIER = 32
+CB_PER_STENCIL = 64
 PAIRS = {"candidate": 0, "filtered": 1, "core": 2, "active": 3, "ccd": 4, "rest_filtered": 5}
 MODES = {"double": CB_FILTER_DOUBLE, "single": CB_FILTER_SINGLE, "off": CB_FILTER_OFF, "kaldor": CB_FILTER_KALDOR}
 
@@ -117,7 +118,7 @@ class Stats(C.Structure):
                 ("ccd_max_iters", C.c_int32), ("device_bytes", C.c_int64),
                 ("n_candidates_fp32", C.c_int64), ("n_fp64_decided", C.c_int64),
                 ("n_hess_face", C.c_int64), ("n_hess_pe_frame", C.c_int64), ("n_hess_pe", C.c_int64),
-                ("n_pair_overflow", C.c_int64), ("n_mollified", C.c_int64)]
+                ("n_pair_overflow", C.c_int64), ("n_mollified", C.c_int64), ("n_stencil_dropped", C.c_int64)]
 
 
 def build(force: bool = False) -> str:
@@ -254,7 +255,8 @@ class ContactScene:
     def __init__(self, kind: str, rest, thickness: float, dhat: float, rod_ptr=None, tris=None,
                  kappa: float = 1.0, mode: str = "double", paper_literal: bool = False,
                  core_temp: bool = True, cull_radius: int = 0, per_component: bool = False, rod_closed=None,
-                 mollifier: bool = False, rest_uv=None, stream=None, allocator="torch"):
+                 mollifier: bool = False, rest_uv=None, per_stencil: bool = False, stream=None,
+                 allocator="torch"):
         L = lib()
         rest = np.ascontiguousarray(np.asarray(rest, np.float64).reshape(3, -1))
         self.n = rest.shape[1]
@@ -290,7 +292,7 @@ class ContactScene:
         d.kappa = float(kappa)
         d.mode = MODES[mode] | (CB_THICK_PAPER_LITERAL if paper_literal else 0) | \
             (0 if core_temp else CB_NO_CORE_TEMP) | (CB_DBAR_PER_COMPONENT if per_component else 0) | \
-            (CB_EE_MOLLIFIER if mollifier else 0)
+            (CB_EE_MOLLIFIER if mollifier else 0) | (CB_PER_STENCIL if per_stencil else 0)
         d.cull_radius = int(cull_radius)
         h = C.c_void_p()
         _check(L.cb_scene_create(C.byref(d), _allocator_arg(allocator), _stream_ptr(stream), C.byref(h)),

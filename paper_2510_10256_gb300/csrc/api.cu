@@ -86,13 +86,13 @@ static void scene_release(cb_scene* s) {
   cudaStream_t st = s->last_stream;
   DevBuf* bufs[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->wst,
                     &s->rloop, &s->rlast, &s->elen2, &s->hmoll, &s->mlist, &s->ruv, &s->frest,
-                    &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
+                    &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cand_alt, &s->klass_alt, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
                     &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col, &s->bsr_val,
                     &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->mp, &s->vsc, &s->macc, &s->hstage, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag, &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist,
                     &s->fr_key, &s->fr_st, &s->fr_dat, &s->fr_hw, &s->dev_scalars};
   for (DevBuf* b : bufs) buf_free(*b, st);
   for (BroadWork* w : {&s->bw, &s->bwc}) {
-    DevBuf* wb[] = {&w->grids, &w->cx, &w->box32,   &w->box64,  &w->bounds,   &w->cell_cnt, &w->cell_off, &w->ekey[0], &w->ekey[1],
+    DevBuf* wb[] = {&w->grids, &w->cx, &w->box32,   &w->box64,  &w->box_raw, &w->bounds,   &w->cell_cnt, &w->cell_off, &w->ekey[0], &w->ekey[1],
                     &w->eval[0], &w->eval[1], &w->run_flag, &w->run_id,   &w->run_start, &w->pair_cnt,
                     &w->pair_off, &w->ebox, &w->ckey[0], &w->ckey[1],  &w->stage, &w->ovl, &w->scan_tmp, &w->hist};
     for (DevBuf* b : wb) buf_free(*b, st);
@@ -212,7 +212,7 @@ cb_status cb_scene_create(const cb_scene_desc* d, const cb_allocator* allocator,
     return CB_ERR_ARG;
   const int fm = d->mode & CB_FILTER_MASK;
   if (d->mode & ~(CB_FILTER_MASK | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP | CB_DBAR_PER_COMPONENT |
-                  CB_EE_MOLLIFIER))
+                  CB_EE_MOLLIFIER | CB_PER_STENCIL))
     return CB_ERR_ARG;
   if (fm == CB_FILTER_KALDOR && (d->kind != CB_ROD || d->cull_radius < 1)) return CB_ERR_ARG;
   if (d->rest_uv && d->kind != CB_SHELL) return CB_ERR_ARG;
@@ -322,12 +322,15 @@ cb_status cb_scene_create(const cb_scene_desc* d, const cb_allocator* allocator,
   s->kappa = d->kappa > 0.0 ? d->kappa : 1.0;
   s->last_stream = st;
   cudaGetDevice(&s->device);
+  cudaDeviceGetAttribute(&s->n_sms, cudaDevAttrMultiProcessorCount, s->device);
+  if (s->n_sms < 1) s->n_sms = 1;
   s->count = 1;
   s->hmp.assign(1, MemberParams{s->xi, s->dhat, s->a, s->kappa, 0.0, fm == CB_FILTER_SINGLE ? 1 : 0, s->core_temp,
                                 (fm == CB_FILTER_OFF || fm == CB_FILTER_KALDOR) ? 1 : 0, s->n_prims});
   s->hmp[0].cull_radius = fm == CB_FILTER_KALDOR ? d->cull_radius : 0;
   s->hmp[0].per_comp = (d->mode & CB_DBAR_PER_COMPONENT) ? 1 : 0;
   s->hmp[0].mollify = (d->mode & CB_EE_MOLLIFIER) ? 1 : 0;
+  s->hmp[0].per_stencil = (d->mode & CB_PER_STENCIL) ? 1 : 0;
   s->hmp[0].loops = 0;
   for (int32_t lc : rloop) s->hmp[0].loops |= lc > 0 ? 1 : 0;
   s->voff = {0, (int64_t)n};
@@ -416,6 +419,8 @@ cb_status cb_batch_create(cb_scene* const* members, int32_t count, const cb_allo
     dst.pair_block = src.pair_block;
   }
   cudaGetDevice(&b->device);
+  cudaDeviceGetAttribute(&b->n_sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (b->n_sms < 1) b->n_sms = 1;
   b->voff.assign(count + 1, 0);
   b->eoff.assign(count + 1, 0);
   b->toff.assign(count + 1, 0);
@@ -857,6 +862,7 @@ cb_status cb_get_stats(cb_scene* s, cb_stats* o) {
   o->n_hess_pe = s->n_hq[2];
   o->n_pair_overflow = (int64_t)(uint32_t)h[SC_NOVF];
   o->n_mollified = (int64_t)(uint32_t)h[SC_NMOLL];
+  o->n_stencil_dropped = s->n_dropped;
   o->device_bytes = s->live_bytes;
   return CB_OK;
 }

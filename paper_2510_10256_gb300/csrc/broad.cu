@@ -98,7 +98,8 @@ __device__ __forceinline__ int prim_member(const Topo& t, const int32_t* __restr
 
 __global__ void k_boxes(Topo t, int np, const double* __restrict__ x, const double* __restrict__ p,
                         const double* __restrict__ hm, const int32_t* __restrict__ vsc,
-                        float4* __restrict__ box32, double* __restrict__ box64, uint32_t* bounds) {
+                        float4* __restrict__ box32, double* __restrict__ box64, double* __restrict__ box_raw,
+                        uint32_t* bounds) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   float lo32[3] = {INFINITY, INFINITY, INFINITY}, hi32[3] = {-INFINITY, -INFINITY, -INFINITY};
   float ext = 0.f;
@@ -121,6 +122,10 @@ __global__ void k_boxes(Topo t, int np, const double* __restrict__ x, const doub
           mn = fmin(mn, c2);
           mx = fmax(mx, c2);
         }
+      }
+      if (box_raw) {  // the primitive's own box (per-stencil activation inflates it by each pair's width)
+        box_raw[(size_t)q * 6 + k] = mn;
+        box_raw[(size_t)q * 6 + 3 + k] = mx;
       }
       lo[k] = xsub(mn, h);
       hi[k] = xadd(mx, h);
@@ -501,6 +506,156 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
 }
 
 
+// Count pass with lane refill: the same tests, decisions and outputs as
+// pairs_of_entry<false, RR> for every entry, but an entry's partner range
+// (from none to thousands of positions) no longer holds its warp: the warps
+// are persistent and a lane that finishes an entry takes the next one
+// (warp_take), so the lanes of a warp stay busy until the entries run out.
+// Triangle entries of shell cells (no partners) are finished at once.
+// Outputs per entry: cnt[i]; rods (RR) the first PAIR_STAGE keys in stage
+// (element-major) and overflowing entries in ovl; shells the partner bits of
+// the first 32 mask_words positions and entries with pairs past them in ovl.
+template <bool RR>
+__global__ void __launch_bounds__(CB_THREADS) k_pairs_count(PairArgs A, uint32_t* __restrict__ cnt,
+                                                            uint64_t* __restrict__ stage, uint32_t* __restrict__ ovl,
+                                                            unsigned int* __restrict__ novl,
+                                                            unsigned long long* __restrict__ fetch) {
+  const Topo& t = A.t;
+  constexpr uint32_t K = RR ? PAIR_STAGE : 0;
+  const int nbits = 32 * A.mask_words;
+  int64_t next = 0, end = 0;
+  bool drained = false, have = false;
+  // the lane's entry
+  int64_t i = 0;
+  uint32_t P = 0, type = 0, ibase = 0, jbase = 0, home = 0;
+  int rs = 0, rm = 0, ra = 0, j0 = 0, j1 = 0, jj = 0;
+  Grid G{};
+  float4 plo{}, phi{};
+  int pv[3] = {-1, -1, -1};
+  uint32_t count = 0, word = 0, beyond = 0;
+  // per-lane totals, reduced once at the end
+  uint32_t n32 = 0, n64 = 0;
+  unsigned maxr = 0;
+  for (;;) {
+    // idle lanes take entries until each has one with partners or none are left
+    for (;;) {
+      const int64_t e = warp_take(!have, fetch, A.ne, 128, next, end, drained);
+      if (e >= 0) {
+        const EntryRange R = entry_range(A, e);
+        int a0 = R.j0, a1 = R.j1;
+        const int m = R.e - R.s, a = (int)(e - R.s);
+        if (RR && !R.none) {
+          a0 = 0;
+          a1 = (m % 2 == 0 && a < m / 2) ? m / 2 : (m - 1) / 2;
+        }
+        if (!RR && !R.none) maxr = max(maxr, (unsigned)(a1 - a0));
+        if (R.none || a1 <= a0) {
+          cnt[e] = 0;
+        } else {
+          i = e;
+          P = R.P;
+          type = R.type;
+          ibase = R.ibase;
+          jbase = R.jbase;
+          rs = R.s;
+          rm = m;
+          ra = a;
+          j0 = a0;
+          j1 = a1;
+          jj = a0;
+          const uint64_t kc = A.ekey[e];
+          G = A.grids[kc >> 30];
+          home = (uint32_t)(kc & 0x3fffffffull);
+          plo = A.ebox[2 * (size_t)e];
+          phi = A.ebox[2 * (size_t)e + 1];
+          prim_verts(t, (int)P, pv);
+          count = word = beyond = 0;
+          have = true;
+        }
+      }
+      if (drained || __all_sync(0xffffffffu, have)) break;
+    }
+    if (!__any_sync(0xffffffffu, have)) break;  // drained, and every lane done
+    if (have) {
+      int j = jj;
+      if (RR) {
+        j = ra + 1 + jj;
+        if (j >= rm) j -= rm;
+        j += rs;
+      }
+      const uint32_t Q = A.eval[j];
+      bool acc = false;
+      const float4 qlo = A.ebox[2 * (size_t)j], qhi = A.ebox[2 * (size_t)j + 1];
+      if (plo.x <= qhi.x && qlo.x <= phi.x && plo.y <= qhi.y && qlo.y <= phi.y && plo.z <= qhi.z &&
+          qlo.z <= phi.z) {
+        // home cell: low corner of the intersection
+        const uint32_t hc = morton(cell_of(fmaxf(plo.x, qlo.x), G.ox, G.inv, G.dx),
+                                   cell_of(fmaxf(plo.y, qlo.y), G.oy, G.inv, G.dy),
+                                   cell_of(fmaxf(plo.z, qlo.z), G.oz, G.inv, G.dz));
+        if (hc == home) {
+          int qv[3];
+          prim_verts(t, (int)Q, qv);
+          bool inc = false;
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) inc |= (pv[a] >= 0 && pv[a] == qv[b]);
+          if (!inc) {
+            const bool sure = nextup(plo.x) <= nextdn(qhi.x) && nextup(qlo.x) <= nextdn(phi.x) &&
+                              nextup(plo.y) <= nextdn(qhi.y) && nextup(qlo.y) <= nextdn(phi.y) &&
+                              nextup(plo.z) <= nextdn(qhi.z) && nextup(qlo.z) <= nextdn(phi.z);
+            ++n32;
+            acc = true;
+            if (!sure) {
+              ++n64;
+              const double* b1 = A.box64 + (size_t)P * 6;
+              const double* b2 = A.box64 + (size_t)Q * 6;
+#pragma unroll
+              for (int k = 0; k < 3; ++k) acc = acc && (b1[k] <= b2[3 + k]) && (b2[k] <= b1[3 + k]);
+            }
+          }
+        }
+      }
+      if (acc) {
+        if (RR && count < K) {
+          // the pair's key: RR pairs whose partner is the lower primitive take it first
+          const bool swap = j < (int)i;
+          stage[(size_t)count * A.ne + i] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
+        }
+        ++count;
+      }
+      if (!RR) {
+        const int b = jj - j0;
+        if (b < nbits) {
+          word |= (uint32_t)acc << (b & 31);
+          if ((b & 31) == 31 || jj + 1 == j1) {
+            A.mask[(size_t)(b >> 5) * A.ne + i] = word;
+            word = 0;
+          }
+        } else {
+          beyond += acc;
+        }
+      }
+      if (++jj >= j1) {
+        cnt[i] = count;
+        if ((RR && count > K) || (!RR && beyond > 0)) ovl[atomicAdd(novl, 1u)] = (uint32_t)i;
+        have = false;
+      }
+    }
+  }
+  if (A.fpstat) {
+    const unsigned a32 = __reduce_add_sync(0xffffffffu, n32), a64 = __reduce_add_sync(0xffffffffu, n64);
+    if ((threadIdx.x & 31) == 0) {
+      if (a32) atomicAdd(&A.fpstat[0], (unsigned long long)a32);
+      if (a64) atomicAdd(&A.fpstat[1], (unsigned long long)a64);
+    }
+  }
+  if (!RR && A.maxr) {
+    const unsigned mr = __reduce_max_sync(0xffffffffu, maxr);
+    if ((threadIdx.x & 31) == 0 && mr) atomicMax(A.maxr, mr);
+  }
+}
+
 // count pass (FILL = false, one thread per entry): cnt[i] = number of pairs
 // entry i reports.  Rod cells (RR): the first PAIR_STAGE of them are staged
 // (element-major, stage[k * ne + i]) and entries with more are listed in
@@ -582,6 +737,20 @@ __global__ void k_expand(int64_t nc, const uint64_t* __restrict__ ck, int bi, in
   out[q] = cb_key(type, i, j);
 }
 
+// resident blocks per SM of the count pass for a block size (queried once)
+int count_blocks_per_sm(bool rods, int pb) {
+  static int cache[2][3] = {};
+  const int k = pb == 64 ? 0 : pb == 128 ? 1 : 2;
+  int& v = cache[rods ? 1 : 0][k];
+  if (v == 0) {
+    int b = 0;
+    if (rods) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_count<true>, pb, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_count<false>, pb, 0);
+    v = std::max(b, 1);
+  }
+  return v;
+}
+
 }  // namespace
 
 cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* p, bool swept, bool sort_out,
@@ -595,6 +764,9 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   Topo t{s->kind, s->n, s->T, s->E, bp<int32_t>(s->ev0), bp<int32_t>(s->ev1), bp<int32_t>(s->tv)};
   CB_TRY(buf_ensure(w.box32, sizeof(float4) * 2 * (size_t)np, st));
   CB_TRY(buf_ensure(w.box64, sizeof(double) * 6 * (size_t)np, st));
+  // per-stencil activation: the static phase keeps the uninflated boxes for contact_filter
+  const bool raw = !swept && !p && !sort_out && s->per_stencil();
+  if (raw) CB_TRY(buf_ensure(w.box_raw, sizeof(double) * 6 * (size_t)np, st));
   CB_TRY(buf_ensure(w.bounds, sizeof(uint32_t) * BOUNDS_STRIDE * (size_t)M, st));
   CB_TRY(buf_ensure(w.grids, sizeof(Grid) * (size_t)M, st));
   CB_TRY(buf_ensure(w.cx, sizeof(double) * 4 * (size_t)M, st));
@@ -609,7 +781,8 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   CB_CUDA(cudaMemcpyAsync(s->hstage.p, hstage, sizeof(double) * M, cudaMemcpyHostToDevice, st));
   k_bounds_init<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(bounds, M);
   k_boxes<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(t, np, x, p, bp<double>(s->hstage), bp<int32_t>(s->vsc),
-                                                       bp<float4>(w.box32), bp<double>(w.box64), bounds);
+                                                       bp<float4>(w.box32), bp<double>(w.box64),
+                                                       raw ? bp<double>(w.box_raw) : nullptr, bounds);
   CB_CUDA(cudaGetLastError());
   std::vector<uint32_t> hb((size_t)M * BOUNDS_STRIDE);
   CB_CUDA(cudaMemcpyAsync(hstage, bounds, sizeof(uint32_t) * BOUNDS_STRIDE * M, cudaMemcpyDeviceToHost, st));
@@ -753,7 +926,7 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   unsigned int* maxr = (unsigned int*)(scalars(s) + SC_MAXR) + wi;
   A.maxr = rods ? nullptr : maxr;
   if (!rods) CB_CUDA(cudaMemsetAsync(maxr, 0, sizeof(unsigned int), st));
-  auto pairs = [&](bool fill, uint64_t* o) {
+  auto pairs = [&](bool fill, uint64_t* o) -> cb_status {
     uint32_t* c = bp<uint32_t>(w.pair_cnt);
     const uint32_t* f = fill ? bp<uint32_t>(w.pair_off) : nullptr;
     uint64_t* sg = bp<uint64_t>(w.stage);
@@ -769,11 +942,16 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
         k_pairs<true, false><<<g, pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
       }
     } else {
-      if (rods) k_pairs<false, true><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
-      else k_pairs<false, false><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
+      // persistent warps over the entries: as many blocks as are resident at once
+      unsigned long long* fetch = (unsigned long long*)(scalars(s) + SC_FETCH);
+      CB_CUDA(cudaMemsetAsync(fetch, 0, sizeof(unsigned long long), st));
+      const int grid = (int)std::min<int64_t>(cb_grid(ne, pb), (int64_t)s->n_sms * count_blocks_per_sm(rods, pb));
+      if (rods) k_pairs_count<true><<<grid, pb, 0, cb_count(st)>>>(A, c, sg, ov, novl, fetch);
+      else k_pairs_count<false><<<grid, pb, 0, cb_count(st)>>>(A, c, sg, ov, novl, fetch);
     }
+    return CB_OK;
   };
-  pairs(false, nullptr);
+  CB_TRY(pairs(false, nullptr));
   cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off), ne,
                                           bp<uint32_t>(w.scan_tmp), tot_dev, st);
   CB_CUDA(cudaGetLastError());
@@ -788,12 +966,12 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   if (!sort_out) {
     // canonical keys straight from the fill pass, in hash-cell order
     CB_TRY(buf_ensure(out, sizeof(uint64_t) * (size_t)nc, st));
-    pairs(true, bp<uint64_t>(out));
+    CB_TRY(pairs(true, bp<uint64_t>(out)));
     CB_CUDA(cudaGetLastError());
     return CB_OK;
   }
   for (int b = 0; b < 2; ++b) CB_TRY(buf_ensure(w.ckey[b], sizeof(uint64_t) * (size_t)nc, st));
-  pairs(true, bp<uint64_t>(w.ckey[0]));
+  CB_TRY(pairs(true, bp<uint64_t>(w.ckey[0])));
   const int cbits = s->bits_i + s->bits_j + (s->kind == CB_SHELL ? 2 : 0);
   CB_TRY(buf_ensure(w.hist, sizeof(uint32_t) * (size_t)cbp::radix_hist_elems(nc), st));
   CB_TRY(buf_ensure(w.scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(cbp::radix_hist_elems(nc)) + 8),

@@ -137,13 +137,44 @@ __global__ void k_rest_filter(int64_t nc, const uint64_t* __restrict__ keys, con
   if ((threadIdx.x & 31) == 0 && mb != 0x7ff0000000000000ull) atomicMin(dmin_bits, mb);
 }
 
+// Per-stencil activation: whether the FP64 boxes of a pair's two primitives
+// (uninflated boxes of the static broad phase), each inflated by half the
+// pair's own width fw, overlap on all three axes (closed intervals).
+__device__ __forceinline__ bool within_own_width(const double* __restrict__ box_raw, int64_t prim1, int64_t prim2,
+                                                 double fw) {
+  const double h = xmul(0.5, fw);
+  const double* b1 = box_raw + prim1 * 6;
+  const double* b2 = box_raw + prim2 * 6;
+  bool ov = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) ov = ov && xsub(b1[k], h) <= xadd(b2[3 + k], h) && xsub(b2[k], h) <= xadd(b1[3 + k], h);
+  return ov;
+}
+
+// class-F width of a pair whose first stencil vertex is v0 (per member:
+// dbar_min, or its component's with CB_DBAR_PER_COMPONENT)
+__device__ __forceinline__ double member_f_width(const MemberParams& M, const unsigned long long* __restrict__ dbar_comp,
+                                                 const int32_t* __restrict__ comp, int v0) {
+  return M.per_comp ? __longlong_as_double((long long)dbar_comp[comp[v0]]) : M.dbar_min;
+}
+
+// class byte of a filtered candidate dropped by the per-stencil activation
+constexpr uint8_t KL_DROPPED = 0xFE;
+
+struct StencilArgs {
+  const double* __restrict__ box_raw;            // null unless a member uses per-stencil activation
+  const unsigned long long* __restrict__ dbar_comp;
+  const int32_t* __restrict__ comp;
+  unsigned long long* __restrict__ ndrop;
+};
+
 __global__ void k_filter_rod(int64_t nc, const uint64_t* __restrict__ cand, const int32_t* __restrict__ ev0,
                              const int32_t* __restrict__ comp, const int32_t* __restrict__ win,
                              const int32_t* __restrict__ wst, const int32_t* __restrict__ rloop,
                              const int32_t* __restrict__ vsc, const MemberParams* __restrict__ mp,
-                             uint8_t* __restrict__ klass, unsigned long long* __restrict__ nfilt) {
+                             uint8_t* __restrict__ klass, unsigned long long* __restrict__ nfilt, StencilArgs SA) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t f = 0;
+  uint32_t f = 0, dropped = 0;
   if (c < nc) {
     const uint64_t key = cand[c];
     const uint32_t k = cb_key_i(key), l = cb_key_j(key);
@@ -153,27 +184,67 @@ __global__ void k_filter_rod(int64_t nc, const uint64_t* __restrict__ cand, cons
     f = (!M.filter_off && same && rod_filtered(win, wst, M.loops != 0, k, l)) ? 1u : 0u;
     // Kaldor culling: edges are numbered along each polyline, so the gap is
     // l - k (the shorter way round on a closed loop)
-    klass[c] = (M.cull_radius > 0 && same && rod_gap(rloop, k, l) <= M.cull_radius) ? (uint8_t)3 : (uint8_t)f;
+    uint8_t kl = (M.cull_radius > 0 && same && rod_gap(rloop, k, l) <= M.cull_radius) ? (uint8_t)3 : (uint8_t)f;
+    if (kl == 1 && M.per_stencil &&
+        !within_own_width(SA.box_raw, k, l, member_f_width(M, SA.dbar_comp, SA.comp, v0))) {
+      kl = KL_DROPPED;
+      f = 0;
+      dropped = 1;
+    }
+    klass[c] = kl;
   }
   uint32_t b = __ballot_sync(0xffffffffu, f);
   if ((threadIdx.x & 31) == 0 && b) atomicAdd(nfilt, (unsigned long long)__popc(b));
+  b = __ballot_sync(0xffffffffu, dropped);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(SA.ndrop, (unsigned long long)__popc(b));
 }
 
 __global__ void k_filter_shell(int64_t nc, const uint64_t* __restrict__ cand, const uint64_t* __restrict__ frest,
                                const uint32_t* __restrict__ row_pt, const uint32_t* __restrict__ row_ee, int64_t nf,
                                const int32_t* __restrict__ ev0, const int32_t* __restrict__ vsc,
                                const MemberParams* __restrict__ mp, uint8_t* __restrict__ klass,
-                               unsigned long long* __restrict__ nfilt) {
+                               unsigned long long* __restrict__ nfilt, int n, int T, StencilArgs SA) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t f = 0;
+  uint32_t f = 0, dropped = 0;
   if (c < nc) {
     const uint64_t key = cand[c];
-    const int v0 = cb_key_type(key) == CB_KEY_PT ? (int)cb_key_i(key) : ev0[cb_key_i(key)];
-    if (!mp[vsc[v0]].filter_off && nf > 0) f = frest_contains(frest, row_pt, row_ee, key) ? 1u : 0u;
-    klass[c] = (uint8_t)f;
+    const bool pt = cb_key_type(key) == CB_KEY_PT;
+    const int v0 = pt ? (int)cb_key_i(key) : ev0[cb_key_i(key)];
+    const MemberParams& M = mp[vsc[v0]];
+    if (!M.filter_off && nf > 0) f = frest_contains(frest, row_pt, row_ee, key) ? 1u : 0u;
+    uint8_t kl = (uint8_t)f;
+    if (f && M.per_stencil) {
+      // broad-phase primitive ids: vertices, then triangles, then edges
+      const int64_t p1 = pt ? (int64_t)cb_key_i(key) : (int64_t)n + T + cb_key_i(key);
+      const int64_t p2 = pt ? (int64_t)n + cb_key_j(key) : (int64_t)n + T + cb_key_j(key);
+      if (!within_own_width(SA.box_raw, p1, p2, member_f_width(M, SA.dbar_comp, SA.comp, v0))) {
+        kl = KL_DROPPED;
+        f = 0;
+        dropped = 1;
+      }
+    }
+    klass[c] = kl;
   }
   uint32_t b = __ballot_sync(0xffffffffu, f);
   if ((threadIdx.x & 31) == 0 && b) atomicAdd(nfilt, (unsigned long long)__popc(b));
+  b = __ballot_sync(0xffffffffu, dropped);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(SA.ndrop, (unsigned long long)__popc(b));
+}
+
+// per-stencil activation: keep flags of the candidates, then the kept ones
+// (keys and classes) in their order
+__global__ void k_keep_flag(int64_t nc, const uint8_t* __restrict__ klass, uint32_t* __restrict__ flag) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc) flag[c] = klass[c] != KL_DROPPED ? 1u : 0u;
+}
+__global__ void k_keep_write(int64_t nc, const uint64_t* __restrict__ cand, const uint8_t* __restrict__ klass,
+                             const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                             uint64_t* __restrict__ cand_out, uint8_t* __restrict__ klass_out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc && flag[c]) {
+    cand_out[pos[c]] = cand[c];
+    klass_out[pos[c]] = klass[c];
+  }
 }
 
 // ------------------------------------------------------------------ (c) ----
@@ -2126,17 +2197,48 @@ cb_status filter_apply(cb_scene* s, cudaStream_t st) {
   CB_TRY(buf_ensure(s->klass, (size_t)std::max<int64_t>(1, nc), st));
   unsigned long long* nf = (unsigned long long*)(scalars(s) + SC_NFILT);
   k_set_u64<<<1, 1, 0, cb_count(st)>>>(nf, 0ull);
+  s->n_dropped = 0;
   if (nc == 0) return CB_OK;
+  const bool ps = s->per_stencil();
+  unsigned long long* ndrop = (unsigned long long*)(scalars(s) + SC_COUNT1);
+  if (ps) {
+    if (!s->bw.box_raw.p) return CB_ERR_ARG;  // the candidates came from before the mode was set
+    k_set_u64<<<1, 1, 0, cb_count(st)>>>(ndrop, 0ull);
+  }
+  const StencilArgs SA{ps ? bp<double>(s->bw.box_raw) : nullptr, bp<unsigned long long>(s->dbar_comp),
+                       bp<int32_t>(s->comp), ndrop};
   if (s->kind == CB_ROD)
     k_filter_rod<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(
         nc, bp<uint64_t>(s->cand), bp<int32_t>(s->ev0), bp<int32_t>(s->comp), bp<int32_t>(s->win),
         bp<int32_t>(s->wst), bp<int32_t>(s->rloop), bp<int32_t>(s->vsc), bp<MemberParams>(s->mp),
-        bp<uint8_t>(s->klass), nf);
+        bp<uint8_t>(s->klass), nf, SA);
   else
     k_filter_shell<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(
         nc, bp<uint64_t>(s->cand), bp<uint64_t>(s->frest), bp<uint32_t>(s->frow_pt), bp<uint32_t>(s->frow_ee),
-        s->n_frest, bp<int32_t>(s->ev0), bp<int32_t>(s->vsc), bp<MemberParams>(s->mp), bp<uint8_t>(s->klass), nf);
+        s->n_frest, bp<int32_t>(s->ev0), bp<int32_t>(s->vsc), bp<MemberParams>(s->mp), bp<uint8_t>(s->klass), nf,
+        s->n, s->T, SA);
   CB_CUDA(cudaGetLastError());
+  if (!ps) return CB_OK;
+  // per-stencil activation: drop the class-F candidates outside their own width
+  uint64_t hd;
+  CB_TRY(read_scalars(s, SC_COUNT1, 1, &hd, st));
+  s->n_dropped = (int64_t)hd;
+  if (hd == 0) return CB_OK;
+  CB_TRY(buf_ensure(s->cflag, sizeof(uint32_t) * (size_t)nc, st));
+  CB_TRY(buf_ensure(s->cpos, sizeof(uint32_t) * ((size_t)nc + 1), st));
+  CB_TRY(buf_ensure(s->scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(nc) + 8), st));
+  CB_TRY(buf_ensure(s->cand_alt, sizeof(uint64_t) * (size_t)nc, st));
+  CB_TRY(buf_ensure(s->klass_alt, (size_t)nc, st));
+  k_keep_flag<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(nc, bp<uint8_t>(s->klass), bp<uint32_t>(s->cflag));
+  cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(s->cflag), bp<uint32_t>(s->cpos), nc,
+                                          bp<uint32_t>(s->scan_tmp), (uint32_t*)nullptr, st);
+  k_keep_write<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(nc, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass),
+                                                            bp<uint32_t>(s->cflag), bp<uint32_t>(s->cpos),
+                                                            bp<uint64_t>(s->cand_alt), bp<uint8_t>(s->klass_alt));
+  CB_CUDA(cudaGetLastError());
+  std::swap(s->cand, s->cand_alt);
+  std::swap(s->klass, s->klass_alt);
+  s->n_cand = nc - s->n_dropped;
   return CB_OK;
 }
 

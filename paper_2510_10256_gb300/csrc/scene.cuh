@@ -56,6 +56,7 @@ struct MemberParams {
   double dbar_fmax;       // largest class-F width of the member (= dbar_min unless per_comp)
   int32_t loops;          // rods: the member has closed loops (backward arc-length windows to test)
   int32_t mollify;        // CB_EE_MOLLIFIER: edge-edge pairs take IPC's mollifier
+  int32_t per_stencil;    // CB_PER_STENCIL: class-F candidates outside their own width are dropped
 };
 
 // Spatial-hash grid of one member.
@@ -71,6 +72,7 @@ struct BroadWork {
   int pair_block = CB_THREADS;  // threads per block of the pair enumeration (tuning knob)
   DevBuf box32;       // float4 lo, float4 hi per primitive
   DevBuf box64;       // double lo[3], hi[3] per primitive
+  DevBuf box_raw;     // per-stencil activation (static phase): double lo[3], hi[3] per primitive, not inflated
   DevBuf bounds;      // per member: 6 x uint32 ordered-float min/max, 2 pad, double extent sum
   DevBuf grids;       // Grid per member
   DevBuf cx;          // per member: double centre[3], X (max |coordinate - centre|)
@@ -120,6 +122,7 @@ struct cb_scene {
   void* hstage_host = nullptr;  // pinned staging (the largest per-member record x members + 256)
   cudaStream_t last_stream = nullptr;
   int device = 0;
+  int n_sms = 152;      // multiprocessors of the device (grid sizes of persistent kernels)
 
   // topology on device
   DevBuf ev0, ev1;      // int32 [E]
@@ -149,6 +152,13 @@ struct cb_scene {
   DevBuf cand;          // uint64 [nc] sorted candidate keys
   int64_t n_cand = 0;
   DevBuf klass;         // uint8 [nc]
+  DevBuf cand_alt, klass_alt;  // per-stencil activation: the compacted candidates before the swap
+  int64_t n_dropped = 0;       // last contact_filter: class-F candidates outside their own width
+  bool per_stencil() const {
+    for (const MemberParams& m : hmp)
+      if (m.per_stencil) return true;
+    return false;
+  }
   DevBuf cd;            // double [nc] distance
   DevBuf cflag;         // uint32 [nc] active flag
   DevBuf cpos;          // uint32 [nc+1] scan of flags
@@ -227,7 +237,8 @@ enum {
   SC_NBK = 18,          // BSR pattern: keys left after the per-run sets of k_block_keys
   SC_MAXR = 19,         // broad phase, shells: two uint32 -- longest partner range (static, swept)
   SC_NMOLL = 20,        // barrier_eval: mollified edge-edge pairs
-  SC_N = 21
+  SC_FETCH = 21,        // ccd_step: next list position the exact-CCD warps take
+  SC_N = 22
 };
 // slot of the pinned host scratch that receives the SC_MAXR pair (read_scalars uses the first SC_N)
 constexpr int H_PINNED_MAXR = 62;

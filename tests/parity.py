@@ -23,12 +23,13 @@ import oracle as O
 
 
 def run_gpu(sc, mode="double", core_temp=True, x=None, p=None, paper_literal=False, cull_radius=0,
-            per_component=False, mollifier=False):
+            per_component=False, mollifier=False, per_stencil=False):
     import torch
     from paper_2510_10256_gb300.contact import ContactScene
     dev = torch.device("cuda:0")
     cs = ContactScene.from_scene(sc, mode=mode, core_temp=core_temp, paper_literal=paper_literal,
-                                 cull_radius=cull_radius, per_component=per_component, mollifier=mollifier)
+                                 cull_radius=cull_radius, per_component=per_component, mollifier=mollifier,
+                                 per_stencil=per_stencil)
     xx = torch.from_numpy(np.ascontiguousarray(sc.x if x is None else x)).to(dev)
     pp = torch.from_numpy(np.ascontiguousarray(sc.p if p is None else p)).to(dev)
     energy = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -173,13 +174,13 @@ def _compare_bsr(sc, g, orc: O.PassResult, diff: set) -> dict:
             "bsr_relerr": float((verr / (va + 1e-300)).max()) if verr.size else 0.0}
 
 
-def run_gpu_batch(scenes, mode="double", xs=None, ps=None):
+def run_gpu_batch(scenes, mode="double", xs=None, ps=None, **kw):
     """One batched pass over several scenes (cb_batch_create); returns one
     result dict per member in run_gpu's format (member-local numbering)."""
     import torch
     from paper_2510_10256_gb300.contact import ContactBatch, ContactScene
     dev = torch.device("cuda:0")
-    members = [ContactScene.from_scene(sc, mode=mode) for sc in scenes]
+    members = [ContactScene.from_scene(sc, mode=mode, **kw) for sc in scenes]
     dbar = [m.stats()["dbar_min"] for m in members]
     b = ContactBatch(members)
     for m in members:

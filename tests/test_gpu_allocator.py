@@ -48,13 +48,13 @@ def test_torch_allocator_accounts_for_the_scene():
     held = cs.stats()["device_bytes"]
     assert held > 0
     d = torch.cuda.memory_allocated() - base
-    # torch rounds each block up to 512 bytes
-    assert held <= d <= held + 512 * 200, (held, d)
+    # torch rounds each block up: to 512 bytes, and blocks of 10 MiB or more to 2 MiB
+    assert held <= d <= 1.05 * held + 512 * 200, (held, d)
     keep = _pass(cs, sc)
     held2 = cs.stats()["device_bytes"]
     assert held2 > held                              # the pass buffers
     d2 = torch.cuda.memory_allocated() - base - sum(t.numel() * t.element_size() for t in keep)
-    assert held2 <= d2 <= held2 + 512 * 200, (held2, d2)
+    assert held2 <= d2 <= 1.05 * held2 + 512 * 200, (held2, d2)
     assert torch.cuda.memory_reserved() >= base + held2
     # the results are the oracle's
     o = O.contact_pass(sc)
