@@ -2106,12 +2106,14 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
   } else {
     // rest broad phase at the full activation, then rest distances below a
     int64_t nr = 0;
-    DevBuf rc;
+    ScopedBuf rcs(st);
+    DevBuf& rc = rcs.b;
     // positions of the reference distances: the flat pattern when given, else the rest shape
     const double* rf = s->ruv.p ? bp<double>(s->ruv) : bp<double>(s->rest);
     CB_TRY(broad_phase(s, s->bw, rf, nullptr, false, true, rc, &nr, st));
     if (nr > 0) {
-      DevBuf flag, pos, dbar;
+      ScopedBuf flags(st), poss(st), dbars(st);
+      DevBuf &flag = flags.b, &pos = poss.b, &dbar = dbars.b;
       CB_TRY(buf_ensure(flag, sizeof(uint32_t) * (size_t)nr, st));
       CB_TRY(buf_ensure(pos, sizeof(uint32_t) * ((size_t)nr + 1), st));
       CB_TRY(buf_ensure(dbar, sizeof(double) * (size_t)nr, st));
@@ -2138,14 +2140,10 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
       CB_TRY(read_scalars(s, SC_DBAR_MIN_BITS, 1, &h[1], st));
       memcpy(&s->dbar_min, &h[1], 8);
       s->n_frest = nf_;
-      buf_free(flag, st);
-      buf_free(pos, st);
-      buf_free(dbar, st);
     } else {
       s->dbar_min = INFINITY;
       s->n_frest = 0;
     }
-    buf_free(rc, st);
   }
   if (s->n_frest > 0 && !(s->dbar_min > 0.0)) return CB_ERR_DEGENERATE;
   s->dbar_fmax = s->dbar_min;

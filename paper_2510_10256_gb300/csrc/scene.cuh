@@ -36,6 +36,17 @@ struct AllocScope {
 // hand the memory out again at once).
 cb_status buf_ensure(DevBuf& b, size_t bytes, cudaStream_t st);
 void buf_free(DevBuf& b, cudaStream_t st);
+
+// A device buffer local to one call, released on every way out of its scope
+// (error returns included).
+struct ScopedBuf {
+  DevBuf b;
+  cudaStream_t st;
+  explicit ScopedBuf(cudaStream_t s) : st(s) {}
+  ~ScopedBuf() { buf_free(b, st); }
+  ScopedBuf(const ScopedBuf&) = delete;
+  ScopedBuf& operator=(const ScopedBuf&) = delete;
+};
 template <typename T>
 static inline T* bp(const DevBuf& b) {
   return (T*)b.p;
