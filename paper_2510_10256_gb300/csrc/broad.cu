@@ -506,156 +506,6 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
 }
 
 
-// Count pass with lane refill: the same tests, decisions and outputs as
-// pairs_of_entry<false, RR> for every entry, but an entry's partner range
-// (from none to thousands of positions) no longer holds its warp: the warps
-// are persistent and a lane that finishes an entry takes the next one
-// (warp_take), so the lanes of a warp stay busy until the entries run out.
-// Triangle entries of shell cells (no partners) are finished at once.
-// Outputs per entry: cnt[i]; rods (RR) the first PAIR_STAGE keys in stage
-// (element-major) and overflowing entries in ovl; shells the partner bits of
-// the first 32 mask_words positions and entries with pairs past them in ovl.
-template <bool RR>
-__global__ void __launch_bounds__(CB_THREADS) k_pairs_count(PairArgs A, uint32_t* __restrict__ cnt,
-                                                            uint64_t* __restrict__ stage, uint32_t* __restrict__ ovl,
-                                                            unsigned int* __restrict__ novl,
-                                                            unsigned long long* __restrict__ fetch) {
-  const Topo& t = A.t;
-  constexpr uint32_t K = RR ? PAIR_STAGE : 0;
-  const int nbits = 32 * A.mask_words;
-  int64_t next = 0, end = 0;
-  bool drained = false, have = false;
-  // the lane's entry
-  int64_t i = 0;
-  uint32_t P = 0, type = 0, ibase = 0, jbase = 0, home = 0;
-  int rs = 0, rm = 0, ra = 0, j0 = 0, j1 = 0, jj = 0;
-  Grid G{};
-  float4 plo{}, phi{};
-  int pv[3] = {-1, -1, -1};
-  uint32_t count = 0, word = 0, beyond = 0;
-  // per-lane totals, reduced once at the end
-  uint32_t n32 = 0, n64 = 0;
-  unsigned maxr = 0;
-  for (;;) {
-    // idle lanes take entries until each has one with partners or none are left
-    for (;;) {
-      const int64_t e = warp_take(!have, fetch, A.ne, 128, next, end, drained);
-      if (e >= 0) {
-        const EntryRange R = entry_range(A, e);
-        int a0 = R.j0, a1 = R.j1;
-        const int m = R.e - R.s, a = (int)(e - R.s);
-        if (RR && !R.none) {
-          a0 = 0;
-          a1 = (m % 2 == 0 && a < m / 2) ? m / 2 : (m - 1) / 2;
-        }
-        if (!RR && !R.none) maxr = max(maxr, (unsigned)(a1 - a0));
-        if (R.none || a1 <= a0) {
-          cnt[e] = 0;
-        } else {
-          i = e;
-          P = R.P;
-          type = R.type;
-          ibase = R.ibase;
-          jbase = R.jbase;
-          rs = R.s;
-          rm = m;
-          ra = a;
-          j0 = a0;
-          j1 = a1;
-          jj = a0;
-          const uint64_t kc = A.ekey[e];
-          G = A.grids[kc >> 30];
-          home = (uint32_t)(kc & 0x3fffffffull);
-          plo = A.ebox[2 * (size_t)e];
-          phi = A.ebox[2 * (size_t)e + 1];
-          prim_verts(t, (int)P, pv);
-          count = word = beyond = 0;
-          have = true;
-        }
-      }
-      if (drained || __all_sync(0xffffffffu, have)) break;
-    }
-    if (!__any_sync(0xffffffffu, have)) break;  // drained, and every lane done
-    if (have) {
-      int j = jj;
-      if (RR) {
-        j = ra + 1 + jj;
-        if (j >= rm) j -= rm;
-        j += rs;
-      }
-      const uint32_t Q = A.eval[j];
-      bool acc = false;
-      const float4 qlo = A.ebox[2 * (size_t)j], qhi = A.ebox[2 * (size_t)j + 1];
-      if (plo.x <= qhi.x && qlo.x <= phi.x && plo.y <= qhi.y && qlo.y <= phi.y && plo.z <= qhi.z &&
-          qlo.z <= phi.z) {
-        // home cell: low corner of the intersection
-        const uint32_t hc = morton(cell_of(fmaxf(plo.x, qlo.x), G.ox, G.inv, G.dx),
-                                   cell_of(fmaxf(plo.y, qlo.y), G.oy, G.inv, G.dy),
-                                   cell_of(fmaxf(plo.z, qlo.z), G.oz, G.inv, G.dz));
-        if (hc == home) {
-          int qv[3];
-          prim_verts(t, (int)Q, qv);
-          bool inc = false;
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) inc |= (pv[a] >= 0 && pv[a] == qv[b]);
-          if (!inc) {
-            const bool sure = nextup(plo.x) <= nextdn(qhi.x) && nextup(qlo.x) <= nextdn(phi.x) &&
-                              nextup(plo.y) <= nextdn(qhi.y) && nextup(qlo.y) <= nextdn(phi.y) &&
-                              nextup(plo.z) <= nextdn(qhi.z) && nextup(qlo.z) <= nextdn(phi.z);
-            ++n32;
-            acc = true;
-            if (!sure) {
-              ++n64;
-              const double* b1 = A.box64 + (size_t)P * 6;
-              const double* b2 = A.box64 + (size_t)Q * 6;
-#pragma unroll
-              for (int k = 0; k < 3; ++k) acc = acc && (b1[k] <= b2[3 + k]) && (b2[k] <= b1[3 + k]);
-            }
-          }
-        }
-      }
-      if (acc) {
-        if (RR && count < K) {
-          // the pair's key: RR pairs whose partner is the lower primitive take it first
-          const bool swap = j < (int)i;
-          stage[(size_t)count * A.ne + i] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
-        }
-        ++count;
-      }
-      if (!RR) {
-        const int b = jj - j0;
-        if (b < nbits) {
-          word |= (uint32_t)acc << (b & 31);
-          if ((b & 31) == 31 || jj + 1 == j1) {
-            A.mask[(size_t)(b >> 5) * A.ne + i] = word;
-            word = 0;
-          }
-        } else {
-          beyond += acc;
-        }
-      }
-      if (++jj >= j1) {
-        cnt[i] = count;
-        if ((RR && count > K) || (!RR && beyond > 0)) ovl[atomicAdd(novl, 1u)] = (uint32_t)i;
-        have = false;
-      }
-    }
-  }
-  if (A.fpstat) {
-    const unsigned a32 = __reduce_add_sync(0xffffffffu, n32), a64 = __reduce_add_sync(0xffffffffu, n64);
-    if ((threadIdx.x & 31) == 0) {
-      if (a32) atomicAdd(&A.fpstat[0], (unsigned long long)a32);
-      if (a64) atomicAdd(&A.fpstat[1], (unsigned long long)a64);
-    }
-  }
-  if (!RR && A.maxr) {
-    const unsigned mr = __reduce_max_sync(0xffffffffu, maxr);
-    if ((threadIdx.x & 31) == 0 && mr) atomicMax(A.maxr, mr);
-  }
-}
-
 // count pass (FILL = false, one thread per entry): cnt[i] = number of pairs
 // entry i reports.  Rod cells (RR): the first PAIR_STAGE of them are staged
 // (element-major, stage[k * ne + i]) and entries with more are listed in
@@ -735,20 +585,6 @@ __global__ void k_expand(int64_t nc, const uint64_t* __restrict__ ck, int bi, in
   uint32_t i = (uint32_t)((c >> bj) & ((1ull << bi) - 1ull));
   uint32_t j = (uint32_t)(c & ((1ull << bj) - 1ull));
   out[q] = cb_key(type, i, j);
-}
-
-// resident blocks per SM of the count pass for a block size (queried once)
-int count_blocks_per_sm(bool rods, int pb) {
-  static int cache[2][3] = {};
-  const int k = pb == 64 ? 0 : pb == 128 ? 1 : 2;
-  int& v = cache[rods ? 1 : 0][k];
-  if (v == 0) {
-    int b = 0;
-    if (rods) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_count<true>, pb, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_count<false>, pb, 0);
-    v = std::max(b, 1);
-  }
-  return v;
 }
 
 }  // namespace
@@ -942,12 +778,8 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
         k_pairs<true, false><<<g, pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
       }
     } else {
-      // persistent warps over the entries: as many blocks as are resident at once
-      unsigned long long* fetch = (unsigned long long*)(scalars(s) + SC_FETCH);
-      CB_CUDA(cudaMemsetAsync(fetch, 0, sizeof(unsigned long long), st));
-      const int grid = (int)std::min<int64_t>(cb_grid(ne, pb), (int64_t)s->n_sms * count_blocks_per_sm(rods, pb));
-      if (rods) k_pairs_count<true><<<grid, pb, 0, cb_count(st)>>>(A, c, sg, ov, novl, fetch);
-      else k_pairs_count<false><<<grid, pb, 0, cb_count(st)>>>(A, c, sg, ov, novl, fetch);
+      if (rods) k_pairs<false, true><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
+      else k_pairs<false, false><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
     }
     return CB_OK;
   };
