@@ -770,11 +770,11 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     if (fill) {
       if (rods) {
         k_pairs_copy<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, c, f, sg, o);
-        const int g = (int)std::min<int64_t>(cb_grid(ne, pb), 152 * 8);
+        const int g = (int)std::min<int64_t>(cb_grid(ne, pb), (int64_t)s->n_sms * 8);
         k_pairs<true, true><<<g, pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
       } else {
         k_pairs_emit<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, c, f, o);
-        const int g = (int)std::min<int64_t>(cb_grid(ne, pb), 152 * 8);
+        const int g = (int)std::min<int64_t>(cb_grid(ne, pb), (int64_t)s->n_sms * 8);
         k_pairs<true, false><<<g, pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
       }
     } else {

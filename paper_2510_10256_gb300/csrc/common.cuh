@@ -52,41 +52,6 @@ static inline cudaStream_t cb_count(cudaStream_t st) {
   return st;
 }
 
-// Work distribution of persistent warps over a list of m items (entries of
-// a list, pairs to iterate) whose costs differ widely: a lane that has no
-// item asks for one, the warp claims chunks of `chunk` consecutive items with
-// one atomicAdd on *fetch (zeroed before the launch) and hands them to its
-// asking lanes in lane order.  Every lane of the warp calls it at once with
-// the same warp-uniform state (next, end, drained); it returns this lane's
-// new item, or -1 (not asking, or the list is used up: drained).
-__device__ __forceinline__ int64_t warp_take(bool want, unsigned long long* fetch, int64_t m, int chunk,
-                                             int64_t& next, int64_t& end, bool& drained) {
-  const unsigned lane = threadIdx.x & 31u;
-  unsigned need = __ballot_sync(0xffffffffu, want);
-  int64_t mine = -1;
-  while (need && !drained) {
-    if (next >= end) {
-      unsigned long long b = 0;
-      if (lane == 0) b = atomicAdd(fetch, (unsigned long long)chunk);
-      b = __shfl_sync(0xffffffffu, b, 0);
-      if ((int64_t)b >= m) {
-        drained = true;
-        break;
-      }
-      next = (int64_t)b;
-      end = (int64_t)b + chunk < m ? (int64_t)b + chunk : m;
-    }
-    const int64_t avail = end - next;
-    const int r = __popc(need & ((1u << lane) - 1u));
-    const bool got = ((need >> lane) & 1u) && (int64_t)r < avail;
-    if (got) mine = next + r;
-    const int n_need = __popc(need);
-    next += (int64_t)n_need < avail ? n_need : avail;
-    need &= ~__ballot_sync(0xffffffffu, got);
-  }
-  return mine;
-}
-
 static inline int cb_grid(int64_t n, int per_block = CB_THREADS) {
   int64_t g = (n + per_block - 1) / per_block;
   if (g < 1) g = 1;

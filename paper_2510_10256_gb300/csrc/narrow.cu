@@ -2287,7 +2287,7 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
         bp<int32_t>(s->tv), s->T, bp<float4>(s->xf), bp<double>(s->bw.cx), bp<int32_t>(s->vsc),
         bp<MemberParams>(s->mp), s->n, bp<double>(s->cd),
         bp<int8_t>(s->ctype), bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), bp<uint32_t>(s->dlist), nl);
-    (energy_only ? k_distance_exact<true> : k_distance_exact<false>)<<<std::min<int64_t>(cb_grid(nc), 152 * 16), CB_THREADS, 0, cb_count(st)>>>(
+    (energy_only ? k_distance_exact<true> : k_distance_exact<false>)<<<std::min<int64_t>(cb_grid(nc), (int64_t)s->n_sms * 16), CB_THREADS, 0, cb_count(st)>>>(
         bp<uint32_t>(s->dlist), nc, nl, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass), bp<int32_t>(s->ev0),
         bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T, x, s->n, bp<int32_t>(s->vsc), bp<MemberParams>(s->mp),
         bp<double>(s->cd), bp<int8_t>(s->ctype), bp<uint8_t>(s->ccls), bp<uint32_t>(s->cflag), status, ncore,

@@ -133,7 +133,7 @@ struct cb_scene {
   void* hstage_host = nullptr;  // pinned staging (the largest per-member record x members + 256)
   cudaStream_t last_stream = nullptr;
   int device = 0;
-  int n_sms = 152;      // multiprocessors of the device (grid sizes of persistent kernels)
+  int n_sms = 152;      // multiprocessors of the device (caps of grid-stride launches: a few blocks per SM)
 
   // topology on device
   DevBuf ev0, ev1;      // int32 [E]
@@ -248,8 +248,7 @@ enum {
   SC_NBK = 18,          // BSR pattern: keys left after the per-run sets of k_block_keys
   SC_MAXR = 19,         // broad phase, shells: two uint32 -- longest partner range (static, swept)
   SC_NMOLL = 20,        // barrier_eval: mollified edge-edge pairs
-  SC_FETCH = 21,        // ccd_step: next list position the exact-CCD warps take
-  SC_N = 22
+  SC_N = 21
 };
 // slot of the pinned host scratch that receives the SC_MAXR pair (read_scalars uses the first SC_N)
 constexpr int H_PINNED_MAXR = 62;
