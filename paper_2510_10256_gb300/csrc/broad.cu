@@ -221,6 +221,30 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
 __device__ __forceinline__ uint32_t morton(int x, int y, int z) {
   return spread10((uint32_t)x) | (spread10((uint32_t)y) << 1) | (spread10((uint32_t)z) << 2);
 }
+// x cell index of a Morton cell code (every third bit from bit 0)
+__device__ __forceinline__ int morton_x(uint32_t m) {
+  uint32_t v = m & 0x09249249u;
+  v = (v ^ (v >> 2)) & 0x030C30C3u;
+  v = (v ^ (v >> 4)) & 0x0300F00Fu;
+  v = (v ^ (v >> 8)) & 0x030000FFu;
+  v = (v ^ (v >> 16)) & 0x000003FFu;
+  return (int)v;
+}
+
+// Shell cells are swept along x: within each type group of a cell, entries
+// are sorted by the position of their box's lower x bound inside the cell,
+// quantized to XQ_LEVELS steps.  The map is monotone (FP32 operations with
+// the rounding written out, then floor and clamp), so a partner whose level
+// is above the level of an entry's upper x bound lies beyond it, and so does
+// every partner after it: the entry's scan stops there.
+constexpr int XQ_BITS = 10, XQ_LEVELS = 1 << XQ_BITS;
+constexpr int SWEEP_SHIFT = XQ_BITS + 2;  // cell code above [type group : 2][x level : XQ_BITS]
+__device__ __forceinline__ uint32_t x_level(float v, const Grid& G, int cx) {
+  const float tt = __fmul_rn(__fsub_rn(v, G.ox), G.inv);
+  const float f = __fmul_rn(__fsub_rn(tt, (float)cx), (float)XQ_LEVELS);
+  const float q = floorf(f);
+  return q <= 0.f ? 0u : (q >= (float)(XQ_LEVELS - 1) ? (uint32_t)(XQ_LEVELS - 1) : (uint32_t)q);
+}
 
 __global__ void k_cell_count(Topo t, int np, const float4* __restrict__ box32, const int32_t* __restrict__ vsc,
                              const Grid* __restrict__ grids, uint32_t* __restrict__ cnt) {
@@ -236,7 +260,7 @@ __global__ void k_cell_count(Topo t, int np, const float4* __restrict__ box32, c
 
 __global__ void k_cell_fill(Topo t, int np, const float4* __restrict__ box32, const int32_t* __restrict__ vsc,
                             const Grid* __restrict__ grids, const uint32_t* __restrict__ off,
-                            uint64_t* __restrict__ ekey, uint32_t* __restrict__ eval) {
+                            uint64_t* __restrict__ ekey, uint32_t* __restrict__ eval, bool sweep) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= np) return;
   const int mem = prim_member(t, vsc, q);
@@ -247,10 +271,13 @@ __global__ void k_cell_fill(Topo t, int np, const float4* __restrict__ box32, co
   int z0 = cell_of(lo.z, g.oz, g.inv, g.dz), z1 = cell_of(hi.z, g.oz, g.inv, g.dz);
   uint32_t w = off[q];
   const uint64_t mbits = (uint64_t)mem << 30;
+  // shells: type group (vertex 0, triangle 1, edge 2) and x level below the cell code
+  const uint32_t grp = q < t.n ? 0u : (q < t.n + t.T ? 1u : 2u);
   for (int z = z0; z <= z1; ++z)
     for (int y = y0; y <= y1; ++y)
       for (int xx = x0; xx <= x1; ++xx) {
-        ekey[w] = mbits | morton(xx, y, z);
+        const uint64_t cell = mbits | morton(xx, y, z);
+        ekey[w] = sweep ? (cell << SWEEP_SHIFT) | ((uint64_t)grp << XQ_BITS) | x_level(lo.x, g, xx) : cell;
         eval[w] = (uint32_t)q;
         ++w;
       }
@@ -266,10 +293,10 @@ __global__ void k_gather_boxes(int64_t ne, const uint32_t* __restrict__ eval, co
   ebox[2 * i + 1] = box32[2 * (size_t)q + 1];
 }
 
-__global__ void k_run_flag(int64_t ne, const uint64_t* __restrict__ key, uint32_t* __restrict__ flag) {
+__global__ void k_run_flag(int64_t ne, const uint64_t* __restrict__ key, int shift, uint32_t* __restrict__ flag) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ne) return;
-  flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1u : 0u;
+  flag[i] = (i == 0 || (key[i] >> shift) != (key[i - 1] >> shift)) ? 1u : 0u;
 }
 
 // run_id[i] = index of the run holding entry i; run_start[r] = first entry of run r
@@ -286,11 +313,12 @@ __global__ void k_run_start(int64_t ne, const uint32_t* __restrict__ flag, const
 __device__ __forceinline__ float nextup(float v) { return nextafterf(v, INFINITY); }
 __device__ __forceinline__ float nextdn(float v) { return nextafterf(v, -INFINITY); }
 
-// first index in [lo, hi) with eval >= bound (entries of a run are sorted by primitive)
-__device__ __forceinline__ int lower_bound_u32(const uint32_t* __restrict__ a, int lo, int hi, uint32_t bound) {
+// first index in [lo, hi) of a shell cell's run whose type group is >= g
+// (the run's keys share the cell code and ascend by group, then x level)
+__device__ __forceinline__ int lower_bound_group(const uint64_t* __restrict__ key, int lo, int hi, uint32_t g) {
   while (lo < hi) {
     int mid = (lo + hi) >> 1;
-    if (a[mid] < bound) lo = mid + 1;
+    if ((uint32_t)((key[mid] >> XQ_BITS) & 3u) < g) lo = mid + 1;
     else hi = mid;
   }
   return lo;
@@ -322,6 +350,8 @@ struct PairArgs {
   int mask_words;                    // shells: words of partner bits per entry
   unsigned int* maxr;                // shells, count pass: longest partner range (atomic max)
   int bi, bj;
+  int shift;                   // bits of type group and x level below the cell code (shells: swept)
+  uint32_t* __restrict__ pend; // shells: per entry, the end of the partner positions the sweep tested
   unsigned long long* fpstat;  // count pass: [0] FP32-accepted pairs, [1] FP64-decided (may be null)
   bool canonical;              // fill pass: write canonical keys (else compact ones for the sort)
 };
@@ -348,8 +378,8 @@ __device__ __forceinline__ EntryRange entry_range(const PairArgs& A, int64_t i) 
     R.j1 = R.e;
     R.type = CB_KEY_ROD_EE;
   } else if (R.P < (uint32_t)t.n) {
-    R.j0 = lower_bound_u32(A.eval, R.s, R.e, (uint32_t)t.n);
-    R.j1 = lower_bound_u32(A.eval, R.j0, R.e, (uint32_t)(t.n + t.T));
+    R.j0 = lower_bound_group(A.ekey, R.s, R.e, 1u);
+    R.j1 = lower_bound_group(A.ekey, R.j0, R.e, 2u);
     R.type = CB_KEY_PT;
     R.jbase = (uint32_t)t.n;
   } else if (R.P < (uint32_t)(t.n + t.T)) {
@@ -394,12 +424,14 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
     return;
   }
   const uint32_t P = R.P;
-  const uint64_t kc = A.ekey[i];
+  const uint64_t kc = A.ekey[i] >> A.shift;
   const Grid G = A.grids[kc >> 30];
   int j0 = R.j0, j1 = R.j1;
   const float4 plo = A.ebox[2 * (size_t)i], phi = A.ebox[2 * (size_t)i + 1];
   int pv[3];
   prim_verts(t, (int)P, pv);
+  // shells: the sweep stops at the first partner whose x level is above this level
+  const uint32_t xhi = RR ? 0u : x_level(phi.x, G, morton_x((uint32_t)(kc & 0x3fffffffull)));
   uint32_t count = 0, n32 = 0, n64 = 0;
   // the fill pass re-makes the count pass's decisions; never write past them
   const uint32_t c_end = FILL ? cnt[i] : 0;
@@ -420,12 +452,16 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
     for (int w = 0; w < A.mask_words; ++w) count += __popc(A.mask[(size_t)w * A.ne + i]);
   }
   uint32_t word = 0, beyond = 0;
+  int jend = j1;
   for (int jj = jb; jj < j1; ++jj) {
     int j = jj;
     if (RR) {
       j = a + 1 + jj;
       if (j >= m) j -= m;
       j += R.s;
+    } else if ((uint32_t)(A.ekey[j] & (XQ_LEVELS - 1)) > xhi) {
+      jend = jj;  // this partner and every later one lie beyond the entry's box along x
+      break;
     }
     const uint32_t Q = A.eval[j];
     bool acc = false;
@@ -477,7 +513,7 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
       const int b = jj - j0;
       if (b < 32 * A.mask_words) {
         word |= (uint32_t)acc << (b & 31);
-        if ((b & 31) == 31 || jj + 1 == j1) {
+        if ((b & 31) == 31) {
           A.mask[(size_t)(b >> 5) * A.ne + i] = word;
           word = 0;
         }
@@ -485,6 +521,12 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
         beyond += acc;
       }
     }
+  }
+  if (!RR && !FILL) {
+    // the last partial word of the tested positions, and where they end
+    const int nt = jend - j0;
+    if ((nt & 31) != 0 && nt <= 32 * A.mask_words) A.mask[(size_t)((nt - 1) >> 5) * A.ne + i] = word;
+    A.pend[i] = (uint32_t)jend;
   }
   if (!FILL) {
     cnt[i] = count;
@@ -499,7 +541,7 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
     }
     if (!RR && A.maxr) {
       const unsigned mask = __activemask();
-      const unsigned mr = __reduce_max_sync(mask, (unsigned)(j1 - j0));
+      const unsigned mr = __reduce_max_sync(mask, (unsigned)(jend - j0));
       if ((int)(threadIdx.x & 31) == __ffs(mask) - 1 && mr) atomicMax(A.maxr, mr);
     }
   }
@@ -539,7 +581,7 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs_emit(PairArgs A, const uin
   const uint32_t c_end = cnt[i];
   if (c_end == 0) return;
   const EntryRange R = entry_range(A, i);
-  const int nb = min(R.j1 - R.j0, 32 * A.mask_words);
+  const int nb = min((int)A.pend[i] - R.j0, 32 * A.mask_words);
   const size_t o = off[i];
   uint32_t count = 0;
   for (int w = 0; 32 * w < nb; ++w) {
@@ -699,18 +741,23 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     CB_TRY(buf_ensure(w.ekey[b], sizeof(uint64_t) * (size_t)ne, st));
     CB_TRY(buf_ensure(w.eval[b], sizeof(uint32_t) * (size_t)ne, st));
   }
+  int mbits = 0;
+  while ((1 << mbits) < M) ++mbits;
+  // shell cells are swept along x (type group and x level below the cell code)
+  const bool sweep = s->kind == CB_SHELL;
+  const int shift = sweep ? SWEEP_SHIFT : 0;
+  if (30 + mbits + shift > 64) return CB_ERR_ARG;  // more members than the cell keys can number
   k_cell_fill<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(t, np, bp<float4>(w.box32), bp<int32_t>(s->vsc), dgrids,
                                                            bp<uint32_t>(w.cell_off), bp<uint64_t>(w.ekey[0]),
-                                                           bp<uint32_t>(w.eval[0]));
+                                                           bp<uint32_t>(w.eval[0]), sweep);
   CB_TRY(buf_ensure(w.hist, sizeof(uint32_t) * (size_t)cbp::radix_hist_elems(ne), st));
   CB_TRY(buf_ensure(w.scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(cbp::radix_hist_elems(ne)) +
                                                              cbp::scan_tmp_elems(ne + 1) + 8),
                     st));
-  int mbits = 0;
-  while ((1 << mbits) < M) ++mbits;
   int r = cbp::radix_sort<uint64_t, uint32_t, true>(bp<uint64_t>(w.ekey[0]), bp<uint32_t>(w.eval[0]),
                                                     bp<uint64_t>(w.ekey[1]), bp<uint32_t>(w.eval[1]), ne, 0,
-                                                    30 + mbits, bp<uint32_t>(w.hist), bp<uint32_t>(w.scan_tmp), st);
+                                                    30 + mbits + shift, bp<uint32_t>(w.hist), bp<uint32_t>(w.scan_tmp),
+                                                    st);
   const uint64_t* ekey = bp<uint64_t>(w.ekey[r]);
   const uint32_t* eval = bp<uint32_t>(w.eval[r]);
   CB_TRY(buf_ensure(w.run_flag, sizeof(uint32_t) * (size_t)ne, st));
@@ -718,7 +765,7 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   CB_TRY(buf_ensure(w.run_start, sizeof(uint32_t) * ((size_t)ne + 2), st));
   CB_TRY(buf_ensure(w.pair_cnt, sizeof(uint32_t) * (size_t)ne, st));
   CB_TRY(buf_ensure(w.pair_off, sizeof(uint32_t) * ((size_t)ne + 1), st));
-  k_run_flag<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, ekey, bp<uint32_t>(w.run_flag));
+  k_run_flag<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, ekey, shift, bp<uint32_t>(w.run_flag));
   // exclusive scan of the flags into pair_off (used as scratch here)
   cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.run_flag), bp<uint32_t>(w.pair_off), ne,
                                           bp<uint32_t>(w.scan_tmp), (uint32_t*)nullptr, st);
@@ -728,6 +775,12 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   A.t = t;
   A.ne = ne;
   A.ekey = ekey;
+  A.shift = shift;
+  A.pend = nullptr;
+  if (sweep) {
+    CB_TRY(buf_ensure(w.pair_end, sizeof(uint32_t) * (size_t)ne, st));
+    A.pend = bp<uint32_t>(w.pair_end);
+  }
   A.eval = eval;
   A.run_id = bp<uint32_t>(w.run_id);
   A.run_start = bp<uint32_t>(w.run_start);

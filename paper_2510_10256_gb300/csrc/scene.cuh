@@ -89,13 +89,15 @@ struct BroadWork {
   DevBuf cx;          // per member: double centre[3], X (max |coordinate - centre|)
   DevBuf cell_cnt;    // uint32 per primitive
   DevBuf cell_off;    // uint32 per primitive (+1)
-  DevBuf ekey[2];     // uint64 (member << 30 | Morton cell) per entry (ping-pong)
+  DevBuf ekey[2];     // uint64 (member << 30 | Morton cell) per entry (ping-pong); shells: shifted up by
+                      // 12 bits above the entry's type group and x level in the cell
   DevBuf eval[2];     // uint32 primitive per entry
   DevBuf run_flag;    // uint32 per entry
   DevBuf run_id;      // uint32 per entry
   DevBuf run_start;   // uint32 per run (+1)
   DevBuf pair_cnt;    // uint32 per entry
   DevBuf pair_off;    // uint32 per entry (+1)
+  DevBuf pair_end;    // shells: uint32 per entry, the end of the partner positions its sweep tested
   DevBuf ebox;        // float4 lo, float4 hi per entry (boxes gathered into entry order)
   DevBuf ckey[2];     // uint64 compact candidate keys (ping-pong)
   DevBuf stage;       // uint64 [PAIR_STAGE][entries]: the count pass's first pairs of each entry
