@@ -497,8 +497,9 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
       }
     }
     if (acc) {
-      // the pair's key: RR pairs whose partner is the lower primitive take it first
-      const bool swap = RR && j < (int)i;
+      // the pair's key takes the lower primitive first: rods in round-robin
+      // order, and shell edge-edge pairs (swept cells order edges by x, not by id)
+      const bool swap = RR ? j < (int)i : (R.type == CB_KEY_EE && Q < P);
       const uint64_t key = pair_key(A, R.type, (swap ? Q : P) - R.ibase, (swap ? P : Q) - R.jbase);
       if (FILL) {
         // the pairs past the staged ones, at their place in the entry's range
@@ -601,7 +602,11 @@ __global__ void __launch_bounds__(CB_THREADS) k_pairs_emit(PairArgs A, const uin
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (jb[u] < 0) break;
-        if (count < c_end) out[o + count] = pair_key(A, R.type, R.P - R.ibase, Q[u] - R.jbase);
+        if (count < c_end) {
+          // edge-edge keys take the lower edge first (swept cells order edges by x)
+          const bool swap = R.type == CB_KEY_EE && Q[u] < R.P;
+          out[o + count] = pair_key(A, R.type, (swap ? Q[u] : R.P) - R.ibase, (swap ? R.P : Q[u]) - R.jbase);
+        }
         ++count;
       }
     }
