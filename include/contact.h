@@ -245,6 +245,52 @@ cb_status ccd_step(cb_scene* scene, const double* x_dev, const double* p_dev, do
  * itself a batch, index overflow), CB_ERR_OOM, CB_ERR_CUDA. */
 cb_status cb_batch_create(cb_scene* const* members, int32_t count, const cb_allocator* allocator, void* stream,
                           cb_scene** out);
+/* Serving (no counterpart in the paper: the request loop around its pass).
+ * A server holds up to `slots` resident scenes of one kind under a device
+ * memory budget and advances all of them with one batched pass: one launch
+ * sequence per stage for every resident scene, the batch rebuilt only when
+ * the residents change.  The caller keeps ownership of the scenes: release a
+ * slot before destroying its scene.
+ *   cb_server_create: kind CB_ROD / CB_SHELL, slots >= 1, budget in bytes,
+ *     allocator for the server's own buffers (as cb_scene_create; NULL: the
+ *     library's pool).
+ *   cb_batch_admit: puts a plain scene (not a batch) of the server's kind into
+ *     a free slot (*slot) if the device memory charged -- every resident scene,
+ *     the batch and the pass buffers as they are now, plus twice the new
+ *     scene's bytes (its pass buffers and its copy in the batch) -- stays
+ *     within the budget.  CB_ERR_CAPACITY: no free slot; CB_ERR_OOM: over the
+ *     budget (nothing changes); CB_ERR_ARG: wrong kind, a batch, or already
+ *     resident.
+ *   cb_batch_release: frees a slot.
+ *   cb_batch_pass: stages a-e for every resident scene.  x, p, energy, grad,
+ *     alpha: HOST arrays of `slots` DEVICE pointers indexed by slot (entries
+ *     of free slots are not read; energy, grad, alpha may be NULL or hold
+ *     NULL entries): x[k], p[k] [3][n_k] FP64 in, energy[k], alpha[k] one
+ *     double out, grad[k] [3][n_k] out -- the values cb_scene's own pass would
+ *     give (summation order aside).  Asynchronous on `stream` except for the
+ *     count reads of the stages; builds the batch (sync) after the residents
+ *     changed.
+ *   cb_server_stats: resident scenes, bytes charged now, candidates of the
+ *     last pass.
+ * Errors as above, plus those of the stage calls. */
+typedef struct cb_server cb_server;
+cb_status cb_server_create(int32_t kind, int32_t slots, int64_t hbm_budget_bytes, const cb_allocator* allocator,
+                           cb_server** out);
+cb_status cb_server_destroy(cb_server* server);
+cb_status cb_batch_admit(cb_server* server, cb_scene* scene, int32_t* slot);
+cb_status cb_batch_release(cb_server* server, int32_t slot);
+cb_status cb_batch_pass(cb_server* server, const double* const* x, const double* const* p, double* const* energy,
+                        double* const* grad, double* const* alpha, void* stream);
+cb_status cb_server_stats(cb_server* server, int32_t* resident, int64_t* charged_bytes, int64_t* n_candidates);
+
+/* Pre-sizes a scene's pair-list buffers -- candidates, active pairs (BSR
+ * pattern keys and Hessian queues) and CCD candidates -- for the given
+ * counts, so that a pass with at most those counts allocates nothing for
+ * them (the broad phase's own workspace still follows its first pass).  A
+ * capacity overflow can be retried after reserving more.  sync.
+ * Errors: CB_ERR_ARG, CB_ERR_TOO_LARGE (a count above 2^31 - 1), CB_ERR_OOM. */
+cb_status cb_scene_reserve(cb_scene* scene, int64_t n_candidates, int64_t n_ccd, int64_t n_active, void* stream);
+
 /* HOST arrays of count+1 entries: first vertex / edge / triangle of each
  * member in the batch numbering (a plain scene reports one member). */
 cb_status cb_batch_offsets(cb_scene* scene, int64_t* vert_offsets, int64_t* edge_offsets, int64_t* tri_offsets);

@@ -35,7 +35,8 @@ ABI_FUNCTIONS = ["cb_scene_create", "cb_scene_destroy", "contact_build", "contac
                  "cb_version", "cb_kernel_launches", "cb_measure_fma_tflops", "cb_batch_create",
                  "cb_batch_offsets", "cb_member_count", "ccd_step_noalloc", "cb_set_tuning",
                  "cb_get_tuning", "barrier_energy", "cb_bsr_spmv", "friction_lag", "friction_eval",
-                 "friction_spmv", "cb_get_friction"]
+                 "friction_spmv", "cb_get_friction", "cb_server_create", "cb_server_destroy", "cb_batch_admit",
+                 "cb_batch_release", "cb_batch_pass", "cb_server_stats", "cb_scene_reserve"]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -170,6 +171,13 @@ def lib():
         L.ccd_step_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, i64, vp, vp, vp]
         L.cb_set_tuning.argtypes = [vp, i32, C.c_float, i32]
         L.cb_get_tuning.argtypes = [vp, i32, C.POINTER(C.c_float), C.POINTER(i32)]
+        L.cb_server_create.argtypes = [i32, i32, i64, C.POINTER(Allocator), C.POINTER(vp)]
+        L.cb_server_destroy.argtypes = [vp]
+        L.cb_batch_admit.argtypes = [vp, vp, C.POINTER(i32)]
+        L.cb_batch_release.argtypes = [vp, i32]
+        L.cb_batch_pass.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]
+        L.cb_server_stats.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64)]
+        L.cb_scene_reserve.argtypes = [vp, i64, i64, i64, vp]
         _lib = L
     return _lib
 
@@ -390,6 +398,12 @@ class ContactScene:
         _check(lib().ccd_step(self.h, _dev_ptr(x, self.n), _dev_ptr(p, self.n),
                               _dev_ptr(alpha, None, False), _stream_ptr(stream)), "ccd_step")
 
+    def reserve(self, n_candidates: int, n_ccd: int, n_active: int, stream=None):
+        """Pre-size the pair-list buffers for passes with at most these counts
+        (cb_scene_reserve)."""
+        _check(lib().cb_scene_reserve(self.h, int(n_candidates), int(n_ccd), int(n_active), _stream_ptr(stream)),
+               "cb_scene_reserve")
+
     def run_pass(self, x, p, energy, grad, alpha, stream=None):
         """Stages a-e in order on one stream."""
         self.contact_build(x, stream)
@@ -506,3 +520,59 @@ class ContactBatch(ContactScene):
         self.kind = members[0].kind
         self._keep = []
         self._load_layout()
+
+
+class ContactServer:
+    """Resident scenes of one kind advanced by one batched pass (the C ABI's
+    cb_server: cb_batch_admit / cb_batch_release / cb_batch_pass).  The caller
+    keeps its ContactScene objects; release a slot before closing its scene."""
+
+    def __init__(self, kind: str, slots: int, hbm_budget_bytes: int, allocator="torch"):
+        h = C.c_void_p()
+        _check(lib().cb_server_create(CB_ROD if kind == "rod" else CB_SHELL, int(slots), int(hbm_budget_bytes),
+                                      _allocator_arg(allocator), C.byref(h)), "cb_server_create")
+        self.h = h
+        self.slots = int(slots)
+        self.scenes = [None] * self.slots
+
+    def admit(self, scene: "ContactScene") -> int:
+        """The slot the scene got; ContactError with CB_ERR_CAPACITY (no free
+        slot) or CB_ERR_OOM (over the budget) otherwise."""
+        k = C.c_int32()
+        _check(lib().cb_batch_admit(self.h, scene.h, C.byref(k)), "cb_batch_admit")
+        self.scenes[k.value] = scene
+        return int(k.value)
+
+    def release(self, slot: int):
+        _check(lib().cb_batch_release(self.h, int(slot)), "cb_batch_release")
+        self.scenes[slot] = None
+
+    def run_pass(self, x: dict, p: dict, energy: dict | None = None, grad: dict | None = None,
+                 alpha: dict | None = None, stream=None):
+        """Stages a-e for every resident scene; each argument maps a slot to
+        that scene's CUDA tensor (x, p, grad [3][n]; energy, alpha [1])."""
+        def table(d, out):
+            arr = (C.c_void_p * self.slots)()
+            for k, sc in enumerate(self.scenes):
+                if sc is None or d is None or d.get(k) is None:
+                    continue
+                arr[k] = _dev_ptr(d[k], sc.n if out != "scalar" else None, shape3=out != "scalar")
+            return arr
+        _check(lib().cb_batch_pass(self.h, table(x, "vec"), table(p, "vec"), table(energy, "scalar"),
+                                   table(grad, "vec"), table(alpha, "scalar"), _stream_ptr(stream)), "cb_batch_pass")
+
+    def stats(self) -> dict:
+        r, b, c = C.c_int32(), C.c_int64(), C.c_int64()
+        _check(lib().cb_server_stats(self.h, C.byref(r), C.byref(b), C.byref(c)), "cb_server_stats")
+        return {"resident": int(r.value), "charged_bytes": int(b.value), "n_candidates": int(c.value)}
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().cb_server_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -431,7 +431,8 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
   int pv[3];
   prim_verts(t, (int)P, pv);
   // shells: the sweep stops at the first partner whose x level is above this level
-  const uint32_t xhi = RR ? 0u : x_level(phi.x, G, morton_x((uint32_t)(kc & 0x3fffffffull)));
+  const int cxi = RR ? 0 : morton_x((uint32_t)(kc & 0x3fffffffull));
+  const uint32_t xhi = RR ? 0u : x_level(phi.x, G, cxi);
   uint32_t count = 0, n32 = 0, n64 = 0;
   // the fill pass re-makes the count pass's decisions; never write past them
   const uint32_t c_end = FILL ? cnt[i] : 0;
@@ -459,13 +460,15 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
       j = a + 1 + jj;
       if (j >= m) j -= m;
       j += R.s;
-    } else if ((uint32_t)(A.ekey[j] & (XQ_LEVELS - 1)) > xhi) {
+    }
+    const float4 qlo = A.ebox[2 * (size_t)j], qhi = A.ebox[2 * (size_t)j + 1];
+    // the partner's level, as its key holds it (same cell, same arithmetic)
+    if (!RR && x_level(qlo.x, G, cxi) > xhi) {
       jend = jj;  // this partner and every later one lie beyond the entry's box along x
       break;
     }
     const uint32_t Q = A.eval[j];
     bool acc = false;
-    const float4 qlo = A.ebox[2 * (size_t)j], qhi = A.ebox[2 * (size_t)j + 1];
     if (plo.x <= qhi.x && qlo.x <= phi.x && plo.y <= qhi.y && qlo.y <= phi.y && plo.z <= qhi.z &&
         qlo.z <= phi.z) {
       // home cell: low corner of the intersection
