@@ -88,7 +88,7 @@ static void scene_release(cb_scene* s) {
                     &s->rloop, &s->rlast, &s->elen2, &s->hmoll, &s->mlist, &s->ruv, &s->frest,
                     &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cand_alt, &s->klass_alt, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
                     &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col, &s->bsr_val,
-                    &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->mp, &s->vsc, &s->macc, &s->hstage, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag, &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist,
+                    &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->mp, &s->vsc, &s->macc, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag, &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist,
                     &s->fr_key, &s->fr_st, &s->fr_dat, &s->fr_hw, &s->dev_scalars};
   for (DevBuf* b : bufs) buf_free(*b, st);
   for (BroadWork* w : {&s->bw, &s->bwc}) {
@@ -148,11 +148,10 @@ static cb_status alloc_members(cb_scene* s, cudaStream_t st) {
   const int M = s->count;
   CB_TRY(buf_ensure(s->mp, sizeof(MemberParams) * (size_t)M, st));
   CB_TRY(buf_ensure(s->macc, sizeof(unsigned long long) * MACC_STRIDE * (size_t)M, st));
-  CB_TRY(buf_ensure(s->hstage, sizeof(double) * (size_t)M + 64, st));
   CB_CUDA(cudaMemsetAsync(s->macc.p, 0, sizeof(unsigned long long) * MACC_STRIDE * (size_t)M, st));
   // per member: the largest record staged through it (member parameters,
-  // the CCD accumulators, the broad phase's four doubles)
-  const size_t per = std::max({sizeof(MemberParams), sizeof(unsigned long long) * MACC_STRIDE, 4 * sizeof(double)});
+  // the CCD accumulators)
+  const size_t per = std::max(sizeof(MemberParams), sizeof(unsigned long long) * MACC_STRIDE);
   if (cudaMallocHost(&s->hstage_host, per * (size_t)M + 256) != cudaSuccess) return CB_ERR_OOM;
   return CB_OK;
 }
@@ -379,6 +378,8 @@ cb_status cb_scene_create(const cb_scene_desc* d, const cb_allocator* allocator,
   if (d->kind == CB_SHELL && (rc = buf_ensure(s->rloop, 16, st)) != CB_OK) return fail(rc);
   for (auto& e : s->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(CB_ERR_CUDA);
+  // the rest broad phase reads the member parameters (box inflation, primitive count)
+  if ((rc = upload_members(s, st)) != CB_OK) return fail(rc);
   if ((rc = filter_precompute(s, st)) != CB_OK) return fail(rc);
   s->hmp[0].dbar_min = std::isfinite(s->dbar_min) ? s->dbar_min : 0.0;
   s->hmp[0].dbar_fmax = s->hmp[0].per_comp && std::isfinite(s->dbar_fmax) ? s->dbar_fmax : s->hmp[0].dbar_min;
@@ -857,9 +858,9 @@ cb_status cb_get_stats(cb_scene* s, cb_stats* o) {
   o->ccd_max_iters = (int32_t)h[SC_ITERS];
   o->n_candidates_fp32 = (int64_t)h[SC_FP32_PAIRS];
   o->n_fp64_decided = (int64_t)h[SC_FP64_DECIDED];
-  o->n_hess_face = s->n_hq[0];
-  o->n_hess_pe_frame = s->n_hq[1];
-  o->n_hess_pe = s->n_hq[2];
+  o->n_hess_face = (int64_t)(uint32_t)h[SC_N9];
+  o->n_hess_pe_frame = (int64_t)(uint32_t)h[SC_N4];
+  o->n_hess_pe = (int64_t)(uint32_t)h[SC_N6];
   o->n_pair_overflow = (int64_t)(uint32_t)h[SC_NOVF];
   o->n_mollified = (int64_t)(uint32_t)h[SC_NMOLL];
   o->n_stencil_dropped = s->n_dropped;

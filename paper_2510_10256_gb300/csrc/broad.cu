@@ -96,8 +96,10 @@ __device__ __forceinline__ int prim_member(const Topo& t, const int32_t* __restr
   return vsc[v[0]];
 }
 
+// swept: boxes of x and x + p inflated by xi / 2 (the CCD phase); else boxes
+// of x inflated by a / 2 (full activation)
 __global__ void k_boxes(Topo t, int np, const double* __restrict__ x, const double* __restrict__ p,
-                        const double* __restrict__ hm, const int32_t* __restrict__ vsc,
+                        const MemberParams* __restrict__ mp, bool swept, const int32_t* __restrict__ vsc,
                         float4* __restrict__ box32, double* __restrict__ box64, double* __restrict__ box_raw,
                         uint32_t* bounds) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -108,7 +110,7 @@ __global__ void k_boxes(Topo t, int np, const double* __restrict__ x, const doub
     int v[3];
     const int nv = prim_verts(t, q, v);
     mem = vsc[v[0]];
-    const double h = hm[mem];
+    const double h = swept ? 0.5 * mp[mem].xi : 0.5 * mp[mem].a;
     double lo[3], hi[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -202,6 +204,63 @@ __global__ void k_boxes(Topo t, int np, const double* __restrict__ x, const doub
     }
     atomicAdd((double*)(bq + 8), es);
   }
+}
+
+// One thread per member: its hash grid from the bounds and extent sum of its
+// inflated primitive boxes.  The cell edge is the mean box extent (times the
+// tuned factor) rounded down to a quarter octave, so that summation-order
+// differences in the extent sum never move it, and at least 1/1000 of the
+// member's span along every axis.  cx gets the member's box centre and half
+// its largest extent (the origin of the FP32 positions).
+__global__ void k_grids(int M, const uint32_t* __restrict__ bounds, const MemberParams* __restrict__ mp,
+                        double cell_factor, Grid* __restrict__ grids, double* __restrict__ cx) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const uint32_t* bq = bounds + (size_t)m * BOUNDS_STRIDE;
+  float lo[3], hi[3];
+  bool empty = false;
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = o2f(bq[k]);
+    hi[k] = o2f(bq[3 + k]);
+    if (!(hi[k] >= lo[k])) empty = true;
+  }
+  Grid g;
+  if (empty) {
+    g = Grid{0.f, 0.f, 0.f, 1.f, 1, 1, 1, 0};
+    for (int k = 0; k < 4; ++k) cx[4 * m + k] = 0.0;
+    grids[m] = g;
+    return;
+  }
+  const double ext_sum = __longlong_as_double((long long)((uint64_t)bq[8] | ((uint64_t)bq[9] << 32)));
+  double X = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    cx[4 * m + k] = 0.5 * ((double)lo[k] + (double)hi[k]);
+    X = fmax(X, 0.5 * ((double)hi[k] - (double)lo[k]) * (1.0 + 1e-6));
+  }
+  cx[4 * m + 3] = X;
+  const int npm = max(1, mp[m].n_prims);
+  double c = cell_factor * (ext_sum / npm);
+  if (!(c > 0)) c = 1.0;
+  c = exp2(floor(log2(c) * 4.0) / 4.0);
+  for (int k = 0; k < 3; ++k) {
+    const double span = (double)hi[k] - (double)lo[k];
+    if (span / c > 1000.0) c = span / 1000.0;
+  }
+  g.inv = (float)(1.0 / c);
+  g.ox = lo[0];
+  g.oy = lo[1];
+  g.oz = lo[2];
+  int d3[3];
+  for (int k = 0; k < 3; ++k) {
+    const double span = (double)hi[k] - (double)lo[k];
+    const int d = (int)floor(span * (double)g.inv) + 2;
+    d3[k] = min(max(d, 1), 1024);
+  }
+  g.dx = d3[0];
+  g.dy = d3[1];
+  g.dz = d3[2];
+  g.pad = 0;
+  grids[m] = g;
 }
 
 __device__ __forceinline__ int cell_of(float v, float o, float inv, int dim) {
@@ -656,77 +715,16 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   CB_TRY(buf_ensure(w.bounds, sizeof(uint32_t) * BOUNDS_STRIDE * (size_t)M, st));
   CB_TRY(buf_ensure(w.grids, sizeof(Grid) * (size_t)M, st));
   CB_TRY(buf_ensure(w.cx, sizeof(double) * 4 * (size_t)M, st));
-  // inflation per member: a/2 (static, full activation) or xi/2 (swept, CCD)
-  std::vector<double> hm(M);
-  for (int m = 0; m < M; ++m) hm[m] = swept ? 0.5 * s->hmp[m].xi : 0.5 * s->hmp[m].a;
-  CB_TRY(buf_ensure(s->hstage, sizeof(double) * 8 * (size_t)M + 256, st));
-  double* hstage = (double*)s->hstage_host;
   uint32_t* bounds = bp<uint32_t>(w.bounds);
-  // stage: [0, M) inflation, later grids and centres
-  memcpy(hstage, hm.data(), sizeof(double) * M);
-  CB_CUDA(cudaMemcpyAsync(s->hstage.p, hstage, sizeof(double) * M, cudaMemcpyHostToDevice, st));
   k_bounds_init<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(bounds, M);
-  k_boxes<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(t, np, x, p, bp<double>(s->hstage), bp<int32_t>(s->vsc),
-                                                       bp<float4>(w.box32), bp<double>(w.box64),
-                                                       raw ? bp<double>(w.box_raw) : nullptr, bounds);
+  k_boxes<<<cb_grid(np), CB_THREADS, 0, cb_count(st)>>>(t, np, x, p, bp<MemberParams>(s->mp), swept,
+                                                       bp<int32_t>(s->vsc), bp<float4>(w.box32),
+                                                       bp<double>(w.box64), raw ? bp<double>(w.box_raw) : nullptr,
+                                                       bounds);
+  k_grids<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, bounds, bp<MemberParams>(s->mp),
+                                                      w.cell_factor > 0 ? (double)w.cell_factor : 1.0,
+                                                      bp<Grid>(w.grids), bp<double>(w.cx));
   CB_CUDA(cudaGetLastError());
-  std::vector<uint32_t> hb((size_t)M * BOUNDS_STRIDE);
-  CB_CUDA(cudaMemcpyAsync(hstage, bounds, sizeof(uint32_t) * BOUNDS_STRIDE * M, cudaMemcpyDeviceToHost, st));
-  CB_CUDA(cudaStreamSynchronize(st));
-  memcpy(hb.data(), hstage, sizeof(uint32_t) * BOUNDS_STRIDE * M);
-  std::vector<Grid> grids(M);
-  w.hcx.assign(4 * (size_t)M, 0.0);
-  for (int m = 0; m < M; ++m) {
-    const uint32_t* bq = hb.data() + (size_t)m * BOUNDS_STRIDE;
-    float lo[3], hi[3];
-    bool empty = false;
-    for (int k = 0; k < 3; ++k) {
-      lo[k] = o2f(bq[k]);
-      hi[k] = o2f(bq[3 + k]);
-      if (!(hi[k] >= lo[k])) empty = true;
-    }
-    double ext_sum;
-    memcpy(&ext_sum, bq + 8, 8);
-    Grid& g = grids[m];
-    if (empty) {
-      g = Grid{0.f, 0.f, 0.f, 1.f, 1, 1, 1, 0};
-      continue;
-    }
-    double X = 0.0;
-    for (int k = 0; k < 3; ++k) {
-      w.hcx[4 * m + k] = 0.5 * ((double)lo[k] + (double)hi[k]);
-      X = std::max(X, 0.5 * ((double)hi[k] - (double)lo[k]) * (1.0 + 1e-6));
-    }
-    w.hcx[4 * m + 3] = X;
-    // cell size: mean primitive box extent of the member (scaled by the tuned
-    // factor), rounded to a 1/4-octave grid so tiny summation-order
-    // differences never change it
-    const int npm = std::max(1, s->hmp[m].n_prims);
-    double c = (w.cell_factor > 0 ? (double)w.cell_factor : 1.0) * (ext_sum / npm);
-    if (!(c > 0)) c = 1.0;
-    c = std::exp2(std::floor(std::log2(c) * 4.0) / 4.0);
-    for (int k = 0; k < 3; ++k) {
-      double span = (double)hi[k] - (double)lo[k];
-      if (span / c > 1000.0) c = span / 1000.0;
-    }
-    g.inv = (float)(1.0 / c);
-    g.ox = lo[0];
-    g.oy = lo[1];
-    g.oz = lo[2];
-    int* dims[3] = {&g.dx, &g.dy, &g.dz};
-    for (int k = 0; k < 3; ++k) {
-      double span = (double)hi[k] - (double)lo[k];
-      int d = (int)std::floor(span * (double)g.inv) + 2;
-      *dims[k] = std::min(std::max(d, 1), 1024);
-    }
-    g.pad = 0;
-    if (m == 0) w.cell = (float)c;
-  }
-  memcpy(hstage, grids.data(), sizeof(Grid) * M);
-  CB_CUDA(cudaMemcpyAsync(w.grids.p, hstage, sizeof(Grid) * M, cudaMemcpyHostToDevice, st));
-  CB_CUDA(cudaStreamSynchronize(st));  // the staging buffer is reused below
-  memcpy(hstage, w.hcx.data(), sizeof(double) * 4 * M);
-  CB_CUDA(cudaMemcpyAsync(w.cx.p, hstage, sizeof(double) * 4 * M, cudaMemcpyHostToDevice, st));
   const Grid* dgrids = bp<Grid>(w.grids);
 
   CB_TRY(buf_ensure(w.cell_cnt, sizeof(uint32_t) * (size_t)np + 16, st));

@@ -1171,76 +1171,190 @@ __global__ void __launch_bounds__(128) k_hess_prep(HessArgs A) {
 
 // ---- IPC's edge-edge mollifier (CB_EE_MOLLIFIER) -------------------------
 // A mollified pair's energy m(c) kappa b(d) depends on all four points
-// whatever its distance type, so it leaves the reduced paths of k_hess_prep:
-// here its gradient and Hessian come from hyper-dual evaluation (value + e1
-// + e2 + e1 e2 parts, exact first and second derivatives) of the typed d^2
-// and of c = |e0 x e1|^2 in coordinates relative to the first point, the
-// Hessian by the product rule
+// whatever its distance type, so it leaves the reduced paths of k_hess_prep.
+// Its gradient and Hessian are formed here from analytic derivatives of the
+// typed distance d and of c = |e0 x e1|^2, written in the difference vectors
+// the distance is a function of and mapped to the four points:
+//   point-point  r = q - p:              s = |r|^2
+//   point-line   w = q - e0, u = e1 - e0: s = |w|^2 - (w.u)^2 / |u|^2
+//     (then grad d = grad s / 2d, hess d = (hess s - 2 grad d grad d^T) / 2d)
+//   line-line    w = b0 - a0, u = a1 - a0, v = b1 - b0, n = u x v:
+//     d = |g| / sqrt(N), g = w.n, N = |n|^2, differentiated directly (no
+//     squared distance, whose two large terms cancel for near-parallel edges)
+//   c = N (the same u, v), grad and hess in closed form.
+// The Hessian by the product rule,
 //   H = kappa (m (b'' gd gd^T + b' Hd) + b' m' (gc gd^T + gd gc^T)
 //              + b (m'' gc gc^T + m' Hc)),
 // and the 9x9 matrix of the four-point translation-free basis
 // (B = (K4 x I)^T H (K4 x I)) is queued for k_hess_proj<9>.
-struct hdn {
-  double v, a, b, ab;
+struct LocalDeriv {
+  int nb;                  // difference vectors (blocks of 3)
+  int plus[3], minus[3];   // block b = x[plus[b]] - x[minus[b]] (stencil points 0..3)
+  double g[9];             // gradient in the blocks
+  double H[9][9];          // Hessian in the blocks
 };
-__device__ __forceinline__ hdn operator+(hdn x, hdn y) { return {x.v + y.v, x.a + y.a, x.b + y.b, x.ab + y.ab}; }
-__device__ __forceinline__ hdn operator-(hdn x, hdn y) { return {x.v - y.v, x.a - y.a, x.b - y.b, x.ab - y.ab}; }
-__device__ __forceinline__ hdn operator*(hdn x, hdn y) {
-  return {x.v * y.v, x.a * y.v + x.v * y.a, x.b * y.v + x.v * y.b, x.ab * y.v + x.a * y.b + x.b * y.a + x.v * y.ab};
-}
-__device__ __forceinline__ hdn h_inv(hdn y) {
-  const double i = 1.0 / y.v;
-  return {i, -y.a * i * i, -y.b * i * i, 2.0 * y.a * y.b * i * i * i - y.ab * i * i};
-}
-__device__ __forceinline__ hdn h_sqrt(hdn x) {
-  const double r = sqrt(x.v), i = 0.5 / r;
-  return {r, x.a * i, x.b * i, x.ab * i - x.a * x.b * i / (2.0 * x.v)};
-}
-struct hv {
-  hdn x, y, z;
-};
-__device__ __forceinline__ hv hv_sub(hv p, hv q) { return {p.x - q.x, p.y - q.y, p.z - q.z}; }
-__device__ __forceinline__ hdn hv_dot(hv p, hv q) { return p.x * q.x + p.y * q.y + p.z * q.z; }
-__device__ __forceinline__ hv hv_cross(hv p, hv q) {
-  return {p.y * q.z - p.z * q.y, p.z * q.x - p.x * q.z, p.x * q.y - p.y * q.x};
-}
-// typed squared edge-edge distance (types as in geometry.cuh) of R (a0 a1 b0 b1)
-__device__ hdn ee_d2_typed(int ty, const hv (&R)[4]) {
-  auto pp = [](hv p, hv q) {
-    const hv d = hv_sub(q, p);
-    return hv_dot(d, d);
-  };
-  auto pe = [](hv q, hv e0, hv e1) {
-    const hv u = hv_sub(e1, e0), c = hv_cross(hv_sub(q, e0), u);
-    return hv_dot(c, c) * h_inv(hv_dot(u, u));
-  };
-  switch (ty) {
-    case 0: return pp(R[0], R[2]);
-    case 1: return pp(R[0], R[3]);
-    case 2: return pp(R[1], R[2]);
-    case 3: return pp(R[1], R[3]);
-    case 4: return pe(R[0], R[2], R[3]);
-    case 5: return pe(R[1], R[2], R[3]);
-    case 6: return pe(R[2], R[0], R[1]);
-    case 7: return pe(R[3], R[0], R[1]);
-    default: {
-      const hv n = hv_cross(hv_sub(R[1], R[0]), hv_sub(R[3], R[2]));
-      const hdn g = hv_dot(hv_sub(R[2], R[0]), n);
-      return g * g * h_inv(hv_dot(n, n));
+
+// the gradient and Hessian of a function of the difference vectors, as
+// functions of the 12 coordinates of the four stencil points
+__device__ void local_to_points(const LocalDeriv& L, double (&g12)[12], double (&H12)[12][12]) {
+  double cf[4][3];
+  for (int P = 0; P < 4; ++P)
+    for (int b = 0; b < 3; ++b) cf[P][b] = b < L.nb ? (L.plus[b] == P ? 1.0 : 0.0) - (L.minus[b] == P ? 1.0 : 0.0) : 0.0;
+  for (int P = 0; P < 4; ++P)
+    for (int i = 0; i < 3; ++i) {
+      double v = 0.0;
+      for (int b = 0; b < L.nb; ++b) v += cf[P][b] * L.g[3 * b + i];
+      g12[3 * P + i] = v;
     }
-  }
+  for (int P = 0; P < 4; ++P)
+    for (int Q = 0; Q < 4; ++Q)
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          double v = 0.0;
+          for (int b = 0; b < L.nb; ++b) {
+            if (cf[P][b] == 0.0) continue;
+            for (int e = 0; e < L.nb; ++e) v += cf[P][b] * cf[Q][e] * L.H[3 * b + i][3 * e + j];
+          }
+          H12[3 * P + i][3 * Q + j] = v;
+        }
 }
-// d and c of the stencil X (4 points, 12 doubles point-major) with the
-// hyper-dual parts seeded on coordinates i (e1) and j (e2)
-__device__ void moll_eval(int ty, const double (&X)[12], int i, int j, hdn& d, hdn& c) {
-  hdn Y[12];
-  for (int k = 0; k < 12; ++k) Y[k] = {X[k], k == i ? 1.0 : 0.0, k == j ? 1.0 : 0.0, 0.0};
-  hv R[4];
-  for (int q = 0; q < 4; ++q)
-    R[q] = {Y[3 * q] - Y[0], Y[3 * q + 1] - Y[1], Y[3 * q + 2] - Y[2]};
-  d = h_sqrt(ee_d2_typed(ty, R));
-  const hv n = hv_cross(hv_sub(R[1], R[0]), hv_sub(R[3], R[2]));
-  c = hv_dot(n, n);
+
+// |u x v|^2 of u (block bu) and v (block bv): gradient and Hessian entries added with weight w
+__device__ void add_cross2(LocalDeriv& L, int bu, int bv, const d3& u, const d3& v, double wg, double wh) {
+  const double uu = dot3(u, u), vv = dot3(v, v), uv = dot3(u, v);
+  const double U[3] = {u.x, u.y, u.z}, V[3] = {v.x, v.y, v.z};
+  for (int i = 0; i < 3; ++i) {
+    L.g[3 * bu + i] += wg * (2.0 * vv * U[i] - 2.0 * uv * V[i]);
+    L.g[3 * bv + i] += wg * (2.0 * uu * V[i] - 2.0 * uv * U[i]);
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double dl = i == j ? 1.0 : 0.0;
+      L.H[3 * bu + i][3 * bu + j] += wh * (2.0 * vv * dl - 2.0 * V[i] * V[j]);
+      L.H[3 * bv + i][3 * bv + j] += wh * (2.0 * uu * dl - 2.0 * U[i] * U[j]);
+      const double m = 4.0 * U[i] * V[j] - 2.0 * V[i] * U[j] - 2.0 * uv * dl;  // d2/du_i dv_j
+      L.H[3 * bu + i][3 * bv + j] += wh * m;
+      L.H[3 * bv + j][3 * bu + i] += wh * m;
+    }
+}
+
+// gradient and Hessian of the typed edge-edge distance d (types as in
+// geometry.cuh) in difference vectors of the stencil X (a0 a1 b0 b1)
+__device__ void ee_distance_derivs(int ty, const d3 (&X)[4], double d, LocalDeriv& L) {
+  for (int i = 0; i < 9; ++i) {
+    L.g[i] = 0.0;
+    for (int j = 0; j < 9; ++j) L.H[i][j] = 0.0;
+  }
+  if (ty <= 7) {
+    // squared distance s in (r) or (w, u), then d
+    if (ty <= 3) {
+      const int p = ty <= 1 ? 0 : 1, q = (ty & 1) ? 3 : 2;
+      L.nb = 1;
+      L.plus[0] = q;
+      L.minus[0] = p;
+      const d3 r = sub3(X[q], X[p]);
+      const double R[3] = {r.x, r.y, r.z};
+      for (int i = 0; i < 3; ++i) {
+        L.g[i] = 2.0 * R[i];
+        L.H[i][i] = 2.0;
+      }
+    } else {
+      // point q, line e0 e1: 4 PE(a0, b), 5 PE(a1, b), 6 PE(b0, a), 7 PE(b1, a)
+      const int q = ty == 4 ? 0 : ty == 5 ? 1 : ty == 6 ? 2 : 3;
+      const int e0 = ty <= 5 ? 2 : 0, e1 = ty <= 5 ? 3 : 1;
+      L.nb = 2;
+      L.plus[0] = q;
+      L.minus[0] = e0;
+      L.plus[1] = e1;
+      L.minus[1] = e0;
+      const d3 w = sub3(X[q], X[e0]), u = sub3(X[e1], X[e0]);
+      const double a = dot3(w, u), gg = dot3(u, u), ig = 1.0 / gg;
+      const double W[3] = {w.x, w.y, w.z}, U[3] = {u.x, u.y, u.z};
+      for (int i = 0; i < 3; ++i) {
+        L.g[i] = 2.0 * W[i] - 2.0 * a * U[i] * ig;
+        L.g[3 + i] = -2.0 * a * W[i] * ig + 2.0 * a * a * U[i] * ig * ig;
+      }
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          const double dl = i == j ? 1.0 : 0.0;
+          L.H[i][j] = 2.0 * dl - 2.0 * U[i] * U[j] * ig;
+          const double wu = -2.0 * U[i] * W[j] * ig - 2.0 * a * dl * ig + 4.0 * a * U[i] * U[j] * ig * ig;
+          L.H[i][3 + j] = wu;
+          L.H[3 + j][i] = wu;
+          L.H[3 + i][3 + j] = -2.0 * W[i] * W[j] * ig + 4.0 * a * (W[i] * U[j] + U[i] * W[j]) * ig * ig +
+                              2.0 * a * a * dl * ig * ig - 8.0 * a * a * U[i] * U[j] * ig * ig * ig;
+        }
+    }
+    // s -> d: grad d = grad s / 2d, hess d = (hess s - 2 grad d grad d^T) / 2d
+    const double h = 0.5 / d;
+    for (int i = 0; i < 3 * L.nb; ++i) L.g[i] *= h;
+    for (int i = 0; i < 3 * L.nb; ++i)
+      for (int j = 0; j < 3 * L.nb; ++j) L.H[i][j] = (L.H[i][j] - 2.0 * L.g[i] * L.g[j]) * h;
+    return;
+  }
+  // line-line: d = |g| / sqrt(N), blocks w = b0 - a0, u = a1 - a0, v = b1 - b0
+  L.nb = 3;
+  L.plus[0] = 2;
+  L.minus[0] = 0;
+  L.plus[1] = 1;
+  L.minus[1] = 0;
+  L.plus[2] = 3;
+  L.minus[2] = 2;
+  const d3 w = sub3(X[2], X[0]), u = sub3(X[1], X[0]), v = sub3(X[3], X[2]);
+  const d3 n = cross3(u, v), vw = cross3(v, w), wu = cross3(w, u);
+  const double g = dot3(w, n), N = dot3(n, n);
+  const double sg = g >= 0.0 ? 1.0 : -1.0, r = 1.0 / sqrt(N), r3 = r * r * r, r5 = r3 * r * r;
+  // grad g = (n, v x w, w x u); hess g: the cross-product blocks
+  const double Gg[9] = {n.x, n.y, n.z, vw.x, vw.y, vw.z, wu.x, wu.y, wu.z};
+  // grad N and hess N (blocks u, v)
+  LocalDeriv Nd;
+  Nd.nb = 3;
+  for (int i = 0; i < 9; ++i) {
+    Nd.g[i] = 0.0;
+    for (int j = 0; j < 9; ++j) Nd.H[i][j] = 0.0;
+  }
+  add_cross2(Nd, 1, 2, u, v, 1.0, 1.0);
+  // hess g: d2g/dw du = -[v]x, d2g/dw dv = [u]x, d2g/du dv = -[w]x ([a]x b = a x b)
+  auto crossm = [](const d3& a, double sgn, double (&M)[3][3]) {
+    M[0][0] = 0.0;
+    M[0][1] = -sgn * a.z;
+    M[0][2] = sgn * a.y;
+    M[1][0] = sgn * a.z;
+    M[1][1] = 0.0;
+    M[1][2] = -sgn * a.x;
+    M[2][0] = -sgn * a.y;
+    M[2][1] = sgn * a.x;
+    M[2][2] = 0.0;
+  };
+  double Hg[9][9];
+  for (int i = 0; i < 9; ++i)
+    for (int j = 0; j < 9; ++j) Hg[i][j] = 0.0;
+  {
+    double M[3][3], T[3][3];
+    crossm(v, -1.0, M);  // rows w, cols u
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        Hg[i][3 + j] = M[i][j];
+        Hg[3 + j][i] = M[i][j];
+      }
+    crossm(u, 1.0, T);  // rows w, cols v
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        Hg[i][6 + j] = T[i][j];
+        Hg[6 + j][i] = T[i][j];
+      }
+    crossm(w, -1.0, M);  // rows u, cols v
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        Hg[3 + i][6 + j] = M[i][j];
+        Hg[6 + j][3 + i] = M[i][j];
+      }
+  }
+  for (int i = 0; i < 9; ++i) L.g[i] = sg * (r * Gg[i] - 0.5 * g * r3 * Nd.g[i]);
+  for (int i = 0; i < 9; ++i)
+    for (int j = 0; j < 9; ++j)
+      L.H[i][j] = sg * (r * Hg[i][j] - 0.5 * r3 * (Gg[i] * Nd.g[j] + Nd.g[i] * Gg[j]) - 0.5 * g * r3 * Nd.H[i][j] +
+                        0.75 * g * r5 * Nd.g[i] * Nd.g[j]);
 }
 
 // one thread per mollified pair (listed by k_kind_split)
@@ -1258,22 +1372,36 @@ __global__ void __launch_bounds__(128) k_moll_hess(HessArgs A) {
     const PassParams P = member_pass(A.mp[mem]);
     double xi_p, dh_p;
     pair_params(P, A.ccls[c], f_width(P, A.dbar_comp, A.comp, s.v[0]), xi_p, dh_p);
+    const double d = A.cd[c];
     double b, b1, b2;
-    barrier_b012(A.cd[c] - xi_p, dh_p, b, b1, b2);
-    double X[12];
-    for (int q = 0; q < 4; ++q) {
-      const d3 p = load3(A.x, A.n, s.v[q]);
-      X[3 * q] = p.x;
-      X[3 * q + 1] = p.y;
-      X[3 * q + 2] = p.z;
+    barrier_b012(d - xi_p, dh_p, b, b1, b2);
+    // points relative to the first one (translation changes no derivative)
+    const d3 X0 = load3(A.x, A.n, s.v[0]);
+    d3 X[4];
+    for (int q = 0; q < 4; ++q) X[q] = sub3(load3(A.x, A.n, s.v[q]), X0);
+    double gd[12], gc[12], Hd[12][12], Hc[12][12];
+    {
+      LocalDeriv L;
+      ee_distance_derivs(ty, X, d, L);
+      local_to_points(L, gd, Hd);
     }
-    double gd[12], gc[12], cval = 0.0;
-    for (int i = 0; i < 12; ++i) {
-      hdn d, cc;
-      moll_eval(ty, X, i, i, d, cc);
-      gd[i] = d.a;
-      gc[i] = cc.a;
-      cval = cc.v;
+    double cval;
+    {
+      LocalDeriv L;
+      L.nb = 2;
+      L.plus[0] = 1;
+      L.minus[0] = 0;
+      L.plus[1] = 3;
+      L.minus[1] = 2;
+      for (int i = 0; i < 9; ++i) {
+        L.g[i] = 0.0;
+        for (int j = 0; j < 9; ++j) L.H[i][j] = 0.0;
+      }
+      const d3 u = sub3(X[1], X[0]), v = sub3(X[3], X[2]);
+      const d3 n = cross3(u, v);
+      cval = dot3(n, n);
+      add_cross2(L, 0, 1, u, v, 1.0, 1.0);
+      local_to_points(L, gc, Hc);
     }
     const double eps = 1e-3 * A.elen2[cb_key_i(key)] * A.elen2[cb_key_j(key)];
     double m, m1, m2;
@@ -1289,10 +1417,8 @@ __global__ void __launch_bounds__(128) k_moll_hess(HessArgs A) {
     for (int k = 0; k < 81; ++k) Bf[k] = 0.0;
     for (int i = 0; i < 12; ++i)
       for (int j = i; j < 12; ++j) {
-        hdn d, cc;
-        moll_eval(ty, X, i, j, d, cc);
-        const double h = kap * (m * (b2 * gd[i] * gd[j] + b1 * d.ab) + b1 * m1 * (gc[i] * gd[j] + gd[i] * gc[j]) +
-                                b * (m2 * gc[i] * gc[j] + m1 * cc.ab));
+        const double h = kap * (m * (b2 * gd[i] * gd[j] + b1 * Hd[i][j]) + b1 * m1 * (gc[i] * gd[j] + gd[i] * gc[j]) +
+                                b * (m2 * gc[i] * gc[j] + m1 * Hc[i][j]));
         const int q1 = i / 3, al = i % 3, q2 = j / 3, be = j % 3;
         for (int p1 = 0; p1 < 3; ++p1)
           for (int p2 = 0; p2 < 3; ++p2) {
@@ -1557,181 +1683,207 @@ struct ProjSmem {
 // projected matrix is exact to 1e-14 of ||B||.  B+ is mapped back to the
 // involved points with K (x) I and scattered.
 template <int D, int S>
-__global__ void __launch_bounds__(S) k_hess_proj(HessArgs A, int64_t m) {
+__global__ void __launch_bounds__(S) k_hess_proj(HessArgs A) {
   constexpr int NP = D * (D + 1) / 2;
   extern __shared__ double smem[];
   const int tid = threadIdx.x;
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + tid;
-  double* Vs = smem + tid;                            // V: row i of column k at [(k * D + i) * S]
-  double* Ad = smem + D * D * S + tid;                // A: element e at [e * S]
-  float* V32 = (float*)smem + tid;                    // FP32 V, same indexing, inside the V region
-  float* A32 = (float*)(smem + D * D * S) + tid;      // FP32 A, same indexing, inside the A region
-  const bool act = w < m;                             // no early exit before the last barrier
-  const double* Bg = D == 9 ? A.B9 : A.B6;
-  const uint32_t a = act ? (D == 9 ? A.slot9 : A.slot6)[w] : 0u;
-  // B stays in registers until B+ is formed
-  double Br[NP];
-  double mx = 0.0;
-#pragma unroll
-  for (int e = 0; e < NP; ++e) {
-    Br[e] = act ? Bg[(size_t)e * A.cap + w] : 0.0;
-    mx = fmax(mx, fabs(Br[e]));
-  }
-  const bool work = act && mx != 0.0;
-  if (work) {
-    const double inv = 1.0 / mx;
-#pragma unroll
-    for (int e = 0; e < NP; ++e) A32[e * S] = (float)(Br[e] * inv);
-    for (int k = 0; k < D; ++k)
-      for (int i = 0; i < D; ++i) V32[(k * D + i) * S] = (i == k) ? 1.f : 0.f;
-    jacobi_packed<float, D>(A32, V32, S, PROJ_FP32_TOL2, 12);
-  }
-  // FP64 re-orthonormalisation of the FP32 eigenvectors (modified Gram-Schmidt),
-  // columns in descending order.  Double column k takes the bytes of float
-  // columns 2k and 2k+1 (column 0: 0 and 1), all read before it is written:
-  // higher columns in earlier steps, column k itself before the barrier.
-  for (int k = D - 1; k >= 0; --k) {
-    double v[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) v[i] = work ? (double)V32[(k * D + i) * S] : 0.0;
+  const int64_t m = (int64_t)*(D == 9 ? A.n9 : A.n6);
+  // grid-stride over the queue, S pairs per step; the loop bound is the same
+  // for every thread of a block, and a thread past the end leaves only in the
+  // block's last step, after its last barrier
+  for (int64_t base = (int64_t)blockIdx.x * S; base < m; base += (int64_t)gridDim.x * S) {
+    // the previous step's B+ and V (double layout) overlap other threads' FP32
+    // arrays of this step
     __syncthreads();
+    const int64_t w = base + tid;
+    double* Vs = smem + tid;                            // V: row i of column k at [(k * D + i) * S]
+    double* Ad = smem + D * D * S + tid;                // A: element e at [e * S]
+    float* V32 = (float*)smem + tid;                    // FP32 V, same indexing, inside the V region
+    float* A32 = (float*)(smem + D * D * S) + tid;      // FP32 A, same indexing, inside the A region
+    const bool act = w < m;                             // no early exit before the last barrier
+    const double* Bg = D == 9 ? A.B9 : A.B6;
+    const uint32_t a = act ? (D == 9 ? A.slot9 : A.slot6)[w] : 0u;
+    // B stays in registers until B+ is formed
+    double Br[NP];
+    double mx = 0.0;
+#pragma unroll
+    for (int e = 0; e < NP; ++e) {
+      Br[e] = act ? Bg[(size_t)e * A.cap + w] : 0.0;
+      mx = fmax(mx, fabs(Br[e]));
+    }
+    const bool work = act && mx != 0.0;
     if (work) {
-      for (int j = k + 1; j < D; ++j) {
-        double dp = 0.0;
+      const double inv = 1.0 / mx;
 #pragma unroll
-        for (int i = 0; i < D; ++i) dp += Vs[(j * D + i) * S] * v[i];
-#pragma unroll
-        for (int i = 0; i < D; ++i) v[i] -= dp * Vs[(j * D + i) * S];
-      }
-      double nn = 0.0;
-#pragma unroll
-      for (int i = 0; i < D; ++i) nn += v[i] * v[i];
-      nn = rsqrt_refined(nn);  // nn is 1 to FP32 accuracy here
-#pragma unroll
-      for (int i = 0; i < D; ++i) Vs[(k * D + i) * S] = v[i] * nn;
+      for (int e = 0; e < NP; ++e) A32[e * S] = (float)(Br[e] * inv);
+      for (int k = 0; k < D; ++k)
+        for (int i = 0; i < D; ++i) V32[(k * D + i) * S] = (i == k) ? 1.f : 0.f;
+      jacobi_packed<float, D>(A32, V32, S, PROJ_FP32_TOL2, 12);
     }
-  }
-  // from here on every thread touches only its own elements: no more barriers
-  if (!act) return;
-  // eigenvalues -> diagonal of Ad, eigenvectors -> Vs
-  if (!work) {
-    for (int e = 0; e < NP; ++e) Ad[e * S] = 0.0;
-    for (int k = 0; k < D; ++k)
-      for (int i = 0; i < D; ++i) Vs[(k * D + i) * S] = (i == k) ? 1.0 : 0.0;
-  } else {
-    // A = V^T B V, column by column (the FP32 A is dead: every thread passed
-    // the Gram-Schmidt barriers after its FP32 phase)
-    for (int l = 0; l < D; ++l) {
-      double vl[D], t[D];
+    // FP64 re-orthonormalisation of the FP32 eigenvectors (modified Gram-Schmidt),
+    // columns in descending order.  Double column k takes the bytes of float
+    // columns 2k and 2k+1 (column 0: 0 and 1), all read before it is written:
+    // higher columns in earlier steps, column k itself before the barrier.
+    for (int k = D - 1; k >= 0; --k) {
+      double v[D];
 #pragma unroll
-      for (int j = 0; j < D; ++j) vl[j] = Vs[(l * D + j) * S];
+      for (int i = 0; i < D; ++i) v[i] = work ? (double)V32[(k * D + i) * S] : 0.0;
+      __syncthreads();
+      if (work) {
+        for (int j = k + 1; j < D; ++j) {
+          double dp = 0.0;
 #pragma unroll
-      for (int i = 0; i < D; ++i) {
-        double v = 0.0;
+          for (int i = 0; i < D; ++i) dp += Vs[(j * D + i) * S] * v[i];
 #pragma unroll
-        for (int j = 0; j < D; ++j) v += Br[i <= j ? tri_idx(i, j, D) : tri_idx(j, i, D)] * vl[j];
-        t[i] = v;
-      }
-      for (int k = 0; k <= l; ++k) {
-        double v = 0.0;
+          for (int i = 0; i < D; ++i) v[i] -= dp * Vs[(j * D + i) * S];
+        }
+        double nn = 0.0;
 #pragma unroll
-        for (int i = 0; i < D; ++i) v += Vs[(k * D + i) * S] * t[i];
-        Ad[tri_idx(k, l, D) * S] = v;
+        for (int i = 0; i < D; ++i) nn += v[i] * v[i];
+        nn = rsqrt_refined(nn);  // nn is 1 to FP32 accuracy here
+#pragma unroll
+        for (int i = 0; i < D; ++i) Vs[(k * D + i) * S] = v[i] * nn;
       }
     }
-    jacobi_refine64<D>(Ad, Vs, S, 1e-28, 12);
-  }
-  // B+ (into the A region) from the side with fewer terms: the sum over the
-  // positive eigenpairs of lam v v^T, or B minus the sum over the negative
-  // ones (B = V A V^T to the FP64 sweeps' tolerance).  The loop runs as many
-  // terms as the warp's busiest lane needs; each lane adds its own j-th term.
-  double lam[D];
-  int npos = 0, nneg = 0;
+    // from here on every thread touches only its own elements: no more barriers
+    if (!act) continue;  // the block's last step
+    // eigenvalues -> diagonal of Ad, eigenvectors -> Vs
+    if (!work) {
+      for (int e = 0; e < NP; ++e) Ad[e * S] = 0.0;
+      for (int k = 0; k < D; ++k)
+        for (int i = 0; i < D; ++i) Vs[(k * D + i) * S] = (i == k) ? 1.0 : 0.0;
+    } else {
+      // A = V^T B V, column by column (the FP32 A is dead: every thread passed
+      // the Gram-Schmidt barriers after its FP32 phase)
+      for (int l = 0; l < D; ++l) {
+        double vl[D], t[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) {
-    lam[k] = Ad[tri_idx(k, k, D) * S];
-    npos += lam[k] > 0.0;
-    nneg += lam[k] < 0.0;
-  }
-  const bool from_b = nneg < npos;
-  const int nterm = from_b ? nneg : npos;
-  const int wterm = __reduce_max_sync(__activemask(), nterm);
-  double* Bs = Ad;  // B+ replaces A (for D = 9 scaled by 1/4, the square of K4's entries)
-  constexpr double bsc = D == 9 ? 0.25 : 1.0;
+        for (int j = 0; j < D; ++j) vl[j] = Vs[(l * D + j) * S];
 #pragma unroll
-  for (int e = 0; e < NP; ++e) Bs[e * S] = from_b ? Br[e] * bsc : 0.0;
-  for (int j = 0; j < wterm; ++j) {
-    int k = -1, cnt = 0;
-    double wk = 0.0;
-#pragma unroll
-    for (int kk = 0; kk < D; ++kk) {
-      const bool sel = from_b ? lam[kk] < 0.0 : lam[kk] > 0.0;
-      if (sel && cnt == j) {
-        k = kk;
-        wk = (from_b ? -lam[kk] : lam[kk]) * bsc;
-      }
-      cnt += sel;
-    }
-    if (k < 0) continue;
-    double v[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) v[i] = Vs[(k * D + i) * S];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      const double wi = wk * v[i];
-#pragma unroll
-      for (int jj = i; jj < D; ++jj) Bs[tri_idx(i, jj, D) * S] += wi * v[jj];
-    }
-  }
-  const uint32_t c = A.aidx[a];
-  const Stencil st = stencil_of(A.cand[c], A.ev0, A.ev1, A.tv, A.T);
-  if constexpr (D == 9) {
-    // the plane types involve all four points, in stencil order
-    hadamard_scatter(A, st, Bs, S);
-  } else {
-    // scatter: block (q1, q2) of the involved points
-    //   = sum_ab K[q1][ab] R[q2][ab],  R[q2][ab] = sum_bb K[q2][bb] B+[ab, bb]
-    // (3x3 blocks; R for one q2 at a time)
-    const TypeInfo& TI = st.ee ? c_ee_types[A.ctype[c]] : c_pt_types[A.ctype[c]];
-    const int nz = TI.kind + 1;
-    int pts[4], np = 0;
-    for (int i = 0; i < 4; ++i) {
-      bool used = false;
-      for (int mm = 0; mm < nz; ++mm) used |= TI.C[mm][i] != 0;
-      if (used) pts[np++] = i;
-    }
-    constexpr int NB = D / 3;
-    for (int q2 = 0; q2 < np; ++q2) {
-      double R[NB][9];
-#pragma unroll
-      for (int ab = 0; ab < NB; ++ab)
-#pragma unroll
-        for (int al = 0; al < 3; ++al)
-#pragma unroll
-          for (int be = 0; be < 3; ++be) {
-            double v = 0.0;
-#pragma unroll
-            for (int bb = 0; bb < NB; ++bb) {
-              const int r = 3 * ab + al, cl = 3 * bb + be;
-              v += c_K3[q2][bb] * Bs[(r <= cl ? tri_idx(r, cl, D) : tri_idx(cl, r, D)) * S];
-            }
-            R[ab][3 * al + be] = v;
-          }
-      for (int q1 = 0; q1 <= q2; ++q1) {
-        double blk[9];
-#pragma unroll
-        for (int e = 0; e < 9; ++e) {
+        for (int i = 0; i < D; ++i) {
           double v = 0.0;
 #pragma unroll
-          for (int ab = 0; ab < NB; ++ab) v += c_K3[q1][ab] * R[ab][e];
-          blk[e] = v;
+          for (int j = 0; j < D; ++j) v += Br[i <= j ? tri_idx(i, j, D) : tri_idx(j, i, D)] * vl[j];
+          t[i] = v;
         }
-        const int r = st.v[pts[q1]], cc = st.v[pts[q2]];
-        add_block(A, r, cc, blk, false);
-        if (q1 != q2) add_block(A, cc, r, blk, true);
+        for (int k = 0; k <= l; ++k) {
+          double v = 0.0;
+#pragma unroll
+          for (int i = 0; i < D; ++i) v += Vs[(k * D + i) * S] * t[i];
+          Ad[tri_idx(k, l, D) * S] = v;
+        }
+      }
+      jacobi_refine64<D>(Ad, Vs, S, 1e-28, 12);
+    }
+    // B+ (into the A region) from the side with fewer terms: the sum over the
+    // positive eigenpairs of lam v v^T, or B minus the sum over the negative
+    // ones (B = V A V^T to the FP64 sweeps' tolerance).  The loop runs as many
+    // terms as the warp's busiest lane needs; each lane adds its own j-th term.
+    double lam[D];
+    int npos = 0, nneg = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      lam[k] = Ad[tri_idx(k, k, D) * S];
+      npos += lam[k] > 0.0;
+      nneg += lam[k] < 0.0;
+    }
+    const bool from_b = nneg < npos;
+    const int nterm = from_b ? nneg : npos;
+    const int wterm = __reduce_max_sync(__activemask(), nterm);
+    double* Bs = Ad;  // B+ replaces A (for D = 9 scaled by 1/4, the square of K4's entries)
+    constexpr double bsc = D == 9 ? 0.25 : 1.0;
+#pragma unroll
+    for (int e = 0; e < NP; ++e) Bs[e * S] = from_b ? Br[e] * bsc : 0.0;
+    for (int j = 0; j < wterm; ++j) {
+      int k = -1, cnt = 0;
+      double wk = 0.0;
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) {
+        const bool sel = from_b ? lam[kk] < 0.0 : lam[kk] > 0.0;
+        if (sel && cnt == j) {
+          k = kk;
+          wk = (from_b ? -lam[kk] : lam[kk]) * bsc;
+        }
+        cnt += sel;
+      }
+      if (k < 0) continue;
+      double v[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) v[i] = Vs[(k * D + i) * S];
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const double wi = wk * v[i];
+#pragma unroll
+        for (int jj = i; jj < D; ++jj) Bs[tri_idx(i, jj, D) * S] += wi * v[jj];
+      }
+    }
+    const uint32_t c = A.aidx[a];
+    const Stencil st = stencil_of(A.cand[c], A.ev0, A.ev1, A.tv, A.T);
+    if constexpr (D == 9) {
+      // the plane types involve all four points, in stencil order
+      hadamard_scatter(A, st, Bs, S);
+    } else {
+      // scatter: block (q1, q2) of the involved points
+      //   = sum_ab K[q1][ab] R[q2][ab],  R[q2][ab] = sum_bb K[q2][bb] B+[ab, bb]
+      // (3x3 blocks; R for one q2 at a time)
+      const TypeInfo& TI = st.ee ? c_ee_types[A.ctype[c]] : c_pt_types[A.ctype[c]];
+      const int nz = TI.kind + 1;
+      int pts[4], np = 0;
+      for (int i = 0; i < 4; ++i) {
+        bool used = false;
+        for (int mm = 0; mm < nz; ++mm) used |= TI.C[mm][i] != 0;
+        if (used) pts[np++] = i;
+      }
+      constexpr int NB = D / 3;
+      for (int q2 = 0; q2 < np; ++q2) {
+        double R[NB][9];
+#pragma unroll
+        for (int ab = 0; ab < NB; ++ab)
+#pragma unroll
+          for (int al = 0; al < 3; ++al)
+#pragma unroll
+            for (int be = 0; be < 3; ++be) {
+              double v = 0.0;
+#pragma unroll
+              for (int bb = 0; bb < NB; ++bb) {
+                const int r = 3 * ab + al, cl = 3 * bb + be;
+                v += c_K3[q2][bb] * Bs[(r <= cl ? tri_idx(r, cl, D) : tri_idx(cl, r, D)) * S];
+              }
+              R[ab][3 * al + be] = v;
+            }
+        for (int q1 = 0; q1 <= q2; ++q1) {
+          double blk[9];
+#pragma unroll
+          for (int e = 0; e < 9; ++e) {
+            double v = 0.0;
+#pragma unroll
+            for (int ab = 0; ab < NB; ++ab) v += c_K3[q1][ab] * R[ab][e];
+            blk[e] = v;
+          }
+          const int r = st.v[pts[q1]], cc = st.v[pts[q2]];
+          add_block(A, r, cc, blk, false);
+          if (q1 != q2) add_block(A, cc, r, blk, true);
+        }
       }
     }
   }
+}
+
+// k_hess_proj<D> over at most one resident wave of blocks (the occupancy
+// looked up once per scene)
+template <int D>
+cb_status launch_proj(cb_scene* s, const HessArgs& A, int64_t cap, cudaStream_t st) {
+  const int smem = ProjSmem<D>::PER_THREAD * PROJ_THREADS;
+  int& occ = s->proj_occ[D == 9 ? 0 : 1];
+  CB_CUDA(cudaFuncSetAttribute(k_hess_proj<D, PROJ_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  if (occ <= 0) {
+    CB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hess_proj<D, PROJ_THREADS>, PROJ_THREADS, smem));
+    occ = std::max(1, occ);
+  }
+  const int64_t g = std::min<int64_t>(cb_grid(cap, PROJ_THREADS), (int64_t)s->n_sms * occ);
+  k_hess_proj<D, PROJ_THREADS><<<(int)std::max<int64_t>(1, g), PROJ_THREADS, smem, cb_count(st)>>>(A);
+  CB_CUDA(cudaGetLastError());
+  return CB_OK;
 }
 
 // Register-resident versions of the two Jacobi phases for the 4x4 block of
@@ -1959,9 +2111,9 @@ __device__ __forceinline__ void psd2(double a, double b, double c, double& pa, d
 // eigenproblem instead of a 4x4.  The 2x2 block is projected in closed form,
 // the 6x6 result rotated back block by block (B+ = (I x R) B'+ (I x R)^T) and
 // scattered as in k_hess_proj<6>.
-__global__ void __launch_bounds__(128) k_hess_proj_pe(HessArgs A, int64_t m) {
+__global__ void __launch_bounds__(128) k_hess_proj_pe(HessArgs A) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= m) return;
+  if (w >= (int64_t)*A.n4) return;
   const uint32_t a = A.slot4[w];
   double q[10], R[9];
 #pragma unroll
@@ -2067,6 +2219,17 @@ __global__ void k_macc_reset(int count, unsigned long long* __restrict__ macc, i
 }
 
 __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+
+// One launch for the resets at the start of a barrier pass: the scalar slots
+// in sc_mask and, for every member, the accumulator slots in macc_mask.
+__global__ void k_pass_reset(unsigned long long* __restrict__ sc, uint32_t sc_mask, int count,
+                             unsigned long long* __restrict__ macc, uint32_t macc_mask) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < SC_N && ((sc_mask >> i) & 1u)) sc[i] = 0ull;
+  if (i < count)
+    for (int k = 0; k < MACC_STRIDE; ++k)
+      if ((macc_mask >> k) & 1u) macc[(size_t)i * MACC_STRIDE + k] = 0ull;
+}
 
 }  // namespace
 
@@ -2262,12 +2425,15 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
   unsigned long long* macc = bp<unsigned long long>(s->macc);
   const int M = s->count;
   s->cd_split = false;
-  k_set_u64<<<1, 1, 0, cb_count(st)>>>(ncore, 0ull);
-  k_macc_reset<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, MACC_E, 0ull);
-  k_macc_reset<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, MACC_STATUS, 0ull);
+  // the pass's counters (the queue lengths stay readable until the next pass)
+  {
+    const uint32_t scm = (1u << SC_NCORE) | (1u << SC_NLIST) | (1u << SC_KSPLIT) | (1u << SC_NMOLL) |
+                         (1u << SC_N9) | (1u << SC_N6) | (1u << SC_N4);
+    k_pass_reset<<<cb_grid(std::max(M, (int)SC_N)), CB_THREADS, 0, cb_count(st)>>>(
+        (unsigned long long*)sc, scm, M, macc, (1u << MACC_E) | (1u << MACC_STATUS));
+  }
   if (grad) CB_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * 3 * (size_t)s->n, st));
   s->n_active = 0;
-  s->n_hq[0] = s->n_hq[1] = s->n_hq[2] = 0;
   s->nnzb = 0;
   CB_TRY(buf_ensure(s->bsr_row, sizeof(int32_t) * ((size_t)s->n + 1), st));
   CB_CUDA(cudaMemsetAsync(s->bsr_row.p, 0, sizeof(int32_t) * ((size_t)s->n + 1), st));
@@ -2281,7 +2447,6 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     CB_TRY(to_f32(s, x, bp<double>(s->bw.cx), s->xf, st));
     CB_TRY(buf_ensure(s->dlist, sizeof(uint32_t) * (size_t)nc, st));
     unsigned int* nl = (unsigned int*)(sc + SC_NLIST);
-    k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_NLIST), 0ull);
     k_distance_screen<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(
         nc, bp<uint64_t>(s->cand), bp<uint8_t>(s->klass), bp<int32_t>(s->ev0), bp<int32_t>(s->ev1),
         bp<int32_t>(s->tv), s->T, bp<float4>(s->xf), bp<double>(s->bw.cx), bp<int32_t>(s->vsc),
@@ -2358,14 +2523,12 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     cbp::exclusive_scan<uint32_t, int32_t>(bp<uint32_t>(s->row_cnt), bp<int32_t>(s->bsr_row), (int64_t)s->n + 1,
                                            (int32_t*)bp<uint32_t>(s->scan_tmp), (int32_t*)nullptr, st);
     CB_TRY(buf_ensure(s->horder, sizeof(uint32_t) * (size_t)na, st));
-    k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_KSPLIT), 0ull);
     bool mollify = false;
     for (const MemberParams& mpm : s->hmp) mollify |= mpm.mollify != 0;
     MollArgs MA{};
     if (mollify) {
       CB_TRY(buf_ensure(s->hmoll, (size_t)na, st));
       CB_TRY(buf_ensure(s->mlist, sizeof(uint32_t) * (size_t)na, st));
-      k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_NMOLL), 0ull);
       MA = MollArgs{x, s->n, bp<int32_t>(s->ev0), bp<int32_t>(s->ev1), bp<int32_t>(s->vsc),
                     bp<MemberParams>(s->mp), bp<double>(s->elen2), bp<uint8_t>(s->hmoll),
                     bp<uint32_t>(s->mlist), (unsigned*)(sc + SC_NMOLL)};
@@ -2415,31 +2578,16 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     A.mlist = bp<uint32_t>(s->mlist);
     A.nmoll = (const unsigned*)(sc + SC_NMOLL);
     A.elen2 = bp<double>(s->elen2);
-    k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_N9), 0ull);
-    k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_N6), 0ull);
-    k_set_u64<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_N4), 0ull);
     if (s->timing) cudaEventRecord(s->ev[10], st);
     k_hess_prep<<<cb_grid(na, 128), 128, 0, cb_count(st)>>>(A);
     if (mollify) k_moll_hess<<<cb_grid(na, 128), 128, 0, cb_count(st)>>>(A);
     CB_CUDA(cudaGetLastError());
-    uint64_t hq[SC_N4 - SC_N9 + 1];
-    CB_TRY(read_scalars(s, SC_N9, SC_N4 - SC_N9 + 1, hq, st));
-    const int64_t m9 = (int64_t)(uint32_t)hq[0], m6 = (int64_t)(uint32_t)hq[SC_N6 - SC_N9],
-                  m4 = (int64_t)(uint32_t)hq[SC_N4 - SC_N9];
-    s->n_hq[0] = m9;
-    s->n_hq[1] = m4;
-    s->n_hq[2] = m6;
-    if (m4 > 0) k_hess_proj_pe<<<cb_grid(m4, 128), 128, 0, cb_count(st)>>>(A, m4);
-    if (m9 > 0) {
-      const int smem = ProjSmem<9>::PER_THREAD * PROJ_THREADS;
-      CB_CUDA(cudaFuncSetAttribute(k_hess_proj<9, PROJ_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-      k_hess_proj<9, PROJ_THREADS><<<cb_grid(m9, PROJ_THREADS), PROJ_THREADS, smem, cb_count(st)>>>(A, m9);
-    }
-    if (m6 > 0) {
-      const int smem = ProjSmem<6>::PER_THREAD * PROJ_THREADS;
-      CB_CUDA(cudaFuncSetAttribute(k_hess_proj<6, PROJ_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-      k_hess_proj<6, PROJ_THREADS><<<cb_grid(m6, PROJ_THREADS), PROJ_THREADS, smem, cb_count(st)>>>(A, m6);
-    }
+    // the three queues' lengths stay on the device: every projection kernel
+    // reads its own, the point-edge one over a grid for all active pairs, the
+    // shared-memory ones over at most one wave of blocks (grid-stride)
+    k_hess_proj_pe<<<cb_grid(na, 128), 128, 0, cb_count(st)>>>(A);
+    CB_TRY(launch_proj<9>(s, A, na, st));
+    CB_TRY(launch_proj<6>(s, A, na, st));
     if (s->timing) cudaEventRecord(s->ev[11], st);
     CB_CUDA(cudaGetLastError());
   }

@@ -97,6 +97,37 @@ __global__ void k_scan_apply(const TIn* in, int64_t n, const TOut* block_sums, T
   }
 }
 
+// Small inputs: one block walks the tiles in order with a running carry (one
+// launch instead of three; the tiles are few, so the serial walk is short).
+template <typename TIn, typename TOut>
+__global__ void __launch_bounds__(SCAN_T) k_scan_single(const TIn* in, int64_t n, TOut* out, TOut* total) {
+  __shared__ TOut tot;
+  TOut carry = 0;
+  for (int64_t base = 0; base < n; base += SCAN_TILE) {
+    TOut v[SCAN_ITEMS];
+    TOut s = 0;
+#pragma unroll
+    for (int r = 0; r < SCAN_ITEMS; ++r) {
+      const int64_t i = base + (int64_t)threadIdx.x * SCAN_ITEMS + r;
+      v[r] = (i < n) ? (TOut)in[i] : TOut(0);
+      s += v[r];
+    }
+    TOut ex = block_excl_scan<TOut>(s, &tot) + carry;
+#pragma unroll
+    for (int r = 0; r < SCAN_ITEMS; ++r) {
+      const int64_t i = base + (int64_t)threadIdx.x * SCAN_ITEMS + r;
+      if (i < n) out[i] = ex;
+      ex += v[r];
+    }
+    carry += tot;  // tot is final: block_excl_scan ends with a barrier
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+// Inputs of at most this many tiles take the single-block scan.
+constexpr int64_t SCAN_SINGLE_TILES = 8;
+
 // Exclusive scan out[i] = sum_{k<i} in[k]; *total_dev = sum of all (device).
 // tmp must hold scan_tmp_elems(n) elements of TOut.  in and out may alias.
 inline int64_t scan_tmp_elems(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
@@ -105,6 +136,10 @@ template <typename TIn, typename TOut>
 void exclusive_scan(const TIn* in, TOut* out, int64_t n, TOut* tmp, TOut* total_dev, cudaStream_t st) {
   int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (nb < 1) nb = 1;
+  if (nb <= SCAN_SINGLE_TILES) {
+    k_scan_single<TIn, TOut><<<1, SCAN_T, 0, cb_count(st)>>>(in, n, out, total_dev);
+    return;
+  }
   k_scan_reduce<TIn, TOut><<<(int)nb, SCAN_T, 0, cb_count(st)>>>(in, n, tmp);
   k_scan_block_sums<TOut><<<1, SCAN_T, 0, cb_count(st)>>>(tmp, nb, total_dev);
   k_scan_apply<TIn, TOut><<<(int)nb, SCAN_T, 0, cb_count(st)>>>(in, n, tmp, out);
@@ -133,10 +168,26 @@ __global__ void k_radix_hist(const K* __restrict__ keys, int64_t n, int shift, u
   hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = sh[threadIdx.x];
 }
 
-template <typename K, typename V, bool HAS_V>
+// Scatter of one digit pass.  offs holds the global start of (digit, block)
+// at [digit * nblocks + block]; with FOLD the kernel reads the per-block
+// histograms instead (hist[digit * nblocks + block]) and forms its own starts
+// (few blocks: each thread sums one digit's row), which saves the scan.
+template <typename K, typename V, bool HAS_V, bool FOLD = false>
 __global__ void __launch_bounds__(RS_T) k_radix_scatter(const K* __restrict__ kin, const V* __restrict__ vin,
                                                         K* __restrict__ kout, V* __restrict__ vout, int64_t n,
                                                         int shift, const uint32_t* __restrict__ offs, int nblocks) {
+  __shared__ uint32_t gstart[FOLD ? 256 : 1];
+  if constexpr (FOLD) {
+    const uint32_t* row = offs + (int64_t)threadIdx.x * nblocks;
+    uint32_t before = 0, all = 0;
+    for (int b = 0; b < nblocks; ++b) {
+      const uint32_t c = row[b];
+      before += b < (int)blockIdx.x ? c : 0u;
+      all += c;
+    }
+    __shared__ uint32_t tot_f;
+    gstart[threadIdx.x] = block_excl_scan<uint32_t>(all, &tot_f) + before;
+  }
   __shared__ K sk[RS_TILE];
   __shared__ V sv[HAS_V ? RS_TILE : 1];
   __shared__ uint32_t wcnt[RS_WARPS][256];
@@ -198,13 +249,17 @@ __global__ void __launch_bounds__(RS_T) k_radix_scatter(const K* __restrict__ ki
   for (int i = tid; i < cnt; i += RS_T) {
     K k = sk[i];
     uint32_t d = (uint32_t)(k >> shift) & 255u;
-    int64_t pos = (int64_t)offs[(int64_t)d * nblocks + blockIdx.x] + (i - dstart[d]);
+    const int64_t g0 = FOLD ? (int64_t)gstart[d] : (int64_t)offs[(int64_t)d * nblocks + blockIdx.x];
+    int64_t pos = g0 + (i - dstart[d]);
     kout[pos] = k;
     if (HAS_V) vout[pos] = sv[i];
   }
 }
 
 inline int64_t radix_hist_elems(int64_t n) { return 256 * ((n + RS_TILE - 1) / RS_TILE + 1); }
+
+// Sorts of at most this many tiles form the digit starts inside the scatter.
+constexpr int RS_FOLD_BLOCKS = 32;
 
 // Sort keys (and values) on bits [lo_bit, hi_bit).  Buffers ping-pong between
 // (k0, v0) and (k1, v1); returns 0 if the result is in k0/v0, 1 if in k1/v1.
@@ -221,8 +276,12 @@ int radix_sort(K* k0, V* v0, K* k1, V* v1, int64_t n, int lo_bit, int hi_bit, ui
     K* ko = cur ? k0 : k1;
     V* vo = cur ? v0 : v1;
     k_radix_hist<K><<<nb, RS_T, 0, cb_count(st)>>>(ki, n, sh, hist, nb);
-    exclusive_scan<uint32_t, uint32_t>(hist, hist, (int64_t)256 * nb, scan_tmp, (uint32_t*)nullptr, st);
-    k_radix_scatter<K, V, HAS_V><<<nb, RS_T, 0, cb_count(st)>>>(ki, vi, ko, vo, n, sh, hist, nb);
+    if (nb <= RS_FOLD_BLOCKS) {
+      k_radix_scatter<K, V, HAS_V, true><<<nb, RS_T, 0, cb_count(st)>>>(ki, vi, ko, vo, n, sh, hist, nb);
+    } else {
+      exclusive_scan<uint32_t, uint32_t>(hist, hist, (int64_t)256 * nb, scan_tmp, (uint32_t*)nullptr, st);
+      k_radix_scatter<K, V, HAS_V><<<nb, RS_T, 0, cb_count(st)>>>(ki, vi, ko, vo, n, sh, hist, nb);
+    }
     cur ^= 1;
   }
   return cur;

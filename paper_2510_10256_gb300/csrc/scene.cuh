@@ -104,8 +104,6 @@ struct BroadWork {
   DevBuf ovl;         // uint32 entries with more pairs than the stage holds
   DevBuf scan_tmp;
   DevBuf hist;
-  float cell = 0.f;   // cell size of member 0 used last
-  std::vector<double> hcx;     // host copy of cx
 };
 
 struct cb_scene {
@@ -131,11 +129,11 @@ struct cb_scene {
   std::vector<int64_t> voff, eoff, toff;  // member offsets of vertices, edges, triangles (count+1)
   int64_t n_frest_pt = 0;                 // shells: point-triangle keys at the head of frest
   DevBuf macc;          // per member: double energy, u64 alpha bits, u64 lb bits, u64 status, double lo, hi
-  DevBuf hstage;        // device copy of per-member box inflation
   void* hstage_host = nullptr;  // pinned staging (the largest per-member record x members + 256)
   cudaStream_t last_stream = nullptr;
   int device = 0;
   int n_sms = 152;      // multiprocessors of the device (caps of grid-stride launches: a few blocks per SM)
+  int proj_occ[2] = {0, 0};  // resident blocks per SM of k_hess_proj<9> and <6> (0: not looked up yet)
 
   // topology on device
   DevBuf ev0, ev1;      // int32 [E]
@@ -178,7 +176,6 @@ struct cb_scene {
   DevBuf ctype;         // int8 [nc]
   DevBuf ccls;          // uint8 [nc] final class (with C)
   int64_t n_active = 0;
-  int64_t n_hq[3] = {0, 0, 0};  // last pass: face / line-line, point-edge in frame, generic point-edge pairs
   DevBuf aidx;          // uint32 [na] candidate index of each active pair
   DevBuf bkey[2];       // uint64 [16 na]
   DevBuf bflag, bpos;   // uint32
