@@ -1869,6 +1869,263 @@ __global__ void __launch_bounds__(S) k_hess_proj(HessArgs A) {
   }
 }
 
+// ---- the 9x9 projection for short queues: 16 lanes per pair --------------
+// One thread per pair runs some 8,500 dependent FP64 instructions, and the
+// FP64 pipe of an SM sub-partition completes one warp instruction only every
+// few tens of cycles, so a short queue (a small scene) waits for that chain
+// however idle the device is.  This form spreads one pair over a half-warp:
+// lane r (0..8) owns row r of the working matrix and of the eigenvectors,
+// rows live in shared memory, and a rotation is one round of row updates
+// between two segment barriers.  The arithmetic is that of k_hess_proj<9>:
+// FP32 cyclic Jacobi on the scaled matrix, FP64 modified Gram-Schmidt,
+// A = V^T B V, FP64 sweeps with FP32 tangents to an off-diagonal norm of
+// 1e-14 ||A||, B+ from the positive eigenpairs, the Hadamard scatter; only
+// the order of the sums differs.
+constexpr int PL_PAIRS = 8;                 // pairs per block
+constexpr int PL_THREADS = 16 * PL_PAIRS;   // one half-warp per pair
+constexpr int PL_SMEM = 81 + 81 + 108;      // doubles per pair: A, V, staging (W, R; FP32 A and V)
+// queues of at most this many active pairs take the lane-parallel form
+constexpr int64_t PL_MAX_ACTIVE = 4096;
+
+// sum over the 16 lanes of the caller's half-warp (every lane gets the same bits)
+template <typename R>
+__device__ __forceinline__ R seg_sum(R v, unsigned mask) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, 16);
+  return v;
+}
+
+__global__ void __launch_bounds__(PL_THREADS) k_hess_proj_lanes(HessArgs A) {
+  extern __shared__ double pl_smem[];
+  const int seg = threadIdx.x >> 4, r = threadIdx.x & 15;
+  const unsigned mask = 0xffffu << (16 * (seg & 1));
+  const bool row = r < 9;
+  const int64_t w = (int64_t)blockIdx.x * PL_PAIRS + seg;
+  if (w >= (int64_t)*A.n9) return;  // the whole half-warp leaves together
+  double* As = pl_smem + (size_t)seg * PL_SMEM;  // A[i][j] at [9 i + j]
+  double* Vs = As + 81;                          // V[i][k] (component i of eigenvector k) at [9 i + k]
+  double* Xs = Vs + 81;                          // staging
+  float* A32 = (float*)Xs;                       // FP32 phase: A at [9 i + j], V at [81 + 9 i + k]
+  float* V32 = A32 + 81;
+  const uint32_t a = A.slot9[w];
+  double Br[9];
+  double mx = 0.0;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    Br[j] = row ? A.B9[(size_t)(r <= j ? tri_idx(r, j, 9) : tri_idx(j, r, 9)) * A.cap + w] : 0.0;
+    mx = fmax(mx, fabs(Br[j]));
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(mask, mx, o, 16));
+  if (mx == 0.0) return;  // B+ = 0: nothing to add
+  // FP32 phase on B / max|B|
+  {
+    const double inv = 1.0 / mx;
+    if (row)
+#pragma unroll
+      for (int j = 0; j < 9; ++j) {
+        A32[9 * r + j] = (float)(Br[j] * inv);
+        V32[9 * r + j] = r == j ? 1.f : 0.f;
+      }
+    __syncwarp(mask);
+    for (int sweep = 0; sweep < 12; ++sweep) {
+      float off = 0.f, fro = 0.f;
+      if (row)
+        for (int j = 0; j < 9; ++j) {
+          const float v = A32[9 * r + j];
+          if (j == r) fro += v * v;
+          else off += v * v;
+        }
+      off = seg_sum(off, mask);
+      fro = seg_sum(fro, mask) + off;
+      if (fro == 0.f || off <= PROJ_FP32_TOL2 * fro) break;
+      const float skip = 1e-16f * sqrtf(fro);
+      for (int p = 0; p < 8; ++p)
+        for (int q = p + 1; q < 9; ++q) {
+          const float apq = A32[9 * p + q];
+          if (fabsf(apq) <= skip) continue;  // the same value in every lane of the pair
+          const float app = A32[9 * p + p], aqq = A32[9 * q + q];
+          const float tau = (aqq - app) / (2.f * apq);
+          const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+          const float c = 1.f / sqrtf(1.f + t * t), sn = t * c;
+          const bool other = row && r != p && r != q;
+          float nrp = 0.f, nrq = 0.f;
+          if (other) {
+            const float arp = A32[9 * r + p], arq = A32[9 * r + q];
+            nrp = c * arp - sn * arq;
+            nrq = sn * arp + c * arq;
+          }
+          if (row) {
+            const float vp = V32[9 * r + p], vq = V32[9 * r + q];
+            V32[9 * r + p] = c * vp - sn * vq;
+            V32[9 * r + q] = sn * vp + c * vq;
+          }
+          __syncwarp(mask);
+          if (other) {
+            A32[9 * r + p] = nrp;
+            A32[9 * p + r] = nrp;
+            A32[9 * r + q] = nrq;
+            A32[9 * q + r] = nrq;
+          } else if (r == p) {
+            A32[9 * p + p] = app - t * apq;
+            A32[9 * q + q] = aqq + t * apq;
+            A32[9 * p + q] = 0.f;
+            A32[9 * q + p] = 0.f;
+          }
+          __syncwarp(mask);
+        }
+    }
+  }
+  // FP64 modified Gram-Schmidt on the FP32 eigenvectors, columns in descending order
+  for (int k = 8; k >= 0; --k) {
+    double v = row ? (double)V32[9 * r + k] : 0.0;
+    for (int j = k + 1; j < 9; ++j) {
+      const double vj = row ? Vs[9 * r + j] : 0.0;
+      const double dp = seg_sum(vj * v, mask);
+      v -= dp * vj;
+    }
+    const double nn = rsqrt_refined(seg_sum(v * v, mask));  // 1 to FP32 accuracy here
+    if (row) Vs[9 * r + k] = v * nn;
+  }
+  __syncwarp(mask);  // V complete; the FP32 arrays are dead
+  // A = V^T (B V): row r of W = B V into the staging rows, then the upper
+  // triangle of row r of A from the columns of V and W, mirrored
+  if (row)
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+      double t = 0.0;
+#pragma unroll
+      for (int j = 0; j < 9; ++j) t += Br[j] * Vs[9 * j + l];
+      Xs[9 * r + l] = t;
+    }
+  __syncwarp(mask);
+  if (row)
+    for (int l = r; l < 9; ++l) {
+      double t = 0.0;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) t += Vs[9 * i + r] * Xs[9 * i + l];
+      As[9 * r + l] = t;
+      As[9 * l + r] = t;
+    }
+  __syncwarp(mask);
+  // FP64 sweeps (the rotation arithmetic of jacobi_refine64)
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    double off = 0.0, fro = 0.0;
+    if (row)
+      for (int j = 0; j < 9; ++j) {
+        const double v = As[9 * r + j];
+        if (j == r) fro += v * v;
+        else off += v * v;
+      }
+    off = seg_sum(off, mask);
+    fro = seg_sum(fro, mask) + off;
+    if (fro == 0.0 || off <= 1e-28 * fro) break;
+    const double nrm = sqrt(fro);
+    const double skip = 1e-16 * nrm, inv = 1.0 / nrm;
+    for (int p = 0; p < 8; ++p)
+      for (int q = p + 1; q < 9; ++q) {
+        const double apq = As[9 * p + q];
+        if (fabs(apq) <= skip) continue;
+        const double app = As[9 * p + p], aqq = As[9 * q + q];
+        const float apq32 = (float)(apq * inv), dd32 = (float)((aqq - app) * inv);
+        const float tau = dd32 / (2.f * apq32);
+        const float t32 = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+        const double t = (double)t32;
+        const bool small = fabsf(t32) < 1e-8f;  // c rounds to 1: s = t, the residual a_pq dropped
+        double c = 1.0, sn = t;
+        if (!small) {
+          c = rsqrt_refined(1.0 + t * t);
+          sn = t * c;
+        }
+        const bool other = row && r != p && r != q;
+        double nrp = 0.0, nrq = 0.0;
+        if (other) {
+          const double arp = As[9 * r + p], arq = As[9 * r + q];
+          nrp = small ? arp - t * arq : c * arp - sn * arq;
+          nrq = small ? arq + t * arp : sn * arp + c * arq;
+        }
+        if (row) {
+          const double vp = Vs[9 * r + p], vq = Vs[9 * r + q];
+          Vs[9 * r + p] = small ? vp - t * vq : c * vp - sn * vq;
+          Vs[9 * r + q] = small ? vq + t * vp : sn * vp + c * vq;
+        }
+        __syncwarp(mask);
+        if (other) {
+          As[9 * r + p] = nrp;
+          As[9 * p + r] = nrp;
+          As[9 * r + q] = nrq;
+          As[9 * q + r] = nrq;
+        } else if (r == p) {
+          double npp, nqq, npq;
+          if (small) {
+            npp = app - t * apq;
+            nqq = aqq + t * apq;
+            npq = 0.0;
+          } else {
+            const double cc = c * c, ss = sn * sn, cs = c * sn;
+            npp = cc * app - 2.0 * cs * apq + ss * aqq;
+            nqq = ss * app + 2.0 * cs * apq + cc * aqq;
+            npq = cs * (app - aqq) + (cc - ss) * apq;
+          }
+          As[9 * p + p] = npp;
+          As[9 * q + q] = nqq;
+          As[9 * p + q] = npq;
+          As[9 * q + p] = npq;
+        }
+        __syncwarp(mask);
+      }
+  }
+  // B+ / 4 (the square of K4's entries), row r: sum over the positive
+  // eigenpairs of lam v v^T; then the point transform of row r (lane 3a + i
+  // holds point a, axis i) into the staging rows
+  // (the product v_r v_j is formed first, so rows r and j get the same bits)
+  double P[9];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) P[j] = 0.0;
+  if (row)
+    for (int k = 0; k < 9; ++k) {
+      const double lam = As[9 * k + k];
+      if (!(lam > 0.0)) continue;
+      const double l4 = 0.25 * lam, vr = Vs[9 * r + k];
+#pragma unroll
+      for (int j = 0; j < 9; ++j) P[j] = fma(vr * Vs[9 * j + k], l4, P[j]);
+    }
+  __syncwarp(mask);  // every lane is done with W
+  if (row)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double h[4];
+      had3(P[j], P[3 + j], P[6 + j], h);  // over the column points
+#pragma unroll
+      for (int q2 = 0; q2 < 4; ++q2) Xs[12 * r + 3 * q2 + j] = h[q2];
+    }
+  __syncwarp(mask);
+  // lane l < 12 takes block row q1 = l / 3, axis i = l % 3: the transform
+  // over the row points, and the sixteen blocks' entries of that row
+  if (r < 12) {
+    const int q1 = r / 3, i = r % 3;
+    const uint32_t ci = A.aidx[a];
+    const Stencil st = stencil_of(A.cand[ci], A.ev0, A.ev1, A.tv, A.T);
+    const int rv = st.v[q1];
+#pragma unroll
+    for (int q2 = 0; q2 < 4; ++q2) {
+      const int cv = st.v[q2];
+      const int64_t bi = find_block(A.row_ptr, A.col, rv, cv);
+      if (!(bi < A.row_ptr[rv + 1] && A.col[bi] == cv)) {
+        atomicOr(A.status, (unsigned long long)CB_DEV_CAPACITY);  // pattern miss: never expected
+        continue;
+      }
+      double* dst = A.val + 9 * bi + 3 * i;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        double h[4];
+        had3(Xs[12 * i + 3 * q2 + j], Xs[12 * (3 + i) + 3 * q2 + j], Xs[12 * (6 + i) + 3 * q2 + j], h);
+        atomicAdd(&dst[j], h[q1]);
+      }
+    }
+  }
+}
+
 // k_hess_proj<D> over at most one resident wave of blocks (the occupancy
 // looked up once per scene)
 template <int D>
@@ -2586,7 +2843,13 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     // reads its own, the point-edge one over a grid for all active pairs, the
     // shared-memory ones over at most one wave of blocks (grid-stride)
     k_hess_proj_pe<<<cb_grid(na, 128), 128, 0, cb_count(st)>>>(A);
-    CB_TRY(launch_proj<9>(s, A, na, st));
+    if (na <= PL_MAX_ACTIVE) {
+      const int smem = PL_SMEM * (int)sizeof(double) * PL_PAIRS;
+      k_hess_proj_lanes<<<(int)((na + PL_PAIRS - 1) / PL_PAIRS), PL_THREADS, smem, cb_count(st)>>>(A);
+      CB_CUDA(cudaGetLastError());
+    } else {
+      CB_TRY(launch_proj<9>(s, A, na, st));
+    }
     CB_TRY(launch_proj<6>(s, A, na, st));
     if (s->timing) cudaEventRecord(s->ev[11], st);
     CB_CUDA(cudaGetLastError());
