@@ -341,7 +341,11 @@ __global__ void k_list_u(int64_t nu, const uint32_t* __restrict__ ulist, const u
 }
 
 // pass 2: additive CCD of the selected pairs, each up to its member's ceiling
-__device__ void ccd_exact_one(CcdArgs A, int64_t q, double* __restrict__ lb_out) {
+__global__ void __launch_bounds__(128) k_ccd_exact(CcdArgs A, int64_t m, const uint32_t* __restrict__ list,
+                                                   double* __restrict__ lb_out) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= m) return;
+  const int64_t q = list[w];
   AccdStart S = accd_start(A, q);
   unsigned long long* amin = macc_of(A, S.mem, MACC_ALPHA);
   if (S.lp == 0.0 || S.g0 <= 0.0) {  // only reachable through an FP32 bound below 1
@@ -401,32 +405,14 @@ __device__ void ccd_exact_one(CcdArgs A, int64_t q, double* __restrict__ lb_out)
   atomicMin(amin, (unsigned long long)__double_as_longlong(t));
 }
 
-// one thread per listed pair (grid-stride); the list length is read on the device
-__global__ void __launch_bounds__(128) k_ccd_exact(CcdArgs A, const uint32_t* __restrict__ mcount,
-                                                   const uint32_t* __restrict__ list, double* __restrict__ lb_out) {
-  const int64_t m = (int64_t)*mcount;
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < m; w += (int64_t)gridDim.x * blockDim.x)
-    ccd_exact_one(A, (int64_t)list[w], lb_out);
-}
-
 __global__ void k_alpha_final(int count, const unsigned long long* __restrict__ macc, double* __restrict__ out) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m < count) out[m] = __longlong_as_double(macc[(size_t)m * MACC_STRIDE + MACC_ALPHA]);
 }
-// the step's starting values: every member's minimum 1, lower bound 2 ("none"),
-// status 0; the pass counters 0
-__global__ void k_ccd_reset(int count, unsigned long long* __restrict__ macc, unsigned long long* __restrict__ sc) {
+__global__ void k_set(unsigned long long* p, unsigned long long v) { *p = v; }
+__global__ void k_macc_set(int count, unsigned long long* __restrict__ macc, int slot, unsigned long long v) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m < count) {
-    macc[(size_t)m * MACC_STRIDE + MACC_ALPHA] = 0x3ff0000000000000ull;  // 1.0
-    macc[(size_t)m * MACC_STRIDE + MACC_LB] = 0x4000000000000000ull;     // 2.0
-    macc[(size_t)m * MACC_STRIDE + MACC_STATUS] = 0ull;
-  }
-  if (m == 0) {
-    sc[SC_ITERS] = 0ull;
-    sc[SC_NLIST] = 0ull;
-    sc[SC_NU] = 0ull;
-  }
+  if (m < count) macc[(size_t)m * MACC_STRIDE + slot] = v;
 }
 
 }  // namespace
@@ -437,7 +423,10 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
   const int M = s->count;
   unsigned long long* macc = bp<unsigned long long>(s->macc);
   unsigned long long* mi = (unsigned long long*)(sc + SC_ITERS);
-  k_ccd_reset<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, (unsigned long long*)sc);
+  k_macc_set<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, MACC_ALPHA, 0x3ff0000000000000ull);  // 1.0
+  k_macc_set<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, MACC_LB, 0x4000000000000000ull);     // 2.0
+  k_macc_set<<<cb_grid(M), CB_THREADS, 0, cb_count(st)>>>(M, macc, MACC_STATUS, 0ull);
+  k_set<<<1, 1, 0, cb_count(st)>>>(mi, 0ull);
   const int64_t np = s->n_ccd;
   if (np > 0) {
     CB_TRY(buf_ensure(s->ccd_t, sizeof(double) * (size_t)np, st));
@@ -481,6 +470,8 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     CB_TRY(buf_ensure(s->dlist, sizeof(uint32_t) * (size_t)np, st));
     CB_TRY(buf_ensure(s->ccd_ulist, sizeof(uint32_t) * (size_t)np, st));
     unsigned int* nl = (unsigned int*)(sc + SC_NLIST);
+    k_set<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_NLIST), 0ull);
+    k_set<<<1, 1, 0, cb_count(st)>>>((unsigned long long*)(sc + SC_NU), 0ull);
     A.ulist = bp<uint32_t>(s->ccd_ulist);
     A.nu = (unsigned int*)(sc + SC_NU);
     k_ccd_screen<<<cb_grid(np, 128), 128, 0, cb_count(st)>>>(A, bp<double>(s->ccd_lb), bp<uint32_t>(s->dlist), nl);
@@ -493,16 +484,11 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     // Members whose minimum is already below every remaining bound are done
     // after pass 1.
     std::vector<unsigned long long> hm((size_t)M * MACC_STRIDE);
-    // the members' accumulators, and with them (same wait) the count of
-    // pairs pass 1 left unresolved
-    uint64_t hn = 0;
-    auto read_macc = [&](bool with_nu) -> cb_status {
+    auto read_macc = [&]() -> cb_status {
       CB_CUDA(cudaMemcpyAsync(s->hstage_host, macc, sizeof(unsigned long long) * MACC_STRIDE * M,
                               cudaMemcpyDeviceToHost, st));
-      if (with_nu) CB_CUDA(cudaMemcpyAsync(s->h_pinned, sc + SC_NU, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
       CB_CUDA(cudaStreamSynchronize(st));
       memcpy(hm.data(), s->hstage_host, sizeof(unsigned long long) * MACC_STRIDE * M);
-      if (with_nu) memcpy(&hn, s->h_pinned, sizeof(uint64_t));
       return CB_OK;
     };
     auto upload_band = [&](const std::vector<double>& lo, const std::vector<double>& hi) -> cb_status {
@@ -521,7 +507,7 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
       memcpy(&d, &b, 8);
       return d;
     };
-    CB_TRY(read_macc(true));
+    CB_TRY(read_macc());
     std::vector<double> lo(M, 3.0), hi(M, -1.0);
     std::vector<char> done(M, 1);
     bool any = false;
@@ -538,6 +524,8 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     uint32_t* tot = (uint32_t*)(sc + SC_COUNT1);
     int64_t nu = 0;
     if (any) {
+      uint64_t hn;
+      CB_TRY(read_scalars(s, SC_NU, 1, &hn, st));
       nu = (int64_t)(uint32_t)hn;
       for (int m = 0; m < M; ++m)
         if (!done[m]) hi[m] = std::min(1.0, 4.0 * dbl(hm[(size_t)m * MACC_STRIDE + MACC_LB]));
@@ -552,12 +540,14 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
                                               bp<uint32_t>(s->scan_tmp), tot, st);
       k_list_u<<<cb_grid(nu), CB_THREADS, 0, cb_count(st)>>>(nu, bp<uint32_t>(s->ccd_ulist), bp<uint32_t>(s->ccd_flag),
                                                              bp<uint32_t>(s->ccd_pos), bp<uint32_t>(s->ccd_list));
-      // the selected pairs: as many as the scan counted (read on the device),
-      // at most nu, over at most 16 blocks per SM
-      const int64_t g = std::min<int64_t>(cb_grid(nu, 128), (int64_t)s->n_sms * 16);
-      k_ccd_exact<<<(int)g, 128, 0, cb_count(st)>>>(A, tot, bp<uint32_t>(s->ccd_list), bp<double>(s->ccd_lb));
+      uint64_t hmsel;
+      CB_TRY(read_scalars(s, SC_COUNT1, 1, &hmsel, st));
+      const int64_t msel = (int64_t)(uint32_t)hmsel;
+      if (msel > 0)
+        k_ccd_exact<<<cb_grid(msel, 128), 128, 0, cb_count(st)>>>(A, msel, bp<uint32_t>(s->ccd_list),
+                                                                  bp<double>(s->ccd_lb));
       CB_CUDA(cudaGetLastError());
-      CB_TRY(read_macc(false));
+      CB_TRY(read_macc());
       any = false;
       for (int m = 0; m < M; ++m) {
         if (done[m]) continue;
