@@ -736,8 +736,16 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.cell_cnt), bp<uint32_t>(w.cell_off), np,
                                           bp<uint32_t>(w.scan_tmp), tot_dev, st);
   CB_CUDA(cudaGetLastError());
+  // the grids come back with the entry count (one wait): their sizes bound
+  // the bits of the cell codes the sort has to look at
+  CB_CUDA(cudaMemcpyAsync(s->hstage_host, w.grids.p, sizeof(Grid) * M, cudaMemcpyDeviceToHost, st));
   uint64_t hne;
   CB_TRY(read_scalars(s, SC_COUNT0, 1, &hne, st));
+  int dmax = 1;
+  for (int m = 0; m < M; ++m) {
+    const Grid& g = ((const Grid*)s->hstage_host)[m];
+    dmax = std::max({dmax, g.dx, g.dy, g.dz});
+  }
   const int64_t ne = (uint32_t)hne;
   if (ne == 0) {
     *n_out = 0;
@@ -760,10 +768,17 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   CB_TRY(buf_ensure(w.scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(cbp::radix_hist_elems(ne)) +
                                                              cbp::scan_tmp_elems(ne + 1) + 8),
                     st));
+  // bits a cell key can hold: the Morton code of cell coordinates below
+  // 2^cb (3 cb bits), the member index above bit 30, and for shells the type
+  // group and x level below them (every key is shifted up by `shift`)
+  int cb = 0;
+  while ((1 << cb) < dmax) ++cb;
+  const uint64_t need = ((((1ull << (3 * cb)) - 1ull) | (((1ull << mbits) - 1ull) << 30)) << shift) |
+                        ((1ull << shift) - 1ull);
   int r = cbp::radix_sort<uint64_t, uint32_t, true>(bp<uint64_t>(w.ekey[0]), bp<uint32_t>(w.eval[0]),
                                                     bp<uint64_t>(w.ekey[1]), bp<uint32_t>(w.eval[1]), ne, 0,
                                                     30 + mbits + shift, bp<uint32_t>(w.hist), bp<uint32_t>(w.scan_tmp),
-                                                    st);
+                                                    st, need);
   const uint64_t* ekey = bp<uint64_t>(w.ekey[r]);
   const uint32_t* eval = bp<uint32_t>(w.eval[r]);
   CB_TRY(buf_ensure(w.run_flag, sizeof(uint32_t) * (size_t)ne, st));

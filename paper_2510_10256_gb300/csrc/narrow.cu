@@ -1870,20 +1870,28 @@ __global__ void __launch_bounds__(S) k_hess_proj(HessArgs A) {
 }
 
 // ---- the 9x9 projection for short queues: 16 lanes per pair --------------
-// One thread per pair runs some 8,500 dependent FP64 instructions, and the
-// FP64 pipe of an SM sub-partition completes one warp instruction only every
-// few tens of cycles, so a short queue (a small scene) waits for that chain
-// however idle the device is.  This form spreads one pair over a half-warp:
-// lane r (0..8) owns row r of the working matrix and of the eigenvectors,
-// rows live in shared memory, and a rotation is one round of row updates
-// between two segment barriers.  The arithmetic is that of k_hess_proj<9>:
-// FP32 cyclic Jacobi on the scaled matrix, FP64 modified Gram-Schmidt,
-// A = V^T B V, FP64 sweeps with FP32 tangents to an off-diagonal norm of
-// 1e-14 ||A||, B+ from the positive eigenpairs, the Hadamard scatter; only
-// the order of the sums differs.
+// One thread per pair runs some 8,500 dependent FP64 instructions, and an FP64
+// warp instruction occupies a warp for 64 cycles however many of its lanes
+// are active (measured on GB300: 64 cycles per dependent or independent DFMA
+// of a lone warp; 76 with one warp per SM sub-partition, the SM's FP64 unit
+// then full at one warp instruction per ~19 cycles), so a short queue (a
+// small scene) waits for that chain however idle the device is.  This form
+// spreads one pair over a half-warp, lane r (0..8) owning row and column r,
+// and orders the Jacobi rotations round robin: in round k of a sweep lane r
+// pairs with (2k - r) mod 9 (lane k rests), the four disjoint rotations of a
+// round are applied at once (X = A J by columns, then J^T X by rows, V J by
+// columns), so a sweep is 9 rounds of a few FP64 instructions per lane
+// instead of 36 rotations in sequence.  Each lane computes its own pair's
+// rotation, the same bits in both lanes of the pair.  The arithmetic is
+// otherwise that of k_hess_proj<9>: FP32 Jacobi on the scaled matrix to
+// the same tolerance, FP64 modified Gram-Schmidt, A = V^T B V, FP64 sweeps
+// with FP32 tangents and FP64-normalised rotations to an off-diagonal norm
+// of 1e-14 ||A||, B+ from the positive eigenpairs, the Hadamard scatter.
 constexpr int PL_PAIRS = 8;                 // pairs per block
 constexpr int PL_THREADS = 16 * PL_PAIRS;   // one half-warp per pair
-constexpr int PL_SMEM = 81 + 81 + 108;      // doubles per pair: A, V, staging (W, R; FP32 A and V)
+// doubles per pair: A, X (A J; later the Hadamard staging, 108), V, and the
+// FP32 phase's A, X, V (3 x 81 floats)
+constexpr int PL_SMEM = 81 + 108 + 81 + 122;
 // queues of at most this many active pairs take the lane-parallel form
 constexpr int64_t PL_MAX_ACTIVE = 4096;
 
@@ -1895,6 +1903,31 @@ __device__ __forceinline__ R seg_sum(R v, unsigned mask) {
   return v;
 }
 
+// one round of simultaneous rotations on a 9x9 matrix As and vectors Vs held
+// in shared memory ([9 i + j]); lane r (< 9) applies its pair's rotation
+// (c, sg: sg = -s for the lower index of the pair, +s for the upper, 0 and
+// c = 1 for a resting lane or a skipped pair) to column r, then row r
+template <typename R>
+__device__ __forceinline__ void rr_apply(R* As, R* Xs, R* Vs, int r, int pr, R c, R sg, bool row, unsigned mask) {
+  R vr[9], vp[9];
+  if (row) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      Xs[9 * i + r] = c * As[9 * i + r] + sg * As[9 * i + pr];
+      vr[i] = Vs[9 * i + r];
+      vp[i] = Vs[9 * i + pr];
+    }
+  }
+  __syncwarp(mask);  // X complete; every lane holds the V columns it needs
+  if (row) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Vs[9 * i + r] = c * vr[i] + sg * vp[i];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) As[9 * r + j] = c * Xs[9 * r + j] + sg * Xs[9 * pr + j];
+  }
+  __syncwarp(mask);
+}
+
 __global__ void __launch_bounds__(PL_THREADS) k_hess_proj_lanes(HessArgs A) {
   extern __shared__ double pl_smem[];
   const int seg = threadIdx.x >> 4, r = threadIdx.x & 15;
@@ -1903,10 +1936,11 @@ __global__ void __launch_bounds__(PL_THREADS) k_hess_proj_lanes(HessArgs A) {
   const int64_t w = (int64_t)blockIdx.x * PL_PAIRS + seg;
   if (w >= (int64_t)*A.n9) return;  // the whole half-warp leaves together
   double* As = pl_smem + (size_t)seg * PL_SMEM;  // A[i][j] at [9 i + j]
-  double* Vs = As + 81;                          // V[i][k] (component i of eigenvector k) at [9 i + k]
-  double* Xs = Vs + 81;                          // staging
-  float* A32 = (float*)Xs;                       // FP32 phase: A at [9 i + j], V at [81 + 9 i + k]
-  float* V32 = A32 + 81;
+  double* Xs = As + 81;                          // A J; later the Hadamard staging
+  double* Vs = Xs + 108;                         // V[i][k]: component i of eigenvector k
+  float* A32 = (float*)(Vs + 81);
+  float* X32 = A32 + 81;
+  float* V32 = X32 + 81;
   const uint32_t a = A.slot9[w];
   double Br[9];
   double mx = 0.0;
@@ -1940,40 +1974,22 @@ __global__ void __launch_bounds__(PL_THREADS) k_hess_proj_lanes(HessArgs A) {
       fro = seg_sum(fro, mask) + off;
       if (fro == 0.f || off <= PROJ_FP32_TOL2 * fro) break;
       const float skip = 1e-16f * sqrtf(fro);
-      for (int p = 0; p < 8; ++p)
-        for (int q = p + 1; q < 9; ++q) {
+      for (int k = 0; k < 9; ++k) {
+        const int pr = row ? (2 * k - r + 18) % 9 : r;
+        const int p = min(r, pr), q = max(r, pr);
+        float c = 1.f, sg = 0.f;
+        if (row && pr != r) {
           const float apq = A32[9 * p + q];
-          if (fabsf(apq) <= skip) continue;  // the same value in every lane of the pair
-          const float app = A32[9 * p + p], aqq = A32[9 * q + q];
-          const float tau = (aqq - app) / (2.f * apq);
-          const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-          const float c = 1.f / sqrtf(1.f + t * t), sn = t * c;
-          const bool other = row && r != p && r != q;
-          float nrp = 0.f, nrq = 0.f;
-          if (other) {
-            const float arp = A32[9 * r + p], arq = A32[9 * r + q];
-            nrp = c * arp - sn * arq;
-            nrq = sn * arp + c * arq;
+          if (fabsf(apq) > skip) {
+            const float app = A32[9 * p + p], aqq = A32[9 * q + q];
+            const float tau = (aqq - app) / (2.f * apq);
+            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = 1.f / sqrtf(1.f + t * t);
+            sg = r == p ? -t * c : t * c;
           }
-          if (row) {
-            const float vp = V32[9 * r + p], vq = V32[9 * r + q];
-            V32[9 * r + p] = c * vp - sn * vq;
-            V32[9 * r + q] = sn * vp + c * vq;
-          }
-          __syncwarp(mask);
-          if (other) {
-            A32[9 * r + p] = nrp;
-            A32[9 * p + r] = nrp;
-            A32[9 * r + q] = nrq;
-            A32[9 * q + r] = nrq;
-          } else if (r == p) {
-            A32[9 * p + p] = app - t * apq;
-            A32[9 * q + q] = aqq + t * apq;
-            A32[9 * p + q] = 0.f;
-            A32[9 * q + p] = 0.f;
-          }
-          __syncwarp(mask);
         }
+        rr_apply<float>(A32, X32, V32, r, pr, c, sg, row, mask);
+      }
     }
   }
   // FP64 modified Gram-Schmidt on the FP32 eigenvectors, columns in descending order
@@ -1987,9 +2003,9 @@ __global__ void __launch_bounds__(PL_THREADS) k_hess_proj_lanes(HessArgs A) {
     const double nn = rsqrt_refined(seg_sum(v * v, mask));  // 1 to FP32 accuracy here
     if (row) Vs[9 * r + k] = v * nn;
   }
-  __syncwarp(mask);  // V complete; the FP32 arrays are dead
-  // A = V^T (B V): row r of W = B V into the staging rows, then the upper
-  // triangle of row r of A from the columns of V and W, mirrored
+  __syncwarp(mask);
+  // A = V^T (B V): row r of W = B V into X, then the upper triangle of row r
+  // of A from the columns of V and W, mirrored
   if (row)
 #pragma unroll
     for (int l = 0; l < 9; ++l) {
@@ -2008,7 +2024,8 @@ __global__ void __launch_bounds__(PL_THREADS) k_hess_proj_lanes(HessArgs A) {
       As[9 * l + r] = t;
     }
   __syncwarp(mask);
-  // FP64 sweeps (the rotation arithmetic of jacobi_refine64)
+  // FP64 sweeps: tangents from FP32 arithmetic on the values scaled by the
+  // norm, c = 1/sqrt(1 + t^2) to FP64 rounding (exactly 1 for |t| < 1e-8)
   for (int sweep = 0; sweep < 12; ++sweep) {
     double off = 0.0, fro = 0.0;
     if (row)
@@ -2022,63 +2039,29 @@ __global__ void __launch_bounds__(PL_THREADS) k_hess_proj_lanes(HessArgs A) {
     if (fro == 0.0 || off <= 1e-28 * fro) break;
     const double nrm = sqrt(fro);
     const double skip = 1e-16 * nrm, inv = 1.0 / nrm;
-    for (int p = 0; p < 8; ++p)
-      for (int q = p + 1; q < 9; ++q) {
+    for (int k = 0; k < 9; ++k) {
+      const int pr = row ? (2 * k - r + 18) % 9 : r;
+      const int p = min(r, pr), q = max(r, pr);
+      double c = 1.0, sg = 0.0;
+      if (row && pr != r) {
         const double apq = As[9 * p + q];
-        if (fabs(apq) <= skip) continue;
-        const double app = As[9 * p + p], aqq = As[9 * q + q];
-        const float apq32 = (float)(apq * inv), dd32 = (float)((aqq - app) * inv);
-        const float tau = dd32 / (2.f * apq32);
-        const float t32 = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-        const double t = (double)t32;
-        const bool small = fabsf(t32) < 1e-8f;  // c rounds to 1: s = t, the residual a_pq dropped
-        double c = 1.0, sn = t;
-        if (!small) {
+        if (fabs(apq) > skip) {
+          const double app = As[9 * p + p], aqq = As[9 * q + q];
+          const float apq32 = (float)(apq * inv), dd32 = (float)((aqq - app) * inv);
+          const float tau = dd32 / (2.f * apq32);
+          const float t32 = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+          const double t = (double)t32;
           c = rsqrt_refined(1.0 + t * t);
-          sn = t * c;
+          sg = r == p ? -t * c : t * c;
         }
-        const bool other = row && r != p && r != q;
-        double nrp = 0.0, nrq = 0.0;
-        if (other) {
-          const double arp = As[9 * r + p], arq = As[9 * r + q];
-          nrp = small ? arp - t * arq : c * arp - sn * arq;
-          nrq = small ? arq + t * arp : sn * arp + c * arq;
-        }
-        if (row) {
-          const double vp = Vs[9 * r + p], vq = Vs[9 * r + q];
-          Vs[9 * r + p] = small ? vp - t * vq : c * vp - sn * vq;
-          Vs[9 * r + q] = small ? vq + t * vp : sn * vp + c * vq;
-        }
-        __syncwarp(mask);
-        if (other) {
-          As[9 * r + p] = nrp;
-          As[9 * p + r] = nrp;
-          As[9 * r + q] = nrq;
-          As[9 * q + r] = nrq;
-        } else if (r == p) {
-          double npp, nqq, npq;
-          if (small) {
-            npp = app - t * apq;
-            nqq = aqq + t * apq;
-            npq = 0.0;
-          } else {
-            const double cc = c * c, ss = sn * sn, cs = c * sn;
-            npp = cc * app - 2.0 * cs * apq + ss * aqq;
-            nqq = ss * app + 2.0 * cs * apq + cc * aqq;
-            npq = cs * (app - aqq) + (cc - ss) * apq;
-          }
-          As[9 * p + p] = npp;
-          As[9 * q + q] = nqq;
-          As[9 * p + q] = npq;
-          As[9 * q + p] = npq;
-        }
-        __syncwarp(mask);
       }
+      rr_apply<double>(As, Xs, Vs, r, pr, c, sg, row, mask);
+    }
   }
   // B+ / 4 (the square of K4's entries), row r: sum over the positive
-  // eigenpairs of lam v v^T; then the point transform of row r (lane 3a + i
+  // eigenpairs of lam v v^T (the product v_r v_j is formed first, so rows r
+  // and j get the same bits); then the point transform of row r (lane 3a + i
   // holds point a, axis i) into the staging rows
-  // (the product v_r v_j is formed first, so rows r and j get the same bits)
   double P[9];
 #pragma unroll
   for (int j = 0; j < 9; ++j) P[j] = 0.0;
@@ -2090,7 +2073,7 @@ __global__ void __launch_bounds__(PL_THREADS) k_hess_proj_lanes(HessArgs A) {
 #pragma unroll
       for (int j = 0; j < 9; ++j) P[j] = fma(vr * Vs[9 * j + k], l4, P[j]);
     }
-  __syncwarp(mask);  // every lane is done with W
+  __syncwarp(mask);  // every lane is done with X
   if (row)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {

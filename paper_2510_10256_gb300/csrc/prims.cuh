@@ -264,13 +264,16 @@ constexpr int RS_FOLD_BLOCKS = 32;
 // Sort keys (and values) on bits [lo_bit, hi_bit).  Buffers ping-pong between
 // (k0, v0) and (k1, v1); returns 0 if the result is in k0/v0, 1 if in k1/v1.
 // hist: radix_hist_elems(n) uint32; scan_tmp: scan_tmp_elems(hist elems) uint32.
+// need: the key bits that may be set; a digit with none of them is the same
+// (zero) in every key, so its pass would not move anything and is skipped.
 template <typename K, typename V, bool HAS_V>
 int radix_sort(K* k0, V* v0, K* k1, V* v1, int64_t n, int lo_bit, int hi_bit, uint32_t* hist,
-               uint32_t* scan_tmp, cudaStream_t st) {
+               uint32_t* scan_tmp, cudaStream_t st, uint64_t need = ~0ull) {
   if (n <= 1) return 0;
   int nb = (int)((n + RS_TILE - 1) / RS_TILE);
   int cur = 0;
   for (int sh = lo_bit; sh < hi_bit; sh += 8) {
+    if (((need >> sh) & 0xffull) == 0) continue;
     const K* ki = cur ? k1 : k0;
     const V* vi = cur ? v1 : v0;
     K* ko = cur ? k0 : k1;
