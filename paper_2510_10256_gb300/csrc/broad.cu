@@ -383,16 +383,9 @@ __device__ __forceinline__ int lower_bound_group(const uint64_t* __restrict__ ke
   return lo;
 }
 
-// pairs an entry's thread keeps from the count pass for the fill pass (larger
-// counts are found again by the fill pass's tests)
+// pairs a rod entry's thread keeps from the count pass for the fill pass
+// (larger counts are found again by the fill pass's tests)
 constexpr int PAIR_STAGE = 32;
-// Shell cells: the count pass keeps the outcome of each entry's first
-// 32 mask_words partner positions as bits (bit b = j - j0 of entry i in word
-// mask[(b / 32) * ne + i]), so the keys of those pairs are written from the
-// bits without repeating the tests.  mask_words follows the longest partner
-// range of the previous broad phase (counted by the count pass), within
-// [1, PAIR_MASK_WORDS_MAX]; longer ranges are re-tested past the bits.
-constexpr int PAIR_MASK_WORDS_MAX = 64;
 
 struct PairArgs {
   Topo t;
@@ -405,12 +398,8 @@ struct PairArgs {
   const float4* __restrict__ ebox;   // boxes in entry order: entry j at [2 j], [2 j + 1]
   const double* __restrict__ box64;
   const Grid* __restrict__ grids;
-  uint32_t* __restrict__ mask;       // shells: [mask_words][entries] partner bits
-  int mask_words;                    // shells: words of partner bits per entry
-  unsigned int* maxr;                // shells, count pass: longest partner range (atomic max)
   int bi, bj;
   int shift;                   // bits of type group and x level below the cell code (shells: swept)
-  uint32_t* __restrict__ pend; // shells: per entry, the end of the partner positions the sweep tested
   unsigned long long* fpstat;  // count pass: [0] FP32-accepted pairs, [1] FP64-decided (may be null)
   bool canonical;              // fill pass: write canonical keys (else compact ones for the sort)
 };
@@ -461,71 +450,38 @@ __device__ __forceinline__ uint64_t pair_key(const PairArgs& A, uint32_t type, u
                      : (((uint64_t)type << (A.bi + A.bj)) | ((uint64_t)k1 << A.bj) | (uint64_t)k2);
 }
 
-// The pairs one entry reports, in a fixed order (the count and the fill pass
-// make the same decisions).  A vertex entry of a shell cell tests every triangle entry of the cell (the
-// vertex threads of a cell walk the same triangles in step) and an edge entry
-// every later edge entry.  Rod cells hold many more edges (yarn segments
-// crowd the cells of a knit or weave), so there the m (m - 1) / 2 tests of a
-// cell are shared by its m entries in round-robin order (entry a with
+// Rod cells: the pairs one entry reports, in a fixed order (the count and the
+// fill pass make the same decisions).  Rod cells hold many edges (yarn
+// segments crowd the cells of a knit or weave), so the m (m - 1) / 2 tests of
+// a cell are shared by its m entries in round-robin order (entry a with
 // a + 1, ..., a + (m - 1) / 2 mod m, and with a + m/2 for a < m/2 when m is
 // even): every thread makes about (m - 1) / 2 tests instead of the first one
-// m - 1 and the last none.  (On shell cells the round robin measured slightly
-// slower.)
-template <bool FILL, bool RR>
-__device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uint32_t* __restrict__ cnt,
-                                               const uint32_t* __restrict__ off, uint64_t* __restrict__ out,
-                                               uint64_t* __restrict__ stage, uint32_t* __restrict__ ovl,
-                                               unsigned int* __restrict__ novl) {
+// m - 1 and the last none.  The count pass keeps an entry's first PAIR_STAGE
+// keys (element-major, stage[k * ne + i]) and lists entries with more in ovl.
+template <bool FILL>
+__device__ __forceinline__ void rod_pairs_of_entry(const PairArgs& A, int64_t i, uint32_t* __restrict__ cnt,
+                                                   const uint32_t* __restrict__ off, uint64_t* __restrict__ out,
+                                                   uint64_t* __restrict__ stage, uint32_t* __restrict__ ovl,
+                                                   unsigned int* __restrict__ novl) {
   const Topo& t = A.t;
   const EntryRange R = entry_range(A, i);
-  if (R.none) {
-    if (!FILL) cnt[i] = 0;
-    return;
-  }
   const uint32_t P = R.P;
   const uint64_t kc = A.ekey[i] >> A.shift;
   const Grid G = A.grids[kc >> 30];
-  int j0 = R.j0, j1 = R.j1;
   const float4 plo = A.ebox[2 * (size_t)i], phi = A.ebox[2 * (size_t)i + 1];
   int pv[3];
   prim_verts(t, (int)P, pv);
-  // shells: the sweep stops at the first partner whose x level is above this level
-  const int cxi = RR ? 0 : morton_x((uint32_t)(kc & 0x3fffffffull));
-  const uint32_t xhi = RR ? 0u : x_level(phi.x, G, cxi);
   uint32_t count = 0, n32 = 0, n64 = 0;
   // the fill pass re-makes the count pass's decisions; never write past them
   const uint32_t c_end = FILL ? cnt[i] : 0;
-  // staged pairs (rod cells; shell cells hold too many pairs per vertex entry)
-  constexpr uint32_t K = RR ? PAIR_STAGE : 0;
-  // RR (rod scenes): round robin over the cell (entries are sorted by
-  // primitive, so the key takes the lower of the two first); else j in [j0, j1)
+  constexpr uint32_t K = PAIR_STAGE;
   const int m = R.e - R.s, a = (int)(i - R.s);
-  if (RR) {
-    j0 = 0;
-    j1 = (m % 2 == 0 && a < m / 2) ? m / 2 : (m - 1) / 2;
-  }
-  // shells: the fill pass runs only for entries with pairs past the partner
-  // bits (k_pairs_emit writes the pairs of the bits), from there on
-  int jb = j0;
-  if (!RR && FILL) {
-    jb = j0 + 32 * A.mask_words;
-    for (int w = 0; w < A.mask_words; ++w) count += __popc(A.mask[(size_t)w * A.ne + i]);
-  }
-  uint32_t word = 0, beyond = 0;
-  int jend = j1;
-  for (int jj = jb; jj < j1; ++jj) {
-    int j = jj;
-    if (RR) {
-      j = a + 1 + jj;
-      if (j >= m) j -= m;
-      j += R.s;
-    }
+  const int jn = (m % 2 == 0 && a < m / 2) ? m / 2 : (m - 1) / 2;
+  for (int jj = 0; jj < jn; ++jj) {
+    int j = a + 1 + jj;
+    if (j >= m) j -= m;
+    j += R.s;
     const float4 qlo = A.ebox[2 * (size_t)j], qhi = A.ebox[2 * (size_t)j + 1];
-    // the partner's level, as its key holds it (same cell, same arithmetic)
-    if (!RR && x_level(qlo.x, G, cxi) > xhi) {
-      jend = jj;  // this partner and every later one lie beyond the entry's box along x
-      break;
-    }
     const uint32_t Q = A.eval[j];
     bool acc = false;
     if (plo.x <= qhi.x && qlo.x <= phi.x && plo.y <= qhi.y && qlo.y <= phi.y && plo.z <= qhi.z &&
@@ -539,9 +495,9 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
         prim_verts(t, (int)Q, qv);
         bool inc = false;
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
+        for (int u = 0; u < 3; ++u)
 #pragma unroll
-          for (int b = 0; b < 3; ++b) inc |= (pv[a] >= 0 && pv[a] == qv[b]);
+          for (int b = 0; b < 3; ++b) inc |= (pv[u] >= 0 && pv[u] == qv[b]);
         if (!inc) {
           const bool sure = nextup(plo.x) <= nextdn(qhi.x) && nextup(qlo.x) <= nextdn(phi.x) &&
                             nextup(plo.y) <= nextdn(qhi.y) && nextup(qlo.y) <= nextdn(phi.y) &&
@@ -559,9 +515,8 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
       }
     }
     if (acc) {
-      // the pair's key takes the lower primitive first: rods in round-robin
-      // order, and shell edge-edge pairs (swept cells order edges by x, not by id)
-      const bool swap = RR ? j < (int)i : (R.type == CB_KEY_EE && Q < P);
+      // the pair's key takes the lower primitive first (round-robin order)
+      const bool swap = j < (int)i;
       const uint64_t key = pair_key(A, R.type, (swap ? Q : P) - R.ibase, (swap ? P : Q) - R.jbase);
       if (FILL) {
         // the pairs past the staged ones, at their place in the entry's range
@@ -571,29 +526,10 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
       }
       ++count;
     }
-    if (!RR && !FILL) {
-      // the lanes of a warp are at the same position b: coalesced word stores
-      const int b = jj - j0;
-      if (b < 32 * A.mask_words) {
-        word |= (uint32_t)acc << (b & 31);
-        if ((b & 31) == 31) {
-          A.mask[(size_t)(b >> 5) * A.ne + i] = word;
-          word = 0;
-        }
-      } else {
-        beyond += acc;
-      }
-    }
-  }
-  if (!RR && !FILL) {
-    // the last partial word of the tested positions, and where they end
-    const int nt = jend - j0;
-    if ((nt & 31) != 0 && nt <= 32 * A.mask_words) A.mask[(size_t)((nt - 1) >> 5) * A.ne + i] = word;
-    A.pend[i] = (uint32_t)jend;
   }
   if (!FILL) {
     cnt[i] = count;
-    if ((RR && count > K) || (!RR && beyond > 0)) ovl[atomicAdd(novl, 1u)] = (uint32_t)i;
+    if (count > K) ovl[atomicAdd(novl, 1u)] = (uint32_t)i;
     if (A.fpstat) {  // one atomic per converged group of lanes
       const unsigned mask = __activemask();
       const unsigned a32 = __reduce_add_sync(mask, n32), a64 = __reduce_add_sync(mask, n64);
@@ -602,75 +538,233 @@ __device__ __forceinline__ void pairs_of_entry(const PairArgs& A, int64_t i, uin
         if (a64) atomicAdd(&A.fpstat[1], (unsigned long long)a64);
       }
     }
-    if (!RR && A.maxr) {
-      const unsigned mask = __activemask();
-      const unsigned mr = __reduce_max_sync(mask, (unsigned)(jend - j0));
-      if ((int)(threadIdx.x & 31) == __ffs(mask) - 1 && mr) atomicMax(A.maxr, mr);
+  }
+}
+
+// rod cells, count pass (FILL = false, one thread per entry): cnt[i] = number
+// of pairs entry i reports; the fill pass (FILL = true) then runs over the
+// entries listed in ovl only, writing their pairs past the staged ones
+template <bool FILL>
+__global__ void __launch_bounds__(CB_THREADS) k_rod_pairs(PairArgs A, uint32_t* __restrict__ cnt,
+                                                          const uint32_t* __restrict__ off,
+                                                          uint64_t* __restrict__ out, uint64_t* __restrict__ stage,
+                                                          uint32_t* __restrict__ ovl, unsigned int* __restrict__ novl) {
+  if (!FILL) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < A.ne) rod_pairs_of_entry<FILL>(A, i, cnt, off, out, stage, ovl, novl);
+  } else {
+    const unsigned m = *novl;
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x)
+      rod_pairs_of_entry<true>(A, ovl[q], cnt, off, out, stage, ovl, novl);
+  }
+}
+
+// ---- shells: the pair tests spread evenly over the threads ----------------
+// An entry's partner range (the swept part of its run: every triangle entry
+// of its cell for a vertex entry, every later edge entry for an edge entry,
+// up to the first partner whose x level lies above its own upper bound) has
+// any length from 0 to thousands, so one thread per entry leaves most lanes
+// of a warp idle.  Here the ranges are laid end to end: entry i owns the test
+// slots [toff[i], toff[i+1]) (an exclusive scan of the lengths), slot f of
+// entry i tests partner j = j0[i] + (f - toff[i]).  A warp takes 32 x
+// FLAT_STEPS consecutive slots, lane l the slots with f = l (mod 32), so each
+// step tests 32 neighbouring partners (coalesced box loads) and its ballot is
+// one word of the hit bits.  The pairs come out in the same order as before
+// (entry by entry, partners ascending), so the candidate array is unchanged.
+constexpr int FLAT_STEPS = 32;
+
+// entry i's first partner j0[i] and the length of its swept range (len[ne] = 0)
+__global__ void k_flat_ranges(PairArgs A, uint32_t* __restrict__ len, uint32_t* __restrict__ j0s) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > A.ne) return;
+  if (i == A.ne) {
+    len[i] = 0;
+    return;
+  }
+  const EntryRange R = entry_range(A, i);
+  if (R.none) {
+    len[i] = 0;
+    j0s[i] = 0;
+    return;
+  }
+  const uint64_t kc = A.ekey[i] >> A.shift;
+  const Grid G = A.grids[kc >> 30];
+  const int cxi = morton_x((uint32_t)(kc & 0x3fffffffull));
+  const uint32_t xhi = x_level(A.ebox[2 * (size_t)i + 1].x, G, cxi);
+  // partners of one cell and group are sorted by x level (the key's low bits)
+  int lo = R.j0, hi = R.j1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((uint32_t)(A.ekey[mid] & (uint64_t)(XQ_LEVELS - 1)) <= xhi) lo = mid + 1;
+    else hi = mid;
+  }
+  len[i] = (uint32_t)(lo - R.j0);
+  j0s[i] = (uint32_t)R.j0;
+}
+
+struct FlatEntry {
+  int pv[3];
+  float4 plo, phi;
+  uint32_t P, cell;
+  Grid G;
+};
+
+__device__ __forceinline__ void flat_load(const PairArgs& A, int64_t i, FlatEntry& E) {
+  E.P = A.eval[i];
+  prim_verts(A.t, (int)E.P, E.pv);
+  E.plo = A.ebox[2 * (size_t)i];
+  E.phi = A.ebox[2 * (size_t)i + 1];
+  const uint64_t kc = A.ekey[i] >> A.shift;
+  E.cell = (uint32_t)(kc & 0x3fffffffull);
+  E.G = A.grids[kc >> 30];
+}
+
+// the test of the per-entry pass: FP32 boxes overlap, the overlap's low
+// corner lies in this cell (each pair is reported by one cell), the two share
+// no vertex; the FP64 boxes decide where the FP32 margins cannot
+__device__ __forceinline__ bool flat_test(const PairArgs& A, const FlatEntry& E, int j, uint32_t& n32,
+                                          uint32_t& n64) {
+  const float4 qlo = A.ebox[2 * (size_t)j], qhi = A.ebox[2 * (size_t)j + 1];
+  if (!(E.plo.x <= qhi.x && qlo.x <= E.phi.x && E.plo.y <= qhi.y && qlo.y <= E.phi.y && E.plo.z <= qhi.z &&
+        qlo.z <= E.phi.z))
+    return false;
+  const Grid& G = E.G;
+  const uint32_t hc = morton(cell_of(fmaxf(E.plo.x, qlo.x), G.ox, G.inv, G.dx),
+                             cell_of(fmaxf(E.plo.y, qlo.y), G.oy, G.inv, G.dy),
+                             cell_of(fmaxf(E.plo.z, qlo.z), G.oz, G.inv, G.dz));
+  if (hc != E.cell) return false;
+  const uint32_t Q = A.eval[j];
+  int qv[3];
+  prim_verts(A.t, (int)Q, qv);
+  bool inc = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) inc |= (E.pv[a] >= 0 && E.pv[a] == qv[b]);
+  if (inc) return false;
+  const bool sure = nextup(E.plo.x) <= nextdn(qhi.x) && nextup(qlo.x) <= nextdn(E.phi.x) &&
+                    nextup(E.plo.y) <= nextdn(qhi.y) && nextup(qlo.y) <= nextdn(E.phi.y) &&
+                    nextup(E.plo.z) <= nextdn(qhi.z) && nextup(qlo.z) <= nextdn(E.phi.z);
+  ++n32;
+  if (sure) return true;
+  ++n64;
+  const double* b1 = A.box64 + (size_t)E.P * 6;
+  const double* b2 = A.box64 + (size_t)Q * 6;
+  bool acc = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) acc = acc && (b1[k] <= b2[3 + k]) && (b2[k] <= b1[3 + k]);
+  return acc;
+}
+
+// hit bits of slots [0, T): word w holds slots 32 w .. 32 w + 31 (grid-stride
+// over chunks of FLAT_STEPS words, one warp per chunk)
+__global__ void __launch_bounds__(256) k_pairs_flat(PairArgs A, const uint64_t* __restrict__ toff,
+                                                    const uint32_t* __restrict__ j0s, uint64_t T,
+                                                    uint32_t* __restrict__ bits) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const uint64_t chunk = 32ull * FLAT_STEPS;
+  const int64_t nchunks = (int64_t)((T + chunk - 1) / chunk);
+  uint32_t n32 = 0, n64 = 0;
+  for (int64_t ch = warp; ch < nchunks; ch += nwarps) {
+    const uint64_t base = (uint64_t)ch * chunk;
+    // the entry of this lane's first slot: the last i with toff[i] <= f
+    // (entries with empty ranges share their toff with the next one)
+    uint64_t f = base + (uint64_t)lane;
+    int64_t i = 0;
+    {
+      int64_t lo = 0, hi = A.ne + 1;
+      const uint64_t fs = f < T ? f : T - 1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (toff[mid] <= fs) lo = mid + 1;
+        else hi = mid;
+      }
+      i = lo - 1;
+    }
+    FlatEntry E;
+    flat_load(A, i, E);
+    uint64_t e_end = toff[i + 1], e_beg = toff[i];
+    uint32_t j0 = j0s[i];
+    for (int b = 0; b < FLAT_STEPS; ++b, f += 32) {
+      bool acc = false;
+      if (f < T) {
+        if (f >= e_end) {
+          do {
+            ++i;
+            e_beg = e_end;
+            e_end = toff[i + 1];
+          } while (f >= e_end);
+          flat_load(A, i, E);
+          j0 = j0s[i];
+        }
+        acc = flat_test(A, E, (int)(j0 + (uint32_t)(f - e_beg)), n32, n64);
+      }
+      const unsigned word = __ballot_sync(0xffffffffu, acc);
+      const uint64_t wd = (base >> 5) + (uint64_t)b;
+      if (lane == 0 && 32ull * wd < T) bits[wd] = word;
+    }
+  }
+  if (A.fpstat) {
+    const unsigned a32 = __reduce_add_sync(0xffffffffu, n32), a64 = __reduce_add_sync(0xffffffffu, n64);
+    if (lane == 0) {
+      if (a32) atomicAdd(&A.fpstat[0], (unsigned long long)a32);
+      if (a64) atomicAdd(&A.fpstat[1], (unsigned long long)a64);
     }
   }
 }
 
-
-// count pass (FILL = false, one thread per entry): cnt[i] = number of pairs
-// entry i reports.  Rod cells (RR): the first PAIR_STAGE of them are staged
-// (element-major, stage[k * ne + i]) and entries with more are listed in
-// ovl; k_pairs_copy moves the staged keys.  Shell cells: the outcome of the
-// first 32 mask_words partner positions is kept as bits, entries with pairs
-// past them are listed in ovl, and k_pairs_emit writes the pairs of the bits.
-// The fill pass (FILL = true) then runs over the listed entries only, writing
-// the remaining pairs at their place.
-template <bool FILL, bool RR>
-__global__ void __launch_bounds__(CB_THREADS) k_pairs(PairArgs A, uint32_t* __restrict__ cnt,
-                                                      const uint32_t* __restrict__ off, uint64_t* __restrict__ out,
-                                                      uint64_t* __restrict__ stage, uint32_t* __restrict__ ovl,
-                                                      unsigned int* __restrict__ novl) {
-  if (!FILL) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < A.ne) pairs_of_entry<FILL, RR>(A, i, cnt, off, out, stage, ovl, novl);
-  } else {
-    const unsigned m = *novl;
-    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x)
-      pairs_of_entry<true, RR>(A, ovl[q], cnt, off, out, stage, ovl, novl);
-  }
+// the hit bits of slots [f0, f1) in word wd
+__device__ __forceinline__ uint32_t flat_word(const uint32_t* __restrict__ bits, uint64_t wd, uint64_t f0,
+                                              uint64_t f1) {
+  uint32_t word = bits[wd];
+  const uint64_t w0 = wd << 5;
+  if (f0 > w0) word &= 0xffffffffu << (uint32_t)(f0 - w0);
+  if (f1 < w0 + 32) word &= 0xffffffffu >> (uint32_t)(w0 + 32 - f1);
+  return word;
 }
 
-// Shell cells: the pairs of the count pass's partner bits, at the start of
-// each entry's range in partner order (the order the tests found them in)
-__global__ void __launch_bounds__(CB_THREADS) k_pairs_emit(PairArgs A, const uint32_t* __restrict__ cnt,
-                                                           const uint32_t* __restrict__ off,
-                                                           uint64_t* __restrict__ out) {
+// pairs per entry: the hits of its slots
+__global__ void k_flat_count(int64_t ne, const uint64_t* __restrict__ toff, const uint32_t* __restrict__ bits,
+                             uint32_t* __restrict__ cnt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.ne) return;
-  const uint32_t c_end = cnt[i];
-  if (c_end == 0) return;
-  const EntryRange R = entry_range(A, i);
-  const int nb = min((int)A.pend[i] - R.j0, 32 * A.mask_words);
-  const size_t o = off[i];
-  uint32_t count = 0;
-  for (int w = 0; 32 * w < nb; ++w) {
-    uint32_t word = A.mask[(size_t)w * A.ne + i];
-    const int jw = R.j0 + 32 * w;
-    // four bits per round, their partner loads issued before any store
+  if (i >= ne) return;
+  const uint64_t f0 = toff[i], f1 = toff[i + 1];
+  uint32_t c = 0;
+  if (f1 > f0)
+    for (uint64_t wd = f0 >> 5; wd <= (f1 - 1) >> 5; ++wd) c += __popc(flat_word(bits, wd, f0, f1));
+  cnt[i] = c;
+}
+
+// entry i's pairs at off[i], partners ascending (edge-edge keys take the
+// lower edge first: swept cells order edges by x, not by id)
+__global__ void k_flat_emit(PairArgs A, const uint64_t* __restrict__ toff, const uint32_t* __restrict__ j0s,
+                            const uint32_t* __restrict__ bits, const uint32_t* __restrict__ cnt,
+                            const uint32_t* __restrict__ off, uint64_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.ne || cnt[i] == 0) return;
+  const uint32_t P = A.eval[i];
+  const Topo& t = A.t;
+  uint32_t type, ibase = 0, jbase = 0;
+  if (P < (uint32_t)t.n) {
+    type = CB_KEY_PT;
+    jbase = (uint32_t)t.n;
+  } else {
+    type = CB_KEY_EE;
+    ibase = jbase = (uint32_t)(t.n + t.T);
+  }
+  const uint64_t f0 = toff[i], f1 = toff[i + 1];
+  const uint32_t j0 = j0s[i];
+  size_t o = off[i];
+  for (uint64_t wd = f0 >> 5; wd <= (f1 - 1) >> 5; ++wd) {
+    uint32_t word = flat_word(bits, wd, f0, f1);
     while (word) {
-      int jb[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        jb[u] = word ? jw + __ffs(word) - 1 : -1;
-        word &= word - 1;
-      }
-      uint32_t Q[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) Q[u] = jb[u] >= 0 ? A.eval[jb[u]] : 0u;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (jb[u] < 0) break;
-        if (count < c_end) {
-          // edge-edge keys take the lower edge first (swept cells order edges by x)
-          const bool swap = R.type == CB_KEY_EE && Q[u] < R.P;
-          out[o + count] = pair_key(A, R.type, (swap ? Q[u] : R.P) - R.ibase, (swap ? R.P : Q[u]) - R.jbase);
-        }
-        ++count;
-      }
+      const uint32_t b = (uint32_t)__ffs(word) - 1u;
+      word &= word - 1u;
+      const uint32_t Q = A.eval[j0 + (uint32_t)((wd << 5) + b - f0)];
+      const bool swap = type == CB_KEY_EE && Q < P;
+      out[o++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
     }
   }
 }
@@ -797,11 +891,6 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   A.ne = ne;
   A.ekey = ekey;
   A.shift = shift;
-  A.pend = nullptr;
-  if (sweep) {
-    CB_TRY(buf_ensure(w.pair_end, sizeof(uint32_t) * (size_t)ne, st));
-    A.pend = bp<uint32_t>(w.pair_end);
-  }
   A.eval = eval;
   A.run_id = bp<uint32_t>(w.run_id);
   A.run_start = bp<uint32_t>(w.run_start);
@@ -824,60 +913,68 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   // keys are final from the count pass on: canonical straight out, compact for the sort
   A.canonical = !sort_out;
   unsigned int* novl = (unsigned int*)(scalars(s) + SC_NOVF);
-  CB_TRY(buf_ensure(w.stage, rods ? sizeof(uint64_t) * PAIR_STAGE * (size_t)ne
-                                   : sizeof(uint32_t) * (size_t)w.mask_words * (size_t)ne, st));
-  CB_TRY(buf_ensure(w.ovl, sizeof(uint32_t) * (size_t)ne, st));
-  CB_CUDA(cudaMemsetAsync(novl, 0, sizeof(unsigned int), st));
-  A.mask = rods ? nullptr : bp<uint32_t>(w.stage);
-  A.mask_words = w.mask_words;
-  // the longest partner range of this call, for the next call's mask_words:
-  // counted on the device, copied to pinned host memory with the pair count
-  const int wi = &w == &s->bwc ? 1 : 0;
-  unsigned int* maxr = (unsigned int*)(scalars(s) + SC_MAXR) + wi;
-  A.maxr = rods ? nullptr : maxr;
-  if (!rods) CB_CUDA(cudaMemsetAsync(maxr, 0, sizeof(unsigned int), st));
-  auto pairs = [&](bool fill, uint64_t* o) -> cb_status {
-    uint32_t* c = bp<uint32_t>(w.pair_cnt);
-    const uint32_t* f = fill ? bp<uint32_t>(w.pair_off) : nullptr;
-    uint64_t* sg = bp<uint64_t>(w.stage);
-    uint32_t* ov = bp<uint32_t>(w.ovl);
-    if (fill) {
-      if (rods) {
-        k_pairs_copy<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, c, f, sg, o);
-        const int g = (int)std::min<int64_t>(cb_grid(ne, pb), (int64_t)s->n_sms * 8);
-        k_pairs<true, true><<<g, pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
-      } else {
-        k_pairs_emit<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, c, f, o);
-        const int g = (int)std::min<int64_t>(cb_grid(ne, pb), (int64_t)s->n_sms * 8);
-        k_pairs<true, false><<<g, pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
-      }
+  uint32_t* c = bp<uint32_t>(w.pair_cnt);
+  uint64_t flat_t = 0;
+  if (rods) {
+    CB_TRY(buf_ensure(w.stage, sizeof(uint64_t) * PAIR_STAGE * (size_t)ne, st));
+    CB_TRY(buf_ensure(w.ovl, sizeof(uint32_t) * (size_t)ne, st));
+    CB_CUDA(cudaMemsetAsync(novl, 0, sizeof(unsigned int), st));
+    k_rod_pairs<false><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, nullptr, nullptr, bp<uint64_t>(w.stage),
+                                                                bp<uint32_t>(w.ovl), novl);
+  } else {
+    // shells: the swept ranges laid end to end, tested evenly, counted per entry
+    CB_TRY(buf_ensure(w.flat_len, sizeof(uint32_t) * ((size_t)ne + 1), st));
+    CB_TRY(buf_ensure(w.flat_off, sizeof(uint64_t) * ((size_t)ne + 1), st));
+    CB_TRY(buf_ensure(w.flat_j0, sizeof(uint32_t) * (size_t)ne, st));
+    k_flat_ranges<<<cb_grid(ne + 1), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint32_t>(w.flat_len),
+                                                                    bp<uint32_t>(w.flat_j0));
+    cbp::exclusive_scan<uint32_t, uint64_t>(bp<uint32_t>(w.flat_len), bp<uint64_t>(w.flat_off), ne + 1,
+                                            bp<uint64_t>(w.scan_tmp), scalars(s) + SC_COUNT0, st);
+    CB_CUDA(cudaGetLastError());
+    CB_TRY(read_scalars(s, SC_COUNT0, 1, &flat_t, st));
+    if (flat_t > 0) {
+      CB_TRY(buf_ensure(w.flat_bits, sizeof(uint32_t) * (size_t)((flat_t + 31) / 32), st));
+      const int64_t chunks = (int64_t)((flat_t + 32ull * FLAT_STEPS - 1) / (32ull * FLAT_STEPS));
+      const int64_t g = std::min<int64_t>((chunks + 7) / 8, (int64_t)s->n_sms * 8);
+      k_pairs_flat<<<(int)g, 256, 0, cb_count(st)>>>(A, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_j0), flat_t,
+                                                    bp<uint32_t>(w.flat_bits));
+      k_flat_count<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, bp<uint64_t>(w.flat_off),
+                                                                bp<uint32_t>(w.flat_bits), c);
     } else {
-      if (rods) k_pairs<false, true><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
-      else k_pairs<false, false><<<cb_grid(ne, pb), pb, 0, cb_count(st)>>>(A, c, f, o, sg, ov, novl);
+      CB_CUDA(cudaMemsetAsync(c, 0, sizeof(uint32_t) * (size_t)ne, st));
+    }
+  }
+  // the fill: rods move their staged keys and re-test the entries with more;
+  // shells write the pairs of their hit bits
+  auto pairs = [&](uint64_t* o) -> cb_status {
+    const uint32_t* f = bp<uint32_t>(w.pair_off);
+    if (rods) {
+      uint64_t* sg = bp<uint64_t>(w.stage);
+      k_pairs_copy<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, c, f, sg, o);
+      const int g = (int)std::min<int64_t>(cb_grid(ne, pb), (int64_t)s->n_sms * 8);
+      k_rod_pairs<true><<<g, pb, 0, cb_count(st)>>>(A, c, f, o, sg, bp<uint32_t>(w.ovl), novl);
+    } else if (flat_t > 0) {
+      k_flat_emit<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_j0),
+                                                               bp<uint32_t>(w.flat_bits), c, f, o);
     }
     return CB_OK;
   };
-  CB_TRY(pairs(false, nullptr));
-  cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.pair_cnt), bp<uint32_t>(w.pair_off), ne,
-                                          bp<uint32_t>(w.scan_tmp), tot_dev, st);
+  cbp::exclusive_scan<uint32_t, uint32_t>(c, bp<uint32_t>(w.pair_off), ne, bp<uint32_t>(w.scan_tmp), tot_dev, st);
   CB_CUDA(cudaGetLastError());
-  uint32_t* hmaxr = (uint32_t*)(s->h_pinned + H_PINNED_MAXR) + wi;
-  if (!rods) CB_CUDA(cudaMemcpyAsync(hmaxr, maxr, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   uint64_t hnc;
-  CB_TRY(read_scalars(s, SC_COUNT0, 1, &hnc, st));  // the copy above is complete after this sync
-  if (!rods) w.mask_words = std::min(PAIR_MASK_WORDS_MAX, std::max(1, (int)((*hmaxr + 31) / 32)));
+  CB_TRY(read_scalars(s, SC_COUNT0, 1, &hnc, st));
   const int64_t nc = (uint32_t)hnc;
   *n_out = nc;
   if (nc == 0) return CB_OK;
   if (!sort_out) {
     // canonical keys straight from the fill pass, in hash-cell order
     CB_TRY(buf_ensure(out, sizeof(uint64_t) * (size_t)nc, st));
-    CB_TRY(pairs(true, bp<uint64_t>(out)));
+    CB_TRY(pairs(bp<uint64_t>(out)));
     CB_CUDA(cudaGetLastError());
     return CB_OK;
   }
   for (int b = 0; b < 2; ++b) CB_TRY(buf_ensure(w.ckey[b], sizeof(uint64_t) * (size_t)nc, st));
-  CB_TRY(pairs(true, bp<uint64_t>(w.ckey[0])));
+  CB_TRY(pairs(bp<uint64_t>(w.ckey[0])));
   const int cbits = s->bits_i + s->bits_j + (s->kind == CB_SHELL ? 2 : 0);
   CB_TRY(buf_ensure(w.hist, sizeof(uint32_t) * (size_t)cbp::radix_hist_elems(nc), st));
   CB_TRY(buf_ensure(w.scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(cbp::radix_hist_elems(nc)) + 8),

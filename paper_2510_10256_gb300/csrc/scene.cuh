@@ -79,7 +79,6 @@ struct Grid {
 // Workspace of one broad phase (static or swept) -- reused between calls.
 struct BroadWork {
   float cell_factor = 1.0f;  // hash cell edge = factor x mean primitive box extent (tuning knob)
-  int mask_words = 16;       // shells: words of partner bits per entry (from the last call's longest range)
   int pair_block = CB_THREADS;  // threads per block of the pair enumeration (tuning knob)
   DevBuf box32;       // float4 lo, float4 hi per primitive
   DevBuf box64;       // double lo[3], hi[3] per primitive
@@ -97,11 +96,14 @@ struct BroadWork {
   DevBuf run_start;   // uint32 per run (+1)
   DevBuf pair_cnt;    // uint32 per entry
   DevBuf pair_off;    // uint32 per entry (+1)
-  DevBuf pair_end;    // shells: uint32 per entry, the end of the partner positions its sweep tested
   DevBuf ebox;        // float4 lo, float4 hi per entry (boxes gathered into entry order)
   DevBuf ckey[2];     // uint64 compact candidate keys (ping-pong)
   DevBuf stage;       // uint64 [PAIR_STAGE][entries]: the count pass's first pairs of each entry
   DevBuf ovl;         // uint32 entries with more pairs than the stage holds
+  DevBuf flat_len;    // shells: uint32 per entry (+1), the length of its swept partner range
+  DevBuf flat_off;    // shells: uint64 per entry (+1), its first test slot (exclusive scan of flat_len)
+  DevBuf flat_j0;     // shells: uint32 per entry, its first partner
+  DevBuf flat_bits;   // shells: one hit bit per test slot
   DevBuf scan_tmp;
   DevBuf hist;
 };
@@ -210,7 +212,7 @@ struct cb_scene {
   DevBuf hist;
   DevBuf dev_scalars;   // misc device scalars (counters, energy, alpha bits, status)
 
-  uint64_t* h_pinned = nullptr;  // pinned host scratch (64 slots; [H_PINNED_MAXR]: the broad phases' ranges)
+  uint64_t* h_pinned = nullptr;  // pinned host scratch (64 slots)
   int32_t status_host = 0;
 
   bool timing = false;
@@ -245,13 +247,12 @@ enum {
   SC_KSPLIT = 16,       // two uint32 counters: face / line-line pairs, the other active pairs
   SC_NOVF = 17,         // broad phase: entries whose pairs overflow the stage
   SC_NBK = 18,          // BSR pattern: keys left after the per-run sets of k_block_keys
-  SC_MAXR = 19,         // broad phase, shells: two uint32 -- longest partner range (static, swept)
+  SC_SPARE = 19,        // unused
   SC_NMOLL = 20,        // barrier_eval: mollified edge-edge pairs
   SC_N = 21
 };
-// slot of the pinned host scratch that receives the SC_MAXR pair (read_scalars uses the first SC_N)
-constexpr int H_PINNED_MAXR = 62;
-static_assert(SC_N <= H_PINNED_MAXR, "pinned scratch slots overlap");
+// read_scalars stages up to SC_N scalars through the pinned host scratch
+static_assert(SC_N <= 64, "the scalars must fit the pinned scratch");
 
 static inline uint64_t* scalars(cb_scene* s) { return (uint64_t*)s->dev_scalars.p; }
 
