@@ -161,9 +161,9 @@ typedef struct {
   int64_t n_hess_face;        /* last barrier_eval: active face / line-line pairs (9x9 projection) */
   int64_t n_hess_pe_frame;    /* ... point-edge pairs projected in their own frame (3x3 + 2x2) */
   int64_t n_hess_pe;          /* ... point-edge pairs on the generic 6x6 projection */
-  int64_t n_pair_overflow;    /* last broad phase (ccd_step's, once a pass ran it): entries whose pairs
-                                 went past what the count pass keeps (rods: 32 staged keys; shells: the
-                                 partner bits of the positions the count pass keeps), re-tested by the fill pass */
+  int64_t n_pair_overflow;    /* last broad phase of a rod scene (ccd_step's, once a pass ran it): entries
+                                 with more pairs than the 32 keys the count pass stages, re-tested by the fill
+                                 pass (shell scenes keep one hit bit per test and never re-test: 0) */
   int64_t n_mollified;        /* last barrier_eval with CB_EE_MOLLIFIER: edge-edge pairs below their threshold */
   int64_t n_stencil_dropped;  /* last contact_filter with CB_PER_STENCIL: filtered broad-phase pairs outside
                                  their own width, removed from the candidates */
