@@ -572,9 +572,15 @@ __global__ void __launch_bounds__(CB_THREADS) k_rod_pairs(PairArgs A, uint32_t* 
 // one word of the hit bits.  The pairs come out in the same order as before
 // (entry by entry, partners ascending), so the candidate array is unchanged.
 constexpr int FLAT_STEPS = 32;
+// Entries with fewer partners than this are tested by one thread each (one
+// hit word per entry); only longer ranges are laid end to end, so a lane of
+// the end-to-end pass moves to a new entry at most once per step.
+constexpr int FLAT_MIN = 32;
 
-// entry i's first partner j0[i] and the length of its swept range (len[ne] = 0)
-__global__ void k_flat_ranges(PairArgs A, uint32_t* __restrict__ len, uint32_t* __restrict__ j0s) {
+// entry i's first partner j0[i] and the length of its swept range: short
+// ranges in slen[i] (len[i] = 0), long ones in len[i] (slen[i] = 0); len[ne] = 0
+__global__ void k_flat_ranges(PairArgs A, uint32_t* __restrict__ len, uint8_t* __restrict__ slen,
+                              uint32_t* __restrict__ j0s) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i > A.ne) return;
   if (i == A.ne) {
@@ -584,6 +590,7 @@ __global__ void k_flat_ranges(PairArgs A, uint32_t* __restrict__ len, uint32_t* 
   const EntryRange R = entry_range(A, i);
   if (R.none) {
     len[i] = 0;
+    slen[i] = 0;
     j0s[i] = 0;
     return;
   }
@@ -598,7 +605,9 @@ __global__ void k_flat_ranges(PairArgs A, uint32_t* __restrict__ len, uint32_t* 
     if ((uint32_t)(A.ekey[mid] & (uint64_t)(XQ_LEVELS - 1)) <= xhi) lo = mid + 1;
     else hi = mid;
   }
-  len[i] = (uint32_t)(lo - R.j0);
+  const uint32_t n = (uint32_t)(lo - R.j0);
+  len[i] = n >= (uint32_t)FLAT_MIN ? n : 0u;
+  slen[i] = n >= (uint32_t)FLAT_MIN ? (uint8_t)0 : (uint8_t)n;
   j0s[i] = (uint32_t)R.j0;
 }
 
@@ -654,6 +663,31 @@ __device__ __forceinline__ bool flat_test(const PairArgs& A, const FlatEntry& E,
 #pragma unroll
   for (int k = 0; k < 3; ++k) acc = acc && (b1[k] <= b2[3 + k]) && (b2[k] <= b1[3 + k]);
   return acc;
+}
+
+// entries with short ranges: one thread each, hit bit b for partner j0 + b
+__global__ void k_pairs_short(PairArgs A, const uint8_t* __restrict__ slen, const uint32_t* __restrict__ j0s,
+                              uint32_t* __restrict__ sbits) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t n32 = 0, n64 = 0;
+  if (i < A.ne) {
+    const int n = slen[i];
+    uint32_t word = 0;
+    if (n > 0) {
+      FlatEntry E;
+      flat_load(A, i, E);
+      const int j0 = (int)j0s[i];
+      for (int b = 0; b < n; ++b) word |= (uint32_t)flat_test(A, E, j0 + b, n32, n64) << b;
+    }
+    sbits[i] = word;
+  }
+  if (A.fpstat) {
+    const unsigned a32 = __reduce_add_sync(0xffffffffu, n32), a64 = __reduce_add_sync(0xffffffffu, n64);
+    if ((threadIdx.x & 31) == 0) {
+      if (a32) atomicAdd(&A.fpstat[0], (unsigned long long)a32);
+      if (a64) atomicAdd(&A.fpstat[1], (unsigned long long)a64);
+    }
+  }
 }
 
 // hit bits of slots [0, T): word w holds slots 32 w .. 32 w + 31 (grid-stride
@@ -725,13 +759,13 @@ __device__ __forceinline__ uint32_t flat_word(const uint32_t* __restrict__ bits,
   return word;
 }
 
-// pairs per entry: the hits of its slots
+// pairs per entry: the hits of its short word or of its slots
 __global__ void k_flat_count(int64_t ne, const uint64_t* __restrict__ toff, const uint32_t* __restrict__ bits,
-                             uint32_t* __restrict__ cnt) {
+                             const uint32_t* __restrict__ sbits, uint32_t* __restrict__ cnt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ne) return;
   const uint64_t f0 = toff[i], f1 = toff[i + 1];
-  uint32_t c = 0;
+  uint32_t c = __popc(sbits[i]);
   if (f1 > f0)
     for (uint64_t wd = f0 >> 5; wd <= (f1 - 1) >> 5; ++wd) c += __popc(flat_word(bits, wd, f0, f1));
   cnt[i] = c;
@@ -740,8 +774,9 @@ __global__ void k_flat_count(int64_t ne, const uint64_t* __restrict__ toff, cons
 // entry i's pairs at off[i], partners ascending (edge-edge keys take the
 // lower edge first: swept cells order edges by x, not by id)
 __global__ void k_flat_emit(PairArgs A, const uint64_t* __restrict__ toff, const uint32_t* __restrict__ j0s,
-                            const uint32_t* __restrict__ bits, const uint32_t* __restrict__ cnt,
-                            const uint32_t* __restrict__ off, uint64_t* __restrict__ out) {
+                            const uint32_t* __restrict__ bits, const uint32_t* __restrict__ sbits,
+                            const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off,
+                            uint64_t* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.ne || cnt[i] == 0) return;
   const uint32_t P = A.eval[i];
@@ -757,14 +792,23 @@ __global__ void k_flat_emit(PairArgs A, const uint64_t* __restrict__ toff, const
   const uint64_t f0 = toff[i], f1 = toff[i + 1];
   const uint32_t j0 = j0s[i];
   size_t o = off[i];
-  for (uint64_t wd = f0 >> 5; wd <= (f1 - 1) >> 5; ++wd) {
-    uint32_t word = flat_word(bits, wd, f0, f1);
-    while (word) {
-      const uint32_t b = (uint32_t)__ffs(word) - 1u;
-      word &= word - 1u;
-      const uint32_t Q = A.eval[j0 + (uint32_t)((wd << 5) + b - f0)];
-      const bool swap = type == CB_KEY_EE && Q < P;
-      out[o++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
+  for (uint32_t word = sbits[i]; word;) {  // a short range
+    const uint32_t b = (uint32_t)__ffs(word) - 1u;
+    word &= word - 1u;
+    const uint32_t Q = A.eval[j0 + b];
+    const bool swap = type == CB_KEY_EE && Q < P;
+    out[o++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
+  }
+  if (f1 > f0) {
+    for (uint64_t wd = f0 >> 5; wd <= (f1 - 1) >> 5; ++wd) {
+      uint32_t word = flat_word(bits, wd, f0, f1);
+      while (word) {
+        const uint32_t b = (uint32_t)__ffs(word) - 1u;
+        word &= word - 1u;
+        const uint32_t Q = A.eval[j0 + (uint32_t)((wd << 5) + b - f0)];
+        const bool swap = type == CB_KEY_EE && Q < P;
+        out[o++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
+      }
     }
   }
 }
@@ -926,23 +970,25 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     CB_TRY(buf_ensure(w.flat_len, sizeof(uint32_t) * ((size_t)ne + 1), st));
     CB_TRY(buf_ensure(w.flat_off, sizeof(uint64_t) * ((size_t)ne + 1), st));
     CB_TRY(buf_ensure(w.flat_j0, sizeof(uint32_t) * (size_t)ne, st));
+    CB_TRY(buf_ensure(w.flat_slen, (size_t)ne, st));
+    CB_TRY(buf_ensure(w.flat_sbits, sizeof(uint32_t) * (size_t)ne, st));
     k_flat_ranges<<<cb_grid(ne + 1), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint32_t>(w.flat_len),
-                                                                    bp<uint32_t>(w.flat_j0));
+                                                                    bp<uint8_t>(w.flat_slen), bp<uint32_t>(w.flat_j0));
+    k_pairs_short<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint8_t>(w.flat_slen), bp<uint32_t>(w.flat_j0),
+                                                               bp<uint32_t>(w.flat_sbits));
     cbp::exclusive_scan<uint32_t, uint64_t>(bp<uint32_t>(w.flat_len), bp<uint64_t>(w.flat_off), ne + 1,
                                             bp<uint64_t>(w.scan_tmp), scalars(s) + SC_COUNT0, st);
     CB_CUDA(cudaGetLastError());
     CB_TRY(read_scalars(s, SC_COUNT0, 1, &flat_t, st));
+    CB_TRY(buf_ensure(w.flat_bits, sizeof(uint32_t) * (size_t)std::max<uint64_t>(1, (flat_t + 31) / 32), st));
     if (flat_t > 0) {
-      CB_TRY(buf_ensure(w.flat_bits, sizeof(uint32_t) * (size_t)((flat_t + 31) / 32), st));
       const int64_t chunks = (int64_t)((flat_t + 32ull * FLAT_STEPS - 1) / (32ull * FLAT_STEPS));
       const int64_t g = std::min<int64_t>((chunks + 7) / 8, (int64_t)s->n_sms * 8);
       k_pairs_flat<<<(int)g, 256, 0, cb_count(st)>>>(A, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_j0), flat_t,
                                                     bp<uint32_t>(w.flat_bits));
-      k_flat_count<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, bp<uint64_t>(w.flat_off),
-                                                                bp<uint32_t>(w.flat_bits), c);
-    } else {
-      CB_CUDA(cudaMemsetAsync(c, 0, sizeof(uint32_t) * (size_t)ne, st));
     }
+    k_flat_count<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_bits),
+                                                              bp<uint32_t>(w.flat_sbits), c);
   }
   // the fill: rods move their staged keys and re-test the entries with more;
   // shells write the pairs of their hit bits
@@ -953,9 +999,10 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
       k_pairs_copy<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, c, f, sg, o);
       const int g = (int)std::min<int64_t>(cb_grid(ne, pb), (int64_t)s->n_sms * 8);
       k_rod_pairs<true><<<g, pb, 0, cb_count(st)>>>(A, c, f, o, sg, bp<uint32_t>(w.ovl), novl);
-    } else if (flat_t > 0) {
+    } else {
       k_flat_emit<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_j0),
-                                                               bp<uint32_t>(w.flat_bits), c, f, o);
+                                                               bp<uint32_t>(w.flat_bits), bp<uint32_t>(w.flat_sbits),
+                                                               c, f, o);
     }
     return CB_OK;
   };

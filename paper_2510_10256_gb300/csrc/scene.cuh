@@ -104,6 +104,8 @@ struct BroadWork {
   DevBuf flat_off;    // shells: uint64 per entry (+1), its first test slot (exclusive scan of flat_len)
   DevBuf flat_j0;     // shells: uint32 per entry, its first partner
   DevBuf flat_bits;   // shells: one hit bit per test slot
+  DevBuf flat_slen;   // shells: uint8 per entry, the length of a short range (tested per entry)
+  DevBuf flat_sbits;  // shells: uint32 per entry, the hits of a short range
   DevBuf scan_tmp;
   DevBuf hist;
 };
