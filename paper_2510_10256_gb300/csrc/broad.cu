@@ -578,18 +578,19 @@ constexpr int FLAT_STEPS = 32;
 constexpr int FLAT_MIN = 32;
 
 // entry i's first partner j0[i] and the length of its swept range: short
-// ranges in slen[i] (len[i] = 0), long ones in len[i] (slen[i] = 0); len[ne] = 0
-__global__ void k_flat_ranges(PairArgs A, uint32_t* __restrict__ len, uint8_t* __restrict__ slen,
-                              uint32_t* __restrict__ j0s) {
+// ranges in slen[i], long ones in len[i] with lflag[i] = 1 (lflag[ne] = 0)
+__global__ void k_flat_ranges(PairArgs A, uint32_t* __restrict__ len, uint32_t* __restrict__ lflag,
+                              uint8_t* __restrict__ slen, uint32_t* __restrict__ j0s) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i > A.ne) return;
   if (i == A.ne) {
-    len[i] = 0;
+    lflag[i] = 0;
     return;
   }
   const EntryRange R = entry_range(A, i);
   if (R.none) {
     len[i] = 0;
+    lflag[i] = 0;
     slen[i] = 0;
     j0s[i] = 0;
     return;
@@ -606,9 +607,21 @@ __global__ void k_flat_ranges(PairArgs A, uint32_t* __restrict__ len, uint8_t* _
     else hi = mid;
   }
   const uint32_t n = (uint32_t)(lo - R.j0);
-  len[i] = n >= (uint32_t)FLAT_MIN ? n : 0u;
-  slen[i] = n >= (uint32_t)FLAT_MIN ? (uint8_t)0 : (uint8_t)n;
+  const bool lng = n >= (uint32_t)FLAT_MIN;
+  len[i] = lng ? n : 0u;
+  lflag[i] = lng ? 1u : 0u;
+  slen[i] = lng ? (uint8_t)0 : (uint8_t)n;
   j0s[i] = (uint32_t)R.j0;
+}
+
+// the long entries in entry order: lidx[k] = i, llen[k] = len[i] (k = lpos[i])
+__global__ void k_flat_compact(int64_t ne, const uint32_t* __restrict__ lflag, const uint32_t* __restrict__ lpos,
+                               const uint32_t* __restrict__ len, uint32_t* __restrict__ lidx,
+                               uint32_t* __restrict__ llen) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ne || !lflag[i]) return;
+  lidx[lpos[i]] = (uint32_t)i;
+  llen[lpos[i]] = len[i];
 }
 
 struct FlatEntry {
@@ -693,6 +706,7 @@ __global__ void k_pairs_short(PairArgs A, const uint8_t* __restrict__ slen, cons
 // hit bits of slots [0, T): word w holds slots 32 w .. 32 w + 31 (grid-stride
 // over chunks of FLAT_STEPS words, one warp per chunk)
 __global__ void __launch_bounds__(256) k_pairs_flat(PairArgs A, const uint64_t* __restrict__ toff,
+                                                    const uint32_t* __restrict__ lidx,
                                                     const uint32_t* __restrict__ j0s, uint64_t T,
                                                     uint32_t* __restrict__ bits) {
   const int lane = threadIdx.x & 31;
@@ -703,10 +717,10 @@ __global__ void __launch_bounds__(256) k_pairs_flat(PairArgs A, const uint64_t* 
   uint32_t n32 = 0, n64 = 0;
   for (int64_t ch = warp; ch < nchunks; ch += nwarps) {
     const uint64_t base = (uint64_t)ch * chunk;
-    // the entry of this lane's first slot: the last i with toff[i] <= f
-    // (entries with empty ranges share their toff with the next one)
+    // the long entry of this lane's first slot: the last k with toff[k] <= f
+    // (toff runs over the long entries, then stays at T)
     uint64_t f = base + (uint64_t)lane;
-    int64_t i = 0;
+    int64_t k = 0;
     {
       int64_t lo = 0, hi = A.ne + 1;
       const uint64_t fs = f < T ? f : T - 1;
@@ -715,21 +729,24 @@ __global__ void __launch_bounds__(256) k_pairs_flat(PairArgs A, const uint64_t* 
         if (toff[mid] <= fs) lo = mid + 1;
         else hi = mid;
       }
-      i = lo - 1;
+      k = lo - 1;
     }
+    int64_t i = lidx[k];
     FlatEntry E;
     flat_load(A, i, E);
-    uint64_t e_end = toff[i + 1], e_beg = toff[i];
+    uint64_t e_end = toff[k + 1], e_beg = toff[k];
     uint32_t j0 = j0s[i];
     for (int b = 0; b < FLAT_STEPS; ++b, f += 32) {
       bool acc = false;
       if (f < T) {
         if (f >= e_end) {
+          // every long range holds at least 32 slots: the next entry
           do {
-            ++i;
+            ++k;
             e_beg = e_end;
-            e_end = toff[i + 1];
+            e_end = toff[k + 1];
           } while (f >= e_end);
+          i = lidx[k];
           flat_load(A, i, E);
           j0 = j0s[i];
         }
@@ -760,12 +777,13 @@ __device__ __forceinline__ uint32_t flat_word(const uint32_t* __restrict__ bits,
 }
 
 // pairs per entry: the hits of its short word or of its slots
-__global__ void k_flat_count(int64_t ne, const uint64_t* __restrict__ toff, const uint32_t* __restrict__ bits,
+__global__ void k_flat_count(int64_t ne, const uint64_t* __restrict__ toff, const uint32_t* __restrict__ lflag,
+                             const uint32_t* __restrict__ lpos, const uint32_t* __restrict__ bits,
                              const uint32_t* __restrict__ sbits, uint32_t* __restrict__ cnt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ne) return;
-  const uint64_t f0 = toff[i], f1 = toff[i + 1];
   uint32_t c = __popc(sbits[i]);
+  const uint64_t f0 = lflag[i] ? toff[lpos[i]] : 0, f1 = lflag[i] ? toff[lpos[i] + 1] : 0;
   if (f1 > f0)
     for (uint64_t wd = f0 >> 5; wd <= (f1 - 1) >> 5; ++wd) c += __popc(flat_word(bits, wd, f0, f1));
   cnt[i] = c;
@@ -773,7 +791,8 @@ __global__ void k_flat_count(int64_t ne, const uint64_t* __restrict__ toff, cons
 
 // entry i's pairs at off[i], partners ascending (edge-edge keys take the
 // lower edge first: swept cells order edges by x, not by id)
-__global__ void k_flat_emit(PairArgs A, const uint64_t* __restrict__ toff, const uint32_t* __restrict__ j0s,
+__global__ void k_flat_emit(PairArgs A, const uint64_t* __restrict__ toff, const uint32_t* __restrict__ lflag,
+                            const uint32_t* __restrict__ lpos, const uint32_t* __restrict__ j0s,
                             const uint32_t* __restrict__ bits, const uint32_t* __restrict__ sbits,
                             const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off,
                             uint64_t* __restrict__ out) {
@@ -789,7 +808,7 @@ __global__ void k_flat_emit(PairArgs A, const uint64_t* __restrict__ toff, const
     type = CB_KEY_EE;
     ibase = jbase = (uint32_t)(t.n + t.T);
   }
-  const uint64_t f0 = toff[i], f1 = toff[i + 1];
+  const uint64_t f0 = lflag[i] ? toff[lpos[i]] : 0, f1 = lflag[i] ? toff[lpos[i] + 1] : 0;
   const uint32_t j0 = j0s[i];
   size_t o = off[i];
   for (uint32_t word = sbits[i]; word;) {  // a short range
@@ -972,11 +991,23 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     CB_TRY(buf_ensure(w.flat_j0, sizeof(uint32_t) * (size_t)ne, st));
     CB_TRY(buf_ensure(w.flat_slen, (size_t)ne, st));
     CB_TRY(buf_ensure(w.flat_sbits, sizeof(uint32_t) * (size_t)ne, st));
+    CB_TRY(buf_ensure(w.flat_lflag, sizeof(uint32_t) * ((size_t)ne + 1), st));
+    CB_TRY(buf_ensure(w.flat_lpos, sizeof(uint32_t) * ((size_t)ne + 1), st));
+    CB_TRY(buf_ensure(w.flat_lidx, sizeof(uint32_t) * (size_t)ne, st));
+    CB_TRY(buf_ensure(w.flat_llen, sizeof(uint32_t) * ((size_t)ne + 1), st));
     k_flat_ranges<<<cb_grid(ne + 1), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint32_t>(w.flat_len),
-                                                                    bp<uint8_t>(w.flat_slen), bp<uint32_t>(w.flat_j0));
+                                                                    bp<uint32_t>(w.flat_lflag), bp<uint8_t>(w.flat_slen),
+                                                                    bp<uint32_t>(w.flat_j0));
     k_pairs_short<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint8_t>(w.flat_slen), bp<uint32_t>(w.flat_j0),
                                                                bp<uint32_t>(w.flat_sbits));
-    cbp::exclusive_scan<uint32_t, uint64_t>(bp<uint32_t>(w.flat_len), bp<uint64_t>(w.flat_off), ne + 1,
+    // the long entries in entry order, their ranges laid end to end
+    cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.flat_lflag), bp<uint32_t>(w.flat_lpos), ne + 1,
+                                            bp<uint32_t>(w.scan_tmp), (uint32_t*)nullptr, st);
+    CB_CUDA(cudaMemsetAsync(w.flat_llen.p, 0, sizeof(uint32_t) * ((size_t)ne + 1), st));
+    k_flat_compact<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, bp<uint32_t>(w.flat_lflag),
+                                                                bp<uint32_t>(w.flat_lpos), bp<uint32_t>(w.flat_len),
+                                                                bp<uint32_t>(w.flat_lidx), bp<uint32_t>(w.flat_llen));
+    cbp::exclusive_scan<uint32_t, uint64_t>(bp<uint32_t>(w.flat_llen), bp<uint64_t>(w.flat_off), ne + 1,
                                             bp<uint64_t>(w.scan_tmp), scalars(s) + SC_COUNT0, st);
     CB_CUDA(cudaGetLastError());
     CB_TRY(read_scalars(s, SC_COUNT0, 1, &flat_t, st));
@@ -984,10 +1015,11 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     if (flat_t > 0) {
       const int64_t chunks = (int64_t)((flat_t + 32ull * FLAT_STEPS - 1) / (32ull * FLAT_STEPS));
       const int64_t g = std::min<int64_t>((chunks + 7) / 8, (int64_t)s->n_sms * 8);
-      k_pairs_flat<<<(int)g, 256, 0, cb_count(st)>>>(A, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_j0), flat_t,
-                                                    bp<uint32_t>(w.flat_bits));
+      k_pairs_flat<<<(int)g, 256, 0, cb_count(st)>>>(A, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_lidx),
+                                                    bp<uint32_t>(w.flat_j0), flat_t, bp<uint32_t>(w.flat_bits));
     }
-    k_flat_count<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_bits),
+    k_flat_count<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_lflag),
+                                                              bp<uint32_t>(w.flat_lpos), bp<uint32_t>(w.flat_bits),
                                                               bp<uint32_t>(w.flat_sbits), c);
   }
   // the fill: rods move their staged keys and re-test the entries with more;
@@ -1000,7 +1032,8 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
       const int g = (int)std::min<int64_t>(cb_grid(ne, pb), (int64_t)s->n_sms * 8);
       k_rod_pairs<true><<<g, pb, 0, cb_count(st)>>>(A, c, f, o, sg, bp<uint32_t>(w.ovl), novl);
     } else {
-      k_flat_emit<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_j0),
+      k_flat_emit<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_lflag),
+                                                               bp<uint32_t>(w.flat_lpos), bp<uint32_t>(w.flat_j0),
                                                                bp<uint32_t>(w.flat_bits), bp<uint32_t>(w.flat_sbits),
                                                                c, f, o);
     }

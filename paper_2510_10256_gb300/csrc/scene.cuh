@@ -100,8 +100,12 @@ struct BroadWork {
   DevBuf ckey[2];     // uint64 compact candidate keys (ping-pong)
   DevBuf stage;       // uint64 [PAIR_STAGE][entries]: the count pass's first pairs of each entry
   DevBuf ovl;         // uint32 entries with more pairs than the stage holds
-  DevBuf flat_len;    // shells: uint32 per entry (+1), the length of its swept partner range
-  DevBuf flat_off;    // shells: uint64 per entry (+1), its first test slot (exclusive scan of flat_len)
+  DevBuf flat_len;    // shells: uint32 per entry, the length of a long swept partner range
+  DevBuf flat_lflag;  // shells: uint32 per entry (+1), 1 for a long range
+  DevBuf flat_lpos;   // shells: uint32 per entry (+1), its place among the long entries (scan of flat_lflag)
+  DevBuf flat_lidx;   // shells: uint32 per long entry, the entry
+  DevBuf flat_llen;   // shells: uint32 per long entry (+1), its range length
+  DevBuf flat_off;    // shells: uint64 per long entry (+1), its first test slot (scan of flat_llen)
   DevBuf flat_j0;     // shells: uint32 per entry, its first partner
   DevBuf flat_bits;   // shells: one hit bit per test slot
   DevBuf flat_slen;   // shells: uint8 per entry, the length of a short range (tested per entry)
