@@ -369,8 +369,17 @@ __global__ void k_run_start(int64_t ne, const uint32_t* __restrict__ flag, const
   if (i == ne - 1) run_start[e + f] = (uint32_t)ne;
 }
 
-__device__ __forceinline__ float nextup(float v) { return nextafterf(v, INFINITY); }
-__device__ __forceinline__ float nextdn(float v) { return nextafterf(v, -INFINITY); }
+// the IEEE-754 neighbours of a float towards +inf and -inf, from its bit
+// pattern (a float's successor is the next integer bit pattern for x >= +0
+// and the previous one for x < 0; -0 steps to the smallest subnormal; +inf
+// and -inf stay where they are)
+__device__ __forceinline__ float nextup(float v) {
+  const int u = __float_as_int(v);
+  if (u == (int)0x80000000) return __int_as_float(1);
+  if (u == 0x7f800000) return v;
+  return __int_as_float(u >= 0 ? u + 1 : u - 1);
+}
+__device__ __forceinline__ float nextdn(float v) { return -nextup(-v); }
 
 // first index in [lo, hi) of a shell cell's run whose type group is >= g
 // (the run's keys share the cell code and ascend by group, then x level)
@@ -717,13 +726,14 @@ __global__ void __launch_bounds__(256) k_pairs_flat(PairArgs A, const uint64_t* 
   uint32_t n32 = 0, n64 = 0;
   for (int64_t ch = warp; ch < nchunks; ch += nwarps) {
     const uint64_t base = (uint64_t)ch * chunk;
+    // slots of this chunk (the last one may be short), counted from base
+    const uint32_t nvalid = (uint32_t)(T - base < chunk ? T - base : chunk);
     // the long entry of this lane's first slot: the last k with toff[k] <= f
     // (toff runs over the long entries, then stays at T)
-    uint64_t f = base + (uint64_t)lane;
     int64_t k = 0;
     {
       int64_t lo = 0, hi = A.ne + 1;
-      const uint64_t fs = f < T ? f : T - 1;
+      const uint64_t fs = base + (lane < (int)nvalid ? (uint64_t)lane : (uint64_t)(nvalid - 1));
       while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
         if (toff[mid] <= fs) lo = mid + 1;
@@ -731,30 +741,34 @@ __global__ void __launch_bounds__(256) k_pairs_flat(PairArgs A, const uint64_t* 
       }
       k = lo - 1;
     }
-    int64_t i = lidx[k];
     FlatEntry E;
-    flat_load(A, i, E);
-    uint64_t e_end = toff[k + 1], e_beg = toff[k];
-    uint32_t j0 = j0s[i];
-    for (int b = 0; b < FLAT_STEPS; ++b, f += 32) {
+    flat_load(A, lidx[k], E);
+    // the entry's end and its partner offset, relative to base (a range that
+    // ends past the chunk reads as ending at the chunk's end)
+    uint64_t e_end = toff[k + 1];
+    uint32_t r_end = (uint32_t)(e_end - base < chunk ? e_end - base : chunk);
+    int64_t jofs = (int64_t)j0s[lidx[k]] - (int64_t)(toff[k] - base);
+    for (int b = 0; b < FLAT_STEPS; ++b) {
+      const uint32_t sl = 32u * (uint32_t)b + (uint32_t)lane;
       bool acc = false;
-      if (f < T) {
-        if (f >= e_end) {
+      if (sl < nvalid) {
+        if (sl >= r_end) {
           // every long range holds at least 32 slots: the next entry
+          uint64_t e_beg;
           do {
             ++k;
             e_beg = e_end;
             e_end = toff[k + 1];
-          } while (f >= e_end);
-          i = lidx[k];
+          } while (base + sl >= e_end);
+          const uint32_t i = lidx[k];
           flat_load(A, i, E);
-          j0 = j0s[i];
+          r_end = (uint32_t)(e_end - base < chunk ? e_end - base : chunk);
+          jofs = (int64_t)j0s[i] - (int64_t)(e_beg - base);
         }
-        acc = flat_test(A, E, (int)(j0 + (uint32_t)(f - e_beg)), n32, n64);
+        acc = flat_test(A, E, (int)(jofs + (int64_t)sl), n32, n64);
       }
       const unsigned word = __ballot_sync(0xffffffffu, acc);
-      const uint64_t wd = (base >> 5) + (uint64_t)b;
-      if (lane == 0 && 32ull * wd < T) bits[wd] = word;
+      if (lane == 0 && 32u * (uint32_t)b < nvalid) bits[(base >> 5) + (uint64_t)b] = word;
     }
   }
   if (A.fpstat) {
