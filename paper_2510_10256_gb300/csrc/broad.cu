@@ -581,10 +581,15 @@ __global__ void __launch_bounds__(CB_THREADS) k_rod_pairs(PairArgs A, uint32_t* 
 // one word of the hit bits.  The pairs come out in the same order as before
 // (entry by entry, partners ascending), so the candidate array is unchanged.
 constexpr int FLAT_STEPS = 32;
-// Entries with fewer partners than this are tested by one thread each (one
-// hit word per entry); only longer ranges are laid end to end, so a lane of
-// the end-to-end pass moves to a new entry at most once per step.
-constexpr int FLAT_MIN = 32;
+// Entries with fewer partners than this are tested by one thread each
+// (FLAT_MIN / 32 hit words per entry, element-major); only longer ranges are
+// laid end to end, so a lane of the end-to-end pass moves to a new entry at
+// most once per step.
+#ifndef FLAT_MIN
+#define FLAT_MIN 32
+#endif
+constexpr int SHORT_WORDS = FLAT_MIN / 32;
+static_assert(FLAT_MIN % 32 == 0 && FLAT_MIN >= 32 && FLAT_MIN <= 256, "short ranges fill whole words");
 
 // entry i's first partner j0[i] and the length of its swept range: short
 // ranges in slen[i], long ones in len[i] with lflag[i] = 1 (lflag[ne] = 0)
@@ -688,20 +693,27 @@ __device__ __forceinline__ bool flat_test(const PairArgs& A, const FlatEntry& E,
 }
 
 // entries with short ranges: one thread each, hit bit b for partner j0 + b
+// (word b / 32 at sbits[(b / 32) * ne + i])
 __global__ void k_pairs_short(PairArgs A, const uint8_t* __restrict__ slen, const uint32_t* __restrict__ j0s,
                               uint32_t* __restrict__ sbits) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t n32 = 0, n64 = 0;
   if (i < A.ne) {
     const int n = slen[i];
-    uint32_t word = 0;
+    uint32_t word[SHORT_WORDS];
+#pragma unroll
+    for (int w = 0; w < SHORT_WORDS; ++w) word[w] = 0;
     if (n > 0) {
       FlatEntry E;
       flat_load(A, i, E);
       const int j0 = (int)j0s[i];
-      for (int b = 0; b < n; ++b) word |= (uint32_t)flat_test(A, E, j0 + b, n32, n64) << b;
+#pragma unroll
+      for (int w = 0; w < SHORT_WORDS; ++w)
+        for (int b = 32 * w; b < n && b < 32 * w + 32; ++b)
+          word[w] |= (uint32_t)flat_test(A, E, j0 + b, n32, n64) << (b & 31);
     }
-    sbits[i] = word;
+#pragma unroll
+    for (int w = 0; w < SHORT_WORDS; ++w) sbits[(size_t)w * A.ne + i] = word[w];
   }
   if (A.fpstat) {
     const unsigned a32 = __reduce_add_sync(0xffffffffu, n32), a64 = __reduce_add_sync(0xffffffffu, n64);
@@ -796,7 +808,9 @@ __global__ void k_flat_count(int64_t ne, const uint64_t* __restrict__ toff, cons
                              const uint32_t* __restrict__ sbits, uint32_t* __restrict__ cnt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ne) return;
-  uint32_t c = __popc(sbits[i]);
+  uint32_t c = 0;
+#pragma unroll
+  for (int w = 0; w < SHORT_WORDS; ++w) c += __popc(sbits[(size_t)w * ne + i]);
   const uint64_t f0 = lflag[i] ? toff[lpos[i]] : 0, f1 = lflag[i] ? toff[lpos[i] + 1] : 0;
   if (f1 > f0)
     for (uint64_t wd = f0 >> 5; wd <= (f1 - 1) >> 5; ++wd) c += __popc(flat_word(bits, wd, f0, f1));
@@ -825,13 +839,15 @@ __global__ void k_flat_emit(PairArgs A, const uint64_t* __restrict__ toff, const
   const uint64_t f0 = lflag[i] ? toff[lpos[i]] : 0, f1 = lflag[i] ? toff[lpos[i] + 1] : 0;
   const uint32_t j0 = j0s[i];
   size_t o = off[i];
-  for (uint32_t word = sbits[i]; word;) {  // a short range
-    const uint32_t b = (uint32_t)__ffs(word) - 1u;
-    word &= word - 1u;
-    const uint32_t Q = A.eval[j0 + b];
-    const bool swap = type == CB_KEY_EE && Q < P;
-    out[o++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
-  }
+#pragma unroll
+  for (int w = 0; w < SHORT_WORDS; ++w)  // a short range
+    for (uint32_t word = sbits[(size_t)w * A.ne + i]; word;) {
+      const uint32_t b = 32u * (uint32_t)w + (uint32_t)__ffs(word) - 1u;
+      word &= word - 1u;
+      const uint32_t Q = A.eval[j0 + b];
+      const bool swap = type == CB_KEY_EE && Q < P;
+      out[o++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
+    }
   if (f1 > f0) {
     for (uint64_t wd = f0 >> 5; wd <= (f1 - 1) >> 5; ++wd) {
       uint32_t word = flat_word(bits, wd, f0, f1);
@@ -1004,7 +1020,7 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     CB_TRY(buf_ensure(w.flat_off, sizeof(uint64_t) * ((size_t)ne + 1), st));
     CB_TRY(buf_ensure(w.flat_j0, sizeof(uint32_t) * (size_t)ne, st));
     CB_TRY(buf_ensure(w.flat_slen, (size_t)ne, st));
-    CB_TRY(buf_ensure(w.flat_sbits, sizeof(uint32_t) * (size_t)ne, st));
+    CB_TRY(buf_ensure(w.flat_sbits, sizeof(uint32_t) * SHORT_WORDS * (size_t)ne, st));
     CB_TRY(buf_ensure(w.flat_lflag, sizeof(uint32_t) * ((size_t)ne + 1), st));
     CB_TRY(buf_ensure(w.flat_lpos, sizeof(uint32_t) * ((size_t)ne + 1), st));
     CB_TRY(buf_ensure(w.flat_lidx, sizeof(uint32_t) * (size_t)ne, st));
