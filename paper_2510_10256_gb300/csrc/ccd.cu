@@ -340,69 +340,118 @@ __global__ void k_list_u(int64_t nu, const uint32_t* __restrict__ ulist, const u
   if (w < nu && flag[w]) list[pos[w]] = ulist[w];
 }
 
-// pass 2: additive CCD of the selected pairs, each up to its member's ceiling
-__global__ void __launch_bounds__(128) k_ccd_exact(CcdArgs A, int64_t m, const uint32_t* __restrict__ list,
-                                                   double* __restrict__ lb_out) {
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= m) return;
-  const int64_t q = list[w];
-  AccdStart S = accd_start(A, q);
-  unsigned long long* amin = macc_of(A, S.mem, MACC_ALPHA);
-  if (S.lp == 0.0 || S.g0 <= 0.0) {  // only reachable through an FP32 bound below 1
-    const double t0 = S.lp == 0.0 ? 1.0 : 0.0;
-    if (S.lp != 0.0) {
-      atomicOr(A.status, (unsigned long long)CB_DEV_PENETRATION);
-      atomicOr(macc_of(A, S.mem, MACC_STATUS), (unsigned long long)CB_DEV_PENETRATION);
-    }
-    A.t_out[q] = t0;
-    A.cls_out[q] = (uint8_t)S.cls | EXACT;
-    lb_out[q] = 2.0;
-    atomicMin(amin, (unsigned long long)__double_as_longlong(t0));
-    return;
-  }
-  // ceiling: the band's upper end, lowered to the member's minimum as it falls
-  const double hi = __longlong_as_double(*macc_of(A, S.mem, MACC_HI));
-  double cap = fmin(hi, __longlong_as_double(*(volatile unsigned long long*)amin));
-  const double g = xmul(ACCD_S, S.g0);
-  double t = 0.0, d;
-  double tl = xdiv(xmul(xsub(1.0, ACCD_S), S.g0), S.lp);
+// pass 2: additive CCD of the selected pairs, each up to its member's ceiling.
+// Pairs need very different numbers of steps, and an FP64 warp instruction
+// costs a warp the same whether one lane or 32 use it, so the warps are
+// persistent and hand idle lanes new pairs -- but only once EXACT_REFILL of
+// them are idle (or all are): the set-up of a pair (its first distance) then
+// runs once for a group of lanes instead of once per lane that finishes.
+// A pair's arithmetic is the same whichever lane runs it.
+constexpr int EXACT_REFILL = 8;
+
+struct ExactLane {
+  AccdStart S;
+  int64_t q;
+  double t, tl, g, hi, cap;
   int it;
-  bool capped = true, stopped = false;
-  for (it = 0; it < ACCD_MAX_ITER; ++it) {
-    S.Y0 = axpy3(S.Y0, tl, S.Q0);
-    S.Y1 = axpy3(S.Y1, tl, S.Q1);
-    S.Y2 = axpy3(S.Y2, tl, S.Q2);
-    S.Y3 = axpy3(S.Y3, tl, S.Q3);
-    cbg::stencil_distance(S.ee, S.Y0, S.Y1, S.Y2, S.Y3, d);
-    if (t > 0.0 && xsub(d, S.off) < g) {
-      capped = false;
-      break;
-    }
-    t = xadd(t, tl);
-    if (t > 1.0) {
-      t = 1.0;
-      capped = false;
-      break;
-    }
-    if ((it & 7) == 7) cap = fmin(hi, __longlong_as_double(*(volatile unsigned long long*)amin));
-    if (cap < 1.0 && t >= cap) {  // t_p >= t >= cap: this pair cannot lower the minimum now
-      capped = false;
-      stopped = true;
-      break;
-    }
-    tl = xdiv(xmul(ACCD_C, xsub(d, S.off)), S.lp);
-  }
-  if (capped) atomicOr(A.status, (unsigned long long)CB_DEV_ITER_LIMIT);
-  A.t_out[q] = t;
-  atomicMax(A.max_iters, (unsigned long long)(it + 1));
+};
+
+// finish a pair: exact t_p (lower-bound flag clear) or a lower bound
+__device__ __forceinline__ void exact_finish(const CcdArgs& A, const ExactLane& L, double* __restrict__ lb_out,
+                                             bool stopped, double t) {
+  A.t_out[L.q] = t;
   if (stopped) {
-    A.cls_out[q] = (uint8_t)S.cls;
-    lb_out[q] = t;
+    A.cls_out[L.q] = (uint8_t)L.S.cls;
+    lb_out[L.q] = t;
     return;
   }
-  A.cls_out[q] = (uint8_t)S.cls | EXACT;
-  lb_out[q] = 2.0;
-  atomicMin(amin, (unsigned long long)__double_as_longlong(t));
+  A.cls_out[L.q] = (uint8_t)L.S.cls | EXACT;
+  lb_out[L.q] = 2.0;
+  atomicMin(macc_of(A, L.S.mem, MACC_ALPHA), (unsigned long long)__double_as_longlong(t));
+}
+
+// fetch: a zeroed counter of the pairs handed out
+__global__ void __launch_bounds__(128) k_ccd_exact(CcdArgs A, int64_t m, const uint32_t* __restrict__ list,
+                                                   double* __restrict__ lb_out,
+                                                   unsigned long long* __restrict__ fetch) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned below = (1u << lane) - 1u;
+  ExactLane L;
+  bool have = false, drained = false;
+  int max_it = 0;
+  for (;;) {
+    const unsigned idle = __ballot_sync(0xffffffffu, !have);
+    const int nidle = __popc(idle);
+    if (!drained && (nidle >= EXACT_REFILL || nidle == 32)) {
+      // the group of idle lanes takes the next pairs of the list
+      unsigned long long b = 0;
+      if (lane == 0) b = atomicAdd(fetch, (unsigned long long)nidle);
+      b = __shfl_sync(0xffffffffu, b, 0);
+      if ((int64_t)b + nidle >= m) drained = true;  // nothing left after this group
+      const int64_t w = (int64_t)b + __popc(idle & below);
+      if (!have && w < m) {
+        L.q = list[w];
+        L.S = accd_start(A, L.q);
+        if (L.S.lp == 0.0 || L.S.g0 <= 0.0) {  // only reachable through an FP32 bound below 1
+          if (L.S.lp != 0.0) {
+            atomicOr(A.status, (unsigned long long)CB_DEV_PENETRATION);
+            atomicOr(macc_of(A, L.S.mem, MACC_STATUS), (unsigned long long)CB_DEV_PENETRATION);
+          }
+          exact_finish(A, L, lb_out, false, L.S.lp == 0.0 ? 1.0 : 0.0);
+        } else {
+          // ceiling: the band's upper end, lowered to the member's minimum as it falls
+          L.hi = __longlong_as_double(*macc_of(A, L.S.mem, MACC_HI));
+          L.cap = fmin(L.hi, __longlong_as_double(*(volatile unsigned long long*)macc_of(A, L.S.mem, MACC_ALPHA)));
+          L.g = xmul(ACCD_S, L.S.g0);
+          L.t = 0.0;
+          L.tl = xdiv(xmul(xsub(1.0, ACCD_S), L.S.g0), L.S.lp);
+          L.it = 0;
+          have = true;
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, have)) {
+      if (drained) break;
+      continue;  // every pair of the group finished at its set-up: fetch again
+    }
+    if (have) {
+      // one additive-CCD step
+      AccdStart& S = L.S;
+      S.Y0 = axpy3(S.Y0, L.tl, S.Q0);
+      S.Y1 = axpy3(S.Y1, L.tl, S.Q1);
+      S.Y2 = axpy3(S.Y2, L.tl, S.Q2);
+      S.Y3 = axpy3(S.Y3, L.tl, S.Q3);
+      double d;
+      cbg::stencil_distance(S.ee, S.Y0, S.Y1, S.Y2, S.Y3, d);
+      const int it = L.it++;
+      if (L.t > 0.0 && xsub(d, S.off) < L.g) {
+        exact_finish(A, L, lb_out, false, L.t);
+        have = false;
+      } else {
+        L.t = xadd(L.t, L.tl);
+        if (L.t > 1.0) {
+          exact_finish(A, L, lb_out, false, 1.0);
+          have = false;
+        } else {
+          if ((it & 7) == 7)
+            L.cap = fmin(L.hi, __longlong_as_double(*(volatile unsigned long long*)macc_of(A, S.mem, MACC_ALPHA)));
+          if (L.cap < 1.0 && L.t >= L.cap) {  // t_p >= t >= cap: this pair cannot lower the minimum now
+            exact_finish(A, L, lb_out, true, L.t);
+            have = false;
+          } else if (it + 1 >= ACCD_MAX_ITER) {
+            atomicOr(A.status, (unsigned long long)CB_DEV_ITER_LIMIT);
+            exact_finish(A, L, lb_out, false, L.t);
+            have = false;
+          } else {
+            L.tl = xdiv(xmul(ACCD_C, xsub(d, S.off)), S.lp);
+          }
+        }
+      }
+      if (!have) max_it = max(max_it, it + 1);
+    }
+  }
+  const int wm = __reduce_max_sync(0xffffffffu, max_it);
+  if (lane == 0 && wm > 0) atomicMax(A.max_iters, (unsigned long long)wm);
 }
 
 __global__ void k_alpha_final(int count, const unsigned long long* __restrict__ macc, double* __restrict__ out) {
@@ -543,9 +592,15 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
       uint64_t hmsel;
       CB_TRY(read_scalars(s, SC_COUNT1, 1, &hmsel, st));
       const int64_t msel = (int64_t)(uint32_t)hmsel;
-      if (msel > 0)
-        k_ccd_exact<<<cb_grid(msel, 128), 128, 0, cb_count(st)>>>(A, msel, bp<uint32_t>(s->ccd_list),
-                                                                  bp<double>(s->ccd_lb));
+      if (msel > 0) {
+        // persistent warps: at most three 128-thread blocks per SM (the
+        // kernel's registers), fewer when the list is short
+        unsigned long long* fetch = (unsigned long long*)(sc + SC_FETCH);
+        CB_CUDA(cudaMemsetAsync(fetch, 0, sizeof(unsigned long long), st));
+        const int64_t g = std::min<int64_t>(cb_grid(msel, 128), (int64_t)s->n_sms * 3);
+        k_ccd_exact<<<(int)g, 128, 0, cb_count(st)>>>(A, msel, bp<uint32_t>(s->ccd_list), bp<double>(s->ccd_lb),
+                                                      fetch);
+      }
       CB_CUDA(cudaGetLastError());
       CB_TRY(read_macc());
       any = false;

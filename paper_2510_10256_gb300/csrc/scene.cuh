@@ -253,7 +253,7 @@ enum {
   SC_KSPLIT = 16,       // two uint32 counters: face / line-line pairs, the other active pairs
   SC_NOVF = 17,         // broad phase: entries whose pairs overflow the stage
   SC_NBK = 18,          // BSR pattern: keys left after the per-run sets of k_block_keys
-  SC_SPARE = 19,        // unused
+  SC_FETCH = 19,        // ccd_step, exact rounds: pairs of the list handed out so far
   SC_NMOLL = 20,        // barrier_eval: mollified edge-edge pairs
   SC_N = 21
 };
