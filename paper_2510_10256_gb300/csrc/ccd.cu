@@ -319,25 +319,35 @@ __global__ void __launch_bounds__(128) k_ccd_bound(CcdArgs A, double* __restrict
   }
 }
 
-// select the listed pairs with lb <= hi of their member: flag[w] for pair ulist[w]
+// select the listed pairs with lb <= hi of their member: flag[w] for pair
+// ulist[w], counted by kind (point-triangle in the low 32 bits, edge-edge in
+// the high ones) so that the list puts each kind together: the distance
+// routine branches on the kind, and a warp that mixes them runs both
 __global__ void k_ccd_select_u(int64_t nu, const uint32_t* __restrict__ ulist, const uint64_t* __restrict__ keys,
                                const int32_t* __restrict__ ev0, const int32_t* __restrict__ vsc,
                                const double* __restrict__ lb, const unsigned long long* __restrict__ macc,
-                               uint32_t* __restrict__ flag) {
+                               unsigned long long* __restrict__ flag) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= nu) return;
   const uint32_t q = ulist[w];
   const uint64_t key = keys[q];
-  const int v0 = cb_key_type(key) == CB_KEY_PT ? (int)cb_key_i(key) : ev0[cb_key_i(key)];
+  const bool pt = cb_key_type(key) == CB_KEY_PT;
+  const int v0 = pt ? (int)cb_key_i(key) : ev0[cb_key_i(key)];
   const int mem = vsc[v0];
   const double hi = __longlong_as_double(macc[(size_t)mem * MACC_STRIDE + MACC_HI]);
-  flag[w] = lb[q] <= hi ? 1u : 0u;
+  flag[w] = lb[q] <= hi ? (pt ? 1ull : 1ull << 32) : 0ull;
 }
 
-__global__ void k_list_u(int64_t nu, const uint32_t* __restrict__ ulist, const uint32_t* __restrict__ flag,
-                         const uint32_t* __restrict__ pos, uint32_t* __restrict__ list) {
+// the selected pairs, point-triangle ones first (npt of them, the low half of
+// the scan's total), each kind in list order
+__global__ void k_list_u(int64_t nu, const uint32_t* __restrict__ ulist, const unsigned long long* __restrict__ flag,
+                         const unsigned long long* __restrict__ pos, const unsigned long long* __restrict__ total,
+                         uint32_t* __restrict__ list) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w < nu && flag[w]) list[pos[w]] = ulist[w];
+  if (w >= nu || !flag[w]) return;
+  const unsigned long long p = pos[w];
+  const uint64_t at = (flag[w] & 0xffffffffull) ? (p & 0xffffffffull) : (*total & 0xffffffffull) + (p >> 32);
+  if (at < (uint64_t)nu) list[at] = ulist[w];  // always: at most nu pairs are selected
 }
 
 // pass 2: additive CCD of the selected pairs, each up to its member's ceiling.
@@ -481,8 +491,8 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     CB_TRY(buf_ensure(s->ccd_t, sizeof(double) * (size_t)np, st));
     CB_TRY(buf_ensure(s->ccd_cls, (size_t)np, st));
     CB_TRY(buf_ensure(s->ccd_lb, sizeof(double) * (size_t)np, st));
-    CB_TRY(buf_ensure(s->ccd_flag, sizeof(uint32_t) * (size_t)np, st));
-    CB_TRY(buf_ensure(s->ccd_pos, sizeof(uint32_t) * ((size_t)np + 1), st));
+    CB_TRY(buf_ensure(s->ccd_flag, sizeof(unsigned long long) * (size_t)np, st));
+    CB_TRY(buf_ensure(s->ccd_pos, sizeof(unsigned long long) * ((size_t)np + 1), st));
     CB_TRY(buf_ensure(s->ccd_list, sizeof(uint32_t) * (size_t)np, st));
     CB_TRY(buf_ensure(s->scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(np) + 8), st));
     CcdArgs A;
@@ -582,16 +592,19 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     }
     while (any) {
       CB_TRY(upload_band(lo, hi));
+      unsigned long long* flag64 = bp<unsigned long long>(s->ccd_flag);
+      unsigned long long* pos64 = bp<unsigned long long>(s->ccd_pos);
+      unsigned long long* tot64 = (unsigned long long*)tot;
       k_ccd_select_u<<<cb_grid(nu), CB_THREADS, 0, cb_count(st)>>>(
           nu, bp<uint32_t>(s->ccd_ulist), bp<uint64_t>(s->ccd_keys), bp<int32_t>(s->ev0), bp<int32_t>(s->vsc),
-          bp<double>(s->ccd_lb), macc, bp<uint32_t>(s->ccd_flag));
-      cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(s->ccd_flag), bp<uint32_t>(s->ccd_pos), nu,
-                                              bp<uint32_t>(s->scan_tmp), tot, st);
-      k_list_u<<<cb_grid(nu), CB_THREADS, 0, cb_count(st)>>>(nu, bp<uint32_t>(s->ccd_ulist), bp<uint32_t>(s->ccd_flag),
-                                                             bp<uint32_t>(s->ccd_pos), bp<uint32_t>(s->ccd_list));
+          bp<double>(s->ccd_lb), macc, flag64);
+      cbp::exclusive_scan<unsigned long long, unsigned long long>(flag64, pos64, nu,
+                                                                  bp<unsigned long long>(s->scan_tmp), tot64, st);
+      k_list_u<<<cb_grid(nu), CB_THREADS, 0, cb_count(st)>>>(nu, bp<uint32_t>(s->ccd_ulist), flag64, pos64, tot64,
+                                                             bp<uint32_t>(s->ccd_list));
       uint64_t hmsel;
       CB_TRY(read_scalars(s, SC_COUNT1, 1, &hmsel, st));
-      const int64_t msel = (int64_t)(uint32_t)hmsel;
+      const int64_t msel = (int64_t)(hmsel & 0xffffffffull) + (int64_t)(hmsel >> 32);
       if (msel > 0) {
         // persistent warps: at most three 128-thread blocks per SM (the
         // kernel's registers), fewer when the list is short

@@ -203,7 +203,7 @@ struct cb_scene {
   DevBuf ccd_t;         // double [nccd]
   DevBuf ccd_cls;       // uint8 [nccd] class | 0x80 when t is exact
   DevBuf ccd_lb;        // double [nccd] lower bound of t (2 when resolved)
-  DevBuf ccd_flag, ccd_pos, ccd_list;  // uint32 band selection
+  DevBuf ccd_flag, ccd_pos, ccd_list;  // band selection: u64 kind counts (flag, scan), uint32 list
   DevBuf ccd_ulist;     // uint32 pairs still unresolved after the first-step pass
   int64_t n_ccd = 0;
   // lagged friction (friction_lag / friction_eval / friction_spmv)

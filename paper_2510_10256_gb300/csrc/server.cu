@@ -196,8 +196,8 @@ cb_status cb_scene_reserve(cb_scene* s, int64_t n_candidates, int64_t n_ccd, int
   CB_TRY(buf_ensure(s->ccd_t, sizeof(double) * nq, st));
   CB_TRY(buf_ensure(s->ccd_cls, nq, st));
   CB_TRY(buf_ensure(s->ccd_lb, sizeof(double) * nq, st));
-  CB_TRY(buf_ensure(s->ccd_flag, sizeof(uint32_t) * nq, st));
-  CB_TRY(buf_ensure(s->ccd_pos, sizeof(uint32_t) * (nq + 1), st));
+  CB_TRY(buf_ensure(s->ccd_flag, sizeof(unsigned long long) * nq, st));
+  CB_TRY(buf_ensure(s->ccd_pos, sizeof(unsigned long long) * (nq + 1), st));
   CB_TRY(buf_ensure(s->ccd_list, sizeof(uint32_t) * nq, st));
   CB_TRY(buf_ensure(s->ccd_ulist, sizeof(uint32_t) * nq, st));
   return CB_OK;
