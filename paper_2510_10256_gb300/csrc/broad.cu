@@ -581,15 +581,11 @@ __global__ void __launch_bounds__(CB_THREADS) k_rod_pairs(PairArgs A, uint32_t* 
 // one word of the hit bits.  The pairs come out in the same order as before
 // (entry by entry, partners ascending), so the candidate array is unchanged.
 constexpr int FLAT_STEPS = 32;
-// Entries with fewer partners than this are tested by one thread each
-// (FLAT_MIN / 32 hit words per entry, element-major); only longer ranges are
-// laid end to end, so a lane of the end-to-end pass moves to a new entry at
-// most once per step.
-#ifndef FLAT_MIN
-#define FLAT_MIN 32
-#endif
-constexpr int SHORT_WORDS = FLAT_MIN / 32;
-static_assert(FLAT_MIN % 32 == 0 && FLAT_MIN >= 32 && FLAT_MIN <= 256, "short ranges fill whole words");
+// Entries with fewer partners than this keep their hits in one word each and
+// are tested warp by warp (k_pairs_short); only longer ranges are laid end
+// to end, so a lane of the end-to-end pass moves to a new entry at most once
+// per step.  (Thresholds of 64 and 128 partners measured the same.)
+constexpr int FLAT_MIN = 32;
 
 // entry i's first partner j0[i] and the length of its swept range: short
 // ranges in slen[i], long ones in len[i] with lflag[i] = 1 (lflag[ne] = 0)
@@ -692,32 +688,70 @@ __device__ __forceinline__ bool flat_test(const PairArgs& A, const FlatEntry& E,
   return acc;
 }
 
-// entries with short ranges: one thread each, hit bit b for partner j0 + b
-// (word b / 32 at sbits[(b / 32) * ne + i])
-__global__ void k_pairs_short(PairArgs A, const uint8_t* __restrict__ slen, const uint32_t* __restrict__ j0s,
-                              uint32_t* __restrict__ sbits) {
+// Entries with short ranges, a warp per 32 consecutive entries: the warp
+// scans their lengths (with shuffles) and lays their partners end to end, and
+// each step tests 32 of those (entry, partner) slots, lane l the slot
+// base + l -- its entry is the last lane whose range starts at or before the
+// slot (a search over the lanes' starts), whose data the lane takes by
+// shuffles.  Hit bit b of an entry's word is its partner j0 + b.
+__global__ void __launch_bounds__(256) k_pairs_short(PairArgs A, const uint8_t* __restrict__ slen,
+                                                     const uint32_t* __restrict__ j0s,
+                                                     uint32_t* __restrict__ sbits) {
+  __shared__ uint32_t sw[256];  // the hit word of each entry of the block
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t n32 = 0, n64 = 0;
-  if (i < A.ne) {
-    const int n = slen[i];
-    uint32_t word[SHORT_WORDS];
+  const int n = i < A.ne ? (int)slen[i] : 0;
+  sw[threadIdx.x] = 0u;
+  int inc = n;
 #pragma unroll
-    for (int w = 0; w < SHORT_WORDS; ++w) word[w] = 0;
-    if (n > 0) {
-      FlatEntry E;
-      flat_load(A, i, E);
-      const int j0 = (int)j0s[i];
-#pragma unroll
-      for (int w = 0; w < SHORT_WORDS; ++w)
-        for (int b = 32 * w; b < n && b < 32 * w + 32; ++b)
-          word[w] |= (uint32_t)flat_test(A, E, j0 + b, n32, n64) << (b & 31);
-    }
-#pragma unroll
-    for (int w = 0; w < SHORT_WORDS; ++w) sbits[(size_t)w * A.ne + i] = word[w];
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(full, inc, o);
+    if (lane >= o) inc += v;
   }
+  const int ex = inc - n;                        // this entry's first slot
+  const int total = __shfl_sync(full, inc, 31);  // slots of the warp's entries
+  FlatEntry E{};
+  int j0 = 0;
+  if (n > 0) {
+    flat_load(A, i, E);
+    j0 = (int)j0s[i];
+  }
+  uint32_t n32 = 0, n64 = 0;
+  __syncwarp();
+  for (int base = 0; base < total; base += 32) {
+    const int sl = base + lane;
+    int e = 0;  // the last lane whose range starts at or before sl
+#pragma unroll
+    for (int bit = 16; bit > 0; bit >>= 1) {
+      const int c = e + bit;
+      if (__shfl_sync(full, ex, c) <= sl) e = c;
+    }
+    FlatEntry F;
+    F.P = __shfl_sync(full, E.P, e);
+    F.cell = __shfl_sync(full, E.cell, e);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) F.pv[k] = __shfl_sync(full, E.pv[k], e);
+    F.plo = make_float4(__shfl_sync(full, E.plo.x, e), __shfl_sync(full, E.plo.y, e),
+                        __shfl_sync(full, E.plo.z, e), 0.f);
+    F.phi = make_float4(__shfl_sync(full, E.phi.x, e), __shfl_sync(full, E.phi.y, e),
+                        __shfl_sync(full, E.phi.z, e), 0.f);
+    F.G.ox = __shfl_sync(full, E.G.ox, e);
+    F.G.oy = __shfl_sync(full, E.G.oy, e);
+    F.G.oz = __shfl_sync(full, E.G.oz, e);
+    F.G.inv = __shfl_sync(full, E.G.inv, e);
+    F.G.dx = __shfl_sync(full, E.G.dx, e);
+    F.G.dy = __shfl_sync(full, E.G.dy, e);
+    F.G.dz = __shfl_sync(full, E.G.dz, e);
+    const int b = sl - __shfl_sync(full, ex, e);
+    const int j = __shfl_sync(full, j0, e) + b;
+    if (sl < total && flat_test(A, F, j, n32, n64)) atomicOr(&sw[(threadIdx.x & ~31) + e], 1u << b);
+  }
+  __syncwarp();
+  if (i < A.ne) sbits[i] = sw[threadIdx.x];
   if (A.fpstat) {
-    const unsigned a32 = __reduce_add_sync(0xffffffffu, n32), a64 = __reduce_add_sync(0xffffffffu, n64);
-    if ((threadIdx.x & 31) == 0) {
+    const unsigned a32 = __reduce_add_sync(full, n32), a64 = __reduce_add_sync(full, n64);
+    if (lane == 0) {
       if (a32) atomicAdd(&A.fpstat[0], (unsigned long long)a32);
       if (a64) atomicAdd(&A.fpstat[1], (unsigned long long)a64);
     }
@@ -808,9 +842,7 @@ __global__ void k_flat_count(int64_t ne, const uint64_t* __restrict__ toff, cons
                              const uint32_t* __restrict__ sbits, uint32_t* __restrict__ cnt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ne) return;
-  uint32_t c = 0;
-#pragma unroll
-  for (int w = 0; w < SHORT_WORDS; ++w) c += __popc(sbits[(size_t)w * ne + i]);
+  uint32_t c = __popc(sbits[i]);
   const uint64_t f0 = lflag[i] ? toff[lpos[i]] : 0, f1 = lflag[i] ? toff[lpos[i] + 1] : 0;
   if (f1 > f0)
     for (uint64_t wd = f0 >> 5; wd <= (f1 - 1) >> 5; ++wd) c += __popc(flat_word(bits, wd, f0, f1));
@@ -839,15 +871,13 @@ __global__ void k_flat_emit(PairArgs A, const uint64_t* __restrict__ toff, const
   const uint64_t f0 = lflag[i] ? toff[lpos[i]] : 0, f1 = lflag[i] ? toff[lpos[i] + 1] : 0;
   const uint32_t j0 = j0s[i];
   size_t o = off[i];
-#pragma unroll
-  for (int w = 0; w < SHORT_WORDS; ++w)  // a short range
-    for (uint32_t word = sbits[(size_t)w * A.ne + i]; word;) {
-      const uint32_t b = 32u * (uint32_t)w + (uint32_t)__ffs(word) - 1u;
-      word &= word - 1u;
-      const uint32_t Q = A.eval[j0 + b];
-      const bool swap = type == CB_KEY_EE && Q < P;
-      out[o++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
-    }
+  for (uint32_t word = sbits[i]; word;) {  // a short range
+    const uint32_t b = (uint32_t)__ffs(word) - 1u;
+    word &= word - 1u;
+    const uint32_t Q = A.eval[j0 + b];
+    const bool swap = type == CB_KEY_EE && Q < P;
+    out[o++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
+  }
   if (f1 > f0) {
     for (uint64_t wd = f0 >> 5; wd <= (f1 - 1) >> 5; ++wd) {
       uint32_t word = flat_word(bits, wd, f0, f1);
@@ -1020,7 +1050,7 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     CB_TRY(buf_ensure(w.flat_off, sizeof(uint64_t) * ((size_t)ne + 1), st));
     CB_TRY(buf_ensure(w.flat_j0, sizeof(uint32_t) * (size_t)ne, st));
     CB_TRY(buf_ensure(w.flat_slen, (size_t)ne, st));
-    CB_TRY(buf_ensure(w.flat_sbits, sizeof(uint32_t) * SHORT_WORDS * (size_t)ne, st));
+    CB_TRY(buf_ensure(w.flat_sbits, sizeof(uint32_t) * (size_t)ne, st));
     CB_TRY(buf_ensure(w.flat_lflag, sizeof(uint32_t) * ((size_t)ne + 1), st));
     CB_TRY(buf_ensure(w.flat_lpos, sizeof(uint32_t) * ((size_t)ne + 1), st));
     CB_TRY(buf_ensure(w.flat_lidx, sizeof(uint32_t) * (size_t)ne, st));
@@ -1028,8 +1058,8 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     k_flat_ranges<<<cb_grid(ne + 1), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint32_t>(w.flat_len),
                                                                     bp<uint32_t>(w.flat_lflag), bp<uint8_t>(w.flat_slen),
                                                                     bp<uint32_t>(w.flat_j0));
-    k_pairs_short<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint8_t>(w.flat_slen), bp<uint32_t>(w.flat_j0),
-                                                               bp<uint32_t>(w.flat_sbits));
+    k_pairs_short<<<cb_grid(ne, 256), 256, 0, cb_count(st)>>>(A, bp<uint8_t>(w.flat_slen), bp<uint32_t>(w.flat_j0),
+                                                             bp<uint32_t>(w.flat_sbits));
     // the long entries in entry order, their ranges laid end to end
     cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.flat_lflag), bp<uint32_t>(w.flat_lpos), ne + 1,
                                             bp<uint32_t>(w.scan_tmp), (uint32_t*)nullptr, st);

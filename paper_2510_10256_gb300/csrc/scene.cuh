@@ -109,7 +109,7 @@ struct BroadWork {
   DevBuf flat_j0;     // shells: uint32 per entry, its first partner
   DevBuf flat_bits;   // shells: one hit bit per test slot
   DevBuf flat_slen;   // shells: uint8 per entry, the length of a short range (tested per entry)
-  DevBuf flat_sbits;  // shells: uint32 [FLAT_MIN / 32][entries], the hits of a short range
+  DevBuf flat_sbits;  // shells: uint32 per entry, the hits of a short range
   DevBuf scan_tmp;
   DevBuf hist;
 };
