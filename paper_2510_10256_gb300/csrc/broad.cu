@@ -651,15 +651,16 @@ __device__ __forceinline__ void flat_load(const PairArgs& A, int64_t i, FlatEntr
   E.G = A.grids[kc >> 30];
 }
 
-// the test of the per-entry pass: FP32 boxes overlap, the overlap's low
-// corner lies in this cell (each pair is reported by one cell), the two share
-// no vertex; the FP64 boxes decide where the FP32 margins cannot
-__device__ __forceinline__ bool flat_test(const PairArgs& A, const FlatEntry& E, int j, uint32_t& n32,
-                                          uint32_t& n64) {
-  const float4 qlo = A.ebox[2 * (size_t)j], qhi = A.ebox[2 * (size_t)j + 1];
-  if (!(E.plo.x <= qhi.x && qlo.x <= E.phi.x && E.plo.y <= qhi.y && qlo.y <= E.phi.y && E.plo.z <= qhi.z &&
-        qlo.z <= E.phi.z))
-    return false;
+__device__ __forceinline__ bool box_overlap(const float4& plo, const float4& phi, const float4& qlo,
+                                            const float4& qhi) {
+  return plo.x <= qhi.x && qlo.x <= phi.x && plo.y <= qhi.y && qlo.y <= phi.y && plo.z <= qhi.z && qlo.z <= phi.z;
+}
+
+// the test of a pair whose FP32 boxes overlap: the overlap's low corner lies
+// in this cell (each pair is reported by one cell), the two share no vertex;
+// the FP64 boxes decide where the FP32 margins cannot
+__device__ __forceinline__ bool flat_rest(const PairArgs& A, const FlatEntry& E, const float4& qlo,
+                                          const float4& qhi, int j, uint32_t& n32, uint32_t& n64) {
   const Grid& G = E.G;
   const uint32_t hc = morton(cell_of(fmaxf(E.plo.x, qlo.x), G.ox, G.inv, G.dx),
                              cell_of(fmaxf(E.plo.y, qlo.y), G.oy, G.inv, G.dy),
@@ -686,6 +687,13 @@ __device__ __forceinline__ bool flat_test(const PairArgs& A, const FlatEntry& E,
 #pragma unroll
   for (int k = 0; k < 3; ++k) acc = acc && (b1[k] <= b2[3 + k]) && (b2[k] <= b1[3 + k]);
   return acc;
+}
+
+// the whole test of entry E against partner j
+__device__ __forceinline__ bool flat_test(const PairArgs& A, const FlatEntry& E, int j, uint32_t& n32,
+                                          uint32_t& n64) {
+  const float4 qlo = A.ebox[2 * (size_t)j], qhi = A.ebox[2 * (size_t)j + 1];
+  return box_overlap(E.plo, E.phi, qlo, qhi) && flat_rest(A, E, qlo, qhi, j, n32, n64);
 }
 
 // Entries with short ranges, a warp per 32 consecutive entries: the warp
@@ -759,12 +767,43 @@ __global__ void __launch_bounds__(256) k_pairs_short(PairArgs A, const uint8_t* 
 }
 
 // hit bits of slots [0, T): word w holds slots 32 w .. 32 w + 31 (grid-stride
-// over chunks of FLAT_STEPS words, one warp per chunk)
-__global__ void __launch_bounds__(256) k_pairs_flat(PairArgs A, const uint64_t* __restrict__ toff,
-                                                    const uint32_t* __restrict__ lidx,
-                                                    const uint32_t* __restrict__ j0s, uint64_t T,
-                                                    uint32_t* __restrict__ bits) {
+// over chunks of FLAT_STEPS = 32 words, one warp per chunk).  Most slots fail
+// the box test, and a warp whose lanes disagree runs the longer rest of the
+// test (home cell, shared vertices, FP32 margins) for all of them, so the two
+// are split: each step's box overlaps go to a small queue in shared memory,
+// and the rest of the test runs 32 queued slots at a time with every lane
+// busy (the remainder at the chunk's end); hits set bits of the chunk's 32
+// words in shared memory.
+constexpr int FLAT_WARPS = 8;  // warps per block of k_pairs_flat
+static_assert(FLAT_STEPS == 32, "one hit word per lane at the end of a chunk");
+
+// the rest of the test for queued slots q0 .. q0 + cnt - 1, one per lane
+__device__ __forceinline__ void flat_batch(const PairArgs& A, const uint32_t* qi, const uint32_t* qj,
+                                           const uint16_t* qs, int q0, int cnt, uint32_t* cw, uint32_t& n32,
+                                           uint32_t& n64) {
   const int lane = threadIdx.x & 31;
+  if (lane >= cnt) return;
+  const uint32_t i = qi[q0 + lane], j = qj[q0 + lane];
+  const int sl = qs[q0 + lane];
+  FlatEntry E;
+  flat_load(A, i, E);
+  const float4 qlo = A.ebox[2 * (size_t)j], qhi = A.ebox[2 * (size_t)j + 1];
+  if (flat_rest(A, E, qlo, qhi, (int)j, n32, n64)) atomicOr(&cw[sl >> 5], 1u << (sl & 31));
+}
+
+__global__ void __launch_bounds__(32 * FLAT_WARPS) k_pairs_flat(PairArgs A, const uint64_t* __restrict__ toff,
+                                                                const uint32_t* __restrict__ lidx,
+                                                                const uint32_t* __restrict__ j0s, uint64_t T,
+                                                                uint32_t* __restrict__ bits) {
+  __shared__ uint32_t s_qi[FLAT_WARPS][64], s_qj[FLAT_WARPS][64], s_cw[FLAT_WARPS][32];
+  __shared__ uint16_t s_qs[FLAT_WARPS][64];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
+  uint32_t* qi = s_qi[wb];
+  uint32_t* qj = s_qj[wb];
+  uint16_t* qs = s_qs[wb];
+  uint32_t* cw = s_cw[wb];
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const uint64_t chunk = 32ull * FLAT_STEPS;
@@ -787,16 +826,20 @@ __global__ void __launch_bounds__(256) k_pairs_flat(PairArgs A, const uint64_t* 
       }
       k = lo - 1;
     }
-    FlatEntry E;
-    flat_load(A, lidx[k], E);
+    uint32_t i = lidx[k];
+    float4 plo = A.ebox[2 * (size_t)i], phi = A.ebox[2 * (size_t)i + 1];
     // the entry's end and its partner offset, relative to base (a range that
     // ends past the chunk reads as ending at the chunk's end)
     uint64_t e_end = toff[k + 1];
     uint32_t r_end = (uint32_t)(e_end - base < chunk ? e_end - base : chunk);
-    int64_t jofs = (int64_t)j0s[lidx[k]] - (int64_t)(toff[k] - base);
+    int64_t jofs = (int64_t)j0s[i] - (int64_t)(toff[k] - base);
+    cw[lane] = 0u;
+    int qn = 0;  // queued slots (fewer than 32 between steps)
+    __syncwarp();
     for (int b = 0; b < FLAT_STEPS; ++b) {
       const uint32_t sl = 32u * (uint32_t)b + (uint32_t)lane;
-      bool acc = false;
+      bool pass = false;
+      int j = 0;
       if (sl < nvalid) {
         if (sl >= r_end) {
           // every long range holds at least 32 slots: the next entry
@@ -806,19 +849,37 @@ __global__ void __launch_bounds__(256) k_pairs_flat(PairArgs A, const uint64_t* 
             e_beg = e_end;
             e_end = toff[k + 1];
           } while (base + sl >= e_end);
-          const uint32_t i = lidx[k];
-          flat_load(A, i, E);
+          i = lidx[k];
+          plo = A.ebox[2 * (size_t)i];
+          phi = A.ebox[2 * (size_t)i + 1];
           r_end = (uint32_t)(e_end - base < chunk ? e_end - base : chunk);
           jofs = (int64_t)j0s[i] - (int64_t)(e_beg - base);
         }
-        acc = flat_test(A, E, (int)(jofs + (int64_t)sl), n32, n64);
+        j = (int)(jofs + (int64_t)sl);
+        pass = box_overlap(plo, phi, A.ebox[2 * (size_t)j], A.ebox[2 * (size_t)j + 1]);
       }
-      const unsigned word = __ballot_sync(0xffffffffu, acc);
-      if (lane == 0 && 32u * (uint32_t)b < nvalid) bits[(base >> 5) + (uint64_t)b] = word;
+      const unsigned m = __ballot_sync(full, pass);
+      if (pass) {
+        const int at = qn + __popc(m & below);
+        qi[at] = i;
+        qj[at] = (uint32_t)j;
+        qs[at] = (uint16_t)sl;
+      }
+      qn += __popc(m);
+      __syncwarp();
+      if (qn >= 32) {
+        flat_batch(A, qi, qj, qs, qn - 32, 32, cw, n32, n64);
+        qn -= 32;
+        __syncwarp();  // the batch's slots are read before the next appends
+      }
     }
+    if (qn > 0) flat_batch(A, qi, qj, qs, 0, qn, cw, n32, n64);
+    __syncwarp();
+    if (32u * (uint32_t)lane < nvalid) bits[(base >> 5) + (uint64_t)lane] = cw[lane];
+    __syncwarp();
   }
   if (A.fpstat) {
-    const unsigned a32 = __reduce_add_sync(0xffffffffu, n32), a64 = __reduce_add_sync(0xffffffffu, n64);
+    const unsigned a32 = __reduce_add_sync(full, n32), a64 = __reduce_add_sync(full, n64);
     if (lane == 0) {
       if (a32) atomicAdd(&A.fpstat[0], (unsigned long long)a32);
       if (a64) atomicAdd(&A.fpstat[1], (unsigned long long)a64);
@@ -1074,8 +1135,8 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     CB_TRY(buf_ensure(w.flat_bits, sizeof(uint32_t) * (size_t)std::max<uint64_t>(1, (flat_t + 31) / 32), st));
     if (flat_t > 0) {
       const int64_t chunks = (int64_t)((flat_t + 32ull * FLAT_STEPS - 1) / (32ull * FLAT_STEPS));
-      const int64_t g = std::min<int64_t>((chunks + 7) / 8, (int64_t)s->n_sms * 8);
-      k_pairs_flat<<<(int)g, 256, 0, cb_count(st)>>>(A, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_lidx),
+      const int64_t g = std::min<int64_t>((chunks + FLAT_WARPS - 1) / FLAT_WARPS, (int64_t)s->n_sms * 8);
+      k_pairs_flat<<<(int)g, 32 * FLAT_WARPS, 0, cb_count(st)>>>(A, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_lidx),
                                                     bp<uint32_t>(w.flat_j0), flat_t, bp<uint32_t>(w.flat_bits));
     }
     k_flat_count<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_lflag),
