@@ -637,7 +637,8 @@ __global__ void k_flat_compact(int64_t ne, const uint32_t* __restrict__ lflag, c
 struct FlatEntry {
   int pv[3];
   float4 plo, phi;
-  uint32_t P, cell;
+  uint32_t P;
+  int cx, cy, cz;  // the cell's coordinates (its Morton code decoded)
   Grid G;
 };
 
@@ -647,7 +648,10 @@ __device__ __forceinline__ void flat_load(const PairArgs& A, int64_t i, FlatEntr
   E.plo = A.ebox[2 * (size_t)i];
   E.phi = A.ebox[2 * (size_t)i + 1];
   const uint64_t kc = A.ekey[i] >> A.shift;
-  E.cell = (uint32_t)(kc & 0x3fffffffull);
+  const uint32_t cell = (uint32_t)(kc & 0x3fffffffull);
+  E.cx = morton_x(cell);
+  E.cy = morton_x(cell >> 1);
+  E.cz = morton_x(cell >> 2);
   E.G = A.grids[kc >> 30];
 }
 
@@ -662,10 +666,10 @@ __device__ __forceinline__ bool box_overlap(const float4& plo, const float4& phi
 __device__ __forceinline__ bool flat_rest(const PairArgs& A, const FlatEntry& E, const float4& qlo,
                                           const float4& qhi, int j, uint32_t& n32, uint32_t& n64) {
   const Grid& G = E.G;
-  const uint32_t hc = morton(cell_of(fmaxf(E.plo.x, qlo.x), G.ox, G.inv, G.dx),
-                             cell_of(fmaxf(E.plo.y, qlo.y), G.oy, G.inv, G.dy),
-                             cell_of(fmaxf(E.plo.z, qlo.z), G.oz, G.inv, G.dz));
-  if (hc != E.cell) return false;
+  if (cell_of(fmaxf(E.plo.x, qlo.x), G.ox, G.inv, G.dx) != E.cx ||
+      cell_of(fmaxf(E.plo.y, qlo.y), G.oy, G.inv, G.dy) != E.cy ||
+      cell_of(fmaxf(E.plo.z, qlo.z), G.oz, G.inv, G.dz) != E.cz)
+    return false;
   const uint32_t Q = A.eval[j];
   int qv[3];
   prim_verts(A.t, (int)Q, qv);
@@ -689,91 +693,13 @@ __device__ __forceinline__ bool flat_rest(const PairArgs& A, const FlatEntry& E,
   return acc;
 }
 
-// the whole test of entry E against partner j
-__device__ __forceinline__ bool flat_test(const PairArgs& A, const FlatEntry& E, int j, uint32_t& n32,
-                                          uint32_t& n64) {
-  const float4 qlo = A.ebox[2 * (size_t)j], qhi = A.ebox[2 * (size_t)j + 1];
-  return box_overlap(E.plo, E.phi, qlo, qhi) && flat_rest(A, E, qlo, qhi, j, n32, n64);
-}
-
-// Entries with short ranges, a warp per 32 consecutive entries: the warp
-// scans their lengths (with shuffles) and lays their partners end to end, and
-// each step tests 32 of those (entry, partner) slots, lane l the slot
-// base + l -- its entry is the last lane whose range starts at or before the
-// slot (a search over the lanes' starts), whose data the lane takes by
-// shuffles.  Hit bit b of an entry's word is its partner j0 + b.
-__global__ void __launch_bounds__(256) k_pairs_short(PairArgs A, const uint8_t* __restrict__ slen,
-                                                     const uint32_t* __restrict__ j0s,
-                                                     uint32_t* __restrict__ sbits) {
-  __shared__ uint32_t sw[256];  // the hit word of each entry of the block
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = i < A.ne ? (int)slen[i] : 0;
-  sw[threadIdx.x] = 0u;
-  int inc = n;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int v = __shfl_up_sync(full, inc, o);
-    if (lane >= o) inc += v;
-  }
-  const int ex = inc - n;                        // this entry's first slot
-  const int total = __shfl_sync(full, inc, 31);  // slots of the warp's entries
-  FlatEntry E{};
-  int j0 = 0;
-  if (n > 0) {
-    flat_load(A, i, E);
-    j0 = (int)j0s[i];
-  }
-  uint32_t n32 = 0, n64 = 0;
-  __syncwarp();
-  for (int base = 0; base < total; base += 32) {
-    const int sl = base + lane;
-    int e = 0;  // the last lane whose range starts at or before sl
-#pragma unroll
-    for (int bit = 16; bit > 0; bit >>= 1) {
-      const int c = e + bit;
-      if (__shfl_sync(full, ex, c) <= sl) e = c;
-    }
-    FlatEntry F;
-    F.P = __shfl_sync(full, E.P, e);
-    F.cell = __shfl_sync(full, E.cell, e);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) F.pv[k] = __shfl_sync(full, E.pv[k], e);
-    F.plo = make_float4(__shfl_sync(full, E.plo.x, e), __shfl_sync(full, E.plo.y, e),
-                        __shfl_sync(full, E.plo.z, e), 0.f);
-    F.phi = make_float4(__shfl_sync(full, E.phi.x, e), __shfl_sync(full, E.phi.y, e),
-                        __shfl_sync(full, E.phi.z, e), 0.f);
-    F.G.ox = __shfl_sync(full, E.G.ox, e);
-    F.G.oy = __shfl_sync(full, E.G.oy, e);
-    F.G.oz = __shfl_sync(full, E.G.oz, e);
-    F.G.inv = __shfl_sync(full, E.G.inv, e);
-    F.G.dx = __shfl_sync(full, E.G.dx, e);
-    F.G.dy = __shfl_sync(full, E.G.dy, e);
-    F.G.dz = __shfl_sync(full, E.G.dz, e);
-    const int b = sl - __shfl_sync(full, ex, e);
-    const int j = __shfl_sync(full, j0, e) + b;
-    if (sl < total && flat_test(A, F, j, n32, n64)) atomicOr(&sw[(threadIdx.x & ~31) + e], 1u << b);
-  }
-  __syncwarp();
-  if (i < A.ne) sbits[i] = sw[threadIdx.x];
-  if (A.fpstat) {
-    const unsigned a32 = __reduce_add_sync(full, n32), a64 = __reduce_add_sync(full, n64);
-    if (lane == 0) {
-      if (a32) atomicAdd(&A.fpstat[0], (unsigned long long)a32);
-      if (a64) atomicAdd(&A.fpstat[1], (unsigned long long)a64);
-    }
-  }
-}
-
-// hit bits of slots [0, T): word w holds slots 32 w .. 32 w + 31 (grid-stride
-// over chunks of FLAT_STEPS = 32 words, one warp per chunk).  Most slots fail
-// the box test, and a warp whose lanes disagree runs the longer rest of the
-// test (home cell, shared vertices, FP32 margins) for all of them, so the two
-// are split: each step's box overlaps go to a small queue in shared memory,
-// and the rest of the test runs 32 queued slots at a time with every lane
-// busy (the remainder at the chunk's end); hits set bits of the chunk's 32
-// words in shared memory.
+// The box test is cheap and most slots fail it, while the rest of the test
+// (home cell, shared vertices, FP32 margins) is long, and a warp whose lanes
+// disagree runs it for all of them.  So both pair kernels split the two:
+// each step's box overlaps go to a small per-warp queue in shared memory
+// (entry, partner, and the hit bit to set: word t >> 5, bit t & 31 of a
+// per-warp array), and the rest of the test runs 32 queued slots at a time
+// with every lane busy, the remainder at the end.
 constexpr int FLAT_WARPS = 8;  // warps per block of k_pairs_flat
 static_assert(FLAT_STEPS == 32, "one hit word per lane at the end of a chunk");
 
@@ -791,6 +717,92 @@ __device__ __forceinline__ void flat_batch(const PairArgs& A, const uint32_t* qi
   if (flat_rest(A, E, qlo, qhi, (int)j, n32, n64)) atomicOr(&cw[sl >> 5], 1u << (sl & 31));
 }
 
+// Entries with short ranges, a warp per 32 consecutive entries: the warp
+// scans their lengths (with shuffles) and lays their partners end to end, and
+// each step tests 32 of those (entry, partner) slots, lane l the slot
+// base + l -- its entry is the last lane whose range starts at or before the
+// slot (a search over the lanes' starts), whose data the lane takes by
+// shuffles.  Hit bit b of an entry's word is its partner j0 + b.
+__global__ void __launch_bounds__(32 * FLAT_WARPS) k_pairs_short(PairArgs A, const uint8_t* __restrict__ slen,
+                                                                 const uint32_t* __restrict__ j0s,
+                                                                 uint32_t* __restrict__ sbits) {
+  __shared__ uint32_t s_qi[FLAT_WARPS][64], s_qj[FLAT_WARPS][64], s_sw[FLAT_WARPS][32];
+  __shared__ uint16_t s_qs[FLAT_WARPS][64];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
+  uint32_t* qi = s_qi[wb];
+  uint32_t* qj = s_qj[wb];
+  uint16_t* qs = s_qs[wb];
+  uint32_t* sw = s_sw[wb];  // the hit word of each entry of the warp
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i0 = i - lane;
+  const int n = i < A.ne ? (int)slen[i] : 0;
+  sw[lane] = 0u;
+  int inc = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(full, inc, o);
+    if (lane >= o) inc += v;
+  }
+  const int ex = inc - n;                        // this entry's first slot
+  const int total = __shfl_sync(full, inc, 31);  // slots of the warp's entries
+  float4 plo = make_float4(0.f, 0.f, 0.f, 0.f), phi = plo;
+  int j0 = 0;
+  if (n > 0) {
+    plo = A.ebox[2 * (size_t)i];
+    phi = A.ebox[2 * (size_t)i + 1];
+    j0 = (int)j0s[i];
+  }
+  uint32_t n32 = 0, n64 = 0;
+  int qn = 0;
+  __syncwarp();
+  for (int base = 0; base < total; base += 32) {
+    const int sl = base + lane;
+    int e = 0;  // the last lane whose range starts at or before sl
+#pragma unroll
+    for (int bit = 16; bit > 0; bit >>= 1) {
+      const int c = e + bit;
+      if (__shfl_sync(full, ex, c) <= sl) e = c;
+    }
+    const float4 elo = make_float4(__shfl_sync(full, plo.x, e), __shfl_sync(full, plo.y, e),
+                                   __shfl_sync(full, plo.z, e), 0.f);
+    const float4 ehi = make_float4(__shfl_sync(full, phi.x, e), __shfl_sync(full, phi.y, e),
+                                   __shfl_sync(full, phi.z, e), 0.f);
+    const int b = sl - __shfl_sync(full, ex, e);
+    const int j = __shfl_sync(full, j0, e) + b;
+    const bool pass =
+        sl < total && box_overlap(elo, ehi, A.ebox[2 * (size_t)j], A.ebox[2 * (size_t)j + 1]);
+    const unsigned m = __ballot_sync(full, pass);
+    if (pass) {
+      const int at = qn + __popc(m & below);
+      qi[at] = (uint32_t)(i0 + e);
+      qj[at] = (uint32_t)j;
+      qs[at] = (uint16_t)(32 * e + b);
+    }
+    qn += __popc(m);
+    __syncwarp();
+    if (qn >= 32) {
+      flat_batch(A, qi, qj, qs, qn - 32, 32, sw, n32, n64);
+      qn -= 32;
+      __syncwarp();
+    }
+  }
+  if (qn > 0) flat_batch(A, qi, qj, qs, 0, qn, sw, n32, n64);
+  __syncwarp();
+  if (i < A.ne) sbits[i] = sw[lane];
+  if (A.fpstat) {
+    const unsigned a32 = __reduce_add_sync(full, n32), a64 = __reduce_add_sync(full, n64);
+    if (lane == 0) {
+      if (a32) atomicAdd(&A.fpstat[0], (unsigned long long)a32);
+      if (a64) atomicAdd(&A.fpstat[1], (unsigned long long)a64);
+    }
+  }
+}
+
+// hit bits of slots [0, T): word w holds slots 32 w .. 32 w + 31 (grid-stride
+// over chunks of FLAT_STEPS = 32 words, one warp per chunk); the queued rest
+// of the test sets bits of the chunk's 32 words in shared memory
 __global__ void __launch_bounds__(32 * FLAT_WARPS) k_pairs_flat(PairArgs A, const uint64_t* __restrict__ toff,
                                                                 const uint32_t* __restrict__ lidx,
                                                                 const uint32_t* __restrict__ j0s, uint64_t T,
@@ -1119,8 +1131,8 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     k_flat_ranges<<<cb_grid(ne + 1), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint32_t>(w.flat_len),
                                                                     bp<uint32_t>(w.flat_lflag), bp<uint8_t>(w.flat_slen),
                                                                     bp<uint32_t>(w.flat_j0));
-    k_pairs_short<<<cb_grid(ne, 256), 256, 0, cb_count(st)>>>(A, bp<uint8_t>(w.flat_slen), bp<uint32_t>(w.flat_j0),
-                                                             bp<uint32_t>(w.flat_sbits));
+    k_pairs_short<<<cb_grid(ne, 32 * FLAT_WARPS), 32 * FLAT_WARPS, 0, cb_count(st)>>>(
+        A, bp<uint8_t>(w.flat_slen), bp<uint32_t>(w.flat_j0), bp<uint32_t>(w.flat_sbits));
     // the long entries in entry order, their ranges laid end to end
     cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.flat_lflag), bp<uint32_t>(w.flat_lpos), ne + 1,
                                             bp<uint32_t>(w.scan_tmp), (uint32_t*)nullptr, st);
