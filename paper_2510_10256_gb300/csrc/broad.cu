@@ -693,13 +693,14 @@ __device__ __forceinline__ bool flat_rest(const PairArgs& A, const FlatEntry& E,
   return acc;
 }
 
-// The box test is cheap and most slots fail it, while the rest of the test
-// (home cell, shared vertices, FP32 margins) is long, and a warp whose lanes
-// disagree runs it for all of them.  So both pair kernels split the two:
-// each step's box overlaps go to a small per-warp queue in shared memory
-// (entry, partner, and the hit bit to set: word t >> 5, bit t & 31 of a
-// per-warp array), and the rest of the test runs 32 queued slots at a time
-// with every lane busy, the remainder at the end.
+// The box test is cheap, while the rest of the test (home cell, shared
+// vertices, FP32 margins) is long, and a warp whose lanes disagree runs it
+// for all of them.  So the end-to-end kernel splits the two: each step's box
+// overlaps go to a small per-warp queue in shared memory (entry, partner,
+// and the hit bit to set: word t >> 5, bit t & 31 of a per-warp array), and
+// the rest of the test runs 32 queued slots at a time with every lane busy,
+// the remainder at the end.  (The same split in the short-range kernel
+// measured slower: its lanes already take their entries' data by shuffles.)
 constexpr int FLAT_WARPS = 8;  // warps per block of k_pairs_flat
 static_assert(FLAT_STEPS == 32, "one hit word per lane at the end of a chunk");
 
@@ -717,28 +718,28 @@ __device__ __forceinline__ void flat_batch(const PairArgs& A, const uint32_t* qi
   if (flat_rest(A, E, qlo, qhi, (int)j, n32, n64)) atomicOr(&cw[sl >> 5], 1u << (sl & 31));
 }
 
+// the whole test of entry E against partner j
+__device__ __forceinline__ bool flat_test(const PairArgs& A, const FlatEntry& E, int j, uint32_t& n32,
+                                          uint32_t& n64) {
+  const float4 qlo = A.ebox[2 * (size_t)j], qhi = A.ebox[2 * (size_t)j + 1];
+  return box_overlap(E.plo, E.phi, qlo, qhi) && flat_rest(A, E, qlo, qhi, j, n32, n64);
+}
+
 // Entries with short ranges, a warp per 32 consecutive entries: the warp
 // scans their lengths (with shuffles) and lays their partners end to end, and
 // each step tests 32 of those (entry, partner) slots, lane l the slot
 // base + l -- its entry is the last lane whose range starts at or before the
 // slot (a search over the lanes' starts), whose data the lane takes by
 // shuffles.  Hit bit b of an entry's word is its partner j0 + b.
-__global__ void __launch_bounds__(32 * FLAT_WARPS) k_pairs_short(PairArgs A, const uint8_t* __restrict__ slen,
-                                                                 const uint32_t* __restrict__ j0s,
-                                                                 uint32_t* __restrict__ sbits) {
-  __shared__ uint32_t s_qi[FLAT_WARPS][64], s_qj[FLAT_WARPS][64], s_sw[FLAT_WARPS][32];
-  __shared__ uint16_t s_qs[FLAT_WARPS][64];
+__global__ void __launch_bounds__(256) k_pairs_short(PairArgs A, const uint8_t* __restrict__ slen,
+                                                     const uint32_t* __restrict__ j0s,
+                                                     uint32_t* __restrict__ sbits) {
+  __shared__ uint32_t sw[256];  // the hit word of each entry of the block
   const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
-  const unsigned below = (1u << lane) - 1u;
-  uint32_t* qi = s_qi[wb];
-  uint32_t* qj = s_qj[wb];
-  uint16_t* qs = s_qs[wb];
-  uint32_t* sw = s_sw[wb];  // the hit word of each entry of the warp
+  const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i0 = i - lane;
   const int n = i < A.ne ? (int)slen[i] : 0;
-  sw[lane] = 0u;
+  sw[threadIdx.x] = 0u;
   int inc = n;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -747,15 +748,13 @@ __global__ void __launch_bounds__(32 * FLAT_WARPS) k_pairs_short(PairArgs A, con
   }
   const int ex = inc - n;                        // this entry's first slot
   const int total = __shfl_sync(full, inc, 31);  // slots of the warp's entries
-  float4 plo = make_float4(0.f, 0.f, 0.f, 0.f), phi = plo;
+  FlatEntry E{};
   int j0 = 0;
   if (n > 0) {
-    plo = A.ebox[2 * (size_t)i];
-    phi = A.ebox[2 * (size_t)i + 1];
+    flat_load(A, i, E);
     j0 = (int)j0s[i];
   }
   uint32_t n32 = 0, n64 = 0;
-  int qn = 0;
   __syncwarp();
   for (int base = 0; base < total; base += 32) {
     const int sl = base + lane;
@@ -765,32 +764,30 @@ __global__ void __launch_bounds__(32 * FLAT_WARPS) k_pairs_short(PairArgs A, con
       const int c = e + bit;
       if (__shfl_sync(full, ex, c) <= sl) e = c;
     }
-    const float4 elo = make_float4(__shfl_sync(full, plo.x, e), __shfl_sync(full, plo.y, e),
-                                   __shfl_sync(full, plo.z, e), 0.f);
-    const float4 ehi = make_float4(__shfl_sync(full, phi.x, e), __shfl_sync(full, phi.y, e),
-                                   __shfl_sync(full, phi.z, e), 0.f);
+    FlatEntry F;
+    F.P = __shfl_sync(full, E.P, e);
+    F.cx = __shfl_sync(full, E.cx, e);
+    F.cy = __shfl_sync(full, E.cy, e);
+    F.cz = __shfl_sync(full, E.cz, e);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) F.pv[k] = __shfl_sync(full, E.pv[k], e);
+    F.plo = make_float4(__shfl_sync(full, E.plo.x, e), __shfl_sync(full, E.plo.y, e),
+                        __shfl_sync(full, E.plo.z, e), 0.f);
+    F.phi = make_float4(__shfl_sync(full, E.phi.x, e), __shfl_sync(full, E.phi.y, e),
+                        __shfl_sync(full, E.phi.z, e), 0.f);
+    F.G.ox = __shfl_sync(full, E.G.ox, e);
+    F.G.oy = __shfl_sync(full, E.G.oy, e);
+    F.G.oz = __shfl_sync(full, E.G.oz, e);
+    F.G.inv = __shfl_sync(full, E.G.inv, e);
+    F.G.dx = __shfl_sync(full, E.G.dx, e);
+    F.G.dy = __shfl_sync(full, E.G.dy, e);
+    F.G.dz = __shfl_sync(full, E.G.dz, e);
     const int b = sl - __shfl_sync(full, ex, e);
     const int j = __shfl_sync(full, j0, e) + b;
-    const bool pass =
-        sl < total && box_overlap(elo, ehi, A.ebox[2 * (size_t)j], A.ebox[2 * (size_t)j + 1]);
-    const unsigned m = __ballot_sync(full, pass);
-    if (pass) {
-      const int at = qn + __popc(m & below);
-      qi[at] = (uint32_t)(i0 + e);
-      qj[at] = (uint32_t)j;
-      qs[at] = (uint16_t)(32 * e + b);
-    }
-    qn += __popc(m);
-    __syncwarp();
-    if (qn >= 32) {
-      flat_batch(A, qi, qj, qs, qn - 32, 32, sw, n32, n64);
-      qn -= 32;
-      __syncwarp();
-    }
+    if (sl < total && flat_test(A, F, j, n32, n64)) atomicOr(&sw[(threadIdx.x & ~31) + e], 1u << b);
   }
-  if (qn > 0) flat_batch(A, qi, qj, qs, 0, qn, sw, n32, n64);
   __syncwarp();
-  if (i < A.ne) sbits[i] = sw[lane];
+  if (i < A.ne) sbits[i] = sw[threadIdx.x];
   if (A.fpstat) {
     const unsigned a32 = __reduce_add_sync(full, n32), a64 = __reduce_add_sync(full, n64);
     if (lane == 0) {
@@ -1131,8 +1128,8 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
     k_flat_ranges<<<cb_grid(ne + 1), CB_THREADS, 0, cb_count(st)>>>(A, bp<uint32_t>(w.flat_len),
                                                                     bp<uint32_t>(w.flat_lflag), bp<uint8_t>(w.flat_slen),
                                                                     bp<uint32_t>(w.flat_j0));
-    k_pairs_short<<<cb_grid(ne, 32 * FLAT_WARPS), 32 * FLAT_WARPS, 0, cb_count(st)>>>(
-        A, bp<uint8_t>(w.flat_slen), bp<uint32_t>(w.flat_j0), bp<uint32_t>(w.flat_sbits));
+    k_pairs_short<<<cb_grid(ne, 256), 256, 0, cb_count(st)>>>(A, bp<uint8_t>(w.flat_slen), bp<uint32_t>(w.flat_j0),
+                                                             bp<uint32_t>(w.flat_sbits));
     // the long entries in entry order, their ranges laid end to end
     cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(w.flat_lflag), bp<uint32_t>(w.flat_lpos), ne + 1,
                                             bp<uint32_t>(w.scan_tmp), (uint32_t*)nullptr, st);
