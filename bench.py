@@ -38,12 +38,12 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 # point-edge pair in its own frame; k_hess_proj<6> (generic point-edge pairs,
 # none in that capture) is scaled from k_hess_proj<9> by (6/9)^3.
 HESS_FLOPS = {"prep": 549.1, "face": 11471.0, "pe_frame": 1091.0, "pe": 11471.0 * (6 / 9) ** 3}
-# DRAM bytes (read + write) of the stage-(d) kernels per active pair, taken
-# at full size (256x256 sheet, 805,423 active pairs): k_hess_proj_pe 270.1 MB,
-# k_hess_proj<9> 192.4 MB, k_hess_proj<6> 0.07 MB, k_hess_prep 288.5 MB
-HESS_DRAM_BYTES_PER_ACTIVE = (270.1e6 + 192.4e6 + 0.07e6 + 288.5e6) / 805423
-HESS_TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of one 256x256 pass (the projections: the current build; "
-                       "k_hess_prep: an earlier capture of the same, unchanged kernel), per active pair")
+# DRAM bytes (read + write) of the stage-(d) kernels per active pair, from one
+# ncu capture of a full-size pass (256x256 sheet, 805,423 active pairs):
+# k_hess_prep 289.1 MB, k_hess_proj_pe 266.8 MB, k_hess_proj<9> 191.5 MB,
+# k_hess_proj<6> 0.1 MB
+HESS_DRAM_BYTES_PER_ACTIVE = 747.48e6 / 805423
+HESS_TRAFFIC_SOURCE = "ncu dram__bytes_read+write of the four stage-(d) kernels of one 256x256 pass, per active pair"
 
 
 def hess_flops(st) -> float:
