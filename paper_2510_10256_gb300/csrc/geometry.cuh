@@ -63,6 +63,18 @@ __device__ __forceinline__ int seg_region(d3 q, d3 e0, d3 e1) {
   return 2;
 }
 
+// squared distance of q to segment e0 e1 given its region r (0: e0, 1: e1,
+// 2: interior): the point-point value on the selected end (d2_pp is symmetric
+// bit for bit: b - a and a - b differ only in sign), the point-edge value
+// computed only when some lane of the warp needs it, so the lanes of a warp
+// run one instruction stream whatever their regions
+__device__ __forceinline__ double seg_d2(d3 q, d3 e0, d3 e1, int r) {
+  const double dpp = d2_pp(q, r == 0 ? e0 : e1);
+  double dpe = dpp;
+  if (__any_sync(__activemask(), r == 2)) dpe = d2_pe(q, e0, e1);
+  return r == 2 ? dpe : dpp;
+}
+
 __device__ __forceinline__ void take_min(int& bt, double& bd, int t, double d2) {
   if (d2 < bd || (d2 == bd && t < bt)) {
     bt = t;
@@ -132,13 +144,13 @@ __device__ __forceinline__ int pt_type(const Local& L, double& d2) {
   int r, t;
   r = seg_region(Q, T0, T1);
   t = (r == 0) ? 0 : (r == 1) ? 1 : 3;
-  take_min(bt, bd, t, pt_d2(L, t));
+  take_min(bt, bd, t, seg_d2(Q, T0, T1, r));
   r = seg_region(Q, T1, T2);
   t = (r == 0) ? 1 : (r == 1) ? 2 : 4;
-  take_min(bt, bd, t, pt_d2(L, t));
+  take_min(bt, bd, t, seg_d2(Q, T1, T2, r));
   r = seg_region(Q, T2, T0);
   t = (r == 0) ? 2 : (r == 1) ? 0 : 5;
-  take_min(bt, bd, t, pt_d2(L, t));
+  take_min(bt, bd, t, seg_d2(Q, T2, T0, r));
   d2 = bd;
   return bt;
 }
@@ -162,16 +174,16 @@ __device__ __forceinline__ int ee_type(const Local& L, double& d2) {
   int r, t;
   r = seg_region(A0, B0, B1);
   t = (r == 0) ? 0 : (r == 1) ? 1 : 4;
-  take_min(bt, bd, t, ee_d2(L, t));
+  take_min(bt, bd, t, seg_d2(A0, B0, B1, r));
   r = seg_region(A1, B0, B1);
   t = (r == 0) ? 2 : (r == 1) ? 3 : 5;
-  take_min(bt, bd, t, ee_d2(L, t));
+  take_min(bt, bd, t, seg_d2(A1, B0, B1, r));
   r = seg_region(B0, A0, A1);
   t = (r == 0) ? 0 : (r == 1) ? 2 : 6;
-  take_min(bt, bd, t, ee_d2(L, t));
+  take_min(bt, bd, t, seg_d2(B0, A0, A1, r));
   r = seg_region(B1, A0, A1);
   t = (r == 0) ? 1 : (r == 1) ? 3 : 7;
-  take_min(bt, bd, t, ee_d2(L, t));
+  take_min(bt, bd, t, seg_d2(B1, A0, A1, r));
   d2 = bd;
   return bt;
 }
