@@ -25,7 +25,8 @@ candidates kept at their own width), paper_literal (activation = thickness,
 offset = thickness - dhat); rod scenes may mark closed loops
 (scene.rod_closed: reference distances the shorter way round); shell
 scenes may carry the flat pattern they are cut from (scene.rest_uv:
-reference distances taken there).  Lagged
+reference distances taken there) or ask for geodesic reference distances on
+the rest mesh (scene.rest_geodesic, geodesic.c).  Lagged
 friction on the active pairs: oracle/friction.py.
 
 Pins: tests/test_oracle_*.py.  parity pinned for every function exported here.
@@ -42,6 +43,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = (_SRC, os.path.join(_HERE, "geodesic.c"))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -55,11 +57,11 @@ ACCD_MAX_ITER = 10000
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c with the system gcc (OpenMP, no FP contraction)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    """Compile oracle.c and geodesic.c with the system gcc (OpenMP, no FP contraction)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(map(os.path.getmtime, _SRCS)):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+                               "-fPIC", "-shared", "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -104,6 +106,10 @@ def lib():
         L.orc_accd.argtypes = [i32, vp, vp, dbl, dbl, dbl, dbl, i32, C.POINTER(dbl), C.POINTER(i32)]
         L.orc_stencil.restype = i32
         L.orc_stencil.argtypes = [C.POINTER(_Topo), C.c_uint64, vp]
+        L.orc_geo_source.restype = i32
+        L.orc_geo_source.argtypes = [C.POINTER(_Topo), vp, dbl, i32, vp, vp]
+        L.orc_geo_rest_filter.restype = i64
+        L.orc_geo_rest_filter.argtypes = [C.POINTER(_Topo), vp, dbl, C.POINTER(vp), C.POINTER(vp)]
         L.orc_num_threads.restype = i32
         L.orc_set_num_threads.argtypes = [i32]
         _lib = L
@@ -295,10 +301,36 @@ def arclength(scene) -> np.ndarray:
     return S
 
 
+def geodesic_from(scene, src: int, a: float, topo: Topology | None = None) -> tuple[np.ndarray, np.ndarray]:
+    """Geodesic distances on a shell's rest mesh from vertex src (geodesic.c):
+    to every vertex (n,) and to every edge (E,), below a, +inf elsewhere."""
+    topo = topo or topology(scene)
+    tc = topo.ctype()
+    rest = np.ascontiguousarray(scene.rest, np.float64)
+    dv, de = np.zeros(topo.n), np.zeros(topo.edges.shape[1])
+    rc = lib().orc_geo_source(C.byref(tc), _ptr(rest), float(a), int(src), _ptr(dv), _ptr(de))
+    if rc != 0:
+        raise ValueError("geodesic: non-manifold mesh" if rc == -1 else "geodesic: strip too long")
+    return dv, de
+
+
+def _geodesic_rest_filter(scene, topo: Topology, a: float) -> tuple[np.ndarray, np.ndarray]:
+    tc = topo.ctype()
+    rest = np.ascontiguousarray(scene.rest, np.float64)
+    ok, od = C.c_void_p(), C.c_void_p()
+    m = lib().orc_geo_rest_filter(C.byref(tc), _ptr(rest), float(a), C.byref(ok), C.byref(od))
+    if m < 0:
+        raise ValueError("geodesic: non-manifold mesh" if m == -1 else "geodesic: strip too long")
+    return _take(ok, m, np.uint64), _take(od, m, np.float64)
+
+
 def rest_filter(scene, topo: Topology, a: float) -> tuple[np.ndarray, np.ndarray]:
     """Filtered stencil pairs (same component, dbar < a) and their dbar."""
     if topo.kind == 0 and topo.loop_ne is not None and np.any(topo.loop_ne > 0):
         return _rod_rest_filter_loops(scene, topo, a)
+    if topo.kind == 1 and getattr(scene, "rest_geodesic", False):
+        # a doubly curved rest shell: geodesic distances on the rest mesh
+        return _geodesic_rest_filter(scene, topo, a)
     tc = topo.ctype()
     rest = np.ascontiguousarray(scene.rest, np.float64)
     if topo.kind == 1 and getattr(scene, "rest_uv", None) is not None:

@@ -43,6 +43,7 @@ class Scene:
     meta: dict = field(default_factory=dict)
     rod_closed: np.ndarray | None = None  # uint8 (n_rods,) for rods: 1 = closed loop (last vertex joins the first)
     rest_uv: np.ndarray | None = None     # (2, n) for shells: the flat pattern the rest shape is made from
+    rest_geodesic: bool = False           # shells: reference distances are geodesic distances on the rest mesh
 
     @property
     def n(self) -> int:
