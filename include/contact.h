@@ -81,6 +81,18 @@ typedef enum {
                                        component's), overlap (closed intervals).  A dropped pair is farther
                                        apart than its width, so no barrier value changes; the candidate set
                                        shrinks.  The CCD candidates are unaffected. */
+#define CB_DBAR_GEODESIC 128        /* shells whose rest shape is not cut from a flat pattern (doubly curved):
+                                       the reference distance of a stencil pair (Sec. 3.2's rest-domain
+                                       distance; the paper leaves non-flat rest shapes to future work) is
+                                       the shortest-path distance between its two primitives on the
+                                       polyhedral rest mesh -- exact up to rounding, for distances below the
+                                       activation a (only those decide the filter).  On a flat convex
+                                       sheet, or a sheet isometric to a convex pattern, it equals the
+                                       pattern distance.  Shells only, not with rest_uv, and the mesh must
+                                       be a manifold (at most two faces per edge): else CB_ERR_ARG.  Each
+                                       vertex's geodesic ball of radius a must hold at most 192 vertices
+                                       and 384 edges, and each straight strip at most 64 open branches:
+                                       else cb_scene_create returns CB_ERR_TOO_LARGE. */
 #define CB_EE_MOLLIFIER 32          /* IPC's edge-edge mollifier (App. A: the paper's solver uses IPC's
                                        contact energy): an edge-edge pair's energy is m(c) kappa b with
                                        c = |e0 x e1|^2, m = -c^2/eps_x^2 + 2c/eps_x below eps_x =
@@ -130,7 +142,7 @@ typedef struct {
   double dhat;                /* barrier width; full activation a = thickness + dhat */
   double kappa;               /* barrier stiffness (energy scale); 1 if <= 0 */
   int32_t mode;               /* CB_FILTER_* | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP | CB_DBAR_PER_COMPONENT
-                                 | CB_EE_MOLLIFIER | CB_PER_STENCIL */
+                                 | CB_EE_MOLLIFIER | CB_PER_STENCIL | CB_DBAR_GEODESIC */
   int32_t cull_radius;        /* CB_FILTER_KALDOR: culling radius in edges (>= 1); else ignored */
   const uint8_t* rod_closed;  /* rods, HOST [n_rods] or NULL: 1 = closed loop (an edge from the last vertex
                                  back to the first, numbered after the polyline's others; >= 3 vertices,
@@ -300,6 +312,9 @@ int32_t cb_member_count(cb_scene* scene);
 /* sync getters.  Each copies to HOST buffers of capacity `cap` elements and
  * writes the full count to *count (CB_ERR_CAPACITY if cap is too small). */
 cb_status cb_get_pairs(cb_scene* scene, int32_t which, uint64_t* keys, int64_t cap, int64_t* count);
+/* shells: the rest-filtered stencil pairs (the filtered set F of Sec. 3.2) in key order and their
+ * reference distances dbar; either output may be NULL.  Rods: CB_ERR_ARG. */
+cb_status cb_get_rest_filter(cb_scene* scene, uint64_t* keys, double* dbar, int64_t cap, int64_t* count);
 /* active pairs in key order: key, distance, class (0 U, 1 F, 2 C), distance type */
 cb_status cb_get_active(cb_scene* scene, uint64_t* keys, double* d, uint8_t* klass, int8_t* dtype,
                         int64_t cap, int64_t* count);

@@ -13,7 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcontact.so")
-SOURCES = ["api.cu", "broad.cu", "narrow.cu", "ccd.cu", "peaks.cu", "spmv.cu", "friction.cu", "server.cu"]
+SOURCES = ["api.cu", "broad.cu", "narrow.cu", "ccd.cu", "peaks.cu", "spmv.cu", "friction.cu", "server.cu",
+           "geodesic.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # a non-void function (or lambda) that can fall off its end is an error, not a
 # warning: in the CUDA front end (diagnostic 940) and in the host compiler

@@ -25,6 +25,7 @@ CB_NO_CORE_TEMP = 8
 CB_DBAR_PER_COMPONENT = 16
 CB_EE_MOLLIFIER = 32
 CB_PER_STENCIL = 64
+CB_DBAR_GEODESIC = 128
 PAIRS = {"candidate": 0, "filtered": 1, "core": 2, "active": 3, "ccd": 4, "rest_filtered": 5}
 MODES = {"double": CB_FILTER_DOUBLE, "single": CB_FILTER_SINGLE, "off": CB_FILTER_OFF, "kaldor": CB_FILTER_KALDOR}
 
@@ -36,7 +37,7 @@ ABI_FUNCTIONS = ["cb_scene_create", "cb_scene_destroy", "contact_build", "contac
                  "cb_batch_offsets", "cb_member_count", "ccd_step_noalloc", "cb_set_tuning",
                  "cb_get_tuning", "barrier_energy", "cb_bsr_spmv", "friction_lag", "friction_eval",
                  "friction_spmv", "cb_get_friction", "cb_server_create", "cb_server_destroy", "cb_batch_admit",
-                 "cb_batch_release", "cb_batch_pass", "cb_server_stats", "cb_scene_reserve"]
+                 "cb_batch_release", "cb_batch_pass", "cb_server_stats", "cb_scene_reserve", "cb_get_rest_filter"]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -159,6 +160,7 @@ def lib():
         L.cb_get_friction.argtypes = [vp, vp, vp, vp, i64, C.POINTER(i64)]
         L.ccd_step.argtypes = [vp, vp, vp, vp, vp]
         L.cb_get_pairs.argtypes = [vp, i32, vp, i64, C.POINTER(i64)]
+        L.cb_get_rest_filter.argtypes = [vp, vp, vp, i64, C.POINTER(i64)]
         L.cb_get_active.argtypes = [vp, vp, vp, vp, vp, i64, C.POINTER(i64)]
         L.cb_get_ccd.argtypes = [vp, vp, vp, vp, i64, C.POINTER(i64)]
         L.cb_get_bsr.argtypes = [vp, vp, vp, vp, i64, C.POINTER(i64)]
@@ -263,8 +265,8 @@ class ContactScene:
     def __init__(self, kind: str, rest, thickness: float, dhat: float, rod_ptr=None, tris=None,
                  kappa: float = 1.0, mode: str = "double", paper_literal: bool = False,
                  core_temp: bool = True, cull_radius: int = 0, per_component: bool = False, rod_closed=None,
-                 mollifier: bool = False, rest_uv=None, per_stencil: bool = False, stream=None,
-                 allocator="torch"):
+                 mollifier: bool = False, rest_uv=None, per_stencil: bool = False, rest_geodesic: bool = False,
+                 stream=None, allocator="torch"):
         L = lib()
         rest = np.ascontiguousarray(np.asarray(rest, np.float64).reshape(3, -1))
         self.n = rest.shape[1]
@@ -300,7 +302,8 @@ class ContactScene:
         d.kappa = float(kappa)
         d.mode = MODES[mode] | (CB_THICK_PAPER_LITERAL if paper_literal else 0) | \
             (0 if core_temp else CB_NO_CORE_TEMP) | (CB_DBAR_PER_COMPONENT if per_component else 0) | \
-            (CB_EE_MOLLIFIER if mollifier else 0) | (CB_PER_STENCIL if per_stencil else 0)
+            (CB_EE_MOLLIFIER if mollifier else 0) | (CB_PER_STENCIL if per_stencil else 0) | \
+            (CB_DBAR_GEODESIC if rest_geodesic else 0)
         d.cull_radius = int(cull_radius)
         h = C.c_void_p()
         _check(L.cb_scene_create(C.byref(d), _allocator_arg(allocator), _stream_ptr(stream), C.byref(h)),
@@ -322,7 +325,8 @@ class ContactScene:
     def from_scene(cls, sc, mode: str = "double", **kw) -> "ContactScene":
         return cls(sc.kind, sc.rest, sc.thickness, sc.dhat, rod_ptr=sc.rod_ptr, tris=sc.tris,
                    kappa=sc.kappa, mode=mode, rod_closed=getattr(sc, "rod_closed", None),
-                   rest_uv=getattr(sc, "rest_uv", None), **kw)
+                   rest_uv=getattr(sc, "rest_uv", None),
+                   rest_geodesic=bool(getattr(sc, "rest_geodesic", False)), **kw)
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:
@@ -440,6 +444,16 @@ class ContactScene:
         _check(lib().cb_get_pairs(self.h, PAIRS[which], out.ctypes.data if out.size else None, out.size,
                                   C.byref(cnt)), "cb_get_pairs")
         return out
+
+    def rest_filter(self) -> tuple[np.ndarray, np.ndarray]:
+        """Shells: the rest-filtered stencil pairs (key order) and their reference distances."""
+        cnt = C.c_int64()
+        lib().cb_get_rest_filter(self.h, None, None, 0, C.byref(cnt))
+        keys, dbar = np.zeros(cnt.value, np.uint64), np.zeros(cnt.value)
+        _check(lib().cb_get_rest_filter(self.h, keys.ctypes.data if keys.size else None,
+                                        dbar.ctypes.data if dbar.size else None, keys.size, C.byref(cnt)),
+               "cb_get_rest_filter")
+        return keys, dbar
 
     def active(self) -> dict:
         cnt = C.c_int64()

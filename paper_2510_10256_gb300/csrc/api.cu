@@ -213,10 +213,12 @@ cb_status cb_scene_create(const cb_scene_desc* d, const cb_allocator* allocator,
     return CB_ERR_ARG;
   const int fm = d->mode & CB_FILTER_MASK;
   if (d->mode & ~(CB_FILTER_MASK | CB_THICK_PAPER_LITERAL | CB_NO_CORE_TEMP | CB_DBAR_PER_COMPONENT |
-                  CB_EE_MOLLIFIER | CB_PER_STENCIL))
+                  CB_EE_MOLLIFIER | CB_PER_STENCIL | CB_DBAR_GEODESIC))
     return CB_ERR_ARG;
   if (fm == CB_FILTER_KALDOR && (d->kind != CB_ROD || d->cull_radius < 1)) return CB_ERR_ARG;
   if (d->rest_uv && d->kind != CB_SHELL) return CB_ERR_ARG;
+  const bool geodesic = (d->mode & CB_DBAR_GEODESIC) != 0;
+  if (geodesic && (d->kind != CB_SHELL || d->rest_uv)) return CB_ERR_ARG;
   const int n = d->n_verts;
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<int32_t> e0, e1, comp(n), rloop, rlast;
@@ -284,6 +286,37 @@ cb_status cb_scene_create(const cb_scene_desc* d, const cb_allocator* allocator,
     for (int v = 0; v < n; ++v) comp[v] = find(v);
   }
   const int E = (int)e0.size();
+  // geodesic reference distances: the mesh adjacency (a manifold: at most two faces per edge)
+  std::vector<int32_t> geo_te, geo_ef, geo_vfp, geo_vf;
+  if (geodesic) {
+    auto edge_id = [&](int p, int q) {
+      const uint64_t k = (uint64_t)std::min(p, q) * (uint64_t)n + (uint64_t)std::max(p, q);
+      int lo = 0, hi = E;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((uint64_t)e0[mid] * (uint64_t)n + (uint64_t)e1[mid] < k) lo = mid + 1;
+        else hi = mid;
+      }
+      return lo;
+    };
+    geo_te.resize(3 * (size_t)T);
+    geo_ef.assign(2 * (size_t)E, -1);
+    geo_vfp.assign((size_t)n + 1, 0);
+    geo_vf.resize(3 * (size_t)T);
+    for (int t = 0; t < T; ++t)
+      for (int k = 0; k < 3; ++k) {
+        const int e = edge_id(tris[(size_t)k * T + t], tris[(size_t)((k + 1) % 3) * T + t]);
+        geo_te[3 * (size_t)t + k] = e;
+        if (geo_ef[2 * (size_t)e] < 0) geo_ef[2 * (size_t)e] = t;
+        else if (geo_ef[2 * (size_t)e + 1] < 0) geo_ef[2 * (size_t)e + 1] = t;
+        else return CB_ERR_ARG;  // an edge of three faces: no geodesic distance
+        ++geo_vfp[(size_t)tris[(size_t)k * T + t] + 1];
+      }
+    for (int v = 0; v < n; ++v) geo_vfp[(size_t)v + 1] += geo_vfp[v];
+    std::vector<int32_t> fill(geo_vfp.begin(), geo_vfp.end() - 1);
+    for (int t = 0; t < T; ++t)
+      for (int k = 0; k < 3; ++k) geo_vf[(size_t)fill[tris[(size_t)k * T + t]]++] = t;
+  }
   cb_scene* s = new cb_scene();
   if (allocator) {
     s->allocator = *allocator;
@@ -321,6 +354,11 @@ cb_status cb_scene_create(const cb_scene_desc* d, const cb_allocator* allocator,
   }
   s->dhat = d->dhat;
   s->kappa = d->kappa > 0.0 ? d->kappa : 1.0;
+  s->geodesic = geodesic;
+  s->geo_te.swap(geo_te);
+  s->geo_ef.swap(geo_ef);
+  s->geo_vfp.swap(geo_vfp);
+  s->geo_vf.swap(geo_vf);
   s->last_stream = st;
   cudaGetDevice(&s->device);
   cudaDeviceGetAttribute(&s->n_sms, cudaDevAttrMultiProcessorCount, s->device);
@@ -383,6 +421,11 @@ cb_status cb_scene_create(const cb_scene_desc* d, const cb_allocator* allocator,
   // the rest broad phase reads the member parameters (box inflation, primitive count)
   if ((rc = upload_members(s, st)) != CB_OK) return fail(rc);
   if ((rc = filter_precompute(s, st)) != CB_OK) return fail(rc);
+  // the adjacency served the geodesic rest filter only
+  std::vector<int32_t>().swap(s->geo_te);
+  std::vector<int32_t>().swap(s->geo_ef);
+  std::vector<int32_t>().swap(s->geo_vfp);
+  std::vector<int32_t>().swap(s->geo_vf);
   s->hmp[0].dbar_min = std::isfinite(s->dbar_min) ? s->dbar_min : 0.0;
   s->hmp[0].dbar_fmax = s->hmp[0].per_comp && std::isfinite(s->dbar_fmax) ? s->dbar_fmax : s->hmp[0].dbar_min;
   if ((rc = upload_members(s, st)) != CB_OK) return fail(rc);
@@ -758,6 +801,19 @@ cb_status cb_get_pairs(cb_scene* s, int32_t which, uint64_t* keys, int64_t cap, 
     sort_keys(res, nullptr);
     memcpy(keys, res.data(), res.size() * sizeof(uint64_t));
   }
+  return CB_OK;
+}
+
+cb_status cb_get_rest_filter(cb_scene* s, uint64_t* keys, double* dbar, int64_t cap, int64_t* count) {
+  if (!s || !count || s->kind != CB_SHELL) return CB_ERR_ARG;
+  cudaStream_t st = s->last_stream;
+  *count = s->n_frest;
+  if (s->n_frest > cap) return CB_ERR_CAPACITY;
+  if (s->n_frest > 0 && keys)
+    CB_CUDA(cudaMemcpyAsync(keys, s->frest.p, sizeof(uint64_t) * (size_t)s->n_frest, cudaMemcpyDeviceToHost, st));
+  if (s->n_frest > 0 && dbar)
+    CB_CUDA(cudaMemcpyAsync(dbar, s->frest_dbar.p, sizeof(double) * (size_t)s->n_frest, cudaMemcpyDeviceToHost, st));
+  CB_CUDA(cudaStreamSynchronize(st));
   return CB_OK;
 }
 

@@ -2507,7 +2507,8 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
     memcpy(&s->dbar_min, &h[0], 8);
     s->n_frest = (int64_t)h[1];
   } else {
-    // rest broad phase at the full activation, then rest distances below a
+    // rest broad phase at the full activation, then rest distances below a (a
+    // geodesic distance is at least the 3D one, so the same candidates serve it)
     int64_t nr = 0;
     ScopedBuf rcs(st);
     DevBuf& rc = rcs.b;
@@ -2521,10 +2522,14 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
       CB_TRY(buf_ensure(pos, sizeof(uint32_t) * ((size_t)nr + 1), st));
       CB_TRY(buf_ensure(dbar, sizeof(double) * (size_t)nr, st));
       CB_TRY(buf_ensure(s->scan_tmp, sizeof(uint64_t) * (size_t)(cbp::scan_tmp_elems(nr) + 8), st));
-      k_rest_filter<<<cb_grid(nr), CB_THREADS, 0, cb_count(st)>>>(nr, bp<uint64_t>(rc), bp<int32_t>(s->ev0),
-                                                        bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T,
-                                                        bp<int32_t>(s->comp), rf, s->n, s->a,
-                                                        bp<uint32_t>(flag), bp<double>(dbar), dmin, dcomp);
+      if (s->geodesic) {
+        CB_TRY(geo_rest_dbar(s, bp<uint64_t>(rc), nr, bp<uint32_t>(flag), bp<double>(dbar), dmin, dcomp, st));
+      } else {
+        k_rest_filter<<<cb_grid(nr), CB_THREADS, 0, cb_count(st)>>>(nr, bp<uint64_t>(rc), bp<int32_t>(s->ev0),
+                                                          bp<int32_t>(s->ev1), bp<int32_t>(s->tv), s->T,
+                                                          bp<int32_t>(s->comp), rf, s->n, s->a,
+                                                          bp<uint32_t>(flag), bp<double>(dbar), dmin, dcomp);
+      }
       uint32_t* tot = (uint32_t*)(sc + SC_COUNT1);
       cbp::exclusive_scan<uint32_t, uint32_t>(bp<uint32_t>(flag), bp<uint32_t>(pos), nr, bp<uint32_t>(s->scan_tmp),
                                               tot, st);

@@ -157,6 +157,10 @@ struct cb_scene {
   DevBuf rlast;         // int32 [E] rods: last (closing) edge of the edge's closed loop (-1: open)
   DevBuf elen2;         // double [E] squared rest length of each edge (the mollifier's threshold)
   DevBuf ruv;           // double [3][n] shells: the flat pattern (u, v, 0), when given; reference distances there
+  bool geodesic = false;  // shells, CB_DBAR_GEODESIC: reference distances are geodesic distances on the rest mesh
+  // ... its mesh adjacency, host copies kept until the rest filter has run: edge of (t_k, t_k+1) [T][3],
+  // faces of an edge [E][2] (-1: none), faces around a vertex (CSR [n+1], [3T])
+  std::vector<int32_t> geo_te, geo_ef, geo_vfp, geo_vf;
   DevBuf frest;         // uint64 shells: sorted rest-filtered keys
   DevBuf frest_dbar;    // double
   DevBuf dbar_comp;     // uint64 bits of the per-component dbar_min, by component label (n entries)
@@ -255,7 +259,9 @@ enum {
   SC_NBK = 18,          // BSR pattern: keys left after the per-run sets of k_block_keys
   SC_FETCH = 19,        // ccd_step, exact rounds: pairs of the list handed out so far
   SC_NMOLL = 20,        // barrier_eval: mollified edge-edge pairs
-  SC_N = 21
+  SC_GEO_COUNT = 21,    // geodesic rest filter: (edge, vertex) entries below the activation
+  SC_GEO_ERR = 22,      // ... error bits of its sources (a fixed capacity exceeded)
+  SC_N = 23
 };
 // read_scalars stages up to SC_N scalars through the pinned host scratch
 static_assert(SC_N <= 64, "the scalars must fit the pinned scratch");
@@ -279,6 +285,10 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
 
 // narrow.cu
 cb_status filter_precompute(cb_scene* s, cudaStream_t st);
+// geodesic.cu: the rest filter's flag / dbar / minima of the rest-broad-phase
+// candidates with geodesic reference distances (CB_DBAR_GEODESIC)
+cb_status geo_rest_dbar(cb_scene* s, const uint64_t* cand, int64_t nc, uint32_t* flag, double* dbar,
+                        unsigned long long* dmin, unsigned long long* dcomp, cudaStream_t st);
 cb_status filter_apply(cb_scene* s, cudaStream_t st);
 cb_status frest_rows_build(cb_scene* s, cudaStream_t st);
 // energy_only: distances and energy (no active list, gradient, Hessian or BSR)

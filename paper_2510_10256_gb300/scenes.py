@@ -438,6 +438,48 @@ def rolled_sheet(seed: int = BASE_SEED + 8, nx: int = 24, ny: int = 12, L: float
                  rest_uv=np.ascontiguousarray(np.concatenate(uv_l, axis=1)))
 
 
+def curved_sheet(seed: int = BASE_SEED + 9, shape: str = "dome", nx: int = 32, L: float = 0.05,
+                 curvature: float = 1.0, thickness: float = 0.06, dhat: float = 0.01, layers: int = 2,
+                 sigma: float = 0.02) -> Scene:
+    """Doubly curved rest shells with geodesic reference distances
+    (rest_geodesic): `layers` nested copies of an nx x nx grid (edge about L)
+    laid on a sphere of radius 1 / curvature ("dome", positive Gaussian
+    curvature; the grid's distance from its centre kept as arc length) or on
+    the saddle z = curvature (x^2 - y^2) / 2 ("saddle", negative), each copy
+    offset along the surface normal by thickness +
+    0.6 dhat.  The activation thickness + dhat spans about 1.4 edges, so
+    stencils of one sheet lie within it at rest.  Current positions: the rest
+    shape plus a little noise; p: Gaussian."""
+    rng = np.random.default_rng(seed)
+    pat, t = grid_mesh(nx, nx, L)
+    u, v = pat[0], pat[1]
+    rest_l, tris_l = [], []
+    for k in range(layers):
+        off = k * (thickness + 0.6 * dhat)
+        if shape == "dome":
+            # azimuthal equidistant: the grid's distance from the centre is the arc length
+            R = 1.0 / curvature
+            th = np.hypot(u, v) / R
+            ph = np.arctan2(v, u)
+            nrm = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+            pos = (R + off) * nrm - np.array([[0.0], [0.0], [R]])
+        elif shape == "saddle":
+            z = 0.5 * curvature * (u * u - v * v)
+            g = np.stack([-curvature * u, curvature * v, np.ones(u.size)])
+            nrm = g / np.linalg.norm(g, axis=0)
+            pos = np.stack([u, v, z]) + off * nrm
+        else:
+            raise ValueError(shape)
+        rest_l.append(pos)
+        tris_l.append(t + k * u.size)
+    rest = np.concatenate(rest_l, axis=1)
+    tris = np.concatenate(tris_l, axis=1).astype(np.int32)
+    x = rest + rng.normal(0.0, 0.01 * dhat, size=rest.shape)
+    p = rng.normal(0.0, sigma, size=rest.shape)
+    return Scene("shell", _soa(rest), _soa(x), _soa(p), thickness, dhat, tris=tris, name=f"{shape}_sheet",
+                 seed=seed, rest_geodesic=True)
+
+
 def tiny_shell(seed: int, nx: int = 5, L: float = 0.3, thickness: float = 0.4,
                dhat: float = 0.1, noise: float = 0.08, layers: int = 2,
                sigma: float = 0.1) -> Scene:

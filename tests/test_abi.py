@@ -56,3 +56,39 @@ def test_struct_layouts_match_the_header(cname, pytype, tmp_path):
     out = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert out[0] == ctypes.sizeof(st), (out[0], ctypes.sizeof(st))
     assert out[1:] == [getattr(st, f).offset for f in fields]
+
+
+def _desc(kind, rest, tris=None, rod_ptr=None, mode=0, rest_uv=None, keep=None):
+    import numpy as np
+    d = CT.SceneDesc()
+    d.kind, d.n_verts = kind, rest.shape[1]
+    d.rest_xyz = rest.ctypes.data
+    if tris is not None:
+        d.n_tris, d.tris = tris.shape[1], tris.ctypes.data
+    if rod_ptr is not None:
+        d.n_rods, d.rod_ptr = rod_ptr.size - 1, rod_ptr.ctypes.data
+    if rest_uv is not None:
+        d.rest_uv = rest_uv.ctypes.data
+    d.thickness, d.dhat, d.kappa, d.mode = 0.1, 0.01, 1.0, mode
+    keep.extend(x for x in (rest, tris, rod_ptr, rest_uv) if x is not None)
+    return d
+
+
+def test_geodesic_mode_argument_errors_without_gpu():
+    """CB_DBAR_GEODESIC is refused, before any device call, for rods, for a
+    shell that also gives a flat pattern, and for a mesh with an edge of three
+    faces."""
+    import numpy as np
+    CT.build()
+    L, keep, out = CT.lib(), [], ctypes.c_void_p()
+    G = CT.CB_DBAR_GEODESIC
+    rest = np.ascontiguousarray(np.random.default_rng(0).normal(size=(3, 5)))
+    rod = _desc(CT.CB_ROD, rest, rod_ptr=np.array([0, 5], np.int32), mode=G, keep=keep)
+    assert L.cb_scene_create(ctypes.byref(rod), None, None, ctypes.byref(out)) == CT.CB_ERR_ARG
+    tri = np.ascontiguousarray(np.array([[0, 0, 0], [1, 1, 1], [2, 3, 4]], np.int32))   # edge 0-1 in three faces
+    bad = _desc(CT.CB_SHELL, rest, tris=tri, mode=G, keep=keep)
+    assert L.cb_scene_create(ctypes.byref(bad), None, None, ctypes.byref(out)) == CT.CB_ERR_ARG
+    one = np.ascontiguousarray(tri[:, :1])
+    uv = np.ascontiguousarray(rest[:2])
+    both = _desc(CT.CB_SHELL, rest, tris=one, mode=G, rest_uv=uv, keep=keep)
+    assert L.cb_scene_create(ctypes.byref(both), None, None, ctypes.byref(out)) == CT.CB_ERR_ARG
