@@ -1869,72 +1869,118 @@ __global__ void __launch_bounds__(S) k_hess_proj(HessArgs A) {
   }
 }
 
-// ---- the 9x9 projection for short queues: 16 lanes per pair --------------
+// ---- the 9x9 projection for short queues: a warp per pair ----------------
 // One thread per pair runs some 8,500 dependent FP64 instructions, and an FP64
 // warp instruction occupies a warp for 64 cycles however many of its lanes
 // are active (measured on GB300: 64 cycles per dependent or independent DFMA
 // of a lone warp; 76 with one warp per SM sub-partition, the SM's FP64 unit
 // then full at one warp instruction per ~19 cycles), so a short queue (a
 // small scene) waits for that chain however idle the device is.  This form
-// spreads one pair over a half-warp, lane r (0..8) owning row and column r,
-// and orders the Jacobi rotations round robin: in round k of a sweep lane r
-// pairs with (2k - r) mod 9 (lane k rests), the four disjoint rotations of a
+// spreads one pair over a warp, the three lanes (r, t) = (l / 3, l % 3) of
+// row r (lanes 0..26) owning entries t, t + 3, t + 6 of row and column r,
+// and orders the Jacobi rotations round robin: in round k of a sweep row r
+// pairs with (2k - r) mod 9 (row k rests), the four disjoint rotations of a
 // round are applied at once (X = A J by columns, then J^T X by rows, V J by
-// columns), so a sweep is 9 rounds of a few FP64 instructions per lane
-// instead of 36 rotations in sequence.  Each lane computes its own pair's
-// rotation, the same bits in both lanes of the pair.  The arithmetic is
+// columns), so a sweep is 9 rounds of 18 FP64 instructions per lane
+// instead of 36 rotations in sequence.  Each lane computes its own row's
+// rotation, the same bits in every lane of the pair's two rows.  The arithmetic is
 // otherwise that of k_hess_proj<9>: FP32 Jacobi on the scaled matrix to
 // the same tolerance, FP64 modified Gram-Schmidt, A = V^T B V, FP64 sweeps
 // with FP32 tangents and FP64-normalised rotations to an off-diagonal norm
 // of 1e-14 ||A||, B+ from the positive eigenpairs, the Hadamard scatter.
-constexpr int PL_PAIRS = 8;                 // pairs per block
-constexpr int PL_THREADS = 16 * PL_PAIRS;   // one half-warp per pair
+constexpr int PL_PAIRS = 4;                 // pairs per block
+constexpr int PL_THREADS = 32 * PL_PAIRS;   // one warp per pair: three lanes per row
 // doubles per pair: A, X (A J; later the Hadamard staging, 108), V, and the
 // FP32 phase's A, X, V (3 x 81 floats)
 constexpr int PL_SMEM = 81 + 108 + 81 + 122;
 // queues of at most this many active pairs take the lane-parallel form
 constexpr int64_t PL_MAX_ACTIVE = 4096;
 
-// sum over the 16 lanes of the caller's half-warp (every lane gets the same bits)
+// sum over the warp: a butterfly, so every lane gets the same bits
 template <typename R>
-__device__ __forceinline__ R seg_sum(R v, unsigned mask) {
+__device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
-  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, 16);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
 // one round of simultaneous rotations on a 9x9 matrix As and vectors Vs held
-// in shared memory ([9 i + j]); lane r (< 9) applies its pair's rotation
-// (c, sg: sg = -s for the lower index of the pair, +s for the upper, 0 and
-// c = 1 for a resting lane or a skipped pair) to column r, then row r
+// in shared memory ([9 i + j]); the three lanes (r, t) of row r apply its
+// pair's rotation (c, sg: sg = -s for the lower index of the pair, +s for the
+// upper, 0 and c = 1 for a resting row or a skipped pair) to entries
+// t, t + 3, t + 6 of column r, then of row r
 template <typename R>
-__device__ __forceinline__ void rr_apply(R* As, R* Xs, R* Vs, int r, int pr, R c, R sg, bool row, unsigned mask) {
-  R vr[9], vp[9];
+__device__ __forceinline__ void rr_apply3(R* As, R* Xs, R* Vs, int r, int t, int pr, R c, R sg, bool row) {
+  R vr[3], vp[3];
   if (row) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
+    for (int m = 0; m < 3; ++m) {
+      const int i = t + 3 * m;
       Xs[9 * i + r] = c * As[9 * i + r] + sg * As[9 * i + pr];
-      vr[i] = Vs[9 * i + r];
-      vp[i] = Vs[9 * i + pr];
+      vr[m] = Vs[9 * i + r];
+      vp[m] = Vs[9 * i + pr];
     }
   }
-  __syncwarp(mask);  // X complete; every lane holds the V columns it needs
+  __syncwarp();  // X complete; every lane holds the V entries it needs
   if (row) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Vs[9 * i + r] = c * vr[i] + sg * vp[i];
-#pragma unroll
-    for (int j = 0; j < 9; ++j) As[9 * r + j] = c * Xs[9 * r + j] + sg * Xs[9 * pr + j];
+    for (int m = 0; m < 3; ++m) {
+      const int i = t + 3 * m;
+      Vs[9 * i + r] = c * vr[m] + sg * vp[m];
+      As[9 * r + i] = c * Xs[9 * r + i] + sg * Xs[9 * pr + i];
+    }
   }
-  __syncwarp(mask);
+  __syncwarp();
+}
+
+// the rotation of row r's pair (r, pr) in a round: c and sg as rr_apply3 takes
+// them; every lane of the pair's two rows computes the same bits
+template <typename R>
+__device__ __forceinline__ void pl_rotation(const R* As, int r, int pr, bool row, R skip, double inv, R& c, R& sg);
+
+template <>
+__device__ __forceinline__ void pl_rotation<float>(const float* As, int r, int pr, bool row, float skip, double,
+                                                   float& c, float& sg) {
+  c = 1.f;
+  sg = 0.f;
+  if (!row || pr == r) return;
+  const int p = min(r, pr), q = max(r, pr);
+  const float apq = As[9 * p + q];
+  if (!(fabsf(apq) > skip)) return;
+  const float app = As[9 * p + p], aqq = As[9 * q + q];
+  const float tau = (aqq - app) / (2.f * apq);
+  const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+  c = 1.f / sqrtf(1.f + t * t);
+  sg = r == p ? -t * c : t * c;
+}
+
+// FP64: the tangent from FP32 arithmetic on the values scaled by the norm,
+// c = 1/sqrt(1 + t^2) to FP64 rounding
+template <>
+__device__ __forceinline__ void pl_rotation<double>(const double* As, int r, int pr, bool row, double skip,
+                                                    double inv, double& c, double& sg) {
+  c = 1.0;
+  sg = 0.0;
+  if (!row || pr == r) return;
+  const int p = min(r, pr), q = max(r, pr);
+  const double apq = As[9 * p + q];
+  if (!(fabs(apq) > skip)) return;
+  const double app = As[9 * p + p], aqq = As[9 * q + q];
+  const float apq32 = (float)(apq * inv), dd32 = (float)((aqq - app) * inv);
+  const float tau = dd32 / (2.f * apq32);
+  const float t32 = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+  const double t = (double)t32;
+  c = rsqrt_refined(1.0 + t * t);
+  sg = r == p ? -t * c : t * c;
 }
 
 __global__ void __launch_bounds__(PL_THREADS) k_hess_proj_lanes(HessArgs A) {
   extern __shared__ double pl_smem[];
-  const int seg = threadIdx.x >> 4, r = threadIdx.x & 15;
-  const unsigned mask = 0xffffu << (16 * (seg & 1));
-  const bool row = r < 9;
+  const int seg = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = lane / 3, t = lane - 3 * r;  // row r (< 9 for lanes 0..26), third t
+  const bool row = lane < 27;
   const int64_t w = (int64_t)blockIdx.x * PL_PAIRS + seg;
-  if (w >= (int64_t)*A.n9) return;  // the whole half-warp leaves together
+  if (w >= (int64_t)*A.n9) return;  // the whole warp leaves together
   double* As = pl_smem + (size_t)seg * PL_SMEM;  // A[i][j] at [9 i + j]
   double* Xs = As + 81;                          // A J; later the Hadamard staging
   double* Vs = Xs + 108;                         // V[i][k]: component i of eigenvector k
@@ -1942,7 +1988,7 @@ __global__ void __launch_bounds__(PL_THREADS) k_hess_proj_lanes(HessArgs A) {
   float* X32 = A32 + 81;
   float* V32 = X32 + 81;
   const uint32_t a = A.slot9[w];
-  double Br[9];
+  double Br[9];  // row r of B
   double mx = 0.0;
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
@@ -1950,143 +1996,127 @@ __global__ void __launch_bounds__(PL_THREADS) k_hess_proj_lanes(HessArgs A) {
     mx = fmax(mx, fabs(Br[j]));
   }
 #pragma unroll
-  for (int o = 8; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(mask, mx, o, 16));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (mx == 0.0) return;  // B+ = 0: nothing to add
   // FP32 phase on B / max|B|
   {
     const double inv = 1.0 / mx;
     if (row)
 #pragma unroll
-      for (int j = 0; j < 9; ++j) {
+      for (int m = 0; m < 3; ++m) {
+        const int j = t + 3 * m;
         A32[9 * r + j] = (float)(Br[j] * inv);
         V32[9 * r + j] = r == j ? 1.f : 0.f;
       }
-    __syncwarp(mask);
+    __syncwarp();
     for (int sweep = 0; sweep < 12; ++sweep) {
       float off = 0.f, fro = 0.f;
       if (row)
-        for (int j = 0; j < 9; ++j) {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          const int j = t + 3 * m;
           const float v = A32[9 * r + j];
           if (j == r) fro += v * v;
           else off += v * v;
         }
-      off = seg_sum(off, mask);
-      fro = seg_sum(fro, mask) + off;
+      off = warp_sum(off);
+      fro = warp_sum(fro) + off;
       if (fro == 0.f || off <= PROJ_FP32_TOL2 * fro) break;
       const float skip = 1e-16f * sqrtf(fro);
       for (int k = 0; k < 9; ++k) {
         const int pr = row ? (2 * k - r + 18) % 9 : r;
-        const int p = min(r, pr), q = max(r, pr);
-        float c = 1.f, sg = 0.f;
-        if (row && pr != r) {
-          const float apq = A32[9 * p + q];
-          if (fabsf(apq) > skip) {
-            const float app = A32[9 * p + p], aqq = A32[9 * q + q];
-            const float tau = (aqq - app) / (2.f * apq);
-            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            c = 1.f / sqrtf(1.f + t * t);
-            sg = r == p ? -t * c : t * c;
-          }
-        }
-        rr_apply<float>(A32, X32, V32, r, pr, c, sg, row, mask);
+        float c, sg;
+        pl_rotation<float>(A32, r, pr, row, skip, 0.0, c, sg);
+        rr_apply3<float>(A32, X32, V32, r, t, pr, c, sg, row);
       }
     }
   }
-  // FP64 modified Gram-Schmidt on the FP32 eigenvectors, columns in descending order
+  // FP64 modified Gram-Schmidt on the FP32 eigenvectors, columns in
+  // descending order; the three lanes of row r hold component r (the same
+  // bits), and only lane t = 0 of each row enters the sums
   for (int k = 8; k >= 0; --k) {
     double v = row ? (double)V32[9 * r + k] : 0.0;
     for (int j = k + 1; j < 9; ++j) {
       const double vj = row ? Vs[9 * r + j] : 0.0;
-      const double dp = seg_sum(vj * v, mask);
+      const double dp = warp_sum(t == 0 ? vj * v : 0.0);
       v -= dp * vj;
     }
-    const double nn = rsqrt_refined(seg_sum(v * v, mask));  // 1 to FP32 accuracy here
-    if (row) Vs[9 * r + k] = v * nn;
+    const double nn = rsqrt_refined(warp_sum(t == 0 ? v * v : 0.0));  // 1 to FP32 accuracy here
+    if (row) Vs[9 * r + k] = v * nn;  // each lane of the row writes the same bits, then reads its own
   }
-  __syncwarp(mask);
-  // A = V^T (B V): row r of W = B V into X, then the upper triangle of row r
-  // of A from the columns of V and W, mirrored
+  __syncwarp();
+  // A = V^T (B V): entries t, t + 3, t + 6 of row r of W = B V into X, then
+  // those of the upper triangle of row r of A from the columns of V and W, mirrored
   if (row)
 #pragma unroll
-    for (int l = 0; l < 9; ++l) {
-      double t = 0.0;
+    for (int m = 0; m < 3; ++m) {
+      const int l = t + 3 * m;
+      double s = 0.0;
 #pragma unroll
-      for (int j = 0; j < 9; ++j) t += Br[j] * Vs[9 * j + l];
-      Xs[9 * r + l] = t;
+      for (int j = 0; j < 9; ++j) s += Br[j] * Vs[9 * j + l];
+      Xs[9 * r + l] = s;
     }
-  __syncwarp(mask);
+  __syncwarp();
   if (row)
-    for (int l = r; l < 9; ++l) {
-      double t = 0.0;
 #pragma unroll
-      for (int i = 0; i < 9; ++i) t += Vs[9 * i + r] * Xs[9 * i + l];
-      As[9 * r + l] = t;
-      As[9 * l + r] = t;
+    for (int m = 0; m < 3; ++m) {
+      const int l = t + 3 * m;
+      if (l < r) continue;
+      double s = 0.0;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) s += Vs[9 * i + r] * Xs[9 * i + l];
+      As[9 * r + l] = s;
+      As[9 * l + r] = s;
     }
-  __syncwarp(mask);
-  // FP64 sweeps: tangents from FP32 arithmetic on the values scaled by the
-  // norm, c = 1/sqrt(1 + t^2) to FP64 rounding (exactly 1 for |t| < 1e-8)
+  __syncwarp();
+  // FP64 sweeps to an off-diagonal norm of 1e-14 ||A||
   for (int sweep = 0; sweep < 12; ++sweep) {
     double off = 0.0, fro = 0.0;
     if (row)
-      for (int j = 0; j < 9; ++j) {
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const int j = t + 3 * m;
         const double v = As[9 * r + j];
         if (j == r) fro += v * v;
         else off += v * v;
       }
-    off = seg_sum(off, mask);
-    fro = seg_sum(fro, mask) + off;
+    off = warp_sum(off);
+    fro = warp_sum(fro) + off;
     if (fro == 0.0 || off <= 1e-28 * fro) break;
     const double nrm = sqrt(fro);
     const double skip = 1e-16 * nrm, inv = 1.0 / nrm;
     for (int k = 0; k < 9; ++k) {
       const int pr = row ? (2 * k - r + 18) % 9 : r;
-      const int p = min(r, pr), q = max(r, pr);
-      double c = 1.0, sg = 0.0;
-      if (row && pr != r) {
-        const double apq = As[9 * p + q];
-        if (fabs(apq) > skip) {
-          const double app = As[9 * p + p], aqq = As[9 * q + q];
-          const float apq32 = (float)(apq * inv), dd32 = (float)((aqq - app) * inv);
-          const float tau = dd32 / (2.f * apq32);
-          const float t32 = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-          const double t = (double)t32;
-          c = rsqrt_refined(1.0 + t * t);
-          sg = r == p ? -t * c : t * c;
-        }
-      }
-      rr_apply<double>(As, Xs, Vs, r, pr, c, sg, row, mask);
+      double c, sg;
+      pl_rotation<double>(As, r, pr, row, skip, inv, c, sg);
+      rr_apply3<double>(As, Xs, Vs, r, t, pr, c, sg, row);
     }
   }
-  // B+ / 4 (the square of K4's entries), row r: sum over the positive
-  // eigenpairs of lam v v^T (the product v_r v_j is formed first, so rows r
-  // and j get the same bits); then the point transform of row r (lane 3a + i
-  // holds point a, axis i) into the staging rows
-  double P[9];
-#pragma unroll
-  for (int j = 0; j < 9; ++j) P[j] = 0.0;
+  // B+ / 4 (the square of K4's entries), entries j = t, t + 3, t + 6 of row
+  // r: sum over the positive eigenpairs of lam v v^T (the product v_r v_j is
+  // formed first, so rows r and j get the same bits); then the point
+  // transform over those three column points (axis t) into the staging rows
+  double P[3] = {0.0, 0.0, 0.0};
   if (row)
     for (int k = 0; k < 9; ++k) {
       const double lam = As[9 * k + k];
       if (!(lam > 0.0)) continue;
       const double l4 = 0.25 * lam, vr = Vs[9 * r + k];
 #pragma unroll
-      for (int j = 0; j < 9; ++j) P[j] = fma(vr * Vs[9 * j + k], l4, P[j]);
+      for (int m = 0; m < 3; ++m) P[m] = fma(vr * Vs[9 * (t + 3 * m) + k], l4, P[m]);
     }
-  __syncwarp(mask);  // every lane is done with X
-  if (row)
+  __syncwarp();  // every lane is done with X
+  if (row) {
+    double h[4];
+    had3(P[0], P[1], P[2], h);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      double h[4];
-      had3(P[j], P[3 + j], P[6 + j], h);  // over the column points
-#pragma unroll
-      for (int q2 = 0; q2 < 4; ++q2) Xs[12 * r + 3 * q2 + j] = h[q2];
-    }
-  __syncwarp(mask);
+    for (int q2 = 0; q2 < 4; ++q2) Xs[12 * r + 3 * q2 + t] = h[q2];
+  }
+  __syncwarp();
   // lane l < 12 takes block row q1 = l / 3, axis i = l % 3: the transform
   // over the row points, and the sixteen blocks' entries of that row
-  if (r < 12) {
-    const int q1 = r / 3, i = r % 3;
+  if (lane < 12) {
+    const int q1 = lane / 3, i = lane % 3;
     const uint32_t ci = A.aidx[a];
     const Stencil st = stencil_of(A.cand[ci], A.ev0, A.ev1, A.tv, A.T);
     const int rv = st.v[q1];
