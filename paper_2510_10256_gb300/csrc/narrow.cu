@@ -1974,12 +1974,12 @@ __device__ __forceinline__ void pl_rotation<double>(const double* As, int r, int
   sg = r == p ? -t * c : t * c;
 }
 
-__global__ void __launch_bounds__(PL_THREADS) k_hess_proj_lanes(HessArgs A) {
+__device__ __forceinline__ void proj_lanes_block(const HessArgs& A, int block) {
   extern __shared__ double pl_smem[];
   const int seg = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = lane / 3, t = lane - 3 * r;  // row r (< 9 for lanes 0..26), third t
   const bool row = lane < 27;
-  const int64_t w = (int64_t)blockIdx.x * PL_PAIRS + seg;
+  const int64_t w = (int64_t)block * PL_PAIRS + seg;
   if (w >= (int64_t)*A.n9) return;  // the whole warp leaves together
   double* As = pl_smem + (size_t)seg * PL_SMEM;  // A[i][j] at [9 i + j]
   double* Xs = As + 81;                          // A J; later the Hadamard staging
@@ -2381,8 +2381,8 @@ __device__ __forceinline__ void psd2(double a, double b, double c, double& pa, d
 // eigenproblem instead of a 4x4.  The 2x2 block is projected in closed form,
 // the 6x6 result rotated back block by block (B+ = (I x R) B'+ (I x R)^T) and
 // scattered as in k_hess_proj<6>.
-__global__ void __launch_bounds__(128) k_hess_proj_pe(HessArgs A) {
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void proj_pe_block(const HessArgs& A, int block) {
+  const int64_t w = (int64_t)block * 128 + threadIdx.x;
   if (w >= (int64_t)*A.n4) return;
   const uint32_t a = A.slot4[w];
   double q[10], R[9];
@@ -2473,6 +2473,19 @@ __global__ void __launch_bounds__(128) k_hess_proj_pe(HessArgs A) {
     add_block(A, r, cc, blk, false);
     if (k >= 3) add_block(A, cc, r, blk, true);
   }
+}
+
+// the point-edge pairs projected in their own frame, one thread per pair
+__global__ void __launch_bounds__(128) k_hess_proj_pe(HessArgs A) { proj_pe_block(A, blockIdx.x); }
+
+// Short queues (a small scene): the warp-per-pair 9x9 projection in blocks
+// [0, nb9) and the point-edge pairs in the blocks after them, one launch, so
+// that the two independent queues run side by side (both only add into the
+// BSR values, atomically) instead of one after the other.
+__global__ void __launch_bounds__(PL_THREADS) k_hess_proj_short(HessArgs A, int nb9) {
+  static_assert(PL_THREADS == 128, "both halves run 128-thread blocks");
+  if ((int)blockIdx.x < nb9) proj_lanes_block(A, blockIdx.x);
+  else proj_pe_block(A, blockIdx.x - nb9);
 }
 
 __global__ void k_energy_final(int count, const unsigned long long* __restrict__ macc, double* __restrict__ out) {
@@ -2860,12 +2873,13 @@ cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad
     // the three queues' lengths stay on the device: every projection kernel
     // reads its own, the point-edge one over a grid for all active pairs, the
     // shared-memory ones over at most one wave of blocks (grid-stride)
-    k_hess_proj_pe<<<cb_grid(na, 128), 128, 0, cb_count(st)>>>(A);
     if (na <= PL_MAX_ACTIVE) {
       const int smem = PL_SMEM * (int)sizeof(double) * PL_PAIRS;
-      k_hess_proj_lanes<<<(int)((na + PL_PAIRS - 1) / PL_PAIRS), PL_THREADS, smem, cb_count(st)>>>(A);
+      const int nb9 = (int)((na + PL_PAIRS - 1) / PL_PAIRS);
+      k_hess_proj_short<<<nb9 + (int)cb_grid(na, 128), PL_THREADS, smem, cb_count(st)>>>(A, nb9);
       CB_CUDA(cudaGetLastError());
     } else {
+      k_hess_proj_pe<<<cb_grid(na, 128), 128, 0, cb_count(st)>>>(A);
       CB_TRY(launch_proj<9>(s, A, na, st));
     }
     CB_TRY(launch_proj<6>(s, A, na, st));
