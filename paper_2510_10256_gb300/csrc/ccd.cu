@@ -195,21 +195,12 @@ __device__ __forceinline__ void warp_append(bool flag, uint32_t value, uint32_t*
 // operations per candidate on the FP64 pipe, which issues 1/64 as fast.)
 __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restrict__ lb_out,
                                                     uint32_t* __restrict__ list, unsigned int* __restrict__ nlist) {
-  __shared__ uint64_t fsm[4][FREST_WARP_CAP];  // the warps' staged table rows (128 threads)
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool need = false, unres = false;
   double m_exact = 2.0, m_lb = 2.0;  // this lane's contributions to the two minima
   int mem = -1;
-  // shells: the rest-filter table lookup, the warp's rows staged together
-  bool look = false;
-  const uint64_t qkey = q < A.np ? A.keys[q] : 0;
-  if (q < A.np && A.kind == CB_SHELL && A.nf > 0) {
-    const int u0 = cb_key_type(qkey) == CB_KEY_PT ? (int)cb_key_i(qkey) : A.ev0[cb_key_i(qkey)];
-    look = !A.mp[A.vsc[u0]].filter_off;
-  }
-  const bool tab = frest_contains_warp(A.frest, A.frow_pt, A.frow_ee, look, qkey, fsm[threadIdx.x >> 5]);
   if (q < A.np) {
-    const uint64_t key = qkey;
+    const uint64_t key = A.keys[q];
     const uint32_t ty = cb_key_type(key), ki = cb_key_i(key), kj = cb_key_j(key);
     int v[4];
     bool ee;
@@ -228,7 +219,7 @@ __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restric
     }
     mem = A.vsc[v[0]];
     const MemberParams& M = A.mp[mem];
-    const bool filt = A.kind == CB_SHELL ? tab : is_filtered(A, M, key, ki, kj);
+    const bool filt = is_filtered(A, M, key, ki, kj);
     need = true;
     // Kaldor culling (rods: edges numbered along each polyline): the pair
     // does not constrain the step

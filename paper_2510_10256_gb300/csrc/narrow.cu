@@ -204,17 +204,14 @@ __global__ void k_filter_shell(int64_t nc, const uint64_t* __restrict__ cand, co
                                const int32_t* __restrict__ ev0, const int32_t* __restrict__ vsc,
                                const MemberParams* __restrict__ mp, uint8_t* __restrict__ klass,
                                unsigned long long* __restrict__ nfilt, int n, int T, StencilArgs SA) {
-  __shared__ uint64_t fsm[CB_THREADS / 32][FREST_WARP_CAP];  // the warps' staged table rows
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t f = 0, dropped = 0;
-  const uint64_t key = c < nc ? cand[c] : 0;
-  const bool pt = cb_key_type(key) == CB_KEY_PT;
-  const int v0 = c < nc ? (pt ? (int)cb_key_i(key) : ev0[cb_key_i(key)]) : 0;
-  const bool look = c < nc && nf > 0 && !mp[vsc[v0]].filter_off;
-  const bool hit = frest_contains_warp(frest, row_pt, row_ee, look, key, fsm[threadIdx.x >> 5]);
   if (c < nc) {
+    const uint64_t key = cand[c];
+    const bool pt = cb_key_type(key) == CB_KEY_PT;
+    const int v0 = pt ? (int)cb_key_i(key) : ev0[cb_key_i(key)];
     const MemberParams& M = mp[vsc[v0]];
-    f = hit ? 1u : 0u;
+    if (!M.filter_off && nf > 0) f = frest_contains(frest, row_pt, row_ee, key) ? 1u : 0u;
     uint8_t kl = (uint8_t)f;
     if (f && M.per_stencil) {
       // broad-phase primitive ids: vertices, then triangles, then edges
