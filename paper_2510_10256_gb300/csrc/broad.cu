@@ -938,26 +938,69 @@ __global__ void k_flat_emit(PairArgs A, const uint64_t* __restrict__ toff, const
     type = CB_KEY_EE;
     ibase = jbase = (uint32_t)(t.n + t.T);
   }
-  const uint64_t f0 = lflag[i] ? toff[lpos[i]] : 0, f1 = lflag[i] ? toff[lpos[i] + 1] : 0;
   const uint32_t j0 = j0s[i];
   size_t o = off[i];
-  for (uint32_t word = sbits[i]; word;) {  // a short range
+  for (uint32_t word = sbits[i]; word;) {  // a short range (a long one: k_flat_emit_long)
     const uint32_t b = (uint32_t)__ffs(word) - 1u;
     word &= word - 1u;
     const uint32_t Q = A.eval[j0 + b];
     const bool swap = type == CB_KEY_EE && Q < P;
     out[o++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
   }
-  if (f1 > f0) {
-    for (uint64_t wd = f0 >> 5; wd <= (f1 - 1) >> 5; ++wd) {
-      uint32_t word = flat_word(bits, wd, f0, f1);
+}
+
+// The pairs of the long entries (their slots laid end to end), after their
+// short pairs: a warp per entry, lane l taking hit word l of each run of 32,
+// a warp scan of the words' hit counts placing each lane's pairs, so that
+// the warp writes one contiguous run per 32 words.  Grid-stride over the
+// long entries, whose count is lpos[ne].
+__global__ void __launch_bounds__(256) k_flat_emit_long(PairArgs A, const uint64_t* __restrict__ toff,
+                                                        const uint32_t* __restrict__ lidx,
+                                                        const uint32_t* __restrict__ lpos,
+                                                        const uint32_t* __restrict__ j0s,
+                                                        const uint32_t* __restrict__ bits,
+                                                        const uint32_t* __restrict__ sbits,
+                                                        const uint32_t* __restrict__ off, uint64_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nl = lpos[A.ne];
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const Topo& t = A.t;
+  for (int64_t wl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wl < nl; wl += nwarps) {
+    const uint32_t i = lidx[wl];
+    const uint64_t f0 = toff[wl], f1 = toff[wl + 1];
+    if (f1 <= f0) continue;
+    const uint32_t P = A.eval[i];
+    uint32_t type, ibase = 0, jbase = 0;
+    if (P < (uint32_t)t.n) {
+      type = CB_KEY_PT;
+      jbase = (uint32_t)t.n;
+    } else {
+      type = CB_KEY_EE;
+      ibase = jbase = (uint32_t)(t.n + t.T);
+    }
+    const uint32_t j0 = j0s[i];
+    size_t o = (size_t)off[i] + (size_t)__popc(sbits[i]);
+    const uint64_t w_end = (f1 - 1) >> 5;
+    for (uint64_t w0 = f0 >> 5; w0 <= w_end; w0 += 32) {
+      const uint64_t wd = w0 + (uint64_t)lane;
+      uint32_t word = wd <= w_end ? flat_word(bits, wd, f0, f1) : 0u;
+      const uint32_t c = (uint32_t)__popc(word);
+      uint32_t before = c;  // inclusive scan of the hit counts over the lanes
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, before, d);
+        if (lane >= d) before += u;
+      }
+      const uint32_t total = __shfl_sync(0xffffffffu, before, 31);
+      size_t q = o + before - c;
       while (word) {
         const uint32_t b = (uint32_t)__ffs(word) - 1u;
         word &= word - 1u;
         const uint32_t Q = A.eval[j0 + (uint32_t)((wd << 5) + b - f0)];
         const bool swap = type == CB_KEY_EE && Q < P;
-        out[o++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
+        out[q++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
       }
+      o += total;
     }
   }
 }
@@ -1166,6 +1209,12 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
                                                                bp<uint32_t>(w.flat_lpos), bp<uint32_t>(w.flat_j0),
                                                                bp<uint32_t>(w.flat_bits), bp<uint32_t>(w.flat_sbits),
                                                                c, f, o);
+      if (flat_t > 0) {
+        const int g = (int)std::min<int64_t>(cb_grid(ne, 256), (int64_t)s->n_sms * 16);
+        k_flat_emit_long<<<g, 256, 0, cb_count(st)>>>(A, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_lidx),
+                                                      bp<uint32_t>(w.flat_lpos), bp<uint32_t>(w.flat_j0),
+                                                      bp<uint32_t>(w.flat_bits), bp<uint32_t>(w.flat_sbits), f, o);
+      }
     }
     return CB_OK;
   };
