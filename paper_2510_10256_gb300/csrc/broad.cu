@@ -919,6 +919,11 @@ __global__ void k_flat_count(int64_t ne, const uint64_t* __restrict__ toff, cons
   cnt[i] = c;
 }
 
+// Slots of an entry's range from which its pairs are written by a warp
+// (k_flat_emit_long) rather than by the entry's thread: shorter ranges
+// would leave most of the warp's lanes without a word.
+constexpr uint64_t FLAT_EMIT_WARP = 256;
+
 // entry i's pairs at off[i], partners ascending (edge-edge keys take the
 // lower edge first: swept cells order edges by x, not by id)
 __global__ void k_flat_emit(PairArgs A, const uint64_t* __restrict__ toff, const uint32_t* __restrict__ lflag,
@@ -938,19 +943,32 @@ __global__ void k_flat_emit(PairArgs A, const uint64_t* __restrict__ toff, const
     type = CB_KEY_EE;
     ibase = jbase = (uint32_t)(t.n + t.T);
   }
+  const uint64_t f0 = lflag[i] ? toff[lpos[i]] : 0, f1 = lflag[i] ? toff[lpos[i] + 1] : 0;
   const uint32_t j0 = j0s[i];
   size_t o = off[i];
-  for (uint32_t word = sbits[i]; word;) {  // a short range (a long one: k_flat_emit_long)
+  for (uint32_t word = sbits[i]; word;) {  // a short range
     const uint32_t b = (uint32_t)__ffs(word) - 1u;
     word &= word - 1u;
     const uint32_t Q = A.eval[j0 + b];
     const bool swap = type == CB_KEY_EE && Q < P;
     out[o++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
   }
+  if (f1 > f0 && f1 - f0 < FLAT_EMIT_WARP) {  // a long range, not long enough for k_flat_emit_long
+    for (uint64_t wd = f0 >> 5; wd <= (f1 - 1) >> 5; ++wd) {
+      uint32_t word = flat_word(bits, wd, f0, f1);
+      while (word) {
+        const uint32_t b = (uint32_t)__ffs(word) - 1u;
+        word &= word - 1u;
+        const uint32_t Q = A.eval[j0 + (uint32_t)((wd << 5) + b - f0)];
+        const bool swap = type == CB_KEY_EE && Q < P;
+        out[o++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
+      }
+    }
+  }
 }
 
-// The pairs of the long entries (their slots laid end to end), after their
-// short pairs: a warp per entry, lane l taking hit word l of each run of 32,
+// The pairs of the entries with at least FLAT_EMIT_WARP slots (laid end to
+// end), after their short pairs: a warp per entry, lane l taking hit word l of each run of 32,
 // a warp scan of the words' hit counts placing each lane's pairs, so that
 // the warp writes one contiguous run per 32 words.  Grid-stride over the
 // long entries, whose count is lpos[ne].
@@ -968,7 +986,7 @@ __global__ void __launch_bounds__(256) k_flat_emit_long(PairArgs A, const uint64
   for (int64_t wl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wl < nl; wl += nwarps) {
     const uint32_t i = lidx[wl];
     const uint64_t f0 = toff[wl], f1 = toff[wl + 1];
-    if (f1 <= f0) continue;
+    if (f1 - f0 < FLAT_EMIT_WARP) continue;  // written by k_flat_emit
     const uint32_t P = A.eval[i];
     uint32_t type, ibase = 0, jbase = 0;
     if (P < (uint32_t)t.n) {
