@@ -51,8 +51,9 @@ struct CcdArgs {
   const int32_t* __restrict__ win;
   const int32_t* __restrict__ wst;
   const int32_t* __restrict__ rloop;
-  const uint64_t* __restrict__ fhash;  // hash set of the rest-filtered keys (frest.cuh)
-  uint64_t fmask;
+  const uint64_t* __restrict__ frest;  // sorted rest-filtered keys
+  const uint32_t* __restrict__ frow_pt;  // ... their row offsets by vertex and by edge (frest.cuh)
+  const uint32_t* __restrict__ frow_ee;
   int64_t nf;
   int T, n, kind;
   const int32_t* __restrict__ vsc;           // member of each vertex
@@ -89,7 +90,7 @@ __device__ __forceinline__ bool is_filtered(const CcdArgs& A, const MemberParams
   if (M.filter_off) return false;
   if (A.kind == CB_ROD) return A.comp[A.ev0[ki]] == A.comp[A.ev0[kj]] && rod_filtered(A.win, A.wst, M.loops != 0, ki, kj);
   if (A.nf <= 0) return false;
-  return frest_contains(A.fhash, A.fmask, key);
+  return frest_contains(A.frest, A.frow_pt, A.frow_ee, key);
 }
 
 // Everything additive CCD needs before its first step.
@@ -504,8 +505,9 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     A.win = bp<int32_t>(s->win);
     A.wst = bp<int32_t>(s->wst);
     A.rloop = bp<int32_t>(s->rloop);
-    A.fhash = bp<uint64_t>(s->fhash);
-    A.fmask = s->fhash_mask;
+    A.frest = bp<uint64_t>(s->frest);
+    A.frow_pt = bp<uint32_t>(s->frow_pt);
+    A.frow_ee = bp<uint32_t>(s->frow_ee);
     A.nf = s->n_frest;
     A.T = s->T;
     A.n = s->n;

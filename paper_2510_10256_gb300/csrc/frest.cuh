@@ -1,33 +1,28 @@
 // frest.cuh -- filter membership (Sec. 3.2).  Shells: a candidate is
 // filtered iff its stencil is in the rest-filter table built at scene
-// creation.  Rods: through the per-edge arc-length windows (below).
+// creation.  Rods: through the per-edge arc-length windows (below).  The shell
+// table is sorted by key (type, i, j), so the keys with one first primitive i
+// form a contiguous row; per-row offsets (by vertex for point-triangle keys,
+// by edge for edge-edge keys) bound the search to that row, a few dozen keys
+// that consecutive candidates (in hash-cell order, grouped by i) share.
 #pragma once
 #include <cstdint>
 
 #include "common.cuh"
 
-// The table's keys are also held in an open-addressing hash set (built with
-// the row offsets, at most half full; an empty slot holds FREST_EMPTY, which
-// no key equals: its type bits would be 3), probed linearly from a mixed
-// hash of the key -- one or two dependent loads per lookup instead of a
-// binary search's chain.  The mixer is the SplitMix64 finalizer (Vigna).
-constexpr uint64_t FREST_EMPTY = ~0ull;
-
-__host__ __device__ __forceinline__ uint64_t frest_hash(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-  return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ bool frest_contains(const uint64_t* __restrict__ tab, uint64_t mask, uint64_t key) {
-  uint64_t h = frest_hash(key) & mask;
-  for (uint64_t probe = 0; probe <= mask; ++probe) {
-    const uint64_t v = tab[h];
-    if (v == key) return true;
-    if (v == FREST_EMPTY) return false;
-    h = (h + 1) & mask;
+__device__ __forceinline__ bool frest_contains(const uint64_t* __restrict__ frest,
+                                               const uint32_t* __restrict__ row_pt,
+                                               const uint32_t* __restrict__ row_ee, uint64_t key) {
+  const uint32_t i = cb_key_i(key);
+  const uint32_t* __restrict__ row = cb_key_type(key) == CB_KEY_PT ? row_pt : row_ee;
+  const int64_t end = row[i + 1];
+  int64_t lo = row[i], hi = end;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (frest[mid] < key) lo = mid + 1;
+    else hi = mid;
   }
-  return false;
+  return lo < end && frest[lo] == key;
 }
 
 // Rods: edges ki < kj of one polyline are filtered when kj is within the

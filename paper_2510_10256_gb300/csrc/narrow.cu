@@ -199,8 +199,8 @@ __global__ void k_filter_rod(int64_t nc, const uint64_t* __restrict__ cand, cons
   if ((threadIdx.x & 31) == 0 && b) atomicAdd(SA.ndrop, (unsigned long long)__popc(b));
 }
 
-__global__ void k_filter_shell(int64_t nc, const uint64_t* __restrict__ cand, const uint64_t* __restrict__ fhash,
-                               uint64_t fmask, int64_t nf,
+__global__ void k_filter_shell(int64_t nc, const uint64_t* __restrict__ cand, const uint64_t* __restrict__ frest,
+                               const uint32_t* __restrict__ row_pt, const uint32_t* __restrict__ row_ee, int64_t nf,
                                const int32_t* __restrict__ ev0, const int32_t* __restrict__ vsc,
                                const MemberParams* __restrict__ mp, uint8_t* __restrict__ klass,
                                unsigned long long* __restrict__ nfilt, int n, int T, StencilArgs SA) {
@@ -211,7 +211,7 @@ __global__ void k_filter_shell(int64_t nc, const uint64_t* __restrict__ cand, co
     const bool pt = cb_key_type(key) == CB_KEY_PT;
     const int v0 = pt ? (int)cb_key_i(key) : ev0[cb_key_i(key)];
     const MemberParams& M = mp[vsc[v0]];
-    if (!M.filter_off && nf > 0) f = frest_contains(fhash, fmask, key) ? 1u : 0u;
+    if (!M.filter_off && nf > 0) f = frest_contains(frest, row_pt, row_ee, key) ? 1u : 0u;
     uint8_t kl = (uint8_t)f;
     if (f && M.per_stencil) {
       // broad-phase primitive ids: vertices, then triangles, then edges
@@ -2613,39 +2613,32 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st) {
   return CB_OK;
 }
 
-// The hash set of the rest-filter table's keys (frest.cuh): linear probing
-// from the key's mixed hash, slots claimed with atomicCAS; the table holds
-// at least twice as many slots as keys, so every probe sequence ends.
-__global__ void k_frest_hash(int64_t nf, const uint64_t* __restrict__ frest, unsigned long long* __restrict__ tab,
-                             uint64_t mask, unsigned long long* __restrict__ err) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nf) return;
-  const unsigned long long key = frest[i];
-  uint64_t h = frest_hash(key) & mask;
-  for (uint64_t probe = 0; probe <= mask; ++probe) {
-    const unsigned long long prev = atomicCAS(&tab[h], (unsigned long long)FREST_EMPTY, key);
-    if (prev == FREST_EMPTY || prev == key) return;
-    h = (h + 1) & mask;
+// Row offsets of the sorted rest-filter table: row[r] = first index whose key
+// is at or above (type, r, 0), for r = 0..nrows (row[nrows] ends the type).
+__global__ void k_frest_rows(int64_t nrows, uint32_t type, const uint64_t* __restrict__ frest, int64_t nf,
+                             uint32_t* __restrict__ row) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > nrows) return;
+  const uint64_t bound = ((uint64_t)type << 62) | ((uint64_t)r << 31);
+  int64_t lo = 0, hi = nf;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (frest[mid] < bound) lo = mid + 1;
+    else hi = mid;
   }
-  atomicOr(err, 1ull);  // no free slot: not reachable at half load
+  row[r] = (uint32_t)lo;
 }
 
-cb_status frest_hash_build(cb_scene* s, cudaStream_t st) {
+cb_status frest_rows_build(cb_scene* s, cudaStream_t st) {
   if (s->kind != CB_SHELL || s->n_frest <= 0) return CB_OK;
-  uint64_t slots = 1024;
-  while (slots < 2 * (uint64_t)s->n_frest) slots <<= 1;
-  CB_TRY(buf_ensure(s->fhash, sizeof(uint64_t) * (size_t)slots, st));
-  s->fhash_mask = slots - 1;
-  CB_CUDA(cudaMemsetAsync(s->fhash.p, 0xff, sizeof(uint64_t) * (size_t)slots, st));
-  unsigned long long* err = (unsigned long long*)(scalars(s) + SC_COUNT1);
-  CB_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned long long), st));
-  k_frest_hash<<<cb_grid(s->n_frest), CB_THREADS, 0, cb_count(st)>>>(s->n_frest, bp<uint64_t>(s->frest),
-                                                                    bp<unsigned long long>(s->fhash), s->fhash_mask,
-                                                                    err);
+  CB_TRY(buf_ensure(s->frow_pt, sizeof(uint32_t) * ((size_t)s->n + 1), st));
+  CB_TRY(buf_ensure(s->frow_ee, sizeof(uint32_t) * ((size_t)s->E + 1), st));
+  k_frest_rows<<<cb_grid((int64_t)s->n + 1), CB_THREADS, 0, cb_count(st)>>>(s->n, CB_KEY_PT, bp<uint64_t>(s->frest),
+                                                                           s->n_frest, bp<uint32_t>(s->frow_pt));
+  k_frest_rows<<<cb_grid((int64_t)s->E + 1), CB_THREADS, 0, cb_count(st)>>>(s->E, CB_KEY_EE, bp<uint64_t>(s->frest),
+                                                                           s->n_frest, bp<uint32_t>(s->frow_ee));
   CB_CUDA(cudaGetLastError());
-  uint64_t h;
-  CB_TRY(read_scalars(s, SC_COUNT1, 1, &h, st));
-  return h ? CB_ERR_CUDA : CB_OK;
+  return CB_OK;
 }
 
 cb_status filter_apply(cb_scene* s, cudaStream_t st) {
@@ -2670,7 +2663,8 @@ cb_status filter_apply(cb_scene* s, cudaStream_t st) {
         bp<uint8_t>(s->klass), nf, SA);
   else
     k_filter_shell<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(
-        nc, bp<uint64_t>(s->cand), bp<uint64_t>(s->fhash), s->fhash_mask, s->n_frest, bp<int32_t>(s->ev0), bp<int32_t>(s->vsc), bp<MemberParams>(s->mp), bp<uint8_t>(s->klass), nf,
+        nc, bp<uint64_t>(s->cand), bp<uint64_t>(s->frest), bp<uint32_t>(s->frow_pt), bp<uint32_t>(s->frow_ee),
+        s->n_frest, bp<int32_t>(s->ev0), bp<int32_t>(s->vsc), bp<MemberParams>(s->mp), bp<uint8_t>(s->klass), nf,
         s->n, s->T, SA);
   CB_CUDA(cudaGetLastError());
   if (!ps) return CB_OK;

@@ -166,8 +166,8 @@ struct cb_scene {
   DevBuf dbar_comp;     // uint64 bits of the per-component dbar_min, by component label (n entries)
   double dbar_fmax = 0.0;  // largest per-component dbar_min (finite), or dbar_min
   int64_t n_frest = 0;
-  DevBuf fhash;         // uint64 shells: hash set of the frest keys (frest.cuh), fhash_mask + 1 slots
-  uint64_t fhash_mask = 0;
+  DevBuf frow_pt;       // uint32 shells: row offsets of frest by vertex (point-triangle keys), n + 1
+  DevBuf frow_ee;       // uint32 shells: row offsets of frest by edge (edge-edge keys), E + 1
 
   // pass state
   BroadWork bw;         // static broad phase
@@ -290,7 +290,7 @@ cb_status filter_precompute(cb_scene* s, cudaStream_t st);
 cb_status geo_rest_dbar(cb_scene* s, const uint64_t* cand, int64_t nc, uint32_t* flag, double* dbar,
                         unsigned long long* dmin, unsigned long long* dcomp, cudaStream_t st);
 cb_status filter_apply(cb_scene* s, cudaStream_t st);
-cb_status frest_hash_build(cb_scene* s, cudaStream_t st);
+cb_status frest_rows_build(cb_scene* s, cudaStream_t st);
 // energy_only: distances and energy (no active list, gradient, Hessian or BSR)
 cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad, bool energy_only,
                       cudaStream_t st);
