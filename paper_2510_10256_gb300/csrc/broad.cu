@@ -983,42 +983,52 @@ __global__ void __launch_bounds__(256) k_flat_emit_long(PairArgs A, const uint64
   const int64_t nl = lpos[A.ne];
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const Topo& t = A.t;
-  for (int64_t wl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wl < nl; wl += nwarps) {
-    const uint32_t i = lidx[wl];
-    const uint64_t f0 = toff[wl], f1 = toff[wl + 1];
-    if (f1 - f0 < FLAT_EMIT_WARP) continue;  // written by k_flat_emit
-    const uint32_t P = A.eval[i];
-    uint32_t type, ibase = 0, jbase = 0;
-    if (P < (uint32_t)t.n) {
-      type = CB_KEY_PT;
-      jbase = (uint32_t)t.n;
-    } else {
-      type = CB_KEY_EE;
-      ibase = jbase = (uint32_t)(t.n + t.T);
-    }
-    const uint32_t j0 = j0s[i];
-    size_t o = (size_t)off[i] + (size_t)__popc(sbits[i]);
-    const uint64_t w_end = (f1 - 1) >> 5;
-    for (uint64_t w0 = f0 >> 5; w0 <= w_end; w0 += 32) {
-      const uint64_t wd = w0 + (uint64_t)lane;
-      uint32_t word = wd <= w_end ? flat_word(bits, wd, f0, f1) : 0u;
-      const uint32_t c = (uint32_t)__popc(word);
-      uint32_t before = c;  // inclusive scan of the hit counts over the lanes
+  // 32 long entries per step: their range lengths read together, the ones of
+  // FLAT_EMIT_WARP slots or more taken one after another by the whole warp
+  for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < nl;
+       base += nwarps * 32) {
+    const int64_t mine = base + lane;
+    const uint64_t m0 = mine < nl ? toff[mine] : 0, m1 = mine < nl ? toff[mine + 1] : 0;
+    unsigned sel = __ballot_sync(0xffffffffu, m1 - m0 >= FLAT_EMIT_WARP);
+    while (sel) {
+      const int k = __ffs(sel) - 1;
+      sel &= sel - 1u;
+      const int64_t wl = base + k;
+      const uint64_t f0 = __shfl_sync(0xffffffffu, m0, k), f1 = __shfl_sync(0xffffffffu, m1, k);
+      const uint32_t i = lidx[wl];
+      const uint32_t P = A.eval[i];
+      uint32_t type, ibase = 0, jbase = 0;
+      if (P < (uint32_t)t.n) {
+        type = CB_KEY_PT;
+        jbase = (uint32_t)t.n;
+      } else {
+        type = CB_KEY_EE;
+        ibase = jbase = (uint32_t)(t.n + t.T);
+      }
+      const uint32_t j0 = j0s[i];
+      size_t o = (size_t)off[i] + (size_t)__popc(sbits[i]);
+      const uint64_t w_end = (f1 - 1) >> 5;
+      for (uint64_t w0 = f0 >> 5; w0 <= w_end; w0 += 32) {
+        const uint64_t wd = w0 + (uint64_t)lane;
+        uint32_t word = wd <= w_end ? flat_word(bits, wd, f0, f1) : 0u;
+        const uint32_t c = (uint32_t)__popc(word);
+        uint32_t before = c;  // inclusive scan of the hit counts over the lanes
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xffffffffu, before, d);
-        if (lane >= d) before += u;
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t u = __shfl_up_sync(0xffffffffu, before, d);
+          if (lane >= d) before += u;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, before, 31);
+        size_t q = o + before - c;
+        while (word) {
+          const uint32_t b = (uint32_t)__ffs(word) - 1u;
+          word &= word - 1u;
+          const uint32_t Q = A.eval[j0 + (uint32_t)((wd << 5) + b - f0)];
+          const bool swap = type == CB_KEY_EE && Q < P;
+          out[q++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
+        }
+        o += total;
       }
-      const uint32_t total = __shfl_sync(0xffffffffu, before, 31);
-      size_t q = o + before - c;
-      while (word) {
-        const uint32_t b = (uint32_t)__ffs(word) - 1u;
-        word &= word - 1u;
-        const uint32_t Q = A.eval[j0 + (uint32_t)((wd << 5) + b - f0)];
-        const bool swap = type == CB_KEY_EE && Q < P;
-        out[q++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
-      }
-      o += total;
     }
   }
 }
