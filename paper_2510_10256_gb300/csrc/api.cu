@@ -96,7 +96,7 @@ static void scene_release(cb_scene* s) {
                     &w->eval[0], &w->eval[1], &w->run_flag, &w->run_id,   &w->run_start, &w->pair_cnt,
                     &w->pair_off, &w->ebox, &w->ckey[0], &w->ckey[1],  &w->stage, &w->ovl, &w->scan_tmp, &w->hist,
                     &w->flat_len, &w->flat_off, &w->flat_j0, &w->flat_bits, &w->flat_slen, &w->flat_sbits,
-                    &w->flat_lflag, &w->flat_lpos, &w->flat_lidx, &w->flat_llen};
+                    &w->flat_lflag, &w->flat_lpos, &w->flat_lidx, &w->flat_llen, &w->flat_vlong};
     for (DevBuf* b : wb) buf_free(*b, st);
   }
   cudaStreamSynchronize(st);

@@ -906,10 +906,18 @@ __device__ __forceinline__ uint32_t flat_word(const uint32_t* __restrict__ bits,
   return word;
 }
 
-// pairs per entry: the hits of its short word or of its slots
+// Slots of an entry's range from which its pairs are written by a warp
+// (k_flat_emit_long) rather than by the entry's thread: shorter ranges
+// would leave most of the warp's lanes without a word.
+constexpr uint64_t FLAT_EMIT_WARP = 256;
+
+// pairs per entry: the hits of its short word or of its slots; the long
+// entries of FLAT_EMIT_WARP slots or more are listed (by their index among
+// the long entries, in no particular order) for k_flat_emit_long
 __global__ void k_flat_count(int64_t ne, const uint64_t* __restrict__ toff, const uint32_t* __restrict__ lflag,
                              const uint32_t* __restrict__ lpos, const uint32_t* __restrict__ bits,
-                             const uint32_t* __restrict__ sbits, uint32_t* __restrict__ cnt) {
+                             const uint32_t* __restrict__ sbits, uint32_t* __restrict__ cnt,
+                             uint32_t* __restrict__ vlong, unsigned int* __restrict__ nvlong) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ne) return;
   uint32_t c = __popc(sbits[i]);
@@ -917,12 +925,8 @@ __global__ void k_flat_count(int64_t ne, const uint64_t* __restrict__ toff, cons
   if (f1 > f0)
     for (uint64_t wd = f0 >> 5; wd <= (f1 - 1) >> 5; ++wd) c += __popc(flat_word(bits, wd, f0, f1));
   cnt[i] = c;
+  if (f1 > f0 && f1 - f0 >= FLAT_EMIT_WARP) vlong[atomicAdd(nvlong, 1u)] = lpos[i];
 }
-
-// Slots of an entry's range from which its pairs are written by a warp
-// (k_flat_emit_long) rather than by the entry's thread: shorter ranges
-// would leave most of the warp's lanes without a word.
-constexpr uint64_t FLAT_EMIT_WARP = 256;
 
 // entry i's pairs at off[i], partners ascending (edge-edge keys take the
 // lower edge first: swept cells order edges by x, not by id)
@@ -968,67 +972,59 @@ __global__ void k_flat_emit(PairArgs A, const uint64_t* __restrict__ toff, const
 }
 
 // The pairs of the entries with at least FLAT_EMIT_WARP slots (laid end to
-// end), after their short pairs: a warp per entry, lane l taking hit word l of each run of 32,
-// a warp scan of the words' hit counts placing each lane's pairs, so that
-// the warp writes one contiguous run per 32 words.  Grid-stride over the
-// long entries, whose count is lpos[ne].
+// end), after their short pairs: a warp per entry, lane l taking hit word l
+// of each run of 32, a warp scan of the words' hit counts placing each
+// lane's pairs, so that the warp writes one contiguous run per 32 words.
+// Grid-stride over the list k_flat_count made of those entries (*nvlong of
+// them), so that neighbouring heavy entries go to different warps.
 __global__ void __launch_bounds__(256) k_flat_emit_long(PairArgs A, const uint64_t* __restrict__ toff,
                                                         const uint32_t* __restrict__ lidx,
-                                                        const uint32_t* __restrict__ lpos,
+                                                        const uint32_t* __restrict__ vlong,
+                                                        const unsigned int* __restrict__ nvlong,
                                                         const uint32_t* __restrict__ j0s,
                                                         const uint32_t* __restrict__ bits,
                                                         const uint32_t* __restrict__ sbits,
                                                         const uint32_t* __restrict__ off, uint64_t* __restrict__ out) {
   const int lane = threadIdx.x & 31;
-  const int64_t nl = lpos[A.ne];
+  const int64_t nv = *nvlong;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const Topo& t = A.t;
-  // 32 long entries per step: their range lengths read together, the ones of
-  // FLAT_EMIT_WARP slots or more taken one after another by the whole warp
-  for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < nl;
-       base += nwarps * 32) {
-    const int64_t mine = base + lane;
-    const uint64_t m0 = mine < nl ? toff[mine] : 0, m1 = mine < nl ? toff[mine + 1] : 0;
-    unsigned sel = __ballot_sync(0xffffffffu, m1 - m0 >= FLAT_EMIT_WARP);
-    while (sel) {
-      const int k = __ffs(sel) - 1;
-      sel &= sel - 1u;
-      const int64_t wl = base + k;
-      const uint64_t f0 = __shfl_sync(0xffffffffu, m0, k), f1 = __shfl_sync(0xffffffffu, m1, k);
-      const uint32_t i = lidx[wl];
-      const uint32_t P = A.eval[i];
-      uint32_t type, ibase = 0, jbase = 0;
-      if (P < (uint32_t)t.n) {
-        type = CB_KEY_PT;
-        jbase = (uint32_t)t.n;
-      } else {
-        type = CB_KEY_EE;
-        ibase = jbase = (uint32_t)(t.n + t.T);
-      }
-      const uint32_t j0 = j0s[i];
-      size_t o = (size_t)off[i] + (size_t)__popc(sbits[i]);
-      const uint64_t w_end = (f1 - 1) >> 5;
-      for (uint64_t w0 = f0 >> 5; w0 <= w_end; w0 += 32) {
-        const uint64_t wd = w0 + (uint64_t)lane;
-        uint32_t word = wd <= w_end ? flat_word(bits, wd, f0, f1) : 0u;
-        const uint32_t c = (uint32_t)__popc(word);
-        uint32_t before = c;  // inclusive scan of the hit counts over the lanes
+  for (int64_t v = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < nv; v += nwarps) {
+    const uint32_t wl = vlong[v];
+    const uint64_t f0 = toff[wl], f1 = toff[wl + 1];
+    const uint32_t i = lidx[wl];
+    const uint32_t P = A.eval[i];
+    uint32_t type, ibase = 0, jbase = 0;
+    if (P < (uint32_t)t.n) {
+      type = CB_KEY_PT;
+      jbase = (uint32_t)t.n;
+    } else {
+      type = CB_KEY_EE;
+      ibase = jbase = (uint32_t)(t.n + t.T);
+    }
+    const uint32_t j0 = j0s[i];
+    size_t o = (size_t)off[i] + (size_t)__popc(sbits[i]);
+    const uint64_t w_end = (f1 - 1) >> 5;
+    for (uint64_t w0 = f0 >> 5; w0 <= w_end; w0 += 32) {
+      const uint64_t wd = w0 + (uint64_t)lane;
+      uint32_t word = wd <= w_end ? flat_word(bits, wd, f0, f1) : 0u;
+      const uint32_t c = (uint32_t)__popc(word);
+      uint32_t before = c;  // inclusive scan of the hit counts over the lanes
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const uint32_t u = __shfl_up_sync(0xffffffffu, before, d);
-          if (lane >= d) before += u;
-        }
-        const uint32_t total = __shfl_sync(0xffffffffu, before, 31);
-        size_t q = o + before - c;
-        while (word) {
-          const uint32_t b = (uint32_t)__ffs(word) - 1u;
-          word &= word - 1u;
-          const uint32_t Q = A.eval[j0 + (uint32_t)((wd << 5) + b - f0)];
-          const bool swap = type == CB_KEY_EE && Q < P;
-          out[q++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
-        }
-        o += total;
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, before, d);
+        if (lane >= d) before += u;
       }
+      const uint32_t total = __shfl_sync(0xffffffffu, before, 31);
+      size_t q = o + before - c;
+      while (word) {
+        const uint32_t b = (uint32_t)__ffs(word) - 1u;
+        word &= word - 1u;
+        const uint32_t Q = A.eval[j0 + (uint32_t)((wd << 5) + b - f0)];
+        const bool swap = type == CB_KEY_EE && Q < P;
+        out[q++] = pair_key(A, type, (swap ? Q : P) - ibase, (swap ? P : Q) - jbase);
+      }
+      o += total;
     }
   }
 }
@@ -1177,6 +1173,7 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
   // keys are final from the count pass on: canonical straight out, compact for the sort
   A.canonical = !sort_out;
   unsigned int* novl = (unsigned int*)(scalars(s) + SC_NOVF);
+  unsigned int* nvlong = (unsigned int*)(scalars(s) + SC_NVLONG);
   uint32_t* c = bp<uint32_t>(w.pair_cnt);
   uint64_t flat_t = 0;
   if (rods) {
@@ -1219,9 +1216,12 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
       k_pairs_flat<<<(int)g, 32 * FLAT_WARPS, 0, cb_count(st)>>>(A, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_lidx),
                                                     bp<uint32_t>(w.flat_j0), flat_t, bp<uint32_t>(w.flat_bits));
     }
+    CB_TRY(buf_ensure(w.flat_vlong, sizeof(uint32_t) * (size_t)ne, st));
+    CB_CUDA(cudaMemsetAsync(nvlong, 0, sizeof(unsigned int), st));
     k_flat_count<<<cb_grid(ne), CB_THREADS, 0, cb_count(st)>>>(ne, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_lflag),
                                                               bp<uint32_t>(w.flat_lpos), bp<uint32_t>(w.flat_bits),
-                                                              bp<uint32_t>(w.flat_sbits), c);
+                                                              bp<uint32_t>(w.flat_sbits), c,
+                                                              bp<uint32_t>(w.flat_vlong), nvlong);
   }
   // the fill: rods move their staged keys and re-test the entries with more;
   // shells write the pairs of their hit bits
@@ -1240,7 +1240,7 @@ cb_status broad_phase(cb_scene* s, BroadWork& w, const double* x, const double* 
       if (flat_t > 0) {
         const int g = (int)std::min<int64_t>(cb_grid(ne, 256), (int64_t)s->n_sms * 16);
         k_flat_emit_long<<<g, 256, 0, cb_count(st)>>>(A, bp<uint64_t>(w.flat_off), bp<uint32_t>(w.flat_lidx),
-                                                      bp<uint32_t>(w.flat_lpos), bp<uint32_t>(w.flat_j0),
+                                                      bp<uint32_t>(w.flat_vlong), nvlong, bp<uint32_t>(w.flat_j0),
                                                       bp<uint32_t>(w.flat_bits), bp<uint32_t>(w.flat_sbits), f, o);
       }
     }

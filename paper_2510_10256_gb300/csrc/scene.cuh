@@ -105,6 +105,7 @@ struct BroadWork {
   DevBuf flat_lpos;   // shells: uint32 per entry (+1), its place among the long entries (scan of flat_lflag)
   DevBuf flat_lidx;   // shells: uint32 per long entry, the entry
   DevBuf flat_llen;   // shells: uint32 per long entry (+1), its range length
+  DevBuf flat_vlong;  // shells: uint32, the long entries with ranges of FLAT_EMIT_WARP slots or more (any order)
   DevBuf flat_off;    // shells: uint64 per long entry (+1), its first test slot (scan of flat_llen)
   DevBuf flat_j0;     // shells: uint32 per entry, its first partner
   DevBuf flat_bits;   // shells: one hit bit per test slot
@@ -261,7 +262,8 @@ enum {
   SC_NMOLL = 20,        // barrier_eval: mollified edge-edge pairs
   SC_GEO_COUNT = 21,    // geodesic rest filter: (edge, vertex) entries below the activation
   SC_GEO_ERR = 22,      // ... error bits of its sources (a fixed capacity exceeded)
-  SC_N = 23
+  SC_NVLONG = 23,       // shell broad phase: entries of flat_vlong
+  SC_N = 24
 };
 // read_scalars stages up to SC_N scalars through the pinned host scratch
 static_assert(SC_N <= 64, "the scalars must fit the pinned scratch");
