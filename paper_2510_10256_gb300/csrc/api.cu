@@ -859,10 +859,7 @@ cb_status cb_get_ccd(cb_scene* s, uint64_t* keys, double* t, uint8_t* klass, int
     std::vector<uint8_t> cc;
     CB_TRY(dl(k, s->ccd_keys, s->n_ccd, st));
     if (t) CB_TRY(dl(tt, s->ccd_t, s->n_ccd, st));
-    if (klass) {
-      CB_TRY(ccd_classes_resolve(s, st));
-      CB_TRY(dl(cc, s->ccd_cls, s->n_ccd, st));
-    }
+    if (klass) CB_TRY(dl(cc, s->ccd_cls, s->n_ccd, st));
     CB_CUDA(cudaStreamSynchronize(st));
     std::vector<uint32_t> order;
     sort_keys(k, &order);

@@ -40,7 +40,6 @@ constexpr double ACCD_S = 0.1;
 constexpr double ACCD_C = 0.9;
 constexpr int ACCD_MAX_ITER = 10000;
 constexpr uint8_t EXACT = 0x80;   // class byte flag: t_p is exact (else a lower bound)
-constexpr uint8_t CLS_DEFER = 4;  // class byte: F or U, looked up when the classes are read
 
 struct CcdArgs {
   int64_t np;
@@ -220,10 +219,7 @@ __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restric
     }
     mem = A.vsc[v[0]];
     const MemberParams& M = A.mp[mem];
-    // shells with a rest-filter table: the lookup runs only where the class
-    // changes the bound (below); elsewhere the class is known at once
-    bool have_cls = A.kind != CB_SHELL || M.filter_off || A.nf <= 0;
-    bool filt = have_cls ? is_filtered(A, M, key, ki, kj) : false;
+    const bool filt = is_filtered(A, M, key, ki, kj);
     need = true;
     // Kaldor culling (rods: edges numbered along each polyline): the pair
     // does not constrain the step
@@ -238,11 +234,9 @@ __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restric
       const double Xd = A.cx[4 * mem + 3];
       const float lb = cbb::lower_bound(ee, ldf(A.xf, A.n, v[0]), ldf(A.xf, A.n, v[1]), ldf(A.xf, A.n, v[2]),
                                         ldf(A.xf, A.n, v[3]), (float)Xd);
-      if (!have_cls && !(lb >= M.thrC32)) {  // may be class C unless filtered
-        filt = is_filtered(A, M, key, ki, kj);
-        have_cls = true;
-      }
       if (filt || lb >= M.thrC32) {  // surely not class C at or above thrC32
+        const int cls = filt ? 1 : 0;
+        const float off = (cls == 0 && !M.single) ? M.xi32 : 0.f;
         const cbb::f3 p0 = ldf(A.pf, A.n, v[0]), p1 = ldf(A.pf, A.n, v[1]), p2 = ldf(A.pf, A.n, v[2]),
                       p3 = ldf(A.pf, A.n, v[3]);
         const cbb::f3 pm = cbb::fscale3(cbb::fadd3(cbb::fadd3(p0, p1), cbb::fadd3(p2, p3)), 0.25f);
@@ -255,35 +249,10 @@ __global__ void __launch_bounds__(128) k_ccd_screen(CcdArgs A, double* __restric
         const float u64 = 3.8146973e-6f;  // 64 u, u = 2^-24: exact
         const float lp_ub = __fadd_ru(__fmul_ru(lp32, 1.f + u64), __fmul_ru(u64, Pm));
         const float slack = __fmul_ru(1e-12f, __fadd_ru(1.f, __double2float_ru(Xd)));
-        // lower bound of the first step for offset off, (1 - s) g / l_p (0.9f
-        // rounds below 0.9 = 1 - s); -1 where no positive bound exists
-        auto first_step = [&](float off) -> float {
-          const float g_lb = __fsub_rd(__fsub_rd(lb, off), slack);
-          if (!(lp32 > 1e-30f && g_lb > 0.f)) return -1.f;
-          return __fmul_rd(__fdiv_rd(__fmul_rd(0.9f, g_lb), lp_ub), 0.99999988f);
-        };
-        bool deferred = false;
-        if (!have_cls) {
-          // surely not class C; with the unfiltered offset the step bound is
-          // the smallest the pair can have (the filtered offset is 0), so if
-          // it already clears t = 1 the class changes nothing: its lookup
-          // waits for cb_get_ccd
-          if (first_step(M.single ? 0.f : M.xi32) > 1.f) {
-            deferred = true;
-          } else {
-            filt = is_filtered(A, M, key, ki, kj);
-            have_cls = true;
-          }
-        }
-        const int cls = filt ? 1 : 0;
-        const float off = (cls == 0 && !M.single) ? M.xi32 : 0.f;
-        const float tl_lb = deferred ? 2.f : first_step(off);
-        if (deferred) {
-          A.t_out[q] = 1.0;
-          A.cls_out[q] = CLS_DEFER | EXACT;
-          m_exact = 1.0;
-          need = false;
-        } else if (tl_lb >= 0.f) {
+        const float g_lb = __fsub_rd(__fsub_rd(lb, off), slack);
+        if (lp32 > 1e-30f && g_lb > 0.f) {
+          // (1 - s) g / l_p; 0.9f rounds below 0.9 = 1 - s
+          const float tl_lb = __fmul_rd(__fdiv_rd(__fmul_rd(0.9f, g_lb), lp_ub), 0.99999988f);
           const bool exact = tl_lb > 1.f;
           const double t = exact ? 1.0 : (double)tl_lb;
           A.t_out[q] = t;
@@ -499,19 +468,6 @@ __global__ void k_alpha_final(int count, const unsigned long long* __restrict__ 
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m < count) out[m] = __longlong_as_double(macc[(size_t)m * MACC_STRIDE + MACC_ALPHA]);
 }
-// the classes the first-step screen left to be looked up (CLS_DEFER): F or U
-__global__ void k_ccd_classes(int64_t np, const uint64_t* __restrict__ keys, const int32_t* __restrict__ ev0,
-                              const int32_t* __restrict__ vsc, const MemberParams* __restrict__ mp,
-                              const uint64_t* __restrict__ frest, const uint32_t* __restrict__ row_pt,
-                              const uint32_t* __restrict__ row_ee, uint8_t* __restrict__ cls) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= np || (cls[q] & 0x7f) != CLS_DEFER) return;
-  const uint64_t key = keys[q];
-  const int v0 = cb_key_type(key) == CB_KEY_PT ? (int)cb_key_i(key) : ev0[cb_key_i(key)];
-  const bool filt = !mp[vsc[v0]].filter_off && frest_contains(frest, row_pt, row_ee, key);
-  cls[q] = (uint8_t)(filt ? 1 : 0) | (cls[q] & EXACT);
-}
-
 __global__ void k_set(unsigned long long* p, unsigned long long v) { *p = v; }
 __global__ void k_macc_set(int count, unsigned long long* __restrict__ macc, int slot, unsigned long long v) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -519,15 +475,6 @@ __global__ void k_macc_set(int count, unsigned long long* __restrict__ macc, int
 }
 
 }  // namespace
-
-cb_status ccd_classes_resolve(cb_scene* s, cudaStream_t st) {
-  if (s->kind != CB_SHELL || s->n_ccd <= 0 || s->n_frest <= 0) return CB_OK;
-  k_ccd_classes<<<cb_grid(s->n_ccd), CB_THREADS, 0, cb_count(st)>>>(
-      s->n_ccd, bp<uint64_t>(s->ccd_keys), bp<int32_t>(s->ev0), bp<int32_t>(s->vsc), bp<MemberParams>(s->mp),
-      bp<uint64_t>(s->frest), bp<uint32_t>(s->frow_pt), bp<uint32_t>(s->frow_ee), bp<uint8_t>(s->ccd_cls));
-  CB_CUDA(cudaGetLastError());
-  return CB_OK;
-}
 
 cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, cudaStream_t st) {
   CB_TRY(broad_phase(s, s->bwc, x, p, true, false, s->ccd_keys, &s->n_ccd, st));

@@ -293,9 +293,6 @@ cb_status geo_rest_dbar(cb_scene* s, const uint64_t* cand, int64_t nc, uint32_t*
                         unsigned long long* dmin, unsigned long long* dcomp, cudaStream_t st);
 cb_status filter_apply(cb_scene* s, cudaStream_t st);
 cb_status frest_rows_build(cb_scene* s, cudaStream_t st);
-// ccd.cu: the classes of the CCD pairs whose first step left the rest-filter
-// lookup undone (t = 1 for either class); run before the classes are read
-cb_status ccd_classes_resolve(cb_scene* s, cudaStream_t st);
 // energy_only: distances and energy (no active list, gradient, Hessian or BSR)
 cb_status barrier_run(cb_scene* s, const double* x, double* energy, double* grad, bool energy_only,
                       cudaStream_t st);
