@@ -93,3 +93,22 @@ def test_curved_sheet_pass_matches_oracle(shape):
     sc = S.curved_sheet(shape=shape)
     rep = compare(sc, run_gpu(sc), O.contact_pass(sc))
     assert rep["F"] > 0 and rep["active"] > 0
+
+
+def test_geodesic_scenes_in_a_batch():
+    """Geodesic scenes keep their rest filters when batched with a plain
+    shell: each member's pass matches its own oracle."""
+    from tests.parity import run_gpu_batch
+    scenes = [S.curved_sheet(shape="dome", nx=16), S.curved_sheet(shape="saddle", nx=20, seed=S.BASE_SEED + 10),
+              S.tiny_shell(S.BASE_SEED + 11)]
+    for sc, g in zip(scenes, run_gpu_batch(scenes)):
+        rep = compare(sc, g, O.contact_pass(sc))
+        assert rep["C"] > 0
+
+
+def test_geodesic_with_per_component_widths():
+    """CB_DBAR_PER_COMPONENT on geodesic reference distances: each nested
+    sheet's filtered pairs take their own component's smallest dbar."""
+    sc = S.curved_sheet(shape="saddle", nx=24)
+    rep = compare(sc, run_gpu(sc, per_component=True), O.contact_pass(sc, per_component=True))
+    assert rep["F"] > 0
