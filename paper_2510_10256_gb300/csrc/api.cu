@@ -86,7 +86,7 @@ static void scene_release(cb_scene* s) {
   cudaStream_t st = s->last_stream;
   DevBuf* bufs[] = {&s->ev0, &s->ev1, &s->tv, &s->comp, &s->rest, &s->rod_ptr, &s->S, &s->win, &s->wst,
                     &s->rloop, &s->rlast, &s->elen2, &s->hmoll, &s->mlist, &s->ruv, &s->frest,
-                    &s->frest_dbar, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cand_alt, &s->klass_alt, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
+                    &s->frest_dbar, &s->frest_j, &s->frow_pt, &s->frow_ee, &s->dbar_comp, &s->cand, &s->klass, &s->cand_alt, &s->klass_alt, &s->cd, &s->cflag, &s->cpos, &s->ctype, &s->ccls, &s->aidx,
                     &s->bkey[0], &s->bkey[1], &s->bflag, &s->bpos, &s->bsr_row, &s->bsr_col, &s->bsr_val,
                     &s->row_cnt, &s->hB9, &s->hB6, &s->hB4, &s->hslot, &s->horder, &s->xf, &s->pf, &s->dlist, &s->mp, &s->vsc, &s->macc, &s->ccd_keys, &s->ccd_t, &s->ccd_cls, &s->ccd_lb, &s->ccd_flag, &s->ccd_pos, &s->ccd_list, &s->ccd_ulist, &s->scan_tmp, &s->hist,
                     &s->fr_key, &s->fr_st, &s->fr_dat, &s->fr_hw, &s->dev_scalars};

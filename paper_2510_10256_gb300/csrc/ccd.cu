@@ -51,7 +51,7 @@ struct CcdArgs {
   const int32_t* __restrict__ win;
   const int32_t* __restrict__ wst;
   const int32_t* __restrict__ rloop;
-  const uint64_t* __restrict__ frest;  // sorted rest-filtered keys
+  const uint32_t* __restrict__ frest_j;  // partner index j of the sorted rest-filtered keys
   const uint32_t* __restrict__ frow_pt;  // ... their row offsets by vertex and by edge (frest.cuh)
   const uint32_t* __restrict__ frow_ee;
   int64_t nf;
@@ -90,7 +90,7 @@ __device__ __forceinline__ bool is_filtered(const CcdArgs& A, const MemberParams
   if (M.filter_off) return false;
   if (A.kind == CB_ROD) return A.comp[A.ev0[ki]] == A.comp[A.ev0[kj]] && rod_filtered(A.win, A.wst, M.loops != 0, ki, kj);
   if (A.nf <= 0) return false;
-  return frest_contains(A.frest, A.frow_pt, A.frow_ee, key);
+  return frest_contains(A.frest_j, A.frow_pt, A.frow_ee, key);
 }
 
 // Everything additive CCD needs before its first step.
@@ -505,7 +505,7 @@ cb_status ccd_run(cb_scene* s, const double* x, const double* p, double* alpha, 
     A.win = bp<int32_t>(s->win);
     A.wst = bp<int32_t>(s->wst);
     A.rloop = bp<int32_t>(s->rloop);
-    A.frest = bp<uint64_t>(s->frest);
+    A.frest_j = bp<uint32_t>(s->frest_j);
     A.frow_pt = bp<uint32_t>(s->frow_pt);
     A.frow_ee = bp<uint32_t>(s->frow_ee);
     A.nf = s->n_frest;

@@ -10,19 +10,21 @@
 
 #include "common.cuh"
 
-__device__ __forceinline__ bool frest_contains(const uint64_t* __restrict__ frest,
-                                               const uint32_t* __restrict__ row_pt,
+// A row holds the keys of one (type, i), so the search compares only their
+// partner index j: fj[k] is the j of frest[k] (32 bits), which halves the
+// bytes a search touches.
+__device__ __forceinline__ bool frest_contains(const uint32_t* __restrict__ fj, const uint32_t* __restrict__ row_pt,
                                                const uint32_t* __restrict__ row_ee, uint64_t key) {
-  const uint32_t i = cb_key_i(key);
+  const uint32_t i = cb_key_i(key), j = cb_key_j(key);
   const uint32_t* __restrict__ row = cb_key_type(key) == CB_KEY_PT ? row_pt : row_ee;
   const int64_t end = row[i + 1];
   int64_t lo = row[i], hi = end;
   while (lo < hi) {
     const int64_t mid = (lo + hi) >> 1;
-    if (frest[mid] < key) lo = mid + 1;
+    if (fj[mid] < j) lo = mid + 1;
     else hi = mid;
   }
-  return lo < end && frest[lo] == key;
+  return lo < end && fj[lo] == j;
 }
 
 // Rods: edges ki < kj of one polyline are filtered when kj is within the

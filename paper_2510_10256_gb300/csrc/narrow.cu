@@ -199,7 +199,7 @@ __global__ void k_filter_rod(int64_t nc, const uint64_t* __restrict__ cand, cons
   if ((threadIdx.x & 31) == 0 && b) atomicAdd(SA.ndrop, (unsigned long long)__popc(b));
 }
 
-__global__ void k_filter_shell(int64_t nc, const uint64_t* __restrict__ cand, const uint64_t* __restrict__ frest,
+__global__ void k_filter_shell(int64_t nc, const uint64_t* __restrict__ cand, const uint32_t* __restrict__ frest_j,
                                const uint32_t* __restrict__ row_pt, const uint32_t* __restrict__ row_ee, int64_t nf,
                                const int32_t* __restrict__ ev0, const int32_t* __restrict__ vsc,
                                const MemberParams* __restrict__ mp, uint8_t* __restrict__ klass,
@@ -211,7 +211,7 @@ __global__ void k_filter_shell(int64_t nc, const uint64_t* __restrict__ cand, co
     const bool pt = cb_key_type(key) == CB_KEY_PT;
     const int v0 = pt ? (int)cb_key_i(key) : ev0[cb_key_i(key)];
     const MemberParams& M = mp[vsc[v0]];
-    if (!M.filter_off && nf > 0) f = frest_contains(frest, row_pt, row_ee, key) ? 1u : 0u;
+    if (!M.filter_off && nf > 0) f = frest_contains(frest_j, row_pt, row_ee, key) ? 1u : 0u;
     uint8_t kl = (uint8_t)f;
     if (f && M.per_stencil) {
       // broad-phase primitive ids: vertices, then triangles, then edges
@@ -2629,8 +2629,17 @@ __global__ void k_frest_rows(int64_t nrows, uint32_t type, const uint64_t* __res
   row[r] = (uint32_t)lo;
 }
 
+// the partner index j of every rest-filtered key (the low 31 bits)
+__global__ void k_frest_j(int64_t nf, const uint64_t* __restrict__ frest, uint32_t* __restrict__ fj) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nf) fj[k] = cb_key_j(frest[k]);
+}
+
 cb_status frest_rows_build(cb_scene* s, cudaStream_t st) {
   if (s->kind != CB_SHELL || s->n_frest <= 0) return CB_OK;
+  CB_TRY(buf_ensure(s->frest_j, sizeof(uint32_t) * (size_t)s->n_frest, st));
+  k_frest_j<<<cb_grid(s->n_frest), CB_THREADS, 0, cb_count(st)>>>(s->n_frest, bp<uint64_t>(s->frest),
+                                                                  bp<uint32_t>(s->frest_j));
   CB_TRY(buf_ensure(s->frow_pt, sizeof(uint32_t) * ((size_t)s->n + 1), st));
   CB_TRY(buf_ensure(s->frow_ee, sizeof(uint32_t) * ((size_t)s->E + 1), st));
   k_frest_rows<<<cb_grid((int64_t)s->n + 1), CB_THREADS, 0, cb_count(st)>>>(s->n, CB_KEY_PT, bp<uint64_t>(s->frest),
@@ -2663,7 +2672,7 @@ cb_status filter_apply(cb_scene* s, cudaStream_t st) {
         bp<uint8_t>(s->klass), nf, SA);
   else
     k_filter_shell<<<cb_grid(nc), CB_THREADS, 0, cb_count(st)>>>(
-        nc, bp<uint64_t>(s->cand), bp<uint64_t>(s->frest), bp<uint32_t>(s->frow_pt), bp<uint32_t>(s->frow_ee),
+        nc, bp<uint64_t>(s->cand), bp<uint32_t>(s->frest_j), bp<uint32_t>(s->frow_pt), bp<uint32_t>(s->frow_ee),
         s->n_frest, bp<int32_t>(s->ev0), bp<int32_t>(s->vsc), bp<MemberParams>(s->mp), bp<uint8_t>(s->klass), nf,
         s->n, s->T, SA);
   CB_CUDA(cudaGetLastError());

@@ -164,6 +164,7 @@ struct cb_scene {
   std::vector<int32_t> geo_te, geo_ef, geo_vfp, geo_vf;
   DevBuf frest;         // uint64 shells: sorted rest-filtered keys
   DevBuf frest_dbar;    // double
+  DevBuf frest_j;       // uint32 shells: the partner index j of each frest key (the rows' search keys)
   DevBuf dbar_comp;     // uint64 bits of the per-component dbar_min, by component label (n entries)
   double dbar_fmax = 0.0;  // largest per-component dbar_min (finite), or dbar_min
   int64_t n_frest = 0;
