@@ -15,6 +15,8 @@ What fixes the values independently of the oracle's method:
     saddle apex (angle sum > 2 pi);
   * on the saddle cone, the edge-edge and point-triangle distances across the
     apex are the sums of the closed-form distances to the apex;
+  * a flat L-shaped sheet: a path whose straight segment would leave the
+    sheet bends at the reflex corner, |p - c| + |c - q|;
   * a Steiner-point graph (points on every edge, straight segments within
     each face) gives paths on the surface: its distances bound the geodesic
     from above and close in on it as the points get denser;
@@ -294,3 +296,51 @@ def test_spherical_cap_second_order():
         hs.append(h)
     order = math.log(errs[0] / errs[1]) / math.log(hs[0] / hs[1])
     assert 1.7 <= order <= 2.3
+
+
+def _l_sheet(n, L):
+    """An L-shaped flat sheet: the (2n+1) x (2n+1) vertex grid of spacing L
+    without its upper-right quadrant's open interior, so (0, 0) is a reflex
+    corner of the boundary (inner angle 3 pi / 2)."""
+    idx, pts = {}, []
+    for j in range(-n, n + 1):
+        for i in range(-n, n + 1):
+            if i > 0 and j > 0:
+                continue
+            idx[(i, j)] = len(pts)
+            pts.append((i * L, j * L, 0.0))
+    tris = []
+    for j in range(-n, n):
+        for i in range(-n, n):
+            q = [(i, j), (i + 1, j), (i + 1, j + 1), (i, j + 1)]
+            if not all(c in idx for c in q):
+                continue
+            tris.append((idx[q[0]], idx[q[1]], idx[q[2]]))
+            tris.append((idx[q[0]], idx[q[2]], idx[q[3]]))
+    return np.array(pts).T, np.array(tris, np.int32).T, idx
+
+
+def test_paths_bend_at_a_reflex_boundary_corner():
+    """On a flat L-shaped sheet the shortest path between two vertices is
+    the straight segment when it stays in the sheet, else the two segments
+    through the reflex corner (0, 0): |p - c| + |c - q|."""
+    n, L = 4, 0.25
+    rest, tris, idx = _l_sheet(n, L)
+    sc = _shell(rest, tris)
+    topo = O.topology(sc)
+    src = (4, -1)   # below the corner, right of it
+    dv, _ = O.geodesic_from(sc, idx[src], 100.0, topo)
+    p = np.array(src, float) * L
+    bent = 0
+    for (i, j), v in idx.items():
+        q = np.array((i, j), float) * L
+        # the segment p -> q leaves the sheet iff it passes through the open
+        # quadrant x > 0, y > 0: for p right of the y axis and below the x
+        # axis, iff q is above the x axis and the corner lies strictly left
+        # of the directed segment p -> q
+        straight = float(np.linalg.norm(q - p))
+        crosses = q[1] > 0 and (q[0] - p[0]) * (0 - p[1]) - (q[1] - p[1]) * (0 - p[0]) > 0
+        exact = float(np.linalg.norm(p)) + float(np.linalg.norm(q)) if crosses else straight
+        bent += crosses
+        assert abs(dv[v] - exact) <= 1e-13 * max(exact, 1.0), ((i, j), dv[v], exact)
+    assert bent >= 8
