@@ -112,3 +112,16 @@ def test_geodesic_with_per_component_widths():
     sc = S.curved_sheet(shape="saddle", nx=24)
     rep = compare(sc, run_gpu(sc, per_component=True), O.contact_pass(sc, per_component=True))
     assert rep["F"] > 0
+
+
+def test_l_shaped_sheet_paths_bend_at_the_corner():
+    """A flat L-shaped sheet: pairs on either side of the reflex corner are
+    as far apart as the path around the corner, on the GPU as in the
+    oracle (an activation off the sums of grid distances)."""
+    from tests.test_oracle_geodesic import _l_sheet
+    rest, tris, _ = _l_sheet(8, 0.1)
+    sc = _shell(rest, tris, a=0.3517)
+    F, d = _check_rest_filter(sc, 2000)
+    sc.rest_geodesic = False
+    Fe, de = O.rest_filter(sc, O.topology(sc), 0.3517)
+    assert F.size < Fe.size   # pairs across the corner are farther apart on the sheet than in space
