@@ -19,7 +19,9 @@ What fixes the values independently of the oracle's method:
     sheet bends at the reflex corner, |p - c| + |c - q|;
   * a Steiner-point graph (points on every edge, straight segments within
     each face) gives paths on the surface: its distances bound the geodesic
-    from above and close in on it as the points get denser;
+    from above and close in on it as the points get denser -- vertex to
+    vertex, vertex to edge, and primitive to primitive for the filtered
+    pairs' dbar;
   * symmetry, the triangle inequality, and geodesic >= 3D distance;
   * a spherical cap: distances approach the great-circle arcs at second
     order in the edge length.
@@ -344,3 +346,42 @@ def test_paths_bend_at_a_reflex_boundary_corner():
         bent += crosses
         assert abs(dv[v] - exact) <= 1e-13 * max(exact, 1.0), ((i, j), dv[v], exact)
     assert bent >= 8
+
+
+def test_pair_distances_within_the_steiner_bound():
+    """dbar of every filtered pair of a bumpy sheet (both curvature signs)
+    lies between the 3D distance of its primitives and the Steiner graph's
+    shortest path between their points (a multi-source search from the
+    first primitive's points), which it approaches from below."""
+    pytest.importorskip("scipy")
+    from scipy.sparse.csgraph import dijkstra
+    sc = _bumpy(7, 0.1, 1)
+    a = 0.3
+    topo = O.topology(sc)
+    F, dbar = O.rest_filter(sc, topo, a)
+    k = 8
+    G, _ = _steiner_graph(sc, k)
+    n, E, T = sc.n, topo.edges.shape[1], sc.tris.shape[1]
+    eid = {(int(u), int(v)): i for i, (u, v) in enumerate(zip(*topo.edges))}
+
+    def edge_nodes(e):
+        return [int(topo.edges[0, e]), int(topo.edges[1, e])] + [n + e * k + j for j in range(k)]
+
+    def tri_edges(t):
+        vs = sc.tris[:, t].tolist()
+        return [eid[(min(vs[q], vs[(q + 1) % 3]), max(vs[q], vs[(q + 1) % 3]))] for q in range(3)]
+    sel = np.random.default_rng(2).choice(F.size, size=min(300, F.size), replace=False)
+    worst = 0.0
+    for c in sel:
+        key = int(F[c])
+        ty, i, j = key >> 62, (key >> 31) & 0x7FFFFFFF, key & 0x7FFFFFFF
+        if ty == O.PT:
+            src = [i]
+            dst = sorted({v for e in tri_edges(j) for v in edge_nodes(e)})
+        else:
+            src, dst = edge_nodes(i), edge_nodes(j)
+        dist = dijkstra(G, directed=False, indices=src, min_only=True)
+        ub = float(np.min(dist[dst]))
+        assert dbar[c] <= ub + 1e-13, (key, dbar[c], ub)
+        worst = max(worst, ub - dbar[c])
+    assert worst <= 0.01
